@@ -1,0 +1,359 @@
+"""Benchmark of the PIC step loop on the 512 (y, periodic) x 1024 (x) trench
+workload: particle-steps/s, the HBM roofline fraction of the fused particle
+kernel, Poisson milliseconds to a 1e-6 relative residual, end-to-end
+throughput through the C ABI from pinned host buffers, and the FP64 oracle
+timed on the host cores.
+
+  python bench.py [--gpus N --steps K --warmup W] [--impl reference]
+
+Under torchrun (N > 1) every rank advances its own trench run (a different
+seed) with no data-path exchange; the aggregate is the sum of the ranks'
+particle-steps over the slowest rank's time (weak scaling).
+"""
+from __future__ import annotations
+
+import argparse
+import hashlib
+import json
+import os
+import statistics
+import subprocess
+import sys
+import threading
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+if ROOT not in sys.path:
+    sys.path.insert(0, ROOT)
+
+import synth  # noqa: E402
+
+METRIC = "particle-steps/s & %HBM roofline (trench cfg); Poisson ms to 1e-6 residual"
+UNIT = "particle-steps/s"
+# Algorithmic bytes of the fused particle kernel per particle-step: the
+# 20-byte state (int32 cell, FP32 fx, fy, vx, vy) read once and written once.
+BYTES_PER_PARTICLE_STEP = 40
+# DRAM bytes per live particle of the fused particle kernel from one ncu
+# capture (dram__bytes_read.sum + dram__bytes_write.sum over the launch),
+# valid for the kernel source whose hash is recorded with it.
+NCU_TRAFFIC = {"source_sha256": None, "bytes_per_particle": None}
+
+
+def _peaks():
+    p = os.path.join(ROOT, "MEASURED_PEAKS.json")
+    if os.path.exists(p):
+        d = json.load(open(p))
+        return float(d["hbm_gbs"]), "measured"
+    return 6800.0, "fallback"
+
+
+def _kernel_sha():
+    src = os.path.join(ROOT, "paper_1610_03918_gb300", "csrc", "particles.cu")
+    return hashlib.sha256(open(src, "rb").read()).hexdigest()
+
+
+class ClockSampler:
+    """nvidia-smi clocks and throttle reasons sampled during the timed region."""
+
+    FIELDS = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+              "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+              "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, device: int):
+        self.device = device
+        self.proc = None
+        self.lines = []
+
+    def start(self):
+        try:
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
+                 "--format=csv,noheader,nounits", "-lms", "200"],
+                stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
+            self.thread = threading.Thread(target=self._read, daemon=True)
+            self.thread.start()
+        except OSError:
+            self.proc = None
+
+    def _read(self):
+        for line in self.proc.stdout:
+            self.lines.append(line.strip())
+
+    def stop(self):
+        if self.proc is None:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["nvidia-smi unavailable"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except subprocess.TimeoutExpired:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ("hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap")
+        for ln in self.lines:
+            parts = [p.strip() for p in ln.split(",")]
+            if len(parts) < 9:
+                continue
+            try:
+                sm.append(float(parts[1]))
+                smax.append(float(parts[2]))
+            except ValueError:
+                continue
+            for name, v in zip(names, parts[5:9]):
+                if v.lower() == "active":
+                    reasons.add(name)
+        return {"sm_mhz": statistics.median(sm) if sm else None,
+                "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+def _dist():
+    ws = int(os.environ.get("WORLD_SIZE", "1"))
+    if ws <= 1:
+        return None, 0, 1
+    import torch.distributed as dist
+    dist.init_process_group("nccl")
+    return dist, dist.get_rank(), ws
+
+
+def _reduce_max(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def _reduce_sum(dist, v):
+    if dist is None:
+        return v
+    import torch
+    t = torch.tensor([v], dtype=torch.float64, device="cuda")
+    dist.all_reduce(t, op=dist.ReduceOp.SUM)
+    return float(t.item())
+
+
+def _barrier(dist):
+    if dist is not None:
+        import torch
+        torch.cuda.synchronize()
+        dist.barrier()
+
+
+def oracle_baseline(w, seconds_budget=20.0, n_sample=1_000_000, steps=2):
+    """The FP64 oracle as it stands on a bounded sample of the workload: the
+    full 512x1024 trench grid (factorisation outside the timing) with
+    n_sample particles per species, timed over `steps` steps."""
+    from oracle.sim import Sim as OracleSim
+    from oracle import poisson
+    os_ = OracleSim(w)
+    for s in (0, 1):
+        p = synth.random_state(w, s, n_sample, seed=w.seed + 17)
+        os_.load_particles(s, p)
+    poisson.solve_direct(os_.geom, np.zeros((os_.geom.nxn, os_.geom.nyn)))   # factorise
+    os_.prepare()
+    t0 = time.perf_counter()
+    done = 0
+    while done < steps:
+        live = int(os_.live().sum())
+        os_.step(1)
+        done += 1
+        if time.perf_counter() - t0 > seconds_budget:
+            break
+    dt = time.perf_counter() - t0
+    ps = live * done / dt
+    return {"value": ps, "unit": UNIT, "cores": 1, "kind": "oracle",
+            "sample": f"{w.name}: full grid, {n_sample} particles/species "
+                      f"(of {int(synth.plasma_cells(w).sum()) * w.ppc}), {done} steps, "
+                      f"{dt:.1f} s; numpy/scipy single-threaded"}
+
+
+def run_reference(args):
+    """The oracle as it stands on the host cores, on the trench workload's
+    full grid with a bounded particle sample, one oracle step per step."""
+    dist, rank, ws = _dist()
+    if rank != 0:
+        return 0
+    from oracle.sim import Sim as OracleSim
+    from oracle import poisson
+    w = synth.trench_512x1024()
+    n_sample = 100_000
+    t_start = time.perf_counter()
+    os_ = OracleSim(w)
+    for s in (0, 1):
+        os_.load_particles(s, synth.random_state(w, s, n_sample, seed=w.seed + 17))
+    poisson.solve_direct(os_.geom, np.zeros((os_.geom.nxn, os_.geom.nyn)))   # factorise once
+    os_.prepare()
+    os_.step(max(args.warmup, 0))
+    live = []
+    t0 = time.perf_counter()
+    for _ in range(args.steps):
+        live.append(int(os_.live().sum()))
+        os_.step(1)
+    dt = time.perf_counter() - t0
+    v = float(np.sum(live)) / dt
+    sample = (f"full 512x1024 trench grid (sparse LU factorised once, untimed), "
+              f"{n_sample} particles/species of {int(synth.plasma_cells(w).sum()) * w.ppc}, "
+              f"{args.steps} oracle steps in {dt:.1f} s")
+    line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f64",
+            "data": "synthetic", "config": {"workload": w.name},
+            "cpu_baseline": {"value": v, "unit": UNIT, "cores": 1, "kind": "oracle",
+                             "sample": sample},
+            "e2e": {"value": v, "unit": UNIT, "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+            "wall_s": time.perf_counter() - t_start}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--warmup", type=int, default=20)
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--ppc", type=int, default=None, help="override particles per cell")
+    args = ap.parse_args()
+    if args.impl == "reference":
+        return run_reference(args)
+    args.warmup = max(args.warmup, 3)
+
+    dist, rank, ws = _dist()
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0 or dist is None:
+        __graft_entry__.build()
+    _barrier(dist)
+    import paper_1610_03918_gb300 as pg
+
+    w = synth.trench_512x1024(seed=3 + rank)
+    if args.ppc:
+        w = w.replace(ppc=args.ppc)
+    parts = [synth.maxwellian_load(w, s) for s in (0, 1)]
+    n0 = sum(len(p) for p in parts)
+    sim = pg.Sim(w, capacity=len(parts[0]), device=local)
+    for s in (0, 1):
+        sim.load_particles(s, parts[s], v_at_t0=True)
+    sim.step(args.warmup)
+    sim.timing()
+    live0 = int(sim.counts()[1].sum())
+
+    clocks = ClockSampler(local)
+    clocks.start()
+    _barrier(dist)
+    stream = sim.torch_stream
+    ev0 = torch.cuda.Event(enable_timing=True)
+    ev1 = torch.cuda.Event(enable_timing=True)
+    torch.cuda.synchronize()
+    if stream is not None:
+        ev0.record(stream)
+    else:
+        ev0.record()
+    sim.step(args.steps)
+    if stream is not None:
+        ev1.record(stream)
+    else:
+        ev1.record()
+    torch.cuda.synchronize()
+    _barrier(dist)
+    ms = ev0.elapsed_time(ev1)
+    clk = clocks.stop()
+    tm = sim.timing()
+    live1 = int(sim.counts()[1].sum())
+    pstats = sim.poisson_stats()
+
+    live_mean = 0.5 * (live0 + live1)
+    ps_local = live_mean * args.steps
+    ms_max = _reduce_max(dist, ms)
+    ps_total = _reduce_sum(dist, ps_local)
+    value = ps_total / (ms_max * 1e-3)
+
+    # roofline of the dominant kernel (fused gather/push/absorb/deposit)
+    peak, peak_kind = _peaks()
+    part_ms = tm["ms_particles"] / max(tm["steps"], 1)
+    achieved = BYTES_PER_PARTICLE_STEP * live_mean / (part_ms * 1e-3) / 1e9
+    traffic = None
+    if NCU_TRAFFIC["source_sha256"] == _kernel_sha() and NCU_TRAFFIC["bytes_per_particle"]:
+        traffic = NCU_TRAFFIC["bytes_per_particle"] * live_mean
+
+    # end to end through the C ABI with pinned host buffers: every step loads
+    # the full state from the host, advances one step, reads the energies back
+    e2e = None
+    if args.e2e_steps > 0:
+        st = [sim.state(s) for s in (0, 1)]
+        pinned = []
+        h2d = 0
+        for s in (0, 1):
+            n = st[s].shape[1]
+            bufs = [torch.empty(n, dtype=torch.float64, pin_memory=True).numpy() for _ in range(4)]
+            for k in range(4):
+                bufs[k][:] = st[s][k]
+            ids = torch.empty(n, dtype=torch.int32, pin_memory=True).numpy().view(np.uint32)
+            ids[:] = st[s][4].astype(np.uint32)
+            pinned.append((bufs, ids))
+            h2d += n * (4 * 8 + 4)
+        out = torch.empty(4, dtype=torch.float64, pin_memory=True).numpy()
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for s in (0, 1):
+                bufs, ids = pinned[s]
+                sim.load(s, bufs[0], bufs[1], bufs[2], bufs[3], ids)
+            sim.step(1)
+            sim.diag(pg.PIC_DIAG_ENERGY, out)
+        t_e2e = time.perf_counter() - t0
+        n_state = sum(p[0][0].size for p in pinned)
+        e2e_val = _reduce_sum(dist, n_state * args.e2e_steps) / _reduce_max(dist, t_e2e)
+        e2e = {"value": e2e_val, "unit": UNIT, "h2d_bytes_per_step": int(h2d),
+               "d2h_bytes_per_step": 32,
+               "note": "per step: pic_load of the full state from pinned host memory "
+                       "(which re-deposits and re-solves), pic_step(1), pic_diag(ENERGY)"}
+
+    cpu = None
+    if rank == 0 and not args.no_cpu_baseline:
+        cpu = oracle_baseline(synth.trench_512x1024())
+
+    if rank == 0:
+        line = {
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws,
+            "steps": args.steps, "warmup": args.warmup, "ms_per_step": ms_max / args.steps,
+            "higher_is_better": True, "scaling": "weak", "vs_baseline": None, "dtype": "f32",
+            "data": "synthetic",
+            "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "ppc": w.ppc,
+                       "particles_loaded": n0, "live_particles": live_mean,
+                       "sort_every": w.sort_every, "poisson_rtol": w.poisson_rtol,
+                       "l2": "inputs larger than L2 (particle state %.1f GB)" % (n0 * 24 / 1e9),
+                       "parallelism": f"replicas{ws}" if ws > 1 else "single"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": traffic,
+                         "kernel": "k_particles<0> (gather+push+absorb+deposit)",
+                         "peak_kind": peak_kind, "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP},
+            "phases_ms_per_step": {
+                "particles": part_ms,
+                "sort": tm["ms_sort"] / max(tm["steps"], 1),
+                "poisson": tm["ms_poisson"] / max(tm["steps"], 1),
+                "rho_field": tm["ms_rho_field"] / max(tm["steps"], 1),
+            },
+            "poisson_ms_to_1e-6": tm["ms_poisson"] / max(tm["steps"], 1),
+            "poisson_last": {"iterations": pstats[0], "outer": pstats[1], "rel_residual": pstats[2]},
+            "gpu_launches": int(tm["launches"]),
+            "clocks": clk,
+            "e2e": e2e,
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    sim.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
+if __name__ == "__main__":
+    sys.exit(main())

@@ -1,0 +1,185 @@
+/*
+ * picgb.h -- C ABI of the GB300-native 2D electrostatic PIC step loop.
+ *
+ * The library advances the paper's two-dimensional electrostatic
+ * particle-in-cell model (Lin & Nishimura, arXiv:1610.03918): kinetic
+ * electrons and one ion species in Debye-length / inverse-plasma-frequency
+ * units (Sec. II), between a grounded plate at x = 0 and an electrode at
+ * x = nx, optionally periodic in y (Sec. III-B), with a trench cut into the
+ * electrode (Sec. III-C).  One step is
+ *
+ *   gather E^n -> leapfrog kick + drift (Eqs. 1-4) -> absorption at walls
+ *   and conductors with per-wall tallies and bottom surface charge
+ *   (Sec. III-A, III-C, III-D) -> cloud-in-cell deposit of rho^{n+1} ->
+ *   Poisson solve of Eq. 5 on the conductor-masked grid -> E^{n+1} = -grad Phi
+ *   (central differences inside, two-point at boundaries, Sec. II).
+ *
+ * Conventions: x is normal to the plates, y runs along them.  A bounded
+ * direction with N cells has N + 1 nodes, a periodic one N nodes.  Node and
+ * cell arrays are row-major [i_x][j_y], y fastest.  Positions are absolute
+ * (a particle at x lies in cell floor(x)).
+ *
+ * Ownership: every pointer argument is owned by the caller.  Host arrays
+ * are copied in or out before the call returns.  Device memory is owned by
+ * the library (allocated in pic_init through cfg->alloc, or cudaMalloc when
+ * alloc is NULL) and released by pic_free.
+ *
+ * Errors: every entry point returns a pic_status.  Kernels record
+ * conditions they detect (non-convergence, full hit buffer, particle moved
+ * farther than the walk limit, out-of-range input) as sticky bits of a
+ * device status word; the next synchronising call (pic_diag, or pic_step
+ * when it polls the Poisson solver) returns the matching status, and
+ * PIC_DIAG_STATUS reads and clears the word.  No entry point is thread-safe
+ * for one context; distinct contexts are independent.
+ */
+#ifndef PICGB_H
+#define PICGB_H
+
+#include <stddef.h>
+#include <stdint.h>
+
+#ifdef __cplusplus
+extern "C" {
+#endif
+
+typedef struct pic_ctx pic_ctx;
+
+typedef enum {
+  PIC_OK = 0,
+  PIC_EINVAL = 1,     /* bad argument or configuration */
+  PIC_ENOMEM = 2,     /* allocation failed */
+  PIC_ECUDA = 3,      /* a CUDA call failed */
+  PIC_ENOCONV = 4,    /* Poisson solve hit its iteration cap above rtol */
+  PIC_EOVERFLOW = 5,  /* capacity of a particle store exceeded */
+  PIC_ECFL = 6,       /* a particle moved farther than the face-walk limit */
+  PIC_ETIMEOUT = 7,   /* reserved: a bounded device wait gave up */
+  PIC_EFULL = 8,      /* hit-record buffer full (tallies stay exact) */
+  PIC_ESTATE = 9,     /* call not valid in the current state */
+  PIC_ERANGE = 10     /* pic_load got a particle outside the plasma region */
+} pic_status;
+
+/* Status-word bits (PIC_DIAG_STATUS). */
+#define PIC_ST_NOCONV   (1u << 0)
+#define PIC_ST_FULL     (1u << 1)
+#define PIC_ST_CFL      (1u << 2)
+#define PIC_ST_RANGE    (1u << 3)
+#define PIC_ST_CAPACITY (1u << 4)
+
+/* Wall identifiers of the absorption tallies.  A particle's move is the
+ * straight segment x^n -> x^{n+1}; the first crossed face whose far cell is
+ * a conductor or outside a bounded direction absorbs it (x face first on an
+ * exact tie; ending exactly on a face counts as being in the higher cell). */
+#define PIC_WALL_XMIN     0 /* x = 0 plate */
+#define PIC_WALL_XMAX     1 /* x = nx plate; the trench bottom inside the trench */
+#define PIC_WALL_YMIN     2 /* y = 0 wall (bounded y only) */
+#define PIC_WALL_YMAX     3 /* y = ny wall (bounded y only) */
+#define PIC_WALL_COND_PX  4 /* conductor entered moving +x (electrode top) */
+#define PIC_WALL_COND_MX  5 /* conductor entered moving -x */
+#define PIC_WALL_COND_PY  6 /* conductor entered moving +y (trench wall at its upper y) */
+#define PIC_WALL_COND_MY  7 /* conductor entered moving -y (trench wall at its lower y) */
+#define PIC_NWALLS        8
+
+typedef struct {
+  int32_t nx, ny;                 /* cells along x (normal to the plates) and y */
+  int32_t periodic_x, periodic_y; /* 1 = periodic (Sec. III-B), 0 = bounded */
+  double dt;                      /* time step in 1/omega_e (Sec. III-A: 0.1) */
+  double phi_top;                 /* Dirichlet value of the x = 0 plate, T_e/e */
+  double phi_electrode;           /* x = nx plate and electrode slab value */
+  int32_t trench_depth;           /* electrode slab thickness: cells i >= nx - depth */
+  int32_t trench_y0;              /* first open column of the trench */
+  int32_t trench_width;           /* open columns (0: flat slab) */
+  int32_t surface_charge;         /* 1: charge collected on the x = nx face feeds rho */
+  double alpha[2];                /* Eqs. 1-2: alpha_e = -1, alpha_i = (m_e/m_i)(q_i/e) */
+  double charge[2];               /* species charge in units of e: {-1, +1} */
+  int32_t ppc[2];                 /* particles per cell at density n_0: weight = 1/ppc */
+  int64_t capacity[2];            /* maximum particles per species */
+  int32_t sort_every;             /* steps between tile sorts (>= 1) */
+  int32_t poisson_maxit;          /* cap on inner PCG iterations per solve */
+  double poisson_rtol;            /* target ||b - A phi||_2 / ||b||_2 (FP64) */
+  int32_t warm_start;             /* 0: zero initial guess each solve, 1: previous phi */
+  int32_t device;                 /* CUDA device ordinal */
+  int64_t hit_capacity;           /* hit records kept (PIC_DIAG_HITS) */
+  void *stream;                   /* cudaStream_t to run on; NULL: a library-owned stream */
+  void *(*alloc)(size_t bytes, void *user); /* optional device allocator */
+  void (*free)(void *ptr, void *user);      /* its release function */
+  void *alloc_user;
+} pic_config;
+
+/* One absorbed particle (PIC_DIAG_HITS): velocity is v^{n+1/2}. */
+typedef struct {
+  uint32_t id;
+  int16_t species;
+  int16_t wall;     /* PIC_WALL_* */
+  int32_t cell;     /* cell index along the wall: y index for x faces, x index for y faces */
+  int32_t step;     /* step during which the particle was absorbed (0-based) */
+  float vx, vy;
+} pic_hit;
+
+/* Load flags */
+#define PIC_LOAD_V_AT_T0 1u /* velocities are v^0: back-kick by dt/2 before the first step */
+
+/* Diagnostic kinds for pic_diag.  Unless stated, out receives doubles. */
+enum {
+  PIC_DIAG_ENERGY = 0,   /* [KE_e, KE_i, FE, n]: of the last step, time level n (see below) */
+  PIC_DIAG_MOMENTUM = 1, /* [Px_e, Py_e, Px_i, Py_i] = m_s w_s sum v^{n+1/2} */
+  PIC_DIAG_COUNTS = 2,   /* int64[2*8 + 2]: wall tallies [species][wall], then live counts */
+  PIC_DIAG_SURFACE = 3,  /* int64[2*ny]: hits on the x = nx face per species per y cell */
+  PIC_DIAG_HITS = 4,     /* pic_hit[n_out] (the first hit_capacity records) */
+  PIC_DIAG_RHO = 5,      /* [nxn*nyn]: net charge density of the last deposit */
+  PIC_DIAG_PHI = 6,      /* [nxn*nyn]: potential (FP64 master copy) */
+  PIC_DIAG_E = 7,        /* [2*nxn*nyn]: Ex then Ey at the nodes */
+  PIC_DIAG_STATE_E = 8,  /* [5*n]: x, y, vx, vy, id blocks of live electrons */
+  PIC_DIAG_STATE_I = 9,  /* same for ions */
+  PIC_DIAG_POISSON = 10, /* [inner iterations, outer iterations, rel residual, ms] of the last solve */
+  PIC_DIAG_STATUS = 11,  /* uint32: status word; reading clears it */
+  PIC_DIAG_TIMING = 12   /* [steps, ms particle kernel, ms sort, ms Poisson, ms rho+field,
+                            sorts, kernel launches, particle slots processed]: device time
+                            from CUDA events on the context stream, accumulated over
+                            pic_step calls since the last read; reading resets it */
+};
+
+/* Create a context from cfg.  Builds the conductor mask, Dirichlet nodes and
+ * multigrid hierarchy of the geometry (Sec. III), allocates device memory.
+ * Returns PIC_EINVAL for an inconsistent configuration. */
+pic_status pic_init(const pic_config *cfg, pic_ctx **out);
+
+/* Replace the particles of species s (0 electrons, 1 ions) by n particles at
+ * absolute positions (x, y) with velocities (vx, vy); ids may be NULL
+ * (0..n-1).  All arrays are host memory of length n.  Initial state per
+ * Sec. III-A (uniform positions, Eq. 6 velocities) is the caller's choice.
+ * With flags & PIC_LOAD_V_AT_T0 the velocities are taken at t = 0 and the
+ * species is back-kicked by dt/2 in the field of the full loaded state
+ * before the next step (leapfrog start).
+ * species == -1 loads a fixed external charge density rho_ext (Sec. III-D)
+ * from x[nxn*nyn]; the other pointers are ignored.
+ * Particles outside the domain or in a conductor are dropped and counted
+ * in the PIC_ST_RANGE bit; n > capacity returns PIC_EOVERFLOW. */
+pic_status pic_load(pic_ctx *ctx, int32_t species, int64_t n, const double *x,
+                    const double *y, const double *vx, const double *vy,
+                    const uint32_t *ids, uint32_t flags);
+
+/* Advance nsteps leapfrog steps (Sec. II).  nsteps == 0 only brings the
+ * fields up to date with the loaded state (deposit, Poisson solve, E) and
+ * applies pending dt/2 back-kicks.  Work is queued on the context's stream;
+ * the call returns once it is queued, except that it waits on the Poisson
+ * solver's convergence flag. */
+pic_status pic_step(pic_ctx *ctx, int32_t nsteps);
+
+/* Copy a diagnostic to host memory out (cap_bytes long); *n_out receives the
+ * element count written (may be NULL).  Synchronises the stream.
+ * ENERGY: KE_s = 1/2 m_s w_s sum v^{n-1/2}.v^{n+1/2}, FE = 1/2 sum_nodes |E^n|^2,
+ * m_s = charge_s / alpha_s, w_s = 1/ppc_s.  Too small a buffer: PIC_EINVAL. */
+pic_status pic_diag(pic_ctx *ctx, int32_t kind, void *out, int64_t cap_bytes,
+                    int64_t *n_out);
+
+/* Release the context and all its device memory. */
+pic_status pic_free(pic_ctx *ctx);
+
+/* Static description of a status code. */
+const char *pic_strerror(pic_status st);
+
+#ifdef __cplusplus
+}
+#endif
+
+#endif /* PICGB_H */

@@ -1,0 +1,321 @@
+"""Python binding of the GB300-native 2D electrostatic PIC library.
+
+Argument marshalling only: every step of the loop (sort, gather, push,
+absorption, deposit, Poisson solve, field) runs in the sm_103a kernels of
+``libpicgb.so`` behind the C ABI of ``include/picgb.h``.  The functions
+carry the C names (pic_init, pic_load, pic_step, pic_diag, pic_free,
+pic_strerror); ``Sim`` strings them together.  Device memory is drawn from
+PyTorch's caching allocator and work runs on PyTorch's current CUDA stream
+unless told otherwise.
+
+There is no CPU fallback: if the library was not built, or no GPU is
+visible, loading it raises.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import numpy as np
+
+from .build import lib_path
+
+# status codes and constants mirrored from include/picgb.h
+PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ENOCONV = 0, 1, 2, 3, 4
+PIC_EOVERFLOW, PIC_ECFL, PIC_ETIMEOUT, PIC_EFULL, PIC_ESTATE, PIC_ERANGE = 5, 6, 7, 8, 9, 10
+PIC_ST_NOCONV, PIC_ST_FULL, PIC_ST_CFL, PIC_ST_RANGE, PIC_ST_CAPACITY = 1, 2, 4, 8, 16
+PIC_LOAD_V_AT_T0 = 1
+(PIC_DIAG_ENERGY, PIC_DIAG_MOMENTUM, PIC_DIAG_COUNTS, PIC_DIAG_SURFACE, PIC_DIAG_HITS,
+ PIC_DIAG_RHO, PIC_DIAG_PHI, PIC_DIAG_E, PIC_DIAG_STATE_E, PIC_DIAG_STATE_I,
+ PIC_DIAG_POISSON, PIC_DIAG_STATUS, PIC_DIAG_TIMING) = range(13)
+(WALL_XMIN, WALL_XMAX, WALL_YMIN, WALL_YMAX, WALL_COND_PX, WALL_COND_MX,
+ WALL_COND_PY, WALL_COND_MY) = range(8)
+
+EXPORTED = ("pic_init", "pic_load", "pic_step", "pic_diag", "pic_free", "pic_strerror")
+
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+class PicConfig(ctypes.Structure):
+    _fields_ = [
+        ("nx", ctypes.c_int32), ("ny", ctypes.c_int32),
+        ("periodic_x", ctypes.c_int32), ("periodic_y", ctypes.c_int32),
+        ("dt", ctypes.c_double),
+        ("phi_top", ctypes.c_double), ("phi_electrode", ctypes.c_double),
+        ("trench_depth", ctypes.c_int32), ("trench_y0", ctypes.c_int32),
+        ("trench_width", ctypes.c_int32), ("surface_charge", ctypes.c_int32),
+        ("alpha", ctypes.c_double * 2), ("charge", ctypes.c_double * 2),
+        ("ppc", ctypes.c_int32 * 2),
+        ("capacity", ctypes.c_int64 * 2),
+        ("sort_every", ctypes.c_int32), ("poisson_maxit", ctypes.c_int32),
+        ("poisson_rtol", ctypes.c_double),
+        ("warm_start", ctypes.c_int32), ("device", ctypes.c_int32),
+        ("hit_capacity", ctypes.c_int64),
+        ("stream", ctypes.c_void_p),
+        ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+    ]
+
+
+class PicHit(ctypes.Structure):
+    _fields_ = [("id", ctypes.c_uint32), ("species", ctypes.c_int16), ("wall", ctypes.c_int16),
+                ("cell", ctypes.c_int32), ("step", ctypes.c_int32),
+                ("vx", ctypes.c_float), ("vy", ctypes.c_float)]
+
+
+HIT_DTYPE = np.dtype([("id", np.uint32), ("species", np.int16), ("wall", np.int16),
+                      ("cell", np.int32), ("step", np.int32), ("vx", np.float32),
+                      ("vy", np.float32)])
+
+_lib = None
+
+
+def load_library():
+    """Load libpicgb.so (built by paper_1610_03918_gb300.build); raises if absent."""
+    global _lib
+    if _lib is not None:
+        return _lib
+    path = lib_path()
+    if not os.path.exists(path):
+        raise RuntimeError(f"CUDA library not built: {path} is missing "
+                           "(run __graft_entry__.build())")
+    lib = ctypes.CDLL(path)
+    P = ctypes.c_void_p
+    D = ctypes.POINTER(ctypes.c_double)
+    lib.pic_init.argtypes = [ctypes.POINTER(PicConfig), ctypes.POINTER(ctypes.c_void_p)]
+    lib.pic_load.argtypes = [P, ctypes.c_int32, ctypes.c_int64, D, D, D, D,
+                             ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32]
+    lib.pic_step.argtypes = [P, ctypes.c_int32]
+    lib.pic_diag.argtypes = [P, ctypes.c_int32, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    lib.pic_free.argtypes = [P]
+    lib.pic_strerror.argtypes = [ctypes.c_int]
+    lib.pic_strerror.restype = ctypes.c_char_p
+    for name in ("pic_init", "pic_load", "pic_step", "pic_diag", "pic_free"):
+        getattr(lib, name).restype = ctypes.c_int
+    _lib = lib
+    return lib
+
+
+class PicError(RuntimeError):
+    def __init__(self, code, where):
+        self.code = code
+        super().__init__(f"{where}: {pic_strerror(code)} ({code})")
+
+
+def pic_strerror(code: int) -> str:
+    return load_library().pic_strerror(int(code)).decode()
+
+
+def _dptr(a):
+    return a.ctypes.data_as(ctypes.POINTER(ctypes.c_double)) if a is not None else None
+
+
+def pic_init(cfg: PicConfig) -> ctypes.c_void_p:
+    ctx = ctypes.c_void_p()
+    st = load_library().pic_init(ctypes.byref(cfg), ctypes.byref(ctx))
+    if st != PIC_OK:
+        raise PicError(st, "pic_init")
+    return ctx
+
+
+def pic_load(ctx, species: int, x, y=None, vx=None, vy=None, ids=None, flags: int = 0) -> int:
+    x = np.ascontiguousarray(x, dtype=np.float64)
+    n = x.size
+    arrs = [np.ascontiguousarray(a, dtype=np.float64) if a is not None else None
+            for a in (y, vx, vy)]
+    idp = None
+    if ids is not None:
+        ids = np.ascontiguousarray(ids, dtype=np.uint32)
+        idp = ids.ctypes.data_as(ctypes.POINTER(ctypes.c_uint32))
+    return load_library().pic_load(ctx, int(species), int(n), _dptr(x), *[_dptr(a) for a in arrs],
+                                   idp, int(flags))
+
+
+def pic_step(ctx, nsteps: int) -> int:
+    return load_library().pic_step(ctx, int(nsteps))
+
+
+def pic_diag(ctx, kind: int, out: np.ndarray):
+    """Fill ``out`` (a contiguous numpy array) and return (status, count)."""
+    n = ctypes.c_int64(0)
+    st = load_library().pic_diag(ctx, int(kind), out.ctypes.data_as(ctypes.c_void_p),
+                                 int(out.nbytes), ctypes.byref(n))
+    return st, int(n.value)
+
+
+def pic_free(ctx) -> int:
+    return load_library().pic_free(ctx)
+
+
+# ---------------------------------------------------------------------------
+class _TorchAllocator:
+    """Device memory from PyTorch's caching allocator on the given stream."""
+
+    def __init__(self, device: int, stream: int):
+        import torch
+        self.torch = torch
+        self.device = device
+        self.stream = stream
+
+        def _alloc(nbytes, user):
+            try:
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+            except Exception:
+                return None
+
+        def _free(ptr, user):
+            torch.cuda.caching_allocator_delete(int(ptr))
+
+        self.alloc = ALLOC_FN(_alloc)
+        self.free = FREE_FN(_free)
+
+
+def make_config(w, capacity=None, device: int = 0, stream=None, hit_capacity: int = 1 << 20,
+                poisson_maxit: int = 200, warm_start: int = 1, allocator=None) -> PicConfig:
+    """PicConfig from a workload description (an object with the fields of
+    synth.Workload)."""
+    cfg = PicConfig()
+    cfg.nx, cfg.ny = int(w.nx), int(w.ny)
+    cfg.periodic_x, cfg.periodic_y = int(w.periodic_x), int(w.periodic_y)
+    cfg.dt = float(w.dt)
+    cfg.phi_top, cfg.phi_electrode = float(w.phi_top), float(w.phi_electrode)
+    cfg.trench_depth, cfg.trench_y0 = int(w.trench_depth), int(w.trench_y0)
+    cfg.trench_width = int(w.trench_width)
+    cfg.surface_charge = int(bool(w.surface_charge))
+    cfg.alpha[0], cfg.alpha[1] = w.alpha
+    cfg.charge[0], cfg.charge[1] = w.charge
+    cfg.ppc[0] = cfg.ppc[1] = int(w.ppc)
+    if capacity is None:
+        capacity = int(w.nx) * int(w.ny) * int(w.ppc)
+    cfg.capacity[0] = cfg.capacity[1] = int(capacity)
+    cfg.sort_every = int(getattr(w, "sort_every", 8))
+    cfg.poisson_maxit = int(poisson_maxit)
+    cfg.poisson_rtol = float(getattr(w, "poisson_rtol", 1e-6))
+    cfg.warm_start = int(warm_start)
+    cfg.device = int(device)
+    cfg.hit_capacity = int(hit_capacity)
+    cfg.stream = stream
+    if allocator is not None:
+        cfg.alloc = allocator.alloc
+        cfg.free = allocator.free
+    return cfg
+
+
+class Sim:
+    """One simulation context.  ``torch_memory``: allocate through PyTorch's
+    caching allocator and run on PyTorch's current stream of ``device``."""
+
+    def __init__(self, w, capacity=None, device: int = 0, torch_memory: bool = True, **kw):
+        load_library()
+        self.w = w
+        self._allocator = None
+        stream = None
+        self.torch_stream = None
+        if torch_memory:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device visible")
+            torch.cuda.set_device(device)
+            # a stream of its own, shared by the library and the allocator
+            self.torch_stream = torch.cuda.Stream(device)
+            stream = self.torch_stream.cuda_stream
+            self._allocator = _TorchAllocator(device, stream)
+        self.cfg = make_config(w, capacity=capacity, device=device, stream=stream,
+                               allocator=self._allocator, **kw)
+        self.ctx = pic_init(self.cfg)
+        self.nxn = w.nx if w.periodic_x else w.nx + 1
+        self.nyn = w.ny if w.periodic_y else w.ny + 1
+
+    def close(self):
+        if self.ctx:
+            pic_free(self.ctx)
+            self.ctx = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+    def _check(self, st, where, allow=()):
+        if st != PIC_OK and st not in allow:
+            raise PicError(st, where)
+        return st
+
+    def load(self, species, x, y, vx, vy, ids=None, v_at_t0=False, allow=()):
+        return self._check(pic_load(self.ctx, species, x, y, vx, vy, ids,
+                                    PIC_LOAD_V_AT_T0 if v_at_t0 else 0), "pic_load", allow)
+
+    def load_particles(self, species, p, v_at_t0=False, allow=()):
+        return self.load(species, p.x, p.y, p.vx, p.vy, p.ids, v_at_t0, allow)
+
+    def set_rho_ext(self, rho_ext):
+        return self._check(pic_load(self.ctx, -1, np.asarray(rho_ext, np.float64).ravel()),
+                           "pic_load(rho_ext)")
+
+    def step(self, n=1, allow=()):
+        return self._check(pic_step(self.ctx, n), "pic_step", allow)
+
+    def diag(self, kind, out, allow=(PIC_EFULL, PIC_ERANGE)):
+        st, n = pic_diag(self.ctx, kind, out)
+        self._check(st, "pic_diag", allow)
+        return out, n
+
+    # convenience views -------------------------------------------------
+    def grid(self, kind):
+        out = np.empty((self.nxn, self.nyn), np.float64)
+        return self.diag(kind, out)[0]
+
+    def rho(self):
+        return self.grid(PIC_DIAG_RHO)
+
+    def phi(self):
+        return self.grid(PIC_DIAG_PHI)
+
+    def efield(self):
+        out = np.empty((2, self.nxn, self.nyn), np.float64)
+        self.diag(PIC_DIAG_E, out)
+        return out[0], out[1]
+
+    def energy(self):
+        return self.diag(PIC_DIAG_ENERGY, np.empty(4))[0]
+
+    def momentum(self):
+        return self.diag(PIC_DIAG_MOMENTUM, np.empty(4))[0].reshape(2, 2)
+
+    def counts(self):
+        out = self.diag(PIC_DIAG_COUNTS, np.empty(18, np.int64))[0]
+        return out[:16].reshape(2, 8), out[16:]
+
+    def surface(self):
+        return self.diag(PIC_DIAG_SURFACE, np.empty(2 * self.w.ny, np.int64))[0].reshape(2, -1)
+
+    def hits(self, cap=None):
+        cap = int(self.cfg.hit_capacity if cap is None else cap)
+        out = np.empty(cap, HIT_DTYPE)
+        _, n = self.diag(PIC_DIAG_HITS, out)
+        return out[:n]
+
+    def state(self, species):
+        live = self.counts()[1][species]
+        out = np.empty((5, int(live)), np.float64)
+        self.diag(PIC_DIAG_STATE_E if species == 0 else PIC_DIAG_STATE_I, out)
+        return out
+
+    def poisson_stats(self):
+        return self.diag(PIC_DIAG_POISSON, np.empty(4))[0]
+
+    def timing(self):
+        """Per-phase device time since the last call (and resets it):
+        dict of steps, ms_particles, ms_sort, ms_poisson, ms_rho_field,
+        sorts, launches, slots."""
+        v = self.diag(PIC_DIAG_TIMING, np.empty(8))[0]
+        keys = ("steps", "ms_particles", "ms_sort", "ms_poisson", "ms_rho_field", "sorts",
+                "launches", "slots")
+        return dict(zip(keys, v.tolist()))
+
+    def status(self):
+        out = np.zeros(1, np.uint32)
+        st, _ = pic_diag(self.ctx, PIC_DIAG_STATUS, out)
+        self._check(st, "pic_diag(status)")
+        return int(out[0])

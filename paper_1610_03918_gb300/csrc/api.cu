@@ -1,0 +1,637 @@
+// C ABI: context set-up (geometry of Sec. III), particle loading, the step
+// driver and diagnostics.  Kernels live in particles.cu and poisson.cu.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace picgb {
+
+void *dev_alloc(pic_ctx *c, size_t bytes) {
+  if (bytes == 0) bytes = 16;
+  bytes = (bytes + 255) & ~size_t(255);
+  void *p = nullptr;
+  if (c->cfg.alloc) {
+    p = c->cfg.alloc(bytes, c->cfg.alloc_user);
+  } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
+    p = nullptr;
+  }
+  if (p) c->allocs.push_back(p);
+  return p;
+}
+
+namespace {
+
+constexpr int64_t kStageParticles = int64_t(1) << 22;
+
+void release(pic_ctx *c, void *p) {
+  if (!p) return;
+  if (c->cfg.alloc) {
+    if (c->cfg.free) c->cfg.free(p, c->cfg.alloc_user);
+  } else {
+    cudaFree(p);
+  }
+}
+
+// Conductor cells: the electrode slab i >= nx - depth with the trench
+// columns [y0, y0 + width) open (Sec. III-C).
+bool plasma_cell(const pic_config &cfg, int i, int j) {
+  if (i < 0 || i >= cfg.nx || j < 0 || j >= cfg.ny) return false;
+  if (cfg.trench_depth > 0 && i >= cfg.nx - cfg.trench_depth) {
+    return cfg.trench_width > 0 && j >= cfg.trench_y0 && j < cfg.trench_y0 + cfg.trench_width;
+  }
+  return true;
+}
+
+bool plasma_cell_wrapped(const pic_config &cfg, int i, int j) {
+  if (cfg.periodic_x) i = ((i % cfg.nx) + cfg.nx) % cfg.nx;
+  if (cfg.periodic_y) j = ((j % cfg.ny) + cfg.ny) % cfg.ny;
+  return plasma_cell(cfg, i, j);
+}
+
+// Node classification: Dirichlet mask and values, open mesh edges, lift.
+// Values where categories meet: conductor-adjacent and x = nx nodes take the
+// electrode value, x = 0 nodes the top-plate value, bounded-y walls 0.
+void build_geometry(pic_ctx *c, std::vector<uint8_t> &cellmask, std::vector<double> &lift) {
+  const pic_config &cfg = c->cfg;
+  const Geom &g = c->g;
+  cellmask.assign(size_t(g.nx) * g.ny, 0);
+  for (int i = 0; i < g.nx; ++i)
+    for (int j = 0; j < g.ny; ++j) cellmask[size_t(i) * g.ny + j] = plasma_cell(cfg, i, j) ? 1 : 0;
+  const size_t nn = size_t(g.nxn) * g.nyn;
+  std::vector<uint8_t> dir(nn, 0);
+  std::vector<double> val(nn, 0.0);
+  for (int i = 0; i < g.nxn; ++i) {
+    for (int j = 0; j < g.nyn; ++j) {
+      const size_t n = size_t(i) * g.nyn + j;
+      if (!g.py && (j == 0 || j == g.nyn - 1)) {
+        dir[n] = 1;
+        val[n] = 0.0;
+      }
+      if (!g.px && i == 0) {
+        dir[n] = 1;
+        val[n] = cfg.phi_top;
+      }
+      if (!g.px && i == g.nxn - 1) {
+        dir[n] = 1;
+        val[n] = cfg.phi_electrode;
+      }
+      // touching a conductor cell (in-domain cells only)
+      bool touch = false;
+      for (int di = -1; di <= 0; ++di)
+        for (int dj = -1; dj <= 0; ++dj) {
+          int ci = i + di, cj = j + dj;
+          if (g.px) ci = (ci + g.nx) % g.nx;
+          if (g.py) cj = (cj + g.ny) % g.ny;
+          if (ci < 0 || ci >= g.nx || cj < 0 || cj >= g.ny) continue;
+          if (!cellmask[size_t(ci) * g.ny + cj]) touch = true;
+        }
+      if (touch) {
+        dir[n] = 1;
+        val[n] = cfg.phi_electrode;
+      }
+    }
+  }
+  c->h_nodeflags.assign(nn, 0);
+  c->h_g.assign(nn, 0.0);
+  lift.assign(nn, 0.0);
+  for (int i = 0; i < g.nxn; ++i) {
+    for (int j = 0; j < g.nyn; ++j) {
+      const size_t n = size_t(i) * g.nyn + j;
+      uint8_t f = dir[n] ? 0 : kFree;
+      // x edge (i, j) - (i+1, j) borders cells (i, j-1) and (i, j)
+      const bool has_xp = g.px || i + 1 < g.nxn;
+      const bool has_xm = g.px || i - 1 >= 0;
+      const bool has_yp = g.py || j + 1 < g.nyn;
+      const bool has_ym = g.py || j - 1 >= 0;
+      if (has_xp && (plasma_cell_wrapped(cfg, i, j - 1) || plasma_cell_wrapped(cfg, i, j)))
+        f |= kOpenXp;
+      if (has_xm && (plasma_cell_wrapped(cfg, i - 1, j - 1) || plasma_cell_wrapped(cfg, i - 1, j)))
+        f |= kOpenXm;
+      // y edge (i, j) - (i, j+1) borders cells (i-1, j) and (i, j)
+      if (has_yp && (plasma_cell_wrapped(cfg, i - 1, j) || plasma_cell_wrapped(cfg, i, j)))
+        f |= kOpenYp;
+      if (has_ym && (plasma_cell_wrapped(cfg, i - 1, j - 1) || plasma_cell_wrapped(cfg, i, j - 1)))
+        f |= kOpenYm;
+      c->h_nodeflags[n] = f;
+      c->h_g[n] = dir[n] ? val[n] : 0.0;
+    }
+  }
+  for (int i = 0; i < g.nxn; ++i) {
+    for (int j = 0; j < g.nyn; ++j) {
+      const size_t n = size_t(i) * g.nyn + j;
+      if (dir[n]) continue;
+      const int nb[4][2] = {{i - 1, j}, {i + 1, j}, {i, j - 1}, {i, j + 1}};
+      double s = 0.0;
+      for (auto &q : nb) {
+        int a = q[0], b = q[1];
+        if (g.px) a = (a + g.nxn) % g.nxn;
+        if (g.py) b = (b + g.nyn) % g.nyn;
+        const size_t m = size_t(a) * g.nyn + b;
+        if (dir[m]) s += val[m];
+      }
+      lift[n] = s;
+    }
+  }
+}
+
+pic_status check(cudaError_t e) { return e == cudaSuccess ? PIC_OK : PIC_ECUDA; }
+
+pic_status status_from_bits(uint32_t bits) {
+  if (bits & PIC_ST_NOCONV) return PIC_ENOCONV;
+  if (bits & PIC_ST_CFL) return PIC_ECFL;
+  if (bits & PIC_ST_CAPACITY) return PIC_EOVERFLOW;
+  if (bits & PIC_ST_RANGE) return PIC_ERANGE;
+  if (bits & PIC_ST_FULL) return PIC_EFULL;
+  return PIC_OK;
+}
+
+pic_status validate(const pic_config *cfg) {
+  if (!cfg) return PIC_EINVAL;
+  if (cfg->nx < 2 || cfg->ny < 2) return PIC_EINVAL;
+  if (int64_t(cfg->nx + 1) * int64_t(cfg->ny + 1) >= (int64_t(1) << 30)) return PIC_EINVAL;
+  // red-black colouring of a periodic direction needs an even node count
+  if (cfg->periodic_x && (cfg->nx % 2)) return PIC_EINVAL;
+  if (cfg->periodic_y && (cfg->ny % 2)) return PIC_EINVAL;
+  if (!(cfg->dt > 0) || !(cfg->poisson_rtol > 0)) return PIC_EINVAL;
+  if (cfg->poisson_maxit < 1 || cfg->sort_every < 1) return PIC_EINVAL;
+  for (int s = 0; s < 2; ++s) {
+    if (cfg->ppc[s] < 1 || cfg->capacity[s] < 0) return PIC_EINVAL;
+    if (cfg->capacity[s] > (int64_t(1) << 31) - (int64_t(1) << 26)) return PIC_EINVAL;
+    if (!(cfg->charge[s] == cfg->charge[s]) || !(cfg->alpha[s] == cfg->alpha[s])) return PIC_EINVAL;
+  }
+  if (cfg->trench_depth < 0 || cfg->trench_depth > cfg->nx) return PIC_EINVAL;
+  if (cfg->trench_width < 0 || cfg->trench_y0 < 0 || cfg->trench_y0 + cfg->trench_width > cfg->ny)
+    return PIC_EINVAL;
+  if (cfg->trench_depth > 0 && cfg->periodic_x) return PIC_EINVAL;
+  if (cfg->hit_capacity < 0) return PIC_EINVAL;
+  if (cfg->alloc && !cfg->free) return PIC_EINVAL;
+  return PIC_OK;
+}
+
+pic_status prepare(pic_ctx *c) {
+  if (!c->fields_dirty) return PIC_OK;
+  pic_status st;
+  if ((st = check(launch_sort(c))) != PIC_OK) return st;
+  c->steps_since_sort = 0;
+  if ((st = check(launch_particles(c, 1, 0.f, nullptr))) != PIC_OK) return st;
+  if ((st = check(launch_rho(c, 0))) != PIC_OK) return st;
+  st = poisson_solve(c, true);
+  if (st != PIC_OK) return st;
+  if ((st = check(launch_field(c))) != PIC_OK) return st;
+  if (c->pending_kick[0] || c->pending_kick[1]) {
+    if ((st = check(launch_particles(c, 2, -0.5f, c->pending_kick))) != PIC_OK) return st;
+    c->pending_kick[0] = c->pending_kick[1] = 0;
+  }
+  c->fields_dirty = 0;
+  return PIC_OK;
+}
+
+}  // namespace
+}  // namespace picgb
+
+using namespace picgb;
+
+extern "C" {
+
+const char *pic_strerror(pic_status st) {
+  switch (st) {
+    case PIC_OK: return "ok";
+    case PIC_EINVAL: return "invalid argument or configuration";
+    case PIC_ENOMEM: return "device allocation failed";
+    case PIC_ECUDA: return "CUDA error";
+    case PIC_ENOCONV: return "Poisson solve did not reach the tolerance";
+    case PIC_EOVERFLOW: return "particle capacity exceeded";
+    case PIC_ECFL: return "a particle moved farther than the face-walk limit";
+    case PIC_ETIMEOUT: return "bounded device wait gave up";
+    case PIC_EFULL: return "hit-record buffer full";
+    case PIC_ESTATE: return "call not valid in the current state";
+    case PIC_ERANGE: return "particle outside the plasma region";
+  }
+  return "unknown status";
+}
+
+pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
+  if (!out) return PIC_EINVAL;
+  *out = nullptr;
+  pic_status st = validate(cfg);
+  if (st != PIC_OK) return st;
+  pic_ctx *c = new (std::nothrow) pic_ctx();
+  if (!c) return PIC_ENOMEM;
+  c->cfg = *cfg;
+  c->dev = cfg->device;
+  if (cudaSetDevice(c->dev) != cudaSuccess) {
+    delete c;
+    return PIC_ECUDA;
+  }
+  cudaDeviceGetAttribute(&c->num_sms, cudaDevAttrMultiProcessorCount, c->dev);
+  if (cfg->stream) {
+    c->stream = (cudaStream_t)cfg->stream;
+    c->own_stream = false;
+  } else {
+    cudaStreamCreateWithFlags(&c->stream, cudaStreamNonBlocking);
+    c->own_stream = true;
+  }
+  Geom &g = c->g;
+  g.nx = cfg->nx;
+  g.ny = cfg->ny;
+  g.px = cfg->periodic_x ? 1 : 0;
+  g.py = cfg->periodic_y ? 1 : 0;
+  g.nxn = g.px ? g.nx : g.nx + 1;
+  g.nyn = g.py ? g.ny : g.ny + 1;
+  g.ntx = (g.nx + kTileX - 1) / kTileX;
+  g.nty = (g.ny + kTileY - 1) / kTileY;
+  const int ntiles = g.ntx * g.nty;
+  const size_t nn = size_t(g.nxn) * g.nyn;
+
+  std::vector<uint8_t> cellmask;
+  std::vector<double> lift;
+  build_geometry(c, cellmask, lift);
+
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void *p = dev_alloc(c, bytes);
+    if (!p) ok = false;
+    return p;
+  };
+  c->d_cellmask = (uint8_t *)A(cellmask.size());
+  c->d_nodeflags = (uint8_t *)A(nn);
+  c->d_lift = (double *)A(nn * 8);
+  c->d_g = (double *)A(nn * 8);
+  c->d_acc = (unsigned long long *)A(2 * nn * 8);
+  c->d_rho_ext = (double *)A(nn * 8);
+  c->d_rho = (double *)A(nn * 8);
+  c->d_b = (double *)A(nn * 8);
+  c->d_phi = (double *)A(nn * 8);
+  c->d_E = (float2 *)A(nn * sizeof(float2));
+  c->d_fe = (double *)A(2 * 8);
+  for (int s = 0; s < 2; ++s) {
+    c->cap[s] = ((cfg->capacity[s] + 4 * int64_t(ntiles) + 3) / 4) * 4;
+    for (int b = 0; b < 2; ++b) {
+      ParticleBuf &P = c->pb[s][b];
+      P.cell = (int32_t *)A(c->cap[s] * 4);
+      P.fx = (float *)A(c->cap[s] * 4);
+      P.fy = (float *)A(c->cap[s] * 4);
+      P.vx = (float *)A(c->cap[s] * 4);
+      P.vy = (float *)A(c->cap[s] * 4);
+      P.id = (uint32_t *)A(c->cap[s] * 4);
+    }
+    c->cur[s] = 0;
+  }
+  c->d_tile_count = (uint32_t *)A(2 * size_t(ntiles) * 4);
+  c->d_tile_cursor = (uint32_t *)A(2 * size_t(ntiles) * 4);
+  c->d_tile_start = (uint32_t *)A(2 * size_t(ntiles) * 4);
+  c->max_chunks = 0;
+  for (int s = 0; s < 2; ++s) c->max_chunks += ntiles + c->cap[s] / kChunk + 1;
+  c->d_chunks = (Chunk *)A(size_t(c->max_chunks) * sizeof(Chunk));
+  c->d_nchunks = (int32_t *)A(4);
+  c->d_nslots = (int64_t *)A(4 * 8);
+  c->d_ke_part = (double *)A(size_t(c->max_chunks) * 8);
+  c->d_step = (int32_t *)A(4);
+  c->d_walls = (unsigned long long *)A(2 * PIC_NWALLS * 8);
+  c->d_bottom = (unsigned long long *)A(2 * size_t(g.ny) * 8);
+  c->d_hits = (pic_hit *)A(std::max<int64_t>(cfg->hit_capacity, 1) * sizeof(pic_hit));
+  c->d_nhits = (unsigned long long *)A(8);
+  c->d_status = (uint32_t *)A(4);
+  c->stage_n = std::min<int64_t>(kStageParticles,
+                                 std::max<int64_t>(std::max(cfg->capacity[0], cfg->capacity[1]), 1));
+  c->d_stage = (double *)A(size_t(c->stage_n) * 5 * 8);
+  c->d_diag = (double *)A(size_t(c->num_sms) * 2 * 2 * 3 * 8);
+  if (!ok) {
+    pic_free(c);
+    return PIC_ENOMEM;
+  }
+  cudaError_t e = cudaMallocHost((void **)&c->h_status, 4);
+  if (e != cudaSuccess) {
+    pic_free(c);
+    return PIC_ENOMEM;
+  }
+  cudaMemcpyAsync(c->d_cellmask, cellmask.data(), cellmask.size(), cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->d_nodeflags, c->h_nodeflags.data(), nn, cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->d_lift, lift.data(), nn * 8, cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->d_g, c->h_g.data(), nn * 8, cudaMemcpyHostToDevice, c->stream);
+  cudaMemcpyAsync(c->d_phi, c->h_g.data(), nn * 8, cudaMemcpyHostToDevice, c->stream);
+  cudaMemsetAsync(c->d_acc, 0, 2 * nn * 8, c->stream);
+  cudaMemsetAsync(c->d_rho_ext, 0, nn * 8, c->stream);
+  cudaMemsetAsync(c->d_rho, 0, nn * 8, c->stream);
+  cudaMemsetAsync(c->d_b, 0, nn * 8, c->stream);
+  cudaMemsetAsync(c->d_E, 0, nn * sizeof(float2), c->stream);
+  cudaMemsetAsync(c->d_fe, 0, 16, c->stream);
+  cudaMemsetAsync(c->d_tile_count, 0, 2 * size_t(ntiles) * 4, c->stream);
+  cudaMemsetAsync(c->d_tile_cursor, 0, 2 * size_t(ntiles) * 4, c->stream);
+  cudaMemsetAsync(c->d_nchunks, 0, 4, c->stream);
+  cudaMemsetAsync(c->d_nslots, 0, 32, c->stream);
+  cudaMemsetAsync(c->d_step, 0, 4, c->stream);
+  cudaMemsetAsync(c->d_walls, 0, 2 * PIC_NWALLS * 8, c->stream);
+  cudaMemsetAsync(c->d_bottom, 0, 2 * size_t(g.ny) * 8, c->stream);
+  cudaMemsetAsync(c->d_nhits, 0, 8, c->stream);
+  cudaMemsetAsync(c->d_status, 0, 4, c->stream);
+  for (int s = 0; s < 2; ++s)
+    for (int b = 0; b < 2; ++b) cudaMemsetAsync(c->pb[s][b].cell, 0xff, c->cap[s] * 4, c->stream);
+  for (int k = 0; k < 6; ++k) cudaEventCreate(&c->tev[k]);
+  e = poisson_setup(c);
+  if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) {
+    pic_free(c);
+    return e == cudaErrorMemoryAllocation ? PIC_ENOMEM : PIC_ECUDA;
+  }
+  c->fields_dirty = 1;
+  c->needs_sort = 1;
+  c->step = 0;
+  *out = c;
+  return PIC_OK;
+}
+
+pic_status pic_load(pic_ctx *c, int32_t species, int64_t n, const double *x, const double *y,
+                    const double *vx, const double *vy, const uint32_t *ids, uint32_t flags) {
+  if (!c) return PIC_EINVAL;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
+  const size_t nn = size_t(c->g.nxn) * c->g.nyn;
+  if (species == -1) {
+    if (!x || n != int64_t(nn)) return PIC_EINVAL;
+    if (cudaMemcpyAsync(c->d_rho_ext, x, nn * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      return PIC_ECUDA;
+    c->fields_dirty = 1;
+    return check(cudaStreamSynchronize(c->stream));
+  }
+  if (species < 0 || species > 1 || n < 0) return PIC_EINVAL;
+  if (n > 0 && (!x || !y || !vx || !vy)) return PIC_EINVAL;
+  if (n > c->cfg.capacity[species]) return PIC_EOVERFLOW;
+  const int s = species;
+  double *sx = c->d_stage, *sy = sx + c->stage_n, *svx = sy + c->stage_n, *svy = svx + c->stage_n;
+  uint32_t *sid = (uint32_t *)(svy + c->stage_n);
+  for (int64_t off = 0; off < n; off += c->stage_n) {
+    const int64_t m = std::min<int64_t>(c->stage_n, n - off);
+    cudaMemcpyAsync(sx, x + off, m * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(sy, y + off, m * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(svx, vx + off, m * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(svy, vy + off, m * 8, cudaMemcpyHostToDevice, c->stream);
+    if (ids) cudaMemcpyAsync(sid, ids + off, m * 4, cudaMemcpyHostToDevice, c->stream);
+    cudaError_t e = launch_load_convert(c, s, sx, sy, svx, svy, ids ? sid : nullptr, off, m);
+    if (e != cudaSuccess) return PIC_ECUDA;
+  }
+  int64_t slots[1] = {n};
+  cudaMemcpyAsync(c->d_nslots + s, slots, 8, cudaMemcpyHostToDevice, c->stream);
+  cudaError_t e = cudaStreamSynchronize(c->stream);
+  if (e != cudaSuccess) return PIC_ECUDA;
+  c->pending_kick[s] = (flags & PIC_LOAD_V_AT_T0) ? 1 : 0;
+  c->fields_dirty = 1;
+  c->needs_sort = 1;
+  return PIC_OK;
+}
+
+pic_status pic_step(pic_ctx *c, int32_t nsteps) {
+  if (!c || nsteps < 0) return PIC_EINVAL;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
+  pic_status st = prepare(c);
+  if (st != PIC_OK) return st;
+  for (int32_t k = 0; k < nsteps; ++k) {
+    const bool sorting = c->steps_since_sort >= c->cfg.sort_every;
+    cudaEventRecord(c->tev[0], c->stream);
+    if (sorting) {
+      if ((st = check(launch_sort(c))) != PIC_OK) return st;
+      c->steps_since_sort = 0;
+      c->launches += 4;
+      c->t_sorts += 1;
+    }
+    cudaEventRecord(c->tev[1], c->stream);
+    if ((st = check(launch_particles(c, 0, 1.f, nullptr))) != PIC_OK) return st;
+    cudaEventRecord(c->tev[2], c->stream);
+    if ((st = check(launch_rho(c, 1))) != PIC_OK) return st;
+    cudaEventRecord(c->tev[3], c->stream);
+    st = poisson_solve(c, c->cfg.warm_start == 0);
+    if (st != PIC_OK) return st;
+    cudaEventRecord(c->tev[4], c->stream);
+    if ((st = check(launch_field(c))) != PIC_OK) return st;
+    cudaEventRecord(c->tev[5], c->stream);
+    c->launches += 3;
+    // the Poisson solve synchronised the stream, so the first events are done
+    float ms[3] = {0.f, 0.f, 0.f};
+    cudaEventElapsedTime(&ms[0], c->tev[0], c->tev[1]);
+    cudaEventElapsedTime(&ms[1], c->tev[1], c->tev[2]);
+    cudaEventElapsedTime(&ms[2], c->tev[2], c->tev[3]);
+    c->t_sort += ms[0];
+    c->t_part += ms[1];
+    c->t_other += ms[2];
+    c->t_poisson += c->last_ms;
+    c->t_steps += 1;
+    c->steps_since_sort += 1;
+    c->step += 1;
+  }
+  return PIC_OK;
+}
+
+pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int64_t *n_out) {
+  if (!c || (!out && kind != PIC_DIAG_STATUS)) return PIC_EINVAL;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
+  const Geom &g = c->g;
+  const size_t nn = size_t(g.nxn) * g.nyn;
+  int64_t count = 0;
+  auto need = [&](int64_t bytes) { return bytes <= cap_bytes; };
+  uint32_t bits = 0;
+  if (cudaMemcpy(&bits, c->d_status, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
+  auto species_moments = [&](double m[2][3]) -> pic_status {
+    const int nb = c->num_sms * 2;
+    double *d = c->d_diag;
+    for (int s = 0; s < 2; ++s) {
+      if (launch_moments(c, s, d + s * 3 * nb, nb) != cudaSuccess) return PIC_ECUDA;
+    }
+    std::vector<double> h(2 * 3 * nb);
+    if (cudaMemcpyAsync(h.data(), d, h.size() * 8, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+        cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return PIC_ECUDA;
+    for (int s = 0; s < 2; ++s)
+      for (int k = 0; k < 3; ++k) {
+        double t = 0;
+        for (int b = 0; b < nb; ++b) t += h[(s * nb + b) * 3 + k];
+        m[s][k] = t;
+      }
+    return PIC_OK;
+  };
+  switch (kind) {
+    case PIC_DIAG_ENERGY: {
+      if (!need(4 * 8)) return PIC_EINVAL;
+      int32_t nch = 0;
+      cudaMemcpy(&nch, c->d_nchunks, 4, cudaMemcpyDeviceToHost);
+      std::vector<double> ke(std::max(nch, 1));
+      std::vector<Chunk> ch(std::max(nch, 1));
+      cudaMemcpy(ke.data(), c->d_ke_part, size_t(nch) * 8, cudaMemcpyDeviceToHost);
+      cudaMemcpy(ch.data(), c->d_chunks, size_t(nch) * sizeof(Chunk), cudaMemcpyDeviceToHost);
+      double fe[2];
+      cudaMemcpy(fe, c->d_fe, 16, cudaMemcpyDeviceToHost);
+      double kes[2] = {0, 0};
+      for (int k = 0; k < nch; ++k) kes[ch[k].species] += ke[k];
+      double *o = (double *)out;
+      for (int s = 0; s < 2; ++s) {
+        const double m = c->cfg.charge[s] / c->cfg.alpha[s];
+        o[s] = 0.5 * m * kes[s] / double(c->cfg.ppc[s]);
+      }
+      o[2] = fe[1];
+      o[3] = double(c->step - 1);
+      count = 4;
+      break;
+    }
+    case PIC_DIAG_MOMENTUM: {
+      if (!need(4 * 8)) return PIC_EINVAL;
+      double m[2][3];
+      pic_status st = species_moments(m);
+      if (st != PIC_OK) return st;
+      double *o = (double *)out;
+      for (int s = 0; s < 2; ++s) {
+        const double mw = c->cfg.charge[s] / c->cfg.alpha[s] / double(c->cfg.ppc[s]);
+        o[2 * s] = mw * m[s][0];
+        o[2 * s + 1] = mw * m[s][1];
+      }
+      count = 4;
+      break;
+    }
+    case PIC_DIAG_COUNTS: {
+      if (!need(18 * 8)) return PIC_EINVAL;
+      double m[2][3];
+      pic_status st = species_moments(m);
+      if (st != PIC_OK) return st;
+      unsigned long long w[2 * PIC_NWALLS];
+      cudaMemcpy(w, c->d_walls, sizeof(w), cudaMemcpyDeviceToHost);
+      int64_t *o = (int64_t *)out;
+      for (int k = 0; k < 2 * PIC_NWALLS; ++k) o[k] = int64_t(w[k]);
+      o[16] = int64_t(m[0][2]);
+      o[17] = int64_t(m[1][2]);
+      count = 18;
+      break;
+    }
+    case PIC_DIAG_SURFACE: {
+      if (!need(2 * int64_t(g.ny) * 8)) return PIC_EINVAL;
+      cudaMemcpy(out, c->d_bottom, 2 * size_t(g.ny) * 8, cudaMemcpyDeviceToHost);
+      count = 2 * g.ny;
+      break;
+    }
+    case PIC_DIAG_HITS: {
+      unsigned long long nh = 0;
+      cudaMemcpy(&nh, c->d_nhits, 8, cudaMemcpyDeviceToHost);
+      int64_t m = std::min<int64_t>(int64_t(nh), c->cfg.hit_capacity);
+      m = std::min<int64_t>(m, cap_bytes / int64_t(sizeof(pic_hit)));
+      if (m > 0) cudaMemcpy(out, c->d_hits, size_t(m) * sizeof(pic_hit), cudaMemcpyDeviceToHost);
+      count = m;
+      break;
+    }
+    case PIC_DIAG_RHO:
+    case PIC_DIAG_PHI: {
+      if (!need(int64_t(nn) * 8)) return PIC_EINVAL;
+      cudaMemcpy(out, kind == PIC_DIAG_RHO ? c->d_rho : c->d_phi, nn * 8, cudaMemcpyDeviceToHost);
+      count = int64_t(nn);
+      break;
+    }
+    case PIC_DIAG_E: {
+      if (!need(2 * int64_t(nn) * 8)) return PIC_EINVAL;
+      std::vector<float2> e(nn);
+      cudaMemcpy(e.data(), c->d_E, nn * sizeof(float2), cudaMemcpyDeviceToHost);
+      double *o = (double *)out;
+      for (size_t n = 0; n < nn; ++n) {
+        o[n] = e[n].x;
+        o[nn + n] = e[n].y;
+      }
+      count = 2 * int64_t(nn);
+      break;
+    }
+    case PIC_DIAG_STATE_E:
+    case PIC_DIAG_STATE_I: {
+      const int s = kind == PIC_DIAG_STATE_E ? 0 : 1;
+      double m[2][3];
+      pic_status st = species_moments(m);
+      if (st != PIC_OK) return st;
+      const int64_t live = int64_t(m[s][2]);
+      if (!need(5 * live * 8)) return PIC_EINVAL;
+      double *buf = nullptr;
+      unsigned long long *ctr = nullptr;
+      if (cudaMalloc(&buf, size_t(std::max<int64_t>(live, 1)) * 5 * 8) != cudaSuccess) return PIC_ENOMEM;
+      if (cudaMalloc(&ctr, 8) != cudaSuccess) {
+        cudaFree(buf);
+        return PIC_ENOMEM;
+      }
+      cudaMemsetAsync(ctr, 0, 8, c->stream);
+      cudaError_t e = launch_export_state(c, s, buf, live, ctr);
+      if (e == cudaSuccess)
+        e = cudaMemcpyAsync(out, buf, size_t(live) * 5 * 8, cudaMemcpyDeviceToHost, c->stream);
+      if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
+      cudaFree(buf);
+      cudaFree(ctr);
+      if (e != cudaSuccess) return PIC_ECUDA;
+      count = live;
+      break;
+    }
+    case PIC_DIAG_POISSON: {
+      if (!need(4 * 8)) return PIC_EINVAL;
+      PoissonState ps;
+      cudaMemcpy(&ps, c->d_ps, sizeof(ps), cudaMemcpyDeviceToHost);
+      double *o = (double *)out;
+      o[0] = ps.total_iters;
+      o[1] = c->last_outer;
+      o[2] = ps.rel;
+      o[3] = c->last_ms;
+      count = 4;
+      break;
+    }
+    case PIC_DIAG_TIMING: {
+      if (!need(8 * 8)) return PIC_EINVAL;
+      float fms = 0.f;
+      // the field kernel of the last step ran after the last event pair read
+      if (c->t_steps > 0 && cudaEventElapsedTime(&fms, c->tev[4], c->tev[5]) == cudaSuccess)
+        c->t_other += fms;
+      int64_t slots[2] = {0, 0};
+      cudaMemcpy(slots, c->d_nslots, 16, cudaMemcpyDeviceToHost);
+      double *o = (double *)out;
+      o[0] = double(c->t_steps);
+      o[1] = c->t_part;
+      o[2] = c->t_sort;
+      o[3] = c->t_poisson;
+      o[4] = c->t_other;
+      o[5] = double(c->t_sorts);
+      o[6] = double(c->launches);
+      o[7] = double(slots[0] + slots[1]);
+      c->t_part = c->t_sort = c->t_poisson = c->t_other = 0.0;
+      c->t_steps = c->t_sorts = c->launches = 0;
+      count = 8;
+      break;
+    }
+    case PIC_DIAG_STATUS: {
+      if (out) {
+        if (!need(4)) return PIC_EINVAL;
+        *(uint32_t *)out = bits;
+      }
+      cudaMemsetAsync(c->d_status, 0, 4, c->stream);
+      count = 1;
+      if (n_out) *n_out = count;
+      return cudaStreamSynchronize(c->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+    }
+    default:
+      return PIC_EINVAL;
+  }
+  if (n_out) *n_out = count;
+  if (cudaGetLastError() != cudaSuccess) return PIC_ECUDA;
+  return status_from_bits(bits);
+}
+
+pic_status pic_free(pic_ctx *c) {
+  if (!c) return PIC_OK;
+  cudaSetDevice(c->dev);
+  if (c->stream) cudaStreamSynchronize(c->stream);
+  for (void *p : c->allocs) release(c, p);
+  c->allocs.clear();
+  if (c->h_status) cudaFreeHost(c->h_status);
+  if (c->h_ps) cudaFreeHost(c->h_ps);
+  for (int k = 0; k < 6; ++k)
+    if (c->tev[k]) cudaEventDestroy(c->tev[k]);
+  if (c->ev0) cudaEventDestroy(c->ev0);
+  if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
+  delete c;
+  return PIC_OK;
+}
+
+}  // extern "C"

@@ -1,0 +1,181 @@
+// Internal declarations shared by the library's translation units.
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <vector>
+
+#include "picgb.h"
+
+namespace picgb {
+
+// Fixed-point deposit: one particle's CIC shares are quantised to 2^-20 of
+// its weight, three shares rounded to nearest-even and the fourth the
+// remainder, so each particle deposits exactly 2^20 units.
+constexpr int kFracBits = 20;
+constexpr uint32_t kQ = 1u << kFracBits;
+
+// Particle tiles: a sorted tile's particles are processed by one CTA with
+// the field and the deposit of a window (tile + halo) held in shared memory.
+constexpr int kTileX = 16;
+constexpr int kTileY = 16;
+constexpr int kHalo = 4;
+constexpr int kChunk = 2048;     // particles per work item (multiple of 4, <= 4095)
+constexpr int kParticleThreads = 256;
+constexpr int kWalkLimit = 16;   // face crossings followed per move
+
+struct Geom {
+  int nx, ny;          // cells
+  int px, py;          // periodic flags
+  int nxn, nyn;        // nodes
+  int ntx, nty;        // tiles
+};
+
+// Node flag bits (uint8 per node)
+constexpr uint8_t kFree = 1;     // not a Dirichlet node
+constexpr uint8_t kOpenXm = 2;   // edge (i-1, j) - (i, j) borders a plasma cell
+constexpr uint8_t kOpenXp = 4;   // edge (i, j) - (i+1, j)
+constexpr uint8_t kOpenYm = 8;   // edge (i, j-1) - (i, j)
+constexpr uint8_t kOpenYp = 16;  // edge (i, j) - (i, j+1)
+
+struct ParticleBuf {
+  int32_t *cell;
+  float *fx, *fy, *vx, *vy;
+  uint32_t *id;
+};
+
+struct Chunk {
+  int32_t species, tile, begin, end;
+};
+
+// Device-side scalars of one Poisson solve.
+struct PoissonState {
+  double bb;          // ||b||^2 (FP64)
+  double rr64;        // ||b - A phi||^2 (FP64, outer)
+  double rel;         // sqrt(rr64 / bb)
+  double bmean;       // mean of b (doubly periodic box only)
+  double rz, rz_old, pq, rr, rr0;   // inner PCG scalars
+  double alpha, beta;
+  double zmean;
+  double tol_in;      // inner target relative to the inner initial residual
+  int32_t inner_done, outer_done;
+  int32_t inner_iters, total_iters;
+  int32_t outer_iters, pad;
+};
+
+struct MGLevel {
+  int nx, ny, nxn, nyn;
+  float h2;            // squared mesh spacing (4^level)
+  uint8_t *free;       // 1 = unknown, 0 = Dirichlet (zero correction)
+  float *u, *f;        // correction and right-hand side
+};
+
+struct Reducer {
+  double *part;        // per-block partials
+  unsigned int *ticket;
+  int nblocks;
+};
+
+}  // namespace picgb
+
+struct pic_ctx {
+  pic_config cfg;
+  picgb::Geom g;
+  int dev;
+  int num_sms;
+  cudaStream_t stream;
+  bool own_stream;
+
+  // geometry
+  uint8_t *d_cellmask;      // [nx*ny] 1 = plasma
+  uint8_t *d_nodeflags;     // [nxn*nyn]
+  double *d_lift;           // [nxn*nyn] sum of Dirichlet neighbour values (free nodes)
+  double *d_g;              // [nxn*nyn] Dirichlet values (0 at free nodes)
+  std::vector<uint8_t> h_nodeflags;
+  std::vector<double> h_g;
+
+  // fields
+  unsigned long long *d_acc;   // [2][nnodes] fixed-point species weights
+  double *d_rho_ext;
+  double *d_rho;               // net charge density
+  double *d_b;                 // right-hand side on free nodes
+  double *d_phi;               // FP64 master potential (Dirichlet values included)
+  float2 *d_E;
+  double *d_fe;                // [2]: field energy of E just computed, of E used by last step
+
+  // Poisson
+  int nlev, lc;                // levels, first level solved by the single-CTA kernel
+  std::vector<picgb::MGLevel> lev;
+  float *d_r32, *d_z, *d_p0, *d_p1, *d_q, *d_e;
+  double *d_r64;
+  picgb::PoissonState *d_ps;
+  picgb::PoissonState *h_ps;   // pinned mirror
+  picgb::Reducer red;
+  int singular;
+  double last_ms;
+  int last_outer;
+  cudaEvent_t ev0, ev1;
+
+  // particles
+  picgb::ParticleBuf pb[2][2];
+  int cur[2];
+  int64_t cap[2];              // slots allocated per buffer
+  int needs_sort;
+  int pending_kick[2];
+  int steps_since_sort;
+  uint32_t *d_tile_count;      // [2][ntiles]
+  uint32_t *d_tile_cursor;     // [2][ntiles]
+  uint32_t *d_tile_start;      // [2][ntiles]
+  picgb::Chunk *d_chunks;
+  int32_t *d_nchunks;
+  int64_t max_chunks;
+  int64_t *d_nslots;           // [4]: slots in use per species; [2..3] staged by the sort
+  double *d_ke_part;           // [max_chunks]
+  int32_t *d_step;
+
+  // tallies and status
+  unsigned long long *d_walls;    // [2][8]
+  unsigned long long *d_bottom;   // [2][ny]
+  pic_hit *d_hits;
+  unsigned long long *d_nhits;
+  uint32_t *d_status;
+  uint32_t *h_status;             // pinned
+
+  // staging for pic_load / diag
+  double *d_stage;
+  double *d_diag;                 // per-block partials of the particle moments
+  int64_t stage_n;
+  int fields_dirty;
+  int64_t step;
+  // per-phase timing (PIC_DIAG_TIMING)
+  cudaEvent_t tev[6];
+  double t_part, t_sort, t_poisson, t_other;
+  int64_t t_steps, t_sorts, launches, t_slots;
+  std::vector<void *> allocs;
+};
+
+namespace picgb {
+
+// api.cu
+void *dev_alloc(pic_ctx *c, size_t bytes);
+
+// particles.cu
+cudaError_t launch_sort(pic_ctx *c);
+// mode 0: full step; 1: deposit only; 2: kick only (factor * dt, flagged species)
+cudaError_t launch_particles(pic_ctx *c, int mode, float kick_factor, const int *species_mask);
+cudaError_t launch_load_convert(pic_ctx *c, int s, const double *d_x, const double *d_y,
+                                const double *d_vx, const double *d_vy, const uint32_t *d_id,
+                                int64_t offset, int64_t n);
+cudaError_t launch_export_state(pic_ctx *c, int s, double *d_out, int64_t n_live,
+                                unsigned long long *d_counter);
+// per-block partials [sum vx, sum vy, live] of species s into d_part[3 * nblocks]
+cudaError_t launch_moments(pic_ctx *c, int s, double *d_part, int nblocks);
+
+// poisson.cu
+cudaError_t poisson_setup(pic_ctx *c);
+cudaError_t launch_rho(pic_ctx *c, int advance_step);
+pic_status poisson_solve(pic_ctx *c, bool zero_guess);
+cudaError_t launch_field(pic_ctx *c);
+
+}  // namespace picgb

@@ -1,0 +1,656 @@
+// Particle-side kernels: tile counting sort, the fused gather / leapfrog
+// push / absorption / cloud-in-cell deposit kernel, and state conversion.
+//
+// Particles are stored per species as structure-of-arrays: int32 cell
+// index (i * ny + j, -1 = dead or padding), FP32 offsets fx, fy in [0, 1)
+// inside the cell, FP32 velocities vx, vy (at half steps), uint32 id.
+// Every sort_every steps they are counting-sorted by 16x16-cell tile; each
+// tile's segment is padded to a multiple of 4 slots so that one thread moves
+// four particles with 16-byte vector loads and stores.
+#include <cuda_runtime.h>
+
+#include "internal.cuh"
+
+namespace picgb {
+namespace {
+
+__device__ __forceinline__ int wrapmod(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+__device__ __forceinline__ int tile_of(const Geom &g, int c) {
+  const int i = c / g.ny;
+  const int j = c - i * g.ny;
+  return (i / kTileX) * g.nty + j / kTileY;
+}
+
+// ---------------------------------------------------------------------------
+// Counting sort by tile
+// ---------------------------------------------------------------------------
+struct SortArgs {
+  ParticleBuf src[2], dst[2];
+  const int64_t *nslots;   // slots in use in src, per species
+  uint32_t *count, *cursor, *start;   // [2][ntiles]
+  Chunk *chunks;
+  int32_t *nchunks;
+  int64_t *nslots_out;
+  Geom g;
+  int ntiles;
+};
+
+__global__ void k_sort_hist(SortArgs a) {
+  const int s = blockIdx.y;
+  const int64_t n = a.nslots[s];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  uint32_t *cnt = a.count + int64_t(s) * a.ntiles;
+  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+    const int64_t p = base + lane;
+    int t = -1;
+    if (p < n) {
+      const int c = a.src[s].cell[p];
+      if (c >= 0) t = tile_of(a.g, c);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, t);
+    if (t >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[t], (uint32_t)__popc(peers));
+  }
+}
+
+// Block-wide exclusive scan of one value per thread (blockDim == 1024).
+__device__ uint32_t block_exscan(uint32_t v, uint32_t *total) {
+  __shared__ uint32_t warp_sums[32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
+  uint32_t x = v;
+#pragma unroll
+  for (int o = 1; o < 32; o <<= 1) {
+    const uint32_t y = __shfl_up_sync(0xffffffffu, x, o);
+    if (lane >= o) x += y;
+  }
+  if (lane == 31) warp_sums[w] = x;
+  __syncthreads();
+  if (w == 0) {
+    uint32_t s = warp_sums[lane];
+#pragma unroll
+    for (int o = 1; o < 32; o <<= 1) {
+      const uint32_t y = __shfl_up_sync(0xffffffffu, s, o);
+      if (lane >= o) s += y;
+    }
+    warp_sums[lane] = s;
+  }
+  __syncthreads();
+  const uint32_t before = (w > 0 ? warp_sums[w - 1] : 0u) + x - v;
+  *total = warp_sums[31];
+  __syncthreads();
+  return before;
+}
+
+// One CTA of 1024 threads: tile starts (padded to 4 slots), the chunk work
+// list of both species, padding slots marked dead, counters reset.
+__global__ void __launch_bounds__(1024) k_sort_scan(SortArgs a) {
+  uint32_t chunk_base = 0;
+  for (int s = 0; s < 2; ++s) {
+    uint32_t slot_base = 0;
+    uint32_t *cnt = a.count + int64_t(s) * a.ntiles;
+    uint32_t *cur = a.cursor + int64_t(s) * a.ntiles;
+    uint32_t *st = a.start + int64_t(s) * a.ntiles;
+    for (int t0 = 0; t0 < a.ntiles; t0 += 1024) {
+      const int t = t0 + threadIdx.x;
+      uint32_t n = 0, padded = 0, nch = 0;
+      if (t < a.ntiles) {
+        n = cnt[t];
+        padded = (n + 3u) & ~3u;
+        nch = (padded + kChunk - 1) / kChunk;
+      }
+      uint32_t tot_slots, tot_ch;
+      const uint32_t off = block_exscan(padded, &tot_slots) + slot_base;
+      const uint32_t coff = block_exscan(nch, &tot_ch) + chunk_base;
+      if (t < a.ntiles) {
+        st[t] = off;
+        cur[t] = 0;
+        cnt[t] = 0;
+        for (uint32_t k = n; k < padded; ++k) a.dst[s].cell[off + k] = -1;
+        for (uint32_t k = 0; k < nch; ++k) {
+          Chunk ch;
+          ch.species = s;
+          ch.tile = t;
+          ch.begin = int32_t(off + k * kChunk);
+          ch.end = int32_t(off + min(padded, (k + 1) * kChunk));
+          a.chunks[coff + k] = ch;
+        }
+      }
+      slot_base += tot_slots;
+      chunk_base += tot_ch;
+    }
+    if (threadIdx.x == 0) a.nslots_out[s] = slot_base;   // published by k_sort_finish
+  }
+  if (threadIdx.x == 0) *a.nchunks = int32_t(chunk_base);
+}
+
+__global__ void k_sort_finish(int64_t *nslots) {
+  nslots[0] = nslots[2];
+  nslots[1] = nslots[3];
+}
+
+__global__ void k_sort_scatter(SortArgs a) {
+  const int s = blockIdx.y;
+  const int64_t n = a.nslots[s];
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  uint32_t *cur = a.cursor + int64_t(s) * a.ntiles;
+  const uint32_t *st = a.start + int64_t(s) * a.ntiles;
+  const ParticleBuf S = a.src[s], D = a.dst[s];
+  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
+    const int64_t p = base + lane;
+    int t = -1, c = -1;
+    if (p < n) {
+      c = S.cell[p];
+      if (c >= 0) t = tile_of(a.g, c);
+    }
+    const unsigned peers = __match_any_sync(0xffffffffu, t);
+    const int leader = __ffs(peers) - 1;
+    uint32_t b = 0;
+    if (t >= 0 && lane == leader) b = atomicAdd(&cur[t], (uint32_t)__popc(peers));
+    b = __shfl_sync(0xffffffffu, b, leader);
+    if (t >= 0) {
+      const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
+      const int64_t d = int64_t(st[t]) + b + rank;
+      D.cell[d] = c;
+      D.fx[d] = S.fx[p];
+      D.fy[d] = S.fy[p];
+      D.vx[d] = S.vx[p];
+      D.vy[d] = S.vy[p];
+      D.id[d] = S.id[p];
+    }
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Fused particle kernel
+// ---------------------------------------------------------------------------
+struct PArgs {
+  ParticleBuf pb[2];
+  const Chunk *chunks;
+  const int32_t *nchunks;
+  const float2 *E;
+  unsigned long long *acc;   // [2][nnodes]
+  const uint8_t *cellmask;
+  Geom g;
+  float qdt[2];              // alpha_s * dt (times the kick factor in kick mode)
+  float dt;
+  int kick[2];               // kick mode: species to kick
+  unsigned long long *walls, *bottom;
+  pic_hit *hits;
+  unsigned long long *nhits;
+  long long hit_cap;
+  uint32_t *status;
+  const int32_t *step;
+  double *ke_part;
+  double *fe;                // [0] energy of the current E, [1] of the E used by the last step
+};
+
+constexpr int WXc = kTileX + 2 * kHalo;   // window cells
+constexpr int WYc = kTileY + 2 * kHalo;
+constexpr int NWX = WXc + 1;              // window nodes
+constexpr int NWY = WYc + 1;
+
+// Local window cell coordinate of global cell index i (window origin w0,
+// period n when periodic); returns a value >= W when outside the window.
+__device__ __forceinline__ int local_coord(int i, int w0, int n, int periodic) {
+  int l = i - w0;
+  if (periodic) l = wrapmod(l, n);
+  return l;
+}
+
+__device__ __forceinline__ void deposit_global(const PArgs &a, unsigned long long *acc, int i,
+                                               int j, int w00, int w01, int w10, int w11) {
+  const Geom &g = a.g;
+  int i1 = i + 1, j1 = j + 1;
+  if (g.px && i1 == g.nxn) i1 = 0;
+  if (g.py && j1 == g.nyn) j1 = 0;
+  atomicAdd(&acc[i * g.nyn + j], (unsigned long long)(long long)w00);
+  atomicAdd(&acc[i * g.nyn + j1], (unsigned long long)(long long)w01);
+  atomicAdd(&acc[i1 * g.nyn + j], (unsigned long long)(long long)w10);
+  atomicAdd(&acc[i1 * g.nyn + j1], (unsigned long long)(long long)w11);
+}
+
+__device__ __forceinline__ void cic_weights(float fx, float fy, int &w00, int &w01, int &w10,
+                                            int &w11) {
+  const float gx = 1.0f - fx, gy = 1.0f - fy;
+  const float q = float(kQ);
+  w00 = __float2int_rn(gx * gy * q);
+  w10 = __float2int_rn(fx * gy * q);
+  w01 = __float2int_rn(gx * fy * q);
+  w11 = int(kQ) - w00 - w10 - w01;
+}
+
+template <int MODE>
+__device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint32_t *sAcc,
+                                         unsigned long long *acc, int s, int wi0, int wj0,
+                                         int64_t slot, int &c, float &fx, float &fy, float &vx,
+                                         float &vy, float &ke) {
+  if (c < 0) return;
+  const Geom &g = a.g;
+  const int i = c / g.ny;
+  const int j = c - i * g.ny;
+  if (MODE != 1) {
+    const int li = local_coord(i, wi0, g.nx, g.px);
+    const int lj = local_coord(j, wj0, g.ny, g.py);
+    float2 e00, e01, e10, e11;
+    if ((unsigned)li < (unsigned)WXc && (unsigned)lj < (unsigned)WYc) {
+      const int k = li * NWY + lj;
+      e00 = sE[k];
+      e01 = sE[k + 1];
+      e10 = sE[k + NWY];
+      e11 = sE[k + NWY + 1];
+    } else {
+      int i1 = i + 1, j1 = j + 1;
+      if (g.px && i1 == g.nxn) i1 = 0;
+      if (g.py && j1 == g.nyn) j1 = 0;
+      e00 = __ldg(&a.E[i * g.nyn + j]);
+      e01 = __ldg(&a.E[i * g.nyn + j1]);
+      e10 = __ldg(&a.E[i1 * g.nyn + j]);
+      e11 = __ldg(&a.E[i1 * g.nyn + j1]);
+    }
+    const float gx = 1.0f - fx, gy = 1.0f - fy;
+    const float ex = gx * (gy * e00.x + fy * e01.x) + fx * (gy * e10.x + fy * e11.x);
+    const float ey = gx * (gy * e00.y + fy * e01.y) + fx * (gy * e10.y + fy * e11.y);
+    if (MODE == 2) {
+      if (a.kick[s]) {
+        vx += a.qdt[s] * ex;
+        vy += a.qdt[s] * ey;
+      }
+      return;
+    }
+    const float vx1 = vx + a.qdt[s] * ex;
+    const float vy1 = vy + a.qdt[s] * ey;
+    ke += vx * vx1 + vy * vy1;
+    vx = vx1;
+    vy = vy1;
+    const float dx = vx1 * a.dt, dy = vy1 * a.dt;
+    float nfx = fx + dx, nfy = fy + dy;
+    const float cxf = floorf(nfx), cyf = floorf(nfy);
+    const int cx = int(cxf), cy = int(cyf);
+    int ni = i, nj = j;
+    if (cx | cy) {
+      // Walk the crossed faces in order of the segment parameter (x first on a tie).
+      const int si = cx > 0 ? 1 : -1, sj = cy > 0 ? 1 : -1;
+      const float adx = fabsf(dx), ady = fabsf(dy);
+      int oi = 0, oj = 0, k = 0;
+      bool dead = false;
+      int wall = -1, wcell = -1;
+      for (; k < kWalkLimit; ++k) {
+        const bool needx = oi != cx, needy = oj != cy;
+        if (!needx && !needy) break;
+        const float facex = float(si > 0 ? oi + 1 : oi);
+        const float facey = float(sj > 0 ? oj + 1 : oj);
+        const bool xfirst = fabsf(facex - fx) * ady <= fabsf(facey - fy) * adx;
+        const bool takex = needx && (!needy || xfirst);
+        if (takex) oi += si; else oj += sj;
+        int gi = i + oi, gj = j + oj;
+        bool outx = false, outy = false;
+        if (g.px) gi = wrapmod(gi, g.nx); else outx = gi < 0 || gi >= g.nx;
+        if (g.py) gj = wrapmod(gj, g.ny); else outy = gj < 0 || gj >= g.ny;
+        if (outx || outy || !__ldg(&a.cellmask[gi * g.ny + gj])) {
+          dead = true;
+          if (takex) {
+            wall = si > 0 ? (outx ? PIC_WALL_XMAX : PIC_WALL_COND_PX)
+                          : (outx ? PIC_WALL_XMIN : PIC_WALL_COND_MX);
+            wcell = gj;
+          } else {
+            wall = sj > 0 ? (outy ? PIC_WALL_YMAX : PIC_WALL_COND_PY)
+                          : (outy ? PIC_WALL_YMIN : PIC_WALL_COND_MY);
+            wcell = gi;
+          }
+          break;
+        }
+        ni = gi;
+        nj = gj;
+      }
+      if (!dead && (oi != cx || oj != cy)) {
+        // moved farther than the walk limit: flag and drop without a tally
+        atomicOr(a.status, PIC_ST_CFL);
+        c = -1;
+        return;
+      }
+      if (dead) {
+        c = -1;
+        atomicAdd(&a.walls[s * PIC_NWALLS + wall], 1ull);
+        if (wall == PIC_WALL_XMAX) atomicAdd(&a.bottom[s * g.ny + wcell], 1ull);
+        const unsigned long long h = atomicAdd(a.nhits, 1ull);
+        if ((long long)h < a.hit_cap) {
+          pic_hit rec;
+          rec.id = a.pb[s].id[slot];
+          rec.species = int16_t(s);
+          rec.wall = int16_t(wall);
+          rec.cell = wcell;
+          rec.step = *a.step;
+          rec.vx = vx1;
+          rec.vy = vy1;
+          a.hits[h] = rec;
+        } else {
+          atomicOr(a.status, PIC_ST_FULL);
+        }
+        return;
+      }
+      nfx -= cxf;
+      nfy -= cyf;
+      nfx = fminf(nfx, 0x1.fffffep-1f);
+      nfy = fminf(nfy, 0x1.fffffep-1f);
+    }
+    fx = nfx;
+    fy = nfy;
+    c = ni * g.ny + nj;
+    // fall through to the deposit at the new position
+    int w00, w01, w10, w11;
+    cic_weights(fx, fy, w00, w01, w10, w11);
+    const int lni = local_coord(ni, wi0, g.nx, g.px);
+    const int lnj = local_coord(nj, wj0, g.ny, g.py);
+    if ((unsigned)lni < (unsigned)WXc && (unsigned)lnj < (unsigned)WYc) {
+      const int kk = lni * NWY + lnj;
+      atomicAdd(&sAcc[kk], (uint32_t)w00);
+      atomicAdd(&sAcc[kk + 1], (uint32_t)w01);
+      atomicAdd(&sAcc[kk + NWY], (uint32_t)w10);
+      atomicAdd(&sAcc[kk + NWY + 1], (uint32_t)w11);
+    } else {
+      deposit_global(a, acc, ni, nj, w00, w01, w10, w11);
+    }
+  } else {
+    // deposit only, at the current position
+    int w00, w01, w10, w11;
+    cic_weights(fx, fy, w00, w01, w10, w11);
+    const int li = local_coord(i, wi0, g.nx, g.px);
+    const int lj = local_coord(j, wj0, g.ny, g.py);
+    if ((unsigned)li < (unsigned)WXc && (unsigned)lj < (unsigned)WYc) {
+      const int kk = li * NWY + lj;
+      atomicAdd(&sAcc[kk], (uint32_t)w00);
+      atomicAdd(&sAcc[kk + 1], (uint32_t)w01);
+      atomicAdd(&sAcc[kk + NWY], (uint32_t)w10);
+      atomicAdd(&sAcc[kk + NWY + 1], (uint32_t)w11);
+    } else {
+      deposit_global(a, acc, i, j, w00, w01, w10, w11);
+    }
+  }
+}
+
+template <int MODE>
+__global__ void __launch_bounds__(kParticleThreads) k_particles(PArgs a) {
+  __shared__ float2 sE[NWX * NWY];
+  __shared__ uint32_t sAcc[NWX * NWY];
+  __shared__ double sRed[kParticleThreads / 32];
+  const Geom g = a.g;
+  const int nch = *a.nchunks;
+  const int nnodes = g.nxn * g.nyn;
+  if (MODE == 0 && blockIdx.x == 0 && threadIdx.x == 0) a.fe[1] = a.fe[0];
+  for (int ci = blockIdx.x; ci < nch; ci += gridDim.x) {
+    const Chunk ch = a.chunks[ci];
+    const int s = ch.species;
+    const int ti = ch.tile / g.nty;
+    const int tj = ch.tile - ti * g.nty;
+    const int wi0 = ti * kTileX - kHalo;
+    const int wj0 = tj * kTileY - kHalo;
+    for (int k = threadIdx.x; k < NWX * NWY; k += blockDim.x) {
+      if (MODE != 1) {
+        const int wi = k / NWY, wj = k - (k / NWY) * NWY;
+        int gi = wi0 + wi, gj = wj0 + wj;
+        if (g.px) gi = wrapmod(gi, g.nxn);
+        if (g.py) gj = wrapmod(gj, g.nyn);
+        float2 e = make_float2(0.f, 0.f);
+        if (gi >= 0 && gi < g.nxn && gj >= 0 && gj < g.nyn) e = a.E[gi * g.nyn + gj];
+        sE[k] = e;
+      }
+      sAcc[k] = 0u;
+    }
+    __syncthreads();
+    unsigned long long *acc = a.acc + (int64_t)s * nnodes;
+    const ParticleBuf P = a.pb[s];
+    float ke = 0.f;
+    for (int64_t base = ch.begin + 4 * threadIdx.x; base < ch.end; base += 4 * blockDim.x) {
+      int4 c4 = *reinterpret_cast<const int4 *>(P.cell + base);
+      float4 fx4 = *reinterpret_cast<const float4 *>(P.fx + base);
+      float4 fy4 = *reinterpret_cast<const float4 *>(P.fy + base);
+      float4 vx4 = make_float4(0.f, 0.f, 0.f, 0.f), vy4 = vx4;
+      if (MODE != 1) {
+        vx4 = *reinterpret_cast<const float4 *>(P.vx + base);
+        vy4 = *reinterpret_cast<const float4 *>(P.vy + base);
+      }
+      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, base + 0, c4.x, fx4.x, fy4.x, vx4.x, vy4.x, ke);
+      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, base + 1, c4.y, fx4.y, fy4.y, vx4.y, vy4.y, ke);
+      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, base + 2, c4.z, fx4.z, fy4.z, vx4.z, vy4.z, ke);
+      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, base + 3, c4.w, fx4.w, fy4.w, vx4.w, vy4.w, ke);
+      if (MODE == 0) {
+        *reinterpret_cast<int4 *>(P.cell + base) = c4;
+        *reinterpret_cast<float4 *>(P.fx + base) = fx4;
+        *reinterpret_cast<float4 *>(P.fy + base) = fy4;
+      }
+      if (MODE != 1) {
+        *reinterpret_cast<float4 *>(P.vx + base) = vx4;
+        *reinterpret_cast<float4 *>(P.vy + base) = vy4;
+      }
+    }
+    __syncthreads();
+    if (MODE != 2) {
+      for (int k = threadIdx.x; k < NWX * NWY; k += blockDim.x) {
+        const uint32_t v = sAcc[k];
+        if (v) {
+          const int wi = k / NWY, wj = k - (k / NWY) * NWY;
+          int gi = wi0 + wi, gj = wj0 + wj;
+          if (g.px) gi = wrapmod(gi, g.nxn);
+          if (g.py) gj = wrapmod(gj, g.nyn);
+          if (gi >= 0 && gi < g.nxn && gj >= 0 && gj < g.nyn)
+            atomicAdd(&acc[gi * g.nyn + gj], (unsigned long long)v);
+        }
+      }
+    }
+    if (MODE == 0) {
+      double v = ke;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+      if ((threadIdx.x & 31) == 0) sRed[threadIdx.x >> 5] = v;
+      __syncthreads();
+      if (threadIdx.x == 0) {
+        double t = 0.0;
+        for (int w = 0; w < kParticleThreads / 32; ++w) t += sRed[w];
+        a.ke_part[ci] = t;
+      }
+    }
+    __syncthreads();
+  }
+}
+
+// ---------------------------------------------------------------------------
+// Load conversion, export, reductions
+// ---------------------------------------------------------------------------
+__global__ void k_load_convert(ParticleBuf P, Geom g, const uint8_t *cellmask, const double *x,
+                               const double *y, const double *vx, const double *vy,
+                               const uint32_t *id, int64_t offset, int64_t n, uint32_t *status) {
+  const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
+  if (k >= n) return;
+  double X = x[k], Y = y[k];
+  if (g.px) {
+    X = fmod(X, double(g.nx));
+    if (X < 0) X += g.nx;
+    if (X >= g.nx) X -= g.nx;
+  }
+  if (g.py) {
+    Y = fmod(Y, double(g.ny));
+    if (Y < 0) Y += g.ny;
+    if (Y >= g.ny) Y -= g.ny;
+  }
+  const double fi = floor(X), fj = floor(Y);
+  int c = -1;
+  float fx = 0.f, fy = 0.f;
+  if (X == X && Y == Y && fi >= 0 && fi < g.nx && fj >= 0 && fj < g.ny) {
+    const int i = int(fi), j = int(fj);
+    if (cellmask[i * g.ny + j]) {
+      c = i * g.ny + j;
+      fx = fminf(float(X - fi), 0x1.fffffep-1f);
+      fy = fminf(float(Y - fj), 0x1.fffffep-1f);
+    }
+  }
+  if (c < 0) atomicOr(status, PIC_ST_RANGE);
+  const int64_t d = offset + k;
+  P.cell[d] = c;
+  P.fx[d] = fx;
+  P.fy[d] = fy;
+  P.vx[d] = float(vx[k]);
+  P.vy[d] = float(vy[k]);
+  P.id[d] = id ? id[k] : uint32_t(offset + k);
+}
+
+__global__ void k_export(ParticleBuf P, Geom g, const int64_t *nslots_p, double *out, int64_t cap,
+                         unsigned long long *counter) {
+  const int64_t nslots = *nslots_p;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < nslots; base += nwarps * 32) {
+    const int64_t p = base + lane;
+    const int c = p < nslots ? P.cell[p] : -1;
+    const unsigned live = __ballot_sync(0xffffffffu, c >= 0);
+    unsigned long long b = 0;
+    if (lane == 0 && live) b = atomicAdd(counter, (unsigned long long)__popc(live));
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (c >= 0) {
+      const int64_t d = int64_t(b) + __popc(live & ((1u << lane) - 1u));
+      if (d < cap) {
+        const int i = c / g.ny, j = c - (c / g.ny) * g.ny;
+        out[d] = double(i) + double(P.fx[p]);
+        out[cap + d] = double(j) + double(P.fy[p]);
+        out[2 * cap + d] = double(P.vx[p]);
+        out[3 * cap + d] = double(P.vy[p]);
+        out[4 * cap + d] = double(P.id[p]);
+      }
+    }
+  }
+}
+
+// per-block partial sums of [vx, vy, live] of one species
+__global__ void k_moments(ParticleBuf P, const int64_t *nslots_p, double *part) {
+  const int64_t nslots = *nslots_p;
+  double sx = 0, sy = 0, sn = 0;
+  for (int64_t p = int64_t(blockIdx.x) * blockDim.x + threadIdx.x; p < nslots;
+       p += int64_t(gridDim.x) * blockDim.x) {
+    if (P.cell[p] >= 0) {
+      sx += P.vx[p];
+      sy += P.vy[p];
+      sn += 1.0;
+    }
+  }
+  __shared__ double r[3][32];
+  for (int o = 16; o > 0; o >>= 1) {
+    sx += __shfl_down_sync(0xffffffffu, sx, o);
+    sy += __shfl_down_sync(0xffffffffu, sy, o);
+    sn += __shfl_down_sync(0xffffffffu, sn, o);
+  }
+  const int w = threadIdx.x >> 5;
+  if ((threadIdx.x & 31) == 0) {
+    r[0][w] = sx;
+    r[1][w] = sy;
+    r[2][w] = sn;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    double a = 0, b = 0, n = 0;
+    for (int k = 0; k < int(blockDim.x >> 5); ++k) {
+      a += r[0][k];
+      b += r[1][k];
+      n += r[2][k];
+    }
+    part[3 * blockIdx.x + 0] = a;
+    part[3 * blockIdx.x + 1] = b;
+    part[3 * blockIdx.x + 2] = n;
+  }
+}
+
+int particle_grid(pic_ctx *c) {
+  int per_sm = 0;
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_particles<0>, kParticleThreads, 0);
+  if (per_sm < 1) per_sm = 1;
+  return c->num_sms * per_sm;
+}
+
+}  // namespace
+
+cudaError_t launch_sort(pic_ctx *c) {
+  SortArgs a;
+  for (int s = 0; s < 2; ++s) {
+    a.src[s] = c->pb[s][c->cur[s]];
+    a.dst[s] = c->pb[s][c->cur[s] ^ 1];
+  }
+  a.nslots = c->d_nslots;
+  a.count = c->d_tile_count;
+  a.cursor = c->d_tile_cursor;
+  a.start = c->d_tile_start;
+  a.chunks = c->d_chunks;
+  a.nchunks = c->d_nchunks;
+  a.nslots_out = c->d_nslots + 2;
+  a.g = c->g;
+  a.ntiles = c->g.ntx * c->g.nty;
+  const dim3 grid(c->num_sms * 4, 2);
+  k_sort_hist<<<grid, 256, 0, c->stream>>>(a);
+  k_sort_scan<<<1, 1024, 0, c->stream>>>(a);
+  k_sort_scatter<<<grid, 256, 0, c->stream>>>(a);
+  k_sort_finish<<<1, 1, 0, c->stream>>>(c->d_nslots);
+  for (int s = 0; s < 2; ++s) c->cur[s] ^= 1;
+  return cudaGetLastError();
+}
+
+cudaError_t launch_particles(pic_ctx *c, int mode, float kick_factor, const int *species_mask) {
+  PArgs a;
+  for (int s = 0; s < 2; ++s) {
+    a.pb[s] = c->pb[s][c->cur[s]];
+    a.qdt[s] = float(c->cfg.alpha[s] * c->cfg.dt * kick_factor);
+    a.kick[s] = species_mask ? species_mask[s] : 1;
+  }
+  a.chunks = c->d_chunks;
+  a.nchunks = c->d_nchunks;
+  a.E = c->d_E;
+  a.acc = c->d_acc;
+  a.cellmask = c->d_cellmask;
+  a.g = c->g;
+  a.dt = float(c->cfg.dt);
+  a.walls = c->d_walls;
+  a.bottom = c->d_bottom;
+  a.hits = c->d_hits;
+  a.nhits = c->d_nhits;
+  a.hit_cap = c->cfg.hit_capacity;
+  a.status = c->d_status;
+  a.step = c->d_step;
+  a.ke_part = c->d_ke_part;
+  a.fe = c->d_fe;
+  const int grid = particle_grid(c);
+  switch (mode) {
+    case 0: k_particles<0><<<grid, kParticleThreads, 0, c->stream>>>(a); break;
+    case 1: k_particles<1><<<grid, kParticleThreads, 0, c->stream>>>(a); break;
+    default: k_particles<2><<<grid, kParticleThreads, 0, c->stream>>>(a); break;
+  }
+  return cudaGetLastError();
+}
+
+cudaError_t launch_load_convert(pic_ctx *c, int s, const double *d_x, const double *d_y,
+                                const double *d_vx, const double *d_vy, const uint32_t *d_id,
+                                int64_t offset, int64_t n) {
+  if (n <= 0) return cudaSuccess;
+  const int64_t blocks = (n + 255) / 256;
+  k_load_convert<<<dim3((unsigned)blocks), 256, 0, c->stream>>>(
+      c->pb[s][c->cur[s]], c->g, c->d_cellmask, d_x, d_y, d_vx, d_vy, d_id, offset, n,
+      c->d_status);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_state(pic_ctx *c, int s, double *d_out, int64_t cap,
+                                unsigned long long *d_counter) {
+  k_export<<<c->num_sms * 4, 256, 0, c->stream>>>(c->pb[s][c->cur[s]], c->g, c->d_nslots + s,
+                                                   d_out, cap, d_counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_moments(pic_ctx *c, int s, double *d_part, int nblocks) {
+  k_moments<<<nblocks, 256, 0, c->stream>>>(c->pb[s][c->cur[s]], c->d_nslots + s, d_part);
+  return cudaGetLastError();
+}
+
+}  // namespace picgb

@@ -1,0 +1,57 @@
+"""The C-ABI library builds, loads and exports every entry point that
+include/*.h declares (CPU only: no compute call is made)."""
+import ctypes
+import glob
+import os
+import re
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+
+
+def declared_symbols():
+    names = set()
+    for h in glob.glob(os.path.join(ROOT, "include", "*.h")):
+        text = open(h).read()
+        text = re.sub(r"/\*.*?\*/", "", text, flags=re.S)
+        for m in re.finditer(r"^\s*(?:const\s+)?[A-Za-z_][A-Za-z0-9_]*\s*\*?\s*(pic_[a-z0-9_]+)\s*\(",
+                             text, flags=re.M):
+            names.add(m.group(1))
+    return names
+
+
+@pytest.fixture(scope="module")
+def lib():
+    from paper_1610_03918_gb300 import build
+    if not os.path.exists(build.lib_path()):
+        build.build()
+    return ctypes.CDLL(build.lib_path())
+
+
+def test_header_declares_the_boundary():
+    names = declared_symbols()
+    for n in ("pic_init", "pic_load", "pic_step", "pic_diag", "pic_free", "pic_strerror"):
+        assert n in names, names
+
+
+def test_library_exports_every_declared_symbol(lib):
+    for n in sorted(declared_symbols()):
+        assert hasattr(lib, n), f"{n} declared in include/ but not exported"
+
+
+def test_strerror_without_gpu(lib):
+    lib.pic_strerror.restype = ctypes.c_char_p
+    assert lib.pic_strerror(0) == b"ok"
+    assert b"Poisson" in lib.pic_strerror(4)
+
+
+def test_init_rejects_bad_config_without_touching_gpu(lib):
+    import paper_1610_03918_gb300 as pg
+    import synth
+    cfg = pg.make_config(synth.periodic_square_64(nx=63))   # odd periodic size
+    ctx = ctypes.c_void_p()
+    assert pg.load_library().pic_init(ctypes.byref(cfg), ctypes.byref(ctx)) == pg.PIC_EINVAL
+    cfg = pg.make_config(synth.small_trench())
+    cfg.sort_every = 0
+    assert pg.load_library().pic_init(ctypes.byref(cfg), ctypes.byref(ctx)) == pg.PIC_EINVAL

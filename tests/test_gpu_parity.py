@@ -1,0 +1,238 @@
+"""CUDA path (through the C ABI) against the FP64 oracle on identical seeded
+states: deposit, Poisson solve, field, push, absorption tallies, surface
+charge, per-step parity and edge cases.  Needs a GB300."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import field as ofield
+from oracle import poisson as opoisson
+from oracle.geometry import from_workload
+
+from gpu_helpers import (FIELD_TOL, RHO_TOL, compare_states, compare_states_grazing, gpu_sim,
+                         load_both, off_face_state, oracle_sim, oracle_state, vacuum_field)
+
+pytestmark = pytest.mark.gpu
+
+# workloads small enough for the oracle, spanning several 16x16 tiles with
+# ragged tails
+SMALL = {
+    "trench": synth.small_trench(nx=72, ny=40, depth=20, width=6, ppc=12, seed=11),
+    "bounded": synth.bounded_square_256(nx=45, ny=38, ppc=10, seed=12),
+    "periodic": synth.periodic_square_64(nx=48, ny=34, ppc=10, seed=13),
+}
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _loaded(w, rtol=1e-10, **kw):
+    w = w.replace(poisson_rtol=rtol)
+    gs = gpu_sim(w, **kw)
+    os_ = oracle_sim(w)
+    for s in (0, 1):
+        load_both(gs, os_, s, synth.maxwellian_load(w, s))
+    return w, gs, os_
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_deposit_matches_oracle(name):
+    w, gs, os_ = _loaded(SMALL[name])
+    gs.step(0)
+    rg = gs.rho()
+    ro = os_.charge_density()
+    scale = np.abs(ro).max()
+    assert np.abs(rg - ro).max() <= RHO_TOL * scale, np.abs(rg - ro).max() / scale
+    # charge conservation: the fixed-point deposit is exact per particle
+    assert rg.sum() == pytest.approx(ro.sum(), abs=1e-9 * np.abs(ro).sum())
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_poisson_and_field_match_oracle(name):
+    w = SMALL[name].replace(poisson_rtol=1e-10)
+    gs = gpu_sim(w)
+    geom = from_workload(w)
+    rho = synth.random_rho(w, seed=21, scale=0.3)
+    gs.set_rho_ext(rho)
+    gs.step(0)
+    it, outer, rel, ms = gs.poisson_stats()
+    assert rel <= 1e-10
+    phi_g = gs.phi()
+    phi_o = opoisson.solve_direct(geom, rho)
+    # the oracle's own FP64 residual of the GPU potential certifies it
+    assert opoisson.residual_rel(geom, phi_g, rho) <= 2e-10
+    assert np.abs(phi_g - phi_o).max() <= 1e-6 * np.abs(phi_o).max()
+    Exg, Eyg = gs.efield()
+    Exo, Eyo = ofield.efield(geom, phi_o)
+    emax = max(np.abs(Exo).max(), np.abs(Eyo).max())
+    assert np.abs(Exg - Exo).max() <= FIELD_TOL * emax
+    assert np.abs(Eyg - Eyo).max() <= FIELD_TOL * emax
+
+
+def test_poisson_trench_bias_vacuum():
+    # the biased electrode with the trench and no charge: a pure Laplace solve
+    w = synth.small_trench(nx=96, ny=64, depth=40, width=10).replace(poisson_rtol=1e-10)
+    gs = gpu_sim(w)
+    gs.step(0)
+    geom = from_workload(w)
+    phi_o = opoisson.solve_direct(geom, np.zeros((geom.nxn, geom.nyn)))
+    assert np.abs(gs.phi() - phi_o).max() <= 1e-6 * 20.0
+
+
+@pytest.mark.parametrize("name", list(SMALL))
+def test_step_by_step_parity(name):
+    """Each step starts both sides from the GPU's state; the oracle recomputes
+    its own fields from it."""
+    w, gs, os_ = _loaded(SMALL[name])
+    geom = from_workload(w)
+    gs.step(0)
+    os_.prepare()
+    for k in range(4):
+        st = [gs.state(0), gs.state(1)]
+        os_ = oracle_sim(w)
+        for s in (0, 1):
+            os_.load(s, st[s][0], st[s][1], st[s][2], st[s][3], st[s][4].astype(np.uint32))
+        # the charge collected on the trench bottom so far is part of the state
+        os_.bottom[:] = gs.surface()
+        os_.counts[:] = gs.counts()[0]
+        os_.prepare()
+        # fields of the same state agree
+        Exg, Eyg = gs.efield()
+        emax = max(np.abs(os_.Ex).max(), np.abs(os_.Ey).max())
+        assert np.abs(Exg - os_.Ex).max() <= FIELD_TOL * emax
+        assert np.abs(Eyg - os_.Ey).max() <= FIELD_TOL * emax
+        gs.step(1)
+        os_.step(1)
+        for s in (0, 1):
+            compare_states_grazing(gs.state(s), oracle_state(os_, s), w, s)
+        rg, ro = gs.rho(), os_.rho
+        assert np.abs(rg - ro).max() <= RHO_TOL * np.abs(ro).max() + 1e-3 / w.ppc
+        e = gs.energy()
+        assert e[0] == pytest.approx(os_.ke[0], rel=1e-5)
+        assert e[1] == pytest.approx(os_.ke[1], rel=1e-5)
+        assert e[2] == pytest.approx(os_.fe, rel=1e-5)
+
+
+def test_absorption_tallies_bit_exact():
+    # negligible particle weight: the field is the vacuum field of the biased
+    # electrode, so the off-face margins hold for both sides
+    w = synth.small_trench(nx=72, ny=40, depth=24, width=8, ppc=10 ** 7, seed=5).replace(
+        poisson_rtol=1e-10)
+    E = vacuum_field(w)
+    gs = gpu_sim(w, capacity=200000)
+    os_ = oracle_sim(w)
+    pe = off_face_state(w, 0, 120000, seed=1, vscale=6.0, E=E)
+    pi = off_face_state(w, 1, 120000, seed=2, vscale=400.0, E=E)
+    load_both(gs, os_, 0, pe)
+    load_both(gs, os_, 1, pi)
+    gs.step(1)
+    os_.step(1)
+    walls, live = gs.counts()
+    assert np.array_equal(walls, os_.counts)
+    assert np.array_equal(live, os_.live())
+    assert walls.sum() > 1000 and walls[1, 1] > 10 and walls[0, 6] > 0 and walls[0, 7] > 0
+    assert np.array_equal(gs.surface(), os_.bottom)
+    hg = gs.hits()
+    ho = os_.hit_table()
+    kg = sorted(zip(hg["species"].tolist(), hg["id"].tolist(), hg["wall"].tolist(), hg["cell"].tolist()))
+    ko = sorted(zip(ho["species"].tolist(), ho["ids"].tolist(), ho["wall"].tolist(), ho["cell"].tolist()))
+    assert kg == ko
+    for s in (0, 1):
+        compare_states(gs.state(s), oracle_state(os_, s), w, s)
+
+
+def test_surface_charge_feeds_rho():
+    w = synth.small_trench(nx=48, ny=32, depth=16, width=6, ppc=4).replace(poisson_rtol=1e-10)
+    gs = gpu_sim(w)
+    os_ = oracle_sim(w)
+    y0 = w.trench_y0
+    # ions moving straight into the bottom of the trench
+    x = np.full(6, 47.95)
+    y = y0 + 0.5 + np.arange(6, dtype=np.float64)
+    load_both(gs, os_, 1, synth.Particles(x, y, np.full(6, 1.0), np.zeros(6), np.arange(6, dtype=np.uint32)))
+    gs.step(1)
+    os_.step(1)
+    assert np.array_equal(gs.surface(), os_.bottom)
+    assert gs.surface()[1, y0:y0 + 6].tolist() == [1] * 6
+    np.testing.assert_allclose(gs.rho(), os_.rho, atol=1e-12)
+
+
+def test_v_at_t0_half_kick_closed_form():
+    w = synth.Workload(name="plates", nx=40, ny=16, periodic_y=True, phi_top=0.0,
+                       phi_electrode=-20.0, ppc=10 ** 9, poisson_rtol=1e-10)
+    gs = gpu_sim(w, capacity=16)
+    x0, y0, v0x, v0y = 20.3, 3.6, 0.05, -0.02
+    gs.load(1, [x0], [y0], [v0x], [v0y], v_at_t0=True)
+    gs.step(50)
+    t = 50 * w.dt
+    a = w.alpha[1] * 0.5
+    st = gs.state(1)
+    assert st[0, 0] == pytest.approx(x0 + v0x * t + 0.5 * a * t * t, abs=2e-5)
+    assert st[1, 0] == pytest.approx(y0 + v0y * t, abs=2e-5)
+
+
+def test_edge_cases():
+    import paper_1610_03918_gb300 as pg
+    w = SMALL["trench"].replace(poisson_rtol=1e-10)
+    gs = gpu_sim(w, capacity=1000)
+    # empty species and an empty step
+    gs.step(2)
+    assert gs.counts()[1].tolist() == [0, 0]
+    # particles exactly on faces and nodes, one per tile corner
+    x = np.array([0.0, 16.0, 31.0, 47.0, 51.0])
+    y = np.array([0.0, 16.0, 17.0, 32.0, 39.0])
+    os_ = oracle_sim(w)
+    p = synth.Particles(x, y, np.zeros(5), np.zeros(5), np.arange(5, dtype=np.uint32))
+    load_both(gs, os_, 0, p)
+    gs.step(0)
+    os_.prepare()
+    np.testing.assert_allclose(gs.rho(), os_.charge_density(), atol=1e-6)
+    # over capacity
+    big = np.zeros(1001)
+    assert pg.pic_load(gs.ctx, 0, big, big, big, big) == pg.PIC_EOVERFLOW
+    # a particle inside the conductor is dropped and flagged
+    st = pg.pic_load(gs.ctx, 1, np.array([70.5, 3.5]), np.array([2.5, 3.5]), np.zeros(2), np.zeros(2))
+    assert st == pg.PIC_OK
+    gs.step(0)
+    assert gs.counts()[1].tolist()[1] == 1
+    assert gs.status() & pg.PIC_ST_RANGE
+    assert gs.status() == 0
+
+
+def test_hit_buffer_full_keeps_tallies_exact():
+    import paper_1610_03918_gb300 as pg
+    w = synth.small_trench(nx=48, ny=32, depth=16, width=6, ppc=10 ** 7).replace(poisson_rtol=1e-8)
+    gs = gpu_sim(w, capacity=50000, hit_capacity=10)
+    os_ = oracle_sim(w)
+    E = vacuum_field(w)
+    pe = off_face_state(w, 0, 40000, seed=3, vscale=8.0, E=E)
+    load_both(gs, os_, 0, pe)
+    gs.step(1)
+    os_.step(1)
+    walls, _ = gs.counts()
+    assert np.array_equal(walls, os_.counts)
+    assert len(gs.hits()) == 10
+    assert gs.status() & pg.PIC_ST_FULL
+
+
+def test_periodic_box_conservation():
+    w = synth.periodic_square_64(ppc=20, poisson_rtol=1e-8)
+    gs = gpu_sim(w)
+    for s in (0, 1):
+        gs.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
+    gs.step(1)
+    m0 = gs.momentum().sum(axis=0)
+    e0 = gs.energy()
+    tot0 = e0[0] + e0[1] + e0[2]
+    gs.step(199)
+    m1 = gs.momentum().sum(axis=0)
+    e1 = gs.energy()
+    tot1 = e1[0] + e1[1] + e1[2]
+    # thermal momentum scale: sqrt(N) * m w v_th for electrons
+    n = 64 * 64 * 20
+    pscale = np.sqrt(n) / 20
+    assert np.abs(m1 - m0).max() <= 1e-3 * pscale
+    assert abs(tot1 - tot0) <= 0.01 * tot0
