@@ -55,7 +55,8 @@ typedef enum {
   PIC_ETIMEOUT = 7,   /* reserved: a bounded device wait gave up */
   PIC_EFULL = 8,      /* hit-record buffer full (tallies stay exact) */
   PIC_ESTATE = 9,     /* call not valid in the current state */
-  PIC_ERANGE = 10     /* pic_load got a particle outside the plasma region */
+  PIC_ERANGE = 10,    /* pic_load got a particle outside the plasma region */
+  PIC_ESIZE = 11      /* grid larger than the fixed scratch of pic_deposit_static */
 } pic_status;
 
 /* Status-word bits (PIC_DIAG_STATUS). */
@@ -177,6 +178,34 @@ pic_status pic_free(pic_ctx *ctx);
 
 /* Static description of a status code. */
 const char *pic_strerror(pic_status st);
+
+/* Cloud-in-cell deposit that allocates no device memory.  The paper has no
+ * counterpart; this is a service for callers that cannot allocate at the
+ * point where they deposit -- a program whose device memory is owned by
+ * another runtime's pool, or a latency-critical loop that cannot take the
+ * device-wide synchronisation an allocation or release may cause.
+ *
+ * Computes rho[n] = weight * (sum over particles of their bilinear shares at
+ * node n), with the same fixed-point arithmetic as the context-based deposit
+ * (shares quantised to 2^-20 of a particle, summed exactly), for n particles
+ * at absolute positions x[k], y[k] on a grid of nx x ny cells (N + 1 nodes
+ * in a bounded direction, N in a periodic one; periodic coordinates wrap).
+ * x, y (n doubles each) and rho (nodes, row-major, y fastest) are DEVICE
+ * pointers owned by the caller; particles outside the grid are skipped.
+ * Work is queued on `stream` (a cudaStream_t, NULL = legacy default stream)
+ * of the current device and the call returns once it is queued.
+ *
+ * Scratch: one fixed array of 2^20 64-bit accumulators (8 MiB), a static
+ * device variable of the library that every GPU loading the library holds
+ * until the process exits.  Grids with more than 2^20 nodes return
+ * PIC_ESIZE.  The first call on a device (that device current) looks up the
+ * array's device address; make that first call before any stream capture.
+ * Every call clears and reuses the same array, so calls whose work overlaps
+ * on one GPU (different streams, or different host threads) race and must
+ * be serialised by the caller. */
+pic_status pic_deposit_static(int32_t nx, int32_t ny, int32_t periodic_x, int32_t periodic_y,
+                              int64_t n, const double *x, const double *y, double weight,
+                              double *rho, void *stream);
 
 #ifdef __cplusplus
 }

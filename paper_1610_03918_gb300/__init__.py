@@ -23,6 +23,7 @@ from .build import lib_path
 # status codes and constants mirrored from include/picgb.h
 PIC_OK, PIC_EINVAL, PIC_ENOMEM, PIC_ECUDA, PIC_ENOCONV = 0, 1, 2, 3, 4
 PIC_EOVERFLOW, PIC_ECFL, PIC_ETIMEOUT, PIC_EFULL, PIC_ESTATE, PIC_ERANGE = 5, 6, 7, 8, 9, 10
+PIC_ESIZE = 11
 PIC_ST_NOCONV, PIC_ST_FULL, PIC_ST_CFL, PIC_ST_RANGE, PIC_ST_CAPACITY = 1, 2, 4, 8, 16
 PIC_LOAD_V_AT_T0 = 1
 (PIC_DIAG_ENERGY, PIC_DIAG_MOMENTUM, PIC_DIAG_COUNTS, PIC_DIAG_SURFACE, PIC_DIAG_HITS,

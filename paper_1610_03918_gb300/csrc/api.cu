@@ -212,6 +212,7 @@ const char *pic_strerror(pic_status st) {
     case PIC_EFULL: return "hit-record buffer full";
     case PIC_ESTATE: return "call not valid in the current state";
     case PIC_ERANGE: return "particle outside the plasma region";
+    case PIC_ESIZE: return "grid has more nodes than the fixed deposit scratch (2^20)";
   }
   return "unknown status";
 }

@@ -1,0 +1,128 @@
+// Cloud-in-cell deposit that allocates nothing (pic_deposit_static).
+//
+// Who needs it: code that may not call cudaMalloc / cudaFree at the point
+// where it deposits -- for example a host program whose device memory is
+// already fully reserved by another runtime's pool, or a latency-critical
+// loop that cannot afford the device-wide synchronisation an allocation or
+// release can cause.  Such a caller passes its own input and output buffers;
+// the only scratch this entry point uses is the fixed-size accumulator below,
+// which lives in the library image on every GPU that loads the library,
+// until the process exits.
+//
+// The arithmetic is the one of the context-based deposit: each particle's
+// four bilinear shares are quantised to 2^-20 of its weight (three rounded
+// to nearest-even, the fourth the remainder) and summed exactly in 64-bit
+// integers, so the result does not depend on particle order.
+#include <cuda_runtime.h>
+
+#include <mutex>
+
+#include "picgb.h"
+
+namespace {
+
+constexpr long long kStaticMaxNodes = 1ll << 20;   // 8 MiB of 64-bit accumulators
+constexpr int kMaxDevices = 64;
+constexpr int kThreads = 256;
+
+// The scratch.  In host code this name is only a stand-in for the device
+// symbol: its device address comes from cudaGetSymbolAddress below.
+static __device__ __align__(256) unsigned long long g_deposit_scratch[kStaticMaxNodes];
+
+std::mutex g_mu;
+unsigned long long *g_scratch_ptr[kMaxDevices] = {};
+
+// Device address of the scratch on the current device, looked up once per
+// device (with that device current) and cached.
+pic_status scratch_address(int dev, unsigned long long **out) {
+  if (dev < 0 || dev >= kMaxDevices) return PIC_EINVAL;
+  std::lock_guard<std::mutex> lock(g_mu);
+  if (!g_scratch_ptr[dev]) {
+    void *p = nullptr;
+    if (cudaGetSymbolAddress(&p, g_deposit_scratch) != cudaSuccess || !p) return PIC_ECUDA;
+    g_scratch_ptr[dev] = static_cast<unsigned long long *>(p);
+  }
+  *out = g_scratch_ptr[dev];
+  return PIC_OK;
+}
+
+__global__ void k_clear(unsigned long long *acc, long long nn) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nn;
+       k += (long long)gridDim.x * blockDim.x)
+    acc[k] = 0ull;
+}
+
+__global__ void k_deposit(const double *x, const double *y, long long n, int nx, int ny, int px,
+                          int py, int nyn, unsigned long long *acc) {
+  const float q = 1048576.0f;   // 2^20
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < n;
+       k += (long long)gridDim.x * blockDim.x) {
+    double X = x[k], Y = y[k];
+    if (px) {
+      X = fmod(X, double(nx));
+      if (X < 0) X += nx;
+      if (X >= nx) X -= nx;
+    }
+    if (py) {
+      Y = fmod(Y, double(ny));
+      if (Y < 0) Y += ny;
+      if (Y >= ny) Y -= ny;
+    }
+    const double fi = floor(X), fj = floor(Y);
+    if (!(fi >= 0 && fi < nx && fj >= 0 && fj < ny)) continue;   // outside the grid: skipped
+    const int i = int(fi), j = int(fj);
+    const float fx = fminf(float(X - fi), 0x1.fffffep-1f);
+    const float fy = fminf(float(Y - fj), 0x1.fffffep-1f);
+    const float gx = 1.0f - fx, gy = 1.0f - fy;
+    const int w00 = __float2int_rn(gx * gy * q);
+    const int w10 = __float2int_rn(fx * gy * q);
+    const int w01 = __float2int_rn(gx * fy * q);
+    const int w11 = int(1u << 20) - w00 - w10 - w01;
+    int i1 = i + 1, j1 = j + 1;
+    if (px && i1 == nx) i1 = 0;
+    if (py && j1 == ny) j1 = 0;
+    atomicAdd(&acc[(long long)i * nyn + j], (unsigned long long)(long long)w00);
+    atomicAdd(&acc[(long long)i * nyn + j1], (unsigned long long)(long long)w01);
+    atomicAdd(&acc[(long long)i1 * nyn + j], (unsigned long long)(long long)w10);
+    atomicAdd(&acc[(long long)i1 * nyn + j1], (unsigned long long)(long long)w11);
+  }
+}
+
+__global__ void k_finish(const unsigned long long *acc, long long nn, double scale, double *rho) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nn;
+       k += (long long)gridDim.x * blockDim.x)
+    rho[k] = scale * double(acc[k]);
+}
+
+int grid_for(long long n) {
+  long long b = (n + kThreads - 1) / kThreads;
+  if (b < 1) b = 1;
+  if (b > 4096) b = 4096;
+  return int(b);
+}
+
+}  // namespace
+
+extern "C" pic_status pic_deposit_static(int32_t nx, int32_t ny, int32_t periodic_x,
+                                         int32_t periodic_y, int64_t n, const double *x,
+                                         const double *y, double weight, double *rho,
+                                         void *stream) {
+  if (nx < 1 || ny < 1 || n < 0 || !rho || (n > 0 && (!x || !y))) return PIC_EINVAL;
+  const long long nxn = periodic_x ? nx : (long long)nx + 1;
+  const long long nyn = periodic_y ? ny : (long long)ny + 1;
+  const long long nn = nxn * nyn;
+  if (nn > kStaticMaxNodes) return PIC_ESIZE;
+  int dev = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess) return PIC_ECUDA;
+  unsigned long long *acc = nullptr;
+  const pic_status st = scratch_address(dev, &acc);
+  if (st != PIC_OK) return st;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  // the scratch keeps the previous call's sums: clear the part this call uses
+  k_clear<<<grid_for(nn), kThreads, 0, s>>>(acc, nn);
+  if (n > 0)
+    k_deposit<<<grid_for(n), kThreads, 0, s>>>(x, y, n, nx, ny, periodic_x ? 1 : 0,
+                                               periodic_y ? 1 : 0, int(nyn), acc);
+  k_finish<<<grid_for(nn), kThreads, 0, s>>>(acc, nn, weight / 1048576.0, rho);
+  return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
