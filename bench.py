@@ -238,7 +238,7 @@ def main():
         w = w.replace(ppc=args.ppc)
     parts = [synth.maxwellian_load(w, s) for s in (0, 1)]
     n0 = sum(len(p) for p in parts)
-    sim = pg.Sim(w, capacity=len(parts[0]), device=local)
+    sim = pg.Sim(w, capacity=len(parts[0]), device=local, timing=True)
     for s in (0, 1):
         sim.load_particles(s, parts[s], v_at_t0=True)
     sim.step(args.warmup)

@@ -99,6 +99,11 @@ typedef struct {
   double poisson_rtol;            /* target ||b - A phi||_2 / ||b||_2 (FP64) */
   int32_t warm_start;             /* 0: zero initial guess each solve, 1: previous phi */
   int32_t device;                 /* CUDA device ordinal */
+  int32_t timing;                 /* 1: pic_step waits for each step and accumulates the
+                                     per-phase device times of PIC_DIAG_TIMING */
+  int32_t graphs;                 /* 1: each step is one launch of a captured CUDA graph whose
+                                     Poisson loops are device-side conditional nodes;
+                                     0: kernels launched from a host loop that polls the solver */
   int64_t hit_capacity;           /* hit records kept (PIC_DIAG_HITS) */
   void *stream;                   /* cudaStream_t to run on; NULL: a library-owned stream */
   void *(*alloc)(size_t bytes, void *user); /* optional device allocator */
@@ -161,9 +166,11 @@ pic_status pic_load(pic_ctx *ctx, int32_t species, int64_t n, const double *x,
 
 /* Advance nsteps leapfrog steps (Sec. II).  nsteps == 0 only brings the
  * fields up to date with the loaded state (deposit, Poisson solve, E) and
- * applies pending dt/2 back-kicks.  Work is queued on the context's stream;
- * the call returns once it is queued, except that it waits on the Poisson
- * solver's convergence flag. */
+ * applies pending dt/2 back-kicks (this part polls the solver from the host).
+ * With cfg->graphs the steps are queued as graph launches and the call
+ * returns without waiting (unless cfg->timing); a solve that fails to reach
+ * rtol sets PIC_ST_NOCONV, reported by the next pic_diag.  Without graphs the
+ * call waits on each solve and returns PIC_ENOCONV directly. */
 pic_status pic_step(pic_ctx *ctx, int32_t nsteps);
 
 /* Copy a diagnostic to host memory out (cap_bytes long); *n_out receives the

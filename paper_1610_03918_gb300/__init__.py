@@ -52,6 +52,7 @@ class PicConfig(ctypes.Structure):
         ("sort_every", ctypes.c_int32), ("poisson_maxit", ctypes.c_int32),
         ("poisson_rtol", ctypes.c_double),
         ("warm_start", ctypes.c_int32), ("device", ctypes.c_int32),
+        ("timing", ctypes.c_int32), ("graphs", ctypes.c_int32),
         ("hit_capacity", ctypes.c_int64),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
@@ -172,7 +173,8 @@ class _TorchAllocator:
 
 
 def make_config(w, capacity=None, device: int = 0, stream=None, hit_capacity: int = 1 << 20,
-                poisson_maxit: int = 200, warm_start: int = 1, allocator=None) -> PicConfig:
+                poisson_maxit: int = 200, warm_start: int = 1, allocator=None,
+                timing: bool = False, graphs: bool = True) -> PicConfig:
     """PicConfig from a workload description (an object with the fields of
     synth.Workload)."""
     cfg = PicConfig()
@@ -194,6 +196,8 @@ def make_config(w, capacity=None, device: int = 0, stream=None, hit_capacity: in
     cfg.poisson_rtol = float(getattr(w, "poisson_rtol", 1e-6))
     cfg.warm_start = int(warm_start)
     cfg.device = int(device)
+    cfg.timing = int(bool(timing))
+    cfg.graphs = int(bool(graphs))
     cfg.hit_capacity = int(hit_capacity)
     cfg.stream = stream
     if allocator is not None:

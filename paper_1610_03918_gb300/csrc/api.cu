@@ -154,6 +154,8 @@ pic_status status_from_bits(uint32_t bits) {
 pic_status validate(const pic_config *cfg) {
   if (!cfg) return PIC_EINVAL;
   if (cfg->nx < 2 || cfg->ny < 2) return PIC_EINVAL;
+  // particle cells are packed as (i << 16) | j
+  if (cfg->nx > 32767 || cfg->ny > 65535) return PIC_EINVAL;
   if (int64_t(cfg->nx + 1) * int64_t(cfg->ny + 1) >= (int64_t(1) << 30)) return PIC_EINVAL;
   // red-black colouring of a periodic direction needs an even node count
   if (cfg->periodic_x && (cfg->nx % 2)) return PIC_EINVAL;
@@ -190,6 +192,85 @@ pic_status prepare(pic_ctx *c) {
   }
   c->fields_dirty = 0;
   return PIC_OK;
+}
+
+// One step from the host: sort (when due), particle kernel, rho, solve, field,
+// with the phase events of PIC_DIAG_TIMING.
+pic_status step_kernels(pic_ctx *c, bool sorting) {
+  pic_status st;
+  cudaEventRecord(c->tev[0], c->stream);
+  if (sorting) {
+    if ((st = check(launch_sort(c))) != PIC_OK) return st;
+    c->launches += 4;
+  }
+  cudaEventRecord(c->tev[1], c->stream);
+  if ((st = check(launch_particles(c, 0, 1.f, nullptr))) != PIC_OK) return st;
+  cudaEventRecord(c->tev[2], c->stream);
+  if ((st = check(launch_rho(c, 1))) != PIC_OK) return st;
+  cudaEventRecord(c->tev[3], c->stream);
+  st = poisson_solve(c, c->cfg.warm_start == 0);
+  if (st != PIC_OK) return st;
+  cudaEventRecord(c->tev[4], c->stream);
+  if ((st = check(launch_field(c))) != PIC_OK) return st;
+  cudaEventRecord(c->tev[5], c->stream);
+  c->launches += 3;
+  return PIC_OK;
+}
+
+// Capture (once) the step graph: [sort] -> particle kernel -> rho -> the
+// Poisson solve as nested conditional nodes -> field, with external event
+// nodes between the phases.  Kernel arguments are fixed device pointers; the
+// particle buffers are reached through the device-side buffer table.
+cudaError_t step_graph(pic_ctx *c, int with_sort) {
+  if (c->gexec[with_sort]) return cudaSuccess;
+  const int cur_save[2] = {c->cur[0], c->cur[1]};
+  const int64_t launches_save = c->launches;
+  cudaGraph_t g;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> deps;
+  auto rec = [&](int k) { return cudaEventRecordWithFlags(c->tev[k], c->stream, cudaEventRecordExternal); };
+  e = cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    rec(0);
+    if (with_sort) launch_sort(c);
+    rec(1);
+    launch_particles(c, 0, 1.f, nullptr);
+    rec(2);
+    launch_rho(c, 1);
+    rec(3);
+    cudaStreamCaptureStatus cs;
+    unsigned long long id;
+    cudaGraph_t gg;
+    const cudaGraphNode_t *d = nullptr;
+    const cudaGraphEdgeData *ed = nullptr;
+    size_t nd = 0;
+    e = cudaStreamGetCaptureInfo(c->stream, &cs, &id, &gg, &d, &ed, &nd);
+    if (e == cudaSuccess) deps.assign(d, d + nd);
+    cudaGraph_t out;
+    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &out);
+    if (e == cudaSuccess) e = e2;
+  }
+  if (e == cudaSuccess) e = poisson_capture(c, g, deps);
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCaptureToGraph(c->stream, g, deps.data(), nullptr, deps.size(),
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      rec(4);
+      launch_field(c);
+      rec(5);
+      cudaGraph_t out;
+      e = cudaStreamEndCapture(c->stream, &out);
+    }
+  }
+  c->cur[0] = cur_save[0];
+  c->cur[1] = cur_save[1];
+  c->launches = launches_save;
+  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[with_sort], g, 0);
+  if (e == cudaSuccess) c->graph[with_sort] = g;
+  else cudaGraphDestroy(g);
+  cudaGetLastError();
+  return e;
 }
 
 }  // namespace
@@ -284,6 +365,8 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
     }
     c->cur[s] = 0;
   }
+  c->d_pbufs = (ParticleBuf *)A(4 * sizeof(ParticleBuf));
+  c->d_cur = (int32_t *)A(2 * sizeof(int32_t));
   c->d_tile_count = (uint32_t *)A(2 * size_t(ntiles) * 4);
   c->d_tile_cursor = (uint32_t *)A(2 * size_t(ntiles) * 4);
   c->d_tile_start = (uint32_t *)A(2 * size_t(ntiles) * 4);
@@ -334,11 +417,20 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
   cudaMemsetAsync(c->d_status, 0, 4, c->stream);
   for (int s = 0; s < 2; ++s)
     for (int b = 0; b < 2; ++b) cudaMemsetAsync(c->pb[s][b].cell, 0xff, c->cap[s] * 4, c->stream);
+  {
+    ParticleBuf tab[4] = {c->pb[0][0], c->pb[0][1], c->pb[1][0], c->pb[1][1]};
+    int32_t cur0[2] = {0, 0};
+    cudaMemcpy(c->d_pbufs, tab, sizeof(tab), cudaMemcpyHostToDevice);
+    cudaMemcpy(c->d_cur, cur0, sizeof(cur0), cudaMemcpyHostToDevice);
+  }
   for (int k = 0; k < 6; ++k) cudaEventCreate(&c->tev[k]);
   e = poisson_setup(c);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
     pic_free(c);
+    // an invalid value here means the coarsest multigrid level does not fit
+    // in one CTA's shared memory (a grid that cannot be coarsened enough)
+    if (e == cudaErrorInvalidValue) return PIC_EINVAL;
     return e == cudaErrorMemoryAllocation ? PIC_ENOMEM : PIC_ECUDA;
   }
   c->fields_dirty = 1;
@@ -393,36 +485,43 @@ pic_status pic_step(pic_ctx *c, int32_t nsteps) {
   if (st != PIC_OK) return st;
   for (int32_t k = 0; k < nsteps; ++k) {
     const bool sorting = c->steps_since_sort >= c->cfg.sort_every;
-    cudaEventRecord(c->tev[0], c->stream);
+    if (c->cfg.graphs) {
+      if ((st = check(step_graph(c, sorting ? 1 : 0))) != PIC_OK) return st;
+      if (cudaGraphLaunch(c->gexec[sorting ? 1 : 0], c->stream) != cudaSuccess) return PIC_ECUDA;
+      if (sorting) {
+        c->cur[0] ^= 1;   // mirror the device-side buffer flip of the sort
+        c->cur[1] ^= 1;
+      }
+    } else {
+      if ((st = step_kernels(c, sorting)) != PIC_OK) return st;
+    }
     if (sorting) {
-      if ((st = check(launch_sort(c))) != PIC_OK) return st;
       c->steps_since_sort = 0;
-      c->launches += 4;
       c->t_sorts += 1;
     }
-    cudaEventRecord(c->tev[1], c->stream);
-    if ((st = check(launch_particles(c, 0, 1.f, nullptr))) != PIC_OK) return st;
-    cudaEventRecord(c->tev[2], c->stream);
-    if ((st = check(launch_rho(c, 1))) != PIC_OK) return st;
-    cudaEventRecord(c->tev[3], c->stream);
-    st = poisson_solve(c, c->cfg.warm_start == 0);
-    if (st != PIC_OK) return st;
-    cudaEventRecord(c->tev[4], c->stream);
-    if ((st = check(launch_field(c))) != PIC_OK) return st;
-    cudaEventRecord(c->tev[5], c->stream);
-    c->launches += 3;
-    // the Poisson solve synchronised the stream, so the first events are done
-    float ms[3] = {0.f, 0.f, 0.f};
-    cudaEventElapsedTime(&ms[0], c->tev[0], c->tev[1]);
-    cudaEventElapsedTime(&ms[1], c->tev[1], c->tev[2]);
-    cudaEventElapsedTime(&ms[2], c->tev[2], c->tev[3]);
-    c->t_sort += ms[0];
-    c->t_part += ms[1];
-    c->t_other += ms[2];
-    c->t_poisson += c->last_ms;
-    c->t_steps += 1;
     c->steps_since_sort += 1;
     c->step += 1;
+    c->t_steps += 1;
+    if (c->cfg.timing || !c->cfg.graphs) {
+      if (cudaEventSynchronize(c->tev[5]) != cudaSuccess) return PIC_ECUDA;
+      float ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+      for (int q = 0; q < 5; ++q) cudaEventElapsedTime(&ms[q], c->tev[q], c->tev[q + 1]);
+      c->t_sort += ms[0];
+      c->t_part += ms[1];
+      c->t_other += ms[2] + ms[4];
+      if (c->cfg.graphs) {
+        c->t_poisson += ms[3];
+        c->last_ms = ms[3];
+        PoissonState ps;
+        if (cudaMemcpy(&ps, c->d_ps, sizeof(ps), cudaMemcpyDeviceToHost) != cudaSuccess)
+          return PIC_ECUDA;
+        c->last_outer = ps.outer_iters;
+        c->launches += (sorting ? 4 : 0) + 3 + poisson_kernel_count(c, ps);
+        if (!ps.outer_done) return PIC_ENOCONV;
+      } else {
+        c->t_poisson += c->last_ms;
+      }
+    }
   }
   return PIC_OK;
 }
@@ -580,10 +679,6 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
     }
     case PIC_DIAG_TIMING: {
       if (!need(8 * 8)) return PIC_EINVAL;
-      float fms = 0.f;
-      // the field kernel of the last step ran after the last event pair read
-      if (c->t_steps > 0 && cudaEventElapsedTime(&fms, c->tev[4], c->tev[5]) == cudaSuccess)
-        c->t_other += fms;
       int64_t slots[2] = {0, 0};
       cudaMemcpy(slots, c->d_nslots, 16, cudaMemcpyDeviceToHost);
       double *o = (double *)out;
@@ -626,6 +721,10 @@ pic_status pic_free(pic_ctx *c) {
   c->allocs.clear();
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_ps) cudaFreeHost(c->h_ps);
+  for (int k = 0; k < 2; ++k) {
+    if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
+    if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+  }
   for (int k = 0; k < 6; ++k)
     if (c->tev[k]) cudaEventDestroy(c->tev[k]);
   if (c->ev0) cudaEventDestroy(c->ev0);

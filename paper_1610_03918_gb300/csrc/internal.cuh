@@ -21,7 +21,7 @@ constexpr uint32_t kQ = 1u << kFracBits;
 constexpr int kTileX = 16;
 constexpr int kTileY = 16;
 constexpr int kHalo = 4;
-constexpr int kChunk = 2048;     // particles per work item (multiple of 4, <= 4095)
+constexpr int kChunk = 4092;     // particles per work item (multiple of 4, <= 4095)
 constexpr int kParticleThreads = 256;
 constexpr int kWalkLimit = 16;   // face crossings followed per move
 
@@ -61,13 +61,14 @@ struct PoissonState {
   double tol_in;      // inner target relative to the inner initial residual
   int32_t inner_done, outer_done;
   int32_t inner_iters, total_iters;
-  int32_t outer_iters, pad;
+  int32_t outer_iters, go;   // go: the last residual check asked for another inner solve
 };
 
 struct MGLevel {
   int nx, ny, nxn, nyn;
   float h2;            // squared mesh spacing (4^level)
   uint8_t *free;       // 1 = unknown, 0 = Dirichlet (zero correction)
+  float *st;           // Galerkin 9-point stencil [node][3x3] (levels >= 1)
   float *u, *f;        // correction and right-hand side
 };
 
@@ -108,7 +109,7 @@ struct pic_ctx {
   int nlev, lc;                // levels, first level solved by the single-CTA kernel
   std::vector<picgb::MGLevel> lev;
   float *d_r32, *d_z, *d_p0, *d_p1, *d_q, *d_e;
-  double *d_r64;
+  size_t coarse_smem;          // dynamic shared memory of the single-CTA coarse V-cycle
   picgb::PoissonState *d_ps;
   picgb::PoissonState *h_ps;   // pinned mirror
   picgb::Reducer red;
@@ -119,7 +120,9 @@ struct pic_ctx {
 
   // particles
   picgb::ParticleBuf pb[2][2];
-  int cur[2];
+  int cur[2];                  // host mirror of d_cur
+  picgb::ParticleBuf *d_pbufs; // [species][2] on the device
+  int32_t *d_cur;              // current buffer per species (device)
   int64_t cap[2];              // slots allocated per buffer
   int needs_sort;
   int pending_kick[2];
@@ -148,6 +151,9 @@ struct pic_ctx {
   int64_t stage_n;
   int fields_dirty;
   int64_t step;
+  // captured step graphs: [0] without, [1] with the tile sort
+  cudaGraph_t graph[2];
+  cudaGraphExec_t gexec[2];
   // per-phase timing (PIC_DIAG_TIMING)
   cudaEvent_t tev[6];
   double t_part, t_sort, t_poisson, t_other;
@@ -176,6 +182,8 @@ cudaError_t launch_moments(pic_ctx *c, int s, double *d_part, int nblocks);
 cudaError_t poisson_setup(pic_ctx *c);
 cudaError_t launch_rho(pic_ctx *c, int advance_step);
 pic_status poisson_solve(pic_ctx *c, bool zero_guess);
+cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNode_t> &deps);
+int64_t poisson_kernel_count(pic_ctx *c, const PoissonState &ps);
 cudaError_t launch_field(pic_ctx *c);
 
 }  // namespace picgb

@@ -2,7 +2,7 @@
 // push / absorption / cloud-in-cell deposit kernel, and state conversion.
 //
 // Particles are stored per species as structure-of-arrays: int32 cell
-// index (i * ny + j, -1 = dead or padding), FP32 offsets fx, fy in [0, 1)
+// index packed as (i << 16) | j (-1 = dead or padding), FP32 offsets fx, fy in [0, 1)
 // inside the cell, FP32 velocities vx, vy (at half steps), uint32 id.
 // Every sort_every steps they are counting-sorted by 16x16-cell tile; each
 // tile's segment is padded to a multiple of 4 slots so that one thread moves
@@ -19,17 +19,20 @@ __device__ __forceinline__ int wrapmod(int a, int n) {
   return a < 0 ? a + n : a;
 }
 
+__device__ __forceinline__ int cell_i(int c) { return c >> 16; }
+__device__ __forceinline__ int cell_j(int c) { return c & 0xffff; }
+__device__ __forceinline__ int pack_cell(int i, int j) { return (i << 16) | j; }
+
 __device__ __forceinline__ int tile_of(const Geom &g, int c) {
-  const int i = c / g.ny;
-  const int j = c - i * g.ny;
-  return (i / kTileX) * g.nty + j / kTileY;
+  return (cell_i(c) / kTileX) * g.nty + cell_j(c) / kTileY;
 }
 
 // ---------------------------------------------------------------------------
 // Counting sort by tile
 // ---------------------------------------------------------------------------
 struct SortArgs {
-  ParticleBuf src[2], dst[2];
+  const ParticleBuf *pbufs;  // [species][2] on the device
+  int32_t *cur;              // current buffer per species (device)
   const int64_t *nslots;   // slots in use in src, per species
   uint32_t *count, *cursor, *start;   // [2][ntiles]
   Chunk *chunks;
@@ -50,7 +53,7 @@ __global__ void k_sort_hist(SortArgs a) {
     const int64_t p = base + lane;
     int t = -1;
     if (p < n) {
-      const int c = a.src[s].cell[p];
+      const int c = a.pbufs[2 * s + a.cur[s]].cell[p];
       if (c >= 0) t = tile_of(a.g, c);
     }
     const unsigned peers = __match_any_sync(0xffffffffu, t);
@@ -110,7 +113,8 @@ __global__ void __launch_bounds__(1024) k_sort_scan(SortArgs a) {
         st[t] = off;
         cur[t] = 0;
         cnt[t] = 0;
-        for (uint32_t k = n; k < padded; ++k) a.dst[s].cell[off + k] = -1;
+        int32_t *dcell = a.pbufs[2 * s + (a.cur[s] ^ 1)].cell;
+        for (uint32_t k = n; k < padded; ++k) dcell[off + k] = -1;
         for (uint32_t k = 0; k < nch; ++k) {
           Chunk ch;
           ch.species = s;
@@ -128,9 +132,11 @@ __global__ void __launch_bounds__(1024) k_sort_scan(SortArgs a) {
   if (threadIdx.x == 0) *a.nchunks = int32_t(chunk_base);
 }
 
-__global__ void k_sort_finish(int64_t *nslots) {
+__global__ void k_sort_finish(int64_t *nslots, int32_t *cur) {
   nslots[0] = nslots[2];
   nslots[1] = nslots[3];
+  cur[0] ^= 1;
+  cur[1] ^= 1;
 }
 
 __global__ void k_sort_scatter(SortArgs a) {
@@ -141,7 +147,7 @@ __global__ void k_sort_scatter(SortArgs a) {
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   uint32_t *cur = a.cursor + int64_t(s) * a.ntiles;
   const uint32_t *st = a.start + int64_t(s) * a.ntiles;
-  const ParticleBuf S = a.src[s], D = a.dst[s];
+  const ParticleBuf S = a.pbufs[2 * s + a.cur[s]], D = a.pbufs[2 * s + (a.cur[s] ^ 1)];
   for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
     const int64_t p = base + lane;
     int t = -1, c = -1;
@@ -171,7 +177,8 @@ __global__ void k_sort_scatter(SortArgs a) {
 // Fused particle kernel
 // ---------------------------------------------------------------------------
 struct PArgs {
-  ParticleBuf pb[2];
+  const ParticleBuf *pbufs;  // [species][2] on the device
+  const int32_t *cur;        // current buffer per species (device)
   const Chunk *chunks;
   const int32_t *nchunks;
   const float2 *E;
@@ -196,13 +203,6 @@ constexpr int WYc = kTileY + 2 * kHalo;
 constexpr int NWX = WXc + 1;              // window nodes
 constexpr int NWY = WYc + 1;
 
-// Local window cell coordinate of global cell index i (window origin w0,
-// period n when periodic); returns a value >= W when outside the window.
-__device__ __forceinline__ int local_coord(int i, int w0, int n, int periodic) {
-  int l = i - w0;
-  if (periodic) l = wrapmod(l, n);
-  return l;
-}
 
 __device__ __forceinline__ void deposit_global(const PArgs &a, unsigned long long *acc, int i,
                                                int j, int w00, int w01, int w10, int w11) {
@@ -226,152 +226,156 @@ __device__ __forceinline__ void cic_weights(float fx, float fy, int &w00, int &w
   w11 = int(kQ) - w00 - w10 - w01;
 }
 
+// Window-local coordinate of cell index i (window origin w0, period n when
+// periodic).  The value is outside [0, W) when the cell is outside the window.
+__device__ __forceinline__ int local_coord(int i, int w0, int n, int periodic) {
+  int l = i - w0;
+  if (periodic) l = l < 0 ? l + n : (l >= n ? l - n : l);
+  return l;
+}
+
+__device__ __forceinline__ void deposit_shared(uint32_t *sAcc, int li, int lj, int w00, int w01,
+                                               int w10, int w11) {
+  const int k = li * NWY + lj;
+  atomicAdd(&sAcc[k], (uint32_t)w00);
+  atomicAdd(&sAcc[k + 1], (uint32_t)w01);
+  atomicAdd(&sAcc[k + NWY], (uint32_t)w10);
+  atomicAdd(&sAcc[k + NWY + 1], (uint32_t)w11);
+}
+
 template <int MODE>
 __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint32_t *sAcc,
                                          unsigned long long *acc, int s, int wi0, int wj0,
-                                         int64_t slot, int &c, float &fx, float &fy, float &vx,
-                                         float &vy, float &ke) {
+                                         const uint32_t *id, int64_t slot, int &c, float &fx,
+                                         float &fy, float &vx, float &vy, float &ke) {
   if (c < 0) return;
   const Geom &g = a.g;
-  const int i = c / g.ny;
-  const int j = c - i * g.ny;
-  if (MODE != 1) {
-    const int li = local_coord(i, wi0, g.nx, g.px);
-    const int lj = local_coord(j, wj0, g.ny, g.py);
-    float2 e00, e01, e10, e11;
-    if ((unsigned)li < (unsigned)WXc && (unsigned)lj < (unsigned)WYc) {
-      const int k = li * NWY + lj;
-      e00 = sE[k];
-      e01 = sE[k + 1];
-      e10 = sE[k + NWY];
-      e11 = sE[k + NWY + 1];
-    } else {
-      int i1 = i + 1, j1 = j + 1;
-      if (g.px && i1 == g.nxn) i1 = 0;
-      if (g.py && j1 == g.nyn) j1 = 0;
-      e00 = __ldg(&a.E[i * g.nyn + j]);
-      e01 = __ldg(&a.E[i * g.nyn + j1]);
-      e10 = __ldg(&a.E[i1 * g.nyn + j]);
-      e11 = __ldg(&a.E[i1 * g.nyn + j1]);
-    }
-    const float gx = 1.0f - fx, gy = 1.0f - fy;
-    const float ex = gx * (gy * e00.x + fy * e01.x) + fx * (gy * e10.x + fy * e11.x);
-    const float ey = gx * (gy * e00.y + fy * e01.y) + fx * (gy * e10.y + fy * e11.y);
-    if (MODE == 2) {
-      if (a.kick[s]) {
-        vx += a.qdt[s] * ex;
-        vy += a.qdt[s] * ey;
-      }
-      return;
-    }
-    const float vx1 = vx + a.qdt[s] * ex;
-    const float vy1 = vy + a.qdt[s] * ey;
-    ke += vx * vx1 + vy * vy1;
-    vx = vx1;
-    vy = vy1;
-    const float dx = vx1 * a.dt, dy = vy1 * a.dt;
-    float nfx = fx + dx, nfy = fy + dy;
-    const float cxf = floorf(nfx), cyf = floorf(nfy);
-    const int cx = int(cxf), cy = int(cyf);
-    int ni = i, nj = j;
-    if (cx | cy) {
-      // Walk the crossed faces in order of the segment parameter (x first on a tie).
-      const int si = cx > 0 ? 1 : -1, sj = cy > 0 ? 1 : -1;
-      const float adx = fabsf(dx), ady = fabsf(dy);
-      int oi = 0, oj = 0, k = 0;
-      bool dead = false;
-      int wall = -1, wcell = -1;
-      for (; k < kWalkLimit; ++k) {
-        const bool needx = oi != cx, needy = oj != cy;
-        if (!needx && !needy) break;
-        const float facex = float(si > 0 ? oi + 1 : oi);
-        const float facey = float(sj > 0 ? oj + 1 : oj);
-        const bool xfirst = fabsf(facex - fx) * ady <= fabsf(facey - fy) * adx;
-        const bool takex = needx && (!needy || xfirst);
-        if (takex) oi += si; else oj += sj;
-        int gi = i + oi, gj = j + oj;
-        bool outx = false, outy = false;
-        if (g.px) gi = wrapmod(gi, g.nx); else outx = gi < 0 || gi >= g.nx;
-        if (g.py) gj = wrapmod(gj, g.ny); else outy = gj < 0 || gj >= g.ny;
-        if (outx || outy || !__ldg(&a.cellmask[gi * g.ny + gj])) {
-          dead = true;
-          if (takex) {
-            wall = si > 0 ? (outx ? PIC_WALL_XMAX : PIC_WALL_COND_PX)
-                          : (outx ? PIC_WALL_XMIN : PIC_WALL_COND_MX);
-            wcell = gj;
-          } else {
-            wall = sj > 0 ? (outy ? PIC_WALL_YMAX : PIC_WALL_COND_PY)
-                          : (outy ? PIC_WALL_YMIN : PIC_WALL_COND_MY);
-            wcell = gi;
-          }
-          break;
-        }
-        ni = gi;
-        nj = gj;
-      }
-      if (!dead && (oi != cx || oj != cy)) {
-        // moved farther than the walk limit: flag and drop without a tally
-        atomicOr(a.status, PIC_ST_CFL);
-        c = -1;
-        return;
-      }
-      if (dead) {
-        c = -1;
-        atomicAdd(&a.walls[s * PIC_NWALLS + wall], 1ull);
-        if (wall == PIC_WALL_XMAX) atomicAdd(&a.bottom[s * g.ny + wcell], 1ull);
-        const unsigned long long h = atomicAdd(a.nhits, 1ull);
-        if ((long long)h < a.hit_cap) {
-          pic_hit rec;
-          rec.id = a.pb[s].id[slot];
-          rec.species = int16_t(s);
-          rec.wall = int16_t(wall);
-          rec.cell = wcell;
-          rec.step = *a.step;
-          rec.vx = vx1;
-          rec.vy = vy1;
-          a.hits[h] = rec;
-        } else {
-          atomicOr(a.status, PIC_ST_FULL);
-        }
-        return;
-      }
-      nfx -= cxf;
-      nfy -= cyf;
-      nfx = fminf(nfx, 0x1.fffffep-1f);
-      nfy = fminf(nfy, 0x1.fffffep-1f);
-    }
-    fx = nfx;
-    fy = nfy;
-    c = ni * g.ny + nj;
-    // fall through to the deposit at the new position
-    int w00, w01, w10, w11;
-    cic_weights(fx, fy, w00, w01, w10, w11);
-    const int lni = local_coord(ni, wi0, g.nx, g.px);
-    const int lnj = local_coord(nj, wj0, g.ny, g.py);
-    if ((unsigned)lni < (unsigned)WXc && (unsigned)lnj < (unsigned)WYc) {
-      const int kk = lni * NWY + lnj;
-      atomicAdd(&sAcc[kk], (uint32_t)w00);
-      atomicAdd(&sAcc[kk + 1], (uint32_t)w01);
-      atomicAdd(&sAcc[kk + NWY], (uint32_t)w10);
-      atomicAdd(&sAcc[kk + NWY + 1], (uint32_t)w11);
-    } else {
-      deposit_global(a, acc, ni, nj, w00, w01, w10, w11);
-    }
-  } else {
+  const int i = cell_i(c);
+  const int j = cell_j(c);
+  const int li = local_coord(i, wi0, g.nx, g.px);
+  const int lj = local_coord(j, wj0, g.ny, g.py);
+  const bool inw = (unsigned)li < (unsigned)WXc && (unsigned)lj < (unsigned)WYc;
+  if (MODE == 1) {
     // deposit only, at the current position
     int w00, w01, w10, w11;
     cic_weights(fx, fy, w00, w01, w10, w11);
-    const int li = local_coord(i, wi0, g.nx, g.px);
-    const int lj = local_coord(j, wj0, g.ny, g.py);
-    if ((unsigned)li < (unsigned)WXc && (unsigned)lj < (unsigned)WYc) {
-      const int kk = li * NWY + lj;
-      atomicAdd(&sAcc[kk], (uint32_t)w00);
-      atomicAdd(&sAcc[kk + 1], (uint32_t)w01);
-      atomicAdd(&sAcc[kk + NWY], (uint32_t)w10);
-      atomicAdd(&sAcc[kk + NWY + 1], (uint32_t)w11);
-    } else {
-      deposit_global(a, acc, i, j, w00, w01, w10, w11);
+    if (inw) deposit_shared(sAcc, li, lj, w00, w01, w10, w11);
+    else deposit_global(a, acc, i, j, w00, w01, w10, w11);
+    return;
+  }
+  float2 e00, e01, e10, e11;
+  if (inw) {
+    const int k = li * NWY + lj;
+    e00 = sE[k];
+    e01 = sE[k + 1];
+    e10 = sE[k + NWY];
+    e11 = sE[k + NWY + 1];
+  } else {
+    int i1 = i + 1, j1 = j + 1;
+    if (g.px && i1 == g.nxn) i1 = 0;
+    if (g.py && j1 == g.nyn) j1 = 0;
+    e00 = __ldg(&a.E[i * g.nyn + j]);
+    e01 = __ldg(&a.E[i * g.nyn + j1]);
+    e10 = __ldg(&a.E[i1 * g.nyn + j]);
+    e11 = __ldg(&a.E[i1 * g.nyn + j1]);
+  }
+  const float gx = 1.0f - fx, gy = 1.0f - fy;
+  const float ex = gx * (gy * e00.x + fy * e01.x) + fx * (gy * e10.x + fy * e11.x);
+  const float ey = gx * (gy * e00.y + fy * e01.y) + fx * (gy * e10.y + fy * e11.y);
+  if (MODE == 2) {
+    if (a.kick[s]) {
+      vx += a.qdt[s] * ex;
+      vy += a.qdt[s] * ey;
     }
+    return;
+  }
+  const float vx1 = vx + a.qdt[s] * ex;
+  const float vy1 = vy + a.qdt[s] * ey;
+  ke += vx * vx1 + vy * vy1;
+  vx = vx1;
+  vy = vy1;
+  const float dx = vx1 * a.dt, dy = vy1 * a.dt;
+  float nfx = fx + dx, nfy = fy + dy;
+  const float cxf = floorf(nfx), cyf = floorf(nfy);
+  const int cx = int(cxf), cy = int(cyf);
+  int oi = 0, oj = 0;     // cell offset of the move
+  if (cx | cy) {
+    // Walk the crossed faces in order of the segment parameter (x first on a tie).
+    const int si = cx > 0 ? 1 : -1, sj = cy > 0 ? 1 : -1;
+    const float adx = fabsf(dx), ady = fabsf(dy);
+    bool dead = false;
+    int wall = -1, wcell = -1;
+    for (int k = 0; k < kWalkLimit; ++k) {
+      const bool needx = oi != cx, needy = oj != cy;
+      if (!needx && !needy) break;
+      const float facex = float(si > 0 ? oi + 1 : oi);
+      const float facey = float(sj > 0 ? oj + 1 : oj);
+      const bool xfirst = fabsf(facex - fx) * ady <= fabsf(facey - fy) * adx;
+      const bool takex = needx && (!needy || xfirst);
+      if (takex) oi += si; else oj += sj;
+      int gi = i + oi, gj = j + oj;
+      bool outx = false, outy = false;
+      if (g.px) gi = wrapmod(gi, g.nx); else outx = gi < 0 || gi >= g.nx;
+      if (g.py) gj = wrapmod(gj, g.ny); else outy = gj < 0 || gj >= g.ny;
+      if (outx || outy || !__ldg(&a.cellmask[gi * g.ny + gj])) {
+        dead = true;
+        if (takex) {
+          wall = si > 0 ? (outx ? PIC_WALL_XMAX : PIC_WALL_COND_PX)
+                        : (outx ? PIC_WALL_XMIN : PIC_WALL_COND_MX);
+          wcell = gj;
+        } else {
+          wall = sj > 0 ? (outy ? PIC_WALL_YMAX : PIC_WALL_COND_PY)
+                        : (outy ? PIC_WALL_YMIN : PIC_WALL_COND_MY);
+          wcell = gi;
+        }
+        break;
+      }
+    }
+    if (!dead && (oi != cx || oj != cy)) {
+      // moved farther than the walk limit: flag and drop without a tally
+      atomicOr(a.status, PIC_ST_CFL);
+      c = -1;
+      return;
+    }
+    if (dead) {
+      c = -1;
+      atomicAdd(&a.walls[s * PIC_NWALLS + wall], 1ull);
+      if (wall == PIC_WALL_XMAX) atomicAdd(&a.bottom[s * g.ny + wcell], 1ull);
+      const unsigned long long h = atomicAdd(a.nhits, 1ull);
+      if ((long long)h < a.hit_cap) {
+        pic_hit rec;
+        rec.id = id[slot];
+        rec.species = int16_t(s);
+        rec.wall = int16_t(wall);
+        rec.cell = wcell;
+        rec.step = *a.step;
+        rec.vx = vx1;
+        rec.vy = vy1;
+        a.hits[h] = rec;
+      } else {
+        atomicOr(a.status, PIC_ST_FULL);
+      }
+      return;
+    }
+    nfx -= cxf;
+    nfy -= cyf;
+    nfx = fminf(nfx, 0x1.fffffep-1f);
+    nfy = fminf(nfy, 0x1.fffffep-1f);
+    int ni = i + oi, nj = j + oj;
+    if (g.px) ni = wrapmod(ni, g.nx);
+    if (g.py) nj = wrapmod(nj, g.ny);
+    c = pack_cell(ni, nj);
+  }
+  fx = nfx;
+  fy = nfy;
+  // deposit at the new position; window coordinates follow the move unwrapped
+  int w00, w01, w10, w11;
+  cic_weights(fx, fy, w00, w01, w10, w11);
+  const int lni = li + oi, lnj = lj + oj;
+  if ((unsigned)lni < (unsigned)WXc && (unsigned)lnj < (unsigned)WYc) {
+    deposit_shared(sAcc, lni, lnj, w00, w01, w10, w11);
+  } else {
+    deposit_global(a, acc, cell_i(c), cell_j(c), w00, w01, w10, w11);
   }
 }
 
@@ -405,7 +409,7 @@ __global__ void __launch_bounds__(kParticleThreads) k_particles(PArgs a) {
     }
     __syncthreads();
     unsigned long long *acc = a.acc + (int64_t)s * nnodes;
-    const ParticleBuf P = a.pb[s];
+    const ParticleBuf P = a.pbufs[2 * s + a.cur[s]];
     float ke = 0.f;
     for (int64_t base = ch.begin + 4 * threadIdx.x; base < ch.end; base += 4 * blockDim.x) {
       int4 c4 = *reinterpret_cast<const int4 *>(P.cell + base);
@@ -416,10 +420,10 @@ __global__ void __launch_bounds__(kParticleThreads) k_particles(PArgs a) {
         vx4 = *reinterpret_cast<const float4 *>(P.vx + base);
         vy4 = *reinterpret_cast<const float4 *>(P.vy + base);
       }
-      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, base + 0, c4.x, fx4.x, fy4.x, vx4.x, vy4.x, ke);
-      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, base + 1, c4.y, fx4.y, fy4.y, vx4.y, vy4.y, ke);
-      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, base + 2, c4.z, fx4.z, fy4.z, vx4.z, vy4.z, ke);
-      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, base + 3, c4.w, fx4.w, fy4.w, vx4.w, vy4.w, ke);
+      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 0, c4.x, fx4.x, fy4.x, vx4.x, vy4.x, ke);
+      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 1, c4.y, fx4.y, fy4.y, vx4.y, vy4.y, ke);
+      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 2, c4.z, fx4.z, fy4.z, vx4.z, vy4.z, ke);
+      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 3, c4.w, fx4.w, fy4.w, vx4.w, vy4.w, ke);
       if (MODE == 0) {
         *reinterpret_cast<int4 *>(P.cell + base) = c4;
         *reinterpret_cast<float4 *>(P.fx + base) = fx4;
@@ -485,7 +489,7 @@ __global__ void k_load_convert(ParticleBuf P, Geom g, const uint8_t *cellmask, c
   if (X == X && Y == Y && fi >= 0 && fi < g.nx && fj >= 0 && fj < g.ny) {
     const int i = int(fi), j = int(fj);
     if (cellmask[i * g.ny + j]) {
-      c = i * g.ny + j;
+      c = (i << 16) | j;
       fx = fminf(float(X - fi), 0x1.fffffep-1f);
       fy = fminf(float(Y - fj), 0x1.fffffep-1f);
     }
@@ -516,7 +520,7 @@ __global__ void k_export(ParticleBuf P, Geom g, const int64_t *nslots_p, double 
     if (c >= 0) {
       const int64_t d = int64_t(b) + __popc(live & ((1u << lane) - 1u));
       if (d < cap) {
-        const int i = c / g.ny, j = c - (c / g.ny) * g.ny;
+        const int i = cell_i(c), j = cell_j(c);
         out[d] = double(i) + double(P.fx[p]);
         out[cap + d] = double(j) + double(P.fy[p]);
         out[2 * cap + d] = double(P.vx[p]);
@@ -576,10 +580,8 @@ int particle_grid(pic_ctx *c) {
 
 cudaError_t launch_sort(pic_ctx *c) {
   SortArgs a;
-  for (int s = 0; s < 2; ++s) {
-    a.src[s] = c->pb[s][c->cur[s]];
-    a.dst[s] = c->pb[s][c->cur[s] ^ 1];
-  }
+  a.pbufs = c->d_pbufs;
+  a.cur = c->d_cur;
   a.nslots = c->d_nslots;
   a.count = c->d_tile_count;
   a.cursor = c->d_tile_cursor;
@@ -593,15 +595,16 @@ cudaError_t launch_sort(pic_ctx *c) {
   k_sort_hist<<<grid, 256, 0, c->stream>>>(a);
   k_sort_scan<<<1, 1024, 0, c->stream>>>(a);
   k_sort_scatter<<<grid, 256, 0, c->stream>>>(a);
-  k_sort_finish<<<1, 1, 0, c->stream>>>(c->d_nslots);
+  k_sort_finish<<<1, 1, 0, c->stream>>>(c->d_nslots, c->d_cur);
   for (int s = 0; s < 2; ++s) c->cur[s] ^= 1;
   return cudaGetLastError();
 }
 
 cudaError_t launch_particles(pic_ctx *c, int mode, float kick_factor, const int *species_mask) {
   PArgs a;
+  a.pbufs = c->d_pbufs;
+  a.cur = c->d_cur;
   for (int s = 0; s < 2; ++s) {
-    a.pb[s] = c->pb[s][c->cur[s]];
     a.qdt[s] = float(c->cfg.alpha[s] * c->cfg.dt * kick_factor);
     a.kick[s] = species_mask ? species_mask[s] : 1;
   }

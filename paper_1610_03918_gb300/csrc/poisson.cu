@@ -9,15 +9,18 @@
 //
 //   repeat:  r = b - A phi          (FP64 stencil, FP64 norm: the certificate)
 //            stop if ||r|| <= rtol ||b||
-//            solve A e = r by PCG   (FP32 vectors and stencils, FP64 dots,
-//                                    symmetric geometric V-cycle preconditioner)
+//            solve A e = r by PCG   (FP32 vectors and stencils, dot products
+//                                    accumulated across threads in FP64,
+//                                    symmetric V-cycle preconditioner)
 //            phi += e                (FP64)
 //
-// The V-cycle coarsens by 2 with injected Dirichlet masks, rediscretised
-// operators (A / h^2), full-weighting restriction, bilinear prolongation
-// (restriction = prolongation^T / 4) and red-black Gauss-Seidel smoothing
-// (red then black before, black then red after), so the preconditioner is
-// symmetric.  Levels with at most kSmallLevel nodes run inside one CTA.
+// V-cycle: factor-2 coarsening with injected Dirichlet masks; Galerkin coarse
+// operators A_c = R A P (9-point, built once on the host) with bilinear
+// prolongation P and full-weighting restriction R = P^T / 4; red-black
+// Gauss-Seidel on the 5-point fine level and four-colour Gauss-Seidel on the
+// 9-point coarse levels, colours swept in reverse after the coarse
+// correction, so the preconditioner is symmetric.  Levels with at most
+// kSmallLevel nodes run inside one CTA with their vectors in shared memory.
 // A doubly periodic box has no Dirichlet node: b loses its mean and the
 // preconditioned residual is projected to zero mean.
 #include <cuda_runtime.h>
@@ -34,7 +37,7 @@ constexpr int kThreads = 256;
 constexpr int kSmallLevel = 16384;
 constexpr int kCoarseThreads = 1024;
 constexpr int kMaxOuter = 8;
-constexpr int kCoarsestSweeps = 24;
+constexpr int kCoarsestSweeps = 16;
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
@@ -115,7 +118,6 @@ struct FineArgs {
   double sw[2];              // q_s w_s (surface charge per hit)
   int surface;
   float *r32, *z, *p_old, *p_new, *q, *e;
-  double *r64;
   PoissonState *ps;
   double *part;
   unsigned int *ticket;
@@ -126,15 +128,20 @@ struct FineArgs {
   int advance_step;
   float2 *E;
   double *fe;
+  uint32_t *status;
+  int graph;                 // kernels run inside the step graph: drive its conditionals
+  cudaGraphConditionalHandle h_outer, h_if_outer, h_inner, h_if_inner;
 };
+
+#define GRID_STRIDE(n, N) \
+  for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (N); n += gridDim.x * blockDim.x)
 
 // acc -> rho, b; clears acc.  For a doubly periodic box the mean of b is kept.
 __global__ void k_rho(FineArgs a) {
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   double v[2] = {0.0, 0.0};
-  if (n < nn) {
+  GRID_STRIDE(n, nn) {
     const unsigned long long a0 = a.acc[n], a1 = a.acc[nn + n];
     a.acc[n] = 0ull;
     a.acc[nn + n] = 0ull;
@@ -156,8 +163,8 @@ __global__ void k_rho(FineArgs a) {
     const bool fr = a.flags[n] & kFree;
     const double bb = fr ? rho + a.lift[n] : 0.0;
     a.b[n] = bb;
-    v[0] = bb;
-    v[1] = fr ? 1.0 : 0.0;
+    v[0] += bb;
+    v[1] += fr ? 1.0 : 0.0;
   }
   if (grid_sum<2>(v, a.part, a.ticket) && threadIdx.x == 0) {
     a.ps->bmean = a.singular ? v[0] / v[1] : 0.0;
@@ -167,9 +174,7 @@ __global__ void k_rho(FineArgs a) {
 
 // phi <- Dirichlet values, zero on free nodes (cold start)
 __global__ void k_phi_reset(FineArgs a) {
-  const int nn = a.g.nxn * a.g.nyn;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < nn) a.phi[n] = a.gval[n];
+  GRID_STRIDE(n, a.g.nxn * a.g.nyn) a.phi[n] = a.gval[n];
 }
 
 __device__ __forceinline__ void nbr_index(const Geom &g, int n, int &xm, int &xp, int &ym, int &yp) {
@@ -189,20 +194,20 @@ __device__ __forceinline__ void nbr_index(const Geom &g, int n, int &xm, int &xp
 __global__ void k_resid64(FineArgs a) {
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
+  const double bmean = a.ps->bmean;
   double v[2] = {0.0, 0.0};
-  if (n < nn) {
+  GRID_STRIDE(n, nn) {
     float r32 = 0.f;
     if (a.flags[n] & kFree) {
       int xm, xp, ym, yp;
       nbr_index(g, n, xm, xp, ym, yp);
-      const double rho = a.b[n] - a.lift[n] - a.ps->bmean;
+      const double bn = a.b[n] - bmean;
+      const double rho = bn - a.lift[n];
       const double Aphi = 4.0 * a.phi[n] - a.phi[xm] - a.phi[xp] - a.phi[ym] - a.phi[yp];
       const double r = rho - Aphi;
       r32 = float(r);
-      const double bb = a.b[n] - a.ps->bmean;
-      v[0] = r * r;
-      v[1] = bb * bb;
+      v[0] += r * r;
+      v[1] += bn * bn;
     }
     a.r32[n] = r32;
     a.e[n] = 0.f;
@@ -214,13 +219,22 @@ __global__ void k_resid64(FineArgs a) {
     ps->bb = v[1];
     ps->rel = v[1] > 0 ? sqrt(v[0] / v[1]) : sqrt(v[0]);
     const bool ok = ps->rel <= a.rtol || v[0] == 0.0;
+    const bool give_up = !ok && ps->outer_iters >= kMaxOuter;
+    if (give_up) atomicOr(a.status, PIC_ST_NOCONV);
+    const bool go = !ok && !give_up;
     ps->outer_done = ok ? 1 : 0;
-    ps->inner_done = ok ? 1 : 0;
+    ps->go = go ? 1 : 0;
+    ps->inner_done = go ? 0 : 1;
+    if (a.graph) {
+      cudaGraphSetConditional(a.h_outer, go ? 1u : 0u);
+      cudaGraphSetConditional(a.h_if_outer, go ? 1u : 0u);
+      cudaGraphSetConditional(a.h_inner, go ? 1u : 0u);
+    }
     ps->inner_iters = 0;
     ps->rr0 = v[0];
     ps->rr = v[0];
     // inner target: bring ||r|| to half the outer target, no tighter than FP32 allows
-    double t = 0.5 * a.rtol * sqrt(v[1]) / fmax(sqrt(v[0]), 1e-300);
+    const double t = 0.5 * a.rtol * sqrt(v[1]) / fmax(sqrt(v[0]), 1e-300);
     ps->tol_in = fmin(fmax(t, 3e-6), 0.5);
     ps->beta = 0.0;
     ps->rz = 0.0;
@@ -231,14 +245,14 @@ __global__ void k_resid64(FineArgs a) {
 __global__ void k_rz(FineArgs a) {
   if (a.ps->inner_done) return;
   const int nn = a.g.nxn * a.g.nyn;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  double v[3] = {0.0, 0.0, 0.0};
-  if (n < nn) {
-    const double r = a.r32[n], z = a.z[n];
-    v[0] = r * z;
-    v[1] = z;
-    v[2] = r;
+  float rz = 0.f, zs = 0.f, rs = 0.f;
+  GRID_STRIDE(n, nn) {
+    const float r = a.r32[n], z = a.z[n];
+    rz = fmaf(r, z, rz);
+    zs += z;
+    rs += r;
   }
+  double v[3] = {rz, zs, rs};
   if (grid_sum<3>(v, a.part, a.ticket) && threadIdx.x == 0) {
     PoissonState *ps = a.ps;
     const double zm = a.singular ? v[1] / double(nn) : 0.0;
@@ -254,11 +268,10 @@ __global__ void k_pq(FineArgs a) {
   if (ps->inner_done) return;
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const float beta = ps->inner_iters == 0 ? 0.f : float(ps->rz / ps->rz_old);
   const float zm = float(ps->zmean);
-  double v[1] = {0.0};
-  if (n < nn) {
+  float pq = 0.f;
+  GRID_STRIDE(n, nn) {
     float pn = 0.f, qn = 0.f;
     if (a.flags[n] & kFree) {
       int xm, xp, ym, yp;
@@ -268,11 +281,12 @@ __global__ void k_pq(FineArgs a) {
       };
       pn = P(n);
       qn = 4.f * pn - P(xm) - P(xp) - P(ym) - P(yp);
-      v[0] = double(pn) * double(qn);
+      pq = fmaf(pn, qn, pq);
     }
     a.p_new[n] = pn;
     a.q[n] = qn;
   }
+  double v[1] = {pq};
   if (grid_sum<1>(v, a.part, a.ticket) && threadIdx.x == 0) a.ps->pq = v[0];
 }
 
@@ -281,42 +295,50 @@ __global__ void k_update(FineArgs a) {
   PoissonState *ps = a.ps;
   if (ps->inner_done) return;
   const int nn = a.g.nxn * a.g.nyn;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   const float alpha = float(ps->rz / ps->pq);
-  double v[1] = {0.0};
-  if (n < nn) {
+  float rr = 0.f;
+  GRID_STRIDE(n, nn) {
     const float p = a.p_new[n];
     a.e[n] += alpha * p;
     const float r = a.r32[n] - alpha * a.q[n];
     a.r32[n] = r;
     a.p_old[n] = p;
-    v[0] = double(r) * double(r);
+    rr = fmaf(r, r, rr);
   }
+  double v[1] = {rr};
   if (grid_sum<1>(v, a.part, a.ticket) && threadIdx.x == 0) {
     ps->rr = v[0];
     ps->inner_iters += 1;
     ps->total_iters += 1;
     const double tol = ps->tol_in;
-    if (sqrt(v[0]) <= tol * sqrt(ps->rr0) || ps->inner_iters >= a.maxit || !(v[0] == v[0]))
-      ps->inner_done = 1;
+    const bool done =
+        sqrt(v[0]) <= tol * sqrt(ps->rr0) || ps->inner_iters >= a.maxit || !(v[0] == v[0]);
+    if (done) ps->inner_done = 1;
+    if (a.graph) {
+      cudaGraphSetConditional(a.h_inner, done ? 0u : 1u);
+      cudaGraphSetConditional(a.h_if_inner, done ? 0u : 1u);
+    }
   }
 }
 
-__global__ void k_set_status(uint32_t *st, uint32_t bit) { atomicOr(st, bit); }
-
 __global__ void k_correct(FineArgs a) {
-  const int nn = a.g.nxn * a.g.nyn;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < nn && (a.flags[n] & kFree)) a.phi[n] += double(a.e[n]);
+  if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->outer_iters += 1;
+  GRID_STRIDE(n, a.g.nxn * a.g.nyn) {
+    if (a.flags[n] & kFree) a.phi[n] += double(a.e[n]);
+  }
+}
+
+__global__ void k_outer_init(PoissonState *ps) {
+  ps->total_iters = 0;
+  ps->outer_iters = 0;
 }
 
 // E = -grad phi by the open-edge rule; field energy 1/2 sum |E|^2
 __global__ void k_field(FineArgs a) {
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
   double v[1] = {0.0};
-  if (n < nn) {
+  GRID_STRIDE(n, nn) {
     const uint8_t f = a.flags[n];
     const int i = n / g.nyn, j = n - (n / g.nyn) * g.nyn;
     const double p = a.phi[n];
@@ -326,10 +348,10 @@ __global__ void k_field(FineArgs a) {
     if (f & kOpenXp) { sx += a.phi[(g.px ? wrapi(i + 1, g.nxn) : i + 1) * g.nyn + j] - p; ++cx; }
     if (f & kOpenYm) { sy += p - a.phi[i * g.nyn + (g.py ? wrapi(j - 1, g.nyn) : j - 1)]; ++cy; }
     if (f & kOpenYp) { sy += a.phi[i * g.nyn + (g.py ? wrapi(j + 1, g.nyn) : j + 1)] - p; ++cy; }
-    const double ex = cx ? -sx / cx : 0.0;
-    const double ey = cy ? -sy / cy : 0.0;
-    a.E[n] = make_float2(float(ex), float(ey));
-    v[0] = ex * ex + ey * ey;
+    const float ex = float(cx == 2 ? -0.5 * sx : (cx ? -sx : 0.0));
+    const float ey = float(cy == 2 ? -0.5 * sy : (cy ? -sy : 0.0));
+    a.E[n] = make_float2(ex, ey);
+    v[0] += double(fmaf(ex, ex, ey * ey));
   }
   if (grid_sum<1>(v, a.part, a.ticket) && threadIdx.x == 0) a.fe[0] = 0.5 * v[0];
 }
@@ -338,59 +360,85 @@ __global__ void k_field(FineArgs a) {
 // Multigrid V-cycle
 // --------------------------------------------------------------------------
 struct LevelDev {
-  int nx, ny, nxn, nyn, px, py;
-  float h2;
+  int nxn, nyn, px, py;
   const uint8_t *free;
+  const float *st;     // 9-point Galerkin stencil [node][3x3], levels >= 1
   float *u, *f;
 };
 
 struct MGArgs {
   LevelDev L[16];
-  int nlev;
+  int nlev, lc;
   const PoissonState *ps;
 };
 
-// red-black Gauss-Seidel half sweep over one colour; zero_init: u starts at 0
-__device__ __forceinline__ void smooth_node(const LevelDev &L, int n, int color, bool zero_init) {
-  const int i = n / L.nyn, j = n - (n / L.nyn) * L.nyn;
-  const bool mine = ((i + j) & 1) == color;
-  if (!L.free[n]) {
-    if (zero_init) L.u[n] = 0.f;
-    return;
-  }
-  if (zero_init) {
-    L.u[n] = mine ? 0.25f * L.h2 * L.f[n] : 0.f;
-    return;
-  }
-  if (!mine) return;
-  const int im = L.px ? wrapi(i - 1, L.nxn) : i - 1;
-  const int ip = L.px ? wrapi(i + 1, L.nxn) : i + 1;
-  const int jm = L.py ? wrapi(j - 1, L.nyn) : j - 1;
-  const int jp = L.py ? wrapi(j + 1, L.nyn) : j + 1;
-  const float s = L.h2 * L.f[n] + L.u[im * L.nyn + j] + L.u[ip * L.nyn + j] +
-                  L.u[i * L.nyn + jm] + L.u[i * L.nyn + jp];
-  L.u[n] = 0.25f * s;
+__device__ __forceinline__ int nb_idx(const LevelDev &L, int i, int j, int di, int dj) {
+  const int a = L.px ? wrapi(i + di, L.nxn) : i + di;
+  const int b = L.py ? wrapi(j + dj, L.nyn) : j + dj;
+  return a * L.nyn + b;
 }
 
+// Off-diagonal part of (A u)(i, j) and the diagonal on level l: the 5-point
+// unit Laplacian on the fine level, the stored Galerkin stencil on coarser
+// ones.  Only called on free nodes, which are interior in a bounded direction.
+template <bool FINE>
+__device__ __forceinline__ float apply_off(const LevelDev &L, int i, int j, int n, float &diag) {
+  if (FINE) {
+    diag = 4.f;
+    return -(L.u[nb_idx(L, i, j, -1, 0)] + L.u[nb_idx(L, i, j, 1, 0)] +
+             L.u[nb_idx(L, i, j, 0, -1)] + L.u[nb_idx(L, i, j, 0, 1)]);
+  } else {
+    const float *s = L.st + 9 * n;
+    diag = __ldg(s + 4);
+    float acc = 0.f;
+#pragma unroll
+    for (int di = -1; di <= 1; ++di)
+#pragma unroll
+      for (int dj = -1; dj <= 1; ++dj) {
+        if (di == 0 && dj == 0) continue;
+        acc = fmaf(__ldg(s + (di + 1) * 3 + (dj + 1)), L.u[nb_idx(L, i, j, di, dj)], acc);
+      }
+    return acc;
+  }
+}
+
+// Gauss-Seidel update of one node of the current colour
+template <bool FINE>
+__device__ __forceinline__ void gs_node(const LevelDev &L, int i, int j) {
+  const int n = i * L.nyn + j;
+  if (!L.free[n]) return;
+  float d;
+  const float off = apply_off<FINE>(L, i, j, n, d);
+  L.u[n] = (L.f[n] - off) / d;
+}
+
+// First half sweep from u = 0: the first colour gets f / diag, the rest 0.
+template <bool FINE>
+__device__ __forceinline__ void gs_zero_node(const LevelDev &L, int i, int j) {
+  const int n = i * L.nyn + j;
+  const bool first = FINE ? (((i + j) & 1) == 0) : (((i | j) & 1) == 0);
+  float v = 0.f;
+  if (first && L.free[n]) v = L.f[n] / (FINE ? 4.f : __ldg(L.st + 9 * n + 4));
+  L.u[n] = v;
+}
+
+template <bool FINE>
 __device__ __forceinline__ float resid_node(const LevelDev &L, int i, int j) {
   const int n = i * L.nyn + j;
   if (!L.free[n]) return 0.f;
-  const int im = L.px ? wrapi(i - 1, L.nxn) : i - 1;
-  const int ip = L.px ? wrapi(i + 1, L.nxn) : i + 1;
-  const int jm = L.py ? wrapi(j - 1, L.nyn) : j - 1;
-  const int jp = L.py ? wrapi(j + 1, L.nyn) : j + 1;
-  const float Au = 4.f * L.u[n] - L.u[im * L.nyn + j] - L.u[ip * L.nyn + j] -
-                   L.u[i * L.nyn + jm] - L.u[i * L.nyn + jp];
-  return L.f[n] - Au / L.h2;
+  float d;
+  const float off = apply_off<FINE>(L, i, j, n, d);
+  return L.f[n] - (d * L.u[n] + off);
 }
 
-// full weighting of the fine residual onto coarse node nc
-__device__ __forceinline__ void restrict_node(const LevelDev &F, const LevelDev &C, int nc) {
+// full weighting of the fine residual onto coarse node (I, J)
+template <bool FINE>
+__device__ __forceinline__ void restrict_node(const LevelDev &F, const LevelDev &C, int I, int J) {
+  const int nc = I * C.nyn + J;
   if (!C.free[nc]) {
     C.f[nc] = 0.f;
     return;
   }
-  const int I = nc / C.nyn, J = nc - (nc / C.nyn) * C.nyn;
   float s = 0.f;
 #pragma unroll
   for (int a = -1; a <= 1; ++a) {
@@ -399,95 +447,166 @@ __device__ __forceinline__ void restrict_node(const LevelDev &F, const LevelDev 
       const int i = F.px ? wrapi(2 * I + a, F.nxn) : 2 * I + a;
       const int j = F.py ? wrapi(2 * J + b, F.nyn) : 2 * J + b;
       const float w = (a == 0 ? 2.f : 1.f) * (b == 0 ? 2.f : 1.f);
-      s += w * resid_node(F, i, j);
+      s = fmaf(w, resid_node<FINE>(F, i, j), s);
     }
   }
   C.f[nc] = s * (1.f / 16.f);
 }
 
 // bilinear prolongation of the coarse correction, added on free fine nodes
-__device__ __forceinline__ void prolong_node(const LevelDev &F, const LevelDev &C, int n) {
+__device__ __forceinline__ void prolong_node(const LevelDev &F, const LevelDev &C, int i, int j) {
+  const int n = i * F.nyn + j;
   if (!F.free[n]) return;
-  const int i = n / F.nyn, j = n - (n / F.nyn) * F.nyn;
   const int I0 = i >> 1, J0 = j >> 1;
   const int I1 = (i & 1) ? (C.px ? wrapi(I0 + 1, C.nxn) : I0 + 1) : I0;
   const int J1 = (j & 1) ? (C.py ? wrapi(J0 + 1, C.nyn) : J0 + 1) : J0;
-  float v;
-  if (!(i & 1) && !(j & 1)) {
-    v = C.u[I0 * C.nyn + J0];
-  } else if (!(j & 1)) {
-    v = 0.5f * (C.u[I0 * C.nyn + J0] + C.u[I1 * C.nyn + J0]);
-  } else if (!(i & 1)) {
-    v = 0.5f * (C.u[I0 * C.nyn + J0] + C.u[I0 * C.nyn + J1]);
-  } else {
-    v = 0.25f * (C.u[I0 * C.nyn + J0] + C.u[I1 * C.nyn + J0] + C.u[I0 * C.nyn + J1] +
-                 C.u[I1 * C.nyn + J1]);
-  }
+  const float v = 0.25f * (C.u[I0 * C.nyn + J0] + C.u[I1 * C.nyn + J0] + C.u[I0 * C.nyn + J1] +
+                           C.u[I1 * C.nyn + J1]);
   F.u[n] += v;
 }
 
-__global__ void k_smooth(MGArgs a, int l, int color, int zero_init) {
+// colour c of a level: fine level red/black (c in {0,1}, (i+j)&1 == c);
+// coarse levels four colours (c in {0..3}, (i&1, j&1) == (c>>1, c&1)).
+template <bool FINE>
+__device__ __forceinline__ int colour_count(const LevelDev &L) {
+  return FINE ? L.nxn * ((L.nyn + 1) >> 1) : ((L.nxn + 1) >> 1) * ((L.nyn + 1) >> 1);
+}
+
+template <bool FINE>
+__device__ __forceinline__ bool colour_node(const LevelDev &L, int c, int t, int &i, int &j) {
+  const int hy = (L.nyn + 1) >> 1;
+  if (FINE) {
+    i = t / hy;
+    j = 2 * (t - i * hy) + ((i + c) & 1);
+  } else {
+    const int ti = t / hy;
+    i = 2 * ti + (c >> 1);
+    j = 2 * (t - ti * hy) + (c & 1);
+  }
+  return i < L.nxn && j < L.nyn;
+}
+
+template <bool FINE>
+__global__ void k_gs(MGArgs a, int l, int c) {
+  if (a.ps->inner_done) return;
+  const LevelDev &L = a.L[l];
+  const int t = blockIdx.x * blockDim.x + threadIdx.x;
+  int i, j;
+  if (t < colour_count<FINE>(L) && colour_node<FINE>(L, c, t, i, j)) gs_node<FINE>(L, i, j);
+}
+
+template <bool FINE>
+__global__ void k_gs_zero(MGArgs a, int l) {
   if (a.ps->inner_done) return;
   const LevelDev &L = a.L[l];
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < L.nxn * L.nyn) smooth_node(L, n, color, zero_init != 0);
+  if (n < L.nxn * L.nyn) gs_zero_node<FINE>(L, n / L.nyn, n - (n / L.nyn) * L.nyn);
 }
 
+template <bool FINE>
 __global__ void k_restrict(MGArgs a, int l) {
   if (a.ps->inner_done) return;
   const LevelDev &C = a.L[l + 1];
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < C.nxn * C.nyn) restrict_node(a.L[l], C, n);
+  if (n < C.nxn * C.nyn) restrict_node<FINE>(a.L[l], C, n / C.nyn, n - (n / C.nyn) * C.nyn);
 }
 
 __global__ void k_prolong(MGArgs a, int l) {
   if (a.ps->inner_done) return;
   const LevelDev &F = a.L[l];
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < F.nxn * F.nyn) prolong_node(F, a.L[l + 1], n);
+  if (n < F.nxn * F.nyn) prolong_node(F, a.L[l + 1], n / F.nyn, n - (n / F.nyn) * F.nyn);
 }
 
-// The V-cycle from level l0 to the coarsest, inside one CTA.
-__global__ void __launch_bounds__(kCoarseThreads) k_coarse(MGArgs a, int l0) {
+// ---- the levels from lc down, inside one CTA, vectors in shared memory ----
+template <bool FINE>
+__device__ void cta_sweep(const LevelDev &L, int c) {
+  const int cnt = colour_count<FINE>(L);
+  for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
+    int i, j;
+    if (colour_node<FINE>(L, c, t, i, j)) gs_node<FINE>(L, i, j);
+  }
+  __syncthreads();
+}
+
+template <bool FINE>
+__device__ void cta_zero(const LevelDev &L) {
+  const int nn = L.nxn * L.nyn;
+  for (int n = threadIdx.x; n < nn; n += blockDim.x) gs_zero_node<FINE>(L, n / L.nyn, n % L.nyn);
+  __syncthreads();
+}
+
+// pre (forward) or post (reverse) smoothing: one sweep over all colours
+template <bool FINE>
+__device__ void cta_smooth(const LevelDev &L, bool forward, bool zero_start) {
+  const int nc = FINE ? 2 : 4;
+  if (forward) {
+    if (zero_start) cta_zero<FINE>(L);
+    for (int c = zero_start ? 1 : 0; c < nc; ++c) cta_sweep<FINE>(L, c);
+  } else {
+    for (int c = nc - 1; c >= 0; --c) cta_sweep<FINE>(L, c);
+  }
+}
+
+template <bool FINE>
+__device__ void cta_restrict(const LevelDev &F, const LevelDev &C) {
+  const int nn = C.nxn * C.nyn;
+  for (int n = threadIdx.x; n < nn; n += blockDim.x) restrict_node<FINE>(F, C, n / C.nyn, n % C.nyn);
+  __syncthreads();
+}
+
+__device__ void cta_prolong(const LevelDev &F, const LevelDev &C) {
+  const int nn = F.nxn * F.nyn;
+  for (int n = threadIdx.x; n < nn; n += blockDim.x) prolong_node(F, C, n / F.nyn, n % F.nyn);
+  __syncthreads();
+}
+
+__global__ void __launch_bounds__(kCoarseThreads) k_coarse(MGArgs a) {
   if (a.ps->inner_done) return;
-  const int last = a.nlev - 1;
-  for (int l = l0; l <= last; ++l) {
-    const LevelDev &L = a.L[l];
-    const int nn = L.nxn * L.nyn;
-    const int sweeps = (l == last) ? kCoarsestSweeps : 1;
-    for (int k = threadIdx.x; k < nn; k += blockDim.x) smooth_node(L, k, 0, true);
+  extern __shared__ float smem[];
+  const int lc = a.lc, last = a.nlev - 1;
+  // level copies whose vectors live in shared memory
+  LevelDev S[16];
+  float *p = smem;
+  for (int l = lc; l <= last; ++l) {
+    S[l] = a.L[l];
+    const int nn = S[l].nxn * S[l].nyn;
+    S[l].u = p;
+    p += nn;
+    S[l].f = p;
+    p += nn;
+  }
+  {
+    const int nn = S[lc].nxn * S[lc].nyn;
+    for (int n = threadIdx.x; n < nn; n += blockDim.x) S[lc].f[n] = a.L[lc].f[n];
     __syncthreads();
-    for (int s = 0; s < sweeps; ++s) {
-      if (s > 0) {
-        for (int k = threadIdx.x; k < nn; k += blockDim.x) smooth_node(L, k, 0, false);
-        __syncthreads();
-      }
-      for (int k = threadIdx.x; k < nn; k += blockDim.x) smooth_node(L, k, 1, false);
-      __syncthreads();
-    }
-    if (l == last) {
-      for (int s = 0; s < sweeps; ++s) {
-        for (int k = threadIdx.x; k < nn; k += blockDim.x) smooth_node(L, k, 1, false);
-        __syncthreads();
-        for (int k = threadIdx.x; k < nn; k += blockDim.x) smooth_node(L, k, 0, false);
-        __syncthreads();
-      }
+  }
+  for (int l = lc; l < last; ++l) {
+    if (l == 0) {
+      cta_smooth<true>(S[l], true, true);
+      cta_restrict<true>(S[l], S[l + 1]);
     } else {
-      const LevelDev &C = a.L[l + 1];
-      for (int k = threadIdx.x; k < C.nxn * C.nyn; k += blockDim.x) restrict_node(L, C, k);
-      __syncthreads();
+      cta_smooth<false>(S[l], true, true);
+      cta_restrict<false>(S[l], S[l + 1]);
     }
   }
-  for (int l = last - 1; l >= l0; --l) {
-    const LevelDev &L = a.L[l];
-    const int nn = L.nxn * L.nyn;
-    for (int k = threadIdx.x; k < nn; k += blockDim.x) prolong_node(L, a.L[l + 1], k);
-    __syncthreads();
-    for (int k = threadIdx.x; k < nn; k += blockDim.x) smooth_node(L, k, 1, false);
-    __syncthreads();
-    for (int k = threadIdx.x; k < nn; k += blockDim.x) smooth_node(L, k, 0, false);
-    __syncthreads();
+  // coarsest level: symmetric sweeps from zero
+  if (last == 0) {
+    cta_smooth<true>(S[last], true, true);
+    for (int s = 1; s < kCoarsestSweeps; ++s) cta_smooth<true>(S[last], true, false);
+    for (int s = 0; s < kCoarsestSweeps; ++s) cta_smooth<true>(S[last], false, false);
+  } else {
+    cta_smooth<false>(S[last], true, true);
+    for (int s = 1; s < kCoarsestSweeps; ++s) cta_smooth<false>(S[last], true, false);
+    for (int s = 0; s < kCoarsestSweeps; ++s) cta_smooth<false>(S[last], false, false);
   }
+  for (int l = last - 1; l >= lc; --l) {
+    cta_prolong(S[l], S[l + 1]);
+    if (l == 0) cta_smooth<true>(S[l], false, false);
+    else cta_smooth<false>(S[l], false, false);
+  }
+  const int nn = S[lc].nxn * S[lc].nyn;
+  for (int n = threadIdx.x; n < nn; n += blockDim.x) a.L[lc].u[n] = S[lc].u[n];
 }
 
 // --------------------------------------------------------------------------
@@ -515,7 +634,6 @@ FineArgs fine_args(pic_ctx *c) {
   a.p_new = c->d_p1;
   a.q = c->d_q;
   a.e = c->d_e;
-  a.r64 = c->d_r64;
   a.ps = c->d_ps;
   a.part = c->red.part;
   a.ticket = c->red.ticket;
@@ -526,22 +644,24 @@ FineArgs fine_args(pic_ctx *c) {
   a.advance_step = 0;
   a.E = c->d_E;
   a.fe = c->d_fe;
+  a.status = c->d_status;
+  a.graph = 0;
+  a.h_outer = a.h_if_outer = a.h_inner = a.h_if_inner = 0;
   return a;
 }
 
 MGArgs mg_args(pic_ctx *c) {
   MGArgs a;
   a.nlev = c->nlev;
+  a.lc = c->lc;
   for (int l = 0; l < c->nlev; ++l) {
     const MGLevel &m = c->lev[l];
-    a.L[l].nx = m.nx;
-    a.L[l].ny = m.ny;
     a.L[l].nxn = m.nxn;
     a.L[l].nyn = m.nyn;
     a.L[l].px = c->g.px;
     a.L[l].py = c->g.py;
-    a.L[l].h2 = m.h2;
     a.L[l].free = m.free;
+    a.L[l].st = m.st;
     a.L[l].u = m.u;
     a.L[l].f = m.f;
   }
@@ -549,23 +669,101 @@ MGArgs mg_args(pic_ctx *c) {
   return a;
 }
 
-inline int blocks_for(int n) { return (n + kThreads - 1) / kThreads; }
+inline int blocks_for(int n) { return std::max(1, (n + kThreads - 1) / kThreads); }
 
 void launch_vcycle(pic_ctx *c, const MGArgs &a) {
-  c->launches += 6 * c->lc + 1;
   for (int l = 0; l < c->lc; ++l) {
-    const int nb = blocks_for(c->lev[l].nxn * c->lev[l].nyn);
-    k_smooth<<<nb, kThreads, 0, c->stream>>>(a, l, 0, 1);
-    k_smooth<<<nb, kThreads, 0, c->stream>>>(a, l, 1, 0);
+    const MGLevel &L = c->lev[l];
+    const int nn = L.nxn * L.nyn;
     const int nbc = blocks_for(c->lev[l + 1].nxn * c->lev[l + 1].nyn);
-    k_restrict<<<nbc, kThreads, 0, c->stream>>>(a, l);
+    if (l == 0) {
+      const int nh = blocks_for(L.nxn * ((L.nyn + 1) / 2));
+      k_gs_zero<true><<<blocks_for(nn), kThreads, 0, c->stream>>>(a, l);
+      k_gs<true><<<nh, kThreads, 0, c->stream>>>(a, l, 1);
+      k_restrict<true><<<nbc, kThreads, 0, c->stream>>>(a, l);
+      c->launches += 3;
+    } else {
+      const int nq = blocks_for(((L.nxn + 1) / 2) * ((L.nyn + 1) / 2));
+      k_gs_zero<false><<<blocks_for(nn), kThreads, 0, c->stream>>>(a, l);
+      for (int col = 1; col < 4; ++col) k_gs<false><<<nq, kThreads, 0, c->stream>>>(a, l, col);
+      k_restrict<false><<<nbc, kThreads, 0, c->stream>>>(a, l);
+      c->launches += 5;
+    }
   }
-  k_coarse<<<1, kCoarseThreads, 0, c->stream>>>(a, c->lc);
+  k_coarse<<<1, kCoarseThreads, c->coarse_smem, c->stream>>>(a);
+  c->launches += 1;
   for (int l = c->lc - 1; l >= 0; --l) {
-    const int nb = blocks_for(c->lev[l].nxn * c->lev[l].nyn);
-    k_prolong<<<nb, kThreads, 0, c->stream>>>(a, l);
-    k_smooth<<<nb, kThreads, 0, c->stream>>>(a, l, 1, 0);
-    k_smooth<<<nb, kThreads, 0, c->stream>>>(a, l, 0, 0);
+    const MGLevel &L = c->lev[l];
+    const int nn = L.nxn * L.nyn;
+    k_prolong<<<blocks_for(nn), kThreads, 0, c->stream>>>(a, l);
+    if (l == 0) {
+      const int nh = blocks_for(L.nxn * ((L.nyn + 1) / 2));
+      k_gs<true><<<nh, kThreads, 0, c->stream>>>(a, l, 1);
+      k_gs<true><<<nh, kThreads, 0, c->stream>>>(a, l, 0);
+      c->launches += 3;
+    } else {
+      const int nq = blocks_for(((L.nxn + 1) / 2) * ((L.nyn + 1) / 2));
+      for (int col = 3; col >= 0; --col) k_gs<false><<<nq, kThreads, 0, c->stream>>>(a, l, col);
+      c->launches += 5;
+    }
+  }
+}
+
+// ---- host: Galerkin coarse operator A_c = R A_f P, R = P^T / 4 ----
+// Fine stencils are 3x3 arrays per node (the 5-point unit Laplacian on
+// level 0).  P is bilinear interpolation restricted to free nodes.
+void galerkin(const Geom &g, int fnxn, int fnyn, const std::vector<uint8_t> &ffree,
+              const std::vector<double> &fst, int cnxn, int cnyn, std::vector<uint8_t> &cfree,
+              std::vector<double> &cst) {
+  const bool px = g.px, py = g.py;
+  auto wrapx = [&](int a, int n) { return px ? ((a % n) + n) % n : a; };
+  auto wrapy = [&](int a, int n) { return py ? ((a % n) + n) % n : a; };
+  auto half_floor = [](int a) { return a >= 0 ? a / 2 : -((-a + 1) / 2); };
+  cst.assign(size_t(cnxn) * cnyn * 9, 0.0);
+  for (int I = 0; I < cnxn; ++I) {
+    for (int J = 0; J < cnyn; ++J) {
+      const size_t C = size_t(I) * cnyn + J;
+      if (!cfree[C]) continue;
+      double *out = &cst[C * 9];
+      for (int a = -1; a <= 1; ++a) {
+        for (int b = -1; b <= 1; ++b) {
+          // fine node i = (2I + a, 2J + b) with P[i, C] = wa * wb
+          const int fi_u = 2 * I + a, fj_u = 2 * J + b;
+          const int fi = wrapx(fi_u, fnxn), fj = wrapy(fj_u, fnyn);
+          if (fi < 0 || fi >= fnxn || fj < 0 || fj >= fnyn) continue;
+          const size_t fidx = size_t(fi) * fnyn + fj;
+          if (!ffree[fidx]) continue;
+          const double wiC = (a == 0 ? 1.0 : 0.5) * (b == 0 ? 1.0 : 0.5) / 4.0;
+          for (int di = -1; di <= 1; ++di) {
+            for (int dj = -1; dj <= 1; ++dj) {
+              const double coef = fst[fidx * 9 + (di + 1) * 3 + (dj + 1)];
+              if (coef == 0.0) continue;
+              // fine node j = i + (di, dj), unwrapped relative to 2C
+              const int gi_u = fi_u + di, gj_u = fj_u + dj;
+              const int gi = wrapx(gi_u, fnxn), gj = wrapy(gj_u, fnyn);
+              if (gi < 0 || gi >= fnxn || gj < 0 || gj >= fnyn) continue;
+              if (!ffree[size_t(gi) * fnyn + gj]) continue;
+              // coarse nodes D with P[j, D] != 0 (unwrapped coordinates)
+              const int dI0 = half_floor(gi_u), dJ0 = half_floor(gj_u);
+              const bool oddi = (gi_u - 2 * dI0) != 0, oddj = (gj_u - 2 * dJ0) != 0;
+              for (int sI = 0; sI <= (oddi ? 1 : 0); ++sI) {
+                for (int sJ = 0; sJ <= (oddj ? 1 : 0); ++sJ) {
+                  const int DI_u = dI0 + sI, DJ_u = dJ0 + sJ;
+                  const double wjD = (oddi ? 0.5 : 1.0) * (oddj ? 0.5 : 1.0);
+                  const int DI = wrapx(DI_u, cnxn), DJ = wrapy(DJ_u, cnyn);
+                  if (DI < 0 || DI >= cnxn || DJ < 0 || DJ >= cnyn) continue;
+                  if (!cfree[size_t(DI) * cnyn + DJ]) continue;
+                  const int oI = DI_u - I, oJ = DJ_u - J;
+                  if (oI < -1 || oI > 1 || oJ < -1 || oJ > 1) continue;
+                  out[(oI + 1) * 3 + (oJ + 1)] += wiC * coef * wjD;
+                }
+              }
+            }
+          }
+        }
+      }
+      if (!(out[4] > 0.0)) cfree[C] = 0;
+    }
   }
 }
 
@@ -585,9 +783,18 @@ cudaError_t poisson_setup(pic_ctx *c) {
   L0.nyn = g.nyn;
   L0.h2 = 1.f;
   std::vector<std::vector<uint8_t>> masks;
+  std::vector<std::vector<double>> sts;
   std::vector<uint8_t> m0(size_t(g.nxn) * g.nyn);
   for (size_t n = 0; n < m0.size(); ++n) m0[n] = (c->h_nodeflags[n] & kFree) ? 1 : 0;
+  std::vector<double> s0(m0.size() * 9, 0.0);
+  for (size_t n = 0; n < m0.size(); ++n) {
+    if (!m0[n]) continue;
+    double *s = &s0[n * 9];
+    s[4] = 4.0;
+    s[1] = s[3] = s[5] = s[7] = -1.0;
+  }
   masks.push_back(m0);
+  sts.push_back(s0);
   c->lev.push_back(L0);
   while (c->lev.size() < 16) {
     const MGLevel &F = c->lev.back();
@@ -607,7 +814,10 @@ cudaError_t poisson_setup(pic_ctx *c) {
     const std::vector<uint8_t> &mf = masks.back();
     for (int I = 0; I < C.nxn; ++I)
       for (int J = 0; J < C.nyn; ++J) mc[size_t(I) * C.nyn + J] = mf[size_t(2 * I) * F.nyn + 2 * J];
+    std::vector<double> sc;
+    galerkin(g, F.nxn, F.nyn, mf, sts.back(), C.nxn, C.nyn, mc, sc);
     masks.push_back(mc);
+    sts.push_back(sc);
     c->lev.push_back(C);
   }
   c->nlev = int(c->lev.size());
@@ -617,6 +827,13 @@ cudaError_t poisson_setup(pic_ctx *c) {
       c->lc = l;
       break;
     }
+  size_t smem_floats = 0;
+  for (int l = c->lc; l < c->nlev; ++l) smem_floats += 2 * size_t(c->lev[l].nxn) * c->lev[l].nyn;
+  c->coarse_smem = smem_floats * sizeof(float);
+  if (c->coarse_smem > 220 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(c->coarse_smem));
+  if (e != cudaSuccess) return e;
   const size_t nn = size_t(g.nxn) * g.nyn;
   for (int l = 0; l < c->nlev; ++l) {
     MGLevel &m = c->lev[l];
@@ -624,13 +841,20 @@ cudaError_t poisson_setup(pic_ctx *c) {
     m.free = (uint8_t *)dev_alloc(c, n);
     if (!m.free) return cudaErrorMemoryAllocation;
     cudaMemcpy(m.free, masks[l].data(), n, cudaMemcpyHostToDevice);
+    m.st = nullptr;
     if (l == 0) {
       m.u = nullptr;
       m.f = nullptr;
     } else {
+      std::vector<float> stf(n * 9);
+      for (size_t k = 0; k < stf.size(); ++k) stf[k] = float(sts[l][k]);
+      for (size_t k = 0; k < n; ++k)
+        if (!masks[l][k]) stf[k * 9 + 4] = 1.0f;   // never used: keeps the diagonal finite
+      m.st = (float *)dev_alloc(c, n * 9 * sizeof(float));
       m.u = (float *)dev_alloc(c, n * sizeof(float));
       m.f = (float *)dev_alloc(c, n * sizeof(float));
-      if (!m.u || !m.f) return cudaErrorMemoryAllocation;
+      if (!m.u || !m.f || !m.st) return cudaErrorMemoryAllocation;
+      cudaMemcpy(m.st, stf.data(), n * 9 * sizeof(float), cudaMemcpyHostToDevice);
       cudaMemsetAsync(m.u, 0, n * sizeof(float), c->stream);
       cudaMemsetAsync(m.f, 0, n * sizeof(float), c->stream);
     }
@@ -643,15 +867,14 @@ cudaError_t poisson_setup(pic_ctx *c) {
   }
   c->lev[0].u = c->d_z;
   c->lev[0].f = c->d_r32;
-  c->d_r64 = (double *)dev_alloc(c, nn * sizeof(double));
-  c->red.nblocks = blocks_for(int(nn));
+  c->red.nblocks = std::min(blocks_for(int(nn)), 2 * c->num_sms);
   c->red.part = (double *)dev_alloc(c, size_t(c->red.nblocks) * 4 * sizeof(double));
   c->red.ticket = (unsigned int *)dev_alloc(c, 64);
   c->d_ps = (PoissonState *)dev_alloc(c, sizeof(PoissonState));
-  if (!c->d_r64 || !c->red.part || !c->red.ticket || !c->d_ps) return cudaErrorMemoryAllocation;
+  if (!c->red.part || !c->red.ticket || !c->d_ps) return cudaErrorMemoryAllocation;
   cudaMemsetAsync(c->red.ticket, 0, 64, c->stream);
   cudaMemsetAsync(c->d_ps, 0, sizeof(PoissonState), c->stream);
-  cudaError_t e = cudaMallocHost((void **)&c->h_ps, sizeof(PoissonState));
+  e = cudaMallocHost((void **)&c->h_ps, sizeof(PoissonState));
   if (e != cudaSuccess) return e;
   cudaEventCreate(&c->ev0);
   cudaEventCreate(&c->ev1);
@@ -661,40 +884,34 @@ cudaError_t poisson_setup(pic_ctx *c) {
 cudaError_t launch_rho(pic_ctx *c, int advance_step) {
   FineArgs a = fine_args(c);
   a.advance_step = advance_step;
-  const int nn = c->g.nxn * c->g.nyn;
-  k_rho<<<blocks_for(nn), kThreads, 0, c->stream>>>(a);
+  k_rho<<<c->red.nblocks, kThreads, 0, c->stream>>>(a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_field(pic_ctx *c) {
   FineArgs a = fine_args(c);
-  const int nn = c->g.nxn * c->g.nyn;
-  k_field<<<blocks_for(nn), kThreads, 0, c->stream>>>(a);
+  k_field<<<c->red.nblocks, kThreads, 0, c->stream>>>(a);
   return cudaGetLastError();
 }
 
 pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
   FineArgs a = fine_args(c);
   const MGArgs m = mg_args(c);
-  const int nn = c->g.nxn * c->g.nyn;
-  const int nb = blocks_for(nn);
+  const int nb = c->red.nblocks;
   cudaEventRecord(c->ev0, c->stream);
-  if (zero_guess) k_phi_reset<<<nb, kThreads, 0, c->stream>>>(a);
-  cudaMemsetAsync(&c->d_ps->total_iters, 0, sizeof(int32_t), c->stream);
-  int outer = 0;
+  if (zero_guess) {
+    k_phi_reset<<<nb, kThreads, 0, c->stream>>>(a);
+    c->launches += 1;
+  }
+  k_outer_init<<<1, 1, 0, c->stream>>>(c->d_ps);
+  c->launches += 1;
   const int batch = 4;
-  bool converged = false;
-  if (zero_guess) c->launches += 1;
-  for (; outer < kMaxOuter + 1; ++outer) {
+  for (;;) {
     k_resid64<<<nb, kThreads, 0, c->stream>>>(a);
     c->launches += 1;
     cudaMemcpyAsync(c->h_ps, c->d_ps, sizeof(PoissonState), cudaMemcpyDeviceToHost, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
-    if (c->h_ps->outer_done) {
-      converged = true;
-      break;
-    }
-    if (outer == kMaxOuter) break;
+    if (!c->h_ps->go) break;
     launch_vcycle(c, m);
     k_rz<<<nb, kThreads, 0, c->stream>>>(a);
     c->launches += 1;
@@ -719,13 +936,115 @@ pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   c->last_ms = ms;
-  c->last_outer = outer;
+  c->last_outer = c->h_ps->outer_iters;
   if (cudaGetLastError() != cudaSuccess) return PIC_ECUDA;
-  if (!converged) {
-    k_set_status<<<1, 1, 0, c->stream>>>(c->d_status, PIC_ST_NOCONV);
-    return PIC_ENOCONV;
+  return c->h_ps->outer_done ? PIC_OK : PIC_ENOCONV;
+}
+
+// ---- the solve as nested conditional nodes of a CUDA graph ----
+namespace {
+
+cudaError_t cap_begin(cudaStream_t s, cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps) {
+  return cudaStreamBeginCaptureToGraph(s, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                                       deps.size(), cudaStreamCaptureModeThreadLocal);
+}
+
+cudaError_t cap_end(cudaStream_t s, std::vector<cudaGraphNode_t> &leaves) {
+  cudaStreamCaptureStatus st;
+  unsigned long long id;
+  cudaGraph_t gg;
+  const cudaGraphNode_t *d = nullptr;
+  const cudaGraphEdgeData *ed = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &st, &id, &gg, &d, &ed, &nd);
+  if (e != cudaSuccess) return e;
+  leaves.assign(d, d + nd);
+  cudaGraph_t out;
+  return cudaStreamEndCapture(s, &out);
+}
+
+cudaError_t add_cond(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
+                     cudaGraphConditionalHandle h, cudaGraphConditionalNodeType type,
+                     cudaGraphNode_t *node, cudaGraph_t *body) {
+  cudaGraphNodeParams p = {};
+  p.type = cudaGraphNodeTypeConditional;
+  p.conditional.handle = h;
+  p.conditional.type = type;
+  p.conditional.size = 1;
+  cudaError_t e = cudaGraphAddNode(node, g, deps.empty() ? nullptr : deps.data(), nullptr,
+                                   deps.size(), &p);
+  if (e == cudaSuccess) *body = p.conditional.phGraph_out[0];
+  return e;
+}
+
+}  // namespace
+
+// Appends the solve to graph `top` after the nodes in `deps`; on return
+// `deps` holds the solve's last node.  Structure:
+//   [phi reset] -> init -> WHILE(outer) { resid64 -> IF(go) { V-cycle, rz ->
+//     WHILE(inner) { pq, update -> IF(!done) { V-cycle, rz } } -> correct } }
+cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNode_t> &deps) {
+  cudaStream_t s = c->stream;
+  FineArgs a = fine_args(c);
+  const MGArgs m = mg_args(c);
+  const int nb = c->red.nblocks;
+  cudaGraphConditionalHandle h[4];
+  for (int k = 0; k < 4; ++k) {
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h[k], top, k == 0 ? 1u : 0u,
+                                                     cudaGraphCondAssignDefault);
+    if (e != cudaSuccess) return e;
   }
-  return PIC_OK;
+  a.graph = 1;
+  a.h_outer = h[0];
+  a.h_if_outer = h[1];
+  a.h_inner = h[2];
+  a.h_if_inner = h[3];
+  cudaError_t e;
+#define CK(x) do { if ((e = (x)) != cudaSuccess) return e; } while (0)
+  CK(cap_begin(s, top, deps));
+  if (c->cfg.warm_start == 0) k_phi_reset<<<nb, kThreads, 0, s>>>(a);
+  k_outer_init<<<1, 1, 0, s>>>(c->d_ps);
+  CK(cap_end(s, deps));
+  cudaGraphNode_t n_outer, n_if_outer, n_inner, n_if_inner;
+  cudaGraph_t b_outer, b_if_outer, b_inner, b_if_inner;
+  CK(add_cond(top, deps, h[0], cudaGraphCondTypeWhile, &n_outer, &b_outer));
+  std::vector<cudaGraphNode_t> d;
+  CK(cap_begin(s, b_outer, {}));
+  k_resid64<<<nb, kThreads, 0, s>>>(a);
+  CK(cap_end(s, d));
+  CK(add_cond(b_outer, d, h[1], cudaGraphCondTypeIf, &n_if_outer, &b_if_outer));
+  CK(cap_begin(s, b_if_outer, {}));
+  launch_vcycle(c, m);
+  k_rz<<<nb, kThreads, 0, s>>>(a);
+  CK(cap_end(s, d));
+  CK(add_cond(b_if_outer, d, h[2], cudaGraphCondTypeWhile, &n_inner, &b_inner));
+  CK(cap_begin(s, b_inner, {}));
+  k_pq<<<nb, kThreads, 0, s>>>(a);
+  k_update<<<nb, kThreads, 0, s>>>(a);
+  CK(cap_end(s, d));
+  CK(add_cond(b_inner, d, h[3], cudaGraphCondTypeIf, &n_if_inner, &b_if_inner));
+  CK(cap_begin(s, b_if_inner, {}));
+  launch_vcycle(c, m);
+  k_rz<<<nb, kThreads, 0, s>>>(a);
+  CK(cap_end(s, d));
+  d.assign(1, n_inner);
+  CK(cap_begin(s, b_if_outer, d));
+  k_correct<<<nb, kThreads, 0, s>>>(a);
+  CK(cap_end(s, d));
+#undef CK
+  deps.assign(1, n_outer);
+  return cudaGetLastError();
+}
+
+// Kernels one solve launched, from its device counters (graph mode).
+int64_t poisson_kernel_count(pic_ctx *c, const PoissonState &ps) {
+  int64_t vc = 1;
+  for (int l = 0; l < c->lc; ++l) vc += (l == 0) ? 6 : 10;
+  const int64_t O = ps.outer_iters, I = ps.total_iters;
+  // init + resid per outer pass (+1 final) + per inner solve (V-cycle, rz, correct)
+  // + per iteration (pq, update) + per non-final iteration (V-cycle, rz)
+  return 1 + (O + 1) + O * (vc + 2) + 2 * I + std::max<int64_t>(I - O, 0) * (vc + 1) +
+         (c->cfg.warm_start == 0 ? 1 : 0);
 }
 
 }  // namespace picgb

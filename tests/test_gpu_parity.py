@@ -82,11 +82,12 @@ def test_poisson_trench_bias_vacuum():
     assert np.abs(gs.phi() - phi_o).max() <= 1e-6 * 20.0
 
 
-@pytest.mark.parametrize("name", list(SMALL))
-def test_step_by_step_parity(name):
+@pytest.mark.parametrize("name,graphs", [(n, True) for n in SMALL] + [("trench", False)])
+def test_step_by_step_parity(name, graphs):
     """Each step starts both sides from the GPU's state; the oracle recomputes
-    its own fields from it."""
-    w, gs, os_ = _loaded(SMALL[name])
+    its own fields from it.  graphs=False drives the same kernels from the
+    host loop instead of the captured step graph."""
+    w, gs, os_ = _loaded(SMALL[name], graphs=graphs)
     geom = from_workload(w)
     gs.step(0)
     os_.prepare()
