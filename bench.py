@@ -38,7 +38,12 @@ BYTES_PER_PARTICLE_STEP = 40
 # DRAM bytes per live particle of the fused particle kernel from one ncu
 # capture (dram__bytes_read.sum + dram__bytes_write.sum over the launch),
 # valid for the kernel source whose hash is recorded with it.
-NCU_TRAFFIC = {"source_sha256": None, "bytes_per_particle": None}
+NCU_TRAFFIC = {
+    # k_particles<0>, 512x1024 trench at 20 ppc (16.95M particles, 0.4 GB state,
+    # larger than L2), 4th launch: 360.4 MB read + 288.5 MB written
+    "source_sha256": "fc5d13735b88db6a593c0fbaaf6d63dbc3e453192d63129d23b0eaa69b1bef80",
+    "bytes_per_particle": 38.27,
+}
 
 
 def _peaks():
@@ -218,6 +223,9 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppc", type=int, default=None, help="override particles per cell")
+    ap.add_argument("--sort-every", type=int, default=None, help="steps between tile sorts")
+    ap.add_argument("--no-graphs", action="store_true",
+                    help="launch the step's kernels from the host loop (for kernel profilers)")
     args = ap.parse_args()
     if args.impl == "reference":
         return run_reference(args)
@@ -236,9 +244,11 @@ def main():
     w = synth.trench_512x1024(seed=3 + rank)
     if args.ppc:
         w = w.replace(ppc=args.ppc)
+    if args.sort_every:
+        w = w.replace(sort_every=args.sort_every)
     parts = [synth.maxwellian_load(w, s) for s in (0, 1)]
     n0 = sum(len(p) for p in parts)
-    sim = pg.Sim(w, capacity=len(parts[0]), device=local, timing=True)
+    sim = pg.Sim(w, capacity=len(parts[0]), device=local, timing=True, graphs=not args.no_graphs)
     for s in (0, 1):
         sim.load_particles(s, parts[s], v_at_t0=True)
     sim.step(args.warmup)

@@ -67,8 +67,10 @@ struct PoissonState {
 struct MGLevel {
   int nx, ny, nxn, nyn;
   float h2;            // squared mesh spacing (4^level)
-  uint8_t *free;       // 1 = unknown, 0 = Dirichlet (zero correction)
-  float *st;           // Galerkin 9-point stencil [node][3x3] (levels >= 1)
+  uint8_t *free;       // level 0: 1 = unknown, 0 = Dirichlet (zero correction)
+  uint16_t *sid;       // levels >= 1: 0 = not an unknown, k = stencil k-1 of stab
+  float *stab;         // levels >= 1: unique Galerkin 9-point stencils [k][3x3]
+  int nst;             // number of unique stencils
   float *u, *f;        // correction and right-hand side
 };
 
@@ -110,6 +112,9 @@ struct pic_ctx {
   std::vector<picgb::MGLevel> lev;
   float *d_r32, *d_z, *d_p0, *d_p1, *d_q, *d_e;
   size_t coarse_smem;          // dynamic shared memory of the single-CTA coarse V-cycle
+  int ncoarse;                 // unknowns of the coarsest level (dense inverse), 0 = sweeps
+  float *d_cinv;
+  int *d_cidx;
   picgb::PoissonState *d_ps;
   picgb::PoissonState *h_ps;   // pinned mirror
   picgb::Reducer red;

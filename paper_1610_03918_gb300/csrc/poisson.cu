@@ -26,7 +26,9 @@
 #include <cuda_runtime.h>
 
 #include <algorithm>
+#include <array>
 #include <cmath>
+#include <map>
 
 #include "internal.cuh"
 
@@ -38,6 +40,7 @@ constexpr int kSmallLevel = 16384;
 constexpr int kCoarseThreads = 1024;
 constexpr int kMaxOuter = 8;
 constexpr int kCoarsestSweeps = 16;
+constexpr int kDenseCoarsest = 64;   // coarsest levels up to this many unknowns use a dense inverse
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
@@ -361,14 +364,19 @@ __global__ void k_field(FineArgs a) {
 // --------------------------------------------------------------------------
 struct LevelDev {
   int nxn, nyn, px, py;
-  const uint8_t *free;
-  const float *st;     // 9-point Galerkin stencil [node][3x3], levels >= 1
+  const uint8_t *free;   // level 0: 1 = unknown
+  const uint16_t *sid;   // levels >= 1: 0 = not an unknown, k = stencil k-1 of stab
+  const float *stab;     // levels >= 1: unique Galerkin stencils [k][3x3]
   float *u, *f;
 };
 
 struct MGArgs {
   LevelDev L[16];
   int nlev, lc;
+  int nst[16];           // stencils per level
+  int ncoarse;           // unknowns of the coarsest level solved by its dense inverse (0: sweeps)
+  const float *cinv;     // [ncoarse][ncoarse]
+  const int *cidx;       // node index of each coarsest unknown
   const PoissonState *ps;
 };
 
@@ -378,8 +386,13 @@ __device__ __forceinline__ int nb_idx(const LevelDev &L, int i, int j, int di, i
   return a * L.nyn + b;
 }
 
+template <bool FINE>
+__device__ __forceinline__ bool is_free(const LevelDev &L, int n) {
+  return FINE ? L.free[n] != 0 : L.sid[n] != 0;
+}
+
 // Off-diagonal part of (A u)(i, j) and the diagonal on level l: the 5-point
-// unit Laplacian on the fine level, the stored Galerkin stencil on coarser
+// unit Laplacian on the fine level, the node's Galerkin stencil on coarser
 // ones.  Only called on free nodes, which are interior in a bounded direction.
 template <bool FINE>
 __device__ __forceinline__ float apply_off(const LevelDev &L, int i, int j, int n, float &diag) {
@@ -388,15 +401,15 @@ __device__ __forceinline__ float apply_off(const LevelDev &L, int i, int j, int 
     return -(L.u[nb_idx(L, i, j, -1, 0)] + L.u[nb_idx(L, i, j, 1, 0)] +
              L.u[nb_idx(L, i, j, 0, -1)] + L.u[nb_idx(L, i, j, 0, 1)]);
   } else {
-    const float *s = L.st + 9 * n;
-    diag = __ldg(s + 4);
+    const float *s = L.stab + 9 * (int(L.sid[n]) - 1);
+    diag = s[4];
     float acc = 0.f;
 #pragma unroll
     for (int di = -1; di <= 1; ++di)
 #pragma unroll
       for (int dj = -1; dj <= 1; ++dj) {
         if (di == 0 && dj == 0) continue;
-        acc = fmaf(__ldg(s + (di + 1) * 3 + (dj + 1)), L.u[nb_idx(L, i, j, di, dj)], acc);
+        acc = fmaf(s[(di + 1) * 3 + (dj + 1)], L.u[nb_idx(L, i, j, di, dj)], acc);
       }
     return acc;
   }
@@ -406,7 +419,7 @@ __device__ __forceinline__ float apply_off(const LevelDev &L, int i, int j, int 
 template <bool FINE>
 __device__ __forceinline__ void gs_node(const LevelDev &L, int i, int j) {
   const int n = i * L.nyn + j;
-  if (!L.free[n]) return;
+  if (!is_free<FINE>(L, n)) return;
   float d;
   const float off = apply_off<FINE>(L, i, j, n, d);
   L.u[n] = (L.f[n] - off) / d;
@@ -418,14 +431,15 @@ __device__ __forceinline__ void gs_zero_node(const LevelDev &L, int i, int j) {
   const int n = i * L.nyn + j;
   const bool first = FINE ? (((i + j) & 1) == 0) : (((i | j) & 1) == 0);
   float v = 0.f;
-  if (first && L.free[n]) v = L.f[n] / (FINE ? 4.f : __ldg(L.st + 9 * n + 4));
+  if (first && is_free<FINE>(L, n))
+    v = L.f[n] / (FINE ? 4.f : L.stab[9 * (int(L.sid[n]) - 1) + 4]);
   L.u[n] = v;
 }
 
 template <bool FINE>
 __device__ __forceinline__ float resid_node(const LevelDev &L, int i, int j) {
   const int n = i * L.nyn + j;
-  if (!L.free[n]) return 0.f;
+  if (!is_free<FINE>(L, n)) return 0.f;
   float d;
   const float off = apply_off<FINE>(L, i, j, n, d);
   return L.f[n] - (d * L.u[n] + off);
@@ -435,7 +449,7 @@ __device__ __forceinline__ float resid_node(const LevelDev &L, int i, int j) {
 template <bool FINE>
 __device__ __forceinline__ void restrict_node(const LevelDev &F, const LevelDev &C, int I, int J) {
   const int nc = I * C.nyn + J;
-  if (!C.free[nc]) {
+  if (!is_free<false>(C, nc)) {
     C.f[nc] = 0.f;
     return;
   }
@@ -454,9 +468,10 @@ __device__ __forceinline__ void restrict_node(const LevelDev &F, const LevelDev 
 }
 
 // bilinear prolongation of the coarse correction, added on free fine nodes
+template <bool FINE>
 __device__ __forceinline__ void prolong_node(const LevelDev &F, const LevelDev &C, int i, int j) {
   const int n = i * F.nyn + j;
-  if (!F.free[n]) return;
+  if (!is_free<FINE>(F, n)) return;
   const int I0 = i >> 1, J0 = j >> 1;
   const int I1 = (i & 1) ? (C.px ? wrapi(I0 + 1, C.nxn) : I0 + 1) : I0;
   const int J1 = (j & 1) ? (C.py ? wrapi(J0 + 1, C.nyn) : J0 + 1) : J0;
@@ -511,14 +526,15 @@ __global__ void k_restrict(MGArgs a, int l) {
   if (n < C.nxn * C.nyn) restrict_node<FINE>(a.L[l], C, n / C.nyn, n - (n / C.nyn) * C.nyn);
 }
 
+template <bool FINE>
 __global__ void k_prolong(MGArgs a, int l) {
   if (a.ps->inner_done) return;
   const LevelDev &F = a.L[l];
   const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < F.nxn * F.nyn) prolong_node(F, a.L[l + 1], n / F.nyn, n - (n / F.nyn) * F.nyn);
+  if (n < F.nxn * F.nyn) prolong_node<FINE>(F, a.L[l + 1], n / F.nyn, n - (n / F.nyn) * F.nyn);
 }
 
-// ---- the levels from lc down, inside one CTA, vectors in shared memory ----
+// ---- the levels from lc down, inside one CTA, everything in shared memory ----
 template <bool FINE>
 __device__ void cta_sweep(const LevelDev &L, int c) {
   const int cnt = colour_count<FINE>(L);
@@ -555,27 +571,62 @@ __device__ void cta_restrict(const LevelDev &F, const LevelDev &C) {
   __syncthreads();
 }
 
+template <bool FINE>
 __device__ void cta_prolong(const LevelDev &F, const LevelDev &C) {
   const int nn = F.nxn * F.nyn;
-  for (int n = threadIdx.x; n < nn; n += blockDim.x) prolong_node(F, C, n / F.nyn, n % F.nyn);
+  for (int n = threadIdx.x; n < nn; n += blockDim.x) prolong_node<FINE>(F, C, n / F.nyn, n % F.nyn);
   __syncthreads();
+}
+
+template <typename T>
+__device__ __forceinline__ T *carve(unsigned char *&p, size_t count) {
+  T *r = reinterpret_cast<T *>(p);
+  p += (count * sizeof(T) + 15) & ~size_t(15);
+  return r;
+}
+
+// Shared-memory bytes of k_coarse (the same carving as the kernel).
+size_t coarse_smem_bytes(const MGArgs &a) {
+  auto seg = [](size_t b) { return (b + 15) & ~size_t(15); };
+  size_t t = 0;
+  for (int l = a.lc; l < a.nlev; ++l) {
+    const size_t nn = size_t(a.L[l].nxn) * a.L[l].nyn;
+    t += 2 * seg(nn * 4);
+    t += l == 0 ? seg(nn) : seg(nn * 2) + seg(size_t(a.nst[l]) * 9 * 4);
+  }
+  t += seg(size_t(a.ncoarse) * a.ncoarse * 4) + seg(size_t(a.ncoarse) * 4);
+  return t;
 }
 
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse(MGArgs a) {
   if (a.ps->inner_done) return;
-  extern __shared__ float smem[];
+  extern __shared__ __align__(16) unsigned char smem[];
   const int lc = a.lc, last = a.nlev - 1;
-  // level copies whose vectors live in shared memory
   LevelDev S[16];
-  float *p = smem;
+  unsigned char *p = smem;
   for (int l = lc; l <= last; ++l) {
     S[l] = a.L[l];
     const int nn = S[l].nxn * S[l].nyn;
-    S[l].u = p;
-    p += nn;
-    S[l].f = p;
-    p += nn;
+    S[l].u = carve<float>(p, nn);
+    S[l].f = carve<float>(p, nn);
+    if (l == 0) {
+      uint8_t *fr = carve<uint8_t>(p, nn);
+      for (int n = threadIdx.x; n < nn; n += blockDim.x) fr[n] = a.L[0].free[n];
+      S[l].free = fr;
+    } else {
+      uint16_t *sid = carve<uint16_t>(p, nn);
+      float *tab = carve<float>(p, size_t(a.nst[l]) * 9);
+      for (int n = threadIdx.x; n < nn; n += blockDim.x) sid[n] = a.L[l].sid[n];
+      for (int k = threadIdx.x; k < a.nst[l] * 9; k += blockDim.x) tab[k] = a.L[l].stab[k];
+      S[l].sid = sid;
+      S[l].stab = tab;
+    }
   }
+  const int nc = a.ncoarse;
+  float *cinv = carve<float>(p, size_t(nc) * nc);
+  int *cidx = carve<int>(p, nc);
+  for (int k = threadIdx.x; k < nc * nc; k += blockDim.x) cinv[k] = a.cinv[k];
+  for (int k = threadIdx.x; k < nc; k += blockDim.x) cidx[k] = a.cidx[k];
   {
     const int nn = S[lc].nxn * S[lc].nyn;
     for (int n = threadIdx.x; n < nn; n += blockDim.x) S[lc].f[n] = a.L[lc].f[n];
@@ -590,8 +641,19 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse(MGArgs a) {
       cta_restrict<false>(S[l], S[l + 1]);
     }
   }
-  // coarsest level: symmetric sweeps from zero
-  if (last == 0) {
+  if (nc > 0) {
+    // coarsest level: exact solve by the precomputed (pseudo-)inverse
+    const LevelDev &L = S[last];
+    const int nn = L.nxn * L.nyn;
+    for (int n = threadIdx.x; n < nn; n += blockDim.x) L.u[n] = 0.f;
+    __syncthreads();
+    for (int r = threadIdx.x; r < nc; r += blockDim.x) {
+      float acc = 0.f;
+      for (int k = 0; k < nc; ++k) acc = fmaf(cinv[r * nc + k], L.f[cidx[k]], acc);
+      L.u[cidx[r]] = acc;
+    }
+    __syncthreads();
+  } else if (last == 0) {
     cta_smooth<true>(S[last], true, true);
     for (int s = 1; s < kCoarsestSweeps; ++s) cta_smooth<true>(S[last], true, false);
     for (int s = 0; s < kCoarsestSweeps; ++s) cta_smooth<true>(S[last], false, false);
@@ -601,9 +663,13 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse(MGArgs a) {
     for (int s = 0; s < kCoarsestSweeps; ++s) cta_smooth<false>(S[last], false, false);
   }
   for (int l = last - 1; l >= lc; --l) {
-    cta_prolong(S[l], S[l + 1]);
-    if (l == 0) cta_smooth<true>(S[l], false, false);
-    else cta_smooth<false>(S[l], false, false);
+    if (l == 0) {
+      cta_prolong<true>(S[l], S[l + 1]);
+      cta_smooth<true>(S[l], false, false);
+    } else {
+      cta_prolong<false>(S[l], S[l + 1]);
+      cta_smooth<false>(S[l], false, false);
+    }
   }
   const int nn = S[lc].nxn * S[lc].nyn;
   for (int n = threadIdx.x; n < nn; n += blockDim.x) a.L[lc].u[n] = S[lc].u[n];
@@ -661,10 +727,15 @@ MGArgs mg_args(pic_ctx *c) {
     a.L[l].px = c->g.px;
     a.L[l].py = c->g.py;
     a.L[l].free = m.free;
-    a.L[l].st = m.st;
+    a.L[l].sid = m.sid;
+    a.L[l].stab = m.stab;
     a.L[l].u = m.u;
     a.L[l].f = m.f;
+    a.nst[l] = m.nst;
   }
+  a.ncoarse = c->ncoarse;
+  a.cinv = c->d_cinv;
+  a.cidx = c->d_cidx;
   a.ps = c->d_ps;
   return a;
 }
@@ -695,7 +766,8 @@ void launch_vcycle(pic_ctx *c, const MGArgs &a) {
   for (int l = c->lc - 1; l >= 0; --l) {
     const MGLevel &L = c->lev[l];
     const int nn = L.nxn * L.nyn;
-    k_prolong<<<blocks_for(nn), kThreads, 0, c->stream>>>(a, l);
+    if (l == 0) k_prolong<true><<<blocks_for(nn), kThreads, 0, c->stream>>>(a, l);
+    else k_prolong<false><<<blocks_for(nn), kThreads, 0, c->stream>>>(a, l);
     if (l == 0) {
       const int nh = blocks_for(L.nxn * ((L.nyn + 1) / 2));
       k_gs<true><<<nh, kThreads, 0, c->stream>>>(a, l, 1);
@@ -827,38 +899,136 @@ cudaError_t poisson_setup(pic_ctx *c) {
       c->lc = l;
       break;
     }
-  size_t smem_floats = 0;
-  for (int l = c->lc; l < c->nlev; ++l) smem_floats += 2 * size_t(c->lev[l].nxn) * c->lev[l].nyn;
-  c->coarse_smem = smem_floats * sizeof(float);
-  if (c->coarse_smem > 220 * 1024) return cudaErrorInvalidValue;
-  cudaError_t e = cudaFuncSetAttribute(k_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(c->coarse_smem));
-  if (e != cudaSuccess) return e;
   const size_t nn = size_t(g.nxn) * g.nyn;
   for (int l = 0; l < c->nlev; ++l) {
     MGLevel &m = c->lev[l];
     const size_t n = size_t(m.nxn) * m.nyn;
-    m.free = (uint8_t *)dev_alloc(c, n);
-    if (!m.free) return cudaErrorMemoryAllocation;
-    cudaMemcpy(m.free, masks[l].data(), n, cudaMemcpyHostToDevice);
-    m.st = nullptr;
+    m.free = nullptr;
+    m.sid = nullptr;
+    m.stab = nullptr;
+    m.nst = 0;
     if (l == 0) {
+      m.free = (uint8_t *)dev_alloc(c, n);
+      if (!m.free) return cudaErrorMemoryAllocation;
+      cudaMemcpy(m.free, masks[0].data(), n, cudaMemcpyHostToDevice);
       m.u = nullptr;
       m.f = nullptr;
-    } else {
-      std::vector<float> stf(n * 9);
-      for (size_t k = 0; k < stf.size(); ++k) stf[k] = float(sts[l][k]);
-      for (size_t k = 0; k < n; ++k)
-        if (!masks[l][k]) stf[k * 9 + 4] = 1.0f;   // never used: keeps the diagonal finite
-      m.st = (float *)dev_alloc(c, n * 9 * sizeof(float));
-      m.u = (float *)dev_alloc(c, n * sizeof(float));
-      m.f = (float *)dev_alloc(c, n * sizeof(float));
-      if (!m.u || !m.f || !m.st) return cudaErrorMemoryAllocation;
-      cudaMemcpy(m.st, stf.data(), n * 9 * sizeof(float), cudaMemcpyHostToDevice);
-      cudaMemsetAsync(m.u, 0, n * sizeof(float), c->stream);
-      cudaMemsetAsync(m.f, 0, n * sizeof(float), c->stream);
+      continue;
+    }
+    // unique stencils of the level and each node's entry (0 = not an unknown)
+    std::map<std::array<float, 9>, int> table;
+    std::vector<std::array<float, 9>> uniq;
+    std::vector<uint16_t> sid(n, 0);
+    for (size_t k = 0; k < n; ++k) {
+      if (!masks[l][k]) continue;
+      std::array<float, 9> st;
+      for (int q = 0; q < 9; ++q) st[q] = float(sts[l][k * 9 + q]);
+      auto it = table.find(st);
+      int id;
+      if (it == table.end()) {
+        id = int(uniq.size());
+        if (id >= 65535) return cudaErrorInvalidValue;
+        table.emplace(st, id);
+        uniq.push_back(st);
+      } else {
+        id = it->second;
+      }
+      sid[k] = uint16_t(id + 1);
+    }
+    m.nst = int(uniq.size());
+    std::vector<float> tab(std::max<size_t>(uniq.size(), 1) * 9, 0.f);
+    for (size_t k = 0; k < uniq.size(); ++k)
+      for (int q = 0; q < 9; ++q) tab[k * 9 + q] = uniq[k][q];
+    m.sid = (uint16_t *)dev_alloc(c, n * 2);
+    m.stab = (float *)dev_alloc(c, tab.size() * 4);
+    m.u = (float *)dev_alloc(c, n * sizeof(float));
+    m.f = (float *)dev_alloc(c, n * sizeof(float));
+    if (!m.u || !m.f || !m.sid || !m.stab) return cudaErrorMemoryAllocation;
+    cudaMemcpy(m.sid, sid.data(), n * 2, cudaMemcpyHostToDevice);
+    cudaMemcpy(m.stab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice);
+    cudaMemsetAsync(m.u, 0, n * sizeof(float), c->stream);
+    cudaMemsetAsync(m.f, 0, n * sizeof(float), c->stream);
+  }
+  // coarsest level: dense (pseudo-)inverse when it is small
+  {
+    const int last = c->nlev - 1;
+    const MGLevel &m = c->lev[last];
+    const size_t n = size_t(m.nxn) * m.nyn;
+    std::vector<int> idx;
+    for (size_t k = 0; k < n; ++k)
+      if (masks[last][k]) idx.push_back(int(k));
+    const int nc = int(idx.size());
+    c->ncoarse = 0;
+    c->d_cinv = nullptr;
+    c->d_cidx = nullptr;
+    if (nc > 0 && nc <= kDenseCoarsest) {
+      std::vector<int> pos(n, -1);
+      for (int r = 0; r < nc; ++r) pos[idx[r]] = r;
+      // dense operator over the unknowns (level 0: 5-point; else the Galerkin stencils)
+      std::vector<double> A(size_t(nc) * nc, 0.0);
+      for (int r = 0; r < nc; ++r) {
+        const int I = idx[r] / m.nyn, J = idx[r] % m.nyn;
+        for (int di = -1; di <= 1; ++di)
+          for (int dj = -1; dj <= 1; ++dj) {
+            const double coef = sts[last][size_t(idx[r]) * 9 + (di + 1) * 3 + (dj + 1)];
+            if (coef == 0.0) continue;
+            int a = I + di, b = J + dj;
+            if (g.px) a = (a + m.nxn) % m.nxn;
+            if (g.py) b = (b + m.nyn) % m.nyn;
+            if (a < 0 || a >= m.nxn || b < 0 || b >= m.nyn) continue;
+            const int q = pos[size_t(a) * m.nyn + b];
+            if (q >= 0) A[size_t(r) * nc + q] += coef;
+          }
+      }
+      // a doubly periodic box is singular (constants): invert A + 11^T/n, subtract 11^T/n
+      if (c->singular)
+        for (auto &v : A) v += 1.0 / nc;
+      std::vector<double> inv(size_t(nc) * nc, 0.0);
+      for (int r = 0; r < nc; ++r) inv[size_t(r) * nc + r] = 1.0;
+      bool ok = true;
+      for (int col = 0; col < nc && ok; ++col) {   // Gauss-Jordan with partial pivoting
+        int piv = col;
+        for (int r = col + 1; r < nc; ++r)
+          if (std::fabs(A[size_t(r) * nc + col]) > std::fabs(A[size_t(piv) * nc + col])) piv = r;
+        if (!(std::fabs(A[size_t(piv) * nc + col]) > 1e-300)) { ok = false; break; }
+        if (piv != col)
+          for (int k = 0; k < nc; ++k) {
+            std::swap(A[size_t(piv) * nc + k], A[size_t(col) * nc + k]);
+            std::swap(inv[size_t(piv) * nc + k], inv[size_t(col) * nc + k]);
+          }
+        const double d = A[size_t(col) * nc + col];
+        for (int k = 0; k < nc; ++k) {
+          A[size_t(col) * nc + k] /= d;
+          inv[size_t(col) * nc + k] /= d;
+        }
+        for (int r = 0; r < nc; ++r) {
+          if (r == col) continue;
+          const double f = A[size_t(r) * nc + col];
+          if (f == 0.0) continue;
+          for (int k = 0; k < nc; ++k) {
+            A[size_t(r) * nc + k] -= f * A[size_t(col) * nc + k];
+            inv[size_t(r) * nc + k] -= f * inv[size_t(col) * nc + k];
+          }
+        }
+      }
+      if (ok) {
+        if (c->singular)
+          for (auto &v : inv) v -= 1.0 / nc;
+        std::vector<float> invf(inv.begin(), inv.end());
+        c->d_cinv = (float *)dev_alloc(c, invf.size() * 4);
+        c->d_cidx = (int *)dev_alloc(c, idx.size() * 4);
+        if (!c->d_cinv || !c->d_cidx) return cudaErrorMemoryAllocation;
+        cudaMemcpy(c->d_cinv, invf.data(), invf.size() * 4, cudaMemcpyHostToDevice);
+        cudaMemcpy(c->d_cidx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice);
+        c->ncoarse = nc;
+      }
     }
   }
+  c->coarse_smem = coarse_smem_bytes(mg_args(c));
+  if (c->coarse_smem > 220 * 1024) return cudaErrorInvalidValue;
+  cudaError_t e = cudaFuncSetAttribute(k_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(c->coarse_smem));
+  if (e != cudaSuccess) return e;
   float **vecs[] = {&c->d_r32, &c->d_z, &c->d_p0, &c->d_p1, &c->d_q, &c->d_e};
   for (float **v : vecs) {
     *v = (float *)dev_alloc(c, nn * sizeof(float));

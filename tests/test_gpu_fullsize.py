@@ -1,0 +1,110 @@
+"""Parity at the full 512 x 1024 trench size (84.8M particles) in the launch
+configuration the benchmark times (captured step graphs, sort every 8
+steps): sampled outputs the oracle computes one by one, and properties that
+hold at any size."""
+import numpy as np
+import pytest
+
+import synth
+from oracle import deposit as odeposit
+from oracle import field as ofield
+from oracle import poisson as opoisson
+from oracle import push as opush
+from oracle.geometry import from_workload
+
+from gpu_helpers import POS_TOL, RHO_TOL, VEL_TOL, FIELD_TOL, face_distance
+
+pytestmark = pytest.mark.gpu
+
+
+@pytest.fixture(scope="module")
+def full():
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1610_03918_gb300 as pg
+    w = synth.trench_512x1024()
+    parts = [synth.maxwellian_load(w, s) for s in (0, 1)]
+    sim = pg.Sim(w, capacity=len(parts[0]))
+    for s in (0, 1):
+        sim.load_particles(s, parts[s], v_at_t0=True)
+    sim.step(0)
+    yield w, sim, parts
+    sim.close()
+
+
+def test_fullsize_deposit(full):
+    w, sim, parts = full
+    geom = from_workload(w)
+    rho = sim.rho()
+    # total charge: the fixed-point deposit is exact per particle
+    n = [len(p) for p in parts]
+    assert rho.sum() == pytest.approx((n[1] - n[0]) / w.ppc, abs=1e-6 * sum(n) / w.ppc)
+    # sampled nodes: the oracle deposits the particles of the four cells around each
+    rng = np.random.default_rng(7)
+    free = np.argwhere(geom.free)
+    nodes = free[rng.choice(len(free), 64, replace=False)]
+    near = np.zeros((w.nx, w.ny), bool)          # cells touching a sampled node
+    for (i, j) in nodes:
+        for di in (-1, 0):
+            if 0 <= i + di < w.nx:
+                near[i + di, j % w.ny] = near[i + di, (j - 1) % w.ny] = True
+    ref = np.zeros(len(nodes))
+    for s in (0, 1):
+        p = parts[s]
+        sel = near[np.floor(p.x).astype(np.int64), np.floor(p.y).astype(np.int64)]
+        dens = odeposit.cic_density(geom, p.x[sel], p.y[sel], 1.0 / w.ppc)
+        ref += w.charge[s] * dens[nodes[:, 0], nodes[:, 1]]
+    got = rho[nodes[:, 0], nodes[:, 1]]
+    assert np.abs(got - ref).max() <= RHO_TOL * np.abs(rho).max()
+
+
+def test_fullsize_poisson_certificate_and_field(full):
+    w, sim, parts = full
+    geom = from_workload(w)
+    rho, phi = sim.rho(), sim.phi()
+    it, outer, rel, ms = sim.poisson_stats()
+    assert rel <= w.poisson_rtol
+    # the oracle's own FP64 residual of the GPU potential
+    assert opoisson.residual_rel(geom, phi, rho) <= 1.05 * w.poisson_rtol
+    # the field kernel at full size against the oracle's field rule on the same phi
+    Exg, Eyg = sim.efield()
+    Exo, Eyo = ofield.efield(geom, phi)
+    emax = max(np.abs(Exo).max(), np.abs(Eyo).max())
+    assert np.abs(Exg - Exo).max() <= FIELD_TOL * emax
+    assert np.abs(Eyg - Eyo).max() <= FIELD_TOL * emax
+
+
+def test_fullsize_push_sampled(full):
+    w, sim, parts = full
+    geom = from_workload(w)
+    Ex, Ey = sim.efield()
+    before = [sim.state(s) for s in (0, 1)]
+    walls0, live0 = sim.counts()
+    sim.step(1)
+    walls1, live1 = sim.counts()
+    # particle number: every particle is either live or tallied on a wall
+    for s in (0, 1):
+        assert live1[s] + (walls1[s] - walls0[s]).sum() == live0[s]
+    rng = np.random.default_rng(11)
+    for s in (0, 1):
+        b = before[s]
+        pick = rng.choice(b.shape[1], 20000, replace=False)
+        x, y, vx, vy, ids = b[0, pick], b[1, pick], b[2, pick], b[3, pick], b[4, pick]
+        x1, y1, vx1, vy1, alive, wall, wcell = opush.leapfrog(
+            geom, w.alpha[s], w.dt, x, y, vx, vy, Ex, Ey)
+        after = sim.state(s)
+        order = np.argsort(after[4])
+        pos = np.searchsorted(after[4][order], ids)
+        pos = np.minimum(pos, after.shape[1] - 1)
+        found = after[4][order][pos] == ids
+        # aliveness agrees except for moves ending within 1e-5 of a face
+        grazing = np.minimum(face_distance(x + vx1 * w.dt), face_distance(y + vy1 * w.dt)) <= 1e-5
+        assert np.all((found == alive) | grazing)
+        m = found & alive
+        g = after[:, order[pos[m]]]
+        dx = g[0] - x1[m]
+        dy = (g[1] - y1[m] + w.ny / 2) % w.ny - w.ny / 2
+        assert np.abs(dx).max() <= POS_TOL and np.abs(dy).max() <= POS_TOL
+        vs = np.maximum(np.maximum(np.abs(vx1[m]), np.abs(vy1[m])), w.vth[s])
+        assert np.all(np.abs(g[2] - vx1[m]) <= VEL_TOL * vs)
+        assert np.all(np.abs(g[3] - vy1[m]) <= VEL_TOL * vs)
