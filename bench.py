@@ -224,6 +224,8 @@ def main():
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppc", type=int, default=None, help="override particles per cell")
     ap.add_argument("--sort-every", type=int, default=None, help="steps between tile sorts")
+    ap.add_argument("--warm-start", type=int, default=1,
+                    help="Poisson initial guess: 0 zero, 1 previous, 2 extrapolated")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the step's kernels from the host loop (for kernel profilers)")
     args = ap.parse_args()
@@ -248,7 +250,8 @@ def main():
         w = w.replace(sort_every=args.sort_every)
     parts = [synth.maxwellian_load(w, s) for s in (0, 1)]
     n0 = sum(len(p) for p in parts)
-    sim = pg.Sim(w, capacity=len(parts[0]), device=local, timing=True, graphs=not args.no_graphs)
+    sim = pg.Sim(w, capacity=len(parts[0]), device=local, timing=True, graphs=not args.no_graphs,
+                 warm_start=args.warm_start)
     for s in (0, 1):
         sim.load_particles(s, parts[s], v_at_t0=True)
     sim.step(args.warmup)
@@ -339,6 +342,7 @@ def main():
             "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "ppc": w.ppc,
                        "particles_loaded": n0, "live_particles": live_mean,
                        "sort_every": w.sort_every, "poisson_rtol": w.poisson_rtol,
+                       "warm_start": ["zero", "previous", "extrapolated"][args.warm_start],
                        "l2": "inputs larger than L2 (particle state %.1f GB)" % (n0 * 24 / 1e9),
                        "parallelism": f"replicas{ws}" if ws > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",

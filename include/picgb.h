@@ -97,7 +97,8 @@ typedef struct {
   int32_t sort_every;             /* steps between tile sorts (>= 1) */
   int32_t poisson_maxit;          /* cap on inner PCG iterations per solve */
   double poisson_rtol;            /* target ||b - A phi||_2 / ||b||_2 (FP64) */
-  int32_t warm_start;             /* 0: zero initial guess each solve, 1: previous phi */
+  int32_t warm_start;             /* 0: zero initial guess each solve, 1: previous phi,
+                                     2: extrapolated 2 phi^n - phi^{n-1} */
   int32_t device;                 /* CUDA device ordinal */
   int32_t timing;                 /* 1: pic_step waits for each step and accumulates the
                                      per-phase device times of PIC_DIAG_TIMING */

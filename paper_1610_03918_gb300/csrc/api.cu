@@ -162,6 +162,7 @@ pic_status validate(const pic_config *cfg) {
   if (cfg->periodic_y && (cfg->ny % 2)) return PIC_EINVAL;
   if (!(cfg->dt > 0) || !(cfg->poisson_rtol > 0)) return PIC_EINVAL;
   if (cfg->poisson_maxit < 1 || cfg->sort_every < 1) return PIC_EINVAL;
+  if (cfg->warm_start < 0 || cfg->warm_start > 2) return PIC_EINVAL;
   for (int s = 0; s < 2; ++s) {
     if (cfg->ppc[s] < 1 || cfg->capacity[s] < 0) return PIC_EINVAL;
     if (cfg->capacity[s] > (int64_t(1) << 31) - (int64_t(1) << 26)) return PIC_EINVAL;
@@ -185,6 +186,10 @@ pic_status prepare(pic_ctx *c) {
   if ((st = check(launch_rho(c, 0))) != PIC_OK) return st;
   st = poisson_solve(c, true);
   if (st != PIC_OK) return st;
+  // the extrapolated warm start begins from a constant history
+  if (cudaMemcpyAsync(c->d_phi_prev, c->d_phi, size_t(c->g.nxn) * c->g.nyn * sizeof(double),
+                      cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+    return PIC_ECUDA;
   if ((st = check(launch_field(c))) != PIC_OK) return st;
   if (c->pending_kick[0] || c->pending_kick[1]) {
     if ((st = check(launch_particles(c, 2, -0.5f, c->pending_kick))) != PIC_OK) return st;

@@ -23,6 +23,7 @@ constexpr int kTileY = 16;
 constexpr int kHalo = 4;
 constexpr int kChunk = 4092;     // particles per work item (multiple of 4, <= 4095)
 constexpr int kParticleThreads = 256;
+constexpr int kParticleMinBlocks = 4;   // resident CTAs per SM the register budget allows
 constexpr int kWalkLimit = 16;   // face crossings followed per move
 
 struct Geom {
@@ -104,6 +105,7 @@ struct pic_ctx {
   double *d_rho;               // net charge density
   double *d_b;                 // right-hand side on free nodes
   double *d_phi;               // FP64 master potential (Dirichlet values included)
+  double *d_phi_prev;          // potential of the previous step (extrapolated warm start)
   float2 *d_E;
   double *d_fe;                // [2]: field energy of E just computed, of E used by last step
 

@@ -380,7 +380,7 @@ __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint3
 }
 
 template <int MODE>
-__global__ void __launch_bounds__(kParticleThreads) k_particles(PArgs a) {
+__global__ void __launch_bounds__(kParticleThreads, kParticleMinBlocks) k_particles(PArgs a) {
   __shared__ float2 sE[NWX * NWY];
   __shared__ uint32_t sAcc[NWX * NWY];
   __shared__ double sRed[kParticleThreads / 32];

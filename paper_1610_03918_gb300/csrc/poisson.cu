@@ -114,6 +114,7 @@ struct FineArgs {
   const double *lift;
   const double *gval;
   double *rho, *b, *phi;
+  double *phi_prev;          // potential of the previous step (extrapolated warm start)
   unsigned long long *acc;
   const double *rho_ext;
   const unsigned long long *bottom;
@@ -178,6 +179,17 @@ __global__ void k_rho(FineArgs a) {
 // phi <- Dirichlet values, zero on free nodes (cold start)
 __global__ void k_phi_reset(FineArgs a) {
   GRID_STRIDE(n, a.g.nxn * a.g.nyn) a.phi[n] = a.gval[n];
+}
+
+// initial guess extrapolated in time: phi <- 2 phi^n - phi^{n-1} on free nodes
+__global__ void k_extrapolate(FineArgs a) {
+  GRID_STRIDE(n, a.g.nxn * a.g.nyn) {
+    if (a.flags[n] & kFree) {
+      const double p = a.phi[n];
+      a.phi[n] = 2.0 * p - a.phi_prev[n];
+      a.phi_prev[n] = p;
+    }
+  }
 }
 
 __device__ __forceinline__ void nbr_index(const Geom &g, int n, int &xm, int &xp, int &ym, int &yp) {
@@ -685,6 +697,7 @@ FineArgs fine_args(pic_ctx *c) {
   a.rho = c->d_rho;
   a.b = c->d_b;
   a.phi = c->d_phi;
+  a.phi_prev = c->d_phi_prev;
   a.acc = c->d_acc;
   a.rho_ext = c->d_rho_ext;
   a.bottom = c->d_bottom;
@@ -1037,6 +1050,8 @@ cudaError_t poisson_setup(pic_ctx *c) {
   }
   c->lev[0].u = c->d_z;
   c->lev[0].f = c->d_r32;
+  c->d_phi_prev = (double *)dev_alloc(c, nn * sizeof(double));
+  if (!c->d_phi_prev) return cudaErrorMemoryAllocation;
   c->red.nblocks = std::min(blocks_for(int(nn)), 2 * c->num_sms);
   c->red.part = (double *)dev_alloc(c, size_t(c->red.nblocks) * 4 * sizeof(double));
   c->red.ticket = (unsigned int *)dev_alloc(c, 64);
@@ -1071,6 +1086,9 @@ pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
   cudaEventRecord(c->ev0, c->stream);
   if (zero_guess) {
     k_phi_reset<<<nb, kThreads, 0, c->stream>>>(a);
+    c->launches += 1;
+  } else if (c->cfg.warm_start == 2) {
+    k_extrapolate<<<nb, kThreads, 0, c->stream>>>(a);
     c->launches += 1;
   }
   k_outer_init<<<1, 1, 0, c->stream>>>(c->d_ps);
@@ -1173,6 +1191,7 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
 #define CK(x) do { if ((e = (x)) != cudaSuccess) return e; } while (0)
   CK(cap_begin(s, top, deps));
   if (c->cfg.warm_start == 0) k_phi_reset<<<nb, kThreads, 0, s>>>(a);
+  if (c->cfg.warm_start == 2) k_extrapolate<<<nb, kThreads, 0, s>>>(a);
   k_outer_init<<<1, 1, 0, s>>>(c->d_ps);
   CK(cap_end(s, deps));
   cudaGraphNode_t n_outer, n_if_outer, n_inner, n_if_inner;
@@ -1214,7 +1233,7 @@ int64_t poisson_kernel_count(pic_ctx *c, const PoissonState &ps) {
   // init + resid per outer pass (+1 final) + per inner solve (V-cycle, rz, correct)
   // + per iteration (pq, update) + per non-final iteration (V-cycle, rz)
   return 1 + (O + 1) + O * (vc + 2) + 2 * I + std::max<int64_t>(I - O, 0) * (vc + 1) +
-         (c->cfg.warm_start == 0 ? 1 : 0);
+         (c->cfg.warm_start != 1 ? 1 : 0);
 }
 
 }  // namespace picgb
