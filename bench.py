@@ -214,12 +214,75 @@ def run_reference(args):
     return 0
 
 
+def run_ensemble(args):
+    """The trench-width sweep: members k = 0..M-1 of the recipe (widths
+    1..40, grids 128x256 .. 512x512, 64 ppc), one graph launch per step."""
+    dist, rank, ws = _dist()
+    import torch
+    local = int(os.environ.get("LOCAL_RANK", "0"))
+    torch.cuda.set_device(local)
+    import __graft_entry__
+    if rank == 0 or dist is None:
+        __graft_entry__.build()
+    _barrier(dist)
+    import paper_1610_03918_gb300 as pg
+    wl = [synth.ensemble_member(k) for k in range(args.members)]
+    if args.ppc:
+        wl = [w.replace(ppc=args.ppc) for w in wl]
+    if args.sort_every:
+        wl = [w.replace(sort_every=args.sort_every) for w in wl]
+    batch = pg.Batch(wl, capacities=[int(synth.plasma_cells(w).sum()) * w.ppc for w in wl],
+                     device=local, timing=True)
+    n0 = 0
+    for m, w in zip(batch.members, wl):
+        for s in (0, 1):
+            p = synth.maxwellian_load(w, s)
+            n0 += len(p)
+            m.load_particles(s, p, v_at_t0=True)
+            del p
+    batch.step(args.warmup)
+    batch.timing()
+    live0 = sum(int(m.counts()[1].sum()) for m in batch.members)
+    clocks = ClockSampler(local)
+    clocks.start()
+    _barrier(dist)
+    batch.step(args.steps)
+    t = batch.timing()
+    _barrier(dist)
+    clk = clocks.stop()
+    live1 = sum(int(m.counts()[1].sum()) for m in batch.members)
+    ms = _reduce_max(dist, t["ms"])
+    ps_total = _reduce_sum(dist, 0.5 * (live0 + live1) * args.steps)
+    value = ps_total / (ms * 1e-3)
+    peak, peak_kind = _peaks()
+    achieved = BYTES_PER_PARTICLE_STEP * value / 1e9
+    if rank == 0:
+        print(json.dumps({
+            "metric": METRIC, "value": value, "unit": UNIT, "n_gpus": ws, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms / args.steps, "higher_is_better": True,
+            "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
+            "config": {"workload": f"trench_width_ensemble_{args.members}", "members": args.members,
+                       "ppc": wl[0].ppc, "particles_loaded": n0, "sort_every": wl[0].sort_every,
+                       "l2": "inputs larger than L2"},
+            "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
+                         "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
+                         "note": "whole ensemble step (all phases) at 40 B per particle-step"},
+            "clocks": clk}), flush=True)
+    batch.close()
+    if dist is not None:
+        dist.destroy_process_group()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--workload", default="trench", choices=["trench", "ensemble"],
+                    help="trench: the 512x1024 trench run; ensemble: the 48-run width sweep")
+    ap.add_argument("--members", type=int, default=48, help="ensemble members")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppc", type=int, default=None, help="override particles per cell")
@@ -232,6 +295,8 @@ def main():
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(args.warmup, 3)
+    if args.workload == "ensemble":
+        return run_ensemble(args)
 
     dist, rank, ws = _dist()
     import torch

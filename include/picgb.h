@@ -187,6 +187,40 @@ pic_status pic_free(pic_ctx *ctx);
 /* Static description of a status code. */
 const char *pic_strerror(pic_status st);
 
+/* Text of the last failure recorded on the calling thread (the failing CUDA
+ * call and its error string), or "" if none. */
+const char *pic_last_error(void);
+
+/* Ensemble of independent runs on one GPU (the trench-width sweep of
+ * Sec. III-C run as a batch).  Each member is a full context built from
+ * cfgs[k] (its own grid size, trench, particles and tallies); all members
+ * share one CUDA stream (`stream`, or a library-owned one when NULL) and one
+ * tile-sort schedule (equal sort_every, else PIC_EINVAL).  One ensemble step
+ * is one launch of a captured CUDA graph in which every member's step (sort
+ * when due, particle kernel, rho, Poisson solve with its own device-side
+ * convergence loop, field) is an independent branch, so the members' phases
+ * overlap on the GPU.  Load and read members with pic_load / pic_diag on
+ * pic_batch_member(b, k); advance them only through pic_batch_step. */
+typedef struct pic_batch pic_batch;
+
+pic_status pic_batch_init(const pic_config *cfgs, int32_t n, void *stream, pic_batch **out);
+
+/* Member k's context (owned by the batch), or NULL for an invalid index. */
+pic_ctx *pic_batch_member(pic_batch *b, int32_t k);
+
+/* Advance every member by nsteps.  Members whose fields are out of date
+ * (after pic_load) are brought up to date first, as pic_step(ctx, 0) does.
+ * Returns once the steps are queued; with cfgs[0].timing it waits for each
+ * step and accumulates its device time. */
+pic_status pic_batch_step(pic_batch *b, int32_t nsteps);
+
+/* out[0] = ensemble steps and out[1] = their device milliseconds (CUDA
+ * events around each ensemble graph launch) since the last call. */
+pic_status pic_batch_timing(pic_batch *b, double *out);
+
+/* Release the batch and all its members. */
+pic_status pic_batch_free(pic_batch *b);
+
 /* Cloud-in-cell deposit that allocates no device memory.  The paper has no
  * counterpart; this is a service for callers that cannot allocate at the
  * point where they deposit -- a program whose device memory is owned by

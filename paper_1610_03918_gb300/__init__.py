@@ -32,7 +32,9 @@ PIC_LOAD_V_AT_T0 = 1
 (WALL_XMIN, WALL_XMAX, WALL_YMIN, WALL_YMAX, WALL_COND_PX, WALL_COND_MX,
  WALL_COND_PY, WALL_COND_MY) = range(8)
 
-EXPORTED = ("pic_init", "pic_load", "pic_step", "pic_diag", "pic_free", "pic_strerror")
+EXPORTED = ("pic_init", "pic_load", "pic_step", "pic_diag", "pic_free", "pic_strerror",
+            "pic_batch_init", "pic_batch_member", "pic_batch_step", "pic_batch_timing",
+            "pic_batch_free", "pic_deposit_static")
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -92,6 +94,17 @@ def load_library():
     lib.pic_free.argtypes = [P]
     lib.pic_strerror.argtypes = [ctypes.c_int]
     lib.pic_strerror.restype = ctypes.c_char_p
+    lib.pic_last_error.argtypes = []
+    lib.pic_last_error.restype = ctypes.c_char_p
+    lib.pic_batch_init.argtypes = [ctypes.POINTER(PicConfig), ctypes.c_int32, P,
+                                   ctypes.POINTER(ctypes.c_void_p)]
+    lib.pic_batch_member.argtypes = [P, ctypes.c_int32]
+    lib.pic_batch_member.restype = ctypes.c_void_p
+    lib.pic_batch_step.argtypes = [P, ctypes.c_int32]
+    lib.pic_batch_timing.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
+    lib.pic_batch_free.argtypes = [P]
+    for name in ("pic_batch_init", "pic_batch_step", "pic_batch_timing", "pic_batch_free"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("pic_init", "pic_load", "pic_step", "pic_diag", "pic_free"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
@@ -101,7 +114,8 @@ def load_library():
 class PicError(RuntimeError):
     def __init__(self, code, where):
         self.code = code
-        super().__init__(f"{where}: {pic_strerror(code)} ({code})")
+        detail = load_library().pic_last_error().decode()
+        super().__init__(f"{where}: {pic_strerror(code)} ({code})" + (f" [{detail}]" if detail else ""))
 
 
 def pic_strerror(code: int) -> str:
@@ -210,9 +224,19 @@ class Sim:
     """One simulation context.  ``torch_memory``: allocate through PyTorch's
     caching allocator and run on PyTorch's current stream of ``device``."""
 
-    def __init__(self, w, capacity=None, device: int = 0, torch_memory: bool = True, **kw):
+    def __init__(self, w, capacity=None, device: int = 0, torch_memory: bool = True,
+                 _ctx=None, **kw):
         load_library()
         self.w = w
+        self.nxn = w.nx if w.periodic_x else w.nx + 1
+        self.nyn = w.ny if w.periodic_y else w.ny + 1
+        self._owned = _ctx is None
+        if _ctx is not None:        # a member of a Batch: the batch owns it
+            self.ctx = _ctx
+            self.cfg = kw.pop("_cfg")
+            self.torch_stream = None
+            self._allocator = None
+            return
         self._allocator = None
         stream = None
         self.torch_stream = None
@@ -228,13 +252,11 @@ class Sim:
         self.cfg = make_config(w, capacity=capacity, device=device, stream=stream,
                                allocator=self._allocator, **kw)
         self.ctx = pic_init(self.cfg)
-        self.nxn = w.nx if w.periodic_x else w.nx + 1
-        self.nyn = w.ny if w.periodic_y else w.ny + 1
 
     def close(self):
-        if self.ctx:
+        if self.ctx and self._owned:
             pic_free(self.ctx)
-            self.ctx = None
+        self.ctx = None
 
     def __del__(self):
         try:
@@ -324,3 +346,64 @@ class Sim:
         st, _ = pic_diag(self.ctx, PIC_DIAG_STATUS, out)
         self._check(st, "pic_diag(status)")
         return int(out[0])
+
+
+class Batch:
+    """An ensemble of independent runs advanced together: one captured CUDA
+    graph per ensemble step with every member's step as a parallel branch.
+    ``members[k]`` is a Sim view of member k for loading and diagnostics."""
+
+    def __init__(self, workloads, capacities=None, device: int = 0, timing: bool = False,
+                 torch_memory: bool = True, **kw):
+        lib = load_library()
+        self.workloads = list(workloads)
+        n = len(self.workloads)
+        capacities = capacities or [None] * n
+        self._allocator = None
+        self.torch_stream = None
+        stream = None
+        if torch_memory:
+            import torch
+            if not torch.cuda.is_available():
+                raise RuntimeError("no CUDA device visible")
+            torch.cuda.set_device(device)
+            self.torch_stream = torch.cuda.Stream(device)
+            stream = self.torch_stream.cuda_stream
+            self._allocator = _TorchAllocator(device, stream)
+        cfgs = (PicConfig * n)()
+        for k, w in enumerate(self.workloads):
+            cfgs[k] = make_config(w, capacity=capacities[k], device=device, stream=stream,
+                                  allocator=self._allocator, timing=timing, **kw)
+        self.cfgs = cfgs
+        h = ctypes.c_void_p()
+        st = lib.pic_batch_init(cfgs, n, stream, ctypes.byref(h))
+        if st != PIC_OK:
+            raise PicError(st, "pic_batch_init")
+        self.h = h
+        self.members = [Sim(w, _ctx=ctypes.c_void_p(lib.pic_batch_member(h, k)), _cfg=cfgs[k])
+                        for k, w in enumerate(self.workloads)]
+
+    def step(self, n=1):
+        st = load_library().pic_batch_step(self.h, int(n))
+        if st != PIC_OK:
+            raise PicError(st, "pic_batch_step")
+
+    def timing(self):
+        out = (ctypes.c_double * 2)()
+        st = load_library().pic_batch_timing(self.h, out)
+        if st != PIC_OK:
+            raise PicError(st, "pic_batch_timing")
+        return {"steps": out[0], "ms": out[1]}
+
+    def close(self):
+        if getattr(self, "h", None):
+            for m in self.members:
+                m.ctx = None
+            load_library().pic_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass

@@ -6,11 +6,19 @@
 #include <cmath>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "internal.cuh"
 
 namespace picgb {
+
+thread_local std::string g_last_error;
+
+cudaError_t note(cudaError_t e, const char *where) {
+  if (e != cudaSuccess) g_last_error = std::string(where) + ": " + cudaGetErrorString(e);
+  return e;
+}
 
 void *dev_alloc(pic_ctx *c, size_t bytes) {
   if (bytes == 0) bytes = 16;
@@ -199,6 +207,21 @@ pic_status prepare(pic_ctx *c) {
   return PIC_OK;
 }
 
+// Ends the capture on stream s and returns its current leaf nodes in `leaves`.
+cudaError_t capture_leaves(cudaStream_t s, std::vector<cudaGraphNode_t> &leaves) {
+  cudaStreamCaptureStatus cs;
+  unsigned long long id;
+  cudaGraph_t gg;
+  const cudaGraphNode_t *d = nullptr;
+  const cudaGraphEdgeData *ed = nullptr;
+  size_t nd = 0;
+  cudaError_t e = cudaStreamGetCaptureInfo(s, &cs, &id, &gg, &d, &ed, &nd);
+  if (e == cudaSuccess) leaves.assign(d, d + nd);
+  cudaGraph_t out;
+  const cudaError_t e2 = cudaStreamEndCapture(s, &out);
+  return e == cudaSuccess ? e2 : e;
+}
+
 // One step from the host: sort (when due), particle kernel, rho, solve, field,
 // with the phase events of PIC_DIAG_TIMING.
 pic_status step_kernels(pic_ctx *c, bool sorting) {
@@ -222,20 +245,21 @@ pic_status step_kernels(pic_ctx *c, bool sorting) {
   return PIC_OK;
 }
 
-// Capture (once) the step graph: [sort] -> particle kernel -> rho -> the
-// Poisson solve as nested conditional nodes -> field, with external event
-// nodes between the phases.  Kernel arguments are fixed device pointers; the
-// particle buffers are reached through the device-side buffer table.
-cudaError_t step_graph(pic_ctx *c, int with_sort) {
-  if (c->gexec[with_sort]) return cudaSuccess;
+// Appends one step of context c to graph g after the nodes in `deps`:
+// [sort] -> particle kernel -> rho -> the Poisson solve as nested conditional
+// nodes -> field.  With `events`, external event nodes separate the phases
+// (PIC_DIAG_TIMING).  On return `deps` holds the step's last node(s).
+// Kernel arguments are fixed device pointers; the particle buffers are reached
+// through the device-side buffer table, so the sort's swap needs no re-capture.
+cudaError_t capture_step(pic_ctx *c, cudaGraph_t g, std::vector<cudaGraphNode_t> &deps,
+                         int with_sort, bool events) {
   const int cur_save[2] = {c->cur[0], c->cur[1]};
   const int64_t launches_save = c->launches;
-  cudaGraph_t g;
-  cudaError_t e = cudaGraphCreate(&g, 0);
-  if (e != cudaSuccess) return e;
-  std::vector<cudaGraphNode_t> deps;
-  auto rec = [&](int k) { return cudaEventRecordWithFlags(c->tev[k], c->stream, cudaEventRecordExternal); };
-  e = cudaStreamBeginCaptureToGraph(c->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  auto rec = [&](int k) {
+    if (events) cudaEventRecordWithFlags(c->tev[k], c->stream, cudaEventRecordExternal);
+  };
+  cudaError_t e = cudaStreamBeginCaptureToGraph(c->stream, g, deps.empty() ? nullptr : deps.data(),
+                                                nullptr, deps.size(), cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     rec(0);
     if (with_sort) launch_sort(c);
@@ -244,19 +268,9 @@ cudaError_t step_graph(pic_ctx *c, int with_sort) {
     rec(2);
     launch_rho(c, 1);
     rec(3);
-    cudaStreamCaptureStatus cs;
-    unsigned long long id;
-    cudaGraph_t gg;
-    const cudaGraphNode_t *d = nullptr;
-    const cudaGraphEdgeData *ed = nullptr;
-    size_t nd = 0;
-    e = cudaStreamGetCaptureInfo(c->stream, &cs, &id, &gg, &d, &ed, &nd);
-    if (e == cudaSuccess) deps.assign(d, d + nd);
-    cudaGraph_t out;
-    const cudaError_t e2 = cudaStreamEndCapture(c->stream, &out);
-    if (e == cudaSuccess) e = e2;
+    e = note(capture_leaves(c->stream, deps), "capture: particle phase");
   }
-  if (e == cudaSuccess) e = poisson_capture(c, g, deps);
+  if (e == cudaSuccess) e = note(poisson_capture(c, g, deps), "capture: Poisson conditionals");
   if (e == cudaSuccess) {
     e = cudaStreamBeginCaptureToGraph(c->stream, g, deps.data(), nullptr, deps.size(),
                                       cudaStreamCaptureModeThreadLocal);
@@ -264,14 +278,25 @@ cudaError_t step_graph(pic_ctx *c, int with_sort) {
       rec(4);
       launch_field(c);
       rec(5);
-      cudaGraph_t out;
-      e = cudaStreamEndCapture(c->stream, &out);
+      e = capture_leaves(c->stream, deps);
     }
   }
   c->cur[0] = cur_save[0];
   c->cur[1] = cur_save[1];
   c->launches = launches_save;
-  if (e == cudaSuccess) e = cudaGraphInstantiate(&c->gexec[with_sort], g, 0);
+  cudaGetLastError();
+  return e;
+}
+
+// Capture (once) and instantiate the step graph of one context.
+cudaError_t step_graph(pic_ctx *c, int with_sort) {
+  if (c->gexec[with_sort]) return cudaSuccess;
+  cudaGraph_t g;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> deps;
+  e = note(capture_step(c, g, deps, with_sort, true), "step graph capture");
+  if (e == cudaSuccess) e = note(cudaGraphInstantiate(&c->gexec[with_sort], g, 0), "step graph instantiate");
   if (e == cudaSuccess) c->graph[with_sort] = g;
   else cudaGraphDestroy(g);
   cudaGetLastError();
@@ -283,7 +308,181 @@ cudaError_t step_graph(pic_ctx *c, int with_sort) {
 
 using namespace picgb;
 
+struct pic_batch {
+  std::vector<pic_ctx *> m;
+  cudaStream_t stream = nullptr;
+  bool own_stream = false;
+  int dev = 0;
+  int sort_every = 1;
+  int steps_since_sort = 0;
+  int timing = 0;
+  cudaGraph_t graph[2] = {nullptr, nullptr};
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  cudaEvent_t ev[2] = {nullptr, nullptr};
+  double t_ms = 0.0;
+  int64_t t_steps = 0;
+};
+
+namespace picgb {
+namespace {
+
+// The ensemble graph: an event node, then every member's step as an
+// independent branch, then an event node after all of them.
+cudaError_t batch_graph(pic_batch *b, int with_sort) {
+  if (b->gexec[with_sort]) return cudaSuccess;
+  cudaGraph_t g;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> root, leaves;
+  e = cudaStreamBeginCaptureToGraph(b->stream, g, nullptr, nullptr, 0, cudaStreamCaptureModeThreadLocal);
+  if (e == cudaSuccess) {
+    cudaEventRecordWithFlags(b->ev[0], b->stream, cudaEventRecordExternal);
+    e = capture_leaves(b->stream, root);
+  }
+  for (size_t k = 0; e == cudaSuccess && k < b->m.size(); ++k) {
+    std::vector<cudaGraphNode_t> d = root;
+    e = capture_step(b->m[k], g, d, with_sort, false);
+    leaves.insert(leaves.end(), d.begin(), d.end());
+  }
+  if (e == cudaSuccess) {
+    e = cudaStreamBeginCaptureToGraph(b->stream, g, leaves.data(), nullptr, leaves.size(),
+                                      cudaStreamCaptureModeThreadLocal);
+    if (e == cudaSuccess) {
+      cudaEventRecordWithFlags(b->ev[1], b->stream, cudaEventRecordExternal);
+      std::vector<cudaGraphNode_t> tail;
+      e = capture_leaves(b->stream, tail);
+    }
+  }
+  note(e, "ensemble graph capture");
+  if (e == cudaSuccess) e = note(cudaGraphInstantiate(&b->gexec[with_sort], g, 0), "ensemble graph instantiate");
+  if (e == cudaSuccess) b->graph[with_sort] = g;
+  else cudaGraphDestroy(g);
+  cudaGetLastError();
+  return e;
+}
+
+}  // namespace
+}  // namespace picgb
+
 extern "C" {
+
+pic_status pic_batch_init(const pic_config *cfgs, int32_t n, void *stream, pic_batch **out) {
+  if (!out || !cfgs || n < 1) return PIC_EINVAL;
+  *out = nullptr;
+  for (int32_t k = 0; k < n; ++k) {
+    if (cfgs[k].sort_every != cfgs[0].sort_every || cfgs[k].device != cfgs[0].device)
+      return PIC_EINVAL;
+    const pic_status st = validate(&cfgs[k]);
+    if (st != PIC_OK) return st;
+  }
+  pic_batch *b = new (std::nothrow) pic_batch();
+  if (!b) return PIC_ENOMEM;
+  b->dev = cfgs[0].device;
+  b->sort_every = cfgs[0].sort_every;
+  b->timing = cfgs[0].timing;
+  if (cudaSetDevice(b->dev) != cudaSuccess) {
+    delete b;
+    return PIC_ECUDA;
+  }
+  if (stream) {
+    b->stream = (cudaStream_t)stream;
+  } else {
+    cudaStreamCreateWithFlags(&b->stream, cudaStreamNonBlocking);
+    b->own_stream = true;
+  }
+  cudaEventCreate(&b->ev[0]);
+  cudaEventCreate(&b->ev[1]);
+  for (int32_t k = 0; k < n; ++k) {
+    pic_config cfg = cfgs[k];
+    cfg.stream = b->stream;
+    cfg.graphs = 1;
+    cfg.timing = 0;
+    pic_ctx *c = nullptr;
+    const pic_status st = pic_init(&cfg, &c);
+    if (st != PIC_OK) {
+      pic_batch_free(b);
+      return st;
+    }
+    b->m.push_back(c);
+  }
+  *out = b;
+  return PIC_OK;
+}
+
+pic_ctx *pic_batch_member(pic_batch *b, int32_t k) {
+  if (!b || k < 0 || k >= int32_t(b->m.size())) return nullptr;
+  return b->m[k];
+}
+
+pic_status pic_batch_step(pic_batch *b, int32_t nsteps) {
+  if (!b || nsteps < 0) return PIC_EINVAL;
+  if (cudaSetDevice(b->dev) != cudaSuccess) return PIC_ECUDA;
+  bool prepared = false;
+  for (pic_ctx *c : b->m) {
+    if (!c->fields_dirty) continue;
+    const pic_status st = prepare(c);
+    if (st != PIC_OK) return st;
+    prepared = true;
+  }
+  if (prepared) {
+    b->steps_since_sort = 0;
+    for (pic_ctx *c : b->m) c->steps_since_sort = 0;
+  }
+  for (int32_t k = 0; k < nsteps; ++k) {
+    const int sorting = b->steps_since_sort >= b->sort_every ? 1 : 0;
+    if (check(batch_graph(b, sorting)) != PIC_OK) return PIC_ECUDA;
+    if (note(cudaGraphLaunch(b->gexec[sorting], b->stream), "ensemble graph launch") != cudaSuccess)
+      return PIC_ECUDA;
+    for (pic_ctx *c : b->m) {
+      if (sorting) {
+        c->cur[0] ^= 1;
+        c->cur[1] ^= 1;
+        c->steps_since_sort = 0;
+      }
+      c->steps_since_sort += 1;
+      c->step += 1;
+    }
+    b->steps_since_sort = sorting ? 1 : b->steps_since_sort + 1;
+    if (b->timing) {
+      if (note(cudaEventSynchronize(b->ev[1]), "ensemble step") != cudaSuccess) return PIC_ECUDA;
+      float ms = 0.f;
+      cudaEventElapsedTime(&ms, b->ev[0], b->ev[1]);
+      b->t_ms += ms;
+      b->t_steps += 1;
+    }
+  }
+  return PIC_OK;
+}
+
+pic_status pic_batch_timing(pic_batch *b, double *out) {
+  if (!b || !out) return PIC_EINVAL;
+  if (cudaSetDevice(b->dev) != cudaSuccess || cudaStreamSynchronize(b->stream) != cudaSuccess)
+    return PIC_ECUDA;
+  out[0] = double(b->t_steps);
+  out[1] = b->t_ms;
+  b->t_steps = 0;
+  b->t_ms = 0.0;
+  return PIC_OK;
+}
+
+pic_status pic_batch_free(pic_batch *b) {
+  if (!b) return PIC_OK;
+  cudaSetDevice(b->dev);
+  if (b->stream) cudaStreamSynchronize(b->stream);
+  for (int k = 0; k < 2; ++k) {
+    if (b->gexec[k]) cudaGraphExecDestroy(b->gexec[k]);
+    if (b->graph[k]) cudaGraphDestroy(b->graph[k]);
+  }
+  for (pic_ctx *c : b->m) pic_free(c);
+  for (int k = 0; k < 2; ++k)
+    if (b->ev[k]) cudaEventDestroy(b->ev[k]);
+  if (b->own_stream && b->stream) cudaStreamDestroy(b->stream);
+  delete b;
+  return PIC_OK;
+}
+
+
+const char *pic_last_error(void) { return g_last_error.c_str(); }
 
 const char *pic_strerror(pic_status st) {
   switch (st) {
@@ -492,7 +691,9 @@ pic_status pic_step(pic_ctx *c, int32_t nsteps) {
     const bool sorting = c->steps_since_sort >= c->cfg.sort_every;
     if (c->cfg.graphs) {
       if ((st = check(step_graph(c, sorting ? 1 : 0))) != PIC_OK) return st;
-      if (cudaGraphLaunch(c->gexec[sorting ? 1 : 0], c->stream) != cudaSuccess) return PIC_ECUDA;
+      if (note(cudaGraphLaunch(c->gexec[sorting ? 1 : 0], c->stream), "step graph launch") !=
+          cudaSuccess)
+        return PIC_ECUDA;
       if (sorting) {
         c->cur[0] ^= 1;   // mirror the device-side buffer flip of the sort
         c->cur[1] ^= 1;

@@ -73,10 +73,10 @@ __global__ void k_deposit(const double *x, const double *y, long long n, int nx,
     const int i = int(fi), j = int(fj);
     const float fx = fminf(float(X - fi), 0x1.fffffep-1f);
     const float fy = fminf(float(Y - fj), 0x1.fffffep-1f);
-    const float gx = 1.0f - fx, gy = 1.0f - fy;
-    const int w00 = __float2int_rn(gx * gy * q);
-    const int w10 = __float2int_rn(fx * gy * q);
-    const int w01 = __float2int_rn(gx * fy * q);
+    const float gx = __fsub_rn(1.0f, fx), gy = __fsub_rn(1.0f, fy);
+    const int w00 = __float2int_rn(__fmul_rn(__fmul_rn(gx, gy), q));
+    const int w10 = __float2int_rn(__fmul_rn(__fmul_rn(fx, gy), q));
+    const int w01 = __float2int_rn(__fmul_rn(__fmul_rn(gx, fy), q));
     const int w11 = int(1u << 20) - w00 - w10 - w01;
     int i1 = i + 1, j1 = j + 1;
     if (px && i1 == nx) i1 = 0;

@@ -172,6 +172,8 @@ namespace picgb {
 
 // api.cu
 void *dev_alloc(pic_ctx *c, size_t bytes);
+// records "where: CUDA error string" as the calling thread's last error; returns e
+cudaError_t note(cudaError_t e, const char *where);
 
 // particles.cu
 cudaError_t launch_sort(pic_ctx *c);

@@ -216,14 +216,25 @@ __device__ __forceinline__ void deposit_global(const PArgs &a, unsigned long lon
   atomicAdd(&acc[i1 * g.nyn + j1], (unsigned long long)(long long)w11);
 }
 
+// Fixed-point CIC shares.  Every rounding is spelled out (no contraction
+// left to the compiler) so a particle's shares do not depend on the code
+// path it took, and hence not on the particle order.
 __device__ __forceinline__ void cic_weights(float fx, float fy, int &w00, int &w01, int &w10,
                                             int &w11) {
-  const float gx = 1.0f - fx, gy = 1.0f - fy;
+  const float gx = __fsub_rn(1.0f, fx), gy = __fsub_rn(1.0f, fy);
   const float q = float(kQ);
-  w00 = __float2int_rn(gx * gy * q);
-  w10 = __float2int_rn(fx * gy * q);
-  w01 = __float2int_rn(gx * fy * q);
+  w00 = __float2int_rn(__fmul_rn(__fmul_rn(gx, gy), q));
+  w10 = __float2int_rn(__fmul_rn(__fmul_rn(fx, gy), q));
+  w01 = __float2int_rn(__fmul_rn(__fmul_rn(gx, fy), q));
   w11 = int(kQ) - w00 - w10 - w01;
+}
+
+// Bilinear interpolation of one component with explicit roundings.
+__device__ __forceinline__ float bilerp(float fx, float fy, float gx, float gy, float e00,
+                                        float e01, float e10, float e11) {
+  const float lo = __fmaf_rn(fy, e01, __fmul_rn(gy, e00));
+  const float hi = __fmaf_rn(fy, e11, __fmul_rn(gy, e10));
+  return __fmaf_rn(fx, hi, __fmul_rn(gx, lo));
 }
 
 // Window-local coordinate of cell index i (window origin w0, period n when
@@ -279,23 +290,23 @@ __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint3
     e10 = __ldg(&a.E[i1 * g.nyn + j]);
     e11 = __ldg(&a.E[i1 * g.nyn + j1]);
   }
-  const float gx = 1.0f - fx, gy = 1.0f - fy;
-  const float ex = gx * (gy * e00.x + fy * e01.x) + fx * (gy * e10.x + fy * e11.x);
-  const float ey = gx * (gy * e00.y + fy * e01.y) + fx * (gy * e10.y + fy * e11.y);
+  const float gx = __fsub_rn(1.0f, fx), gy = __fsub_rn(1.0f, fy);
+  const float ex = bilerp(fx, fy, gx, gy, e00.x, e01.x, e10.x, e11.x);
+  const float ey = bilerp(fx, fy, gx, gy, e00.y, e01.y, e10.y, e11.y);
   if (MODE == 2) {
     if (a.kick[s]) {
-      vx += a.qdt[s] * ex;
-      vy += a.qdt[s] * ey;
+      vx = __fmaf_rn(a.qdt[s], ex, vx);
+      vy = __fmaf_rn(a.qdt[s], ey, vy);
     }
     return;
   }
-  const float vx1 = vx + a.qdt[s] * ex;
-  const float vy1 = vy + a.qdt[s] * ey;
-  ke += vx * vx1 + vy * vy1;
+  const float vx1 = __fmaf_rn(a.qdt[s], ex, vx);
+  const float vy1 = __fmaf_rn(a.qdt[s], ey, vy);
+  ke = __fadd_rn(ke, __fmaf_rn(vx, vx1, __fmul_rn(vy, vy1)));
   vx = vx1;
   vy = vy1;
-  const float dx = vx1 * a.dt, dy = vy1 * a.dt;
-  float nfx = fx + dx, nfy = fy + dy;
+  const float dx = __fmul_rn(vx1, a.dt), dy = __fmul_rn(vy1, a.dt);
+  float nfx = __fadd_rn(fx, dx), nfy = __fadd_rn(fy, dy);
   const float cxf = floorf(nfx), cyf = floorf(nfy);
   const int cx = int(cxf), cy = int(cyf);
   int oi = 0, oj = 0;     // cell offset of the move
@@ -310,7 +321,8 @@ __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint3
       if (!needx && !needy) break;
       const float facex = float(si > 0 ? oi + 1 : oi);
       const float facey = float(sj > 0 ? oj + 1 : oj);
-      const bool xfirst = fabsf(facex - fx) * ady <= fabsf(facey - fy) * adx;
+      const bool xfirst = __fmul_rn(fabsf(__fsub_rn(facex, fx)), ady) <=
+                          __fmul_rn(fabsf(__fsub_rn(facey, fy)), adx);
       const bool takex = needx && (!needy || xfirst);
       if (takex) oi += si; else oj += sj;
       int gi = i + oi, gj = j + oj;
@@ -357,8 +369,8 @@ __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint3
       }
       return;
     }
-    nfx -= cxf;
-    nfy -= cyf;
+    nfx = __fsub_rn(nfx, cxf);
+    nfy = __fsub_rn(nfy, cyf);
     nfx = fminf(nfx, 0x1.fffffep-1f);
     nfy = fminf(nfy, 0x1.fffffep-1f);
     int ni = i + oi, nj = j + oj;

@@ -40,7 +40,8 @@ constexpr int kSmallLevel = 16384;
 constexpr int kCoarseThreads = 1024;
 constexpr int kMaxOuter = 8;
 constexpr int kCoarsestSweeps = 16;
-constexpr int kDenseCoarsest = 64;   // coarsest levels up to this many unknowns use a dense inverse
+constexpr int kDenseCoarsest = 64;
+constexpr size_t kCoarseSmemMax = 220 * 1024;   // dynamic shared memory granted to k_coarse   // coarsest levels up to this many unknowns use a dense inverse
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
@@ -1038,9 +1039,11 @@ cudaError_t poisson_setup(pic_ctx *c) {
     }
   }
   c->coarse_smem = coarse_smem_bytes(mg_args(c));
-  if (c->coarse_smem > 220 * 1024) return cudaErrorInvalidValue;
+  if (c->coarse_smem > kCoarseSmemMax) return cudaErrorInvalidValue;
+  // the attribute belongs to the kernel, not to this context: always grant the
+  // largest size any context may use, so contexts of different sizes coexist
   cudaError_t e = cudaFuncSetAttribute(k_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                       int(c->coarse_smem));
+                                       int(kCoarseSmemMax));
   if (e != cudaSuccess) return e;
   float **vecs[] = {&c->d_r32, &c->d_z, &c->d_p0, &c->d_p1, &c->d_q, &c->d_e};
   for (float **v : vecs) {
@@ -1125,7 +1128,7 @@ pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   c->last_ms = ms;
   c->last_outer = c->h_ps->outer_iters;
-  if (cudaGetLastError() != cudaSuccess) return PIC_ECUDA;
+  if (note(cudaGetLastError(), "Poisson solve") != cudaSuccess) return PIC_ECUDA;
   return c->h_ps->outer_done ? PIC_OK : PIC_ENOCONV;
 }
 
@@ -1180,7 +1183,7 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   for (int k = 0; k < 4; ++k) {
     cudaError_t e = cudaGraphConditionalHandleCreate(&h[k], top, k == 0 ? 1u : 0u,
                                                      cudaGraphCondAssignDefault);
-    if (e != cudaSuccess) return e;
+    if (e != cudaSuccess) return note(e, "cudaGraphConditionalHandleCreate");
   }
   a.graph = 1;
   a.h_outer = h[0];
@@ -1188,7 +1191,7 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   a.h_inner = h[2];
   a.h_if_inner = h[3];
   cudaError_t e;
-#define CK(x) do { if ((e = (x)) != cudaSuccess) return e; } while (0)
+#define CK(x) do { if ((e = (x)) != cudaSuccess) { note(e, #x); return e; } } while (0)
   CK(cap_begin(s, top, deps));
   if (c->cfg.warm_start == 0) k_phi_reset<<<nb, kThreads, 0, s>>>(a);
   if (c->cfg.warm_start == 2) k_extrapolate<<<nb, kThreads, 0, s>>>(a);
