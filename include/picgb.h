@@ -139,10 +139,12 @@ enum {
   PIC_DIAG_STATE_I = 9,  /* same for ions */
   PIC_DIAG_POISSON = 10, /* [inner iterations, outer iterations, rel residual, ms] of the last solve */
   PIC_DIAG_STATUS = 11,  /* uint32: status word; reading clears it */
-  PIC_DIAG_TIMING = 12   /* [steps, ms particle kernel, ms sort, ms Poisson, ms rho+field,
+  PIC_DIAG_TIMING = 12,  /* [steps, ms particle kernel, ms sort, ms Poisson, ms rho+field,
                             sorts, kernel launches, particle slots processed]: device time
                             from CUDA events on the context stream, accumulated over
                             pic_step calls since the last read; reading resets it */
+  PIC_DIAG_PHI_VACUUM = 13 /* [nxn*nyn]: potential of the empty box (Dirichlet values only),
+                              solved once to 1e-10 */
 };
 
 /* Create a context from cfg.  Builds the conductor mask, Dirichlet nodes and
@@ -220,6 +222,52 @@ pic_status pic_batch_timing(pic_batch *b, double *out);
 
 /* Release the batch and all its members. */
 pic_status pic_batch_free(pic_batch *b);
+
+/* ---- Learned warm start for the Poisson solve of Eq. 5 ------------------
+ * The paper solves Eq. 5 by Gauss-Seidel / Jacobi and names a faster field
+ * solver as future work (Sec. II, Sec. IV).  A U-Net U maps (rho / s, conductor
+ * mask) to (phi - phi_L) / s, s = max |rho|, phi_L the potential of the empty
+ * box; phi_L + s U(...) is the initial guess of the solve, which still runs to
+ * its tolerance.  Four levels (32/64/128/256 channels), two 3x3 conv + ReLU per
+ * level, 2x2 average pool down, 2x2 stride-2 transposed conv up with skip
+ * concatenation, 1x1 head; BF16 activations and weights, FP32 accumulation
+ * and master weights.  All arrays are DEVICE memory, NHWC, FP32:
+ * x [batch][height][width][2], y and targets [batch][height][width].
+ * height and width are multiples of 8 (at least 16).  Parameters travel as
+ * one flat FP32 vector (layer by layer: enc0a..enc3b conv weights [out][3][3][in]
+ * and biases, then per decoder level the transposed conv [2][2][in][out] and
+ * bias and the two convs, then the head weight [32] and bias). */
+typedef struct pic_unet pic_unet;
+
+pic_status pic_unet_create(int32_t batch, int32_t height, int32_t width, void *stream, pic_unet **out);
+int64_t pic_unet_num_params(const pic_unet *u);
+pic_status pic_unet_set_params(pic_unet *u, const float *host_params); /* resets Adam state */
+pic_status pic_unet_get_params(pic_unet *u, float *host_params);
+/* y = U(x) (queued on the net's stream) */
+pic_status pic_unet_forward(pic_unet *u, const float *x, float *y);
+/* MSE loss of U(x) against t and the gradient of every parameter (host copy,
+ * may be NULL); synchronous */
+pic_status pic_unet_gradients(pic_unet *u, const float *x, const float *t, float *host_grad,
+                              double *loss);
+/* one Adam step (lr, beta 0.9 / 0.999) on the MSE loss; *loss (host, may be
+ * NULL) receives the loss once the stream reaches it */
+pic_status pic_unet_train_step(pic_unet *u, const float *x, const float *t, float lr, double *loss);
+pic_status pic_unet_free(pic_unet *u);
+
+/* Input of the warm-start network for the context's current charge density:
+ * x [hpad][nyn][2] (device, FP32) = (rho / s, 1 on Dirichlet nodes), rows
+ * nxn..hpad-1 filled as conductor; *scale = s = max |rho| (host).
+ * hpad >= nxn.  Synchronous. */
+pic_status pic_learned_input(pic_ctx *c, int32_t hpad, float *x, double *scale);
+
+/* Solve Eq. 5 again for the context's current charge density, to the
+ * configured tolerance, from the initial guess `guess`: 0 zero, 1 the current
+ * potential (the previous step's), 2 the empty-box potential phi_L, 3 the
+ * learned guess phi_L + scale * y (y device FP32, row-major over the nodes
+ * with row pitch nyn, e.g. the network's output).  The field is recomputed.
+ * stats (host, may be NULL) = [PCG iterations, refinement passes, relative
+ * residual, device ms from the guess to the solution].  Synchronous. */
+pic_status pic_poisson(pic_ctx *c, int32_t guess, const float *y, double scale, double *stats);
 
 /* Cloud-in-cell deposit that allocates no device memory.  The paper has no
  * counterpart; this is a service for callers that cannot allocate at the

@@ -17,6 +17,11 @@ U is a four-level U-Net, restated plainly (NHWC arrays, float64):
 
 Loss: mean squared error over the pixels.
 
+`forward` and `loss_and_grads` take an optional rounding function q applied
+to every tensor a low-precision implementation would store (layer outputs,
+pooled and upsampled tensors, and the activation gradients passed between
+layers); the default is the identity, i.e. plain FP64.
+
 Pinned by (tests/test_oracle_unet.py): the 3x3 convolution against
 scipy.signal.correlate, the pooling and the transposed convolution by hand,
 and every parameter gradient of the backward pass against central finite
@@ -119,8 +124,13 @@ def init_params(seed=0, cin=2):
     return p
 
 
-def forward(p, x):
+def _ident(a):
+    return a
+
+
+def forward(p, x, q=None):
     """Returns (y [B,H,W], cache)."""
+    q = q or _ident
     cache = {"x": x}
     h = x
     skips = []
@@ -129,54 +139,57 @@ def forward(p, x):
             pre = conv3x3(h, p[f"enc{l}{s}.W"], p[f"enc{l}{s}.b"])
             cache[f"enc{l}{s}.in"] = h
             cache[f"enc{l}{s}.pre"] = pre
-            h = np.maximum(pre, 0.0)
+            h = q(np.maximum(pre, 0.0))
         skips.append(h)
         if l < 3:
-            h = avgpool2(h)
+            h = q(avgpool2(h))
     for l in (2, 1, 0):
         cache[f"up{l}.in"] = h
-        u = upconv2x2(h, p[f"up{l}.W"], p[f"up{l}.b"])
+        u = q(upconv2x2(h, p[f"up{l}.W"], p[f"up{l}.b"]))
         h = np.concatenate([u, skips[l]], axis=3)
         for s in "ab":
             pre = conv3x3(h, p[f"dec{l}{s}.W"], p[f"dec{l}{s}.b"])
             cache[f"dec{l}{s}.in"] = h
             cache[f"dec{l}{s}.pre"] = pre
-            h = np.maximum(pre, 0.0)
+            h = q(np.maximum(pre, 0.0))
     cache["head.in"] = h
     y = np.einsum("bhwc,c->bhw", h, p["head.W"]) + p["head.b"][0]
     return y, cache
 
 
-def loss_and_grads(p, x, t):
+def loss_and_grads(p, x, t, q=None):
     """MSE loss over pixels and the gradient of every parameter (manual
     backward pass through the layers of forward, last layer first)."""
-    y, cache = forward(p, x)
+    q = q or _ident
+    y, cache = forward(p, x, q)
     n = y.size
     loss = float(np.sum((y - t) ** 2) / n)
     dy = 2.0 * (y - t) / n
     g = {}
     g["head.W"] = np.einsum("bhw,bhwc->c", dy, cache["head.in"])
     g["head.b"] = np.array([dy.sum()])
-    dh = dy[..., None] * p["head.W"]
+    dh = q(dy[..., None] * p["head.W"])
     C = CHANNELS
     dskip = [None] * 3
 
-    def conv_block_back(prefix, dh):
+    def conv_block_back(prefix, dh, last=False):
         for s in "ba":
             dpre = dh * (cache[f"{prefix}{s}.pre"] > 0)
             dh, g[f"{prefix}{s}.W"], g[f"{prefix}{s}.b"] = conv3x3_backward(
                 cache[f"{prefix}{s}.in"], p[f"{prefix}{s}.W"], dpre)
+            dh = q(dh)
         return dh
 
     for l in (0, 1, 2):                       # decoder, from the output upwards
         dh = conv_block_back(f"dec{l}", dh)
         du, dskip[l] = dh[..., :C[l]], dh[..., C[l]:]
         dh, g[f"up{l}.W"], g[f"up{l}.b"] = upconv2x2_backward(cache[f"up{l}.in"], p[f"up{l}.W"], du)
+        dh = q(dh)
         # dh: gradient at the input of up{l} = output of decoder level l+1
         # (the bottleneck for l = 2)
     dh = conv_block_back("enc3", dh)          # bottleneck
     for l in (2, 1, 0):                       # encoder, back down
-        dh = avgpool2_backward(dh) + dskip[l]
+        dh = q(avgpool2_backward(dh) + dskip[l])
         dh = conv_block_back(f"enc{l}", dh)
     return loss, g
 

@@ -28,13 +28,14 @@ PIC_ST_NOCONV, PIC_ST_FULL, PIC_ST_CFL, PIC_ST_RANGE, PIC_ST_CAPACITY = 1, 2, 4,
 PIC_LOAD_V_AT_T0 = 1
 (PIC_DIAG_ENERGY, PIC_DIAG_MOMENTUM, PIC_DIAG_COUNTS, PIC_DIAG_SURFACE, PIC_DIAG_HITS,
  PIC_DIAG_RHO, PIC_DIAG_PHI, PIC_DIAG_E, PIC_DIAG_STATE_E, PIC_DIAG_STATE_I,
- PIC_DIAG_POISSON, PIC_DIAG_STATUS, PIC_DIAG_TIMING) = range(13)
+ PIC_DIAG_POISSON, PIC_DIAG_STATUS, PIC_DIAG_TIMING, PIC_DIAG_PHI_VACUUM) = range(14)
 (WALL_XMIN, WALL_XMAX, WALL_YMIN, WALL_YMAX, WALL_COND_PX, WALL_COND_MX,
  WALL_COND_PY, WALL_COND_MY) = range(8)
 
 EXPORTED = ("pic_init", "pic_load", "pic_step", "pic_diag", "pic_free", "pic_strerror",
             "pic_batch_init", "pic_batch_member", "pic_batch_step", "pic_batch_timing",
-            "pic_batch_free", "pic_deposit_static")
+            "pic_batch_free", "pic_deposit_static", "pic_unet_create", "pic_unet_forward",
+            "pic_unet_gradients", "pic_unet_train_step", "pic_unet_free")
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
@@ -104,6 +105,24 @@ def load_library():
     lib.pic_batch_timing.argtypes = [P, ctypes.POINTER(ctypes.c_double)]
     lib.pic_batch_free.argtypes = [P]
     for name in ("pic_batch_init", "pic_batch_step", "pic_batch_timing", "pic_batch_free"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.pic_learned_input.argtypes = [P, ctypes.c_int32, P, ctypes.POINTER(ctypes.c_double)]
+    lib.pic_learned_input.restype = ctypes.c_int
+    lib.pic_poisson.argtypes = [P, ctypes.c_int32, P, ctypes.c_double, ctypes.POINTER(ctypes.c_double)]
+    lib.pic_poisson.restype = ctypes.c_int
+    lib.pic_unet_create.argtypes = [ctypes.c_int32, ctypes.c_int32, ctypes.c_int32, P,
+                                    ctypes.POINTER(ctypes.c_void_p)]
+    lib.pic_unet_num_params.argtypes = [P]
+    lib.pic_unet_num_params.restype = ctypes.c_int64
+    lib.pic_unet_set_params.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+    lib.pic_unet_get_params.argtypes = [P, ctypes.POINTER(ctypes.c_float)]
+    lib.pic_unet_forward.argtypes = [P, P, P]
+    lib.pic_unet_gradients.argtypes = [P, P, P, ctypes.POINTER(ctypes.c_float),
+                                       ctypes.POINTER(ctypes.c_double)]
+    lib.pic_unet_train_step.argtypes = [P, P, P, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
+    lib.pic_unet_free.argtypes = [P]
+    for name in ("pic_unet_create", "pic_unet_set_params", "pic_unet_get_params",
+                 "pic_unet_forward", "pic_unet_gradients", "pic_unet_train_step", "pic_unet_free"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("pic_init", "pic_load", "pic_step", "pic_diag", "pic_free"):
         getattr(lib, name).restype = ctypes.c_int
@@ -341,6 +360,28 @@ class Sim:
                 "launches", "slots")
         return dict(zip(keys, v.tolist()))
 
+    def phi_vacuum(self):
+        return self.grid(PIC_DIAG_PHI_VACUUM)
+
+    def learned_input(self, hpad):
+        """(x, s): the warm-start network's input for the current rho as a
+        torch CUDA tensor [1, hpad, nyn, 2], and the scale s = max |rho|."""
+        import torch
+        x = torch.empty((1, hpad, self.nyn, 2), dtype=torch.float32, device="cuda")
+        s = ctypes.c_double(0.0)
+        self._check(load_library().pic_learned_input(self.ctx, int(hpad), x.data_ptr(), ctypes.byref(s)),
+                    "pic_learned_input")
+        return x, s.value
+
+    def poisson(self, guess, y=None, scale=0.0):
+        """Re-solve for the current rho from guess 0 zero, 1 previous, 2 vacuum,
+        3 learned (y: network output tensor); returns [iterations, passes,
+        relative residual, ms]."""
+        out = (ctypes.c_double * 4)()
+        self._check(load_library().pic_poisson(self.ctx, int(guess), y.data_ptr() if y is not None else None,
+                                               float(scale), out), "pic_poisson")
+        return list(out)
+
     def status(self):
         out = np.zeros(1, np.uint32)
         st, _ = pic_diag(self.ctx, PIC_DIAG_STATUS, out)
@@ -400,6 +441,77 @@ class Batch:
             for m in self.members:
                 m.ctx = None
             load_library().pic_batch_free(self.h)
+            self.h = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class Unet:
+    """The learned warm start's U-Net on the GPU (training and inference by
+    the library's kernels).  Inputs and outputs are torch CUDA tensors:
+    x [B, H, W, 2] float32, targets and outputs [B, H, W] float32."""
+
+    def __init__(self, batch, height, width, stream=None):
+        import torch
+        lib = load_library()
+        self.torch = torch
+        self.stream = stream or torch.cuda.Stream()
+        h = ctypes.c_void_p()
+        st = lib.pic_unet_create(int(batch), int(height), int(width), self.stream.cuda_stream,
+                                 ctypes.byref(h))
+        if st != PIC_OK:
+            raise PicError(st, "pic_unet_create")
+        self.h = h
+        self.shape = (batch, height, width)
+        self.nparam = int(lib.pic_unet_num_params(h))
+
+    def set_params(self, flat):
+        flat = np.ascontiguousarray(flat, dtype=np.float32)
+        assert flat.size == self.nparam
+        st = load_library().pic_unet_set_params(self.h, flat.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        if st != PIC_OK:
+            raise PicError(st, "pic_unet_set_params")
+
+    def get_params(self):
+        out = np.empty(self.nparam, np.float32)
+        st = load_library().pic_unet_get_params(self.h, out.ctypes.data_as(ctypes.POINTER(ctypes.c_float)))
+        if st != PIC_OK:
+            raise PicError(st, "pic_unet_get_params")
+        return out
+
+    def forward(self, x):
+        y = self.torch.empty(self.shape, dtype=self.torch.float32, device=x.device)
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+        st = load_library().pic_unet_forward(self.h, x.data_ptr(), y.data_ptr())
+        if st != PIC_OK:
+            raise PicError(st, "pic_unet_forward")
+        self.torch.cuda.current_stream().wait_stream(self.stream)
+        return y
+
+    def gradients(self, x, t):
+        g = np.empty(self.nparam, np.float32)
+        loss = ctypes.c_double(0.0)
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+        st = load_library().pic_unet_gradients(self.h, x.data_ptr(), t.data_ptr(),
+                                               g.ctypes.data_as(ctypes.POINTER(ctypes.c_float)),
+                                               ctypes.byref(loss))
+        if st != PIC_OK:
+            raise PicError(st, "pic_unet_gradients")
+        return loss.value, g
+
+    def train_step(self, x, t, lr):
+        self.stream.wait_stream(self.torch.cuda.current_stream())
+        st = load_library().pic_unet_train_step(self.h, x.data_ptr(), t.data_ptr(), float(lr), None)
+        if st != PIC_OK:
+            raise PicError(st, "pic_unet_train_step")
+
+    def close(self):
+        if getattr(self, "h", None):
+            load_library().pic_unet_free(self.h)
             self.h = None
 
     def __del__(self):

@@ -484,6 +484,22 @@ pic_status pic_batch_free(pic_batch *b) {
 
 const char *pic_last_error(void) { return g_last_error.c_str(); }
 
+pic_status pic_learned_input(pic_ctx *c, int32_t hpad, float *x, double *scale) {
+  if (!c || !x || !scale) return PIC_EINVAL;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
+  return learned_input(c, hpad, x, scale);
+}
+
+pic_status pic_poisson(pic_ctx *c, int32_t guess, const float *y, double scale, double *stats) {
+  if (!c || guess < 0 || guess > 3) return PIC_EINVAL;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
+  if (c->fields_dirty) {
+    const pic_status st = pic_step(c, 0);
+    if (st != PIC_OK) return st;
+  }
+  return poisson_with_guess(c, guess, y, scale, stats);
+}
+
 const char *pic_strerror(pic_status st) {
   switch (st) {
     case PIC_OK: return "ok";
@@ -881,6 +897,14 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
       o[2] = ps.rel;
       o[3] = c->last_ms;
       count = 4;
+      break;
+    }
+    case PIC_DIAG_PHI_VACUUM: {
+      if (!need(int64_t(nn) * 8)) return PIC_EINVAL;
+      const pic_status st = ensure_vacuum_potential(c);
+      if (st != PIC_OK) return st;
+      cudaMemcpy(out, c->d_phiL, nn * 8, cudaMemcpyDeviceToHost);
+      count = int64_t(nn);
       break;
     }
     case PIC_DIAG_TIMING: {

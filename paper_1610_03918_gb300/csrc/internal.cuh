@@ -106,6 +106,7 @@ struct pic_ctx {
   double *d_b;                 // right-hand side on free nodes
   double *d_phi;               // FP64 master potential (Dirichlet values included)
   double *d_phi_prev;          // potential of the previous step (extrapolated warm start)
+  double *d_phiL;              // potential of the empty box (learned warm start), lazily
   float2 *d_E;
   double *d_fe;                // [2]: field energy of E just computed, of E used by last step
 
@@ -193,6 +194,9 @@ cudaError_t launch_rho(pic_ctx *c, int advance_step);
 pic_status poisson_solve(pic_ctx *c, bool zero_guess);
 cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNode_t> &deps);
 int64_t poisson_kernel_count(pic_ctx *c, const PoissonState &ps);
+pic_status ensure_vacuum_potential(pic_ctx *c);
+pic_status learned_input(pic_ctx *c, int hpad, float *x, double *scale);
+pic_status poisson_with_guess(pic_ctx *c, int guess, const float *y, double scale, double *stats);
 cudaError_t launch_field(pic_ctx *c);
 
 }  // namespace picgb

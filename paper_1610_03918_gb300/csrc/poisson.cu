@@ -28,6 +28,7 @@
 #include <algorithm>
 #include <array>
 #include <cmath>
+#include <cstring>
 #include <map>
 
 #include "internal.cuh"
@@ -1237,6 +1238,121 @@ int64_t poisson_kernel_count(pic_ctx *c, const PoissonState &ps) {
   // + per iteration (pq, update) + per non-final iteration (V-cycle, rz)
   return 1 + (O + 1) + O * (vc + 2) + 2 * I + std::max<int64_t>(I - O, 0) * (vc + 1) +
          (c->cfg.warm_start != 1 ? 1 : 0);
+}
+
+
+// ---- initial guesses for the learned warm start ----
+namespace {
+
+__global__ void k_absmax(const double *rho, int nn, unsigned int *out) {
+  float m = 0.f;
+  GRID_STRIDE(n, nn) m = fmaxf(m, float(fabs(rho[n])));
+  for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
+  if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));   // m >= 0: bit order = value order
+}
+
+// x[i][j] = (rho / s, 1 for a Dirichlet node); rows beyond the grid count as conductor
+__global__ void k_learned_input(const double *rho, const uint8_t *flags, int nxn, int nyn, int hpad,
+                                const unsigned int *smax, float *x) {
+  const float s = fmaxf(__uint_as_float(*smax), 1e-30f);
+  GRID_STRIDE(n, hpad * nyn) {
+    const int i = n / nyn;
+    float r = 0.f, m = 1.f;
+    if (i < nxn) {
+      r = float(rho[n] / double(s));
+      m = (flags[n] & kFree) ? 0.f : 1.f;
+    }
+    x[2 * n] = r;
+    x[2 * n + 1] = m;
+  }
+}
+
+__global__ void k_guess_learned(double *phi, const double *phiL, const uint8_t *flags, const float *y,
+                                double scale, int nn) {
+  GRID_STRIDE(n, nn) {
+    if (flags[n] & kFree) phi[n] = phiL[n] + scale * double(y[n]);
+  }
+}
+
+__global__ void k_b_lift(double *b, const double *lift, const uint8_t *flags, int nn) {
+  GRID_STRIDE(n, nn) b[n] = (flags[n] & kFree) ? lift[n] : 0.0;
+}
+
+}  // namespace
+
+// The potential of the empty box (Dirichlet values only), solved once to
+// 1e-10 and kept.
+pic_status ensure_vacuum_potential(pic_ctx *c) {
+  if (c->d_phiL) return PIC_OK;
+  const size_t nn = size_t(c->g.nxn) * c->g.nyn;
+  c->d_phiL = (double *)dev_alloc(c, nn * 8);
+  double *save_phi = (double *)dev_alloc(c, nn * 8);
+  double *save_b = (double *)dev_alloc(c, nn * 8);
+  if (!c->d_phiL || !save_phi || !save_b) return PIC_ENOMEM;
+  cudaMemcpyAsync(save_phi, c->d_phi, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(save_b, c->d_b, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
+  PoissonState ps_save;
+  cudaMemcpyAsync(&ps_save, c->d_ps, sizeof(ps_save), cudaMemcpyDeviceToHost, c->stream);
+  cudaStreamSynchronize(c->stream);
+  k_b_lift<<<c->red.nblocks, kThreads, 0, c->stream>>>(c->d_b, c->d_lift, c->d_nodeflags, int(nn));
+  cudaMemsetAsync(&c->d_ps->bmean, 0, sizeof(double), c->stream);
+  const double rtol = c->cfg.poisson_rtol;
+  c->cfg.poisson_rtol = 1e-10;
+  const pic_status st = poisson_solve(c, true);
+  c->cfg.poisson_rtol = rtol;
+  cudaMemcpyAsync(c->d_phiL, c->d_phi, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(c->d_phi, save_phi, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(c->d_b, save_b, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(c->d_ps, &ps_save, sizeof(ps_save), cudaMemcpyHostToDevice, c->stream);
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
+  return st;
+}
+
+pic_status learned_input(pic_ctx *c, int hpad, float *x, double *scale) {
+  const int nn = c->g.nxn * c->g.nyn;
+  if (hpad < c->g.nxn) return PIC_EINVAL;
+  unsigned int *smax = reinterpret_cast<unsigned int *>(c->red.ticket) + 8;   // spare word
+  cudaMemsetAsync(smax, 0, 4, c->stream);
+  k_absmax<<<c->red.nblocks, kThreads, 0, c->stream>>>(c->d_rho, nn, smax);
+  k_learned_input<<<c->red.nblocks, kThreads, 0, c->stream>>>(c->d_rho, c->d_nodeflags, c->g.nxn,
+                                                                c->g.nyn, hpad, smax, x);
+  unsigned int bits = 0;
+  if (cudaMemcpyAsync(&bits, smax, 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+      cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return PIC_ECUDA;
+  float f;
+  std::memcpy(&f, &bits, 4);
+  *scale = std::max(double(f), 1e-30);
+  return PIC_OK;
+}
+
+pic_status poisson_with_guess(pic_ctx *c, int guess, const float *y, double scale, double *stats) {
+  const int nn = c->g.nxn * c->g.nyn;
+  if (guess >= 2) {
+    const pic_status st = ensure_vacuum_potential(c);
+    if (st != PIC_OK) return st;
+  }
+  cudaEventRecord(c->tev[0], c->stream);
+  if (guess == 2)
+    cudaMemcpyAsync(c->d_phi, c->d_phiL, size_t(nn) * 8, cudaMemcpyDeviceToDevice, c->stream);
+  if (guess == 3) {
+    if (!y) return PIC_EINVAL;
+    k_guess_learned<<<c->red.nblocks, kThreads, 0, c->stream>>>(c->d_phi, c->d_phiL, c->d_nodeflags,
+                                                                  y, scale, nn);
+  }
+  const pic_status st = poisson_solve(c, guess == 0);
+  cudaEventRecord(c->tev[1], c->stream);
+  if (launch_field(c) != cudaSuccess) return PIC_ECUDA;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
+  float ms = 0.f;
+  cudaEventElapsedTime(&ms, c->tev[0], c->tev[1]);
+  if (stats) {
+    stats[0] = c->h_ps->total_iters;
+    stats[1] = c->h_ps->outer_iters;
+    stats[2] = c->h_ps->rel;
+    stats[3] = ms;
+  }
+  return st;
 }
 
 }  // namespace picgb

@@ -1,0 +1,922 @@
+// U-Net of the learned Poisson warm start: BF16 activations and weights,
+// FP32 accumulation, training and inference on the GPU.
+//
+// Architecture (four levels, channels 32/64/128/256): per level two 3x3
+// convolutions with ReLU, 2x2 average pooling down, 2x2 stride-2 transposed
+// convolution up, skip concatenation (upsampled channels first), 1x1 head.
+// Tensors are NHWC; a concatenation buffer holds [upsampled | skip] so no
+// copy is made.  The input has 2 channels (rho / s, conductor mask) padded to
+// 16 so that every convolution's K is a multiple of 16.
+//
+// 3x3 convolutions (forward and data gradient) are implicit GEMMs on the
+// tensor cores (mma.sync m16n8k16 BF16 -> FP32, ldmatrix fragments, cp.async
+// double-buffered tiles): M = pixels of one row segment, N = output
+// channels, K = 9 taps x input channels.  The data gradient is the same
+// kernel with the weights flipped in space and transposed in channels.  The
+// weight gradient is a tensor-core GEMM over pixels (M = out channels,
+// N = in channels per tap) accumulated with FP32 atomics.  The transposed
+// convolutions, pooling, head, loss and Adam are small CUDA-core kernels.
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <cstring>
+#include <new>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace picgb {
+namespace unet {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kC[4] = {32, 64, 128, 256};
+constexpr int kC0 = 32;      // channels of the top level (the head's input)
+constexpr int kCin0 = 16;    // padded input channels
+
+// ---------------------------------------------------------------- PTX helpers
+__device__ __forceinline__ unsigned smem_u32(const void *p) {
+  return static_cast<unsigned>(__cvta_generic_to_shared(p));
+}
+
+__device__ __forceinline__ void cp_async16(void *smem, const void *gmem, bool valid) {
+  const int n = valid ? 16 : 0;   // 0 bytes read: the 16 bytes are zero-filled
+  asm volatile("cp.async.cg.shared.global [%0], [%1], 16, %2;\n" ::"r"(smem_u32(smem)),
+               "l"(gmem), "r"(n));
+}
+__device__ __forceinline__ void cp_async_commit() { asm volatile("cp.async.commit_group;\n" ::); }
+__device__ __forceinline__ void cp_async_wait_all() { asm volatile("cp.async.wait_group 0;\n" ::); }
+
+__device__ __forceinline__ void ldsm_x4(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3,
+                                        const void *p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void ldsm_x4_t(unsigned &r0, unsigned &r1, unsigned &r2, unsigned &r3,
+                                          const void *p) {
+  asm volatile("ldmatrix.sync.aligned.m8n8.x4.trans.shared.b16 {%0,%1,%2,%3}, [%4];\n"
+               : "=r"(r0), "=r"(r1), "=r"(r2), "=r"(r3)
+               : "r"(smem_u32(p)));
+}
+__device__ __forceinline__ void mma16816(float (&d)[4], unsigned a0, unsigned a1, unsigned a2,
+                                         unsigned a3, unsigned b0, unsigned b1) {
+  asm volatile(
+      "mma.sync.aligned.m16n8k16.row.col.f32.bf16.bf16.f32 {%0,%1,%2,%3}, {%4,%5,%6,%7}, "
+      "{%8,%9}, {%0,%1,%2,%3};\n"
+      : "+f"(d[0]), "+f"(d[1]), "+f"(d[2]), "+f"(d[3])
+      : "r"(a0), "r"(a1), "r"(a2), "r"(a3), "r"(b0), "r"(b1));
+}
+
+// ---------------------------------------------------------------- 3x3 conv (implicit GEMM)
+struct ConvArgs {
+  const bf16 *in;
+  int in_cs, in_off, cin;     // channel stride / offset / count of the input
+  const bf16 *w;              // [cout][9][cin]
+  const float *bias;          // [cout] or null
+  bf16 *out;
+  int out_cs, out_off, cout;
+  int B, H, W;
+  int relu;
+};
+
+constexpr int kTM = 128;      // pixels per CTA (one row segment)
+constexpr int kConvThreads = 256;
+
+template <int TN, int KC>
+__global__ void __launch_bounds__(kConvThreads) k_conv3x3(ConvArgs a) {
+  constexpr int LDA = KC + 8;            // padded rows: conflict-free ldmatrix
+  constexpr int WARPS_N = TN / 32;
+  constexpr int WARPS_M = 8 / WARPS_N;
+  constexpr int WTM = kTM / WARPS_M;     // pixels per warp
+  constexpr int MF = WTM / 16;
+  __shared__ __align__(16) bf16 As[2][kTM * LDA];
+  __shared__ __align__(16) bf16 Bs[2][TN * LDA];
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int wm = warp / WARPS_N, wn = warp % WARPS_N;
+  const int nwt = (a.W + kTM - 1) / kTM;
+  const int wt = blockIdx.x % nwt;
+  const int bh = blockIdx.x / nwt;       // b * H + h
+  const int h = bh % a.H;
+  const int w0 = wt * kTM;
+  const int n0 = blockIdx.y * TN;
+  const int kchunks = a.cin / KC;
+  const int nk = 9 * kchunks;
+
+  auto load = [&](int ks, int st) {
+    const int tap = ks / kchunks, c0 = (ks - tap * kchunks) * KC;
+    const int di = tap / 3 - 1, dj = tap % 3 - 1;
+    const int hh = h + di;
+    constexpr int ACH = kTM * KC / 8;    // 16-byte chunks of the A tile
+    for (int q = tid; q < ACH; q += kConvThreads) {
+      const int m = q / (KC / 8), cc = (q % (KC / 8)) * 8;
+      const int ww = w0 + m + dj;
+      const bool ok = hh >= 0 && hh < a.H && ww >= 0 && ww < a.W;
+      const bf16 *src = ok ? a.in + (size_t(bh + di) * a.W + ww) * a.in_cs + a.in_off + c0 + cc : a.in;
+      cp_async16(&As[st][m * LDA + cc], src, ok);
+    }
+    constexpr int BCH = TN * KC / 8;
+    for (int q = tid; q < BCH; q += kConvThreads) {
+      const int n = q / (KC / 8), cc = (q % (KC / 8)) * 8;
+      const bool ok = n0 + n < a.cout;
+      const bf16 *src = ok ? a.w + (size_t(n0 + n) * 9 + tap) * a.cin + c0 + cc : a.w;
+      cp_async16(&Bs[st][n * LDA + cc], src, ok);
+    }
+    cp_async_commit();
+  };
+
+  float acc[MF][4][4];
+#pragma unroll
+  for (int i = 0; i < MF; ++i)
+#pragma unroll
+    for (int j = 0; j < 4; ++j)
+#pragma unroll
+      for (int k = 0; k < 4; ++k) acc[i][j][k] = 0.f;
+
+  load(0, 0);
+  for (int ks = 0; ks < nk; ++ks) {
+    const int st = ks & 1;
+    cp_async_wait_all();
+    __syncthreads();
+    if (ks + 1 < nk) load(ks + 1, st ^ 1);
+#pragma unroll
+    for (int kk = 0; kk < KC; kk += 16) {
+      unsigned af[MF][4];
+#pragma unroll
+      for (int mf = 0; mf < MF; ++mf) {
+        const int row = wm * WTM + mf * 16 + (lane & 15);
+        const int col = kk + (lane >> 4) * 8;
+        ldsm_x4(af[mf][0], af[mf][1], af[mf][2], af[mf][3], &As[st][row * LDA + col]);
+      }
+#pragma unroll
+      for (int np = 0; np < 2; ++np) {     // two n16 blocks per warp (32 channels)
+        unsigned b0, b1, b2, b3;
+        const int mi = lane >> 3;
+        const int n = wn * 32 + np * 16 + (lane & 7) + ((mi >> 1) << 3);
+        const int k = kk + ((mi & 1) << 3);
+        ldsm_x4(b0, b1, b2, b3, &Bs[st][n * LDA + k]);
+#pragma unroll
+        for (int mf = 0; mf < MF; ++mf) {
+          mma16816(acc[mf][np * 2 + 0], af[mf][0], af[mf][1], af[mf][2], af[mf][3], b0, b1);
+          mma16816(acc[mf][np * 2 + 1], af[mf][0], af[mf][1], af[mf][2], af[mf][3], b2, b3);
+        }
+      }
+    }
+  }
+  // epilogue: bias, ReLU, BF16 store (two channels per store)
+#pragma unroll
+  for (int mf = 0; mf < MF; ++mf) {
+#pragma unroll
+    for (int nf = 0; nf < 4; ++nf) {
+#pragma unroll
+      for (int half = 0; half < 2; ++half) {
+        const int m = wm * WTM + mf * 16 + (lane >> 2) + half * 8;
+        const int n = n0 + wn * 32 + nf * 8 + (lane & 3) * 2;
+        if (w0 + m >= a.W || n >= a.cout) continue;
+        float v0 = acc[mf][nf][half * 2 + 0], v1 = acc[mf][nf][half * 2 + 1];
+        if (a.bias) {
+          v0 += a.bias[n];
+          v1 += a.bias[n + 1];
+        }
+        if (a.relu) {
+          v0 = fmaxf(v0, 0.f);
+          v1 = fmaxf(v1, 0.f);
+        }
+        bf16 *dst = a.out + (size_t(bh) * a.W + w0 + m) * a.out_cs + a.out_off + n;
+        *reinterpret_cast<__nv_bfloat162 *>(dst) = __floats2bfloat162_rn(v0, v1);
+      }
+    }
+  }
+}
+
+// ---------------------------------------------------------------- 3x3 weight gradient
+// dW[co][tap][ci] += sum_p dpre[p][co] * in[p + off(tap)][ci] over a group of
+// rows; 32 x 32 tile of (co, ci) per CTA, 4 warps of 16 x 16.
+struct WgradArgs {
+  const bf16 *dpre;           // [B][H][W][cout] (contiguous)
+  const bf16 *in;
+  int in_cs, in_off, cin, cout;
+  float *dw;                  // [cout][9][cin] FP32, accumulated
+  int B, H, W;
+  int rows_per_cta;
+};
+
+constexpr int kKP = 64;       // pixels per k-step
+
+__global__ void __launch_bounds__(128) k_wgrad3x3(WgradArgs a) {
+  constexpr int LD = 32 + 8;
+  __shared__ __align__(16) bf16 Ds[kKP * LD];   // [pixel][co]
+  __shared__ __align__(16) bf16 Xs[kKP * LD];   // [pixel][ci]
+  const int tid = threadIdx.x, lane = tid & 31, warp = tid >> 5;
+  const int tap = blockIdx.z;
+  const int di = tap / 3 - 1, dj = tap % 3 - 1;
+  const int ncb = (a.cin + 31) / 32;
+  const int co0 = (blockIdx.y / ncb) * 32, ci0 = (blockIdx.y % ncb) * 32;
+  const int wco = (warp >> 1) * 16, wci = (warp & 1) * 16;
+  float acc[2][4] = {{0.f, 0.f, 0.f, 0.f}, {0.f, 0.f, 0.f, 0.f}};
+  const int rows = a.B * a.H;
+  const int r0 = blockIdx.x * a.rows_per_cta;
+  const int r1 = min(rows, r0 + a.rows_per_cta);
+  for (int r = r0; r < r1; ++r) {
+    const int h = r % a.H;
+    for (int w0 = 0; w0 < a.W; w0 += kKP) {
+      __syncthreads();
+      // 64 pixels x 32 channels of each operand = 256 chunks of 16 bytes each
+      for (int q = tid; q < kKP * 4; q += 128) {
+        const int p = q >> 2, cc = (q & 3) * 8;
+        const int w = w0 + p;
+        const bool okd = w < a.W && co0 + cc < a.cout;
+        cp_async16(&Ds[p * LD + cc], okd ? a.dpre + (size_t(r) * a.W + w) * a.cout + co0 + cc : a.dpre, okd);
+        const int hh = h + di, ww = w + dj;
+        const bool okx = w < a.W && hh >= 0 && hh < a.H && ww >= 0 && ww < a.W && ci0 + cc < a.cin;
+        cp_async16(&Xs[p * LD + cc],
+                   okx ? a.in + (size_t(r + di) * a.W + ww) * a.in_cs + a.in_off + ci0 + cc : a.in, okx);
+      }
+      cp_async_commit();
+      cp_async_wait_all();
+      __syncthreads();
+#pragma unroll
+      for (int kk = 0; kk < kKP; kk += 16) {
+        const int mi = lane >> 3, rr = lane & 7;
+        // A = dpre^T (rows co, k = pixel) from [pixel][co] storage
+        unsigned a0, a1, a2, a3;
+        {
+          const int koff = (mi >> 1) << 3, moff = (mi & 1) << 3;
+          ldsm_x4_t(a0, a1, a2, a3, &Ds[(kk + koff + rr) * LD + wco + moff]);
+        }
+        // B = in (k = pixel, n = ci) from [pixel][ci] storage
+        unsigned b0, b1, b2, b3;
+        {
+          const int koff = (mi & 1) << 3, noff = (mi >> 1) << 3;
+          ldsm_x4_t(b0, b1, b2, b3, &Xs[(kk + koff + rr) * LD + wci + noff]);
+        }
+        mma16816(acc[0], a0, a1, a2, a3, b0, b1);
+        mma16816(acc[1], a0, a1, a2, a3, b2, b3);
+      }
+    }
+  }
+#pragma unroll
+  for (int nf = 0; nf < 2; ++nf)
+#pragma unroll
+    for (int half = 0; half < 2; ++half)
+#pragma unroll
+      for (int e = 0; e < 2; ++e) {
+        const int co = co0 + wco + (lane >> 2) + half * 8;
+        const int ci = ci0 + wci + nf * 8 + (lane & 3) * 2 + e;
+        if (co < a.cout && ci < a.cin)
+          atomicAdd(&a.dw[(size_t(co) * 9 + tap) * a.cin + ci], acc[nf][half * 2 + e]);
+      }
+}
+
+// ---------------------------------------------------------------- elementwise kernels
+#define GSTRIDE(i, n) \
+  for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
+
+// input: x [B][H][W][2] FP32 -> [B][H][W][16] BF16, channels 2..15 zero
+__global__ void k_input(const float *x, bf16 *out, long long npix) {
+  GSTRIDE(p, npix) {
+    bf16 *o = out + p * kCin0;
+    o[0] = __float2bfloat16(x[2 * p]);
+    o[1] = __float2bfloat16(x[2 * p + 1]);
+    for (int c = 2; c < kCin0; ++c) o[c] = __float2bfloat16(0.f);
+  }
+}
+
+// dpre[p][c] = g[p][c] * (y[p][c] > 0) (contiguous output)
+__global__ void k_relu_mask(const bf16 *g, int g_cs, int g_off, const bf16 *y, int y_cs, int y_off,
+                            bf16 *dpre, int C, long long npix) {
+  GSTRIDE(i, npix * C) {
+    const long long p = i / C;
+    const int c = int(i - p * C);
+    const float yv = __bfloat162float(y[p * y_cs + y_off + c]);
+    dpre[i] = yv > 0.f ? g[p * g_cs + g_off + c] : __float2bfloat16(0.f);
+  }
+}
+
+// db[c] += sum_p dpre[p][c]
+__global__ void k_bias_grad(const bf16 *dpre, int C, long long npix, float *db) {
+  const int c = blockIdx.y;
+  float s = 0.f;
+  GSTRIDE(p, npix) s += __bfloat162float(dpre[p * C + c]);
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  __shared__ float sh[32];
+  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    float t = 0.f;
+    for (int k = 0; k < int(blockDim.x >> 5); ++k) t += sh[k];
+    atomicAdd(&db[c], t);
+  }
+}
+
+// W'[ci][tap][co] = W[co][8 - tap][ci]
+__global__ void k_wflip(const bf16 *w, bf16 *wt, int cout, int cin) {
+  GSTRIDE(i, (long long)cout * 9 * cin) {
+    const int ci = int(i % cin);
+    const int tap = int((i / cin) % 9);
+    const int co = int(i / (9LL * cin));
+    wt[(size_t(ci) * 9 + (8 - tap)) * cout + co] = w[i];
+  }
+}
+
+// 2x2 average pool: out (H/2 x W/2) from in (H x W), C channels
+__global__ void k_pool(const bf16 *in, int in_cs, int in_off, bf16 *out, int C, int B, int H, int W) {
+  const int Ho = H / 2, Wo = W / 2;
+  GSTRIDE(i, (long long)B * Ho * Wo * C) {
+    const int c = int(i % C);
+    const long long p = i / C;
+    const int wo = int(p % Wo), ho = int((p / Wo) % Ho), b = int(p / ((long long)Wo * Ho));
+    float s = 0.f;
+    for (int a = 0; a < 2; ++a)
+      for (int d = 0; d < 2; ++d)
+        s += __bfloat162float(in[((size_t(b) * H + 2 * ho + a) * W + 2 * wo + d) * in_cs + in_off + c]);
+    out[i] = __float2bfloat16(0.25f * s);
+  }
+}
+
+// gradient of the pool, added into g (H x W, channel stride/offset)
+__global__ void k_pool_back_add(const bf16 *gp, bf16 *g, int g_cs, int g_off, int C, int B, int H, int W) {
+  const int Ho = H / 2, Wo = W / 2;
+  GSTRIDE(i, (long long)B * H * W * C) {
+    const int c = int(i % C);
+    const long long p = i / C;
+    const int w = int(p % W), h = int((p / W) % H), b = int(p / ((long long)W * H));
+    const float v = 0.25f * __bfloat162float(gp[((size_t(b) * Ho + h / 2) * Wo + w / 2) * C + c]);
+    bf16 *d = g + p * g_cs + g_off + c;
+    *d = __float2bfloat16(__bfloat162float(*d) + v);
+  }
+}
+
+// transposed 2x2 stride-2 convolution: out (2h x 2w) from in (h x w); W [2][2][ci][co] FP32
+__global__ void k_up_fwd(const bf16 *in, int cin, const float *w, const float *bias, bf16 *out,
+                         int out_cs, int out_off, int cout, int B, int h, int wd) {
+  const int H = 2 * h, W = 2 * wd;
+  GSTRIDE(i, (long long)B * H * W * cout) {
+    const int co = int(i % cout);
+    const long long p = i / cout;
+    const int x = int(p % W), y = int((p / W) % H), b = int(p / ((long long)W * H));
+    const int a = y & 1, c = x & 1;
+    const bf16 *src = in + ((size_t(b) * h + (y >> 1)) * wd + (x >> 1)) * cin;
+    const float *wk = w + (size_t(a * 2 + c) * cin) * cout + co;
+    float s = bias[co];
+    for (int ci = 0; ci < cin; ++ci) s = fmaf(__bfloat162float(src[ci]), wk[size_t(ci) * cout], s);
+    out[p * out_cs + out_off + co] = __float2bfloat16(s);
+  }
+}
+
+// data gradient of the transposed convolution: gin (h x w, cin) from gout (2h x 2w, cout)
+__global__ void k_up_back_data(const bf16 *gout, int gout_cs, int gout_off, int cout, const float *w,
+                               bf16 *gin, int cin, int B, int h, int wd) {
+  const int W = 2 * wd;
+  GSTRIDE(i, (long long)B * h * wd * cin) {
+    const int ci = int(i % cin);
+    const long long p = i / cin;
+    const int x = int(p % wd), y = int((p / wd) % h), b = int(p / ((long long)wd * h));
+    float s = 0.f;
+    for (int a = 0; a < 2; ++a)
+      for (int c = 0; c < 2; ++c) {
+        const bf16 *g = gout + ((size_t(b) * 2 * h + 2 * y + a) * W + 2 * x + c) * gout_cs + gout_off;
+        const float *wk = w + (size_t(a * 2 + c) * cin + ci) * cout;
+        for (int co = 0; co < cout; ++co) s = fmaf(__bfloat162float(g[co]), wk[co], s);
+      }
+    gin[i] = __float2bfloat16(s);
+  }
+}
+
+// weight gradient of the transposed convolution: dw[a][c][ci][co] += sum over input pixels
+// of in[p][ci] * gout[child (a, c) of p][co]; one CTA per (a c, 32 ci, 32 co) and row group
+__global__ void __launch_bounds__(256) k_up_back_w(const bf16 *in, int cin, const bf16 *gout,
+                                                   int gout_cs, int gout_off, int cout, float *dw,
+                                                   float *db, int B, int h, int wd, int rows_per_cta) {
+  __shared__ float xs[32][33], gs[32][33];
+  const int ac = blockIdx.z, a = ac >> 1, c = ac & 1;
+  const int ncb = (cout + 31) / 32;
+  const int ci0 = (blockIdx.y / ncb) * 32, co0 = (blockIdx.y % ncb) * 32;
+  const int tx = threadIdx.x & 31, ty = threadIdx.x >> 5;   // 32 x 8 threads
+  float acc[4] = {0.f, 0.f, 0.f, 0.f};
+  float bacc = 0.f;
+  const int rows = B * h;
+  const int r0 = blockIdx.x * rows_per_cta, r1 = min(rows, r0 + rows_per_cta);
+  const int W = 2 * wd;
+  for (int r = r0; r < r1; ++r) {
+    const int b = r / h, y = r % h;
+    for (int x0 = 0; x0 < wd; x0 += 32) {
+      __syncthreads();
+      for (int k = ty; k < 32; k += 8) {
+        const int x = x0 + k;
+        float xv = 0.f, gv = 0.f;
+        if (x < wd) {
+          if (ci0 + tx < cin) xv = __bfloat162float(in[((size_t(b) * h + y) * wd + x) * cin + ci0 + tx]);
+          if (co0 + tx < cout)
+            gv = __bfloat162float(gout[((size_t(b) * 2 * h + 2 * y + a) * W + 2 * x + c) * gout_cs + gout_off + co0 + tx]);
+        }
+        xs[k][tx] = xv;
+        gs[k][tx] = gv;
+      }
+      __syncthreads();
+      for (int k = 0; k < 32; ++k) {
+        const float g = gs[k][tx];
+#pragma unroll
+        for (int q = 0; q < 4; ++q) acc[q] = fmaf(xs[k][ty * 4 + q], g, acc[q]);
+        if (ty == 0 && ci0 == 0) bacc += g;
+      }
+    }
+  }
+  for (int q = 0; q < 4; ++q) {
+    const int ci = ci0 + ty * 4 + q, co = co0 + tx;
+    if (ci < cin && co < cout) atomicAdd(&dw[(size_t(ac) * cin + ci) * cout + co], acc[q]);
+  }
+  if (ty == 0 && ci0 == 0 && co0 + tx < cout) atomicAdd(&db[co0 + tx], bacc);
+}
+
+// head: y[p] = sum_c h[p][c] w[c] + b
+__global__ void k_head_fwd(const bf16 *hin, const float *w, const float *b, float *y, long long npix) {
+  GSTRIDE(p, npix) {
+    float s = b[0];
+    for (int c = 0; c < kC0; ++c) s = fmaf(__bfloat162float(hin[p * kC0 + c]), w[c], s);
+    y[p] = s;
+  }
+}
+
+// MSE: dy = 2 (y - t) / n, loss partial sums in FP64
+__global__ void k_mse(const float *y, const float *t, float *dy, long long n, double *loss) {
+  double s = 0.0;
+  GSTRIDE(p, n) {
+    const float d = y[p] - t[p];
+    dy[p] = 2.f * d / float(n);
+    s += double(d) * double(d);
+  }
+  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(loss, s / double(n));
+}
+
+// head backward: gh[p][c] = dy[p] w[c]; dw[c] += sum_p dy h; db += sum dy
+__global__ void k_head_back(const float *dy, const bf16 *hin, const float *w, bf16 *gh, float *dw,
+                            float *db, long long npix) {
+  float acc[kC0];
+  for (int c = 0; c < kC0; ++c) acc[c] = 0.f;
+  float bs = 0.f;
+  GSTRIDE(p, npix) {
+    const float d = dy[p];
+    bs += d;
+    for (int c = 0; c < kC0; ++c) {
+      gh[p * kC0 + c] = __float2bfloat16(d * w[c]);
+      acc[c] = fmaf(d, __bfloat162float(hin[p * kC0 + c]), acc[c]);
+    }
+  }
+  for (int c = 0; c < kC0; ++c) {
+    float v = acc[c];
+    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
+    if ((threadIdx.x & 31) == 0) atomicAdd(&dw[c], v);
+  }
+  for (int o = 16; o > 0; o >>= 1) bs += __shfl_down_sync(0xffffffffu, bs, o);
+  if ((threadIdx.x & 31) == 0) atomicAdd(db, bs);
+}
+
+// Adam on the FP32 master parameters
+__global__ void k_adam(float *p, const float *g, float *m, float *v, long long n, float lr,
+                       float b1, float b2, float eps, float c1, float c2) {
+  GSTRIDE(i, n) {
+    const float gi = g[i];
+    const float mi = b1 * m[i] + (1.f - b1) * gi;
+    const float vi = b2 * v[i] + (1.f - b2) * gi * gi;
+    m[i] = mi;
+    v[i] = vi;
+    p[i] -= lr * (mi / c1) / (sqrtf(vi / c2) + eps);
+  }
+}
+
+// BF16 compute copy of a conv weight from the FP32 master [co][9][ci_m],
+// expanded to ci_c >= ci_m input channels with zeros
+__global__ void k_w_to_bf16(const float *m, bf16 *w, int cout, int ci_m, int ci_c) {
+  GSTRIDE(i, (long long)cout * 9 * ci_c) {
+    const int ci = int(i % ci_c);
+    const long long ct = i / ci_c;
+    w[i] = __float2bfloat16(ci < ci_m ? m[ct * ci_m + ci] : 0.f);
+  }
+}
+
+// gradient of an expanded conv weight folded back to the master layout
+__global__ void k_w_fold(const float *gc, float *gm, int cout, int ci_m, int ci_c) {
+  GSTRIDE(i, (long long)cout * 9 * ci_m) {
+    const int ci = int(i % ci_m);
+    const long long ct = i / ci_m;
+    gm[i] += gc[ct * ci_c + ci];
+  }
+}
+
+inline int gridn(long long n, int t = 256) {
+  long long b = (n + t - 1) / t;
+  return int(b < 1 ? 1 : (b > 65535 * 8 ? 65535 * 8 : b));
+}
+
+}  // namespace unet
+}  // namespace picgb
+
+// ============================================================================
+// The network
+// ============================================================================
+struct pic_unet {
+  int B, H, W;
+  cudaStream_t stream = nullptr;
+  std::vector<void *> allocs;
+  // parameters: FP32 master (flat, in the order of the layer list), grads, Adam moments
+  float *P = nullptr, *G = nullptr, *M = nullptr, *V = nullptr;
+  long long nparam = 0;
+  long long step = 0;
+  double *d_loss = nullptr;
+  float *y = nullptr, *dy = nullptr;     // [B][H][W]
+  float *g0tmp = nullptr;                // expanded gradient of the first conv
+  struct Conv {
+    int cin_m, cin_c, cout;              // master / compute input channels, outputs
+    long long w_off, b_off;              // offsets into P
+    picgb::unet::bf16 *w, *wt;           // BF16 weights and their flipped transpose
+  } conv[14];                            // enc0a..enc3b (8), dec2a..dec0b (6)
+  struct Up {
+    int cin, cout;
+    long long w_off, b_off;
+  } up[3];                               // up2, up1, up0 (index = level)
+  long long head_w, head_b;
+  // activations (BF16 NHWC) and gradients
+  picgb::unet::bf16 *x16, *a[4], *cat[3], *da[3], *dout[3], *p[4], *b3;
+  picgb::unet::bf16 *gx[4], *gcat[3], *gda[3], *gdout[3], *gp[4], *gb3, *dpre[4];
+};
+
+namespace picgb {
+namespace unet {
+namespace {
+
+void *ualloc(pic_unet *u, size_t bytes) {
+  void *p = nullptr;
+  if (cudaMalloc(&p, (bytes + 255) & ~size_t(255)) != cudaSuccess) return nullptr;
+  u->allocs.push_back(p);
+  return p;
+}
+
+// conv indices
+enum { E0A, E0B, E1A, E1B, E2A, E2B, E3A, E3B, D2A, D2B, D1A, D1B, D0A, D0B };
+
+int pix(const pic_unet *u, int l) { return u->B * (u->H >> l) * (u->W >> l); }
+
+void conv_fwd(pic_unet *u, int ci, const bf16 *in, int in_cs, int in_off, bf16 *out, int out_cs,
+              int out_off, int l, bool relu) {
+  const pic_unet::Conv &c = u->conv[ci];
+  ConvArgs a;
+  a.in = in;
+  a.in_cs = in_cs;
+  a.in_off = in_off;
+  a.cin = c.cin_c;
+  a.w = c.w;
+  a.bias = u->P + c.b_off;
+  a.out = out;
+  a.out_cs = out_cs;
+  a.out_off = out_off;
+  a.cout = c.cout;
+  a.B = u->B;
+  a.H = u->H >> l;
+  a.W = u->W >> l;
+  a.relu = relu ? 1 : 0;
+  const int nwt = (a.W + kTM - 1) / kTM;
+  if (c.cout == 32) {
+    dim3 g(a.B * a.H * nwt, 1);
+    if (c.cin_c == 16) k_conv3x3<32, 16><<<g, kConvThreads, 0, u->stream>>>(a);
+    else k_conv3x3<32, 32><<<g, kConvThreads, 0, u->stream>>>(a);
+  } else {
+    dim3 g(a.B * a.H * nwt, c.cout / 64);
+    k_conv3x3<64, 32><<<g, kConvThreads, 0, u->stream>>>(a);
+  }
+}
+
+// data gradient: gin (cin channels) = conv(dpre, flipped weights)
+void conv_back_data(pic_unet *u, int ci, const bf16 *dpre, bf16 *gin, int gin_cs, int gin_off, int l) {
+  const pic_unet::Conv &c = u->conv[ci];
+  k_wflip<<<gridn((long long)c.cout * 9 * c.cin_c), 256, 0, u->stream>>>(c.w, c.wt, c.cout, c.cin_c);
+  ConvArgs a;
+  a.in = dpre;
+  a.in_cs = c.cout;
+  a.in_off = 0;
+  a.cin = c.cout;
+  a.w = c.wt;
+  a.bias = nullptr;
+  a.out = gin;
+  a.out_cs = gin_cs;
+  a.out_off = gin_off;
+  a.cout = c.cin_c;
+  a.B = u->B;
+  a.H = u->H >> l;
+  a.W = u->W >> l;
+  a.relu = 0;
+  const int nwt = (a.W + kTM - 1) / kTM;
+  if (a.cout == 32) {
+    k_conv3x3<32, 32><<<dim3(a.B * a.H * nwt, 1), kConvThreads, 0, u->stream>>>(a);
+  } else {
+    k_conv3x3<64, 32><<<dim3(a.B * a.H * nwt, a.cout / 64), kConvThreads, 0, u->stream>>>(a);
+  }
+}
+
+void conv_back_weights(pic_unet *u, int ci, const bf16 *dpre, const bf16 *in, int in_cs, int in_off, int l) {
+  const pic_unet::Conv &c = u->conv[ci];
+  const int H = u->H >> l, W = u->W >> l;
+  float *dw = (c.cin_c == c.cin_m) ? u->G + c.w_off : u->g0tmp;
+  if (c.cin_c != c.cin_m) cudaMemsetAsync(u->g0tmp, 0, size_t(c.cout) * 9 * c.cin_c * 4, u->stream);
+  WgradArgs a;
+  a.dpre = dpre;
+  a.in = in;
+  a.in_cs = in_cs;
+  a.in_off = in_off;
+  a.cin = c.cin_c;
+  a.cout = c.cout;
+  a.dw = dw;
+  a.B = u->B;
+  a.H = H;
+  a.W = W;
+  const int rows = u->B * H;
+  // enough CTAs to fill the GPU: rows split so that every (co, ci, tap) tile has work
+  const int tiles = ((c.cout + 31) / 32) * ((c.cin_c + 31) / 32) * 9;
+  int groups = std::max(1, std::min(rows, 4096 / tiles));
+  a.rows_per_cta = (rows + groups - 1) / groups;
+  groups = (rows + a.rows_per_cta - 1) / a.rows_per_cta;
+  k_wgrad3x3<<<dim3(groups, ((c.cout + 31) / 32) * ((c.cin_c + 31) / 32), 9), 128, 0, u->stream>>>(a);
+  if (c.cin_c != c.cin_m)
+    k_w_fold<<<gridn((long long)c.cout * 9 * c.cin_m), 256, 0, u->stream>>>(u->g0tmp, u->G + c.w_off,
+                                                                          c.cout, c.cin_m, c.cin_c);
+  k_bias_grad<<<dim3(std::min(256, gridn(pix(u, l))), c.cout), 256, 0, u->stream>>>(
+      dpre, c.cout, pix(u, l), u->G + c.b_off);
+}
+
+// backward through relu(conv(in)) given the gradient g at its output;
+// writes the gradient at its input into gin (unless gin is null)
+void conv_block_back(pic_unet *u, int ci, const bf16 *g, int g_cs, int g_off, const bf16 *y, int y_cs,
+                     int y_off, const bf16 *in, int in_cs, int in_off, bf16 *gin, int gin_cs,
+                     int gin_off, int l) {
+  const pic_unet::Conv &c = u->conv[ci];
+  const long long np = pix(u, l);
+  bf16 *dpre = u->dpre[l];
+  k_relu_mask<<<gridn(np * c.cout), 256, 0, u->stream>>>(g, g_cs, g_off, y, y_cs, y_off, dpre, c.cout, np);
+  conv_back_weights(u, ci, dpre, in, in_cs, in_off, l);
+  if (gin) conv_back_data(u, ci, dpre, gin, gin_cs, gin_off, l);
+}
+
+void weights_to_bf16(pic_unet *u) {
+  for (auto &c : u->conv)
+    k_w_to_bf16<<<gridn((long long)c.cout * 9 * c.cin_c), 256, 0, u->stream>>>(u->P + c.w_off, c.w, c.cout,
+                                                                             c.cin_m, c.cin_c);
+}
+
+void forward(pic_unet *u, const float *x) {
+  const int C0 = kC[0], C1 = kC[1], C2 = kC[2], C3 = kC[3];
+  k_input<<<gridn(pix(u, 0)), 256, 0, u->stream>>>(x, u->x16, pix(u, 0));
+  // encoder; each level's output is written into the skip half of its concat buffer
+  conv_fwd(u, E0A, u->x16, kCin0, 0, u->a[0], C0, 0, 0, true);
+  conv_fwd(u, E0B, u->a[0], C0, 0, u->cat[0], 2 * C0, C0, 0, true);
+  k_pool<<<gridn((long long)pix(u, 1) * C0), 256, 0, u->stream>>>(u->cat[0], 2 * C0, C0, u->p[1], C0, u->B, u->H, u->W);
+  conv_fwd(u, E1A, u->p[1], C0, 0, u->a[1], C1, 0, 1, true);
+  conv_fwd(u, E1B, u->a[1], C1, 0, u->cat[1], 2 * C1, C1, 1, true);
+  k_pool<<<gridn((long long)pix(u, 2) * C1), 256, 0, u->stream>>>(u->cat[1], 2 * C1, C1, u->p[2], C1, u->B, u->H >> 1, u->W >> 1);
+  conv_fwd(u, E2A, u->p[2], C1, 0, u->a[2], C2, 0, 2, true);
+  conv_fwd(u, E2B, u->a[2], C2, 0, u->cat[2], 2 * C2, C2, 2, true);
+  k_pool<<<gridn((long long)pix(u, 3) * C2), 256, 0, u->stream>>>(u->cat[2], 2 * C2, C2, u->p[3], C2, u->B, u->H >> 2, u->W >> 2);
+  conv_fwd(u, E3A, u->p[3], C2, 0, u->a[3], C3, 0, 3, true);
+  conv_fwd(u, E3B, u->a[3], C3, 0, u->b3, C3, 0, 3, true);
+  // decoder
+  const bf16 *h = u->b3;
+  int hc = C3;
+  for (int l = 2; l >= 0; --l) {
+    const pic_unet::Up &up = u->up[l];
+    const int hl = u->H >> (l + 1), wl = u->W >> (l + 1);
+    k_up_fwd<<<gridn((long long)pix(u, l) * up.cout), 256, 0, u->stream>>>(
+        h, hc, u->P + up.w_off, u->P + up.b_off, u->cat[l], 2 * kC[l], 0, up.cout, u->B, hl, wl);
+    const int ca = (l == 2) ? D2A : (l == 1) ? D1A : D0A;
+    conv_fwd(u, ca, u->cat[l], 2 * kC[l], 0, u->da[l], kC[l], 0, l, true);
+    conv_fwd(u, ca + 1, u->da[l], kC[l], 0, u->dout[l], kC[l], 0, l, true);
+    h = u->dout[l];
+    hc = kC[l];
+  }
+  k_head_fwd<<<gridn(pix(u, 0)), 256, 0, u->stream>>>(u->dout[0], u->P + u->head_w, u->P + u->head_b, u->y, pix(u, 0));
+}
+
+void backward(pic_unet *u) {
+  const int C3 = kC[3];
+  cudaMemsetAsync(u->G, 0, size_t(u->nparam) * 4, u->stream);
+  k_head_back<<<std::min(1024, gridn(pix(u, 0))), 256, 0, u->stream>>>(
+      u->dy, u->dout[0], u->P + u->head_w, u->gdout[0], u->G + u->head_w, u->G + u->head_b, pix(u, 0));
+  // decoder, from the output up
+  bf16 *g = u->gdout[0];
+  for (int l = 0; l <= 2; ++l) {
+    const int C = kC[l];
+    const int ca = (l == 2) ? D2A : (l == 1) ? D1A : D0A;
+    conv_block_back(u, ca + 1, g, C, 0, u->dout[l], C, 0, u->da[l], C, 0, u->gda[l], C, 0, l);
+    conv_block_back(u, ca, u->gda[l], C, 0, u->da[l], C, 0, u->cat[l], 2 * C, 0, u->gcat[l], 2 * C, 0, l);
+    // transposed conv: gradient at its input (the output of level l+1) from gcat[:, 0:C]
+    const pic_unet::Up &up = u->up[l];
+    const int hl = u->H >> (l + 1), wl = u->W >> (l + 1);
+    const bf16 *hin = (l == 2) ? u->b3 : u->dout[l + 1];
+    bf16 *gin = (l == 2) ? u->gb3 : u->gdout[l + 1];
+    k_up_back_data<<<gridn((long long)pix(u, l + 1) * up.cin), 256, 0, u->stream>>>(
+        u->gcat[l], 2 * C, 0, up.cout, u->P + up.w_off, gin, up.cin, u->B, hl, wl);
+    const int rows = u->B * hl;
+    const int tiles = ((up.cin + 31) / 32) * ((up.cout + 31) / 32) * 4;
+    int groups = std::max(1, std::min(rows, 2048 / tiles));
+    const int rpc = (rows + groups - 1) / groups;
+    groups = (rows + rpc - 1) / rpc;
+    k_up_back_w<<<dim3(groups, ((up.cin + 31) / 32) * ((up.cout + 31) / 32), 4), 256, 0, u->stream>>>(
+        hin, up.cin, u->gcat[l], 2 * C, 0, up.cout, u->G + up.w_off, u->G + up.b_off, u->B, hl, wl, rpc);
+    g = gin;
+  }
+  // bottleneck
+  conv_block_back(u, E3B, u->gb3, C3, 0, u->b3, C3, 0, u->a[3], C3, 0, u->gx[3], C3, 0, 3);
+  conv_block_back(u, E3A, u->gx[3], C3, 0, u->a[3], C3, 0, u->p[3], kC[2], 0, u->gp[3], kC[2], 0, 3);
+  // encoder, back down: the pooled gradient joins the skip gradient in gcat[l][C:2C]
+  for (int l = 2; l >= 0; --l) {
+    const int C = kC[l];
+    k_pool_back_add<<<gridn((long long)pix(u, l) * C), 256, 0, u->stream>>>(
+        u->gp[l + 1], u->gcat[l], 2 * C, C, C, u->B, u->H >> l, u->W >> l);
+    const int ea = 2 * l;   // E0A, E1A, E2A
+    conv_block_back(u, ea + 1, u->gcat[l], 2 * C, C, u->cat[l], 2 * C, C, u->a[l], C, 0, u->gx[l], C, 0, l);
+    if (l > 0)
+      conv_block_back(u, ea, u->gx[l], C, 0, u->a[l], C, 0, u->p[l], kC[l - 1], 0, u->gp[l], kC[l - 1], 0, l);
+    else
+      conv_block_back(u, ea, u->gx[0], C, 0, u->a[0], C, 0, u->x16, kCin0, 0, nullptr, 0, 0, 0);
+  }
+}
+
+}  // namespace
+}  // namespace unet
+}  // namespace picgb
+
+using namespace picgb::unet;
+
+extern "C" {
+
+pic_status pic_unet_create(int32_t batch, int32_t height, int32_t width, void *stream, pic_unet **out) {
+  if (!out || batch < 1 || height < 16 || width < 16 || (height % 8) || (width % 8)) return PIC_EINVAL;
+  pic_unet *u = new (std::nothrow) pic_unet();
+  if (!u) return PIC_ENOMEM;
+  u->B = batch;
+  u->H = height;
+  u->W = width;
+  u->stream = static_cast<cudaStream_t>(stream);
+  // parameter layout (the order of the layer list)
+  long long off = 0;
+  auto add_conv = [&](int idx, int cin_m, int cin_c, int cout) {
+    pic_unet::Conv &c = u->conv[idx];
+    c.cin_m = cin_m;
+    c.cin_c = cin_c;
+    c.cout = cout;
+    c.w_off = off;
+    off += (long long)cout * 9 * cin_m;
+    c.b_off = off;
+    off += cout;
+  };
+  int prev = 2;
+  for (int l = 0; l < 4; ++l) {
+    add_conv(2 * l, prev, l == 0 ? kCin0 : prev, kC[l]);
+    add_conv(2 * l + 1, kC[l], kC[l], kC[l]);
+    prev = kC[l];
+  }
+  for (int l = 2; l >= 0; --l) {
+    pic_unet::Up &up = u->up[l];
+    up.cin = kC[l + 1];
+    up.cout = kC[l];
+    up.w_off = off;
+    off += 4LL * up.cin * up.cout;
+    up.b_off = off;
+    off += up.cout;
+    const int ca = (l == 2) ? D2A : (l == 1) ? D1A : D0A;
+    add_conv(ca, 2 * kC[l], 2 * kC[l], kC[l]);
+    add_conv(ca + 1, kC[l], kC[l], kC[l]);
+  }
+  u->head_w = off;
+  off += kC[0];
+  u->head_b = off;
+  off += 1;
+  u->nparam = off;
+  bool ok = true;
+  auto A = [&](size_t bytes) {
+    void *p = ualloc(u, bytes);
+    if (!p) ok = false;
+    return p;
+  };
+  u->P = (float *)A(off * 4);
+  u->G = (float *)A(off * 4);
+  u->M = (float *)A(off * 4);
+  u->V = (float *)A(off * 4);
+  u->d_loss = (double *)A(8);
+  for (auto &c : u->conv) {
+    c.w = (bf16 *)A(size_t(c.cout) * 9 * c.cin_c * 2);
+    c.wt = (bf16 *)A(size_t(c.cout) * 9 * c.cin_c * 2);
+  }
+  u->g0tmp = (float *)A(size_t(kC[0]) * 9 * kCin0 * 4);
+  const size_t np0 = size_t(batch) * height * width;
+  u->y = (float *)A(np0 * 4);
+  u->dy = (float *)A(np0 * 4);
+  u->x16 = (bf16 *)A(np0 * kCin0 * 2);
+  for (int l = 0; l < 4; ++l) {
+    const size_t np = np0 >> (2 * l);
+    const int C = kC[l];
+    u->a[l] = (bf16 *)A(np * C * 2);
+    u->gx[l] = (bf16 *)A(np * C * 2);
+    u->dpre[l] = (bf16 *)A(np * 2 * C * 2);
+    if (l > 0) {
+      u->p[l] = (bf16 *)A(np * kC[l - 1] * 2);
+      u->gp[l] = (bf16 *)A(np * kC[l - 1] * 2);
+    }
+    if (l < 3) {
+      u->cat[l] = (bf16 *)A(np * 2 * C * 2);
+      u->gcat[l] = (bf16 *)A(np * 2 * C * 2);
+      u->da[l] = (bf16 *)A(np * C * 2);
+      u->gda[l] = (bf16 *)A(np * C * 2);
+      u->dout[l] = (bf16 *)A(np * C * 2);
+      u->gdout[l] = (bf16 *)A(np * C * 2);
+    } else {
+      u->b3 = (bf16 *)A(np * C * 2);
+      u->gb3 = (bf16 *)A(np * C * 2);
+    }
+  }
+  if (!ok) {
+    pic_unet_free(u);
+    return PIC_ENOMEM;
+  }
+  cudaMemsetAsync(u->P, 0, size_t(off) * 4, u->stream);
+  cudaMemsetAsync(u->M, 0, size_t(off) * 4, u->stream);
+  cudaMemsetAsync(u->V, 0, size_t(off) * 4, u->stream);
+  if (cudaStreamSynchronize(u->stream) != cudaSuccess) {
+    pic_unet_free(u);
+    return PIC_ECUDA;
+  }
+  *out = u;
+  return PIC_OK;
+}
+
+int64_t pic_unet_num_params(const pic_unet *u) { return u ? u->nparam : 0; }
+
+pic_status pic_unet_set_params(pic_unet *u, const float *host) {
+  if (!u || !host) return PIC_EINVAL;
+  if (cudaMemcpyAsync(u->P, host, size_t(u->nparam) * 4, cudaMemcpyHostToDevice, u->stream) != cudaSuccess)
+    return PIC_ECUDA;
+  cudaMemsetAsync(u->M, 0, size_t(u->nparam) * 4, u->stream);
+  cudaMemsetAsync(u->V, 0, size_t(u->nparam) * 4, u->stream);
+  u->step = 0;
+  weights_to_bf16(u);
+  return cudaStreamSynchronize(u->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+pic_status pic_unet_get_params(pic_unet *u, float *host) {
+  if (!u || !host) return PIC_EINVAL;
+  if (cudaMemcpyAsync(host, u->P, size_t(u->nparam) * 4, cudaMemcpyDeviceToHost, u->stream) != cudaSuccess)
+    return PIC_ECUDA;
+  return cudaStreamSynchronize(u->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+pic_status pic_unet_forward(pic_unet *u, const float *x, float *y) {
+  if (!u || !x || !y) return PIC_EINVAL;
+  forward(u, x);
+  if (cudaMemcpyAsync(y, u->y, size_t(u->B) * u->H * u->W * 4, cudaMemcpyDeviceToDevice, u->stream) != cudaSuccess)
+    return PIC_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+pic_status pic_unet_gradients(pic_unet *u, const float *x, const float *t, float *host_grad, double *loss) {
+  if (!u || !x || !t) return PIC_EINVAL;
+  forward(u, x);
+  cudaMemsetAsync(u->d_loss, 0, 8, u->stream);
+  const long long n = (long long)u->B * u->H * u->W;
+  k_mse<<<std::min(1024, gridn(n)), 256, 0, u->stream>>>(u->y, t, u->dy, n, u->d_loss);
+  backward(u);
+  if (host_grad &&
+      cudaMemcpyAsync(host_grad, u->G, size_t(u->nparam) * 4, cudaMemcpyDeviceToHost, u->stream) != cudaSuccess)
+    return PIC_ECUDA;
+  if (loss && cudaMemcpyAsync(loss, u->d_loss, 8, cudaMemcpyDeviceToHost, u->stream) != cudaSuccess)
+    return PIC_ECUDA;
+  if (cudaStreamSynchronize(u->stream) != cudaSuccess) return PIC_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+pic_status pic_unet_train_step(pic_unet *u, const float *x, const float *t, float lr, double *loss) {
+  if (!u || !x || !t) return PIC_EINVAL;
+  forward(u, x);
+  cudaMemsetAsync(u->d_loss, 0, 8, u->stream);
+  const long long n = (long long)u->B * u->H * u->W;
+  k_mse<<<std::min(1024, gridn(n)), 256, 0, u->stream>>>(u->y, t, u->dy, n, u->d_loss);
+  backward(u);
+  u->step += 1;
+  const float b1 = 0.9f, b2 = 0.999f;
+  const float c1 = 1.f - std::pow(b1, float(u->step)), c2 = 1.f - std::pow(b2, float(u->step));
+  k_adam<<<gridn(u->nparam), 256, 0, u->stream>>>(u->P, u->G, u->M, u->V, u->nparam, lr, b1, b2, 1e-8f, c1, c2);
+  weights_to_bf16(u);
+  if (loss && cudaMemcpyAsync(loss, u->d_loss, 8, cudaMemcpyDeviceToHost, u->stream) != cudaSuccess)
+    return PIC_ECUDA;
+  return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+pic_status pic_unet_free(pic_unet *u) {
+  if (!u) return PIC_OK;
+  if (u->stream) cudaStreamSynchronize(u->stream);
+  for (void *p : u->allocs) cudaFree(p);
+  delete u;
+  return PIC_OK;
+}
+
+}  // extern "C"
