@@ -274,14 +274,106 @@ def run_ensemble(args):
     return 0
 
 
+def run_warmstart(args):
+    """Poisson time to a 1e-6 relative residual on the trench geometry, from
+    the learned guess (network input, inference and solve) against the zero,
+    empty-box and previous-step starts, on held-out trench widths.  The
+    network is trained here on pairs dumped from runs at other widths."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1610_03918_gb300 as pg
+    from paper_1610_03918_gb300 import warmstart as ws
+    from oracle import unet as ounet   # only for the seeded He initialisation
+    t0 = time.perf_counter()
+
+    def trench(width, seed):
+        return synth.trench_512x1024(trench_width=width, trench_y0=(512 - width) // 2, seed=seed)
+
+    pairs = []
+    for k, width in enumerate(int(v) for v in args.train_widths.split(",")):
+        w = trench(width, 200 + k)
+        sim = pg.Sim(w, capacity=int(synth.plasma_cells(w).sum()) * w.ppc)
+        for s in (0, 1):
+            sim.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
+        sim.step(50)
+        pairs += ws.dump_pairs(sim, steps=2 * args.dumps, every=2)
+        sim.close()
+    t_data = time.perf_counter() - t0
+    net = pg.Unet(1, ws.padded_rows(1025), 512)
+    net.set_params(ounet.flat(ounet.init_params(0)).astype(np.float32))
+    t1 = time.perf_counter()
+    ws.train(net, pairs, epochs=args.epochs, lr=1e-3)
+    t_train = time.perf_counter() - t1
+    del pairs
+    lw = ws.LearnedWarmStart(net)
+    res = {"zero": [], "vacuum": [], "previous": [], "learned": []}
+    its = {k: [] for k in res}
+
+    def timed(fn):
+        e0 = torch.cuda.Event(enable_timing=True)
+        e1 = torch.cuda.Event(enable_timing=True)
+        torch.cuda.synchronize()
+        e0.record()
+        st = fn()
+        e1.record()
+        torch.cuda.synchronize()
+        return st, e0.elapsed_time(e1)
+
+    for k, width in enumerate(int(v) for v in args.eval_widths.split(",")):
+        w = trench(width, 900 + k)
+        sim = pg.Sim(w, capacity=int(synth.plasma_cells(w).sum()) * w.ppc)
+        for s in (0, 1):
+            sim.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
+        sim.step(args.warmup * 10)
+        for rep in range(args.steps):
+            prev = sim.phi()          # the previous step's potential
+            sim.step(1)
+            for name, guess in (("zero", 0), ("vacuum", 2)):
+                st, ms = timed(lambda: sim.poisson(guess))
+                res[name].append(ms)
+                its[name].append(st[0])
+            sim.set_phi(prev)
+            st, ms = timed(lambda: sim.poisson(1))
+            res["previous"].append(ms)
+            its["previous"].append(st[0])
+            st, ms = lw.solve(sim)
+            res["learned"].append(ms)
+            its["learned"].append(st[0])
+        sim.close()
+    out = {k: float(np.median(v)) for k, v in res.items()}
+    line = {
+        "metric": "Poisson ms to 1e-6 residual (learned warm start)",
+        "value": out["learned"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 net / f32+f64 solver",
+        "data": "synthetic", "vs_baseline": None,
+        "config": {"workload": "trench_512x1024 geometry, held-out widths " + args.eval_widths,
+                   "train_widths": args.train_widths, "train_pairs": args.dumps * len(args.train_widths.split(",")),
+                   "epochs": args.epochs, "data_s": t_data, "train_s": t_train},
+        "median_ms": out,
+        "median_iterations": {k: float(np.median(v)) for k, v in its.items()},
+        "speedup_vs_zero": out["zero"] / out["learned"],
+        "speedup_vs_vacuum": out["vacuum"] / out["learned"],
+    }
+    print(json.dumps(line), flush=True)
+    net.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=100)
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="trench", choices=["trench", "ensemble"],
-                    help="trench: the 512x1024 trench run; ensemble: the 48-run width sweep")
+    ap.add_argument("--workload", default="trench", choices=["trench", "ensemble", "warmstart"],
+                    help="trench: the 512x1024 trench run; ensemble: the 48-run width sweep; "
+                         "warmstart: Poisson time to 1e-6 with the learned initial guess")
+    ap.add_argument("--train-widths", default="2,6,10,14,20")
+    ap.add_argument("--eval-widths", default="3,11,19")
+    ap.add_argument("--dumps", type=int, default=200, help="training pairs per training run")
+    ap.add_argument("--epochs", type=int, default=3)
     ap.add_argument("--members", type=int, default=48, help="ensemble members")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
@@ -297,6 +389,8 @@ def main():
     args.warmup = max(args.warmup, 3)
     if args.workload == "ensemble":
         return run_ensemble(args)
+    if args.workload == "warmstart":
+        return run_warmstart(args)
 
     dist, rank, ws = _dist()
     import torch

@@ -160,7 +160,9 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out);
  * species is back-kicked by dt/2 in the field of the full loaded state
  * before the next step (leapfrog start).
  * species == -1 loads a fixed external charge density rho_ext (Sec. III-D)
- * from x[nxn*nyn]; the other pointers are ignored.
+ * from x[nxn*nyn]; species == -2 sets the potential (the initial guess of the
+ * next solve; Dirichlet nodes keep their values) from x[nxn*nyn]; the other
+ * pointers are then ignored.
  * Particles outside the domain or in a conductor are dropped and counted
  * in the PIC_ST_RANGE bit; n > capacity returns PIC_EOVERFLOW. */
 pic_status pic_load(pic_ctx *ctx, int32_t species, int64_t n, const double *x,

@@ -360,6 +360,9 @@ class Sim:
                 "launches", "slots")
         return dict(zip(keys, v.tolist()))
 
+    def set_phi(self, phi):
+        return self._check(pic_load(self.ctx, -2, np.asarray(phi, np.float64).ravel()), "pic_load(phi)")
+
     def phi_vacuum(self):
         return self.grid(PIC_DIAG_PHI_VACUUM)
 

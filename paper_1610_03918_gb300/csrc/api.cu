@@ -672,6 +672,16 @@ pic_status pic_load(pic_ctx *c, int32_t species, int64_t n, const double *x, con
     c->fields_dirty = 1;
     return check(cudaStreamSynchronize(c->stream));
   }
+  if (species == -2) {
+    // the potential (initial guess of the next solve); Dirichlet nodes keep their values
+    if (!x || n != int64_t(nn)) return PIC_EINVAL;
+    std::vector<double> phi(x, x + nn);
+    for (size_t k = 0; k < nn; ++k)
+      if (!(c->h_nodeflags[k] & kFree)) phi[k] = c->h_g[k];
+    if (cudaMemcpyAsync(c->d_phi, phi.data(), nn * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+      return PIC_ECUDA;
+    return check(cudaStreamSynchronize(c->stream));
+  }
   if (species < 0 || species > 1 || n < 0) return PIC_EINVAL;
   if (n > 0 && (!x || !y || !vx || !vy)) return PIC_EINVAL;
   if (n > c->cfg.capacity[species]) return PIC_EOVERFLOW;
