@@ -70,7 +70,17 @@ void build_geometry(pic_ctx *c, std::vector<uint8_t> &cellmask, std::vector<doub
   const Geom &g = c->g;
   cellmask.assign(size_t(g.nx) * g.ny, 0);
   for (int i = 0; i < g.nx; ++i)
-    for (int j = 0; j < g.ny; ++j) cellmask[size_t(i) * g.ny + j] = plasma_cell(cfg, i, j) ? 1 : 0;
+    for (int j = 0; j < g.ny; ++j)
+      cellmask[size_t(i) * g.ny + j] = plasma_cell(cfg, i, j) ? kCellPlasma : 0;
+  // interior cells: every neighbour within one cell is plasma (moves of at
+  // most one cell from them cannot reach a wall)
+  for (int i = 0; i < g.nx; ++i)
+    for (int j = 0; j < g.ny; ++j) {
+      bool all = true;
+      for (int di = -1; di <= 1 && all; ++di)
+        for (int dj = -1; dj <= 1 && all; ++dj) all = plasma_cell_wrapped(cfg, i + di, j + dj);
+      if (all) cellmask[size_t(i) * g.ny + j] |= kCellInterior;
+    }
   const size_t nn = size_t(g.nxn) * g.nyn;
   std::vector<uint8_t> dir(nn, 0);
   std::vector<double> val(nn, 0.0);

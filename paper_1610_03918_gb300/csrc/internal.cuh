@@ -33,6 +33,10 @@ struct Geom {
   int ntx, nty;        // tiles
 };
 
+// Cell mask bits (uint8 per cell)
+constexpr uint8_t kCellPlasma = 1;
+constexpr uint8_t kCellInterior = 2;   // the cell and its eight neighbours are plasma
+
 // Node flag bits (uint8 per node)
 constexpr uint8_t kFree = 1;     // not a Dirichlet node
 constexpr uint8_t kOpenXm = 2;   // edge (i-1, j) - (i, j) borders a plasma cell

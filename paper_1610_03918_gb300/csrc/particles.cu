@@ -254,6 +254,69 @@ __device__ __forceinline__ void deposit_shared(uint32_t *sAcc, int li, int lj, i
   atomicAdd(&sAcc[k + NWY + 1], (uint32_t)w11);
 }
 
+// The rare path of a move: walk the crossed faces in order of the segment
+// parameter (x face first on a tie).  The first face whose far cell is a
+// conductor or outside a bounded direction absorbs the particle: its wall
+// and bottom-cell tallies and a hit record are written and 1 is returned.
+// A move longer than the walk limit is dropped (status bit, no tally) and 1
+// is returned.  Otherwise the cell offset (oi, oj) of the end point is set
+// and 0 returned.  Kept out of line so the common path stays small.
+__device__ __noinline__ int walk_move(const PArgs &a, int s, int i, int j, float fx, float fy,
+                                      float dx, float dy, int cx, int cy, float vx1, float vy1,
+                                      const uint32_t *id, int64_t slot, int &oi, int &oj) {
+  const Geom &g = a.g;
+  const int si = cx > 0 ? 1 : -1, sj = cy > 0 ? 1 : -1;
+  const float adx = fabsf(dx), ady = fabsf(dy);
+  oi = 0;
+  oj = 0;
+  for (int k = 0; k < kWalkLimit; ++k) {
+    const bool needx = oi != cx, needy = oj != cy;
+    if (!needx && !needy) return 0;
+    const float facex = float(si > 0 ? oi + 1 : oi);
+    const float facey = float(sj > 0 ? oj + 1 : oj);
+    const bool xfirst = __fmul_rn(fabsf(__fsub_rn(facex, fx)), ady) <=
+                        __fmul_rn(fabsf(__fsub_rn(facey, fy)), adx);
+    const bool takex = needx && (!needy || xfirst);
+    if (takex) oi += si; else oj += sj;
+    int gi = i + oi, gj = j + oj;
+    bool outx = false, outy = false;
+    if (g.px) gi = wrapmod(gi, g.nx); else outx = gi < 0 || gi >= g.nx;
+    if (g.py) gj = wrapmod(gj, g.ny); else outy = gj < 0 || gj >= g.ny;
+    if (outx || outy || !__ldg(&a.cellmask[gi * g.ny + gj])) {
+      int wall, wcell;
+      if (takex) {
+        wall = si > 0 ? (outx ? PIC_WALL_XMAX : PIC_WALL_COND_PX)
+                      : (outx ? PIC_WALL_XMIN : PIC_WALL_COND_MX);
+        wcell = gj;
+      } else {
+        wall = sj > 0 ? (outy ? PIC_WALL_YMAX : PIC_WALL_COND_PY)
+                      : (outy ? PIC_WALL_YMIN : PIC_WALL_COND_MY);
+        wcell = gi;
+      }
+      atomicAdd(&a.walls[s * PIC_NWALLS + wall], 1ull);
+      if (wall == PIC_WALL_XMAX) atomicAdd(&a.bottom[s * g.ny + wcell], 1ull);
+      const unsigned long long h = atomicAdd(a.nhits, 1ull);
+      if ((long long)h < a.hit_cap) {
+        pic_hit rec;
+        rec.id = id[slot];
+        rec.species = int16_t(s);
+        rec.wall = int16_t(wall);
+        rec.cell = wcell;
+        rec.step = *a.step;
+        rec.vx = vx1;
+        rec.vy = vy1;
+        a.hits[h] = rec;
+      } else {
+        atomicOr(a.status, PIC_ST_FULL);
+      }
+      return 1;
+    }
+  }
+  if (oi == cx && oj == cy) return 0;
+  atomicOr(a.status, PIC_ST_CFL);   // moved farther than the walk limit: dropped untallied
+  return 1;
+}
+
 template <int MODE>
 __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint32_t *sAcc,
                                          unsigned long long *acc, int s, int wi0, int wj0,
@@ -311,62 +374,13 @@ __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint3
   const int cx = int(cxf), cy = int(cyf);
   int oi = 0, oj = 0;     // cell offset of the move
   if (cx | cy) {
-    // Walk the crossed faces in order of the segment parameter (x first on a tie).
-    const int si = cx > 0 ? 1 : -1, sj = cy > 0 ? 1 : -1;
-    const float adx = fabsf(dx), ady = fabsf(dy);
-    bool dead = false;
-    int wall = -1, wcell = -1;
-    for (int k = 0; k < kWalkLimit; ++k) {
-      const bool needx = oi != cx, needy = oj != cy;
-      if (!needx && !needy) break;
-      const float facex = float(si > 0 ? oi + 1 : oi);
-      const float facey = float(sj > 0 ? oj + 1 : oj);
-      const bool xfirst = __fmul_rn(fabsf(__fsub_rn(facex, fx)), ady) <=
-                          __fmul_rn(fabsf(__fsub_rn(facey, fy)), adx);
-      const bool takex = needx && (!needy || xfirst);
-      if (takex) oi += si; else oj += sj;
-      int gi = i + oi, gj = j + oj;
-      bool outx = false, outy = false;
-      if (g.px) gi = wrapmod(gi, g.nx); else outx = gi < 0 || gi >= g.nx;
-      if (g.py) gj = wrapmod(gj, g.ny); else outy = gj < 0 || gj >= g.ny;
-      if (outx || outy || !__ldg(&a.cellmask[gi * g.ny + gj])) {
-        dead = true;
-        if (takex) {
-          wall = si > 0 ? (outx ? PIC_WALL_XMAX : PIC_WALL_COND_PX)
-                        : (outx ? PIC_WALL_XMIN : PIC_WALL_COND_MX);
-          wcell = gj;
-        } else {
-          wall = sj > 0 ? (outy ? PIC_WALL_YMAX : PIC_WALL_COND_PY)
-                        : (outy ? PIC_WALL_YMIN : PIC_WALL_COND_MY);
-          wcell = gi;
-        }
-        break;
-      }
-    }
-    if (!dead && (oi != cx || oj != cy)) {
-      // moved farther than the walk limit: flag and drop without a tally
-      atomicOr(a.status, PIC_ST_CFL);
-      c = -1;
-      return;
-    }
-    if (dead) {
-      c = -1;
-      atomicAdd(&a.walls[s * PIC_NWALLS + wall], 1ull);
-      if (wall == PIC_WALL_XMAX) atomicAdd(&a.bottom[s * g.ny + wcell], 1ull);
-      const unsigned long long h = atomicAdd(a.nhits, 1ull);
-      if ((long long)h < a.hit_cap) {
-        pic_hit rec;
-        rec.id = id[slot];
-        rec.species = int16_t(s);
-        rec.wall = int16_t(wall);
-        rec.cell = wcell;
-        rec.step = *a.step;
-        rec.vx = vx1;
-        rec.vy = vy1;
-        a.hits[h] = rec;
-      } else {
-        atomicOr(a.status, PIC_ST_FULL);
-      }
+    const bool near = (unsigned)(cx + 1) <= 2u && (unsigned)(cy + 1) <= 2u;
+    if (near && (__ldg(&a.cellmask[i * g.ny + j]) & kCellInterior)) {
+      // all eight neighbours are plasma: no face within one cell can absorb
+      oi = cx;
+      oj = cy;
+    } else if (walk_move(a, s, i, j, fx, fy, dx, dy, cx, cy, vx1, vy1, id, slot, oi, oj)) {
+      c = -1;   // absorbed and tallied, or moved beyond the walk limit
       return;
     }
     nfx = __fsub_rn(nfx, cxf);
