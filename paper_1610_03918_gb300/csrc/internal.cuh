@@ -22,8 +22,12 @@ constexpr int kTileX = 16;
 constexpr int kTileY = 16;
 constexpr int kHalo = 4;
 constexpr int kChunk = 4092;     // particles per work item (multiple of 4, <= 4095)
-constexpr int kParticleThreads = 256;
-constexpr int kParticleMinBlocks = 4;   // resident CTAs per SM the register budget allows
+#ifndef PIC_PARTICLE_THREADS
+#define PIC_PARTICLE_THREADS 128
+#endif
+constexpr int kParticleThreads = PIC_PARTICLE_THREADS;
+// resident CTAs per SM the register budget allows (64 registers per thread)
+constexpr int kParticleMinBlocks = 1024 / PIC_PARTICLE_THREADS;
 constexpr int kWalkLimit = 16;   // face crossings followed per move
 
 struct Geom {

@@ -260,8 +260,9 @@ __device__ __forceinline__ void deposit_shared(uint32_t *sAcc, int li, int lj, i
 // and bottom-cell tallies and a hit record are written and 1 is returned.
 // A move longer than the walk limit is dropped (status bit, no tally) and 1
 // is returned.  Otherwise the cell offset (oi, oj) of the end point is set
-// and 0 returned.  Kept out of line so the common path stays small.
-__device__ __noinline__ int walk_move(const PArgs &a, int s, int i, int j, float fx, float fy,
+// and 0 returned.  Only particles in cells next to a wall or conductor, or
+// moving more than one cell, come here.
+__device__ __forceinline__ int walk_move(const PArgs &a, int s, int i, int j, float fx, float fy,
                                       float dx, float dy, int cx, int cy, float vx1, float vy1,
                                       const uint32_t *id, int64_t slot, int &oi, int &oj) {
   const Geom &g = a.g;
