@@ -81,6 +81,7 @@ struct MGLevel {
   float *stab;         // levels >= 1: unique Galerkin 9-point stencils [k][3x3]
   int nst;             // number of unique stencils
   float *u, *f;        // correction and right-hand side
+  float *upre = nullptr;   // levels above lc: u after the pre-smoothing
 };
 
 struct Reducer {

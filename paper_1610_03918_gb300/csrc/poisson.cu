@@ -30,6 +30,7 @@
 #include <cmath>
 #include <cstring>
 #include <map>
+#include <type_traits>
 
 #include "internal.cuh"
 
@@ -42,9 +43,42 @@ constexpr int kCoarseThreads = 1024;
 constexpr int kMaxOuter = 8;
 constexpr int kCoarsestSweeps = 16;
 constexpr int kDenseCoarsest = 64;
-constexpr size_t kCoarseSmemMax = 220 * 1024;   // dynamic shared memory granted to k_coarse   // coarsest levels up to this many unknowns use a dense inverse
+constexpr size_t kCoarseSmemMax = 220 * 1024;   // dynamic shared memory granted to k_coarse
+// A coarse-level stencil entry: the 3x3 Galerkin coefficients, then the
+// reciprocal of the diagonal, padded to 48 bytes for 16-byte vector loads.
+constexpr int kSt = 12;
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
+
+// Programmatic dependent launch.  Every kernel of this file starts by waiting
+// for the grid before it (its results are then visible) and at once lets the
+// next kernel of the stream be scheduled, so that kernel's blocks are resident
+// and waiting when this one ends instead of being launched only then.  Both
+// instructions are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory");
+}
+
+#ifndef PICGB_NO_PDL
+constexpr bool kPdl = true;
+#else
+constexpr bool kPdl = false;
+#endif
+
+template <typename... P, typename... A>
+void launch(void (*k)(P...), int grid, int block, size_t smem, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(unsigned(block));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = kPdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -144,6 +178,7 @@ struct FineArgs {
 
 // acc -> rho, b; clears acc.  For a doubly periodic box the mean of b is kept.
 __global__ void k_rho(FineArgs a) {
+  pdl_enter();
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
   double v[2] = {0.0, 0.0};
@@ -180,11 +215,13 @@ __global__ void k_rho(FineArgs a) {
 
 // phi <- Dirichlet values, zero on free nodes (cold start)
 __global__ void k_phi_reset(FineArgs a) {
+  pdl_enter();
   GRID_STRIDE(n, a.g.nxn * a.g.nyn) a.phi[n] = a.gval[n];
 }
 
 // initial guess extrapolated in time: phi <- 2 phi^n - phi^{n-1} on free nodes
 __global__ void k_extrapolate(FineArgs a) {
+  pdl_enter();
   GRID_STRIDE(n, a.g.nxn * a.g.nyn) {
     if (a.flags[n] & kFree) {
       const double p = a.phi[n];
@@ -209,6 +246,7 @@ __device__ __forceinline__ void nbr_index(const Geom &g, int n, int &xm, int &xp
 // Outer FP64 residual r = b - A phi (the certificate) and the set-up of the
 // inner PCG on A e = r.
 __global__ void k_resid64(FineArgs a) {
+  pdl_enter();
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
   const double bmean = a.ps->bmean;
@@ -260,6 +298,7 @@ __global__ void k_resid64(FineArgs a) {
 
 // rz = <r, z - zmean> and zmean (doubly periodic box)
 __global__ void k_rz(FineArgs a) {
+  pdl_enter();
   if (a.ps->inner_done) return;
   const int nn = a.g.nxn * a.g.nyn;
   float rz = 0.f, zs = 0.f, rs = 0.f;
@@ -281,6 +320,7 @@ __global__ void k_rz(FineArgs a) {
 
 // p_new = (z - zmean) + beta p_old, q = A p_new, pq = <p_new, q>
 __global__ void k_pq(FineArgs a) {
+  pdl_enter();
   const PoissonState *ps = a.ps;
   if (ps->inner_done) return;
   const Geom g = a.g;
@@ -309,6 +349,7 @@ __global__ void k_pq(FineArgs a) {
 
 // e += alpha p, r -= alpha q, rr = <r, r>; convergence of the inner solve
 __global__ void k_update(FineArgs a) {
+  pdl_enter();
   PoissonState *ps = a.ps;
   if (ps->inner_done) return;
   const int nn = a.g.nxn * a.g.nyn;
@@ -339,6 +380,7 @@ __global__ void k_update(FineArgs a) {
 }
 
 __global__ void k_correct(FineArgs a) {
+  pdl_enter();
   if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->outer_iters += 1;
   GRID_STRIDE(n, a.g.nxn * a.g.nyn) {
     if (a.flags[n] & kFree) a.phi[n] += double(a.e[n]);
@@ -346,12 +388,14 @@ __global__ void k_correct(FineArgs a) {
 }
 
 __global__ void k_outer_init(PoissonState *ps) {
+  pdl_enter();
   ps->total_iters = 0;
   ps->outer_iters = 0;
 }
 
 // E = -grad phi by the open-edge rule; field energy 1/2 sum |E|^2
 __global__ void k_field(FineArgs a) {
+  pdl_enter();
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
   double v[1] = {0.0};
@@ -380,8 +424,9 @@ struct LevelDev {
   int nxn, nyn, px, py;
   const uint8_t *free;   // level 0: 1 = unknown
   const uint16_t *sid;   // levels >= 1: 0 = not an unknown, k = stencil k-1 of stab
-  const float *stab;     // levels >= 1: unique Galerkin stencils [k][3x3]
+  const float *stab;     // levels >= 1: unique Galerkin stencils [k][kSt] (3x3, 1/diag)
   float *u, *f;
+  float *upre;           // levels above lc: u after the pre-smoothing
 };
 
 struct MGArgs {
@@ -391,7 +436,10 @@ struct MGArgs {
   int ncoarse;           // unknowns of the coarsest level solved by its dense inverse (0: sweeps)
   const float *cinv;     // [ncoarse][ncoarse]
   const int *cidx;       // node index of each coarsest unknown
-  const PoissonState *ps;
+  PoissonState *ps;
+  double *part;          // grid reduction of <r, z> fused into the level-0 post-smoothing
+  unsigned int *ticket;
+  int singular;
 };
 
 __device__ __forceinline__ int nb_idx(const LevelDev &L, int i, int j, int di, int dj) {
@@ -409,14 +457,19 @@ __device__ __forceinline__ bool is_free(const LevelDev &L, int n) {
 // unit Laplacian on the fine level, the node's Galerkin stencil on coarser
 // ones.  Only called on free nodes, which are interior in a bounded direction.
 template <bool FINE>
-__device__ __forceinline__ float apply_off(const LevelDev &L, int i, int j, int n, float &diag) {
+__device__ __forceinline__ float apply_off(const LevelDev &L, int i, int j, int n, float &diag,
+                                           float &rdiag) {
   if (FINE) {
     diag = 4.f;
+    rdiag = 0.25f;
     return -(L.u[nb_idx(L, i, j, -1, 0)] + L.u[nb_idx(L, i, j, 1, 0)] +
              L.u[nb_idx(L, i, j, 0, -1)] + L.u[nb_idx(L, i, j, 0, 1)]);
   } else {
-    const float *s = L.stab + 9 * (int(L.sid[n]) - 1);
+    const float4 *s4 = reinterpret_cast<const float4 *>(L.stab + kSt * (int(L.sid[n]) - 1));
+    const float4 a = s4[0], b = s4[1], c = s4[2];
+    const float s[10] = {a.x, a.y, a.z, a.w, b.x, b.y, b.z, b.w, c.x, c.y};
     diag = s[4];
+    rdiag = s[9];
     float acc = 0.f;
 #pragma unroll
     for (int di = -1; di <= 1; ++di)
@@ -434,9 +487,9 @@ template <bool FINE>
 __device__ __forceinline__ void gs_node(const LevelDev &L, int i, int j) {
   const int n = i * L.nyn + j;
   if (!is_free<FINE>(L, n)) return;
-  float d;
-  const float off = apply_off<FINE>(L, i, j, n, d);
-  L.u[n] = (L.f[n] - off) / d;
+  float d, rd;
+  const float off = apply_off<FINE>(L, i, j, n, d, rd);
+  L.u[n] = (L.f[n] - off) * rd;
 }
 
 // First half sweep from u = 0: the first colour gets f / diag, the rest 0.
@@ -446,7 +499,7 @@ __device__ __forceinline__ void gs_zero_node(const LevelDev &L, int i, int j) {
   const bool first = FINE ? (((i + j) & 1) == 0) : (((i | j) & 1) == 0);
   float v = 0.f;
   if (first && is_free<FINE>(L, n))
-    v = L.f[n] / (FINE ? 4.f : L.stab[9 * (int(L.sid[n]) - 1) + 4]);
+    v = L.f[n] * (FINE ? 0.25f : L.stab[kSt * (int(L.sid[n]) - 1) + 9]);
   L.u[n] = v;
 }
 
@@ -454,12 +507,16 @@ template <bool FINE>
 __device__ __forceinline__ float resid_node(const LevelDev &L, int i, int j) {
   const int n = i * L.nyn + j;
   if (!is_free<FINE>(L, n)) return 0.f;
-  float d;
-  const float off = apply_off<FINE>(L, i, j, n, d);
+  float d, rd;
+  const float off = apply_off<FINE>(L, i, j, n, d, rd);
   return L.f[n] - (d * L.u[n] + off);
 }
 
-// full weighting of the fine residual onto coarse node (I, J)
+// Full weighting of the fine residual onto coarse node (I, J).  It follows a
+// forward sweep whose last colour has no neighbour of its own colour, so the
+// residual there is zero (up to rounding) and is not evaluated: the black
+// nodes, (a + b) odd, on the red-black level and the corners, a and b odd, on
+// the four-colour levels.  Five of the nine fine residuals remain.
 template <bool FINE>
 __device__ __forceinline__ void restrict_node(const LevelDev &F, const LevelDev &C, int I, int J) {
   const int nc = I * C.nyn + J;
@@ -472,6 +529,7 @@ __device__ __forceinline__ void restrict_node(const LevelDev &F, const LevelDev 
   for (int a = -1; a <= 1; ++a) {
 #pragma unroll
     for (int b = -1; b <= 1; ++b) {
+      if (FINE ? ((a + b) & 1) != 0 : (a != 0 && b != 0)) continue;
       const int i = F.px ? wrapi(2 * I + a, F.nxn) : 2 * I + a;
       const int j = F.py ? wrapi(2 * J + b, F.nyn) : 2 * J + b;
       const float w = (a == 0 ? 2.f : 1.f) * (b == 0 ? 2.f : 1.f);
@@ -501,74 +559,45 @@ __device__ __forceinline__ int colour_count(const LevelDev &L) {
   return FINE ? L.nxn * ((L.nyn + 1) >> 1) : ((L.nxn + 1) >> 1) * ((L.nyn + 1) >> 1);
 }
 
-template <bool FINE>
-__device__ __forceinline__ bool colour_node(const LevelDev &L, int c, int t, int &i, int &j) {
-  const int hy = (L.nyn + 1) >> 1;
-  if (FINE) {
-    i = t / hy;
-    j = 2 * (t - i * hy) + ((i + c) & 1);
-  } else {
-    const int ti = t / hy;
-    i = 2 * ti + (c >> 1);
-    j = 2 * (t - ti * hy) + (c & 1);
-  }
-  return i < L.nxn && j < L.nyn;
-}
-
-template <bool FINE>
-__global__ void k_gs(MGArgs a, int l, int c) {
-  if (a.ps->inner_done) return;
-  const LevelDev &L = a.L[l];
-  const int t = blockIdx.x * blockDim.x + threadIdx.x;
-  int i, j;
-  if (t < colour_count<FINE>(L) && colour_node<FINE>(L, c, t, i, j)) gs_node<FINE>(L, i, j);
-}
-
-template <bool FINE>
-__global__ void k_gs_zero(MGArgs a, int l) {
-  if (a.ps->inner_done) return;
-  const LevelDev &L = a.L[l];
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < L.nxn * L.nyn) gs_zero_node<FINE>(L, n / L.nyn, n - (n / L.nyn) * L.nyn);
-}
-
-template <bool FINE>
-__global__ void k_restrict(MGArgs a, int l) {
-  if (a.ps->inner_done) return;
-  const LevelDev &C = a.L[l + 1];
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < C.nxn * C.nyn) restrict_node<FINE>(a.L[l], C, n / C.nyn, n - (n / C.nyn) * C.nyn);
-}
-
-template <bool FINE>
-__global__ void k_prolong(MGArgs a, int l) {
-  if (a.ps->inner_done) return;
-  const LevelDev &F = a.L[l];
-  const int n = blockIdx.x * blockDim.x + threadIdx.x;
-  if (n < F.nxn * F.nyn) prolong_node<FINE>(F, a.L[l + 1], n / F.nyn, n - (n / F.nyn) * F.nyn);
-}
-
 // ---- the levels from lc down, inside one CTA, everything in shared memory ----
+// The level descriptors are passed by value so their fields stay in registers.
+//
+// t / d for 0 <= t, d < 2^15 from the rounded reciprocal rd = 1/d: the
+// rounded product differs from (t + 0.5) / d by less than 2^-23 (t + 0.5) / d,
+// below that value's distance 0.5 / d to the nearest integer, so the
+// truncation is exact (levels here hold at most 16384 nodes).
+__device__ __forceinline__ int div_small(int t, float rd) {
+  return int(__fmul_rn(__fadd_rn(float(t), 0.5f), rd));
+}
+
 template <bool FINE>
-__device__ void cta_sweep(const LevelDev &L, int c) {
+__device__ void cta_sweep(const LevelDev L, int c) {
   const int cnt = colour_count<FINE>(L);
+  const int hy = (L.nyn + 1) >> 1;
+  const float rhy = __frcp_rn(float(hy));
   for (int t = threadIdx.x; t < cnt; t += blockDim.x) {
-    int i, j;
-    if (colour_node<FINE>(L, c, t, i, j)) gs_node<FINE>(L, i, j);
+    const int ti = div_small(t, rhy);
+    const int i = FINE ? ti : 2 * ti + (c >> 1);
+    const int j = 2 * (t - ti * hy) + (FINE ? ((i + c) & 1) : (c & 1));
+    if (i < L.nxn && j < L.nyn) gs_node<FINE>(L, i, j);
   }
   __syncthreads();
 }
 
 template <bool FINE>
-__device__ void cta_zero(const LevelDev &L) {
+__device__ void cta_zero(const LevelDev L) {
   const int nn = L.nxn * L.nyn;
-  for (int n = threadIdx.x; n < nn; n += blockDim.x) gs_zero_node<FINE>(L, n / L.nyn, n % L.nyn);
+  const float r = __frcp_rn(float(L.nyn));
+  for (int n = threadIdx.x; n < nn; n += blockDim.x) {
+    const int i = div_small(n, r);
+    gs_zero_node<FINE>(L, i, n - i * L.nyn);
+  }
   __syncthreads();
 }
 
 // pre (forward) or post (reverse) smoothing: one sweep over all colours
 template <bool FINE>
-__device__ void cta_smooth(const LevelDev &L, bool forward, bool zero_start) {
+__device__ void cta_smooth(const LevelDev L, bool forward, bool zero_start) {
   const int nc = FINE ? 2 : 4;
   if (forward) {
     if (zero_start) cta_zero<FINE>(L);
@@ -579,17 +608,264 @@ __device__ void cta_smooth(const LevelDev &L, bool forward, bool zero_start) {
 }
 
 template <bool FINE>
-__device__ void cta_restrict(const LevelDev &F, const LevelDev &C) {
+__device__ void cta_restrict(const LevelDev F, const LevelDev C) {
   const int nn = C.nxn * C.nyn;
-  for (int n = threadIdx.x; n < nn; n += blockDim.x) restrict_node<FINE>(F, C, n / C.nyn, n % C.nyn);
+  const float r = __frcp_rn(float(C.nyn));
+  for (int n = threadIdx.x; n < nn; n += blockDim.x) {
+    const int I = div_small(n, r);
+    restrict_node<FINE>(F, C, I, n - I * C.nyn);
+  }
   __syncthreads();
 }
 
 template <bool FINE>
-__device__ void cta_prolong(const LevelDev &F, const LevelDev &C) {
+__device__ void cta_prolong(const LevelDev F, const LevelDev C) {
   const int nn = F.nxn * F.nyn;
-  for (int n = threadIdx.x; n < nn; n += blockDim.x) prolong_node<FINE>(F, C, n / F.nyn, n % F.nyn);
+  const float r = __frcp_rn(float(F.nyn));
+  for (int n = threadIdx.x; n < nn; n += blockDim.x) {
+    const int i = div_small(n, r);
+    prolong_node<FINE>(F, C, i, n - i * F.nyn);
+  }
   __syncthreads();
+}
+
+// ---- the levels above lc: each level's smoothing in two tiled kernels ----
+//
+// k_pre:  from u = 0, one forward sweep over the colours, then the full-
+//         weighting restriction of the residual to level l+1.  A CTA owns a
+//         TI x TJ block of coarse nodes; it repeats the sweep in shared memory
+//         on every fine node those depend on (H = 2 nodes beyond the
+//         restriction footprint on the red-black level, one per colour, 4, on
+//         the four-colour levels), then writes the restricted residual of its
+//         coarse nodes and the swept u of the fine nodes it owns to upre.
+// k_post: u = upre + P u_{l+1} on the free nodes, then one reverse sweep.  A
+//         CTA owns a PI x PJ block of fine nodes and repeats the work on the H
+//         nodes around it.  It reads upre and writes u, so no CTA sees
+//         another's writes.  On level 0 it also sums <r, z>, sum z and sum r
+//         for the conjugate gradient.
+// Colour c is swept at margin m from the edge of the shared region, with m
+// growing by one per colour: a node at margin m reads neighbours at margin
+// m - 1 or more, all of which the earlier colours have finished.
+template <bool FINE> struct TileShape;
+template <> struct TileShape<true> {
+  static constexpr int H = 2, TI = 8, TJ = 32, PI = 16, PJ = 64;
+};
+template <> struct TileShape<false> {
+  static constexpr int H = 4, TI = 8, TJ = 16, PI = 16, PJ = 32;
+};
+constexpr int kTileThreads = 256;
+
+template <bool FINE>
+using NodeCode = typename std::conditional<FINE, uint8_t, uint16_t>::type;
+
+template <bool FINE>
+struct Tile {
+  int gi0, gj0;          // level coordinates of region node (0, 0)
+  int rh, rw;
+  float *u, *f;
+  NodeCode<FINE> *code;  // free flag / stencil id + 1; 0: not an unknown or outside the box
+  const float *stab;
+};
+
+template <bool FINE>
+__device__ __forceinline__ int tile_colour(const Tile<FINE> &T, int ri, int rj) {
+  const int gi = T.gi0 + ri, gj = T.gj0 + rj;
+  return FINE ? ((gi + gj) & 1) : (((gi & 1) << 1) | (gj & 1));
+}
+
+// off-diagonal part of (A u) at region node t, the diagonal and its reciprocal
+template <bool FINE>
+__device__ __forceinline__ float tile_off(const Tile<FINE> &T, int t, float &d, float &rd) {
+  const float *u = T.u;
+  const int w = T.rw;
+  if (FINE) {
+    d = 4.f;
+    rd = 0.25f;
+    return -(u[t - w] + u[t + w] + u[t - 1] + u[t + 1]);
+  } else {
+    const float4 *s4 = reinterpret_cast<const float4 *>(T.stab + kSt * (int(T.code[t]) - 1));
+    const float4 a = __ldg(s4), b = __ldg(s4 + 1), c = __ldg(s4 + 2);
+    d = b.x;
+    rd = c.y;
+    float acc = a.x * u[t - w - 1];
+    acc = fmaf(a.y, u[t - w], acc);
+    acc = fmaf(a.z, u[t - w + 1], acc);
+    acc = fmaf(a.w, u[t - 1], acc);
+    acc = fmaf(b.y, u[t + 1], acc);
+    acc = fmaf(b.z, u[t + w - 1], acc);
+    acc = fmaf(b.w, u[t + w], acc);
+    acc = fmaf(c.x, u[t + w + 1], acc);
+    return acc;
+  }
+}
+
+template <bool FINE>
+__device__ __forceinline__ float tile_resid(const Tile<FINE> &T, int t) {
+  if (!T.code[t]) return 0.f;
+  float d, rd;
+  const float off = tile_off<FINE>(T, t, d, rd);
+  return T.f[t] - (d * T.u[t] + off);
+}
+
+template <bool FINE>
+__device__ void tile_sweep(const Tile<FINE> &T, int c, int m) {
+  const int n = T.rh * T.rw;
+  const float rrw = __frcp_rn(float(T.rw));
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int ri = div_small(t, rrw), rj = t - ri * T.rw;
+    if (ri < m || ri >= T.rh - m || rj < m || rj >= T.rw - m) continue;
+    if (tile_colour<FINE>(T, ri, rj) != c || !T.code[t]) continue;
+    float d, rd;
+    const float off = tile_off<FINE>(T, t, d, rd);
+    T.u[t] = (T.f[t] - off) * rd;
+  }
+  __syncthreads();
+}
+
+__device__ __forceinline__ int wrap_mod(int a, int n) {
+  a %= n;
+  return a < 0 ? a + n : a;
+}
+
+// Fills the region from level F.  PRE: u = 0 except the first colour, which
+// gets f / diag (the first half of the sweep from zero).  Otherwise u = upre
+// plus the bilinear prolongation of level C's u, on the free nodes.
+template <bool FINE, bool PRE>
+__device__ void tile_load(const LevelDev &F, const LevelDev &C, const Tile<FINE> &T) {
+  const int n = T.rh * T.rw;
+  const float rrw = __frcp_rn(float(T.rw));
+  for (int t = threadIdx.x; t < n; t += blockDim.x) {
+    const int ri = div_small(t, rrw), rj = t - ri * T.rw;
+    int gi = T.gi0 + ri, gj = T.gj0 + rj;
+    bool in = true;
+    if (F.px) gi = wrap_mod(gi, F.nxn);
+    else in = gi >= 0 && gi < F.nxn;
+    if (F.py) gj = wrap_mod(gj, F.nyn);
+    else in = in && gj >= 0 && gj < F.nyn;
+    int code = 0;
+    float f = 0.f, u = 0.f;
+    if (in) {
+      const int g = gi * F.nyn + gj;
+      code = FINE ? int(F.free[g]) : int(F.sid[g]);
+      f = F.f[g];
+      if (code) {
+        if (PRE) {
+          if (tile_colour<FINE>(T, ri, rj) == 0)
+            u = f * (FINE ? 0.25f : __ldg(F.stab + kSt * (code - 1) + 9));
+        } else {
+          const int I0 = gi >> 1, J0 = gj >> 1;
+          const int I1 = (gi & 1) ? (C.px ? wrapi(I0 + 1, C.nxn) : I0 + 1) : I0;
+          const int J1 = (gj & 1) ? (C.py ? wrapi(J0 + 1, C.nyn) : J0 + 1) : J0;
+          const float v = 0.25f * (C.u[I0 * C.nyn + J0] + C.u[I1 * C.nyn + J0] +
+                                   C.u[I0 * C.nyn + J1] + C.u[I1 * C.nyn + J1]);
+          u = F.upre[g] + v;
+        }
+      }
+    }
+    T.code[t] = NodeCode<FINE>(code);
+    T.f[t] = f;
+    T.u[t] = u;
+  }
+  __syncthreads();
+}
+
+template <bool FINE>
+__global__ void __launch_bounds__(kTileThreads) k_pre(MGArgs a, int l) {
+  pdl_enter();
+  if (a.ps->inner_done) return;
+  using S = TileShape<FINE>;
+  constexpr int RH = 2 * S::TI + 1 + 2 * S::H, RW = 2 * S::TJ + 1 + 2 * S::H;
+  __shared__ float su[RH * RW], sf[RH * RW];
+  __shared__ NodeCode<FINE> sc[RH * RW];
+  const LevelDev F = a.L[l], C = a.L[l + 1];
+  const int tcj = (C.nyn + S::TJ - 1) / S::TJ;
+  const int I0 = (blockIdx.x / tcj) * S::TI, J0 = (blockIdx.x % tcj) * S::TJ;
+  const Tile<FINE> T{2 * I0 - 1 - S::H, 2 * J0 - 1 - S::H, RH, RW, su, sf, sc, F.stab};
+  tile_load<FINE, true>(F, C, T);
+  for (int c = 1; c < (FINE ? 2 : 4); ++c) tile_sweep<FINE>(T, c, c);
+  // Restriction.  The last colour has no neighbour of its own colour, so its
+  // residual after the sweep is zero up to rounding and is skipped: the black
+  // nodes, (a + b) odd, on the red-black level and the corners, a and b odd,
+  // on the four-colour levels.  Five of the nine fine residuals remain.
+  for (int k = threadIdx.x; k < S::TI * S::TJ; k += blockDim.x) {
+    const int I = I0 + k / S::TJ, J = J0 + k % S::TJ;
+    if (I >= C.nxn || J >= C.nyn) continue;
+    const int nc = I * C.nyn + J;
+    if (!C.sid[nc]) {
+      C.f[nc] = 0.f;
+      continue;
+    }
+    const int t0 = (2 * (I - I0) + 1 + S::H) * RW + 2 * (J - J0) + 1 + S::H;
+    float sum = 0.f;
+#pragma unroll
+    for (int da = -1; da <= 1; ++da)
+#pragma unroll
+      for (int db = -1; db <= 1; ++db) {
+        if (FINE ? ((da + db) & 1) != 0 : (da != 0 && db != 0)) continue;
+        const float w = (da == 0 ? 2.f : 1.f) * (db == 0 ? 2.f : 1.f);
+        sum = fmaf(w, tile_resid<FINE>(T, t0 + da * RW + db), sum);
+      }
+    C.f[nc] = sum * (1.f / 16.f);
+  }
+  // the swept u of the fine nodes this tile owns
+  for (int k = threadIdx.x; k < 4 * S::TI * S::TJ; k += blockDim.x) {
+    const int ri = k / (2 * S::TJ), rj = k % (2 * S::TJ);
+    const int i = 2 * I0 + ri, j = 2 * J0 + rj;
+    if (i < F.nxn && j < F.nyn) F.upre[i * F.nyn + j] = su[(ri + 1 + S::H) * RW + rj + 1 + S::H];
+  }
+}
+
+template <bool FINE>
+__global__ void __launch_bounds__(kTileThreads) k_post(MGArgs a, int l) {
+  pdl_enter();
+  if (a.ps->inner_done) return;
+  using S = TileShape<FINE>;
+  constexpr int RH = S::PI + 2 * S::H, RW = S::PJ + 2 * S::H;
+  __shared__ float su[RH * RW], sf[RH * RW];
+  __shared__ NodeCode<FINE> sc[RH * RW];
+  const LevelDev F = a.L[l], C = a.L[l + 1];
+  const int tpj = (F.nyn + S::PJ - 1) / S::PJ;
+  const int P0 = (blockIdx.x / tpj) * S::PI, Q0 = (blockIdx.x % tpj) * S::PJ;
+  const Tile<FINE> T{P0 - S::H, Q0 - S::H, RH, RW, su, sf, sc, F.stab};
+  tile_load<FINE, false>(F, C, T);
+  for (int c = (FINE ? 1 : 3), m = 1; c >= 0; --c, ++m) tile_sweep<FINE>(T, c, m);
+  float rz = 0.f, zs = 0.f, rs = 0.f;
+  for (int k = threadIdx.x; k < S::PI * S::PJ; k += blockDim.x) {
+    const int ri = k / S::PJ, rj = k % S::PJ;
+    const int i = P0 + ri, j = Q0 + rj;
+    if (i >= F.nxn || j >= F.nyn) continue;
+    const int t = (ri + S::H) * RW + rj + S::H;
+    const float z = su[t];
+    F.u[i * F.nyn + j] = z;
+    if (FINE) {
+      const float r = sf[t];
+      rz = fmaf(r, z, rz);
+      zs += z;
+      rs += r;
+    }
+  }
+  if (!FINE) return;
+  // level 0: u is the preconditioned residual z; rz = <r, z - zmean>
+  double v[3] = {rz, zs, rs};
+  if (grid_sum<3>(v, a.part, a.ticket) && threadIdx.x == 0) {
+    PoissonState *ps = a.ps;
+    const double zm = a.singular ? v[1] / double(F.nxn * F.nyn) : 0.0;
+    ps->zmean = zm;
+    ps->rz_old = ps->rz;
+    ps->rz = v[0] - zm * v[2];
+  }
+}
+
+int pre_tiles(const MGLevel &C, bool fine) {
+  const int ti = fine ? TileShape<true>::TI : TileShape<false>::TI;
+  const int tj = fine ? TileShape<true>::TJ : TileShape<false>::TJ;
+  return ((C.nxn + ti - 1) / ti) * ((C.nyn + tj - 1) / tj);
+}
+
+int post_tiles(const MGLevel &F, bool fine) {
+  const int pi = fine ? TileShape<true>::PI : TileShape<false>::PI;
+  const int pj = fine ? TileShape<true>::PJ : TileShape<false>::PJ;
+  return ((F.nxn + pi - 1) / pi) * ((F.nyn + pj - 1) / pj);
 }
 
 template <typename T>
@@ -606,13 +882,14 @@ size_t coarse_smem_bytes(const MGArgs &a) {
   for (int l = a.lc; l < a.nlev; ++l) {
     const size_t nn = size_t(a.L[l].nxn) * a.L[l].nyn;
     t += 2 * seg(nn * 4);
-    t += l == 0 ? seg(nn) : seg(nn * 2) + seg(size_t(a.nst[l]) * 9 * 4);
+    t += l == 0 ? seg(nn) : seg(nn * 2) + seg(size_t(a.nst[l]) * kSt * 4);
   }
   t += seg(size_t(a.ncoarse) * a.ncoarse * 4) + seg(size_t(a.ncoarse) * 4);
   return t;
 }
 
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse(MGArgs a) {
+  pdl_enter();
   if (a.ps->inner_done) return;
   extern __shared__ __align__(16) unsigned char smem[];
   const int lc = a.lc, last = a.nlev - 1;
@@ -629,9 +906,9 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse(MGArgs a) {
       S[l].free = fr;
     } else {
       uint16_t *sid = carve<uint16_t>(p, nn);
-      float *tab = carve<float>(p, size_t(a.nst[l]) * 9);
+      float *tab = carve<float>(p, size_t(a.nst[l]) * kSt);
       for (int n = threadIdx.x; n < nn; n += blockDim.x) sid[n] = a.L[l].sid[n];
-      for (int k = threadIdx.x; k < a.nst[l] * 9; k += blockDim.x) tab[k] = a.L[l].stab[k];
+      for (int k = threadIdx.x; k < a.nst[l] * kSt; k += blockDim.x) tab[k] = a.L[l].stab[k];
       S[l].sid = sid;
       S[l].stab = tab;
     }
@@ -746,54 +1023,44 @@ MGArgs mg_args(pic_ctx *c) {
     a.L[l].stab = m.stab;
     a.L[l].u = m.u;
     a.L[l].f = m.f;
+    a.L[l].upre = m.upre;
     a.nst[l] = m.nst;
   }
   a.ncoarse = c->ncoarse;
   a.cinv = c->d_cinv;
   a.cidx = c->d_cidx;
   a.ps = c->d_ps;
+  a.part = c->red.part;
+  a.ticket = c->red.ticket;
+  a.singular = c->singular;
   return a;
 }
 
 inline int blocks_for(int n) { return std::max(1, (n + kThreads - 1) / kThreads); }
 
+// One V-cycle: the pre-smoothing and restriction of each level above lc, the
+// levels from lc down in one CTA, then the prolongation and post-smoothing of
+// each level back up.  With lc > 0 the last kernel also forms <r, z>.
 void launch_vcycle(pic_ctx *c, const MGArgs &a) {
   for (int l = 0; l < c->lc; ++l) {
-    const MGLevel &L = c->lev[l];
-    const int nn = L.nxn * L.nyn;
-    const int nbc = blocks_for(c->lev[l + 1].nxn * c->lev[l + 1].nyn);
-    if (l == 0) {
-      const int nh = blocks_for(L.nxn * ((L.nyn + 1) / 2));
-      k_gs_zero<true><<<blocks_for(nn), kThreads, 0, c->stream>>>(a, l);
-      k_gs<true><<<nh, kThreads, 0, c->stream>>>(a, l, 1);
-      k_restrict<true><<<nbc, kThreads, 0, c->stream>>>(a, l);
-      c->launches += 3;
-    } else {
-      const int nq = blocks_for(((L.nxn + 1) / 2) * ((L.nyn + 1) / 2));
-      k_gs_zero<false><<<blocks_for(nn), kThreads, 0, c->stream>>>(a, l);
-      for (int col = 1; col < 4; ++col) k_gs<false><<<nq, kThreads, 0, c->stream>>>(a, l, col);
-      k_restrict<false><<<nbc, kThreads, 0, c->stream>>>(a, l);
-      c->launches += 5;
-    }
+    const int nt = pre_tiles(c->lev[l + 1], l == 0);
+    if (l == 0) launch(k_pre<true>, nt, kTileThreads, 0, c->stream, a, l);
+    else launch(k_pre<false>, nt, kTileThreads, 0, c->stream, a, l);
   }
-  k_coarse<<<1, kCoarseThreads, c->coarse_smem, c->stream>>>(a);
-  c->launches += 1;
+  launch(k_coarse, 1, kCoarseThreads, c->coarse_smem, c->stream, a);
   for (int l = c->lc - 1; l >= 0; --l) {
-    const MGLevel &L = c->lev[l];
-    const int nn = L.nxn * L.nyn;
-    if (l == 0) k_prolong<true><<<blocks_for(nn), kThreads, 0, c->stream>>>(a, l);
-    else k_prolong<false><<<blocks_for(nn), kThreads, 0, c->stream>>>(a, l);
-    if (l == 0) {
-      const int nh = blocks_for(L.nxn * ((L.nyn + 1) / 2));
-      k_gs<true><<<nh, kThreads, 0, c->stream>>>(a, l, 1);
-      k_gs<true><<<nh, kThreads, 0, c->stream>>>(a, l, 0);
-      c->launches += 3;
-    } else {
-      const int nq = blocks_for(((L.nxn + 1) / 2) * ((L.nyn + 1) / 2));
-      for (int col = 3; col >= 0; --col) k_gs<false><<<nq, kThreads, 0, c->stream>>>(a, l, col);
-      c->launches += 5;
-    }
+    const int nt = post_tiles(c->lev[l], l == 0);
+    if (l == 0) launch(k_post<true>, nt, kTileThreads, 0, c->stream, a, l);
+    else launch(k_post<false>, nt, kTileThreads, 0, c->stream, a, l);
   }
+  c->launches += 2 * c->lc + 1;
+}
+
+// <r, z> after a V-cycle that did not form it (every level in one CTA)
+void launch_rz(pic_ctx *c, const FineArgs &f) {
+  if (c->lc > 0) return;
+  launch(k_rz, c->red.nblocks, kThreads, 0, c->stream, f);
+  c->launches += 1;
 }
 
 // ---- host: Galerkin coarse operator A_c = R A_f P, R = P^T / 4 ----
@@ -951,9 +1218,11 @@ cudaError_t poisson_setup(pic_ctx *c) {
       sid[k] = uint16_t(id + 1);
     }
     m.nst = int(uniq.size());
-    std::vector<float> tab(std::max<size_t>(uniq.size(), 1) * 9, 0.f);
-    for (size_t k = 0; k < uniq.size(); ++k)
-      for (int q = 0; q < 9; ++q) tab[k * 9 + q] = uniq[k][q];
+    std::vector<float> tab(std::max<size_t>(uniq.size(), 1) * kSt, 0.f);
+    for (size_t k = 0; k < uniq.size(); ++k) {
+      for (int q = 0; q < 9; ++q) tab[k * kSt + q] = uniq[k][q];
+      tab[k * kSt + 9] = 1.f / uniq[k][4];
+    }
     m.sid = (uint16_t *)dev_alloc(c, n * 2);
     m.stab = (float *)dev_alloc(c, tab.size() * 4);
     m.u = (float *)dev_alloc(c, n * sizeof(float));
@@ -1054,10 +1323,19 @@ cudaError_t poisson_setup(pic_ctx *c) {
   }
   c->lev[0].u = c->d_z;
   c->lev[0].f = c->d_r32;
+  for (int l = 0; l < c->nlev; ++l) {
+    MGLevel &m = c->lev[l];
+    m.upre = nullptr;
+    if (l >= c->lc) continue;
+    m.upre = (float *)dev_alloc(c, size_t(m.nxn) * m.nyn * sizeof(float));
+    if (!m.upre) return cudaErrorMemoryAllocation;
+  }
   c->d_phi_prev = (double *)dev_alloc(c, nn * sizeof(double));
   if (!c->d_phi_prev) return cudaErrorMemoryAllocation;
   c->red.nblocks = std::min(blocks_for(int(nn)), 2 * c->num_sms);
-  c->red.part = (double *)dev_alloc(c, size_t(c->red.nblocks) * 4 * sizeof(double));
+  // partials of the grid reductions: the vector kernels and the level-0 post-smoothing
+  const int nparts = std::max(c->red.nblocks, c->lc > 0 ? post_tiles(c->lev[0], true) : 0);
+  c->red.part = (double *)dev_alloc(c, size_t(nparts) * 4 * sizeof(double));
   c->red.ticket = (unsigned int *)dev_alloc(c, 64);
   c->d_ps = (PoissonState *)dev_alloc(c, sizeof(PoissonState));
   if (!c->red.part || !c->red.ticket || !c->d_ps) return cudaErrorMemoryAllocation;
@@ -1073,13 +1351,13 @@ cudaError_t poisson_setup(pic_ctx *c) {
 cudaError_t launch_rho(pic_ctx *c, int advance_step) {
   FineArgs a = fine_args(c);
   a.advance_step = advance_step;
-  k_rho<<<c->red.nblocks, kThreads, 0, c->stream>>>(a);
+  launch(k_rho, c->red.nblocks, kThreads, 0, c->stream, a);
   return cudaGetLastError();
 }
 
 cudaError_t launch_field(pic_ctx *c) {
   FineArgs a = fine_args(c);
-  k_field<<<c->red.nblocks, kThreads, 0, c->stream>>>(a);
+  launch(k_field, c->red.nblocks, kThreads, 0, c->stream, a);
   return cudaGetLastError();
 }
 
@@ -1089,37 +1367,36 @@ pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
   const int nb = c->red.nblocks;
   cudaEventRecord(c->ev0, c->stream);
   if (zero_guess) {
-    k_phi_reset<<<nb, kThreads, 0, c->stream>>>(a);
+    launch(k_phi_reset, nb, kThreads, 0, c->stream, a);
     c->launches += 1;
   } else if (c->cfg.warm_start == 2) {
-    k_extrapolate<<<nb, kThreads, 0, c->stream>>>(a);
+    launch(k_extrapolate, nb, kThreads, 0, c->stream, a);
     c->launches += 1;
   }
-  k_outer_init<<<1, 1, 0, c->stream>>>(c->d_ps);
+  launch(k_outer_init, 1, 1, 0, c->stream, c->d_ps);
   c->launches += 1;
   const int batch = 4;
   for (;;) {
-    k_resid64<<<nb, kThreads, 0, c->stream>>>(a);
+    launch(k_resid64, nb, kThreads, 0, c->stream, a);
     c->launches += 1;
     cudaMemcpyAsync(c->h_ps, c->d_ps, sizeof(PoissonState), cudaMemcpyDeviceToHost, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
     if (!c->h_ps->go) break;
     launch_vcycle(c, m);
-    k_rz<<<nb, kThreads, 0, c->stream>>>(a);
-    c->launches += 1;
+    launch_rz(c, a);
     for (int it = 0; it < c->cfg.poisson_maxit; it += batch) {
       for (int b = 0; b < batch; ++b) {
-        k_pq<<<nb, kThreads, 0, c->stream>>>(a);
-        k_update<<<nb, kThreads, 0, c->stream>>>(a);
+        launch(k_pq, nb, kThreads, 0, c->stream, a);
+        launch(k_update, nb, kThreads, 0, c->stream, a);
         launch_vcycle(c, m);
-        k_rz<<<nb, kThreads, 0, c->stream>>>(a);
-        c->launches += 3;
+        launch_rz(c, a);
+        c->launches += 2;
       }
       cudaMemcpyAsync(c->h_ps, c->d_ps, sizeof(PoissonState), cudaMemcpyDeviceToHost, c->stream);
       if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
       if (c->h_ps->inner_done) break;
     }
-    k_correct<<<nb, kThreads, 0, c->stream>>>(a);
+    launch(k_correct, nb, kThreads, 0, c->stream, a);
     c->launches += 1;
   }
   cudaEventRecord(c->ev1, c->stream);
@@ -1194,35 +1471,35 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   cudaError_t e;
 #define CK(x) do { if ((e = (x)) != cudaSuccess) { note(e, #x); return e; } } while (0)
   CK(cap_begin(s, top, deps));
-  if (c->cfg.warm_start == 0) k_phi_reset<<<nb, kThreads, 0, s>>>(a);
-  if (c->cfg.warm_start == 2) k_extrapolate<<<nb, kThreads, 0, s>>>(a);
-  k_outer_init<<<1, 1, 0, s>>>(c->d_ps);
+  if (c->cfg.warm_start == 0) launch(k_phi_reset, nb, kThreads, 0, s, a);
+  if (c->cfg.warm_start == 2) launch(k_extrapolate, nb, kThreads, 0, s, a);
+  launch(k_outer_init, 1, 1, 0, s, c->d_ps);
   CK(cap_end(s, deps));
   cudaGraphNode_t n_outer, n_if_outer, n_inner, n_if_inner;
   cudaGraph_t b_outer, b_if_outer, b_inner, b_if_inner;
   CK(add_cond(top, deps, h[0], cudaGraphCondTypeWhile, &n_outer, &b_outer));
   std::vector<cudaGraphNode_t> d;
   CK(cap_begin(s, b_outer, {}));
-  k_resid64<<<nb, kThreads, 0, s>>>(a);
+  launch(k_resid64, nb, kThreads, 0, s, a);
   CK(cap_end(s, d));
   CK(add_cond(b_outer, d, h[1], cudaGraphCondTypeIf, &n_if_outer, &b_if_outer));
   CK(cap_begin(s, b_if_outer, {}));
   launch_vcycle(c, m);
-  k_rz<<<nb, kThreads, 0, s>>>(a);
+  launch_rz(c, a);
   CK(cap_end(s, d));
   CK(add_cond(b_if_outer, d, h[2], cudaGraphCondTypeWhile, &n_inner, &b_inner));
   CK(cap_begin(s, b_inner, {}));
-  k_pq<<<nb, kThreads, 0, s>>>(a);
-  k_update<<<nb, kThreads, 0, s>>>(a);
+  launch(k_pq, nb, kThreads, 0, s, a);
+  launch(k_update, nb, kThreads, 0, s, a);
   CK(cap_end(s, d));
   CK(add_cond(b_inner, d, h[3], cudaGraphCondTypeIf, &n_if_inner, &b_if_inner));
   CK(cap_begin(s, b_if_inner, {}));
   launch_vcycle(c, m);
-  k_rz<<<nb, kThreads, 0, s>>>(a);
+  launch_rz(c, a);
   CK(cap_end(s, d));
   d.assign(1, n_inner);
   CK(cap_begin(s, b_if_outer, d));
-  k_correct<<<nb, kThreads, 0, s>>>(a);
+  launch(k_correct, nb, kThreads, 0, s, a);
   CK(cap_end(s, d));
 #undef CK
   deps.assign(1, n_outer);
@@ -1231,12 +1508,12 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
 
 // Kernels one solve launched, from its device counters (graph mode).
 int64_t poisson_kernel_count(pic_ctx *c, const PoissonState &ps) {
-  int64_t vc = 1;
-  for (int l = 0; l < c->lc; ++l) vc += (l == 0) ? 6 : 10;
+  // a V-cycle with <r, z>: fused into its last kernel unless lc = 0
+  const int64_t vc = 2 * c->lc + 1 + (c->lc == 0 ? 1 : 0);
   const int64_t O = ps.outer_iters, I = ps.total_iters;
-  // init + resid per outer pass (+1 final) + per inner solve (V-cycle, rz, correct)
-  // + per iteration (pq, update) + per non-final iteration (V-cycle, rz)
-  return 1 + (O + 1) + O * (vc + 2) + 2 * I + std::max<int64_t>(I - O, 0) * (vc + 1) +
+  // init + resid per outer pass (+1 final) + per inner solve (V-cycle, correct)
+  // + per iteration (pq, update) + per non-final iteration (V-cycle)
+  return 1 + (O + 1) + O * (vc + 1) + 2 * I + std::max<int64_t>(I - O, 0) * vc +
          (c->cfg.warm_start != 1 ? 1 : 0);
 }
 
@@ -1245,6 +1522,7 @@ int64_t poisson_kernel_count(pic_ctx *c, const PoissonState &ps) {
 namespace {
 
 __global__ void k_absmax(const double *rho, int nn, unsigned int *out) {
+  pdl_enter();
   float m = 0.f;
   GRID_STRIDE(n, nn) m = fmaxf(m, float(fabs(rho[n])));
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
@@ -1254,6 +1532,7 @@ __global__ void k_absmax(const double *rho, int nn, unsigned int *out) {
 // x[i][j] = (rho / s, 1 for a Dirichlet node); rows beyond the grid count as conductor
 __global__ void k_learned_input(const double *rho, const uint8_t *flags, int nxn, int nyn, int hpad,
                                 const unsigned int *smax, float *x) {
+  pdl_enter();
   const float s = fmaxf(__uint_as_float(*smax), 1e-30f);
   GRID_STRIDE(n, hpad * nyn) {
     const int i = n / nyn;
@@ -1269,12 +1548,14 @@ __global__ void k_learned_input(const double *rho, const uint8_t *flags, int nxn
 
 __global__ void k_guess_learned(double *phi, const double *phiL, const uint8_t *flags, const float *y,
                                 double scale, int nn) {
+  pdl_enter();
   GRID_STRIDE(n, nn) {
     if (flags[n] & kFree) phi[n] = phiL[n] + scale * double(y[n]);
   }
 }
 
 __global__ void k_b_lift(double *b, const double *lift, const uint8_t *flags, int nn) {
+  pdl_enter();
   GRID_STRIDE(n, nn) b[n] = (flags[n] & kFree) ? lift[n] : 0.0;
 }
 
@@ -1294,7 +1575,7 @@ pic_status ensure_vacuum_potential(pic_ctx *c) {
   PoissonState ps_save;
   cudaMemcpyAsync(&ps_save, c->d_ps, sizeof(ps_save), cudaMemcpyDeviceToHost, c->stream);
   cudaStreamSynchronize(c->stream);
-  k_b_lift<<<c->red.nblocks, kThreads, 0, c->stream>>>(c->d_b, c->d_lift, c->d_nodeflags, int(nn));
+  launch(k_b_lift, c->red.nblocks, kThreads, 0, c->stream, c->d_b, c->d_lift, c->d_nodeflags, int(nn));
   cudaMemsetAsync(&c->d_ps->bmean, 0, sizeof(double), c->stream);
   const double rtol = c->cfg.poisson_rtol;
   c->cfg.poisson_rtol = 1e-10;
@@ -1313,8 +1594,8 @@ pic_status learned_input(pic_ctx *c, int hpad, float *x, double *scale) {
   if (hpad < c->g.nxn) return PIC_EINVAL;
   unsigned int *smax = reinterpret_cast<unsigned int *>(c->red.ticket) + 8;   // spare word
   cudaMemsetAsync(smax, 0, 4, c->stream);
-  k_absmax<<<c->red.nblocks, kThreads, 0, c->stream>>>(c->d_rho, nn, smax);
-  k_learned_input<<<c->red.nblocks, kThreads, 0, c->stream>>>(c->d_rho, c->d_nodeflags, c->g.nxn,
+  launch(k_absmax, c->red.nblocks, kThreads, 0, c->stream, c->d_rho, nn, smax);
+  launch(k_learned_input, c->red.nblocks, kThreads, 0, c->stream, c->d_rho, c->d_nodeflags, c->g.nxn,
                                                                 c->g.nyn, hpad, smax, x);
   unsigned int bits = 0;
   if (cudaMemcpyAsync(&bits, smax, 4, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
@@ -1337,7 +1618,7 @@ pic_status poisson_with_guess(pic_ctx *c, int guess, const float *y, double scal
     cudaMemcpyAsync(c->d_phi, c->d_phiL, size_t(nn) * 8, cudaMemcpyDeviceToDevice, c->stream);
   if (guess == 3) {
     if (!y) return PIC_EINVAL;
-    k_guess_learned<<<c->red.nblocks, kThreads, 0, c->stream>>>(c->d_phi, c->d_phiL, c->d_nodeflags,
+    launch(k_guess_learned, c->red.nblocks, kThreads, 0, c->stream, c->d_phi, c->d_phiL, c->d_nodeflags,
                                                                   y, scale, nn);
   }
   const pic_status st = poisson_solve(c, guess == 0);
