@@ -91,7 +91,7 @@ __global__ void k_deposit(const double *x, const double *y, long long n, int nx,
 __global__ void k_finish(const unsigned long long *acc, long long nn, double scale, double *rho) {
   for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < nn;
        k += (long long)gridDim.x * blockDim.x)
-    rho[k] = scale * double(acc[k]);
+    rho[k] = scale * double((long long)acc[k]);   // two's complement: a sum can be slightly negative
 }
 
 int grid_for(long long n) {

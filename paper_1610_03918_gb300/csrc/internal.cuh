@@ -64,7 +64,8 @@ struct PoissonState {
   double rr64;        // ||b - A phi||^2 (FP64, outer)
   double rel;         // sqrt(rr64 / bb)
   double bmean;       // mean of b (doubly periodic box only)
-  double rz, rz_old, pq, rr, rr0;   // inner PCG scalars
+  double rz, rz_old, rr, rr0;       // inner PCG: gamma = <r, z>, its previous value, ||r||^2
+  double delta;                      // <z, A z>
   double alpha, beta;
   double zmean;
   double tol_in;      // inner target relative to the inner initial residual
@@ -122,7 +123,7 @@ struct pic_ctx {
   // Poisson
   int nlev, lc;                // levels, first level solved by the single-CTA kernel
   std::vector<picgb::MGLevel> lev;
-  float *d_r32, *d_z, *d_p0, *d_p1, *d_q, *d_e;
+  float *d_r32, *d_z, *d_p, *d_w, *d_q, *d_e;   // inner PCG vectors (w = A z)
   size_t coarse_smem;          // dynamic shared memory of the single-CTA coarse V-cycle
   int ncoarse;                 // unknowns of the coarsest level (dense inverse), 0 = sweeps
   float *d_cinv;

@@ -218,7 +218,10 @@ __device__ __forceinline__ void deposit_global(const PArgs &a, unsigned long lon
 
 // Fixed-point CIC shares.  Every rounding is spelled out (no contraction
 // left to the compiler) so a particle's shares do not depend on the code
-// path it took, and hence not on the particle order.
+// path it took, and hence not on the particle order.  The fourth share is
+// the remainder, so the four sum to exactly 2^20; it is -1 when the three
+// rounded shares overshoot (a particle on a cell edge), which the window
+// flush below accounts for.
 __device__ __forceinline__ void cic_weights(float fx, float fy, int &w00, int &w01, int &w10,
                                             int &w11) {
   const float gx = __fsub_rn(1.0f, fx), gy = __fsub_rn(1.0f, fy);
@@ -470,8 +473,13 @@ __global__ void __launch_bounds__(kParticleThreads, kParticleMinBlocks) k_partic
           int gi = wi0 + wi, gj = wj0 + wj;
           if (g.px) gi = wrapmod(gi, g.nxn);
           if (g.py) gj = wrapmod(gj, g.nyn);
+          // The node's sum over the chunk lies in [-kChunk, kChunk * 2^20]: each of
+          // at most kChunk particles adds a share in [-1, 2^20].  That range is
+          // narrower than 2^32, so the 32-bit sum decodes uniquely; values above
+          // kChunk * 2^20 are the negative ones.
+          const long long x = v > uint32_t(kChunk) * kQ ? (long long)v - (1ll << 32) : (long long)v;
           if (gi >= 0 && gi < g.nxn && gj >= 0 && gj < g.nyn)
-            atomicAdd(&acc[gi * g.nyn + gj], (unsigned long long)v);
+            atomicAdd(&acc[gi * g.nyn + gj], (unsigned long long)x);
         }
       }
     }

@@ -38,15 +38,25 @@ namespace picgb {
 namespace {
 
 constexpr int kThreads = 256;
-constexpr int kSmallLevel = 16384;
-constexpr int kCoarseThreads = 1024;
+#ifndef PICGB_SMALL_LEVEL
+#define PICGB_SMALL_LEVEL 1024
+#endif
+constexpr int kSmallLevel = PICGB_SMALL_LEVEL;
+constexpr int kCoarseThreads = 256;
 constexpr int kMaxOuter = 8;
 constexpr int kCoarsestSweeps = 16;
-constexpr int kDenseCoarsest = 64;
+#ifndef PICGB_DENSE_COARSEST
+#define PICGB_DENSE_COARSEST 160
+#endif
+constexpr int kDenseCoarsest = PICGB_DENSE_COARSEST;   // coarsest levels with at most this many unknowns are solved exactly
 constexpr size_t kCoarseSmemMax = 220 * 1024;   // dynamic shared memory granted to k_coarse
 // A coarse-level stencil entry: the 3x3 Galerkin coefficients, then the
 // reciprocal of the diagonal, padded to 48 bytes for 16-byte vector loads.
 constexpr int kSt = 12;
+
+// byte counts rounded up to 16: arrays staged into shared memory by 16-byte
+// asynchronous copies are allocated with this padding
+__host__ __device__ constexpr size_t pad16(size_t b) { return (b + 15) & ~size_t(15); }
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
@@ -157,7 +167,7 @@ struct FineArgs {
   double qw[2];              // q_s w_s 2^-20
   double sw[2];              // q_s w_s (surface charge per hit)
   int surface;
-  float *r32, *z, *p_old, *p_new, *q, *e;
+  float *r32, *z, *p, *w, *q, *e;
   PoissonState *ps;
   double *part;
   unsigned int *ticket;
@@ -176,36 +186,60 @@ struct FineArgs {
 #define GRID_STRIDE(n, N) \
   for (int n = blockIdx.x * blockDim.x + threadIdx.x; n < (N); n += gridDim.x * blockDim.x)
 
+// The vector kernels take kVB nodes per thread, n = base + k * blockDim.x,
+// and issue all loads of such a batch before its first store, so a thread
+// waits for memory once per batch rather than once per node.
+constexpr int kVB = 4;
+#define VEC_BATCHES(base, N)                                                         \
+  for (int base = blockIdx.x * blockDim.x * kVB + threadIdx.x; base < (N);          \
+       base += gridDim.x * blockDim.x * kVB)
+#define VEC_NODES(k, n, base, N)    \
+  _Pragma("unroll") for (int k = 0; k < kVB; ++k) \
+    if (const int n = (base) + k * int(blockDim.x); n < (N))
+
 // acc -> rho, b; clears acc.  For a doubly periodic box the mean of b is kept.
 __global__ void k_rho(FineArgs a) {
   pdl_enter();
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
   double v[2] = {0.0, 0.0};
-  GRID_STRIDE(n, nn) {
-    const unsigned long long a0 = a.acc[n], a1 = a.acc[nn + n];
-    a.acc[n] = 0ull;
-    a.acc[nn + n] = 0ull;
-    double rho = a.rho_ext[n] + a.qw[0] * double(a0) + a.qw[1] * double(a1);
-    if (a.surface && !g.px) {
-      const int i = n / g.nyn, j = n - (n / g.nyn) * g.nyn;
-      if (i == g.nx - 1) {
-        // half of bottom face k's charge on nodes (nx-1, k) and (nx-1, k+1)
-        double s = 0.0;
-        if (j < g.ny) s += 0.5 * (a.sw[0] * double(a.bottom[j]) + a.sw[1] * double(a.bottom[g.ny + j]));
-        int jm = j - 1;
-        if (g.py && jm < 0) jm += g.ny;
-        if (jm >= 0 && jm < g.ny)
-          s += 0.5 * (a.sw[0] * double(a.bottom[jm]) + a.sw[1] * double(a.bottom[g.ny + jm]));
-        rho += s;
-      }
+  VEC_BATCHES(base, nn) {
+    unsigned long long a0[kVB], a1[kVB];
+    double rx[kVB], lf[kVB];
+    uint8_t fl[kVB];
+    VEC_NODES(k, n, base, nn) {
+      a0[k] = a.acc[n];
+      a1[k] = a.acc[nn + n];
+      rx[k] = a.rho_ext[n];
+      lf[k] = a.lift[n];
+      fl[k] = a.flags[n];
     }
-    a.rho[n] = rho;
-    const bool fr = a.flags[n] & kFree;
-    const double bb = fr ? rho + a.lift[n] : 0.0;
-    a.b[n] = bb;
-    v[0] += bb;
-    v[1] += fr ? 1.0 : 0.0;
+    VEC_NODES(k, n, base, nn) {
+      a.acc[n] = 0ull;
+      a.acc[nn + n] = 0ull;
+      // two's-complement sums: a node's total can be slightly negative (CIC
+      // shares of -1 unit from the fixed-point rounding)
+      double rho = rx[k] + a.qw[0] * double((long long)a0[k]) + a.qw[1] * double((long long)a1[k]);
+      if (a.surface && !g.px) {
+        const int i = n / g.nyn, j = n - (n / g.nyn) * g.nyn;
+        if (i == g.nx - 1) {
+          // half of bottom face k's charge on nodes (nx-1, k) and (nx-1, k+1)
+          double s = 0.0;
+          if (j < g.ny) s += 0.5 * (a.sw[0] * double(a.bottom[j]) + a.sw[1] * double(a.bottom[g.ny + j]));
+          int jm = j - 1;
+          if (g.py && jm < 0) jm += g.ny;
+          if (jm >= 0 && jm < g.ny)
+            s += 0.5 * (a.sw[0] * double(a.bottom[jm]) + a.sw[1] * double(a.bottom[g.ny + jm]));
+          rho += s;
+        }
+      }
+      a.rho[n] = rho;
+      const bool fr = fl[k] & kFree;
+      const double bb = fr ? rho + lf[k] : 0.0;
+      a.b[n] = bb;
+      v[0] += bb;
+      v[1] += fr ? 1.0 : 0.0;
+    }
   }
   if (grid_sum<2>(v, a.part, a.ticket) && threadIdx.x == 0) {
     a.ps->bmean = a.singular ? v[0] / v[1] : 0.0;
@@ -222,11 +256,20 @@ __global__ void k_phi_reset(FineArgs a) {
 // initial guess extrapolated in time: phi <- 2 phi^n - phi^{n-1} on free nodes
 __global__ void k_extrapolate(FineArgs a) {
   pdl_enter();
-  GRID_STRIDE(n, a.g.nxn * a.g.nyn) {
-    if (a.flags[n] & kFree) {
-      const double p = a.phi[n];
-      a.phi[n] = 2.0 * p - a.phi_prev[n];
-      a.phi_prev[n] = p;
+  const int nn = a.g.nxn * a.g.nyn;
+  VEC_BATCHES(base, nn) {
+    double p[kVB], q[kVB];
+    uint8_t fl[kVB];
+    VEC_NODES(k, n, base, nn) {
+      fl[k] = a.flags[n];
+      p[k] = a.phi[n];
+      q[k] = a.phi_prev[n];
+    }
+    VEC_NODES(k, n, base, nn) {
+      if (fl[k] & kFree) {
+        a.phi[n] = 2.0 * p[k] - q[k];
+        a.phi_prev[n] = p[k];
+      }
     }
   }
 }
@@ -251,22 +294,37 @@ __global__ void k_resid64(FineArgs a) {
   const int nn = g.nxn * g.nyn;
   const double bmean = a.ps->bmean;
   double v[2] = {0.0, 0.0};
-  GRID_STRIDE(n, nn) {
-    float r32 = 0.f;
-    if (a.flags[n] & kFree) {
+  VEC_BATCHES(base, nn) {
+    double bv[kVB], lf[kVB], ph[kVB][5];
+    uint8_t fl[kVB];
+    VEC_NODES(k, n, base, nn) {
       int xm, xp, ym, yp;
       nbr_index(g, n, xm, xp, ym, yp);
-      const double bn = a.b[n] - bmean;
-      const double rho = bn - a.lift[n];
-      const double Aphi = 4.0 * a.phi[n] - a.phi[xm] - a.phi[xp] - a.phi[ym] - a.phi[yp];
-      const double r = rho - Aphi;
-      r32 = float(r);
-      v[0] += r * r;
-      v[1] += bn * bn;
+      fl[k] = a.flags[n];
+      bv[k] = a.b[n];
+      lf[k] = a.lift[n];
+      ph[k][0] = a.phi[n];
+      ph[k][1] = a.phi[xm];
+      ph[k][2] = a.phi[xp];
+      ph[k][3] = a.phi[ym];
+      ph[k][4] = a.phi[yp];
     }
-    a.r32[n] = r32;
-    a.e[n] = 0.f;
-    a.p_old[n] = 0.f;
+    VEC_NODES(k, n, base, nn) {
+      float r32 = 0.f;
+      if (fl[k] & kFree) {
+        const double bn = bv[k] - bmean;
+        const double rho = bn - lf[k];
+        const double Aphi = 4.0 * ph[k][0] - ph[k][1] - ph[k][2] - ph[k][3] - ph[k][4];
+        const double r = rho - Aphi;
+        r32 = float(r);
+        v[0] += r * r;
+        v[1] += bn * bn;
+      }
+      a.r32[n] = r32;
+      a.e[n] = 0.f;
+      a.p[n] = 0.f;
+      a.q[n] = 0.f;
+    }
   }
   if (grid_sum<2>(v, a.part, a.ticket) && threadIdx.x == 0) {
     PoissonState *ps = a.ps;
@@ -296,75 +354,101 @@ __global__ void k_resid64(FineArgs a) {
   }
 }
 
-// rz = <r, z - zmean> and zmean (doubly periodic box)
-__global__ void k_rz(FineArgs a) {
+// The scalars after a preconditioner application z = M r, w = A z: zmean (a
+// doubly periodic box projects z to zero mean, which leaves A z unchanged),
+// gamma = <r, z - zmean> and delta = <z - zmean, w>.  v = {<r, z>, sum z,
+// sum r, <z, w>, sum w}.
+__device__ __forceinline__ void store_gamma_delta(PoissonState *ps, const double (&v)[5], int singular,
+                                                  int nn) {
+  const double zm = singular ? v[1] / double(nn) : 0.0;
+  ps->zmean = zm;
+  ps->rz = v[0] - zm * v[2];
+  ps->delta = v[3] - zm * v[4];
+}
+
+// w = A z and the scalars of store_gamma_delta, after a V-cycle that ran
+// entirely in one CTA (the tiled level-0 post-smoothing forms them otherwise)
+__global__ void k_zw(FineArgs a) {
   pdl_enter();
   if (a.ps->inner_done) return;
-  const int nn = a.g.nxn * a.g.nyn;
-  float rz = 0.f, zs = 0.f, rs = 0.f;
-  GRID_STRIDE(n, nn) {
-    const float r = a.r32[n], z = a.z[n];
-    rz = fmaf(r, z, rz);
-    zs += z;
-    rs += r;
-  }
-  double v[3] = {rz, zs, rs};
-  if (grid_sum<3>(v, a.part, a.ticket) && threadIdx.x == 0) {
-    PoissonState *ps = a.ps;
-    const double zm = a.singular ? v[1] / double(nn) : 0.0;
-    ps->zmean = zm;
-    ps->rz_old = ps->rz;
-    ps->rz = v[0] - zm * v[2];
-  }
-}
-
-// p_new = (z - zmean) + beta p_old, q = A p_new, pq = <p_new, q>
-__global__ void k_pq(FineArgs a) {
-  pdl_enter();
-  const PoissonState *ps = a.ps;
-  if (ps->inner_done) return;
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
-  const float beta = ps->inner_iters == 0 ? 0.f : float(ps->rz / ps->rz_old);
-  const float zm = float(ps->zmean);
-  float pq = 0.f;
-  GRID_STRIDE(n, nn) {
-    float pn = 0.f, qn = 0.f;
-    if (a.flags[n] & kFree) {
+  float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
+  VEC_BATCHES(base, nn) {
+    float z[kVB][5], r[kVB];
+    uint8_t fl[kVB];
+    VEC_NODES(k, n, base, nn) {
       int xm, xp, ym, yp;
       nbr_index(g, n, xm, xp, ym, yp);
-      auto P = [&](int m) -> float {
-        return (a.flags[m] & kFree) ? (a.z[m] - zm) + beta * a.p_old[m] : 0.f;
-      };
-      pn = P(n);
-      qn = 4.f * pn - P(xm) - P(xp) - P(ym) - P(yp);
-      pq = fmaf(pn, qn, pq);
+      fl[k] = a.flags[n];
+      r[k] = a.r32[n];
+      z[k][0] = a.z[n];
+      z[k][1] = a.z[xm];
+      z[k][2] = a.z[xp];
+      z[k][3] = a.z[ym];
+      z[k][4] = a.z[yp];
     }
-    a.p_new[n] = pn;
-    a.q[n] = qn;
+    VEC_NODES(k, n, base, nn) {
+      // z is zero on the Dirichlet nodes, so the plain 5-point sum is A z
+      const float w = (fl[k] & kFree) ? 4.f * z[k][0] - z[k][1] - z[k][2] - z[k][3] - z[k][4] : 0.f;
+      a.w[n] = w;
+      s[0] = fmaf(r[k], z[k][0], s[0]);
+      s[1] += z[k][0];
+      s[2] += r[k];
+      s[3] = fmaf(z[k][0], w, s[3]);
+      s[4] += w;
+    }
   }
-  double v[1] = {pq};
-  if (grid_sum<1>(v, a.part, a.ticket) && threadIdx.x == 0) a.ps->pq = v[0];
+  double v[5] = {s[0], s[1], s[2], s[3], s[4]};
+  if (grid_sum<5>(v, a.part, a.ticket) && threadIdx.x == 0) store_gamma_delta(a.ps, v, a.singular, nn);
 }
 
-// e += alpha p, r -= alpha q, rr = <r, r>; convergence of the inner solve
-__global__ void k_update(FineArgs a) {
+// One step of the preconditioned conjugate gradient in its single-reduction
+// form (Chronopoulos and Gear): from gamma = <r, z>, delta = <z, A z> and the
+// previous gamma and alpha,
+//   beta = gamma / gamma_old,  alpha = gamma / (delta - beta gamma / alpha_old)
+// (beta = 0, alpha = gamma / delta on the first step), then
+//   p = (z - zmean) + beta p,  q = w + beta q (= A p),  e += alpha p,  r -= alpha q
+// and rr = <r, r> for the convergence test.  The inner products of a step are
+// all formed by the preconditioner's last kernel, so a step has one grid-wide
+// reduction point besides this kernel's.
+__global__ void k_cg(FineArgs a) {
   pdl_enter();
   PoissonState *ps = a.ps;
   if (ps->inner_done) return;
   const int nn = a.g.nxn * a.g.nyn;
-  const float alpha = float(ps->rz / ps->pq);
+  const bool first = ps->inner_iters == 0;
+  const double gam = ps->rz;
+  const double beta = first ? 0.0 : gam / ps->rz_old;
+  const double alpha = first ? gam / ps->delta : gam / (ps->delta - beta * gam / ps->alpha);
+  const float fb = float(beta), fa = float(alpha), zm = float(ps->zmean);
   float rr = 0.f;
-  GRID_STRIDE(n, nn) {
-    const float p = a.p_new[n];
-    a.e[n] += alpha * p;
-    const float r = a.r32[n] - alpha * a.q[n];
-    a.r32[n] = r;
-    a.p_old[n] = p;
-    rr = fmaf(r, r, rr);
+  VEC_BATCHES(base, nn) {
+    float z[kVB], w[kVB], p[kVB], q[kVB], e[kVB], r[kVB];
+    VEC_NODES(k, n, base, nn) {
+      z[k] = a.z[n];
+      w[k] = a.w[n];
+      p[k] = a.p[n];
+      q[k] = a.q[n];
+      e[k] = a.e[n];
+      r[k] = a.r32[n];
+    }
+    VEC_NODES(k, n, base, nn) {
+      const float pn = (z[k] - zm) + fb * p[k];
+      const float qn = w[k] + fb * q[k];
+      a.p[n] = pn;
+      a.q[n] = qn;
+      a.e[n] = e[k] + fa * pn;
+      const float rn = r[k] - fa * qn;
+      a.r32[n] = rn;
+      rr = fmaf(rn, rn, rr);
+    }
   }
   double v[1] = {rr};
   if (grid_sum<1>(v, a.part, a.ticket) && threadIdx.x == 0) {
+    ps->rz_old = gam;
+    ps->alpha = alpha;
+    ps->beta = beta;
     ps->rr = v[0];
     ps->inner_iters += 1;
     ps->total_iters += 1;
@@ -382,8 +466,19 @@ __global__ void k_update(FineArgs a) {
 __global__ void k_correct(FineArgs a) {
   pdl_enter();
   if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->outer_iters += 1;
-  GRID_STRIDE(n, a.g.nxn * a.g.nyn) {
-    if (a.flags[n] & kFree) a.phi[n] += double(a.e[n]);
+  const int nn = a.g.nxn * a.g.nyn;
+  VEC_BATCHES(base, nn) {
+    double p[kVB];
+    float e[kVB];
+    uint8_t fl[kVB];
+    VEC_NODES(k, n, base, nn) {
+      fl[k] = a.flags[n];
+      p[k] = a.phi[n];
+      e[k] = a.e[n];
+    }
+    VEC_NODES(k, n, base, nn) {
+      if (fl[k] & kFree) a.phi[n] = p[k] + double(e[k]);
+    }
   }
 }
 
@@ -399,20 +494,34 @@ __global__ void k_field(FineArgs a) {
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
   double v[1] = {0.0};
-  GRID_STRIDE(n, nn) {
-    const uint8_t f = a.flags[n];
-    const int i = n / g.nyn, j = n - (n / g.nyn) * g.nyn;
-    const double p = a.phi[n];
-    double sx = 0.0, sy = 0.0;
-    int cx = 0, cy = 0;
-    if (f & kOpenXm) { sx += p - a.phi[(g.px ? wrapi(i - 1, g.nxn) : i - 1) * g.nyn + j]; ++cx; }
-    if (f & kOpenXp) { sx += a.phi[(g.px ? wrapi(i + 1, g.nxn) : i + 1) * g.nyn + j] - p; ++cx; }
-    if (f & kOpenYm) { sy += p - a.phi[i * g.nyn + (g.py ? wrapi(j - 1, g.nyn) : j - 1)]; ++cy; }
-    if (f & kOpenYp) { sy += a.phi[i * g.nyn + (g.py ? wrapi(j + 1, g.nyn) : j + 1)] - p; ++cy; }
-    const float ex = float(cx == 2 ? -0.5 * sx : (cx ? -sx : 0.0));
-    const float ey = float(cy == 2 ? -0.5 * sy : (cy ? -sy : 0.0));
-    a.E[n] = make_float2(ex, ey);
-    v[0] += double(fmaf(ex, ex, ey * ey));
+  VEC_BATCHES(base, nn) {
+    double ph[kVB][5];
+    uint8_t fl[kVB];
+    VEC_NODES(k, n, base, nn) {
+      // neighbour indices clamped to the box; the edge flags say which count
+      int xm, xp, ym, yp;
+      nbr_index(g, n, xm, xp, ym, yp);
+      fl[k] = a.flags[n];
+      ph[k][0] = a.phi[n];
+      ph[k][1] = a.phi[xm];
+      ph[k][2] = a.phi[xp];
+      ph[k][3] = a.phi[ym];
+      ph[k][4] = a.phi[yp];
+    }
+    VEC_NODES(k, n, base, nn) {
+      const uint8_t f = fl[k];
+      const double p = ph[k][0];
+      double sx = 0.0, sy = 0.0;
+      int cx = 0, cy = 0;
+      if (f & kOpenXm) { sx += p - ph[k][1]; ++cx; }
+      if (f & kOpenXp) { sx += ph[k][2] - p; ++cx; }
+      if (f & kOpenYm) { sy += p - ph[k][3]; ++cy; }
+      if (f & kOpenYp) { sy += ph[k][4] - p; ++cy; }
+      const float ex = float(cx == 2 ? -0.5 * sx : (cx ? -sx : 0.0));
+      const float ey = float(cy == 2 ? -0.5 * sy : (cy ? -sy : 0.0));
+      a.E[n] = make_float2(ex, ey);
+      v[0] += double(fmaf(ex, ex, ey * ey));
+    }
   }
   if (grid_sum<1>(v, a.part, a.ticket) && threadIdx.x == 0) a.fe[0] = 0.5 * v[0];
 }
@@ -437,7 +546,8 @@ struct MGArgs {
   const float *cinv;     // [ncoarse][ncoarse]
   const int *cidx;       // node index of each coarsest unknown
   PoissonState *ps;
-  double *part;          // grid reduction of <r, z> fused into the level-0 post-smoothing
+  float *w0;             // level 0: w = A z, formed by the post-smoothing
+  double *part;          // its grid reduction of the PCG inner products
   unsigned int *ticket;
   int singular;
 };
@@ -512,18 +622,15 @@ __device__ __forceinline__ float resid_node(const LevelDev &L, int i, int j) {
   return L.f[n] - (d * L.u[n] + off);
 }
 
-// Full weighting of the fine residual onto coarse node (I, J).  It follows a
-// forward sweep whose last colour has no neighbour of its own colour, so the
-// residual there is zero (up to rounding) and is not evaluated: the black
-// nodes, (a + b) odd, on the red-black level and the corners, a and b odd, on
-// the four-colour levels.  Five of the nine fine residuals remain.
+// Full weighting of the fine residual onto coarse node (I, J) (0 where the
+// coarse node is not an unknown).  It follows a forward sweep whose last
+// colour has no neighbour of its own colour, so the residual there is zero up
+// to rounding and is not evaluated: the black nodes, (a + b) odd, on the
+// red-black level and the corners, a and b odd, on the four-colour levels.
+// Five of the nine fine residuals remain.
 template <bool FINE>
-__device__ __forceinline__ void restrict_node(const LevelDev &F, const LevelDev &C, int I, int J) {
-  const int nc = I * C.nyn + J;
-  if (!is_free<false>(C, nc)) {
-    C.f[nc] = 0.f;
-    return;
-  }
+__device__ __forceinline__ float restrict_value(const LevelDev &F, const LevelDev &C, int I, int J) {
+  if (!is_free<false>(C, I * C.nyn + J)) return 0.f;
   float s = 0.f;
 #pragma unroll
   for (int a = -1; a <= 1; ++a) {
@@ -536,7 +643,7 @@ __device__ __forceinline__ void restrict_node(const LevelDev &F, const LevelDev 
       s = fmaf(w, resid_node<FINE>(F, i, j), s);
     }
   }
-  C.f[nc] = s * (1.f / 16.f);
+  return s * (1.f / 16.f);
 }
 
 // bilinear prolongation of the coarse correction, added on free fine nodes
@@ -595,25 +702,31 @@ __device__ void cta_zero(const LevelDev L) {
   __syncthreads();
 }
 
-// pre (forward) or post (reverse) smoothing: one sweep over all colours
+// forward sweep from colour c0, or a reverse sweep over all colours
 template <bool FINE>
-__device__ void cta_smooth(const LevelDev L, bool forward, bool zero_start) {
-  const int nc = FINE ? 2 : 4;
-  if (forward) {
-    if (zero_start) cta_zero<FINE>(L);
-    for (int c = zero_start ? 1 : 0; c < nc; ++c) cta_sweep<FINE>(L, c);
-  } else {
-    for (int c = nc - 1; c >= 0; --c) cta_sweep<FINE>(L, c);
-  }
+__device__ void cta_forward(const LevelDev L, int c0) {
+  for (int c = c0; c < (FINE ? 2 : 4); ++c) cta_sweep<FINE>(L, c);
 }
 
 template <bool FINE>
-__device__ void cta_restrict(const LevelDev F, const LevelDev C) {
+__device__ void cta_backward(const LevelDev L) {
+  for (int c = (FINE ? 1 : 3); c >= 0; --c) cta_sweep<FINE>(L, c);
+}
+
+// Restriction to level C; with `start` also the first half sweep of C from
+// zero (colour 0 gets f / diag, the rest 0), which needs only the node's own f.
+template <bool FINE>
+__device__ void cta_restrict(const LevelDev F, const LevelDev C, bool start) {
   const int nn = C.nxn * C.nyn;
   const float r = __frcp_rn(float(C.nyn));
   for (int n = threadIdx.x; n < nn; n += blockDim.x) {
-    const int I = div_small(n, r);
-    restrict_node<FINE>(F, C, I, n - I * C.nyn);
+    const int I = div_small(n, r), J = n - I * C.nyn;
+    const float v = restrict_value<FINE>(F, C, I, J);
+    C.f[n] = v;
+    if (start) {
+      const int sid = C.sid[n];
+      C.u[n] = (((I | J) & 1) == 0 && sid) ? v * C.stab[kSt * (sid - 1) + 9] : 0.f;
+    }
   }
   __syncthreads();
 }
@@ -647,13 +760,16 @@ __device__ void cta_prolong(const LevelDev F, const LevelDev C) {
 // growing by one per colour: a node at margin m reads neighbours at margin
 // m - 1 or more, all of which the earlier colours have finished.
 template <bool FINE> struct TileShape;
+// H: halo of the pre-smoothing region, HP: of the post-smoothing region (one
+// more on the red-black level, whose post-smoothing also forms w = A z)
 template <> struct TileShape<true> {
-  static constexpr int H = 2, TI = 8, TJ = 32, PI = 16, PJ = 64;
+  static constexpr int H = 2, HP = 3, TI = 8, TJ = 32, PI = 16, PJ = 64;
 };
 template <> struct TileShape<false> {
-  static constexpr int H = 4, TI = 8, TJ = 16, PI = 16, PJ = 32;
+  static constexpr int H = 4, HP = 4, TI = 16, TJ = 16, PI = 16, PJ = 32;
 };
 constexpr int kTileThreads = 256;
+constexpr int kTileStencils = 128;   // coarse stencil tables up to this size are staged in shared memory
 
 template <bool FINE>
 using NodeCode = typename std::conditional<FINE, uint8_t, uint16_t>::type;
@@ -684,7 +800,7 @@ __device__ __forceinline__ float tile_off(const Tile<FINE> &T, int t, float &d, 
     return -(u[t - w] + u[t + w] + u[t - 1] + u[t + 1]);
   } else {
     const float4 *s4 = reinterpret_cast<const float4 *>(T.stab + kSt * (int(T.code[t]) - 1));
-    const float4 a = __ldg(s4), b = __ldg(s4 + 1), c = __ldg(s4 + 2);
+    const float4 a = s4[0], b = s4[1], c = s4[2];   // shared or global (large tables)
     d = b.x;
     rd = c.y;
     float acc = a.x * u[t - w - 1];
@@ -707,17 +823,24 @@ __device__ __forceinline__ float tile_resid(const Tile<FINE> &T, int t) {
   return T.f[t] - (d * T.u[t] + off);
 }
 
-template <bool FINE>
-__device__ void tile_sweep(const Tile<FINE> &T, int c, int m) {
-  const int n = T.rh * T.rw;
-  const float rrw = __frcp_rn(float(T.rw));
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    const int ri = div_small(t, rrw), rj = t - ri * T.rw;
-    if (ri < m || ri >= T.rh - m || rj < m || rj >= T.rw - m) continue;
-    if (tile_colour<FINE>(T, ri, rj) != c || !T.code[t]) continue;
+// One colour of a sweep on the region nodes at margin M or more; the threads
+// are mapped onto the nodes of that colour only.
+template <bool FINE, int RH, int RW, int M>
+__device__ void tile_sweep(const Tile<FINE> &T, int c) {
+  constexpr int W = (RW - 2 * M + 1) / 2;               // colour nodes per row (at most)
+  constexpr int NR = FINE ? RH - 2 * M : (RH - 2 * M + 1) / 2;
+  const int oi = ((c >> 1) - T.gi0 - M) & 1;             // four-colour row offset
+  const int oj = FINE ? 0 : ((c & 1) - T.gj0 - M) & 1;
+  for (int t = threadIdx.x; t < NR * W; t += blockDim.x) {
+    const int a = t / W, b = t - a * W;
+    const int ri = FINE ? M + a : M + 2 * a + oi;
+    const int rj = FINE ? M + 2 * b + ((c - T.gi0 - ri - T.gj0 - M) & 1) : M + 2 * b + oj;
+    if (ri >= RH - M || rj >= RW - M) continue;
+    const int n = ri * RW + rj;
+    if (!T.code[n]) continue;
     float d, rd;
-    const float off = tile_off<FINE>(T, t, d, rd);
-    T.u[t] = (T.f[t] - off) * rd;
+    const float off = tile_off<FINE>(T, n, d, rd);
+    T.u[n] = (T.f[n] - off) * rd;
   }
   __syncthreads();
 }
@@ -727,85 +850,141 @@ __device__ __forceinline__ int wrap_mod(int a, int n) {
   return a < 0 ? a + n : a;
 }
 
-// Fills the region from level F.  PRE: u = 0 except the first colour, which
-// gets f / diag (the first half of the sweep from zero).  Otherwise u = upre
-// plus the bilinear prolongation of level C's u, on the free nodes.
-template <bool FINE, bool PRE>
-__device__ void tile_load(const LevelDev &F, const LevelDev &C, const Tile<FINE> &T) {
-  const int n = T.rh * T.rw;
-  const float rrw = __frcp_rn(float(T.rw));
-  for (int t = threadIdx.x; t < n; t += blockDim.x) {
-    const int ri = div_small(t, rrw), rj = t - ri * T.rw;
+// Coarse nodes under a fine region: rows from gi0 >> 1 to ((gi0 + RH - 1) >> 1) + 1.
+template <int RH, int RW> struct CoarseBlock {
+  static constexpr int CH = RH / 2 + 2, CW = RW / 2 + 2;
+};
+
+// Fills the region from level F in two parts.  Before the wait for the
+// preceding kernel, the parts that never change during a solve: each node's
+// free flag / stencil id and the stencil table.  After it: PRE: u = 0 except
+// the first colour, which gets f / diag (the first half of the sweep from
+// zero); otherwise u = upre plus the bilinear prolongation of level C's u
+// (staged in cblk), on the free nodes.  Each thread takes K region nodes and
+// issues all their loads before using any.  Returns false when the inner
+// solve is already done.
+template <bool FINE, bool PRE, int RH, int RW>
+__device__ bool tile_load(const MGArgs &a, const LevelDev &F, const LevelDev &C, int nst,
+                          Tile<FINE> &T, float *tab, float *cblk) {
+  constexpr int N = RH * RW, K = (N + kTileThreads - 1) / kTileThreads;
+  using CB = CoarseBlock<RH, RW>;
+  int g[K], code[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int t = threadIdx.x + k * kTileThreads;
+    const int ri = t / RW, rj = t - ri * RW;
     int gi = T.gi0 + ri, gj = T.gj0 + rj;
-    bool in = true;
+    bool in = t < N;
     if (F.px) gi = wrap_mod(gi, F.nxn);
-    else in = gi >= 0 && gi < F.nxn;
+    else in = in && gi >= 0 && gi < F.nxn;
     if (F.py) gj = wrap_mod(gj, F.nyn);
     else in = in && gj >= 0 && gj < F.nyn;
-    int code = 0;
-    float f = 0.f, u = 0.f;
-    if (in) {
-      const int g = gi * F.nyn + gj;
-      code = FINE ? int(F.free[g]) : int(F.sid[g]);
-      f = F.f[g];
-      if (code) {
-        if (PRE) {
-          if (tile_colour<FINE>(T, ri, rj) == 0)
-            u = f * (FINE ? 0.25f : __ldg(F.stab + kSt * (code - 1) + 9));
-        } else {
-          const int I0 = gi >> 1, J0 = gj >> 1;
-          const int I1 = (gi & 1) ? (C.px ? wrapi(I0 + 1, C.nxn) : I0 + 1) : I0;
-          const int J1 = (gj & 1) ? (C.py ? wrapi(J0 + 1, C.nyn) : J0 + 1) : J0;
-          const float v = 0.25f * (C.u[I0 * C.nyn + J0] + C.u[I1 * C.nyn + J0] +
-                                   C.u[I0 * C.nyn + J1] + C.u[I1 * C.nyn + J1]);
-          u = F.upre[g] + v;
-        }
+    g[k] = in ? gi * F.nyn + gj : -1;
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) code[k] = g[k] >= 0 ? (FINE ? int(F.free[g[k]]) : int(F.sid[g[k]])) : 0;
+  if (!FINE && nst <= kTileStencils) {
+    for (int q = threadIdx.x; q < nst * kSt; q += blockDim.x) tab[q] = F.stab[q];
+    T.stab = tab;
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int t = threadIdx.x + k * kTileThreads;
+    if (t < N) T.code[t] = NodeCode<FINE>(code[k]);
+  }
+  __syncthreads();
+  pdl_enter();
+  if (a.ps->inner_done) return false;
+  float f[K], up[K];
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    f[k] = 0.f;
+    up[k] = 0.f;
+    if (g[k] >= 0) {
+      f[k] = F.f[g[k]];
+      if (!PRE) up[k] = F.upre[g[k]];
+    }
+  }
+  const int ci0 = T.gi0 >> 1, cj0 = T.gj0 >> 1;   // floor division
+  if (!PRE) {
+    for (int q = threadIdx.x; q < CB::CH * CB::CW; q += blockDim.x) {
+      const int ca = q / CB::CW;
+      int I = ci0 + ca, J = cj0 + (q - ca * CB::CW);
+      bool in = true;
+      if (C.px) I = wrap_mod(I, C.nxn);
+      else in = I >= 0 && I < C.nxn;
+      if (C.py) J = wrap_mod(J, C.nyn);
+      else in = in && J >= 0 && J < C.nyn;
+      cblk[q] = in ? C.u[I * C.nyn + J] : 0.f;
+    }
+    __syncthreads();
+  }
+#pragma unroll
+  for (int k = 0; k < K; ++k) {
+    const int t = threadIdx.x + k * kTileThreads;
+    if (t >= N) break;
+    const int ri = t / RW, rj = t - ri * RW;
+    float u = 0.f;
+    if (code[k]) {
+      if (PRE) {
+        if (tile_colour<FINE>(T, ri, rj) == 0)
+          u = f[k] * (FINE ? 0.25f : T.stab[kSt * (code[k] - 1) + 9]);
+      } else {
+        const int gi = T.gi0 + ri, gj = T.gj0 + rj;
+        const int a0 = (gi >> 1) - ci0, b0 = (gj >> 1) - cj0;
+        const int a1 = a0 + (gi & 1), b1 = b0 + (gj & 1);
+        u = up[k] + 0.25f * (cblk[a0 * CB::CW + b0] + cblk[a1 * CB::CW + b0] +
+                             cblk[a0 * CB::CW + b1] + cblk[a1 * CB::CW + b1]);
       }
     }
-    T.code[t] = NodeCode<FINE>(code);
-    T.f[t] = f;
+    T.f[t] = f[k];
     T.u[t] = u;
   }
   __syncthreads();
+  return true;
 }
 
 template <bool FINE>
 __global__ void __launch_bounds__(kTileThreads) k_pre(MGArgs a, int l) {
-  pdl_enter();
-  if (a.ps->inner_done) return;
   using S = TileShape<FINE>;
+  static_assert(S::TI * S::TJ == kTileThreads, "one coarse node per thread");
   constexpr int RH = 2 * S::TI + 1 + 2 * S::H, RW = 2 * S::TJ + 1 + 2 * S::H;
   __shared__ float su[RH * RW], sf[RH * RW];
   __shared__ NodeCode<FINE> sc[RH * RW];
+  __shared__ __align__(16) float tab[FINE ? 4 : kTileStencils * kSt];
   const LevelDev F = a.L[l], C = a.L[l + 1];
   const int tcj = (C.nyn + S::TJ - 1) / S::TJ;
   const int I0 = (blockIdx.x / tcj) * S::TI, J0 = (blockIdx.x % tcj) * S::TJ;
-  const Tile<FINE> T{2 * I0 - 1 - S::H, 2 * J0 - 1 - S::H, RH, RW, su, sf, sc, F.stab};
-  tile_load<FINE, true>(F, C, T);
-  for (int c = 1; c < (FINE ? 2 : 4); ++c) tile_sweep<FINE>(T, c, c);
+  // this thread's coarse node and whether it is an unknown (static)
+  const int I = I0 + int(threadIdx.x) / S::TJ, J = J0 + int(threadIdx.x) % S::TJ;
+  const bool own = I < C.nxn && J < C.nyn;
+  const bool cfree = own && C.sid[I * C.nyn + J] != 0;
+  Tile<FINE> T{2 * I0 - 1 - S::H, 2 * J0 - 1 - S::H, RH, RW, su, sf, sc, F.stab};
+  if (!tile_load<FINE, true, RH, RW>(a, F, C, a.nst[l], T, tab, nullptr)) return;
+  tile_sweep<FINE, RH, RW, 1>(T, 1);
+  if (!FINE) {
+    tile_sweep<FINE, RH, RW, 2>(T, 2);
+    tile_sweep<FINE, RH, RW, 3>(T, 3);
+  }
   // Restriction.  The last colour has no neighbour of its own colour, so its
   // residual after the sweep is zero up to rounding and is skipped: the black
   // nodes, (a + b) odd, on the red-black level and the corners, a and b odd,
   // on the four-colour levels.  Five of the nine fine residuals remain.
-  for (int k = threadIdx.x; k < S::TI * S::TJ; k += blockDim.x) {
-    const int I = I0 + k / S::TJ, J = J0 + k % S::TJ;
-    if (I >= C.nxn || J >= C.nyn) continue;
-    const int nc = I * C.nyn + J;
-    if (!C.sid[nc]) {
-      C.f[nc] = 0.f;
-      continue;
-    }
-    const int t0 = (2 * (I - I0) + 1 + S::H) * RW + 2 * (J - J0) + 1 + S::H;
+  if (own) {
     float sum = 0.f;
+    if (cfree) {
+      const int t0 = (2 * (I - I0) + 1 + S::H) * RW + 2 * (J - J0) + 1 + S::H;
 #pragma unroll
-    for (int da = -1; da <= 1; ++da)
+      for (int da = -1; da <= 1; ++da)
 #pragma unroll
-      for (int db = -1; db <= 1; ++db) {
-        if (FINE ? ((da + db) & 1) != 0 : (da != 0 && db != 0)) continue;
-        const float w = (da == 0 ? 2.f : 1.f) * (db == 0 ? 2.f : 1.f);
-        sum = fmaf(w, tile_resid<FINE>(T, t0 + da * RW + db), sum);
-      }
-    C.f[nc] = sum * (1.f / 16.f);
+        for (int db = -1; db <= 1; ++db) {
+          if (FINE ? ((da + db) & 1) != 0 : (da != 0 && db != 0)) continue;
+          const float w = (da == 0 ? 2.f : 1.f) * (db == 0 ? 2.f : 1.f);
+          sum = fmaf(w, tile_resid<FINE>(T, t0 + da * RW + db), sum);
+        }
+      sum *= 1.f / 16.f;
+    }
+    C.f[I * C.nyn + J] = sum;
   }
   // the swept u of the fine nodes this tile owns
   for (int k = threadIdx.x; k < 4 * S::TI * S::TJ; k += blockDim.x) {
@@ -817,43 +996,52 @@ __global__ void __launch_bounds__(kTileThreads) k_pre(MGArgs a, int l) {
 
 template <bool FINE>
 __global__ void __launch_bounds__(kTileThreads) k_post(MGArgs a, int l) {
-  pdl_enter();
-  if (a.ps->inner_done) return;
   using S = TileShape<FINE>;
-  constexpr int RH = S::PI + 2 * S::H, RW = S::PJ + 2 * S::H;
+  constexpr int RH = S::PI + 2 * S::HP, RW = S::PJ + 2 * S::HP;
   __shared__ float su[RH * RW], sf[RH * RW];
   __shared__ NodeCode<FINE> sc[RH * RW];
+  __shared__ __align__(16) float tab[FINE ? 4 : kTileStencils * kSt];
+  __shared__ float cblk[CoarseBlock<RH, RW>::CH * CoarseBlock<RH, RW>::CW];
   const LevelDev F = a.L[l], C = a.L[l + 1];
   const int tpj = (F.nyn + S::PJ - 1) / S::PJ;
   const int P0 = (blockIdx.x / tpj) * S::PI, Q0 = (blockIdx.x % tpj) * S::PJ;
-  const Tile<FINE> T{P0 - S::H, Q0 - S::H, RH, RW, su, sf, sc, F.stab};
-  tile_load<FINE, false>(F, C, T);
-  for (int c = (FINE ? 1 : 3), m = 1; c >= 0; --c, ++m) tile_sweep<FINE>(T, c, m);
-  float rz = 0.f, zs = 0.f, rs = 0.f;
+  Tile<FINE> T{P0 - S::HP, Q0 - S::HP, RH, RW, su, sf, sc, F.stab};
+  if (!tile_load<FINE, false, RH, RW>(a, F, C, a.nst[l], T, tab, cblk)) return;
+  if (FINE) {
+    tile_sweep<FINE, RH, RW, 1>(T, 1);
+    tile_sweep<FINE, RH, RW, 2>(T, 0);
+  } else {
+    tile_sweep<FINE, RH, RW, 1>(T, 3);
+    tile_sweep<FINE, RH, RW, 2>(T, 2);
+    tile_sweep<FINE, RH, RW, 3>(T, 1);
+    tile_sweep<FINE, RH, RW, 4>(T, 0);
+  }
+  float s[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
   for (int k = threadIdx.x; k < S::PI * S::PJ; k += blockDim.x) {
     const int ri = k / S::PJ, rj = k % S::PJ;
     const int i = P0 + ri, j = Q0 + rj;
     if (i >= F.nxn || j >= F.nyn) continue;
-    const int t = (ri + S::H) * RW + rj + S::H;
+    const int t = (ri + S::HP) * RW + rj + S::HP;
     const float z = su[t];
-    F.u[i * F.nyn + j] = z;
+    const int n = i * F.nyn + j;
+    F.u[n] = z;
     if (FINE) {
+      // w = A z (z is zero on the Dirichlet nodes and outside the box)
+      const float w = sc[t] ? 4.f * z - (su[t - RW] + su[t + RW] + su[t - 1] + su[t + 1]) : 0.f;
+      a.w0[n] = w;
       const float r = sf[t];
-      rz = fmaf(r, z, rz);
-      zs += z;
-      rs += r;
+      s[0] = fmaf(r, z, s[0]);
+      s[1] += z;
+      s[2] += r;
+      s[3] = fmaf(z, w, s[3]);
+      s[4] += w;
     }
   }
   if (!FINE) return;
-  // level 0: u is the preconditioned residual z; rz = <r, z - zmean>
-  double v[3] = {rz, zs, rs};
-  if (grid_sum<3>(v, a.part, a.ticket) && threadIdx.x == 0) {
-    PoissonState *ps = a.ps;
-    const double zm = a.singular ? v[1] / double(F.nxn * F.nyn) : 0.0;
-    ps->zmean = zm;
-    ps->rz_old = ps->rz;
-    ps->rz = v[0] - zm * v[2];
-  }
+  // level 0: u is the preconditioned residual z; the PCG scalars of the next step
+  double v[5] = {s[0], s[1], s[2], s[3], s[4]};
+  if (grid_sum<5>(v, a.part, a.ticket) && threadIdx.x == 0)
+    store_gamma_delta(a.ps, v, a.singular, F.nxn * F.nyn);
 }
 
 int pre_tiles(const MGLevel &C, bool fine) {
@@ -866,6 +1054,22 @@ int post_tiles(const MGLevel &F, bool fine) {
   const int pi = fine ? TileShape<true>::PI : TileShape<false>::PI;
   const int pj = fine ? TileShape<true>::PJ : TileShape<false>::PJ;
   return ((F.nxn + pi - 1) / pi) * ((F.nyn + pj - 1) / pj);
+}
+
+// Asynchronous global -> shared copy of `bytes` (a multiple of 16, both
+// addresses 16-byte aligned) in 16-byte pieces spread over the block; all of
+// a block's copies are in flight together and cta_copy_wait ends them.
+__device__ __forceinline__ void cta_copy_async(void *dst, const void *src, size_t bytes) {
+  const unsigned d = unsigned(__cvta_generic_to_shared(dst));
+  const char *g = static_cast<const char *>(src);
+  for (size_t k = size_t(threadIdx.x) * 16; k < bytes; k += size_t(blockDim.x) * 16)
+    asm volatile("cp.async.cg.shared.global [%0], [%1], 16;\n" ::"r"(d + unsigned(k)), "l"(g + k)
+                 : "memory");
+}
+
+__device__ __forceinline__ void cta_copy_wait() {
+  asm volatile("cp.async.wait_all;\n" ::: "memory");
+  __syncthreads();
 }
 
 template <typename T>
@@ -889,77 +1093,94 @@ size_t coarse_smem_bytes(const MGArgs &a) {
 }
 
 __global__ void __launch_bounds__(kCoarseThreads) k_coarse(MGArgs a) {
-  pdl_enter();
-  if (a.ps->inner_done) return;
   extern __shared__ __align__(16) unsigned char smem[];
+  // level descriptors pointing into shared memory: one copy for the block
+  __shared__ LevelDev S[16];
   const int lc = a.lc, last = a.nlev - 1;
-  LevelDev S[16];
+  const int nc = a.ncoarse;
+  // stage the level tables and the coarsest inverse (they do not change
+  // during a solve, so before the wait for the preceding kernel), then the
+  // first level's f
   unsigned char *p = smem;
   for (int l = lc; l <= last; ++l) {
-    S[l] = a.L[l];
-    const int nn = S[l].nxn * S[l].nyn;
-    S[l].u = carve<float>(p, nn);
-    S[l].f = carve<float>(p, nn);
+    LevelDev L = a.L[l];
+    const size_t nn = size_t(L.nxn) * L.nyn;
+    L.u = carve<float>(p, nn);
+    L.f = carve<float>(p, nn);
     if (l == 0) {
       uint8_t *fr = carve<uint8_t>(p, nn);
-      for (int n = threadIdx.x; n < nn; n += blockDim.x) fr[n] = a.L[0].free[n];
-      S[l].free = fr;
+      cta_copy_async(fr, a.L[0].free, pad16(nn));
+      L.free = fr;
     } else {
       uint16_t *sid = carve<uint16_t>(p, nn);
       float *tab = carve<float>(p, size_t(a.nst[l]) * kSt);
-      for (int n = threadIdx.x; n < nn; n += blockDim.x) sid[n] = a.L[l].sid[n];
-      for (int k = threadIdx.x; k < a.nst[l] * kSt; k += blockDim.x) tab[k] = a.L[l].stab[k];
-      S[l].sid = sid;
-      S[l].stab = tab;
+      cta_copy_async(sid, a.L[l].sid, pad16(nn * 2));
+      cta_copy_async(tab, a.L[l].stab, size_t(a.nst[l]) * kSt * 4);
+      L.sid = sid;
+      L.stab = tab;
     }
+    if (threadIdx.x == 0) S[l] = L;
   }
-  const int nc = a.ncoarse;
+  __syncthreads();
   float *cinv = carve<float>(p, size_t(nc) * nc);
   int *cidx = carve<int>(p, nc);
-  for (int k = threadIdx.x; k < nc * nc; k += blockDim.x) cinv[k] = a.cinv[k];
-  for (int k = threadIdx.x; k < nc; k += blockDim.x) cidx[k] = a.cidx[k];
-  {
-    const int nn = S[lc].nxn * S[lc].nyn;
-    for (int n = threadIdx.x; n < nn; n += blockDim.x) S[lc].f[n] = a.L[lc].f[n];
-    __syncthreads();
+  if (nc > 0) {
+    cta_copy_async(cinv, a.cinv, pad16(size_t(nc) * nc * 4));
+    cta_copy_async(cidx, a.cidx, pad16(size_t(nc) * 4));
+    // the dense solve writes the unknowns only
+    const int nn = S[last].nxn * S[last].nyn;
+    for (int n = threadIdx.x; n < nn; n += blockDim.x) S[last].u[n] = 0.f;
   }
+  pdl_enter();
+  if (a.ps->inner_done) {
+    asm volatile("cp.async.wait_all;\n" ::: "memory");
+    return;
+  }
+  {
+    const LevelDev &L = S[lc];
+    cta_copy_async(L.f, a.L[lc].f, pad16(size_t(L.nxn) * L.nyn * 4));
+  }
+  cta_copy_wait();
+  if (lc == 0) cta_zero<true>(S[lc]);
+  else cta_zero<false>(S[lc]);
   for (int l = lc; l < last; ++l) {
+    const bool start = !(l + 1 == last && nc > 0);
     if (l == 0) {
-      cta_smooth<true>(S[l], true, true);
-      cta_restrict<true>(S[l], S[l + 1]);
+      cta_forward<true>(S[l], 1);
+      cta_restrict<true>(S[l], S[l + 1], start);
     } else {
-      cta_smooth<false>(S[l], true, true);
-      cta_restrict<false>(S[l], S[l + 1]);
+      cta_forward<false>(S[l], 1);
+      cta_restrict<false>(S[l], S[l + 1], start);
     }
   }
   if (nc > 0) {
-    // coarsest level: exact solve by the precomputed (pseudo-)inverse
+    // coarsest level: exact solve by the precomputed (pseudo-)inverse, a warp per row
     const LevelDev &L = S[last];
-    const int nn = L.nxn * L.nyn;
-    for (int n = threadIdx.x; n < nn; n += blockDim.x) L.u[n] = 0.f;
-    __syncthreads();
-    for (int r = threadIdx.x; r < nc; r += blockDim.x) {
+    const int lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+    for (int r = threadIdx.x >> 5; r < nc; r += nw) {
       float acc = 0.f;
-      for (int k = 0; k < nc; ++k) acc = fmaf(cinv[r * nc + k], L.f[cidx[k]], acc);
-      L.u[cidx[r]] = acc;
+      for (int k = lane; k < nc; k += 32) acc = fmaf(cinv[r * nc + k], L.f[cidx[k]], acc);
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+      if (lane == 0) L.u[cidx[r]] = acc;
     }
     __syncthreads();
   } else if (last == 0) {
-    cta_smooth<true>(S[last], true, true);
-    for (int s = 1; s < kCoarsestSweeps; ++s) cta_smooth<true>(S[last], true, false);
-    for (int s = 0; s < kCoarsestSweeps; ++s) cta_smooth<true>(S[last], false, false);
+    cta_forward<true>(S[last], 1);
+    for (int s = 1; s < kCoarsestSweeps; ++s) cta_forward<true>(S[last], 0);
+    for (int s = 0; s < kCoarsestSweeps; ++s) cta_backward<true>(S[last]);
   } else {
-    cta_smooth<false>(S[last], true, true);
-    for (int s = 1; s < kCoarsestSweeps; ++s) cta_smooth<false>(S[last], true, false);
-    for (int s = 0; s < kCoarsestSweeps; ++s) cta_smooth<false>(S[last], false, false);
+    cta_forward<false>(S[last], 1);
+    for (int s = 1; s < kCoarsestSweeps; ++s) cta_forward<false>(S[last], 0);
+    for (int s = 0; s < kCoarsestSweeps; ++s) cta_backward<false>(S[last]);
   }
   for (int l = last - 1; l >= lc; --l) {
     if (l == 0) {
       cta_prolong<true>(S[l], S[l + 1]);
-      cta_smooth<true>(S[l], false, false);
+      cta_backward<true>(S[l]);
     } else {
       cta_prolong<false>(S[l], S[l + 1]);
-      cta_smooth<false>(S[l], false, false);
+      cta_backward<false>(S[l]);
     }
   }
   const int nn = S[lc].nxn * S[lc].nyn;
@@ -988,8 +1209,8 @@ FineArgs fine_args(pic_ctx *c) {
   a.surface = c->cfg.surface_charge;
   a.r32 = c->d_r32;
   a.z = c->d_z;
-  a.p_old = c->d_p0;
-  a.p_new = c->d_p1;
+  a.p = c->d_p;
+  a.w = c->d_w;
   a.q = c->d_q;
   a.e = c->d_e;
   a.ps = c->d_ps;
@@ -1030,6 +1251,7 @@ MGArgs mg_args(pic_ctx *c) {
   a.cinv = c->d_cinv;
   a.cidx = c->d_cidx;
   a.ps = c->d_ps;
+  a.w0 = c->d_w;
   a.part = c->red.part;
   a.ticket = c->red.ticket;
   a.singular = c->singular;
@@ -1056,10 +1278,11 @@ void launch_vcycle(pic_ctx *c, const MGArgs &a) {
   c->launches += 2 * c->lc + 1;
 }
 
-// <r, z> after a V-cycle that did not form it (every level in one CTA)
-void launch_rz(pic_ctx *c, const FineArgs &f) {
+// w = A z and the PCG scalars after a V-cycle that did not form them (every
+// level in one CTA)
+void launch_zw(pic_ctx *c, const FineArgs &f) {
   if (c->lc > 0) return;
-  launch(k_rz, c->red.nblocks, kThreads, 0, c->stream, f);
+  launch(k_zw, c->red.nblocks, kThreads, 0, c->stream, f);
   c->launches += 1;
 }
 
@@ -1151,6 +1374,10 @@ cudaError_t poisson_setup(pic_ctx *c) {
   sts.push_back(s0);
   c->lev.push_back(L0);
   while (c->lev.size() < 16) {
+    // a level with at most kDenseCoarsest unknowns is solved exactly: stop there
+    size_t unknowns = 0;
+    for (uint8_t v : masks.back()) unknowns += v;
+    if (unknowns <= size_t(kDenseCoarsest)) break;
     const MGLevel &F = c->lev.back();
     const bool even = (F.nx % 2 == 0) && (F.ny % 2 == 0);
     if (!even) break;
@@ -1190,7 +1417,7 @@ cudaError_t poisson_setup(pic_ctx *c) {
     m.stab = nullptr;
     m.nst = 0;
     if (l == 0) {
-      m.free = (uint8_t *)dev_alloc(c, n);
+      m.free = (uint8_t *)dev_alloc(c, pad16(n));
       if (!m.free) return cudaErrorMemoryAllocation;
       cudaMemcpy(m.free, masks[0].data(), n, cudaMemcpyHostToDevice);
       m.u = nullptr;
@@ -1223,15 +1450,15 @@ cudaError_t poisson_setup(pic_ctx *c) {
       for (int q = 0; q < 9; ++q) tab[k * kSt + q] = uniq[k][q];
       tab[k * kSt + 9] = 1.f / uniq[k][4];
     }
-    m.sid = (uint16_t *)dev_alloc(c, n * 2);
+    m.sid = (uint16_t *)dev_alloc(c, pad16(n * 2));
     m.stab = (float *)dev_alloc(c, tab.size() * 4);
     m.u = (float *)dev_alloc(c, n * sizeof(float));
-    m.f = (float *)dev_alloc(c, n * sizeof(float));
+    m.f = (float *)dev_alloc(c, pad16(n * sizeof(float)));
     if (!m.u || !m.f || !m.sid || !m.stab) return cudaErrorMemoryAllocation;
     cudaMemcpy(m.sid, sid.data(), n * 2, cudaMemcpyHostToDevice);
     cudaMemcpy(m.stab, tab.data(), tab.size() * 4, cudaMemcpyHostToDevice);
     cudaMemsetAsync(m.u, 0, n * sizeof(float), c->stream);
-    cudaMemsetAsync(m.f, 0, n * sizeof(float), c->stream);
+    cudaMemsetAsync(m.f, 0, pad16(n * sizeof(float)), c->stream);
   }
   // coarsest level: dense (pseudo-)inverse when it is small
   {
@@ -1299,8 +1526,8 @@ cudaError_t poisson_setup(pic_ctx *c) {
         if (c->singular)
           for (auto &v : inv) v -= 1.0 / nc;
         std::vector<float> invf(inv.begin(), inv.end());
-        c->d_cinv = (float *)dev_alloc(c, invf.size() * 4);
-        c->d_cidx = (int *)dev_alloc(c, idx.size() * 4);
+        c->d_cinv = (float *)dev_alloc(c, pad16(invf.size() * 4));
+        c->d_cidx = (int *)dev_alloc(c, pad16(idx.size() * 4));
         if (!c->d_cinv || !c->d_cidx) return cudaErrorMemoryAllocation;
         cudaMemcpy(c->d_cinv, invf.data(), invf.size() * 4, cudaMemcpyHostToDevice);
         cudaMemcpy(c->d_cidx, idx.data(), idx.size() * 4, cudaMemcpyHostToDevice);
@@ -1315,11 +1542,11 @@ cudaError_t poisson_setup(pic_ctx *c) {
   cudaError_t e = cudaFuncSetAttribute(k_coarse, cudaFuncAttributeMaxDynamicSharedMemorySize,
                                        int(kCoarseSmemMax));
   if (e != cudaSuccess) return e;
-  float **vecs[] = {&c->d_r32, &c->d_z, &c->d_p0, &c->d_p1, &c->d_q, &c->d_e};
+  float **vecs[] = {&c->d_r32, &c->d_z, &c->d_p, &c->d_w, &c->d_q, &c->d_e};
   for (float **v : vecs) {
-    *v = (float *)dev_alloc(c, nn * sizeof(float));
+    *v = (float *)dev_alloc(c, pad16(nn * sizeof(float)));
     if (!*v) return cudaErrorMemoryAllocation;
-    cudaMemsetAsync(*v, 0, nn * sizeof(float), c->stream);
+    cudaMemsetAsync(*v, 0, pad16(nn * sizeof(float)), c->stream);
   }
   c->lev[0].u = c->d_z;
   c->lev[0].f = c->d_r32;
@@ -1332,10 +1559,11 @@ cudaError_t poisson_setup(pic_ctx *c) {
   }
   c->d_phi_prev = (double *)dev_alloc(c, nn * sizeof(double));
   if (!c->d_phi_prev) return cudaErrorMemoryAllocation;
-  c->red.nblocks = std::min(blocks_for(int(nn)), 2 * c->num_sms);
+  // kVB nodes per thread in the vector kernels
+  c->red.nblocks = blocks_for((int(nn) + kVB - 1) / kVB);
   // partials of the grid reductions: the vector kernels and the level-0 post-smoothing
   const int nparts = std::max(c->red.nblocks, c->lc > 0 ? post_tiles(c->lev[0], true) : 0);
-  c->red.part = (double *)dev_alloc(c, size_t(nparts) * 4 * sizeof(double));
+  c->red.part = (double *)dev_alloc(c, size_t(nparts) * 8 * sizeof(double));
   c->red.ticket = (unsigned int *)dev_alloc(c, 64);
   c->d_ps = (PoissonState *)dev_alloc(c, sizeof(PoissonState));
   if (!c->red.part || !c->red.ticket || !c->d_ps) return cudaErrorMemoryAllocation;
@@ -1383,14 +1611,13 @@ pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
     if (!c->h_ps->go) break;
     launch_vcycle(c, m);
-    launch_rz(c, a);
+    launch_zw(c, a);
     for (int it = 0; it < c->cfg.poisson_maxit; it += batch) {
       for (int b = 0; b < batch; ++b) {
-        launch(k_pq, nb, kThreads, 0, c->stream, a);
-        launch(k_update, nb, kThreads, 0, c->stream, a);
+        launch(k_cg, nb, kThreads, 0, c->stream, a);
         launch_vcycle(c, m);
-        launch_rz(c, a);
-        c->launches += 2;
+        launch_zw(c, a);
+        c->launches += 1;
       }
       cudaMemcpyAsync(c->h_ps, c->d_ps, sizeof(PoissonState), cudaMemcpyDeviceToHost, c->stream);
       if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
@@ -1450,8 +1677,9 @@ cudaError_t add_cond(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
 
 // Appends the solve to graph `top` after the nodes in `deps`; on return
 // `deps` holds the solve's last node.  Structure:
-//   [phi reset] -> init -> WHILE(outer) { resid64 -> IF(go) { V-cycle, rz ->
-//     WHILE(inner) { pq, update -> IF(!done) { V-cycle, rz } } -> correct } }
+//   [phi reset] -> init -> WHILE(outer) { resid64 -> IF(go) { V-cycle ->
+//     WHILE(inner) { cg -> IF(!done) { V-cycle } } -> correct } }
+// where a V-cycle also forms w = A z and the inner products of the next step.
 cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNode_t> &deps) {
   cudaStream_t s = c->stream;
   FineArgs a = fine_args(c);
@@ -1485,17 +1713,16 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   CK(add_cond(b_outer, d, h[1], cudaGraphCondTypeIf, &n_if_outer, &b_if_outer));
   CK(cap_begin(s, b_if_outer, {}));
   launch_vcycle(c, m);
-  launch_rz(c, a);
+  launch_zw(c, a);
   CK(cap_end(s, d));
   CK(add_cond(b_if_outer, d, h[2], cudaGraphCondTypeWhile, &n_inner, &b_inner));
   CK(cap_begin(s, b_inner, {}));
-  launch(k_pq, nb, kThreads, 0, s, a);
-  launch(k_update, nb, kThreads, 0, s, a);
+  launch(k_cg, nb, kThreads, 0, s, a);
   CK(cap_end(s, d));
   CK(add_cond(b_inner, d, h[3], cudaGraphCondTypeIf, &n_if_inner, &b_if_inner));
   CK(cap_begin(s, b_if_inner, {}));
   launch_vcycle(c, m);
-  launch_rz(c, a);
+  launch_zw(c, a);
   CK(cap_end(s, d));
   d.assign(1, n_inner);
   CK(cap_begin(s, b_if_outer, d));
@@ -1508,12 +1735,12 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
 
 // Kernels one solve launched, from its device counters (graph mode).
 int64_t poisson_kernel_count(pic_ctx *c, const PoissonState &ps) {
-  // a V-cycle with <r, z>: fused into its last kernel unless lc = 0
+  // a V-cycle with w = A z and the inner products: fused into its last kernel unless lc = 0
   const int64_t vc = 2 * c->lc + 1 + (c->lc == 0 ? 1 : 0);
   const int64_t O = ps.outer_iters, I = ps.total_iters;
   // init + resid per outer pass (+1 final) + per inner solve (V-cycle, correct)
-  // + per iteration (pq, update) + per non-final iteration (V-cycle)
-  return 1 + (O + 1) + O * (vc + 1) + 2 * I + std::max<int64_t>(I - O, 0) * vc +
+  // + per iteration (cg) + per non-final iteration (V-cycle)
+  return 1 + (O + 1) + O * (vc + 1) + I + std::max<int64_t>(I - O, 0) * vc +
          (c->cfg.warm_start != 1 ? 1 : 0);
 }
 

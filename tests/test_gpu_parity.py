@@ -50,6 +50,31 @@ def test_deposit_matches_oracle(name):
     assert rg.sum() == pytest.approx(ro.sum(), abs=1e-9 * np.abs(ro).sum())
 
 
+def test_deposit_particles_on_grid_lines():
+    # Particles exactly on the horizontal grid lines of every other cell row:
+    # the node row above each line gets shares 0 from the fixed-point rounding
+    # and -1 where the three rounded shares overshoot, and nothing else, so
+    # the chunk sums of those nodes are negative.  The exact CIC density is 0
+    # there; a sum decoded as unsigned would be off by 2^32 units.
+    w = synth.periodic_square_64(nx=48, ny=34, ppc=100, seed=17)
+    rng = np.random.default_rng(17)
+    ci, cj = np.meshgrid(np.arange(48), np.arange(0, 34, 2), indexing="ij")
+    ci, cj = np.repeat(ci.ravel(), 100), np.repeat(cj.ravel(), 100)
+    n = ci.size
+    p = synth.Particles(ci + rng.random(n), cj.astype(np.float64), np.zeros(n), np.zeros(n),
+                        np.arange(n, dtype=np.uint32))
+    gs = gpu_sim(w)
+    os_ = oracle_sim(w)
+    for s in (0, 1):
+        q = p if s == 0 else p.subset(slice(0, n, 3))
+        load_both(gs, os_, s, q)
+    gs.step(0)
+    rg, ro = gs.rho(), os_.charge_density()
+    assert np.all(ro[:, 1::2] == 0.0)
+    assert np.abs(rg - ro).max() <= RHO_TOL * np.abs(ro).max()
+    assert rg.sum() == pytest.approx(ro.sum(), abs=1e-9 * np.abs(ro).sum())
+
+
 @pytest.mark.parametrize("name", list(SMALL))
 def test_poisson_and_field_match_oracle(name):
     w = SMALL[name].replace(poisson_rtol=1e-10)
