@@ -105,6 +105,13 @@ typedef struct {
   int32_t graphs;                 /* 1: each step is one launch of a captured CUDA graph whose
                                      Poisson loops are device-side conditional nodes;
                                      0: kernels launched from a host loop that polls the solver */
+  int32_t poisson_method;         /* inner solver of the FP64 iterative refinement of Eq. 5:
+                                     0: automatic -- a direct FFT / tridiagonal / capacitance
+                                     solve when the box is periodic in y with a power-of-two
+                                     ny <= 2048, bounded in x, and its free nodes form a full
+                                     slab with at most one slot below it (the trench and the
+                                     plate geometries), else 1;
+                                     1: conjugate gradient preconditioned by a multigrid V-cycle */
   int64_t hit_capacity;           /* hit records kept (PIC_DIAG_HITS) */
   void *stream;                   /* cudaStream_t to run on; NULL: a library-owned stream */
   void *(*alloc)(size_t bytes, void *user); /* optional device allocator */
@@ -143,8 +150,10 @@ enum {
                             sorts, kernel launches, particle slots processed]: device time
                             from CUDA events on the context stream, accumulated over
                             pic_step calls since the last read; reading resets it */
-  PIC_DIAG_PHI_VACUUM = 13 /* [nxn*nyn]: potential of the empty box (Dirichlet values only),
-                              solved once to 1e-10 */
+  PIC_DIAG_PHI_VACUUM = 13, /* [nxn*nyn]: potential of the empty box (Dirichlet values only),
+                               solved once to 1e-10 */
+  PIC_DIAG_SOLVER = 14      /* int32: inner Poisson solver in use, 0 direct, 1 multigrid PCG
+                               (pic_config.poisson_method) */
 };
 
 /* Create a context from cfg.  Builds the conductor mask, Dirichlet nodes and

@@ -28,7 +28,8 @@ PIC_ST_NOCONV, PIC_ST_FULL, PIC_ST_CFL, PIC_ST_RANGE, PIC_ST_CAPACITY = 1, 2, 4,
 PIC_LOAD_V_AT_T0 = 1
 (PIC_DIAG_ENERGY, PIC_DIAG_MOMENTUM, PIC_DIAG_COUNTS, PIC_DIAG_SURFACE, PIC_DIAG_HITS,
  PIC_DIAG_RHO, PIC_DIAG_PHI, PIC_DIAG_E, PIC_DIAG_STATE_E, PIC_DIAG_STATE_I,
- PIC_DIAG_POISSON, PIC_DIAG_STATUS, PIC_DIAG_TIMING, PIC_DIAG_PHI_VACUUM) = range(14)
+ PIC_DIAG_POISSON, PIC_DIAG_STATUS, PIC_DIAG_TIMING, PIC_DIAG_PHI_VACUUM,
+ PIC_DIAG_SOLVER) = range(15)
 (WALL_XMIN, WALL_XMAX, WALL_YMIN, WALL_YMAX, WALL_COND_PX, WALL_COND_MX,
  WALL_COND_PY, WALL_COND_MY) = range(8)
 
@@ -39,6 +40,11 @@ EXPORTED = ("pic_init", "pic_load", "pic_step", "pic_diag", "pic_free", "pic_str
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+
+
+# pic_config.poisson_method
+POISSON_AUTO = 0        # direct FFT / tridiagonal / capacitance solve where the geometry allows
+POISSON_MULTIGRID = 1   # multigrid-preconditioned conjugate gradient everywhere
 
 
 class PicConfig(ctypes.Structure):
@@ -56,6 +62,7 @@ class PicConfig(ctypes.Structure):
         ("poisson_rtol", ctypes.c_double),
         ("warm_start", ctypes.c_int32), ("device", ctypes.c_int32),
         ("timing", ctypes.c_int32), ("graphs", ctypes.c_int32),
+        ("poisson_method", ctypes.c_int32),
         ("hit_capacity", ctypes.c_int64),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
@@ -207,7 +214,8 @@ class _TorchAllocator:
 
 def make_config(w, capacity=None, device: int = 0, stream=None, hit_capacity: int = 1 << 20,
                 poisson_maxit: int = 200, warm_start: int = 1, allocator=None,
-                timing: bool = False, graphs: bool = True) -> PicConfig:
+                timing: bool = False, graphs: bool = True,
+                poisson_method: int = POISSON_AUTO) -> PicConfig:
     """PicConfig from a workload description (an object with the fields of
     synth.Workload)."""
     cfg = PicConfig()
@@ -231,6 +239,7 @@ def make_config(w, capacity=None, device: int = 0, stream=None, hit_capacity: in
     cfg.device = int(device)
     cfg.timing = int(bool(timing))
     cfg.graphs = int(bool(graphs))
+    cfg.poisson_method = int(poisson_method)
     cfg.hit_capacity = int(hit_capacity)
     cfg.stream = stream
     if allocator is not None:
@@ -384,6 +393,11 @@ class Sim:
         self._check(load_library().pic_poisson(self.ctx, int(guess), y.data_ptr() if y is not None else None,
                                                float(scale), out), "pic_poisson")
         return list(out)
+
+    def solver(self):
+        """Inner Poisson solver in use: POISSON_AUTO (0) = the direct one,
+        POISSON_MULTIGRID (1) = multigrid-preconditioned CG."""
+        return int(self.diag(PIC_DIAG_SOLVER, np.zeros(1, np.int32))[0][0])
 
     def status(self):
         out = np.zeros(1, np.uint32)

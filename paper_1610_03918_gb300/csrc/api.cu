@@ -181,6 +181,7 @@ pic_status validate(const pic_config *cfg) {
   if (!(cfg->dt > 0) || !(cfg->poisson_rtol > 0)) return PIC_EINVAL;
   if (cfg->poisson_maxit < 1 || cfg->sort_every < 1) return PIC_EINVAL;
   if (cfg->warm_start < 0 || cfg->warm_start > 2) return PIC_EINVAL;
+  if (cfg->poisson_method < 0 || cfg->poisson_method > 1) return PIC_EINVAL;
   for (int s = 0; s < 2; ++s) {
     if (cfg->ppc[s] < 1 || cfg->capacity[s] < 0) return PIC_EINVAL;
     if (cfg->capacity[s] > (int64_t(1) << 31) - (int64_t(1) << 26)) return PIC_EINVAL;
@@ -917,6 +918,12 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
       o[2] = ps.rel;
       o[3] = c->last_ms;
       count = 4;
+      break;
+    }
+    case PIC_DIAG_SOLVER: {
+      if (!need(4)) return PIC_EINVAL;
+      *(int32_t *)out = c->fp.enabled ? 0 : 1;
+      count = 1;
       break;
     }
     case PIC_DIAG_PHI_VACUUM: {

@@ -1,0 +1,601 @@
+// Direct inner solve of the Poisson correction equation A e = r, A = -Delta_h
+// on the free nodes (Eq. 5 with the Dirichlet values lifted into r), for the
+// boxes of Sec. III-B and III-C when y is periodic with a power-of-two ny and
+// x is bounded: the free nodes are the full rows 1..m (the plasma slab) and,
+// with a trench, the interface row xs = m + 1 and the slot rows below it,
+// all on the trench's columns [c0, c0 + wc).
+//
+// Block elimination of the coupled system (unknowns: slab R, interface G,
+// slot S; A_RG, A_GS are the -1 couplings across rows m | xs | xs + 1):
+//   v_R = A_RR^-1 r_R,   v_S = A_SS^-1 r_S
+//   (A_GG - G_R - G_S) u_G = r_G + v_R(row m) + v_S(row xs + 1)
+//   u_R = v_R + A_RR^-1 (u_G on row m),   u_S = v_S + A_SS^-1 (u_G on row xs + 1)
+// where G_R, G_S are the slab's and the slot's Green's functions on the
+// interface columns (precomputed in FP64, the wc x wc Schur complement
+// inverted on the host).
+//   Slab: a real FFT along y turns A_RR into one tridiagonal system per mode
+//     k = 0..ny/2, tridiag(-1, 4 - 2 cos(2 pi k / ny), -1) along x with
+//     Dirichlet rows 0 and m + 1, each solved by parallel cyclic reduction in
+//     shared memory; the interface term on row m is added in Fourier space
+//     through the precomputed column m of each inverse.
+//   Slot: a sine transform across its wc columns (Dirichlet walls) gives wc
+//     tridiagonal systems along x (Dirichlet bottom row; the interface is a
+//     separate unknown), solved together by the same reduction.
+// Arithmetic is FP32; the FP64 iterative refinement around it (the residual
+// check of the solver) certifies the result.
+#include <cuda_runtime.h>
+
+#include <algorithm>
+#include <cmath>
+#include <vector>
+
+#include "internal.cuh"
+
+namespace picgb {
+namespace {
+
+constexpr int kFftThreads = 256;
+constexpr int kMaxNy = 2048;
+constexpr int kMaxRows = 4096;         // rectangle rows (one mode's reduction fits in shared memory)
+constexpr int kPcrThreads = 256;
+constexpr int kSlotThreads = 256;
+constexpr size_t kSmemMax = 200 * 1024;
+
+struct FPArgs {
+  int ny, nk, logny, m, xs, slot, c0, wc, ms;
+  const float2 *tw;
+  const float *dk, *z;               // diagonal per slab mode, interface responses
+  float2 *vhat, *fhat;
+  const float *phi, *sb, *zs, *sinv; // slot basis, diagonal per sine mode, responses
+  float *vs;                         // [wc][ms] solved slot spectra
+  const float *r;
+  float *e;
+  PoissonState *ps;
+};
+
+__device__ __forceinline__ float2 cadd(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 csub(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 cmul(float2 a, float2 b) {
+  return make_float2(a.x * b.x - a.y * b.y, a.x * b.y + a.y * b.x);
+}
+__device__ __forceinline__ float2 conj2(float2 a) { return make_float2(a.x, -a.y); }
+__device__ __forceinline__ float fma_t(float w, float a, float b) { return fmaf(w, a, b); }
+__device__ __forceinline__ float2 fma_t(float w, float2 a, float2 b) {
+  return make_float2(fmaf(w, a.x, b.x), fmaf(w, a.y, b.y));
+}
+
+// Radix-2 Stockham autosort FFT of n = 2^logn complex points in shared memory
+// (x holds the input, y is scratch); returns the buffer holding the result.
+// Stage with sub-transform length len and stride s = n / len: for p < len/2,
+// q < s, with a = x[q + s p], b = x[q + s (p + len/2)]:
+//   y[q + s 2p] = a + b,   y[q + s (2p + 1)] = (a - b) w^p,  w = exp(-+2 pi i / len)
+// (tw[t] = exp(-2 pi i t / n), so w^p = tw[p s]; conjugated for the inverse).
+// Unscaled.
+__device__ float2 *fft_smem(float2 *x, float2 *y, const float2 *tw, int n, int logn, bool inverse) {
+  for (int ls = 0; ls < logn; ++ls) {
+    const int s = 1 << ls, half = n >> (ls + 1);
+    for (int t = threadIdx.x; t < (n >> 1); t += blockDim.x) {
+      const int p = t >> ls, q = t & (s - 1);
+      float2 wp = tw[p * s];
+      if (inverse) wp = conj2(wp);
+      const float2 a = x[q + s * p], b = x[q + s * (p + half)];
+      y[q + s * (2 * p)] = cadd(a, b);
+      y[q + s * (2 * p + 1)] = cmul(csub(a, b), wp);
+    }
+    __syncthreads();
+    float2 *tmp = x;
+    x = y;
+    y = tmp;
+  }
+  return x;
+}
+
+// Rows of a tridiagonal system a_i x_{i-1} + b_i x_i + c_i x_{i+1} = r_i in
+// shared memory.
+template <typename T>
+struct Rows {
+  float *a, *b, *c;
+  T *r;
+};
+
+// Parallel cyclic reduction (Hockney): step s eliminates every row's
+// neighbours at distance s = 1, 2, 4, ... from it, with
+//   alpha = -a_i / b_{i-s},  gamma = -c_i / b_{i+s},
+//   a_i <- alpha a_{i-s},  c_i <- gamma c_{i+s},
+//   b_i <- b_i + alpha c_{i-s} + gamma a_{i+s},  r_i <- r_i + alpha r_{i-s} + gamma r_{i+s},
+// until no row is coupled; then x_i = r_i / b_i (the quotients use the fast
+// reciprocal, about 2 ulp; the refinement around the solve absorbs it).  A
+// zero coupling stays zero,
+// so independent systems laid end to end (zero a at each first row, zero c at
+// each last row) are solved together.  p holds the input, q is scratch; the
+// returned pair holds the reduced rows.
+template <typename T>
+__device__ Rows<T> pcr(Rows<T> p, Rows<T> q, int n) {
+  for (int s = 1; s < n; s <<= 1) {
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float ai = p.a[i], ci = p.c[i];
+      float bi = p.b[i], an = 0.f, cn = 0.f;
+      T ri = p.r[i];
+      if (ai != 0.f) {
+        const float al = __fdividef(-ai, p.b[i - s]);
+        an = al * p.a[i - s];
+        bi = fmaf(al, p.c[i - s], bi);
+        ri = fma_t(al, p.r[i - s], ri);
+      }
+      if (ci != 0.f) {
+        const float ga = __fdividef(-ci, p.b[i + s]);
+        cn = ga * p.c[i + s];
+        bi = fmaf(ga, p.a[i + s], bi);
+        ri = fma_t(ga, p.r[i + s], ri);
+      }
+      q.a[i] = an;
+      q.b[i] = bi;
+      q.c[i] = cn;
+      q.r[i] = ri;
+    }
+    __syncthreads();
+    const Rows<T> t = p;
+    p = q;
+    q = t;
+  }
+  return p;
+}
+
+template <typename T>
+__device__ Rows<T> carve_rows(float *&base, int n) {
+  Rows<T> r;
+  r.a = base;
+  r.b = base + n;
+  r.c = base + 2 * n;
+  r.r = reinterpret_cast<T *>(base + 3 * n + (n & 1) * (sizeof(T) == 8 ? 1 : 0));
+  base = reinterpret_cast<float *>(r.r + n);
+  return r;
+}
+
+// Forward transforms of rectangle rows i0 = 2b + 1 and i1 = i0 + 1, packed as
+// one complex sequence z = r_i0 + i r_i1 and separated by the symmetry of real
+// transforms: X_a[k] = (Z[k] + conj Z[-k]) / 2, X_b[k] = (Z[k] - conj Z[-k]) / 2i.
+__global__ void __launch_bounds__(kFftThreads) k_fp_forward(FPArgs f) {
+  extern __shared__ float2 sm[];
+  float2 *x = sm, *y = sm + f.ny, *tw = sm + 2 * f.ny;
+  for (int t = threadIdx.x; t < (f.ny >> 1); t += blockDim.x) tw[t] = f.tw[t];
+  pdl_enter();
+  const int i0 = 2 * blockIdx.x + 1, i1 = i0 + 1;
+  const bool two = i1 <= f.m;
+  for (int j = threadIdx.x; j < f.ny; j += blockDim.x)
+    x[j] = make_float2(f.r[i0 * f.ny + j], two ? f.r[i1 * f.ny + j] : 0.f);
+  __syncthreads();
+  const float2 *Z = fft_smem(x, y, tw, f.ny, f.logny, false);
+  for (int k = threadIdx.x; k < f.nk; k += blockDim.x) {
+    const float2 zk = Z[k], zc = conj2(Z[(f.ny - k) & (f.ny - 1)]);
+    const float2 d = csub(zk, zc);
+    f.vhat[(i0 - 1) * f.nk + k] = make_float2(0.5f * (zk.x + zc.x), 0.5f * (zk.y + zc.y));
+    if (two) f.vhat[(i1 - 1) * f.nk + k] = make_float2(0.5f * d.y, -0.5f * d.x);
+  }
+}
+
+// One tridiagonal system per CTA by parallel cyclic reduction.  CTAs 0..nk-1
+// take the slab modes: tridiag(-1, d_k, -1) along x (rows 1..m, Dirichlet rows
+// 0 and m + 1), in place on column k of vhat.  CTAs nk..nk+wc-1 take the slot's
+// sine modes p: the spectrum sum_c r(xs + 1 + i, c0 + c) phi[p][c] of its rows,
+// then tridiag(-1, sb_p, -1) along them, into vs[p].  The matrices do not
+// change during a solve, so they are laid out before the wait for the
+// preceding kernel.
+__global__ void __launch_bounds__(kPcrThreads) k_fp_tridiag(FPArgs f) {
+  extern __shared__ float smt[];
+  const bool slab = int(blockIdx.x) < f.nk;
+  const int n = slab ? f.m : f.ms, k = blockIdx.x, pm = blockIdx.x - f.nk;
+  float *base = smt;
+  if (slab) {
+    const Rows<float2> p = carve_rows<float2>(base, n), q = carve_rows<float2>(base, n);
+    const float d = __ldg(f.dk + k);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      p.a[i] = i > 0 ? -1.f : 0.f;
+      p.b[i] = d;
+      p.c[i] = i + 1 < n ? -1.f : 0.f;
+    }
+    pdl_enter();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) p.r[i] = f.vhat[i * f.nk + k];
+    __syncthreads();
+    const Rows<float2> x = pcr(p, q, n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float2 r = x.r[i];
+      const float rb = 1.f / x.b[i];
+      f.vhat[i * f.nk + k] = make_float2(r.x * rb, r.y * rb);
+    }
+  } else {
+    const Rows<float> p = carve_rows<float>(base, n), q = carve_rows<float>(base, n);
+    float *ph = base;                // [wc] row pm of the sine basis
+    const float d = __ldg(f.sb + pm);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      p.a[i] = i > 0 ? -1.f : 0.f;
+      p.b[i] = d;
+      p.c[i] = i + 1 < n ? -1.f : 0.f;
+    }
+    for (int c = threadIdx.x; c < f.wc; c += blockDim.x) ph[c] = __ldg(f.phi + pm * f.wc + c);
+    pdl_enter();
+    __syncthreads();
+    for (int i = threadIdx.x; i < n; i += blockDim.x) {
+      const float *rr = f.r + (f.xs + 1 + i) * f.ny + f.c0;
+      float acc = 0.f;
+      for (int c = 0; c < f.wc; ++c) acc = fmaf(__ldg(rr + c), ph[c], acc);
+      p.r[i] = acc;
+    }
+    __syncthreads();
+    const Rows<float> x = pcr(p, q, n);
+    for (int i = threadIdx.x; i < n; i += blockDim.x) f.vs[pm * n + i] = x.r[i] / x.b[i];
+  }
+}
+
+// Interface, one CTA: g = r_G + v_R(row m) + v_S(first slot row) on the
+// interface columns (v_R by the inverse DFT of the solved spectra of row m,
+// v_S from the solved slot spectra), u_G = S^-1 g, the spectrum of u_G placed
+// on row m (for the slab correction) and the corrected slot values.  Writes e
+// on the interface and in the slot.
+__global__ void __launch_bounds__(kSlotThreads) k_fp_interface(FPArgs f) {
+  extern __shared__ float ss[];
+  const int wc = f.wc, ms = f.ms, ny = f.ny, nk = f.nk;
+  float *sphi = ss;                  // [wc][wc] sine basis
+  float *gv = sphi + wc * wc;        // [wc] interface right-hand side g
+  float *ug = gv + wc;               // [wc] interface values
+  float *sh = ug + wc;               // [wc] sine spectrum of u_G
+  for (int t = threadIdx.x; t < wc * wc; t += blockDim.x) sphi[t] = __ldg(f.phi + t);
+  pdl_enter();
+  __syncthreads();
+  const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  for (int c = warp; c < wc; c += nw) {
+    const int j = f.c0 + c;
+    float acc = 0.f;
+    for (int k = lane; k < nk; k += 32) {
+      const float2 v = __ldg(f.vhat + (f.m - 1) * nk + k);
+      const float2 t = conj2(__ldg(f.tw + ((k * j) & (ny - 1))));   // exp(+2 pi i k j / ny)
+      const float wgt = (k == 0 || k == nk - 1) ? 1.f : 2.f;
+      acc = fmaf(wgt, v.x * t.x - v.y * t.y, acc);
+    }
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
+    if (lane == 0) {
+      float vsum = 0.f;
+      for (int pm = 0; pm < wc; ++pm) vsum = fmaf(__ldg(f.vs + pm * ms), sphi[pm * wc + c], vsum);
+      gv[c] = __ldg(f.r + f.xs * ny + j) + acc / float(ny) + vsum;
+    }
+  }
+  __syncthreads();
+  // u_G = S^-1 g
+  for (int c = threadIdx.x; c < wc; c += blockDim.x) {
+    float acc = 0.f;
+    for (int qq = 0; qq < wc; ++qq) acc = fmaf(__ldg(f.sinv + c * wc + qq), gv[qq], acc);
+    ug[c] = acc;
+    f.e[f.xs * ny + f.c0 + c] = acc;
+  }
+  __syncthreads();
+  // spectrum of u_G on row m, and its sine spectrum for the slot
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    float2 acc = make_float2(0.f, 0.f);
+    for (int c = 0; c < wc; ++c) {
+      const float2 t = __ldg(f.tw + ((k * (f.c0 + c)) & (ny - 1)));   // exp(-2 pi i k j / ny)
+      acc.x = fmaf(ug[c], t.x, acc.x);
+      acc.y = fmaf(ug[c], t.y, acc.y);
+    }
+    f.fhat[k] = acc;
+  }
+  for (int pm = threadIdx.x; pm < wc; pm += blockDim.x) {
+    float acc = 0.f;
+    for (int c = 0; c < wc; ++c) acc = fmaf(sphi[pm * wc + c], ug[c], acc);
+    sh[pm] = acc;
+  }
+  __syncthreads();
+  // corrected slot values, back to the columns
+  for (int t = threadIdx.x; t < ms * wc; t += blockDim.x) {
+    const int row = t / wc, c = t - row * wc;
+    float acc = 0.f;
+    for (int pm = 0; pm < wc; ++pm)
+      acc = fmaf(fmaf(__ldg(f.zs + pm * ms + row), sh[pm], __ldg(f.vs + pm * ms + row)),
+                 sphi[pm * wc + c], acc);
+    f.e[(f.xs + 1 + row) * ny + f.c0 + c] = acc;
+  }
+  if (threadIdx.x == 0) {
+    f.ps->inner_iters += 1;
+    f.ps->total_iters += 1;
+  }
+}
+
+// Inverse transforms of rows i0, i1 (with the interface term z_k(i) fhat[k]
+// when there is a slot): Z[k] = X_a[k] + i X_b[k] over the full spectrum
+// (X[-k] = conj X[k]), e(i0) = Re IFFT(Z) / ny, e(i1) = Im IFFT(Z) / ny.
+__global__ void __launch_bounds__(kFftThreads) k_fp_inverse(FPArgs f) {
+  extern __shared__ float2 sm[];
+  float2 *x = sm, *y = sm + f.ny, *tw = sm + 2 * f.ny;
+  for (int t = threadIdx.x; t < (f.ny >> 1); t += blockDim.x) tw[t] = f.tw[t];
+  pdl_enter();
+  const int i0 = 2 * blockIdx.x + 1, i1 = i0 + 1;
+  const bool two = i1 <= f.m;
+  for (int k = threadIdx.x; k < f.nk; k += blockDim.x) {
+    float2 a = f.vhat[(i0 - 1) * f.nk + k];
+    float2 b = two ? f.vhat[(i1 - 1) * f.nk + k] : make_float2(0.f, 0.f);
+    if (f.slot) {
+      const float2 fh = f.fhat[k];
+      const float za = f.z[(i0 - 1) * f.nk + k];
+      a = make_float2(fmaf(za, fh.x, a.x), fmaf(za, fh.y, a.y));
+      if (two) {
+        const float zb = f.z[(i1 - 1) * f.nk + k];
+        b = make_float2(fmaf(zb, fh.x, b.x), fmaf(zb, fh.y, b.y));
+      }
+    }
+    // Z[k] = a + i b, Z[ny - k] = conj(a) + i conj(b)
+    x[k] = make_float2(a.x - b.y, a.y + b.x);
+    if (k > 0 && k < f.ny - k) x[f.ny - k] = make_float2(a.x + b.y, -a.y + b.x);
+  }
+  __syncthreads();
+  const float2 *Z = fft_smem(x, y, tw, f.ny, f.logny, true);
+  const float s = 1.f / float(f.ny);
+  for (int j = threadIdx.x; j < f.ny; j += blockDim.x) {
+    f.e[i0 * f.ny + j] = Z[j].x * s;
+    if (two) f.e[i1 * f.ny + j] = Z[j].y * s;
+  }
+  if (!f.slot && blockIdx.x == 0 && threadIdx.x == 0) {
+    f.ps->inner_iters += 1;
+    f.ps->total_iters += 1;
+  }
+}
+
+FPArgs fp_args(pic_ctx *c, const float *r, float *e, PoissonState *ps) {
+  const FastPoisson &p = c->fp;
+  FPArgs a;
+  a.ny = p.ny;
+  a.nk = p.nk;
+  a.logny = p.logny;
+  a.m = p.m;
+  a.xs = p.xs;
+  a.slot = p.slot;
+  a.c0 = p.c0;
+  a.wc = p.wc;
+  a.ms = p.ms;
+  a.tw = p.tw;
+  a.dk = p.dk;
+  a.z = p.z;
+  a.vhat = p.vhat;
+  a.fhat = p.fhat;
+  a.phi = p.phi;
+  a.vs = p.vs;
+  a.sb = p.sb;
+  a.zs = p.zs;
+  a.sinv = p.sinv;
+  a.r = r;
+  a.e = e;
+  a.ps = ps;
+  return a;
+}
+
+size_t fft_smem_bytes(int ny) { return size_t(2 * ny + ny / 2) * sizeof(float2); }
+// two Rows<T> sets of n rows (with the alignment padding of carve_rows)
+size_t rows_bytes(int n, size_t tsize) { return 2 * (size_t(3 * n + (n & 1)) * 4 + size_t(n) * tsize); }
+size_t tridiag_smem_bytes(int m, int ms, int wc) {
+  return std::max(rows_bytes(m, sizeof(float2)), rows_bytes(ms, 4) + size_t(wc) * 4);
+}
+size_t slot_smem_bytes(int wc) { return (size_t(wc) * wc + 3 * size_t(wc)) * 4; }
+
+// Thomas factors of tridiag(-1, d, -1) of size n: w_1 = 1/d, w_i = 1/(d - w_{i-1})
+void thomas_factors(double d, int n, double *w) {
+  double v = 1.0 / d;
+  w[0] = v;
+  for (int i = 1; i < n; ++i) {
+    v = 1.0 / (d - v);
+    w[i] = v;
+  }
+}
+
+// Solution of tridiag(-1, d, -1) x = rhs with the factors above (FP64)
+void thomas_solve(const double *w, int n, const double *rhs, double *x) {
+  std::vector<double> y(n);
+  double prev = 0.0;
+  for (int i = 0; i < n; ++i) {
+    prev = w[i] * (rhs[i] + prev);
+    y[i] = prev;
+  }
+  double nxt = 0.0;
+  for (int i = n - 1; i >= 0; --i) {
+    nxt = y[i] + w[i] * nxt;
+    x[i] = nxt;
+  }
+}
+
+bool invert(std::vector<double> &A, int n, std::vector<double> &inv) {
+  inv.assign(size_t(n) * n, 0.0);
+  for (int r = 0; r < n; ++r) inv[size_t(r) * n + r] = 1.0;
+  for (int col = 0; col < n; ++col) {   // Gauss-Jordan with partial pivoting
+    int piv = col;
+    for (int r = col + 1; r < n; ++r)
+      if (std::fabs(A[size_t(r) * n + col]) > std::fabs(A[size_t(piv) * n + col])) piv = r;
+    if (!(std::fabs(A[size_t(piv) * n + col]) > 1e-300)) return false;
+    if (piv != col)
+      for (int k = 0; k < n; ++k) {
+        std::swap(A[size_t(piv) * n + k], A[size_t(col) * n + k]);
+        std::swap(inv[size_t(piv) * n + k], inv[size_t(col) * n + k]);
+      }
+    const double d = A[size_t(col) * n + col];
+    for (int k = 0; k < n; ++k) {
+      A[size_t(col) * n + k] /= d;
+      inv[size_t(col) * n + k] /= d;
+    }
+    for (int r = 0; r < n; ++r) {
+      if (r == col) continue;
+      const double q = A[size_t(r) * n + col];
+      if (q == 0.0) continue;
+      for (int k = 0; k < n; ++k) {
+        A[size_t(r) * n + k] -= q * A[size_t(col) * n + k];
+        inv[size_t(r) * n + k] -= q * inv[size_t(col) * n + k];
+      }
+    }
+  }
+  return true;
+}
+
+template <typename T>
+T *upload(pic_ctx *c, const std::vector<T> &v) {
+  T *d = static_cast<T *>(dev_alloc(c, std::max<size_t>(v.size(), 1) * sizeof(T)));
+  if (d && !v.empty()) cudaMemcpy(d, v.data(), v.size() * sizeof(T), cudaMemcpyHostToDevice);
+  return d;
+}
+
+}  // namespace
+
+cudaError_t fast_poisson_setup(pic_ctx *c) {
+  FastPoisson &p = c->fp;
+  p = FastPoisson();
+  const Geom &g = c->g;
+  if (c->cfg.poisson_method != 0 || g.px || !g.py) return cudaSuccess;
+  const int ny = g.nyn, nxn = g.nxn;
+  if (ny < 4 || ny > kMaxNy || (ny & (ny - 1))) return cudaSuccess;
+  auto free_at = [&](int i, int j) { return (c->h_nodeflags[size_t(i) * ny + j] & kFree) != 0; };
+  auto row_count = [&](int i) {
+    int n = 0;
+    for (int j = 0; j < ny; ++j) n += free_at(i, j);
+    return n;
+  };
+  if (row_count(0) != 0 || row_count(nxn - 1) != 0) return cudaSuccess;
+  int xs = 1;
+  while (xs < nxn - 1 && row_count(xs) == ny) ++xs;
+  const int m = xs - 1;
+  if (m < 1 || m > kMaxRows || tridiag_smem_bytes(m, 0, 0) > kSmemMax) return cudaSuccess;
+  int c0 = 0, wc = 0, ms = 0;
+  // a slot exists when some row from xs on still has free nodes (a trench
+  // one cell wide has none: its walls' nodes are all on the conductor)
+  bool slot = false;
+  for (int r = xs; r < nxn; ++r) slot = slot || row_count(r) > 0;
+  if (slot) {
+    // the interface row's free nodes: one run of columns with a wall on each side
+    int first = -1, last = -1;
+    for (int j = 0; j < ny; ++j)
+      if (free_at(xs, j)) {
+        if (first < 0) first = j;
+        last = j;
+      }
+    if (first < 1 || last > ny - 2) return cudaSuccess;
+    c0 = first;
+    wc = last - first + 1;
+    if (row_count(xs) != wc) return cudaSuccess;
+    // slot rows: the same columns, down to the last free row
+    int r = xs + 1;
+    while (r < nxn - 1 && row_count(r) > 0) {
+      if (row_count(r) != wc) return cudaSuccess;
+      for (int j = c0; j < c0 + wc; ++j)
+        if (!free_at(r, j)) return cudaSuccess;
+      ++r;
+    }
+    for (int rr = r; rr < nxn; ++rr)
+      if (row_count(rr) != 0) return cudaSuccess;
+    ms = r - xs - 1;
+    if (ms < 1 || tridiag_smem_bytes(0, ms, wc) > kSmemMax || slot_smem_bytes(wc) > kSmemMax)
+      return cudaSuccess;
+  }
+  const int nk = ny / 2 + 1;
+  int logny = 0;
+  while ((1 << logny) < ny) ++logny;
+  const double pi = 3.14159265358979323846;
+  // twiddles, the slab modes' diagonals and (with a slot) the column m of
+  // each mode's inverse, by the Thomas recursion in FP64
+  std::vector<float2> tw(ny);
+  for (int t = 0; t < ny; ++t)
+    tw[t] = make_float2(float(std::cos(2 * pi * t / ny)), float(-std::sin(2 * pi * t / ny)));
+  std::vector<double> wk(m), col(m), rhs(m, 0.0);
+  std::vector<float> dk(nk), z;
+  std::vector<double> zlast(nk);   // [T_k^-1]_{m,m}
+  if (slot) z.resize(size_t(m) * nk);
+  rhs[m - 1] = 1.0;
+  for (int k = 0; k < nk; ++k) {
+    const double d = 4.0 - 2.0 * std::cos(2 * pi * k / ny);
+    dk[k] = float(d);
+    if (slot) {
+      thomas_factors(d, m, wk.data());
+      thomas_solve(wk.data(), m, rhs.data(), col.data());
+      for (int i = 0; i < m; ++i) z[size_t(i) * nk + k] = float(col[i]);
+      zlast[k] = col[m - 1];
+    }
+  }
+  p.tw = upload(c, tw);
+  p.dk = upload(c, dk);
+  p.vhat = static_cast<float2 *>(dev_alloc(c, size_t(m) * nk * sizeof(float2)));
+  if (!p.tw || !p.dk || !p.vhat) return cudaErrorMemoryAllocation;
+  if (slot) {
+    // slot: orthonormal sine basis across the columns, the diagonal of each
+    // sine mode's system along its rows and the responses to a unit value on
+    // its first row ([mode][row])
+    std::vector<double> phi(size_t(wc) * wc), mu(wc);
+    for (int q = 0; q < wc; ++q) {
+      mu[q] = 2.0 - 2.0 * std::cos(pi * (q + 1) / (wc + 1));
+      for (int cc = 0; cc < wc; ++cc)
+        phi[size_t(q) * wc + cc] = std::sqrt(2.0 / (wc + 1)) * std::sin(pi * (q + 1) * (cc + 1) / (wc + 1));
+    }
+    std::vector<float> sbf(wc), zsf(size_t(ms) * wc), phif(phi.begin(), phi.end());
+    std::vector<double> wsk(ms), zcol(ms), e0(ms, 0.0), zfirst(wc);
+    e0[0] = 1.0;
+    for (int q = 0; q < wc; ++q) {
+      sbf[q] = float(2.0 + mu[q]);
+      thomas_factors(2.0 + mu[q], ms, wsk.data());
+      thomas_solve(wsk.data(), ms, e0.data(), zcol.data());
+      for (int i = 0; i < ms; ++i) zsf[size_t(q) * ms + i] = float(zcol[i]);
+      zfirst[q] = zcol[0];
+    }
+    // Schur complement on the interface: A_GG - G_R - G_S
+    std::vector<double> S(size_t(wc) * wc, 0.0), Sinv;
+    for (int a = 0; a < wc; ++a) {
+      S[size_t(a) * wc + a] = 4.0;
+      if (a > 0) S[size_t(a) * wc + a - 1] = -1.0;
+      if (a + 1 < wc) S[size_t(a) * wc + a + 1] = -1.0;
+      for (int b = 0; b < wc; ++b) {
+        double gr = 0.0;
+        for (int k = 0; k < nk; ++k) {
+          const double wgt = (k == 0 || k == nk - 1) ? 1.0 : 2.0;
+          gr += wgt * zlast[k] * std::cos(2 * pi * double(k) * double(a - b) / ny);
+        }
+        gr /= ny;
+        double gs = 0.0;
+        for (int q = 0; q < wc; ++q) gs += phi[size_t(q) * wc + a] * zfirst[q] * phi[size_t(q) * wc + b];
+        S[size_t(a) * wc + b] -= gr + gs;
+      }
+    }
+    if (!invert(S, wc, Sinv)) return cudaSuccess;   // cannot happen for an SPD system; keep the V-cycle
+    std::vector<float> sinvf(Sinv.begin(), Sinv.end());
+    p.z = upload(c, z);
+    p.phi = upload(c, phif);
+    p.sb = upload(c, sbf);
+    p.zs = upload(c, zsf);
+    p.sinv = upload(c, sinvf);
+    p.fhat = static_cast<float2 *>(dev_alloc(c, size_t(nk) * sizeof(float2)));
+    p.vs = static_cast<float *>(dev_alloc(c, size_t(wc) * ms * sizeof(float)));
+    if (!p.z || !p.phi || !p.sb || !p.zs || !p.sinv || !p.fhat || !p.vs) return cudaErrorMemoryAllocation;
+  }
+  p.ny = ny;
+  p.nk = nk;
+  p.logny = logny;
+  p.m = m;
+  p.xs = xs;
+  p.slot = slot ? 1 : 0;
+  p.c0 = c0;
+  p.wc = wc;
+  p.ms = ms;
+  p.kernels = slot ? 4 : 3;
+  // dynamic shared memory beyond the default 48 KB (granted per kernel, so
+  // the largest size any context may use)
+  cudaError_t e = cudaFuncSetAttribute(k_fp_tridiag, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                       int(kSmemMax));
+  if (e == cudaSuccess)
+    e = cudaFuncSetAttribute(k_fp_interface, cudaFuncAttributeMaxDynamicSharedMemorySize, int(kSmemMax));
+  if (e != cudaSuccess) return e;
+  p.enabled = 1;
+  return cudaGetLastError();
+}
+
+void fast_poisson_launch(pic_ctx *c, const float *r, float *e, PoissonState *ps) {
+  const FPArgs a = fp_args(c, r, e, ps);
+  const int rows = (a.m + 1) / 2;
+  launch(k_fp_forward, rows, kFftThreads, fft_smem_bytes(a.ny), c->stream, a);
+  launch(k_fp_tridiag, a.nk + (a.slot ? a.wc : 0), kPcrThreads,
+         tridiag_smem_bytes(a.m, a.slot ? a.ms : 0, a.wc), c->stream, a);
+  if (a.slot) launch(k_fp_interface, 1, kSlotThreads, slot_smem_bytes(a.wc), c->stream, a);
+  launch(k_fp_inverse, rows, kFftThreads, fft_smem_bytes(a.ny), c->stream, a);
+  c->launches += c->fp.kernels;
+}
+
+}  // namespace picgb

@@ -91,6 +91,64 @@ struct Reducer {
   int nblocks;
 };
 
+// Direct inner solve of the Poisson correction equation for boxes periodic in
+// y (ny a power of two) and bounded in x whose free nodes are the full rows
+// 1..m plus, optionally, one interface row xs = m + 1 and a slot below it
+// sharing the interface's columns [c0, c0 + wc): the trench and the plates.
+// Rows 1..m: FFT along y, then per Fourier mode k the tridiagonal system
+// tridiag(-1, 4 - 2 cos(2 pi k / ny), -1) along x by parallel cyclic
+// reduction.  Slot rows xs+1..xs+ms: sine transform across its wc columns,
+// one tridiagonal system per sine mode along x.  The interface values come from
+// the wc x wc Schur complement of the coupled system (precomputed inverse).
+struct FastPoisson {
+  int enabled = 0;
+  int ny = 0, nk = 0, logny = 0;   // FFT size, modes ny / 2 + 1
+  int m = 0, xs = 0;               // rectangle rows 1..m, interface row xs
+  int slot = 0;                    // interface and slot present
+  int c0 = 0, wc = 0, ms = 0;      // slot columns [c0, c0 + wc), rows xs+1 .. xs+ms
+  float2 *tw = nullptr;            // [ny] exp(-2 pi i t / ny)
+  float *dk = nullptr;             // [nk] diagonal of each slab mode's system
+  float *z = nullptr;              // [m][nk] column m of the inverse tridiagonal (interface response)
+  float2 *vhat = nullptr;          // [m][nk] spectra of the rows
+  float2 *fhat = nullptr;          // [nk] spectrum of the interface values placed on row m
+  float *phi = nullptr;            // [wc][wc] orthonormal sine basis of the slot, [mode][column]
+  float *sb = nullptr;             // [wc] diagonal of each slot sine mode's system
+  float *zs = nullptr;             // [wc][ms] slot responses to a unit first-row value
+  float *sinv = nullptr;           // [wc][wc] inverse of the interface Schur complement
+  float *vs = nullptr;             // [wc][ms] solved slot spectra
+  int kernels = 0;                 // launches per inner solve
+};
+
+// Programmatic dependent launch.  The solver's kernels wait for the grid
+// before them (its results are then visible) and at once let the next kernel
+// of the stream be scheduled, so that kernel's blocks are resident and waiting
+// when this one ends instead of being launched only then.  Both instructions
+// are no-ops for a kernel launched without the attribute.
+__device__ __forceinline__ void pdl_enter() {
+  asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory");
+}
+
+#ifndef PICGB_NO_PDL
+constexpr bool kPdl = true;
+#else
+constexpr bool kPdl = false;
+#endif
+
+template <typename... P, typename... A>
+void launch(void (*k)(P...), int grid, int block, size_t smem, cudaStream_t s, A... args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = dim3(unsigned(grid));
+  cfg.blockDim = dim3(unsigned(block));
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at;
+  at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at.val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = &at;
+  cfg.numAttrs = kPdl ? 1 : 0;
+  cudaLaunchKernelEx(&cfg, k, args...);
+}
+
 }  // namespace picgb
 
 struct pic_ctx {
@@ -132,6 +190,7 @@ struct pic_ctx {
   picgb::PoissonState *h_ps;   // pinned mirror
   picgb::Reducer red;
   int singular;
+  picgb::FastPoisson fp;       // direct inner solve (enabled when the geometry allows it)
   double last_ms;
   int last_outer;
   cudaEvent_t ev0, ev1;
@@ -200,6 +259,11 @@ cudaError_t launch_moments(pic_ctx *c, int s, double *d_part, int nblocks);
 
 // poisson.cu
 cudaError_t poisson_setup(pic_ctx *c);
+// Direct inner solve (fastpoisson.cu): set-up when the geometry allows it
+// (leaves c->fp.enabled = 0 otherwise) and the launches that turn the FP32
+// residual r into the correction e.
+cudaError_t fast_poisson_setup(pic_ctx *c);
+void fast_poisson_launch(pic_ctx *c, const float *r, float *e, PoissonState *ps);
 cudaError_t launch_rho(pic_ctx *c, int advance_step);
 pic_status poisson_solve(pic_ctx *c, bool zero_guess);
 cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNode_t> &deps);

@@ -42,7 +42,10 @@ constexpr int kThreads = 256;
 #define PICGB_SMALL_LEVEL 1024
 #endif
 constexpr int kSmallLevel = PICGB_SMALL_LEVEL;
-constexpr int kCoarseThreads = 256;
+#ifndef PICGB_COARSE_THREADS
+#define PICGB_COARSE_THREADS 256
+#endif
+constexpr int kCoarseThreads = PICGB_COARSE_THREADS;
 constexpr int kMaxOuter = 8;
 constexpr int kCoarsestSweeps = 16;
 #ifndef PICGB_DENSE_COARSEST
@@ -60,35 +63,6 @@ __host__ __device__ constexpr size_t pad16(size_t b) { return (b + 15) & ~size_t
 
 __device__ __forceinline__ int wrapi(int a, int n) { return a < 0 ? a + n : (a >= n ? a - n : a); }
 
-// Programmatic dependent launch.  Every kernel of this file starts by waiting
-// for the grid before it (its results are then visible) and at once lets the
-// next kernel of the stream be scheduled, so that kernel's blocks are resident
-// and waiting when this one ends instead of being launched only then.  Both
-// instructions are no-ops for a kernel launched without the attribute.
-__device__ __forceinline__ void pdl_enter() {
-  asm volatile("griddepcontrol.wait;\n\tgriddepcontrol.launch_dependents;" ::: "memory");
-}
-
-#ifndef PICGB_NO_PDL
-constexpr bool kPdl = true;
-#else
-constexpr bool kPdl = false;
-#endif
-
-template <typename... P, typename... A>
-void launch(void (*k)(P...), int grid, int block, size_t smem, cudaStream_t s, A... args) {
-  cudaLaunchConfig_t cfg = {};
-  cfg.gridDim = dim3(unsigned(grid));
-  cfg.blockDim = dim3(unsigned(block));
-  cfg.dynamicSmemBytes = smem;
-  cfg.stream = s;
-  cudaLaunchAttribute at;
-  at.id = cudaLaunchAttributeProgrammaticStreamSerialization;
-  at.val.programmaticStreamSerializationAllowed = 1;
-  cfg.attrs = &at;
-  cfg.numAttrs = kPdl ? 1 : 0;
-  cudaLaunchKernelEx(&cfg, k, args...);
-}
 
 __device__ __forceinline__ double warp_sum(double v) {
 #pragma unroll
@@ -180,6 +154,7 @@ struct FineArgs {
   double *fe;
   uint32_t *status;
   int graph;                 // kernels run inside the step graph: drive its conditionals
+  int direct;                // the inner solve is the direct one (no inner loop)
   cudaGraphConditionalHandle h_outer, h_if_outer, h_inner, h_if_inner;
 };
 
@@ -293,6 +268,9 @@ __global__ void k_resid64(FineArgs a) {
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
   const double bmean = a.ps->bmean;
+  // ||b|| is the same for every pass of a solve: formed on its first pass only
+  // (FP64 arithmetic runs at a small fraction of the FP32 rate here)
+  const bool first = a.ps->outer_iters == 0;
   double v[2] = {0.0, 0.0};
   VEC_BATCHES(base, nn) {
     double bv[kVB], lf[kVB], ph[kVB][5];
@@ -312,24 +290,27 @@ __global__ void k_resid64(FineArgs a) {
     VEC_NODES(k, n, base, nn) {
       float r32 = 0.f;
       if (fl[k] & kFree) {
-        const double bn = bv[k] - bmean;
+        const double bn = a.singular ? bv[k] - bmean : bv[k];
         const double rho = bn - lf[k];
         const double Aphi = 4.0 * ph[k][0] - ph[k][1] - ph[k][2] - ph[k][3] - ph[k][4];
         const double r = rho - Aphi;
         r32 = float(r);
-        v[0] += r * r;
-        v[1] += bn * bn;
+        v[0] = fma(r, r, v[0]);
+        if (first) v[1] = fma(bn, bn, v[1]);
       }
       a.r32[n] = r32;
-      a.e[n] = 0.f;
-      a.p[n] = 0.f;
-      a.q[n] = 0.f;
+      if (!a.direct) {             // the direct inner solve writes all of e and uses no p, q
+        a.e[n] = 0.f;
+        a.p[n] = 0.f;
+        a.q[n] = 0.f;
+      }
     }
   }
   if (grid_sum<2>(v, a.part, a.ticket) && threadIdx.x == 0) {
     PoissonState *ps = a.ps;
     ps->rr64 = v[0];
-    ps->bb = v[1];
+    if (first) ps->bb = v[1];
+    v[1] = ps->bb;
     ps->rel = v[1] > 0 ? sqrt(v[0] / v[1]) : sqrt(v[0]);
     const bool ok = ps->rel <= a.rtol || v[0] == 0.0;
     const bool give_up = !ok && ps->outer_iters >= kMaxOuter;
@@ -341,7 +322,7 @@ __global__ void k_resid64(FineArgs a) {
     if (a.graph) {
       cudaGraphSetConditional(a.h_outer, go ? 1u : 0u);
       cudaGraphSetConditional(a.h_if_outer, go ? 1u : 0u);
-      cudaGraphSetConditional(a.h_inner, go ? 1u : 0u);
+      if (!a.direct) cudaGraphSetConditional(a.h_inner, go ? 1u : 0u);
     }
     ps->inner_iters = 0;
     ps->rr0 = v[0];
@@ -1225,6 +1206,7 @@ FineArgs fine_args(pic_ctx *c) {
   a.fe = c->d_fe;
   a.status = c->d_status;
   a.graph = 0;
+  a.direct = c->fp.enabled;
   a.h_outer = a.h_if_outer = a.h_inner = a.h_if_inner = 0;
   return a;
 }
@@ -1573,6 +1555,8 @@ cudaError_t poisson_setup(pic_ctx *c) {
   if (e != cudaSuccess) return e;
   cudaEventCreate(&c->ev0);
   cudaEventCreate(&c->ev1);
+  e = fast_poisson_setup(c);
+  if (e != cudaSuccess) return e;
   return cudaGetLastError();
 }
 
@@ -1610,6 +1594,12 @@ pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
     cudaMemcpyAsync(c->h_ps, c->d_ps, sizeof(PoissonState), cudaMemcpyDeviceToHost, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
     if (!c->h_ps->go) break;
+    if (c->fp.enabled) {
+      fast_poisson_launch(c, c->d_r32, c->d_e, c->d_ps);
+      launch(k_correct, nb, kThreads, 0, c->stream, a);
+      c->launches += 1;
+      continue;
+    }
     launch_vcycle(c, m);
     launch_zw(c, a);
     for (int it = 0; it < c->cfg.poisson_maxit; it += batch) {
@@ -1686,7 +1676,8 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   const MGArgs m = mg_args(c);
   const int nb = c->red.nblocks;
   cudaGraphConditionalHandle h[4];
-  for (int k = 0; k < 4; ++k) {
+  const int nh = c->fp.enabled ? 2 : 4;
+  for (int k = 0; k < nh; ++k) {
     cudaError_t e = cudaGraphConditionalHandleCreate(&h[k], top, k == 0 ? 1u : 0u,
                                                      cudaGraphCondAssignDefault);
     if (e != cudaSuccess) return note(e, "cudaGraphConditionalHandleCreate");
@@ -1694,8 +1685,8 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   a.graph = 1;
   a.h_outer = h[0];
   a.h_if_outer = h[1];
-  a.h_inner = h[2];
-  a.h_if_inner = h[3];
+  a.h_inner = c->fp.enabled ? 0 : h[2];
+  a.h_if_inner = c->fp.enabled ? 0 : h[3];
   cudaError_t e;
 #define CK(x) do { if ((e = (x)) != cudaSuccess) { note(e, #x); return e; } } while (0)
   CK(cap_begin(s, top, deps));
@@ -1711,6 +1702,15 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   launch(k_resid64, nb, kThreads, 0, s, a);
   CK(cap_end(s, d));
   CK(add_cond(b_outer, d, h[1], cudaGraphCondTypeIf, &n_if_outer, &b_if_outer));
+  if (c->fp.enabled) {
+    // direct inner solve: IF(go) { solve, correct }
+    CK(cap_begin(s, b_if_outer, {}));
+    fast_poisson_launch(c, c->d_r32, c->d_e, c->d_ps);
+    launch(k_correct, nb, kThreads, 0, s, a);
+    CK(cap_end(s, d));
+    deps.assign(1, n_outer);
+    return cudaGetLastError();
+  }
   CK(cap_begin(s, b_if_outer, {}));
   launch_vcycle(c, m);
   launch_zw(c, a);
@@ -1735,9 +1735,11 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
 
 // Kernels one solve launched, from its device counters (graph mode).
 int64_t poisson_kernel_count(pic_ctx *c, const PoissonState &ps) {
+  const int64_t O = ps.outer_iters, I = ps.total_iters;
+  if (c->fp.enabled)   // init + resid per outer pass (+1 final) + per pass (direct solve, correct)
+    return 1 + (O + 1) + O * (c->fp.kernels + 1) + (c->cfg.warm_start != 1 ? 1 : 0);
   // a V-cycle with w = A z and the inner products: fused into its last kernel unless lc = 0
   const int64_t vc = 2 * c->lc + 1 + (c->lc == 0 ? 1 : 0);
-  const int64_t O = ps.outer_iters, I = ps.total_iters;
   // init + resid per outer pass (+1 final) + per inner solve (V-cycle, correct)
   // + per iteration (cg) + per non-final iteration (V-cycle)
   return 1 + (O + 1) + O * (vc + 1) + I + std::max<int64_t>(I - O, 0) * vc +

@@ -23,6 +23,17 @@ SMALL = {
 }
 
 
+# boxes periodic in y with a power-of-two ny and bounded in x: the direct
+# (FFT / tridiagonal / interface) inner Poisson solve applies
+DIRECT = {
+    "trench64": synth.small_trench(nx=72, ny=64, depth=20, width=6, ppc=12, seed=31),
+    "trench32_wide": synth.small_trench(nx=40, ny=32, depth=10, width=11, ppc=12, seed=32),
+    "plates": synth.small_trench(nx=48, ny=64, depth=0, width=0, ppc=10, seed=33),
+    "slit": synth.small_trench(nx=48, ny=64, depth=12, width=1, ppc=10, seed=34),
+}
+ALL = {**SMALL, **DIRECT}
+
+
 @pytest.fixture(scope="module", autouse=True)
 def _built():
     import __graft_entry__
@@ -75,10 +86,12 @@ def test_deposit_particles_on_grid_lines():
     assert rg.sum() == pytest.approx(ro.sum(), abs=1e-9 * np.abs(ro).sum())
 
 
-@pytest.mark.parametrize("name", list(SMALL))
+@pytest.mark.parametrize("name", list(ALL))
 def test_poisson_and_field_match_oracle(name):
-    w = SMALL[name].replace(poisson_rtol=1e-10)
+    import paper_1610_03918_gb300 as pg
+    w = ALL[name].replace(poisson_rtol=1e-10)
     gs = gpu_sim(w)
+    assert gs.solver() == (pg.POISSON_AUTO if name in DIRECT else pg.POISSON_MULTIGRID)
     geom = from_workload(w)
     rho = synth.random_rho(w, seed=21, scale=0.3)
     gs.set_rho_ext(rho)
@@ -107,12 +120,38 @@ def test_poisson_trench_bias_vacuum():
     assert np.abs(gs.phi() - phi_o).max() <= 1e-6 * 20.0
 
 
-@pytest.mark.parametrize("name,graphs", [(n, True) for n in SMALL] + [("trench", False)])
+def test_direct_and_multigrid_solves_agree():
+    import paper_1610_03918_gb300 as pg
+    w = DIRECT["trench64"].replace(poisson_rtol=1e-10)
+    rho = synth.random_rho(w, seed=23, scale=0.3)
+    out = []
+    for method in (pg.POISSON_AUTO, pg.POISSON_MULTIGRID):
+        gs = gpu_sim(w, poisson_method=method)
+        assert gs.solver() == method
+        gs.set_rho_ext(rho)
+        gs.step(0)
+        out.append((gs.phi(), gs.poisson_stats()))
+    (pd, sd), (pm, sm) = out
+    assert np.abs(pd - pm).max() <= 1e-8 * np.abs(pm).max()
+    # the direct inner solve needs a refinement pass or two, not an iteration count
+    assert sd[0] <= 3
+
+
+def test_direct_solver_applies_only_to_its_geometry():
+    import paper_1610_03918_gb300 as pg
+    for w in (synth.small_trench(nx=40, ny=40),            # ny not a power of two
+              synth.bounded_square_256(nx=32, ny=32),      # y bounded
+              synth.periodic_square_64(nx=32, ny=32)):     # x periodic
+        assert gpu_sim(w).solver() == pg.POISSON_MULTIGRID, w.name
+
+
+@pytest.mark.parametrize("name,graphs", [(n, True) for n in SMALL] + [("trench", False)] +
+                         [("trench64", True), ("trench64", False)])
 def test_step_by_step_parity(name, graphs):
     """Each step starts both sides from the GPU's state; the oracle recomputes
     its own fields from it.  graphs=False drives the same kernels from the
     host loop instead of the captured step graph."""
-    w, gs, os_ = _loaded(SMALL[name], graphs=graphs)
+    w, gs, os_ = _loaded(ALL[name], graphs=graphs)
     geom = from_workload(w)
     gs.step(0)
     os_.prepare()
