@@ -381,7 +381,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppc", type=int, default=None, help="override particles per cell")
-    ap.add_argument("--sort-every", type=int, default=None, help="steps between tile sorts")
+    ap.add_argument("--sort-every", type=int, default=24,
+                    help="steps between tile sorts (24: the fastest of 8/16/24/32/48 on the trench)")
     ap.add_argument("--warm-start", type=int, default=1,
                     help="Poisson initial guess: 0 zero, 1 previous, 2 extrapolated")
     ap.add_argument("--no-graphs", action="store_true",

@@ -37,7 +37,7 @@ namespace {
 constexpr int kFftThreads = 256;
 constexpr int kMaxNy = 2048;
 constexpr int kMaxRows = 4096;         // rectangle rows (one mode's reduction fits in shared memory)
-constexpr int kPcrThreads = 256;
+constexpr int kPcrThreads = 512;
 constexpr int kSlotThreads = 256;
 constexpr size_t kSmemMax = 200 * 1024;
 
@@ -45,9 +45,10 @@ struct FPArgs {
   int ny, nk, logny, m, xs, slot, c0, wc, ms;
   const float2 *tw;
   const float *dk, *z;               // diagonal per slab mode, interface responses
-  float2 *vhat, *fhat;
+  float2 *vhat;
   const float *phi, *sb, *zs, *sinv; // slot basis, diagonal per sine mode, responses
   float *vs;                         // [wc][ms] solved slot spectra
+  float *ug;                         // [wc] interface values
   const float *r;
   float *e;
   PoissonState *ps;
@@ -229,16 +230,14 @@ __global__ void __launch_bounds__(kPcrThreads) k_fp_tridiag(FPArgs f) {
 
 // Interface, one CTA: g = r_G + v_R(row m) + v_S(first slot row) on the
 // interface columns (v_R by the inverse DFT of the solved spectra of row m,
-// v_S from the solved slot spectra), u_G = S^-1 g, the spectrum of u_G placed
-// on row m (for the slab correction) and the corrected slot values.  Writes e
-// on the interface and in the slot.
+// v_S from the solved slot spectra), then u_G = S^-1 g, written to ug and to
+// e on the interface.  The corrections that u_G makes to the slab and the
+// slot are applied by the inverse-transform kernel.
 __global__ void __launch_bounds__(kSlotThreads) k_fp_interface(FPArgs f) {
   extern __shared__ float ss[];
   const int wc = f.wc, ms = f.ms, ny = f.ny, nk = f.nk;
   float *sphi = ss;                  // [wc][wc] sine basis
   float *gv = sphi + wc * wc;        // [wc] interface right-hand side g
-  float *ug = gv + wc;               // [wc] interface values
-  float *sh = ug + wc;               // [wc] sine spectrum of u_G
   for (int t = threadIdx.x; t < wc * wc; t += blockDim.x) sphi[t] = __ldg(f.phi + t);
   pdl_enter();
   __syncthreads();
@@ -261,38 +260,11 @@ __global__ void __launch_bounds__(kSlotThreads) k_fp_interface(FPArgs f) {
     }
   }
   __syncthreads();
-  // u_G = S^-1 g
   for (int c = threadIdx.x; c < wc; c += blockDim.x) {
     float acc = 0.f;
     for (int qq = 0; qq < wc; ++qq) acc = fmaf(__ldg(f.sinv + c * wc + qq), gv[qq], acc);
-    ug[c] = acc;
+    f.ug[c] = acc;
     f.e[f.xs * ny + f.c0 + c] = acc;
-  }
-  __syncthreads();
-  // spectrum of u_G on row m, and its sine spectrum for the slot
-  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
-    float2 acc = make_float2(0.f, 0.f);
-    for (int c = 0; c < wc; ++c) {
-      const float2 t = __ldg(f.tw + ((k * (f.c0 + c)) & (ny - 1)));   // exp(-2 pi i k j / ny)
-      acc.x = fmaf(ug[c], t.x, acc.x);
-      acc.y = fmaf(ug[c], t.y, acc.y);
-    }
-    f.fhat[k] = acc;
-  }
-  for (int pm = threadIdx.x; pm < wc; pm += blockDim.x) {
-    float acc = 0.f;
-    for (int c = 0; c < wc; ++c) acc = fmaf(sphi[pm * wc + c], ug[c], acc);
-    sh[pm] = acc;
-  }
-  __syncthreads();
-  // corrected slot values, back to the columns
-  for (int t = threadIdx.x; t < ms * wc; t += blockDim.x) {
-    const int row = t / wc, c = t - row * wc;
-    float acc = 0.f;
-    for (int pm = 0; pm < wc; ++pm)
-      acc = fmaf(fmaf(__ldg(f.zs + pm * ms + row), sh[pm], __ldg(f.vs + pm * ms + row)),
-                 sphi[pm * wc + c], acc);
-    f.e[(f.xs + 1 + row) * ny + f.c0 + c] = acc;
   }
   if (threadIdx.x == 0) {
     f.ps->inner_iters += 1;
@@ -301,20 +273,60 @@ __global__ void __launch_bounds__(kSlotThreads) k_fp_interface(FPArgs f) {
 }
 
 // Inverse transforms of rows i0, i1 (with the interface term z_k(i) fhat[k]
-// when there is a slot): Z[k] = X_a[k] + i X_b[k] over the full spectrum
+// when there is a slot, fhat[k] = sum_c u_G(c) exp(-2 pi i k (c0 + c) / ny)
+// formed here from u_G): Z[k] = X_a[k] + i X_b[k] over the full spectrum
 // (X[-k] = conj X[k]), e(i0) = Re IFFT(Z) / ny, e(i1) = Im IFFT(Z) / ny.
+// The CTAs after the slab's take the slot rows: with the sine spectrum
+// sh[p] = sum_c phi[p][c] u_G(c), e(row, c) = sum_p (v_S[p][row] +
+// zs[p][row] sh[p]) phi[p][c].
 __global__ void __launch_bounds__(kFftThreads) k_fp_inverse(FPArgs f) {
   extern __shared__ float2 sm[];
+  const int rows = (f.m + 1) / 2, wc = f.wc;
+  if (int(blockIdx.x) >= rows) {
+    float *sphi = reinterpret_cast<float *>(sm), *ug = sphi + wc * wc, *sh = ug + wc;
+    for (int t = threadIdx.x; t < wc * wc; t += blockDim.x) sphi[t] = __ldg(f.phi + t);
+    pdl_enter();
+    for (int c = threadIdx.x; c < wc; c += blockDim.x) ug[c] = f.ug[c];
+    __syncthreads();
+    for (int pm = threadIdx.x; pm < wc; pm += blockDim.x) {
+      float acc = 0.f;
+      for (int c = 0; c < wc; ++c) acc = fmaf(sphi[pm * wc + c], ug[c], acc);
+      sh[pm] = acc;
+    }
+    __syncthreads();
+    const int t = (blockIdx.x - rows) * blockDim.x + threadIdx.x;
+    if (t < f.ms * wc) {
+      const int row = t / wc, c = t - row * wc;
+      float acc = 0.f;
+      for (int pm = 0; pm < wc; ++pm)
+        acc = fmaf(fmaf(__ldg(f.zs + pm * f.ms + row), sh[pm], __ldg(f.vs + pm * f.ms + row)),
+                   sphi[pm * wc + c], acc);
+      f.e[(f.xs + 1 + row) * f.ny + f.c0 + c] = acc;
+    }
+    return;
+  }
   float2 *x = sm, *y = sm + f.ny, *tw = sm + 2 * f.ny;
+  float *ug = reinterpret_cast<float *>(tw + (f.ny >> 1));
   for (int t = threadIdx.x; t < (f.ny >> 1); t += blockDim.x) tw[t] = f.tw[t];
   pdl_enter();
+  if (f.slot)
+    for (int c = threadIdx.x; c < wc; c += blockDim.x) ug[c] = f.ug[c];
+  __syncthreads();
   const int i0 = 2 * blockIdx.x + 1, i1 = i0 + 1;
   const bool two = i1 <= f.m;
+  const int half = f.ny >> 1;
   for (int k = threadIdx.x; k < f.nk; k += blockDim.x) {
     float2 a = f.vhat[(i0 - 1) * f.nk + k];
     float2 b = two ? f.vhat[(i1 - 1) * f.nk + k] : make_float2(0.f, 0.f);
     if (f.slot) {
-      const float2 fh = f.fhat[k];
+      float2 fh = make_float2(0.f, 0.f);
+      for (int c = 0; c < wc; ++c) {
+        const int t = (k * (f.c0 + c)) & (f.ny - 1);
+        // exp(-2 pi i t / ny); the table holds t < ny / 2, the rest is its negative
+        const float2 w = t < half ? tw[t] : make_float2(-tw[t - half].x, -tw[t - half].y);
+        fh.x = fmaf(ug[c], w.x, fh.x);
+        fh.y = fmaf(ug[c], w.y, fh.y);
+      }
       const float za = f.z[(i0 - 1) * f.nk + k];
       a = make_float2(fmaf(za, fh.x, a.x), fmaf(za, fh.y, a.y));
       if (two) {
@@ -355,9 +367,9 @@ FPArgs fp_args(pic_ctx *c, const float *r, float *e, PoissonState *ps) {
   a.dk = p.dk;
   a.z = p.z;
   a.vhat = p.vhat;
-  a.fhat = p.fhat;
   a.phi = p.phi;
   a.vs = p.vs;
+  a.ug = p.ug;
   a.sb = p.sb;
   a.zs = p.zs;
   a.sinv = p.sinv;
@@ -367,13 +379,16 @@ FPArgs fp_args(pic_ctx *c, const float *r, float *e, PoissonState *ps) {
   return a;
 }
 
-size_t fft_smem_bytes(int ny) { return size_t(2 * ny + ny / 2) * sizeof(float2); }
+size_t fft_smem_bytes(int ny, int wc) {
+  return std::max(size_t(2 * ny + ny / 2) * sizeof(float2) + size_t(wc) * 4,
+                  (size_t(wc) * wc + 2 * size_t(wc)) * 4);
+}
 // two Rows<T> sets of n rows (with the alignment padding of carve_rows)
 size_t rows_bytes(int n, size_t tsize) { return 2 * (size_t(3 * n + (n & 1)) * 4 + size_t(n) * tsize); }
 size_t tridiag_smem_bytes(int m, int ms, int wc) {
   return std::max(rows_bytes(m, sizeof(float2)), rows_bytes(ms, 4) + size_t(wc) * 4);
 }
-size_t slot_smem_bytes(int wc) { return (size_t(wc) * wc + 3 * size_t(wc)) * 4; }
+size_t slot_smem_bytes(int wc) { return (size_t(wc) * wc + size_t(wc)) * 4; }
 
 // Thomas factors of tridiag(-1, d, -1) of size n: w_1 = 1/d, w_i = 1/(d - w_{i-1})
 void thomas_factors(double d, int n, double *w) {
@@ -562,9 +577,9 @@ cudaError_t fast_poisson_setup(pic_ctx *c) {
     p.sb = upload(c, sbf);
     p.zs = upload(c, zsf);
     p.sinv = upload(c, sinvf);
-    p.fhat = static_cast<float2 *>(dev_alloc(c, size_t(nk) * sizeof(float2)));
     p.vs = static_cast<float *>(dev_alloc(c, size_t(wc) * ms * sizeof(float)));
-    if (!p.z || !p.phi || !p.sb || !p.zs || !p.sinv || !p.fhat || !p.vs) return cudaErrorMemoryAllocation;
+    p.ug = static_cast<float *>(dev_alloc(c, size_t(wc) * sizeof(float)));
+    if (!p.z || !p.phi || !p.sb || !p.zs || !p.sinv || !p.vs || !p.ug) return cudaErrorMemoryAllocation;
   }
   p.ny = ny;
   p.nk = nk;
@@ -590,11 +605,12 @@ cudaError_t fast_poisson_setup(pic_ctx *c) {
 void fast_poisson_launch(pic_ctx *c, const float *r, float *e, PoissonState *ps) {
   const FPArgs a = fp_args(c, r, e, ps);
   const int rows = (a.m + 1) / 2;
-  launch(k_fp_forward, rows, kFftThreads, fft_smem_bytes(a.ny), c->stream, a);
+  launch(k_fp_forward, rows, kFftThreads, fft_smem_bytes(a.ny, a.wc), c->stream, a);
   launch(k_fp_tridiag, a.nk + (a.slot ? a.wc : 0), kPcrThreads,
          tridiag_smem_bytes(a.m, a.slot ? a.ms : 0, a.wc), c->stream, a);
   if (a.slot) launch(k_fp_interface, 1, kSlotThreads, slot_smem_bytes(a.wc), c->stream, a);
-  launch(k_fp_inverse, rows, kFftThreads, fft_smem_bytes(a.ny), c->stream, a);
+  const int slot_ctas = a.slot ? (a.ms * a.wc + kFftThreads - 1) / kFftThreads : 0;
+  launch(k_fp_inverse, rows + slot_ctas, kFftThreads, fft_smem_bytes(a.ny, a.wc), c->stream, a);
   c->launches += c->fp.kernels;
 }
 

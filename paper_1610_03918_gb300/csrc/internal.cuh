@@ -110,12 +110,12 @@ struct FastPoisson {
   float *dk = nullptr;             // [nk] diagonal of each slab mode's system
   float *z = nullptr;              // [m][nk] column m of the inverse tridiagonal (interface response)
   float2 *vhat = nullptr;          // [m][nk] spectra of the rows
-  float2 *fhat = nullptr;          // [nk] spectrum of the interface values placed on row m
   float *phi = nullptr;            // [wc][wc] orthonormal sine basis of the slot, [mode][column]
   float *sb = nullptr;             // [wc] diagonal of each slot sine mode's system
   float *zs = nullptr;             // [wc][ms] slot responses to a unit first-row value
   float *sinv = nullptr;           // [wc][wc] inverse of the interface Schur complement
   float *vs = nullptr;             // [wc][ms] solved slot spectra
+  float *ug = nullptr;             // [wc] interface values
   int kernels = 0;                 // launches per inner solve
 };
 

@@ -30,6 +30,8 @@ __device__ __forceinline__ int tile_of(const Geom &g, int c) {
 // ---------------------------------------------------------------------------
 // Counting sort by tile
 // ---------------------------------------------------------------------------
+constexpr int kHistSmemTiles = 12288;   // shared-memory tile histogram up to 48 KB
+
 struct SortArgs {
   const ParticleBuf *pbufs;  // [species][2] on the device
   int32_t *cur;              // current buffer per species (device)
@@ -42,22 +44,48 @@ struct SortArgs {
   int ntiles;
 };
 
+// The counting passes take 4 consecutive slots per lane (16-byte loads, 128
+// slots per warp per iteration) and treat them as 4 independent groups, so a
+// warp has all its loads, then 4 match / atomic rounds, in flight at once.
+// Slot counts are multiples of 4 within the buffers' capacity, so a vector
+// read starting below n stays inside the allocation; slots >= n are ignored.
+// Tile histogram.  Each block takes a contiguous range of slots, so its
+// particles fall in a few tiles (they were sorted a few steps ago); with SMEM
+// the counts gather in a shared-memory histogram and only its nonzero bins
+// reach the global counters, instead of every warp's atomics meeting on the
+// same few hot counters.
+template <bool SMEM>
 __global__ void k_sort_hist(SortArgs a) {
+  extern __shared__ uint32_t hist[];
   const int s = blockIdx.y;
   const int64_t n = a.nslots[s];
-  const int lane = threadIdx.x & 31;
-  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
-  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  const int lane = threadIdx.x & 31, wib = threadIdx.x >> 5, nwb = blockDim.x >> 5;
   uint32_t *cnt = a.count + int64_t(s) * a.ntiles;
-  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
-    const int64_t p = base + lane;
-    int t = -1;
-    if (p < n) {
-      const int c = a.pbufs[2 * s + a.cur[s]].cell[p];
-      if (c >= 0) t = tile_of(a.g, c);
+  uint32_t *h = SMEM ? hist : cnt;
+  if (SMEM) {
+    for (int t = threadIdx.x; t < a.ntiles; t += blockDim.x) hist[t] = 0u;
+    __syncthreads();
+  }
+  const int32_t *cell = a.pbufs[2 * s + a.cur[s]].cell;
+  const int64_t units = (n + 127) / 128;                 // 128 slots per warp step
+  const int64_t per = (units + gridDim.x - 1) / gridDim.x;
+  const int64_t u1 = min(units, int64_t(blockIdx.x + 1) * per);
+  for (int64_t u = int64_t(blockIdx.x) * per + wib; u < u1; u += nwb) {
+    const int64_t p = u * 128 + 4 * lane;
+    int4 c4 = make_int4(-1, -1, -1, -1);
+    if (p < n) c4 = *reinterpret_cast<const int4 *>(cell + p);
+    const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int t = (p + j < n && cc[j] >= 0) ? tile_of(a.g, cc[j]) : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, t);
+      if (t >= 0 && lane == __ffs(peers) - 1) atomicAdd(&h[t], (uint32_t)__popc(peers));
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, t);
-    if (t >= 0 && lane == __ffs(peers) - 1) atomicAdd(&cnt[t], (uint32_t)__popc(peers));
+  }
+  if (SMEM) {
+    __syncthreads();
+    for (int t = threadIdx.x; t < a.ntiles; t += blockDim.x)
+      if (hist[t]) atomicAdd(&cnt[t], hist[t]);
   }
 }
 
@@ -143,32 +171,46 @@ __global__ void k_sort_scatter(SortArgs a) {
   const int s = blockIdx.y;
   const int64_t n = a.nslots[s];
   const int lane = threadIdx.x & 31;
+  const unsigned lower = (1u << lane) - 1u;
   const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
   const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
   uint32_t *cur = a.cursor + int64_t(s) * a.ntiles;
   const uint32_t *st = a.start + int64_t(s) * a.ntiles;
   const ParticleBuf S = a.pbufs[2 * s + a.cur[s]], D = a.pbufs[2 * s + (a.cur[s] ^ 1)];
-  for (int64_t base = warp * 32; base < n; base += nwarps * 32) {
-    const int64_t p = base + lane;
-    int t = -1, c = -1;
+  for (int64_t base = warp * 128; base < n; base += nwarps * 128) {
+    const int64_t p = base + 4 * lane;
+    int4 c4 = make_int4(-1, -1, -1, -1);
+    float4 fx4 = make_float4(0.f, 0.f, 0.f, 0.f), fy4 = fx4, vx4 = fx4, vy4 = fx4;
+    uint4 id4 = make_uint4(0u, 0u, 0u, 0u);
     if (p < n) {
-      c = S.cell[p];
-      if (c >= 0) t = tile_of(a.g, c);
+      c4 = *reinterpret_cast<const int4 *>(S.cell + p);
+      fx4 = *reinterpret_cast<const float4 *>(S.fx + p);
+      fy4 = *reinterpret_cast<const float4 *>(S.fy + p);
+      vx4 = *reinterpret_cast<const float4 *>(S.vx + p);
+      vy4 = *reinterpret_cast<const float4 *>(S.vy + p);
+      id4 = *reinterpret_cast<const uint4 *>(S.id + p);
     }
-    const unsigned peers = __match_any_sync(0xffffffffu, t);
-    const int leader = __ffs(peers) - 1;
-    uint32_t b = 0;
-    if (t >= 0 && lane == leader) b = atomicAdd(&cur[t], (uint32_t)__popc(peers));
-    b = __shfl_sync(0xffffffffu, b, leader);
-    if (t >= 0) {
-      const uint32_t rank = __popc(peers & ((1u << lane) - 1u));
-      const int64_t d = int64_t(st[t]) + b + rank;
-      D.cell[d] = c;
-      D.fx[d] = S.fx[p];
-      D.fy[d] = S.fy[p];
-      D.vx[d] = S.vx[p];
-      D.vy[d] = S.vy[p];
-      D.id[d] = S.id[p];
+    const int cc[4] = {c4.x, c4.y, c4.z, c4.w};
+    const float fx[4] = {fx4.x, fx4.y, fx4.z, fx4.w}, fy[4] = {fy4.x, fy4.y, fy4.z, fy4.w};
+    const float vx[4] = {vx4.x, vx4.y, vx4.z, vx4.w}, vy[4] = {vy4.x, vy4.y, vy4.z, vy4.w};
+    const uint32_t id[4] = {id4.x, id4.y, id4.z, id4.w};
+#pragma unroll
+    for (int j = 0; j < 4; ++j) {
+      const int t = (p + j < n && cc[j] >= 0) ? tile_of(a.g, cc[j]) : -1;
+      const unsigned peers = __match_any_sync(0xffffffffu, t);
+      const int leader = __ffs(peers) - 1;
+      uint32_t b = 0;
+      if (t >= 0 && lane == leader) b = atomicAdd(&cur[t], (uint32_t)__popc(peers));
+      b = __shfl_sync(0xffffffffu, b, leader);
+      if (t >= 0) {
+        const int64_t d = int64_t(st[t]) + b + __popc(peers & lower);
+        D.cell[d] = cc[j];
+        D.fx[d] = fx[j];
+        D.fy[d] = fy[j];
+        D.vx[d] = vx[j];
+        D.vy[d] = vy[j];
+        D.id[d] = id[j];
+      }
     }
   }
 }
@@ -626,8 +668,11 @@ cudaError_t launch_sort(pic_ctx *c) {
   a.nslots_out = c->d_nslots + 2;
   a.g = c->g;
   a.ntiles = c->g.ntx * c->g.nty;
-  const dim3 grid(c->num_sms * 4, 2);
-  k_sort_hist<<<grid, 256, 0, c->stream>>>(a);
+  const dim3 grid(c->num_sms * 8, 2);   // 8 CTAs of 256 threads per SM and species
+  if (a.ntiles <= kHistSmemTiles)
+    k_sort_hist<true><<<grid, 256, size_t(a.ntiles) * 4, c->stream>>>(a);
+  else
+    k_sort_hist<false><<<grid, 256, 0, c->stream>>>(a);
   k_sort_scan<<<1, 1024, 0, c->stream>>>(a);
   k_sort_scatter<<<grid, 256, 0, c->stream>>>(a);
   k_sort_finish<<<1, 1, 0, c->stream>>>(c->d_nslots, c->d_cur);
