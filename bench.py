@@ -40,9 +40,9 @@ BYTES_PER_PARTICLE_STEP = 40
 # valid for the kernel source whose hash is recorded with it.
 NCU_TRAFFIC = {
     # k_particles<0>, 512x1024 trench at 20 ppc (16.95M live particles, 0.4 GB
-    # state, larger than L2), 3rd launch: 361.1 MB read + 291.4 MB written
-    "source_sha256": "34a69de580f8e5fff9bc58381c0ca569daf1b72f409b4a87691c4b16e5cdb706",
-    "bytes_per_particle": 38.50,
+    # state, larger than L2), 3rd launch: 360.8 MB read + 291.1 MB written
+    "source_sha256": "d4aacd3028b1ee578efbd84af8dc5d607133da8647f1211d02017a2fe0456b2e",
+    "bytes_per_particle": 38.46,
 }
 
 
@@ -52,6 +52,10 @@ def _peaks():
         d = json.load(open(p))
         return float(d["hbm_gbs"]), "measured"
     return 6800.0, "fallback"
+
+
+def _poisson_method(pg, args):
+    return pg.POISSON_MULTIGRID if args.poisson_method == "multigrid" else pg.POISSON_AUTO
 
 
 def _kernel_sha():
@@ -232,7 +236,7 @@ def run_ensemble(args):
     if args.sort_every:
         wl = [w.replace(sort_every=args.sort_every) for w in wl]
     batch = pg.Batch(wl, capacities=[int(synth.plasma_cells(w).sum()) * w.ppc for w in wl],
-                     device=local, timing=True)
+                     device=local, timing=True, poisson_method=_poisson_method(pg, args))
     n0 = 0
     for m, w in zip(batch.members, wl):
         for s in (0, 1):
@@ -381,6 +385,8 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppc", type=int, default=None, help="override particles per cell")
+    ap.add_argument("--poisson-method", default="auto", choices=["auto", "multigrid"],
+                    help="inner Poisson solver: auto (direct where the box allows) or multigrid PCG")
     ap.add_argument("--sort-every", type=int, default=24,
                     help="steps between tile sorts (24: the fastest of 8/16/24/32/48 on the trench)")
     ap.add_argument("--warm-start", type=int, default=1,
@@ -414,7 +420,7 @@ def main():
     parts = [synth.maxwellian_load(w, s) for s in (0, 1)]
     n0 = sum(len(p) for p in parts)
     sim = pg.Sim(w, capacity=len(parts[0]), device=local, timing=True, graphs=not args.no_graphs,
-                 warm_start=args.warm_start)
+                 warm_start=args.warm_start, poisson_method=_poisson_method(pg, args))
     for s in (0, 1):
         sim.load_particles(s, parts[s], v_at_t0=True)
     sim.step(args.warmup)
@@ -506,6 +512,7 @@ def main():
                        "particles_loaded": n0, "live_particles": live_mean,
                        "sort_every": w.sort_every, "poisson_rtol": w.poisson_rtol,
                        "warm_start": ["zero", "previous", "extrapolated"][args.warm_start],
+                       "poisson_inner_solver": "direct" if sim.solver() == pg.POISSON_AUTO else "multigrid PCG",
                        "l2": "inputs larger than L2 (particle state %.1f GB)" % (n0 * 24 / 1e9),
                        "parallelism": f"replicas{ws}" if ws > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
