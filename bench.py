@@ -233,8 +233,8 @@ def run_ensemble(args):
     wl = [synth.ensemble_member(k) for k in range(args.members)]
     if args.ppc:
         wl = [w.replace(ppc=args.ppc) for w in wl]
-    if args.sort_every:
-        wl = [w.replace(sort_every=args.sort_every) for w in wl]
+    # an ensemble takes one fixed interval (the tuned one is per context)
+    wl = [w.replace(sort_every=args.sort_every or 24) for w in wl]
     batch = pg.Batch(wl, capacities=[int(synth.plasma_cells(w).sum()) * w.ppc for w in wl],
                      device=local, timing=True, poisson_method=_poisson_method(pg, args))
     n0 = 0
@@ -387,8 +387,9 @@ def main():
     ap.add_argument("--ppc", type=int, default=None, help="override particles per cell")
     ap.add_argument("--poisson-method", default="auto", choices=["auto", "multigrid"],
                     help="inner Poisson solver: auto (direct where the box allows) or multigrid PCG")
-    ap.add_argument("--sort-every", type=int, default=24,
-                    help="steps between tile sorts (24: the fastest of 8/16/24/32/48 on the trench)")
+    ap.add_argument("--sort-every", type=int, default=0,
+                    help="steps between tile sorts; 0 (default): the library times and picks it "
+                         "during the warm-up")
     ap.add_argument("--warm-start", type=int, default=1,
                     help="Poisson initial guess: 0 zero, 1 previous, 2 extrapolated")
     ap.add_argument("--no-graphs", action="store_true",
@@ -415,7 +416,7 @@ def main():
     w = synth.trench_512x1024(seed=3 + rank)
     if args.ppc:
         w = w.replace(ppc=args.ppc)
-    if args.sort_every:
+    if args.sort_every is not None:
         w = w.replace(sort_every=args.sort_every)
     parts = [synth.maxwellian_load(w, s) for s in (0, 1)]
     n0 = sum(len(p) for p in parts)
@@ -424,6 +425,11 @@ def main():
     for s in (0, 1):
         sim.load_particles(s, parts[s], v_at_t0=True)
     sim.step(args.warmup)
+    warm = args.warmup
+    while sim.sort_interval()[0] == 0:    # a tuned sort interval is chosen before timing starts
+        sim.step(8)
+        warm += 8
+    sort_interval, sort_tuned = sim.sort_interval()
     sim.timing()
     live0 = int(sim.counts()[1].sum())
 
@@ -510,7 +516,9 @@ def main():
             "data": "synthetic",
             "config": {"workload": w.name, "nx": w.nx, "ny": w.ny, "ppc": w.ppc,
                        "particles_loaded": n0, "live_particles": live_mean,
-                       "sort_every": w.sort_every, "poisson_rtol": w.poisson_rtol,
+                       "sort_every": (f"tuned by the library: {sort_interval}" if sort_tuned
+                                      else sort_interval),
+                       "warmup_steps_run": warm, "poisson_rtol": w.poisson_rtol,
                        "warm_start": ["zero", "previous", "extrapolated"][args.warm_start],
                        "poisson_inner_solver": "direct" if sim.solver() == pg.POISSON_AUTO else "multigrid PCG",
                        "l2": "inputs larger than L2 (particle state %.1f GB)" % (n0 * 24 / 1e9),

@@ -94,7 +94,13 @@ typedef struct {
   double charge[2];               /* species charge in units of e: {-1, +1} */
   int32_t ppc[2];                 /* particles per cell at density n_0: weight = 1/ppc */
   int64_t capacity[2];            /* maximum particles per species */
-  int32_t sort_every;             /* steps between tile sorts (>= 1) */
+  int32_t sort_every;             /* steps between tile sorts (>= 1); 0: chosen by the library --
+                                     it sorts, times the particle kernel on each of the next 48
+                                     steps (waiting for each of them), and keeps the interval
+                                     S in [4, 48] that minimises (sort time + particle time of
+                                     the S steps after a sort) / S.  Results do not depend on
+                                     it (the deposit is exact and the reductions run in a fixed
+                                     order).  pic_batch_init requires >= 1. */
   int32_t poisson_maxit;          /* cap on inner PCG iterations per solve */
   double poisson_rtol;            /* target ||b - A phi||_2 / ||b||_2 (FP64) */
   int32_t warm_start;             /* 0: zero initial guess each solve, 1: previous phi,
@@ -152,8 +158,10 @@ enum {
                             pic_step calls since the last read; reading resets it */
   PIC_DIAG_PHI_VACUUM = 13, /* [nxn*nyn]: potential of the empty box (Dirichlet values only),
                                solved once to 1e-10 */
-  PIC_DIAG_SOLVER = 14      /* int32: inner Poisson solver in use, 0 direct, 1 multigrid PCG
+  PIC_DIAG_SOLVER = 14,     /* int32: inner Poisson solver in use, 0 direct, 1 multigrid PCG
                                (pic_config.poisson_method) */
+  PIC_DIAG_SORT = 15        /* int32[2]: steps between tile sorts in use (0 while it is being
+                               tuned), and 1 if it was chosen by the tuning of sort_every = 0 */
 };
 
 /* Create a context from cfg.  Builds the conductor mask, Dirichlet nodes and

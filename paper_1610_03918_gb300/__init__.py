@@ -29,7 +29,7 @@ PIC_LOAD_V_AT_T0 = 1
 (PIC_DIAG_ENERGY, PIC_DIAG_MOMENTUM, PIC_DIAG_COUNTS, PIC_DIAG_SURFACE, PIC_DIAG_HITS,
  PIC_DIAG_RHO, PIC_DIAG_PHI, PIC_DIAG_E, PIC_DIAG_STATE_E, PIC_DIAG_STATE_I,
  PIC_DIAG_POISSON, PIC_DIAG_STATUS, PIC_DIAG_TIMING, PIC_DIAG_PHI_VACUUM,
- PIC_DIAG_SOLVER) = range(15)
+ PIC_DIAG_SOLVER, PIC_DIAG_SORT) = range(16)
 (WALL_XMIN, WALL_XMAX, WALL_YMIN, WALL_YMAX, WALL_COND_PX, WALL_COND_MX,
  WALL_COND_PY, WALL_COND_MY) = range(8)
 
@@ -393,6 +393,12 @@ class Sim:
         self._check(load_library().pic_poisson(self.ctx, int(guess), y.data_ptr() if y is not None else None,
                                                float(scale), out), "pic_poisson")
         return list(out)
+
+    def sort_interval(self):
+        """(steps between tile sorts in use, tuned): the interval is 0 while
+        the library is still timing it (sort_every = 0)."""
+        v = self.diag(PIC_DIAG_SORT, np.zeros(2, np.int32))[0]
+        return int(v[0]), bool(v[1])
 
     def solver(self):
         """Inner Poisson solver in use: POISSON_AUTO (0) = the direct one,

@@ -36,6 +36,8 @@ void *dev_alloc(pic_ctx *c, size_t bytes) {
 namespace {
 
 constexpr int64_t kStageParticles = int64_t(1) << 22;
+constexpr int kTuneSteps = 48;   // particle steps timed after a sort when tuning the interval
+constexpr int kTuneMin = 4;      // shortest interval the tuning may choose
 
 void release(pic_ctx *c, void *p) {
   if (!p) return;
@@ -179,7 +181,7 @@ pic_status validate(const pic_config *cfg) {
   if (cfg->periodic_x && (cfg->nx % 2)) return PIC_EINVAL;
   if (cfg->periodic_y && (cfg->ny % 2)) return PIC_EINVAL;
   if (!(cfg->dt > 0) || !(cfg->poisson_rtol > 0)) return PIC_EINVAL;
-  if (cfg->poisson_maxit < 1 || cfg->sort_every < 1) return PIC_EINVAL;
+  if (cfg->poisson_maxit < 1 || cfg->sort_every < 0) return PIC_EINVAL;
   if (cfg->warm_start < 0 || cfg->warm_start > 2) return PIC_EINVAL;
   if (cfg->poisson_method < 0 || cfg->poisson_method > 1) return PIC_EINVAL;
   for (int s = 0; s < 2; ++s) {
@@ -381,7 +383,8 @@ pic_status pic_batch_init(const pic_config *cfgs, int32_t n, void *stream, pic_b
   if (!out || !cfgs || n < 1) return PIC_EINVAL;
   *out = nullptr;
   for (int32_t k = 0; k < n; ++k) {
-    if (cfgs[k].sort_every != cfgs[0].sort_every || cfgs[k].device != cfgs[0].device)
+    if (cfgs[k].sort_every < 1 || cfgs[k].sort_every != cfgs[0].sort_every ||
+        cfgs[k].device != cfgs[0].device)
       return PIC_EINVAL;
     const pic_status st = validate(&cfgs[k]);
     if (st != PIC_OK) return st;
@@ -725,7 +728,14 @@ pic_status pic_step(pic_ctx *c, int32_t nsteps) {
   pic_status st = prepare(c);
   if (st != PIC_OK) return st;
   for (int32_t k = 0; k < nsteps; ++k) {
-    const bool sorting = c->steps_since_sort >= c->cfg.sort_every;
+    // the interval in force: fixed, or tuned (a sort opens the measurement,
+    // none during it, then the chosen interval)
+    const bool tuning = c->cfg.sort_every == 0;
+    bool sorting;
+    if (!tuning) sorting = c->steps_since_sort >= c->cfg.sort_every;
+    else if (c->tune_state == 0) sorting = true;
+    else if (c->tune_state == 1) sorting = false;
+    else sorting = c->steps_since_sort >= c->sort_interval;
     if (c->cfg.graphs) {
       if ((st = check(step_graph(c, sorting ? 1 : 0))) != PIC_OK) return st;
       if (note(cudaGraphLaunch(c->gexec[sorting ? 1 : 0], c->stream), "step graph launch") !=
@@ -745,6 +755,32 @@ pic_status pic_step(pic_ctx *c, int32_t nsteps) {
     c->steps_since_sort += 1;
     c->step += 1;
     c->t_steps += 1;
+    if (tuning && c->tune_state < 2) {
+      if (cudaEventSynchronize(c->tev[5]) != cudaSuccess) return PIC_ECUDA;
+      float ms_sort = 0.f, ms_part = 0.f;
+      cudaEventElapsedTime(&ms_sort, c->tev[0], c->tev[1]);
+      cudaEventElapsedTime(&ms_part, c->tev[1], c->tev[2]);
+      if (c->tune_state == 0) {
+        c->tune_state = 1;
+        c->tune_sort_ms = ms_sort;
+        c->tune_particle_ms.clear();
+      }
+      c->tune_particle_ms.push_back(ms_part);
+      if (int(c->tune_particle_ms.size()) >= kTuneSteps) {
+        double sum = 0.0, best = 0.0;
+        int best_s = kTuneMin;
+        for (int s = 1; s <= kTuneSteps; ++s) {
+          sum += c->tune_particle_ms[s - 1];
+          const double per_step = (c->tune_sort_ms + sum) / s;
+          if (s >= kTuneMin && (s == kTuneMin || per_step < best)) {
+            best = per_step;
+            best_s = s;
+          }
+        }
+        c->sort_interval = best_s;
+        c->tune_state = 2;
+      }
+    }
     if (c->cfg.timing || !c->cfg.graphs) {
       if (cudaEventSynchronize(c->tev[5]) != cudaSuccess) return PIC_ECUDA;
       float ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
@@ -918,6 +954,19 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
       o[2] = ps.rel;
       o[3] = c->last_ms;
       count = 4;
+      break;
+    }
+    case PIC_DIAG_SORT: {
+      if (!need(8)) return PIC_EINVAL;
+      int32_t *o = (int32_t *)out;
+      if (c->cfg.sort_every > 0) {
+        o[0] = c->cfg.sort_every;
+        o[1] = 0;
+      } else {
+        o[0] = c->tune_state == 2 ? c->sort_interval : 0;
+        o[1] = c->tune_state == 2 ? 1 : 0;
+      }
+      count = 2;
       break;
     }
     case PIC_DIAG_SOLVER: {

@@ -204,6 +204,13 @@ struct pic_ctx {
   int needs_sort;
   int pending_kick[2];
   int steps_since_sort;
+  // Sort interval tuning (cfg.sort_every = 0): after one sort the particle
+  // kernel is timed for kTuneSteps steps, then the interval S minimising
+  // (sort time + particle time of the S steps after a sort) / S is kept.
+  int tune_state;              // 0 not started, 1 measuring, 2 chosen
+  int sort_interval;           // the chosen S
+  float tune_sort_ms;
+  std::vector<float> tune_particle_ms;
   uint32_t *d_tile_count;      // [2][ntiles]
   uint32_t *d_tile_cursor;     // [2][ntiles]
   uint32_t *d_tile_start;      // [2][ntiles]

@@ -53,8 +53,19 @@ def test_init_rejects_bad_config_without_touching_gpu(lib):
     ctx = ctypes.c_void_p()
     assert pg.load_library().pic_init(ctypes.byref(cfg), ctypes.byref(ctx)) == pg.PIC_EINVAL
     cfg = pg.make_config(synth.small_trench())
-    cfg.sort_every = 0
+    cfg.sort_every = -1                                       # 0 asks for a tuned interval
     assert pg.load_library().pic_init(ctypes.byref(cfg), ctypes.byref(ctx)) == pg.PIC_EINVAL
+    cfg = pg.make_config(synth.small_trench())
+    cfg.poisson_method = 2
+    assert pg.load_library().pic_init(ctypes.byref(cfg), ctypes.byref(ctx)) == pg.PIC_EINVAL
+
+
+def test_batch_init_rejects_a_tuned_sort_interval_without_gpu(lib):
+    import paper_1610_03918_gb300 as pg
+    import synth
+    with pytest.raises(pg.PicError) as e:
+        pg.Batch([synth.small_trench(sort_every=0)], torch_memory=False)
+    assert e.value.code == pg.PIC_EINVAL
 
 
 def test_batch_init_rejects_mixed_sort_schedules_without_gpu(lib):

@@ -137,6 +137,30 @@ def test_direct_and_multigrid_solves_agree():
     assert sd[0] <= 3
 
 
+def test_tuned_sort_interval_changes_no_result():
+    # sort_every = 0: the library times the particle kernel after a sort and
+    # picks the interval; the physics must be bitwise that of a fixed interval
+    # (exact deposit, order-independent push, fixed-order reductions)
+    w = DIRECT["trench64"]
+    runs = []
+    for se in (0, 8):
+        gs = gpu_sim(w.replace(sort_every=se))
+        for s in (0, 1):
+            gs.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
+        gs.step(60)
+        runs.append(gs)
+    tuned, fixed = runs
+    S, was_tuned = tuned.sort_interval()
+    assert was_tuned and 4 <= S <= 48, S
+    assert fixed.sort_interval() == (8, False)
+    by_id = lambda st: st[:, np.argsort(st[4], kind="stable")]
+    for s in (0, 1):
+        assert np.array_equal(by_id(tuned.state(s)), by_id(fixed.state(s)))
+    assert np.array_equal(tuned.rho(), fixed.rho())
+    assert np.array_equal(tuned.phi(), fixed.phi())
+    assert np.array_equal(tuned.counts()[0], fixed.counts()[0])
+
+
 def test_direct_solver_applies_only_to_its_geometry():
     import paper_1610_03918_gb300 as pg
     for w in (synth.small_trench(nx=40, ny=40),            # ny not a power of two
