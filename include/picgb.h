@@ -102,7 +102,7 @@ typedef struct {
                                      it (the deposit is exact and the reductions run in a fixed
                                      order).  pic_batch_init requires >= 1. */
   int32_t poisson_maxit;          /* cap on inner PCG iterations per solve */
-  double poisson_rtol;            /* target ||b - A phi||_2 / ||b||_2 (FP64) */
+  double poisson_rtol;            /* target ||b - A phi||_2 / ||b||_2 (A phi in double-float) */
   int32_t warm_start;             /* 0: zero initial guess each solve, 1: previous phi,
                                      2: extrapolated 2 phi^n - phi^{n-1} */
   int32_t device;                 /* CUDA device ordinal */
@@ -111,7 +111,7 @@ typedef struct {
   int32_t graphs;                 /* 1: each step is one launch of a captured CUDA graph whose
                                      Poisson loops are device-side conditional nodes;
                                      0: kernels launched from a host loop that polls the solver */
-  int32_t poisson_method;         /* inner solver of the FP64 iterative refinement of Eq. 5:
+  int32_t poisson_method;         /* inner solver of the iterative refinement of Eq. 5:
                                      0: automatic -- a direct FFT / tridiagonal / capacitance
                                      solve when the box is periodic in y with a power-of-two
                                      ny <= 2048, bounded in x, and its free nodes form a full
@@ -146,7 +146,7 @@ enum {
   PIC_DIAG_SURFACE = 3,  /* int64[2*ny]: hits on the x = nx face per species per y cell */
   PIC_DIAG_HITS = 4,     /* pic_hit[n_out] (the first hit_capacity records) */
   PIC_DIAG_RHO = 5,      /* [nxn*nyn]: net charge density of the last deposit */
-  PIC_DIAG_PHI = 6,      /* [nxn*nyn]: potential (FP64 master copy) */
+  PIC_DIAG_PHI = 6,      /* [nxn*nyn]: potential (held as a double-float pair, ~48 bits) */
   PIC_DIAG_E = 7,        /* [2*nxn*nyn]: Ex then Ey at the nodes */
   PIC_DIAG_STATE_E = 8,  /* [5*n]: x, y, vx, vy, id blocks of live electrons */
   PIC_DIAG_STATE_I = 9,  /* same for ions */

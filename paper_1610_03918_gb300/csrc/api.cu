@@ -48,6 +48,19 @@ void release(pic_ctx *c, void *p) {
   }
 }
 
+// Node arrays held on the device as double-float (hi, lo) pairs
+std::vector<float2> to_pairs(const double *x, size_t n) {
+  std::vector<float2> p(n);
+  for (size_t k = 0; k < n; ++k) p[k] = pair_split(x[k]);
+  return p;
+}
+
+void from_pairs(const float2 *d, size_t n, double *out) {
+  std::vector<float2> p(n);
+  cudaMemcpy(p.data(), d, n * sizeof(float2), cudaMemcpyDeviceToHost);
+  for (size_t k = 0; k < n; ++k) out[k] = pair_join(p[k]);
+}
+
 // Conductor cells: the electrode slab i >= nx - depth with the trench
 // columns [y0, y0 + width) open (Sec. III-C).
 bool plasma_cell(const pic_config &cfg, int i, int j) {
@@ -208,7 +221,7 @@ pic_status prepare(pic_ctx *c) {
   st = poisson_solve(c, true);
   if (st != PIC_OK) return st;
   // the extrapolated warm start begins from a constant history
-  if (cudaMemcpyAsync(c->d_phi_prev, c->d_phi, size_t(c->g.nxn) * c->g.nyn * sizeof(double),
+  if (cudaMemcpyAsync(c->d_phi_prev, c->d_phi, size_t(c->g.nxn) * c->g.nyn * sizeof(float2),
                       cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
     return PIC_ECUDA;
   if ((st = check(launch_field(c))) != PIC_OK) return st;
@@ -577,13 +590,12 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
   };
   c->d_cellmask = (uint8_t *)A(cellmask.size());
   c->d_nodeflags = (uint8_t *)A(nn);
-  c->d_lift = (double *)A(nn * 8);
-  c->d_g = (double *)A(nn * 8);
+  c->d_lift = (float *)A(nn * 4);
+  c->d_g = (float2 *)A(nn * 8);
   c->d_acc = (unsigned long long *)A(2 * nn * 8);
-  c->d_rho_ext = (double *)A(nn * 8);
-  c->d_rho = (double *)A(nn * 8);
-  c->d_b = (double *)A(nn * 8);
-  c->d_phi = (double *)A(nn * 8);
+  c->d_rho_ext = (float2 *)A(nn * 8);
+  c->d_rho = (float2 *)A(nn * 8);
+  c->d_phi = (float2 *)A(nn * 8);
   c->d_E = (float2 *)A(nn * sizeof(float2));
   c->d_fe = (double *)A(2 * 8);
   for (int s = 0; s < 2; ++s) {
@@ -631,13 +643,17 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
   }
   cudaMemcpyAsync(c->d_cellmask, cellmask.data(), cellmask.size(), cudaMemcpyHostToDevice, c->stream);
   cudaMemcpyAsync(c->d_nodeflags, c->h_nodeflags.data(), nn, cudaMemcpyHostToDevice, c->stream);
-  cudaMemcpyAsync(c->d_lift, lift.data(), nn * 8, cudaMemcpyHostToDevice, c->stream);
-  cudaMemcpyAsync(c->d_g, c->h_g.data(), nn * 8, cudaMemcpyHostToDevice, c->stream);
-  cudaMemcpyAsync(c->d_phi, c->h_g.data(), nn * 8, cudaMemcpyHostToDevice, c->stream);
+  {
+    std::vector<float> liftf(lift.begin(), lift.end());
+    const std::vector<float2> gp = to_pairs(c->h_g.data(), nn);
+    cudaMemcpyAsync(c->d_lift, liftf.data(), nn * 4, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d_g, gp.data(), nn * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaMemcpyAsync(c->d_phi, gp.data(), nn * 8, cudaMemcpyHostToDevice, c->stream);
+    cudaStreamSynchronize(c->stream);   // the host vectors go out of scope
+  }
   cudaMemsetAsync(c->d_acc, 0, 2 * nn * 8, c->stream);
   cudaMemsetAsync(c->d_rho_ext, 0, nn * 8, c->stream);
   cudaMemsetAsync(c->d_rho, 0, nn * 8, c->stream);
-  cudaMemsetAsync(c->d_b, 0, nn * 8, c->stream);
   cudaMemsetAsync(c->d_E, 0, nn * sizeof(float2), c->stream);
   cudaMemsetAsync(c->d_fe, 0, 16, c->stream);
   cudaMemsetAsync(c->d_tile_count, 0, 2 * size_t(ntiles) * 4, c->stream);
@@ -681,7 +697,8 @@ pic_status pic_load(pic_ctx *c, int32_t species, int64_t n, const double *x, con
   const size_t nn = size_t(c->g.nxn) * c->g.nyn;
   if (species == -1) {
     if (!x || n != int64_t(nn)) return PIC_EINVAL;
-    if (cudaMemcpyAsync(c->d_rho_ext, x, nn * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    const std::vector<float2> xp = to_pairs(x, nn);
+    if (cudaMemcpyAsync(c->d_rho_ext, xp.data(), nn * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
       return PIC_ECUDA;
     c->fields_dirty = 1;
     return check(cudaStreamSynchronize(c->stream));
@@ -692,7 +709,8 @@ pic_status pic_load(pic_ctx *c, int32_t species, int64_t n, const double *x, con
     std::vector<double> phi(x, x + nn);
     for (size_t k = 0; k < nn; ++k)
       if (!(c->h_nodeflags[k] & kFree)) phi[k] = c->h_g[k];
-    if (cudaMemcpyAsync(c->d_phi, phi.data(), nn * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
+    const std::vector<float2> pp = to_pairs(phi.data(), nn);
+    if (cudaMemcpyAsync(c->d_phi, pp.data(), nn * 8, cudaMemcpyHostToDevice, c->stream) != cudaSuccess)
       return PIC_ECUDA;
     return check(cudaStreamSynchronize(c->stream));
   }
@@ -902,7 +920,7 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
     case PIC_DIAG_RHO:
     case PIC_DIAG_PHI: {
       if (!need(int64_t(nn) * 8)) return PIC_EINVAL;
-      cudaMemcpy(out, kind == PIC_DIAG_RHO ? c->d_rho : c->d_phi, nn * 8, cudaMemcpyDeviceToHost);
+      from_pairs(kind == PIC_DIAG_RHO ? c->d_rho : c->d_phi, nn, static_cast<double *>(out));
       count = int64_t(nn);
       break;
     }
@@ -979,7 +997,7 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
       if (!need(int64_t(nn) * 8)) return PIC_EINVAL;
       const pic_status st = ensure_vacuum_potential(c);
       if (st != PIC_OK) return st;
-      cudaMemcpy(out, c->d_phiL, nn * 8, cudaMemcpyDeviceToHost);
+      from_pairs(c->d_phiL, nn, static_cast<double *>(out));
       count = int64_t(nn);
       break;
     }

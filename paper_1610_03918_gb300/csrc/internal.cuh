@@ -30,6 +30,59 @@ constexpr int kParticleThreads = PIC_PARTICLE_THREADS;
 constexpr int kParticleMinBlocks = 1024 / PIC_PARTICLE_THREADS;
 constexpr int kWalkLimit = 16;   // face crossings followed per move
 
+// Double-float values.  The potential, the charge density and the Dirichlet
+// data are held on the device as unevaluated sums hi + lo of two floats
+// (float2: x = hi, y = lo, |lo| <= ulp(hi) / 2), about 48 significant bits,
+// so the field-side kernels run on the FP32 pipes.  The sums are built from
+// the error-free transformations TwoSum (Knuth) and Fast2Sum (Dekker) and
+// the product from the FMA-based TwoProduct; the pair addition is the
+// accurate double-double addition of Hida, Li and Bailey (2001).  Every
+// operation is an explicitly rounded intrinsic, so nothing is contracted or
+// reassociated by the compiler.
+__device__ __forceinline__ float2 two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  const float bv = __fsub_rn(s, a);
+  return make_float2(s, __fadd_rn(__fsub_rn(a, __fsub_rn(s, bv)), __fsub_rn(b, bv)));
+}
+// |a| >= |b| (or a == 0)
+__device__ __forceinline__ float2 fast_two_sum(float a, float b) {
+  const float s = __fadd_rn(a, b);
+  return make_float2(s, __fsub_rn(b, __fsub_rn(s, a)));
+}
+__device__ __forceinline__ float2 pair_add(float2 a, float2 b) {
+  float2 s = two_sum(a.x, b.x);
+  const float2 t = two_sum(a.y, b.y);
+  s = fast_two_sum(s.x, __fadd_rn(s.y, t.x));
+  return fast_two_sum(s.x, __fadd_rn(s.y, t.y));
+}
+__device__ __forceinline__ float2 pair_neg(float2 a) { return make_float2(-a.x, -a.y); }
+__device__ __forceinline__ float2 pair_sub(float2 a, float2 b) { return pair_add(a, pair_neg(b)); }
+// pair + float
+__device__ __forceinline__ float2 pair_add_f(float2 a, float b) {
+  const float2 s = two_sum(a.x, b);
+  return fast_two_sum(s.x, __fadd_rn(s.y, a.y));
+}
+__device__ __forceinline__ float2 pair_mul(float2 a, float2 b) {
+  const float p = __fmul_rn(a.x, b.x);
+  float e = __fmaf_rn(a.x, b.x, -p);
+  e = __fmaf_rn(a.x, b.y, e);
+  e = __fmaf_rn(a.y, b.x, e);
+  return fast_two_sum(p, e);
+}
+// a signed 64-bit integer, exactly when |x| < 2^48: x = h 2^24 + l with
+// 0 <= l < 2^24, both parts exact floats, joined by TwoSum
+__device__ __forceinline__ float2 pair_from_ll(long long x) {
+  const int h = int(x >> 24);
+  const int l = int(x & 0xffffff);
+  return two_sum(__fmul_rn(__int2float_rn(h), 16777216.f), __int2float_rn(l));
+}
+// conversions to and from FP64 (host side, and rare device paths)
+__host__ __device__ inline float2 pair_split(double d) {
+  const float h = float(d);
+  return make_float2(h, float(d - double(h)));
+}
+__host__ __device__ inline double pair_join(float2 p) { return double(p.x) + double(p.y); }
+
 struct Geom {
   int nx, ny;          // cells
   int px, py;          // periodic flags
@@ -60,8 +113,8 @@ struct Chunk {
 
 // Device-side scalars of one Poisson solve.
 struct PoissonState {
-  double bb;          // ||b||^2 (FP64)
-  double rr64;        // ||b - A phi||^2 (FP64, outer)
+  double bb;          // ||b||^2
+  double rr64;        // ||b - A phi||^2 (outer: the certificate)
   double rel;         // sqrt(rr64 / bb)
   double bmean;       // mean of b (doubly periodic box only)
   double rz, rz_old, rr, rr0;       // inner PCG: gamma = <r, z>, its previous value, ||r||^2
@@ -162,19 +215,19 @@ struct pic_ctx {
   // geometry
   uint8_t *d_cellmask;      // [nx*ny] 1 = plasma
   uint8_t *d_nodeflags;     // [nxn*nyn]
-  double *d_lift;           // [nxn*nyn] sum of Dirichlet neighbour values (free nodes)
-  double *d_g;              // [nxn*nyn] Dirichlet values (0 at free nodes)
+  float *d_lift;            // [nxn*nyn] sum of Dirichlet neighbour values (free nodes; norms only)
+  float2 *d_g;              // [nxn*nyn] Dirichlet values (0 at free nodes), double-float
   std::vector<uint8_t> h_nodeflags;
   std::vector<double> h_g;
 
   // fields
   unsigned long long *d_acc;   // [2][nnodes] fixed-point species weights
-  double *d_rho_ext;
-  double *d_rho;               // net charge density
-  double *d_b;                 // right-hand side on free nodes
-  double *d_phi;               // FP64 master potential (Dirichlet values included)
-  double *d_phi_prev;          // potential of the previous step (extrapolated warm start)
-  double *d_phiL;              // potential of the empty box (learned warm start), lazily
+  // double-float (hi, lo) node arrays
+  float2 *d_rho_ext;
+  float2 *d_rho;               // net charge density
+  float2 *d_phi;               // the potential (Dirichlet values included)
+  float2 *d_phi_prev;          // potential of the previous step (extrapolated warm start)
+  float2 *d_phiL;              // potential of the empty box (learned warm start), lazily
   float2 *d_E;
   double *d_fe;                // [2]: field energy of E just computed, of E used by last step
 

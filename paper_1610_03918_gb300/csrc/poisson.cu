@@ -1,18 +1,23 @@
 // Field side of the step: charge density, the Poisson solve of Eq. 5 and
 // E = -grad Phi (Sec. II).
 //
-// rho = sum_s q_s w_s 2^-20 acc_s + rho_ext + bottom surface charge, and on
-// the free (non-Dirichlet) nodes b = rho + sum of Dirichlet neighbour values.
+// rho = sum_s q_s w_s 2^-20 acc_s + rho_ext + bottom surface charge; on the
+// free (non-Dirichlet) nodes b = rho + sum of Dirichlet neighbour values.
 // A = -Delta_h (5-point, unit spacing) on the free nodes, periodic where the
-// box is.  The solve is an FP64 iterative refinement around an FP32
-// multigrid-preconditioned conjugate gradient:
+// box is.  rho and the potential are held as double-float pairs (hi + lo,
+// about 48 bits; FP64 arithmetic runs at a small fraction of the FP32 rate
+// on this GPU).  The solve is an iterative refinement around an FP32 inner
+// solve:
 //
-//   repeat:  r = b - A phi          (FP64 stencil, FP64 norm: the certificate)
+//   repeat:  r = rho - A phi        (double-float stencil over the whole
+//                                    potential, Dirichlet values included:
+//                                    the certificate)
 //            stop if ||r|| <= rtol ||b||
-//            solve A e = r by PCG   (FP32 vectors and stencils, dot products
-//                                    accumulated across threads in FP64,
-//                                    symmetric V-cycle preconditioner)
-//            phi += e                (FP64)
+//            solve A e = r          (FP32: the direct solve of fastpoisson.cu
+//                                    where the geometry allows it, else PCG
+//                                    with a symmetric V-cycle preconditioner,
+//                                    inner products accumulated in FP64)
+//            phi += e               (double-float)
 //
 // V-cycle: factor-2 coarsening with injected Dirichlet masks; Galerkin coarse
 // operators A_c = R A P (9-point, built once on the host) with bilinear
@@ -70,13 +75,12 @@ __device__ __forceinline__ double warp_sum(double v) {
   return v;
 }
 
-// Sum of NV doubles over the block; thread 0 gets the result.
+// Cross-warp part of a block sum: lane 0 of each warp holds its warp's
+// partials in v; thread 0 gets the block totals.
 template <int NV>
-__device__ void block_sum(double (&v)[NV]) {
+__device__ void block_sum_warps(double (&v)[NV]) {
   __shared__ double sh[NV][32];
   const int lane = threadIdx.x & 31, w = threadIdx.x >> 5;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
   if (lane == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) sh[k][w] = v[k];
@@ -94,13 +98,53 @@ __device__ void block_sum(double (&v)[NV]) {
   __syncthreads();
 }
 
+// Sum of NV doubles over the block; thread 0 gets the result.
+template <int NV>
+__device__ void block_sum(double (&v)[NV]) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  block_sum_warps<NV>(v);
+}
+
+// Sums of squares for the norms: a value of moderate size (2^-50 < |x| <
+// 2^50) is squared and summed in FP32, any other in FP64, so no square
+// overflows or underflows.  The FP32 partials are summed over the warp in
+// FP32 unless a lane of the warp holds an FP64 partial.  The relative error
+// of a norm is a few FP32 roundings, which a convergence test and an energy
+// diagnostic can carry.
+__device__ __forceinline__ void sq_add(float &f, double &d, float x) {
+  const float ax = fabsf(x);
+  if (ax < 0x1p50f && (ax > 0x1p-50f || ax == 0.f)) f = fmaf(x, x, f);
+  else d = fma(double(x), double(x), d);
+}
+
+template <int NV>
+__device__ __forceinline__ void warp_sum_sq(const float (&f)[NV], const double (&d)[NV], double (&v)[NV]) {
+  bool wide = false;
+#pragma unroll
+  for (int k = 0; k < NV; ++k) wide |= d[k] != 0.0;
+  if (__any_sync(0xffffffffu, wide)) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = warp_sum(double(f[k]) + d[k]);
+  } else {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) {
+      float s = f[k];
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
+      v[k] = double(s);
+    }
+  }
+}
+
 // Deterministic grid reduction: every block publishes its partials, the
 // last block to arrive sums them in block order.  Returns true in the last
-// block, where thread 0 holds the totals in v.
+// block, where thread 0 holds the totals in v.  grid_sum_blocks starts from
+// warp partials held by lane 0 of each warp.
 template <int NV>
-__device__ bool grid_sum(double (&v)[NV], double *part, unsigned int *ticket) {
+__device__ bool grid_sum_blocks(double (&v)[NV], double *part, unsigned int *ticket) {
   __shared__ bool last;
-  block_sum<NV>(v);
+  block_sum_warps<NV>(v);
   if (threadIdx.x == 0) {
 #pragma unroll
     for (int k = 0; k < NV; ++k) part[blockIdx.x * NV + k] = v[k];
@@ -128,17 +172,32 @@ __device__ bool grid_sum(double (&v)[NV], double *part, unsigned int *ticket) {
   return true;
 }
 
+template <int NV>
+__device__ bool grid_sum(double (&v)[NV], double *part, unsigned int *ticket) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) v[k] = warp_sum(v[k]);
+  return grid_sum_blocks<NV>(v, part, ticket);
+}
+
+// grid sum of the sums of squares formed by sq_add
+template <int NV>
+__device__ bool grid_sum_sq(const float (&f)[NV], const double (&d)[NV], double (&v)[NV], double *part,
+                            unsigned int *ticket) {
+  warp_sum_sq<NV>(f, d, v);
+  return grid_sum_blocks<NV>(v, part, ticket);
+}
+
 struct FineArgs {
   Geom g;
   const uint8_t *flags;
-  const double *lift;
-  const double *gval;
-  double *rho, *b, *phi;
-  double *phi_prev;          // potential of the previous step (extrapolated warm start)
+  const float *lift;         // norms only
+  const float2 *gval;
+  float2 *rho, *phi;         // double-float
+  float2 *phi_prev;          // potential of the previous step (extrapolated warm start)
   unsigned long long *acc;
-  const double *rho_ext;
+  const float2 *rho_ext;
   const unsigned long long *bottom;
-  double qw[2];              // q_s w_s 2^-20
+  float2 qw[2];              // q_s w_s 2^-20 (double-float)
   double sw[2];              // q_s w_s (surface charge per hit)
   int surface;
   float *r32, *z, *p, *w, *q, *e;
@@ -172,29 +231,29 @@ constexpr int kVB = 4;
   _Pragma("unroll") for (int k = 0; k < kVB; ++k) \
     if (const int n = (base) + k * int(blockDim.x); n < (N))
 
-// acc -> rho, b; clears acc.  For a doubly periodic box the mean of b is kept.
+// acc -> rho (double-float); clears acc.  A doubly periodic box also forms
+// the mean of rho, which the solve removes.
 __global__ void k_rho(FineArgs a) {
   pdl_enter();
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
-  double v[2] = {0.0, 0.0};
+  double v[1] = {0.0};
   VEC_BATCHES(base, nn) {
     unsigned long long a0[kVB], a1[kVB];
-    double rx[kVB], lf[kVB];
-    uint8_t fl[kVB];
+    float2 rx[kVB];
     VEC_NODES(k, n, base, nn) {
       a0[k] = a.acc[n];
       a1[k] = a.acc[nn + n];
       rx[k] = a.rho_ext[n];
-      lf[k] = a.lift[n];
-      fl[k] = a.flags[n];
     }
     VEC_NODES(k, n, base, nn) {
       a.acc[n] = 0ull;
       a.acc[nn + n] = 0ull;
       // two's-complement sums: a node's total can be slightly negative (CIC
       // shares of -1 unit from the fixed-point rounding)
-      double rho = rx[k] + a.qw[0] * double((long long)a0[k]) + a.qw[1] * double((long long)a1[k]);
+      float2 rho = pair_add(pair_mul(a.qw[0], pair_from_ll((long long)a0[k])),
+                            pair_mul(a.qw[1], pair_from_ll((long long)a1[k])));
+      rho = pair_add(rx[k], rho);
       if (a.surface && !g.px) {
         const int i = n / g.nyn, j = n - (n / g.nyn) * g.nyn;
         if (i == g.nx - 1) {
@@ -205,21 +264,19 @@ __global__ void k_rho(FineArgs a) {
           if (g.py && jm < 0) jm += g.ny;
           if (jm >= 0 && jm < g.ny)
             s += 0.5 * (a.sw[0] * double(a.bottom[jm]) + a.sw[1] * double(a.bottom[g.ny + jm]));
-          rho += s;
+          rho = pair_add(rho, pair_split(s));
         }
       }
       a.rho[n] = rho;
-      const bool fr = fl[k] & kFree;
-      const double bb = fr ? rho + lf[k] : 0.0;
-      a.b[n] = bb;
-      v[0] += bb;
-      v[1] += fr ? 1.0 : 0.0;
+      if (a.singular) v[0] += pair_join(rho);   // every node is free
     }
   }
-  if (grid_sum<2>(v, a.part, a.ticket) && threadIdx.x == 0) {
-    a.ps->bmean = a.singular ? v[0] / v[1] : 0.0;
-    if (a.advance_step) *a.step += 1;
+  if (a.singular) {
+    if (grid_sum<1>(v, a.part, a.ticket) && threadIdx.x == 0) a.ps->bmean = v[0] / double(nn);
+  } else if (blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ps->bmean = 0.0;
   }
+  if (a.advance_step && blockIdx.x == 0 && threadIdx.x == 0) *a.step += 1;
 }
 
 // phi <- Dirichlet values, zero on free nodes (cold start)
@@ -233,7 +290,7 @@ __global__ void k_extrapolate(FineArgs a) {
   pdl_enter();
   const int nn = a.g.nxn * a.g.nyn;
   VEC_BATCHES(base, nn) {
-    double p[kVB], q[kVB];
+    float2 p[kVB], q[kVB];
     uint8_t fl[kVB];
     VEC_NODES(k, n, base, nn) {
       fl[k] = a.flags[n];
@@ -242,7 +299,7 @@ __global__ void k_extrapolate(FineArgs a) {
     }
     VEC_NODES(k, n, base, nn) {
       if (fl[k] & kFree) {
-        a.phi[n] = 2.0 * p[k] - q[k];
+        a.phi[n] = pair_sub(make_float2(2.f * p[k].x, 2.f * p[k].y), q[k]);
         a.phi_prev[n] = p[k];
       }
     }
@@ -261,26 +318,28 @@ __device__ __forceinline__ void nbr_index(const Geom &g, int n, int &xm, int &xp
   yp = i * g.nyn + jp;
 }
 
-// Outer FP64 residual r = b - A phi (the certificate) and the set-up of the
-// inner PCG on A e = r.
-__global__ void k_resid64(FineArgs a) {
+// Outer residual r = rho - A phi (the certificate; A applied to the whole
+// potential, so the Dirichlet neighbour values enter through phi) in
+// double-float, and the set-up of the inner solve of A e = r.  The norm of
+// b = rho + lift on the free nodes is formed on the first pass of a solve.
+__global__ void k_resid(FineArgs a) {
   pdl_enter();
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
-  const double bmean = a.ps->bmean;
-  // ||b|| is the same for every pass of a solve: formed on its first pass only
-  // (FP64 arithmetic runs at a small fraction of the FP32 rate here)
   const bool first = a.ps->outer_iters == 0;
-  double v[2] = {0.0, 0.0};
+  const float2 bm = a.singular ? pair_split(a.ps->bmean) : make_float2(0.f, 0.f);
+  float f[2] = {0.f, 0.f};
+  double d[2] = {0.0, 0.0}, v[2];
   VEC_BATCHES(base, nn) {
-    double bv[kVB], lf[kVB], ph[kVB][5];
+    float2 rh[kVB], ph[kVB][5];
+    float lf[kVB];
     uint8_t fl[kVB];
     VEC_NODES(k, n, base, nn) {
       int xm, xp, ym, yp;
       nbr_index(g, n, xm, xp, ym, yp);
       fl[k] = a.flags[n];
-      bv[k] = a.b[n];
-      lf[k] = a.lift[n];
+      rh[k] = a.rho[n];
+      lf[k] = first ? a.lift[n] : 0.f;
       ph[k][0] = a.phi[n];
       ph[k][1] = a.phi[xm];
       ph[k][2] = a.phi[xp];
@@ -290,13 +349,13 @@ __global__ void k_resid64(FineArgs a) {
     VEC_NODES(k, n, base, nn) {
       float r32 = 0.f;
       if (fl[k] & kFree) {
-        const double bn = a.singular ? bv[k] - bmean : bv[k];
-        const double rho = bn - lf[k];
-        const double Aphi = 4.0 * ph[k][0] - ph[k][1] - ph[k][2] - ph[k][3] - ph[k][4];
-        const double r = rho - Aphi;
-        r32 = float(r);
-        v[0] = fma(r, r, v[0]);
-        if (first) v[1] = fma(bn, bn, v[1]);
+        const float2 rho = pair_sub(rh[k], bm);
+        // -A phi = phi_xm + phi_xp + phi_ym + phi_yp - 4 phi
+        float2 s = pair_add(pair_add(ph[k][1], ph[k][2]), pair_add(ph[k][3], ph[k][4]));
+        s = pair_sub(s, make_float2(4.f * ph[k][0].x, 4.f * ph[k][0].y));
+        r32 = pair_add(rho, s).x;
+        sq_add(f[0], d[0], r32);
+        if (first) sq_add(f[1], d[1], __fadd_rn(rho.x, __fadd_rn(rho.y, lf[k])));
       }
       a.r32[n] = r32;
       if (!a.direct) {             // the direct inner solve writes all of e and uses no p, q
@@ -306,7 +365,7 @@ __global__ void k_resid64(FineArgs a) {
       }
     }
   }
-  if (grid_sum<2>(v, a.part, a.ticket) && threadIdx.x == 0) {
+  if (grid_sum_sq<2>(f, d, v, a.part, a.ticket) && threadIdx.x == 0) {
     PoissonState *ps = a.ps;
     ps->rr64 = v[0];
     if (first) ps->bb = v[1];
@@ -449,7 +508,7 @@ __global__ void k_correct(FineArgs a) {
   if (blockIdx.x == 0 && threadIdx.x == 0) a.ps->outer_iters += 1;
   const int nn = a.g.nxn * a.g.nyn;
   VEC_BATCHES(base, nn) {
-    double p[kVB];
+    float2 p[kVB];
     float e[kVB];
     uint8_t fl[kVB];
     VEC_NODES(k, n, base, nn) {
@@ -458,7 +517,7 @@ __global__ void k_correct(FineArgs a) {
       e[k] = a.e[n];
     }
     VEC_NODES(k, n, base, nn) {
-      if (fl[k] & kFree) a.phi[n] = p[k] + double(e[k]);
+      if (fl[k] & kFree) a.phi[n] = pair_add_f(p[k], e[k]);
     }
   }
 }
@@ -469,14 +528,16 @@ __global__ void k_outer_init(PoissonState *ps) {
   ps->outer_iters = 0;
 }
 
-// E = -grad phi by the open-edge rule; field energy 1/2 sum |E|^2
+// E = -grad phi by the open-edge rule; field energy 1/2 sum |E|^2.  Each
+// difference of the potential is taken in double-float and rounded once.
 __global__ void k_field(FineArgs a) {
   pdl_enter();
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
-  double v[1] = {0.0};
+  float f[1] = {0.f};
+  double d[1] = {0.0}, v[1];
   VEC_BATCHES(base, nn) {
-    double ph[kVB][5];
+    float2 ph[kVB][5];
     uint8_t fl[kVB];
     VEC_NODES(k, n, base, nn) {
       // neighbour indices clamped to the box; the edge flags say which count
@@ -490,21 +551,20 @@ __global__ void k_field(FineArgs a) {
       ph[k][4] = a.phi[yp];
     }
     VEC_NODES(k, n, base, nn) {
-      const uint8_t f = fl[k];
-      const double p = ph[k][0];
-      double sx = 0.0, sy = 0.0;
-      int cx = 0, cy = 0;
-      if (f & kOpenXm) { sx += p - ph[k][1]; ++cx; }
-      if (f & kOpenXp) { sx += ph[k][2] - p; ++cx; }
-      if (f & kOpenYm) { sy += p - ph[k][3]; ++cy; }
-      if (f & kOpenYp) { sy += ph[k][4] - p; ++cy; }
-      const float ex = float(cx == 2 ? -0.5 * sx : (cx ? -sx : 0.0));
-      const float ey = float(cy == 2 ? -0.5 * sy : (cy ? -sy : 0.0));
+      const uint8_t fk = fl[k];
+      // -dphi/dx: central difference where both edges are open, one-sided
+      // where one is, zero where neither is
+      const bool xm = fk & kOpenXm, xp = fk & kOpenXp, ym = fk & kOpenYm, yp = fk & kOpenYp;
+      const float2 x0 = xm ? ph[k][1] : ph[k][0], x1 = xp ? ph[k][2] : ph[k][0];
+      const float2 y0 = ym ? ph[k][3] : ph[k][0], y1 = yp ? ph[k][4] : ph[k][0];
+      const float ex = (xm || xp) ? -pair_sub(x1, x0).x * ((xm && xp) ? 0.5f : 1.f) : 0.f;
+      const float ey = (ym || yp) ? -pair_sub(y1, y0).x * ((ym && yp) ? 0.5f : 1.f) : 0.f;
       a.E[n] = make_float2(ex, ey);
-      v[0] += double(fmaf(ex, ex, ey * ey));
+      sq_add(f[0], d[0], ex);
+      sq_add(f[0], d[0], ey);
     }
   }
-  if (grid_sum<1>(v, a.part, a.ticket) && threadIdx.x == 0) a.fe[0] = 0.5 * v[0];
+  if (grid_sum_sq<1>(f, d, v, a.part, a.ticket) && threadIdx.x == 0) a.fe[0] = 0.5 * v[0];
 }
 
 // --------------------------------------------------------------------------
@@ -1176,7 +1236,6 @@ FineArgs fine_args(pic_ctx *c) {
   a.lift = c->d_lift;
   a.gval = c->d_g;
   a.rho = c->d_rho;
-  a.b = c->d_b;
   a.phi = c->d_phi;
   a.phi_prev = c->d_phi_prev;
   a.acc = c->d_acc;
@@ -1184,7 +1243,7 @@ FineArgs fine_args(pic_ctx *c) {
   a.bottom = c->d_bottom;
   for (int s = 0; s < 2; ++s) {
     const double w = 1.0 / double(c->cfg.ppc[s]);
-    a.qw[s] = c->cfg.charge[s] * w * std::ldexp(1.0, -kFracBits);
+    a.qw[s] = pair_split(c->cfg.charge[s] * w * std::ldexp(1.0, -kFracBits));
     a.sw[s] = c->cfg.charge[s] * w;
   }
   a.surface = c->cfg.surface_charge;
@@ -1539,7 +1598,7 @@ cudaError_t poisson_setup(pic_ctx *c) {
     m.upre = (float *)dev_alloc(c, size_t(m.nxn) * m.nyn * sizeof(float));
     if (!m.upre) return cudaErrorMemoryAllocation;
   }
-  c->d_phi_prev = (double *)dev_alloc(c, nn * sizeof(double));
+  c->d_phi_prev = (float2 *)dev_alloc(c, nn * sizeof(float2));
   if (!c->d_phi_prev) return cudaErrorMemoryAllocation;
   // kVB nodes per thread in the vector kernels
   c->red.nblocks = blocks_for((int(nn) + kVB - 1) / kVB);
@@ -1589,7 +1648,7 @@ pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
   c->launches += 1;
   const int batch = 4;
   for (;;) {
-    launch(k_resid64, nb, kThreads, 0, c->stream, a);
+    launch(k_resid, nb, kThreads, 0, c->stream, a);
     c->launches += 1;
     cudaMemcpyAsync(c->h_ps, c->d_ps, sizeof(PoissonState), cudaMemcpyDeviceToHost, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
@@ -1699,7 +1758,7 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   CK(add_cond(top, deps, h[0], cudaGraphCondTypeWhile, &n_outer, &b_outer));
   std::vector<cudaGraphNode_t> d;
   CK(cap_begin(s, b_outer, {}));
-  launch(k_resid64, nb, kThreads, 0, s, a);
+  launch(k_resid, nb, kThreads, 0, s, a);
   CK(cap_end(s, d));
   CK(add_cond(b_outer, d, h[1], cudaGraphCondTypeIf, &n_if_outer, &b_if_outer));
   if (c->fp.enabled) {
@@ -1750,16 +1809,16 @@ int64_t poisson_kernel_count(pic_ctx *c, const PoissonState &ps) {
 // ---- initial guesses for the learned warm start ----
 namespace {
 
-__global__ void k_absmax(const double *rho, int nn, unsigned int *out) {
+__global__ void k_absmax(const float2 *rho, int nn, unsigned int *out) {
   pdl_enter();
   float m = 0.f;
-  GRID_STRIDE(n, nn) m = fmaxf(m, float(fabs(rho[n])));
+  GRID_STRIDE(n, nn) m = fmaxf(m, fabsf(rho[n].x));
   for (int o = 16; o > 0; o >>= 1) m = fmaxf(m, __shfl_down_sync(0xffffffffu, m, o));
   if ((threadIdx.x & 31) == 0) atomicMax(out, __float_as_uint(m));   // m >= 0: bit order = value order
 }
 
 // x[i][j] = (rho / s, 1 for a Dirichlet node); rows beyond the grid count as conductor
-__global__ void k_learned_input(const double *rho, const uint8_t *flags, int nxn, int nyn, int hpad,
+__global__ void k_learned_input(const float2 *rho, const uint8_t *flags, int nxn, int nyn, int hpad,
                                 const unsigned int *smax, float *x) {
   pdl_enter();
   const float s = fmaxf(__uint_as_float(*smax), 1e-30f);
@@ -1767,7 +1826,7 @@ __global__ void k_learned_input(const double *rho, const uint8_t *flags, int nxn
     const int i = n / nyn;
     float r = 0.f, m = 1.f;
     if (i < nxn) {
-      r = float(rho[n] / double(s));
+      r = float(pair_join(rho[n]) / double(s));
       m = (flags[n] & kFree) ? 0.f : 1.f;
     }
     x[2 * n] = r;
@@ -1775,17 +1834,12 @@ __global__ void k_learned_input(const double *rho, const uint8_t *flags, int nxn
   }
 }
 
-__global__ void k_guess_learned(double *phi, const double *phiL, const uint8_t *flags, const float *y,
+__global__ void k_guess_learned(float2 *phi, const float2 *phiL, const uint8_t *flags, const float *y,
                                 double scale, int nn) {
   pdl_enter();
   GRID_STRIDE(n, nn) {
-    if (flags[n] & kFree) phi[n] = phiL[n] + scale * double(y[n]);
+    if (flags[n] & kFree) phi[n] = pair_split(pair_join(phiL[n]) + scale * double(y[n]));
   }
-}
-
-__global__ void k_b_lift(double *b, const double *lift, const uint8_t *flags, int nn) {
-  pdl_enter();
-  GRID_STRIDE(n, nn) b[n] = (flags[n] & kFree) ? lift[n] : 0.0;
 }
 
 }  // namespace
@@ -1795,16 +1849,17 @@ __global__ void k_b_lift(double *b, const double *lift, const uint8_t *flags, in
 pic_status ensure_vacuum_potential(pic_ctx *c) {
   if (c->d_phiL) return PIC_OK;
   const size_t nn = size_t(c->g.nxn) * c->g.nyn;
-  c->d_phiL = (double *)dev_alloc(c, nn * 8);
-  double *save_phi = (double *)dev_alloc(c, nn * 8);
-  double *save_b = (double *)dev_alloc(c, nn * 8);
-  if (!c->d_phiL || !save_phi || !save_b) return PIC_ENOMEM;
+  c->d_phiL = (float2 *)dev_alloc(c, nn * 8);
+  float2 *save_phi = (float2 *)dev_alloc(c, nn * 8);
+  float2 *save_rho = (float2 *)dev_alloc(c, nn * 8);
+  if (!c->d_phiL || !save_phi || !save_rho) return PIC_ENOMEM;
   cudaMemcpyAsync(save_phi, c->d_phi, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
-  cudaMemcpyAsync(save_b, c->d_b, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(save_rho, c->d_rho, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
   PoissonState ps_save;
   cudaMemcpyAsync(&ps_save, c->d_ps, sizeof(ps_save), cudaMemcpyDeviceToHost, c->stream);
   cudaStreamSynchronize(c->stream);
-  launch(k_b_lift, c->red.nblocks, kThreads, 0, c->stream, c->d_b, c->d_lift, c->d_nodeflags, int(nn));
+  // no charge: b is the Dirichlet lift alone
+  cudaMemsetAsync(c->d_rho, 0, nn * 8, c->stream);
   cudaMemsetAsync(&c->d_ps->bmean, 0, sizeof(double), c->stream);
   const double rtol = c->cfg.poisson_rtol;
   c->cfg.poisson_rtol = 1e-10;
@@ -1812,7 +1867,7 @@ pic_status ensure_vacuum_potential(pic_ctx *c) {
   c->cfg.poisson_rtol = rtol;
   cudaMemcpyAsync(c->d_phiL, c->d_phi, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
   cudaMemcpyAsync(c->d_phi, save_phi, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
-  cudaMemcpyAsync(c->d_b, save_b, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
+  cudaMemcpyAsync(c->d_rho, save_rho, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
   cudaMemcpyAsync(c->d_ps, &ps_save, sizeof(ps_save), cudaMemcpyHostToDevice, c->stream);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
   return st;
