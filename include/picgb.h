@@ -106,8 +106,10 @@ typedef struct {
   int32_t warm_start;             /* 0: zero initial guess each solve, 1: previous phi,
                                      2: extrapolated 2 phi^n - phi^{n-1} */
   int32_t device;                 /* CUDA device ordinal */
-  int32_t timing;                 /* 1: pic_step waits for each step and accumulates the
-                                     per-phase device times of PIC_DIAG_TIMING */
+  int32_t timing;                 /* 1: each step records its phase boundaries in CUDA
+                                     events (a pool of 64 steps, read back when it fills or
+                                     at pic_diag) for the per-phase device times of
+                                     PIC_DIAG_TIMING */
   int32_t graphs;                 /* 1: each step is one launch of a captured CUDA graph whose
                                      Poisson loops are device-side conditional nodes;
                                      0: kernels launched from a host loop that polls the solver */
@@ -152,7 +154,8 @@ enum {
   PIC_DIAG_STATE_I = 9,  /* same for ions */
   PIC_DIAG_POISSON = 10, /* [inner iterations, outer iterations, rel residual, ms] of the last solve */
   PIC_DIAG_STATUS = 11,  /* uint32: status word; reading clears it */
-  PIC_DIAG_TIMING = 12,  /* [steps, ms particle kernel, ms sort, ms Poisson, ms rho+field,
+  PIC_DIAG_TIMING = 12,  /* [steps, ms particle kernel, ms sort, ms Poisson (the solve's
+                            residual passes also form E), ms rho,
                             sorts, kernel launches, particle slots processed]: device time
                             from CUDA events on the context stream, accumulated over
                             pic_step calls since the last read; reading resets it */
@@ -190,10 +193,20 @@ pic_status pic_load(pic_ctx *ctx, int32_t species, int64_t n, const double *x,
  * fields up to date with the loaded state (deposit, Poisson solve, E) and
  * applies pending dt/2 back-kicks (this part polls the solver from the host).
  * With cfg->graphs the steps are queued as graph launches and the call
- * returns without waiting (unless cfg->timing); a solve that fails to reach
- * rtol sets PIC_ST_NOCONV, reported by the next pic_diag.  Without graphs the
- * call waits on each solve and returns PIC_ENOCONV directly. */
+ * returns without waiting (with cfg->timing it waits once every 64 steps, to
+ * read back the phase events; while the sort interval is being tuned, once
+ * per step); a solve that fails to reach rtol sets PIC_ST_NOCONV, reported by
+ * the next pic_diag.  Without graphs the call waits on each solve and
+ * returns PIC_ENOCONV directly. */
 pic_status pic_step(pic_ctx *ctx, int32_t nsteps);
+
+/* Turn the per-phase timing of cfg->timing on (1) or off (0) for the steps
+ * that follow; totals already recorded are kept until PIC_DIAG_TIMING reads
+ * them.  Graph steps with timing carry event nodes between the phases, which
+ * also end the programmatic overlap of one phase's kernels with the next;
+ * the first step of each kind captures its graph.  Returns PIC_EINVAL for
+ * other values of on. */
+pic_status pic_set_timing(pic_ctx *ctx, int32_t on);
 
 /* Copy a diagnostic to host memory out (cap_bytes long); *n_out receives the
  * element count written (may be NULL).  Synchronises the stream.

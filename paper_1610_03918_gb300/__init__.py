@@ -33,7 +33,7 @@ PIC_LOAD_V_AT_T0 = 1
 (WALL_XMIN, WALL_XMAX, WALL_YMIN, WALL_YMAX, WALL_COND_PX, WALL_COND_MX,
  WALL_COND_PY, WALL_COND_MY) = range(8)
 
-EXPORTED = ("pic_init", "pic_load", "pic_step", "pic_diag", "pic_free", "pic_strerror",
+EXPORTED = ("pic_init", "pic_load", "pic_step", "pic_set_timing", "pic_diag", "pic_free", "pic_strerror",
             "pic_batch_init", "pic_batch_member", "pic_batch_step", "pic_batch_timing",
             "pic_batch_free", "pic_deposit_static", "pic_unet_create", "pic_unet_forward",
             "pic_unet_gradients", "pic_unet_train_step", "pic_unet_free")
@@ -98,6 +98,7 @@ def load_library():
     lib.pic_load.argtypes = [P, ctypes.c_int32, ctypes.c_int64, D, D, D, D,
                              ctypes.POINTER(ctypes.c_uint32), ctypes.c_uint32]
     lib.pic_step.argtypes = [P, ctypes.c_int32]
+    lib.pic_set_timing.argtypes = [P, ctypes.c_int32]
     lib.pic_diag.argtypes = [P, ctypes.c_int32, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     lib.pic_free.argtypes = [P]
     lib.pic_strerror.argtypes = [ctypes.c_int]
@@ -131,7 +132,7 @@ def load_library():
     for name in ("pic_unet_create", "pic_unet_set_params", "pic_unet_get_params",
                  "pic_unet_forward", "pic_unet_gradients", "pic_unet_train_step", "pic_unet_free"):
         getattr(lib, name).restype = ctypes.c_int
-    for name in ("pic_init", "pic_load", "pic_step", "pic_diag", "pic_free"):
+    for name in ("pic_init", "pic_load", "pic_step", "pic_set_timing", "pic_diag", "pic_free"):
         getattr(lib, name).restype = ctypes.c_int
     _lib = lib
     return lib
@@ -175,6 +176,10 @@ def pic_load(ctx, species: int, x, y=None, vx=None, vy=None, ids=None, flags: in
 
 def pic_step(ctx, nsteps: int) -> int:
     return load_library().pic_step(ctx, int(nsteps))
+
+
+def pic_set_timing(ctx, on: bool) -> int:
+    return load_library().pic_set_timing(ctx, int(bool(on)))
 
 
 def pic_diag(ctx, kind: int, out: np.ndarray):
@@ -311,6 +316,11 @@ class Sim:
     def step(self, n=1, allow=()):
         return self._check(pic_step(self.ctx, n), "pic_step", allow)
 
+    def set_timing(self, on: bool):
+        """Per-phase timing (event nodes between the phases) on or off for
+        the steps that follow."""
+        return self._check(pic_set_timing(self.ctx, on), "pic_set_timing")
+
     def diag(self, kind, out, allow=(PIC_EFULL, PIC_ERANGE)):
         st, n = pic_diag(self.ctx, kind, out)
         self._check(st, "pic_diag", allow)
@@ -362,10 +372,10 @@ class Sim:
 
     def timing(self):
         """Per-phase device time since the last call (and resets it):
-        dict of steps, ms_particles, ms_sort, ms_poisson, ms_rho_field,
+        dict of steps, ms_particles, ms_sort, ms_poisson (with the field), ms_rho,
         sorts, launches, slots."""
         v = self.diag(PIC_DIAG_TIMING, np.empty(8))[0]
-        keys = ("steps", "ms_particles", "ms_sort", "ms_poisson", "ms_rho_field", "sorts",
+        keys = ("steps", "ms_particles", "ms_sort", "ms_poisson", "ms_rho", "sorts",
                 "launches", "slots")
         return dict(zip(keys, v.tolist()))
 

@@ -224,7 +224,6 @@ pic_status prepare(pic_ctx *c) {
   if (cudaMemcpyAsync(c->d_phi_prev, c->d_phi, size_t(c->g.nxn) * c->g.nyn * sizeof(float2),
                       cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
     return PIC_ECUDA;
-  if ((st = check(launch_field(c))) != PIC_OK) return st;
   if (c->pending_kick[0] || c->pending_kick[1]) {
     if ((st = check(launch_particles(c, 2, -0.5f, c->pending_kick))) != PIC_OK) return st;
     c->pending_kick[0] = c->pending_kick[1] = 0;
@@ -248,33 +247,32 @@ cudaError_t capture_leaves(cudaStream_t s, std::vector<cudaGraphNode_t> &leaves)
   return e == cudaSuccess ? e2 : e;
 }
 
-// One step from the host: sort (when due), particle kernel, rho, solve, field,
-// with the phase events of PIC_DIAG_TIMING.
-pic_status step_kernels(pic_ctx *c, bool sorting) {
+// One step from the host: sort (when due), particle kernel, rho, solve (which
+// leaves the field), with the phase events ev (kPhaseEvents of them).
+pic_status step_kernels(pic_ctx *c, bool sorting, cudaEvent_t *ev) {
   pic_status st;
-  cudaEventRecord(c->tev[0], c->stream);
+  cudaEventRecord(ev[0], c->stream);
   if (sorting) {
     if ((st = check(launch_sort(c))) != PIC_OK) return st;
     c->launches += 4;
   }
-  cudaEventRecord(c->tev[1], c->stream);
+  cudaEventRecord(ev[1], c->stream);
   if ((st = check(launch_particles(c, 0, 1.f, nullptr))) != PIC_OK) return st;
-  cudaEventRecord(c->tev[2], c->stream);
+  cudaEventRecord(ev[2], c->stream);
   if ((st = check(launch_rho(c, 1))) != PIC_OK) return st;
-  cudaEventRecord(c->tev[3], c->stream);
+  cudaEventRecord(ev[3], c->stream);
   st = poisson_solve(c, c->cfg.warm_start == 0);
   if (st != PIC_OK) return st;
-  cudaEventRecord(c->tev[4], c->stream);
-  if ((st = check(launch_field(c))) != PIC_OK) return st;
-  cudaEventRecord(c->tev[5], c->stream);
-  c->launches += 3;
+  cudaEventRecord(ev[4], c->stream);
+  c->launches += 2;
   return PIC_OK;
 }
 
 // Appends one step of context c to graph g after the nodes in `deps`:
 // [sort] -> particle kernel -> rho -> the Poisson solve as nested conditional
-// nodes -> field.  With `events`, external event nodes separate the phases
-// (PIC_DIAG_TIMING).  On return `deps` holds the step's last node(s).
+// nodes (its residual passes write the field).  With `events`, external event
+// nodes recording c->tev separate the phases (PIC_DIAG_TIMING); the launch
+// points them at a slot of the event pool.  On return `deps` holds the step's last node(s).
 // Kernel arguments are fixed device pointers; the particle buffers are reached
 // through the device-side buffer table, so the sort's swap needs no re-capture.
 cudaError_t capture_step(pic_ctx *c, cudaGraph_t g, std::vector<cudaGraphNode_t> &deps,
@@ -297,13 +295,11 @@ cudaError_t capture_step(pic_ctx *c, cudaGraph_t g, std::vector<cudaGraphNode_t>
     e = note(capture_leaves(c->stream, deps), "capture: particle phase");
   }
   if (e == cudaSuccess) e = note(poisson_capture(c, g, deps), "capture: Poisson conditionals");
-  if (e == cudaSuccess) {
+  if (e == cudaSuccess && events) {
     e = cudaStreamBeginCaptureToGraph(c->stream, g, deps.data(), nullptr, deps.size(),
                                       cudaStreamCaptureModeThreadLocal);
     if (e == cudaSuccess) {
       rec(4);
-      launch_field(c);
-      rec(5);
       e = capture_leaves(c->stream, deps);
     }
   }
@@ -314,19 +310,101 @@ cudaError_t capture_step(pic_ctx *c, cudaGraph_t g, std::vector<cudaGraphNode_t>
   return e;
 }
 
-// Capture (once) and instantiate the step graph of one context.
-cudaError_t step_graph(pic_ctx *c, int with_sort) {
-  if (c->gexec[with_sort]) return cudaSuccess;
+// Capture (once) and instantiate the step graph of one context, with or
+// without the phase event nodes; the event nodes are looked up by the
+// placeholder event each records.
+cudaError_t step_graph(pic_ctx *c, int with_sort, int events) {
+  if (c->gexec[with_sort][events]) return cudaSuccess;
   cudaGraph_t g;
   cudaError_t e = cudaGraphCreate(&g, 0);
   if (e != cudaSuccess) return e;
   std::vector<cudaGraphNode_t> deps;
-  e = note(capture_step(c, g, deps, with_sort, true), "step graph capture");
-  if (e == cudaSuccess) e = note(cudaGraphInstantiate(&c->gexec[with_sort], g, 0), "step graph instantiate");
-  if (e == cudaSuccess) c->graph[with_sort] = g;
+  e = note(capture_step(c, g, deps, with_sort, events != 0), "step graph capture");
+  if (e == cudaSuccess && events) {
+    size_t n = 0;
+    e = cudaGraphGetNodes(g, nullptr, &n);
+    std::vector<cudaGraphNode_t> nodes(n);
+    if (e == cudaSuccess) e = cudaGraphGetNodes(g, nodes.data(), &n);
+    int found = 0;
+    for (size_t k = 0; e == cudaSuccess && k < n; ++k) {
+      cudaGraphNodeType t;
+      cudaEvent_t ev;
+      if (cudaGraphNodeGetType(nodes[k], &t) != cudaSuccess || t != cudaGraphNodeTypeEventRecord) continue;
+      if (cudaGraphEventRecordNodeGetEvent(nodes[k], &ev) != cudaSuccess) continue;
+      for (int q = 0; q < kPhaseEvents; ++q)
+        if (ev == c->tev[q]) {
+          c->evnode[with_sort][q] = nodes[k];
+          found |= 1 << q;
+        }
+    }
+    if (e == cudaSuccess && found != (1 << kPhaseEvents) - 1) e = cudaErrorInvalidValue;
+    note(e, "step graph event nodes");
+  }
+  if (e == cudaSuccess)
+    e = note(cudaGraphInstantiate(&c->gexec[with_sort][events], g, 0), "step graph instantiate");
+  if (e == cudaSuccess) c->graph[with_sort][events] = g;
   else cudaGraphDestroy(g);
   cudaGetLastError();
   return e;
+}
+
+// Reads the phase times of the recorded timing slots (waiting for the last)
+// into the PIC_DIAG_TIMING totals and feeds the sort-interval tuning.
+pic_status flush_timing(pic_ctx *c) {
+  if (c->tpend == 0) return PIC_OK;
+  if (cudaEventSynchronize(c->tpool[c->tpend - 1][kPhaseEvents - 1]) != cudaSuccess) return PIC_ECUDA;
+  for (int s = 0; s < c->tpend; ++s) {
+    float ms[kPhaseEvents - 1] = {};
+    for (int q = 0; q + 1 < kPhaseEvents; ++q) cudaEventElapsedTime(&ms[q], c->tpool[s][q], c->tpool[s][q + 1]);
+    c->t_sort += ms[0];
+    c->t_part += ms[1];
+    c->t_other += ms[2];
+    if (c->cfg.graphs) {
+      c->t_poisson += ms[3];
+      c->last_ms = ms[3];
+    } else {
+      c->t_poisson += c->last_ms;   // the solve's own time, without the host polling
+    }
+    if (c->tslot_tune[s] && c->tune_state < 2) {
+      // a sort opens the measurement, then the particle times of the steps after it
+      if (c->tune_state == 0) {
+        c->tune_state = 1;
+        c->tune_sort_ms = ms[0];
+        c->tune_particle_ms.clear();
+      }
+      c->tune_particle_ms.push_back(ms[1]);
+      if (int(c->tune_particle_ms.size()) >= kTuneSteps) {
+        double sum = 0.0, best = 0.0;
+        int best_s = kTuneMin;
+        for (int k = 1; k <= kTuneSteps; ++k) {
+          sum += c->tune_particle_ms[k - 1];
+          const double per_step = (c->tune_sort_ms + sum) / k;
+          if (k >= kTuneMin && (k == kTuneMin || per_step < best)) {
+            best = per_step;
+            best_s = k;
+          }
+        }
+        c->sort_interval = best_s;
+        c->tune_state = 2;
+      }
+    }
+  }
+  c->tpend = 0;
+  return PIC_OK;
+}
+
+// Adds the kernels of the solves that graph steps ran since the last count
+// (from the solver's running totals on the device) to the launch count.
+pic_status count_solves(pic_ctx *c) {
+  PoissonState ps;
+  if (cudaMemcpy(&ps, c->d_ps, sizeof(ps), cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
+  c->launches += poisson_kernel_count(c, ps.n_solves - c->seen_solves, ps.sum_outer - c->seen_outer,
+                                      ps.sum_total - c->seen_total);
+  c->seen_solves = ps.n_solves;
+  c->seen_outer = ps.sum_outer;
+  c->seen_total = ps.sum_total;
+  c->last_outer = ps.outer_iters;
+  return PIC_OK;
 }
 
 }  // namespace
@@ -573,6 +651,7 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
   g.py = cfg->periodic_y ? 1 : 0;
   g.nxn = g.px ? g.nx : g.nx + 1;
   g.nyn = g.py ? g.ny : g.ny + 1;
+  g.dnyn = make_fastdiv(uint32_t(g.nyn));
   g.ntx = (g.nx + kTileX - 1) / kTileX;
   g.nty = (g.ny + kTileY - 1) / kTileY;
   const int ntiles = g.ntx * g.nty;
@@ -673,7 +752,7 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
     cudaMemcpy(c->d_pbufs, tab, sizeof(tab), cudaMemcpyHostToDevice);
     cudaMemcpy(c->d_cur, cur0, sizeof(cur0), cudaMemcpyHostToDevice);
   }
-  for (int k = 0; k < 6; ++k) cudaEventCreate(&c->tev[k]);
+  for (int k = 0; k < kPhaseEvents; ++k) cudaEventCreate(&c->tev[k]);
   e = poisson_setup(c);
   if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
   if (e != cudaSuccess) {
@@ -748,23 +827,39 @@ pic_status pic_step(pic_ctx *c, int32_t nsteps) {
   for (int32_t k = 0; k < nsteps; ++k) {
     // the interval in force: fixed, or tuned (a sort opens the measurement,
     // none during it, then the chosen interval)
-    const bool tuning = c->cfg.sort_every == 0;
+    const bool tuning = c->cfg.sort_every == 0 && c->tune_state < 2;
     bool sorting;
-    if (!tuning) sorting = c->steps_since_sort >= c->cfg.sort_every;
+    if (c->cfg.sort_every > 0) sorting = c->steps_since_sort >= c->cfg.sort_every;
     else if (c->tune_state == 0) sorting = true;
     else if (c->tune_state == 1) sorting = false;
     else sorting = c->steps_since_sort >= c->sort_interval;
+    // steps of the host loop are always timed; graph steps when timing is on
+    // or the sort interval is being tuned
+    const bool timed = c->cfg.timing || tuning || !c->cfg.graphs;
+    if (timed && !c->tpool[0][0]) {
+      for (int s = 0; s < kTimeSlots; ++s)
+        for (int q = 0; q < kPhaseEvents; ++q)
+          if (cudaEventCreate(&c->tpool[s][q]) != cudaSuccess) return PIC_ECUDA;
+    }
+    const int slot = c->tpend;
     if (c->cfg.graphs) {
-      if ((st = check(step_graph(c, sorting ? 1 : 0))) != PIC_OK) return st;
-      if (note(cudaGraphLaunch(c->gexec[sorting ? 1 : 0], c->stream), "step graph launch") !=
-          cudaSuccess)
+      const int ws = sorting ? 1 : 0, ev = timed ? 1 : 0;
+      if ((st = check(step_graph(c, ws, ev))) != PIC_OK) return st;
+      if (timed) {
+        for (int q = 0; q < kPhaseEvents; ++q)
+          if (note(cudaGraphExecEventRecordNodeSetEvent(c->gexec[ws][1], c->evnode[ws][q], c->tpool[slot][q]),
+                   "step graph event") != cudaSuccess)
+            return PIC_ECUDA;
+      }
+      c->launches += (sorting ? 4 : 0) + 2;   // the solve's kernels are counted from its totals
+      if (note(cudaGraphLaunch(c->gexec[ws][ev], c->stream), "step graph launch") != cudaSuccess)
         return PIC_ECUDA;
       if (sorting) {
         c->cur[0] ^= 1;   // mirror the device-side buffer flip of the sort
         c->cur[1] ^= 1;
       }
     } else {
-      if ((st = step_kernels(c, sorting)) != PIC_OK) return st;
+      if ((st = step_kernels(c, sorting, c->tpool[slot])) != PIC_OK) return st;
     }
     if (sorting) {
       c->steps_since_sort = 0;
@@ -773,53 +868,20 @@ pic_status pic_step(pic_ctx *c, int32_t nsteps) {
     c->steps_since_sort += 1;
     c->step += 1;
     c->t_steps += 1;
-    if (tuning && c->tune_state < 2) {
-      if (cudaEventSynchronize(c->tev[5]) != cudaSuccess) return PIC_ECUDA;
-      float ms_sort = 0.f, ms_part = 0.f;
-      cudaEventElapsedTime(&ms_sort, c->tev[0], c->tev[1]);
-      cudaEventElapsedTime(&ms_part, c->tev[1], c->tev[2]);
-      if (c->tune_state == 0) {
-        c->tune_state = 1;
-        c->tune_sort_ms = ms_sort;
-        c->tune_particle_ms.clear();
-      }
-      c->tune_particle_ms.push_back(ms_part);
-      if (int(c->tune_particle_ms.size()) >= kTuneSteps) {
-        double sum = 0.0, best = 0.0;
-        int best_s = kTuneMin;
-        for (int s = 1; s <= kTuneSteps; ++s) {
-          sum += c->tune_particle_ms[s - 1];
-          const double per_step = (c->tune_sort_ms + sum) / s;
-          if (s >= kTuneMin && (s == kTuneMin || per_step < best)) {
-            best = per_step;
-            best_s = s;
-          }
-        }
-        c->sort_interval = best_s;
-        c->tune_state = 2;
-      }
-    }
-    if (c->cfg.timing || !c->cfg.graphs) {
-      if (cudaEventSynchronize(c->tev[5]) != cudaSuccess) return PIC_ECUDA;
-      float ms[5] = {0.f, 0.f, 0.f, 0.f, 0.f};
-      for (int q = 0; q < 5; ++q) cudaEventElapsedTime(&ms[q], c->tev[q], c->tev[q + 1]);
-      c->t_sort += ms[0];
-      c->t_part += ms[1];
-      c->t_other += ms[2] + ms[4];
-      if (c->cfg.graphs) {
-        c->t_poisson += ms[3];
-        c->last_ms = ms[3];
-        PoissonState ps;
-        if (cudaMemcpy(&ps, c->d_ps, sizeof(ps), cudaMemcpyDeviceToHost) != cudaSuccess)
-          return PIC_ECUDA;
-        c->last_outer = ps.outer_iters;
-        c->launches += (sorting ? 4 : 0) + 3 + poisson_kernel_count(c, ps);
-        if (!ps.outer_done) return PIC_ENOCONV;
-      } else {
-        c->t_poisson += c->last_ms;
-      }
+    if (timed) {
+      c->tslot_tune[slot] = tuning ? 1 : 0;
+      c->tpend += 1;
+      // the tuning decides the next step's sort: read its slot now
+      if (tuning || !c->cfg.graphs || c->tpend == kTimeSlots)
+        if ((st = flush_timing(c)) != PIC_OK) return st;
     }
   }
+  return PIC_OK;
+}
+
+pic_status pic_set_timing(pic_ctx *c, int32_t on) {
+  if (!c || on < 0 || on > 1) return PIC_EINVAL;
+  c->cfg.timing = on;
   return PIC_OK;
 }
 
@@ -827,6 +889,7 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
   if (!c || (!out && kind != PIC_DIAG_STATUS)) return PIC_EINVAL;
   if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
+  if (flush_timing(c) != PIC_OK || count_solves(c) != PIC_OK) return PIC_ECUDA;
   const Geom &g = c->g;
   const size_t nn = size_t(g.nxn) * g.nyn;
   int64_t count = 0;
@@ -1045,12 +1108,16 @@ pic_status pic_free(pic_ctx *c) {
   c->allocs.clear();
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_ps) cudaFreeHost(c->h_ps);
-  for (int k = 0; k < 2; ++k) {
-    if (c->gexec[k]) cudaGraphExecDestroy(c->gexec[k]);
-    if (c->graph[k]) cudaGraphDestroy(c->graph[k]);
+  for (int k = 0; k < 2; ++k)
+    for (int v = 0; v < 2; ++v) {
+      if (c->gexec[k][v]) cudaGraphExecDestroy(c->gexec[k][v]);
+      if (c->graph[k][v]) cudaGraphDestroy(c->graph[k][v]);
+    }
+  for (int q = 0; q < kPhaseEvents; ++q) {
+    if (c->tev[q]) cudaEventDestroy(c->tev[q]);
+    for (int s = 0; s < kTimeSlots; ++s)
+      if (c->tpool[s][q]) cudaEventDestroy(c->tpool[s][q]);
   }
-  for (int k = 0; k < 6; ++k)
-    if (c->tev[k]) cudaEventDestroy(c->tev[k]);
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);

@@ -83,11 +83,42 @@ __host__ __device__ inline float2 pair_split(double d) {
 }
 __host__ __device__ inline double pair_join(float2 p) { return double(p.x) + double(p.y); }
 
+// Step phases timed by events: sort | particle kernel | rho | Poisson solve
+// (with the field), bounded by kPhaseEvents events.
+constexpr int kPhaseEvents = 5;
+constexpr int kTimeSlots = 64;
+
+// Division by a divisor fixed at set-up, by a multiply-high and shifts on the
+// integer pipes (Granlund and Montgomery, PLDI 1994): for 1 <= d < 2^31 and
+// 0 <= n < 2^31, with l = ceil(log2 d) and m = floor(2^32 (2^l - d) / d) + 1,
+// t = hi32(m n) and n / d = (t + ((n - t) >> 1)) >> (l - 1); d = 1 passes n.
+struct FastDiv {
+  uint32_t d, m, l;
+};
+inline FastDiv make_fastdiv(uint32_t d) {
+  FastDiv f;
+  f.d = d;
+  f.l = 0;
+  while ((uint64_t(1) << f.l) < d) ++f.l;
+  f.m = d <= 1 ? 0u : uint32_t(((uint64_t(1) << 32) * ((uint64_t(1) << f.l) - d)) / d + 1);
+  return f;
+}
+__host__ __device__ __forceinline__ int fdiv(int n, const FastDiv &f) {
+  if (f.d == 1) return n;
+#ifdef __CUDA_ARCH__
+  const uint32_t t = __umulhi(f.m, uint32_t(n));
+#else
+  const uint32_t t = uint32_t((uint64_t(f.m) * uint32_t(n)) >> 32);
+#endif
+  return int((t + ((uint32_t(n) - t) >> 1)) >> (f.l - 1));
+}
+
 struct Geom {
   int nx, ny;          // cells
   int px, py;          // periodic flags
   int nxn, nyn;        // nodes
   int ntx, nty;        // tiles
+  FastDiv dnyn;        // division by nyn (node index -> row)
 };
 
 // Cell mask bits (uint8 per cell)
@@ -125,6 +156,9 @@ struct PoissonState {
   int32_t inner_done, outer_done;
   int32_t inner_iters, total_iters;
   int32_t outer_iters, go;   // go: the last residual check asked for another inner solve
+  // running totals over all solves (never reset): solves ended, their outer
+  // passes and inner iterations, for the launch count of timed graph steps
+  long long n_solves, sum_outer, sum_total;
 };
 
 struct MGLevel {
@@ -288,11 +322,18 @@ struct pic_ctx {
   int64_t stage_n;
   int fields_dirty;
   int64_t step;
-  // captured step graphs: [0] without, [1] with the tile sort
-  cudaGraph_t graph[2];
-  cudaGraphExec_t gexec[2];
-  // per-phase timing (PIC_DIAG_TIMING)
-  cudaEvent_t tev[6];
+  // captured step graphs [with the tile sort][with phase event nodes]
+  cudaGraph_t graph[2][2];
+  cudaGraphExec_t gexec[2][2];
+  cudaGraphNode_t evnode[2][picgb::kPhaseEvents];   // event nodes of the [.][1] graphs
+  // per-phase timing (PIC_DIAG_TIMING): each timed step records its phase
+  // boundaries into its own slot of the pool, read back when the pool is full
+  // or a diagnostic is read, so timed steps are not serialised with the host
+  cudaEvent_t tev[picgb::kPhaseEvents];              // capture placeholders, solve timing
+  cudaEvent_t tpool[picgb::kTimeSlots][picgb::kPhaseEvents];
+  int tpend;                                         // slots recorded, not yet read
+  uint8_t tslot_tune[picgb::kTimeSlots];             // the slot's step feeds the sort tuning
+  long long seen_solves, seen_outer, seen_total;     // solve totals already counted
   double t_part, t_sort, t_poisson, t_other;
   int64_t t_steps, t_sorts, launches, t_slots;
   std::vector<void *> allocs;
@@ -327,7 +368,7 @@ void fast_poisson_launch(pic_ctx *c, const float *r, float *e, PoissonState *ps)
 cudaError_t launch_rho(pic_ctx *c, int advance_step);
 pic_status poisson_solve(pic_ctx *c, bool zero_guess);
 cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNode_t> &deps);
-int64_t poisson_kernel_count(pic_ctx *c, const PoissonState &ps);
+int64_t poisson_kernel_count(pic_ctx *c, int64_t S, int64_t O, int64_t I);
 pic_status ensure_vacuum_potential(pic_ctx *c);
 pic_status learned_input(pic_ctx *c, int hpad, float *x, double *scale);
 pic_status poisson_with_guess(pic_ctx *c, int guess, const float *y, double scale, double *stats);

@@ -106,35 +106,24 @@ __device__ void block_sum(double (&v)[NV]) {
   block_sum_warps<NV>(v);
 }
 
-// Sums of squares for the norms: a value of moderate size (2^-50 < |x| <
-// 2^50) is squared and summed in FP32, any other in FP64, so no square
-// overflows or underflows.  The FP32 partials are summed over the warp in
-// FP32 unless a lane of the warp holds an FP64 partial.  The relative error
-// of a norm is a few FP32 roundings, which a convergence test and an energy
-// diagnostic can carry.
-__device__ __forceinline__ void sq_add(float &f, double &d, float x) {
+// Sums of squares for the norms, in FP32 without overflow or underflow:
+// |x| in [2^-50, 2^50] is squared as it is, larger values after scaling by
+// 2^-80 and smaller ones by 2^80, each class in its own accumulator (selects,
+// no branch).  FP64 arithmetic is slow on this GPU, so the grid sum runs in
+// FP32 within each warp and in double-float pairs across warps and blocks;
+// only the last step joins the classes in FP64.  The relative error of a
+// norm is a few FP32 roundings.
+struct SqSum {
+  float mid, big, tiny;
+};
+__device__ __forceinline__ void sq_add(SqSum &a, float x) {
   const float ax = fabsf(x);
-  if (ax < 0x1p50f && (ax > 0x1p-50f || ax == 0.f)) f = fmaf(x, x, f);
-  else d = fma(double(x), double(x), d);
-}
-
-template <int NV>
-__device__ __forceinline__ void warp_sum_sq(const float (&f)[NV], const double (&d)[NV], double (&v)[NV]) {
-  bool wide = false;
-#pragma unroll
-  for (int k = 0; k < NV; ++k) wide |= d[k] != 0.0;
-  if (__any_sync(0xffffffffu, wide)) {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) v[k] = warp_sum(double(f[k]) + d[k]);
-  } else {
-#pragma unroll
-    for (int k = 0; k < NV; ++k) {
-      float s = f[k];
-#pragma unroll
-      for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-      v[k] = double(s);
-    }
-  }
+  const bool big = ax > 0x1p50f, tiny = ax < 0x1p-50f;
+  const float y = x * (big ? 0x1p-80f : (tiny ? 0x1p80f : 1.f));
+  const float y2 = y * y;
+  a.mid += (big || tiny) ? 0.f : y2;
+  a.big += big ? y2 : 0.f;
+  a.tiny += tiny ? y2 : 0.f;
 }
 
 // Deterministic grid reduction: every block publishes its partials, the
@@ -155,13 +144,22 @@ __device__ bool grid_sum_blocks(double (&v)[NV], double *part, unsigned int *tic
   __syncthreads();
   if (!last) return false;
   __threadfence();
+  constexpr int kRound = NV >= 8 ? 1 : 8 / NV;   // partials per thread per round of loads
   double s[NV];
 #pragma unroll
   for (int k = 0; k < NV; ++k) s[k] = 0;
-  const volatile double *vp = part;
-  for (int b = threadIdx.x; b < (int)gridDim.x; b += blockDim.x) {
+  for (int b0 = threadIdx.x; b0 < (int)gridDim.x; b0 += kRound * blockDim.x) {
+    double x[kRound][NV];
 #pragma unroll
-    for (int k = 0; k < NV; ++k) s[k] += vp[b * NV + k];
+    for (int j = 0; j < kRound; ++j) {
+      const int b = b0 + j * int(blockDim.x);
+#pragma unroll
+      for (int k = 0; k < NV; ++k) x[j][k] = b < (int)gridDim.x ? __ldcg(part + b * NV + k) : 0.0;
+    }
+#pragma unroll
+    for (int j = 0; j < kRound; ++j)
+#pragma unroll
+      for (int k = 0; k < NV; ++k) s[k] += x[j][k];
   }
   block_sum<NV>(s);
   if (threadIdx.x == 0) {
@@ -179,12 +177,90 @@ __device__ bool grid_sum(double (&v)[NV], double *part, unsigned int *ticket) {
   return grid_sum_blocks<NV>(v, part, ticket);
 }
 
-// grid sum of the sums of squares formed by sq_add
-template <int NV>
-__device__ bool grid_sum_sq(const float (&f)[NV], const double (&d)[NV], double (&v)[NV], double *part,
-                            unsigned int *ticket) {
-  warp_sum_sq<NV>(f, d, v);
-  return grid_sum_blocks<NV>(v, part, ticket);
+// FP32 tree sums of the sq_add classes.  Each block reduces its NC class
+// sums by shuffles within the warps and then over the warps (block_tree,
+// result in thread 0); the last block to arrive adds the blocks' partials
+// the same way, in a fixed order.  The summands are non-negative, so each
+// level of a tree adds at most one FP32 rounding to the relative error.
+template <int NC>
+__device__ __forceinline__ void block_tree(float (&c)[NC]) {
+  __shared__ float sh[NC][32];
+  const int lane = threadIdx.x & 31, w = threadIdx.x >> 5, nw = blockDim.x >> 5;
+#pragma unroll
+  for (int q = 0; q < NC; ++q)
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) c[q] += __shfl_down_sync(0xffffffffu, c[q], o);
+  __syncthreads();   // sh may still be read by a previous call
+  if (lane == 0) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) sh[q][w] = c[q];
+  }
+  __syncthreads();
+  if (w == 0) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) {
+      c[q] = lane < nw ? sh[q][lane] : 0.f;
+#pragma unroll
+      for (int o = 16; o > 0; o >>= 1) c[q] += __shfl_down_sync(0xffffffffu, c[q], o);
+    }
+  }
+}
+
+// Publishes the block's sums (part[block][NC]) and takes a ticket; true in
+// the last block to arrive.
+template <int NC>
+__device__ bool publish_sums(float (&c)[NC], float *part, unsigned int *ticket) {
+  __shared__ bool last;
+  block_tree<NC>(c);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < NC; ++q) part[blockIdx.x * NC + q] = c[q];
+    __threadfence();
+    last = atomicAdd(ticket, 1u) == gridDim.x - 1;
+  }
+  __syncthreads();
+  return last;
+}
+
+// In the last block: the totals of nb blocks' published sums, in thread 0.
+template <int NC>
+__device__ void sum_published(const float *part, int nb, float (&c)[NC]) {
+  __threadfence();
+#pragma unroll
+  for (int q = 0; q < NC; ++q) c[q] = 0.f;
+  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
+    float x[NC];
+#pragma unroll
+    for (int q = 0; q < NC; ++q) x[q] = __ldcg(part + b * NC + q);
+#pragma unroll
+    for (int q = 0; q < NC; ++q) c[q] += x[q];
+  }
+  block_tree<NC>(c);
+}
+
+// a class triple (mid, big, tiny) of sq_add as a double
+__device__ __forceinline__ double sq_join(const float *c) {
+  return double(c[0]) + double(c[1]) * 0x1p160 + double(c[2]) * 0x1p-160;
+}
+
+// sqrt(num / den) for finite num >= 0 and normal den > 0, to FP32 accuracy,
+// without the FP64 divide and square root (long instruction sequences on
+// this GPU's narrow FP64 unit): the exponents are split off by bit
+// manipulation and the mantissa ratio is taken in FP32.  NaN in, NaN out.
+__device__ double sqrt_ratio(double num, double den) {
+  if (num != num || den != den) return num + den;
+  if (num == 0.0) return 0.0;
+  if (num > 1.7e308) return num;
+  const long long bn = __double_as_longlong(num), bd = __double_as_longlong(den);
+  int e = int((bn >> 52) & 0x7ff) - int((bd >> 52) & 0x7ff);
+  const float mn = __int_as_float(0x3f800000 | int((bn >> 29) & 0x7fffff));
+  const float md = __int_as_float(0x3f800000 | int((bd >> 29) & 0x7fffff));
+  float r = mn / md;
+  if (e & 1) {
+    r *= 2.f;
+    e -= 1;
+  }
+  return double(sqrtf(r)) * __longlong_as_double((long long)(e / 2 + 1023) << 52);
 }
 
 struct FineArgs {
@@ -198,13 +274,16 @@ struct FineArgs {
   const float2 *rho_ext;
   const unsigned long long *bottom;
   float2 qw[2];              // q_s w_s 2^-20 (double-float)
-  double sw[2];              // q_s w_s (surface charge per hit)
+  float2 sw[2];              // q_s w_s / 2: the charge of a surface hit on each of its two nodes
   int surface;
   float *r32, *z, *p, *w, *q, *e;
   PoissonState *ps;
   double *part;
+  float *partf;              // the residual kernel's FP32 block sums
+  float *bbpart;             // ||b||^2 block sums of a first pass that does not check
   unsigned int *ticket;
   int singular;
+  int bb_from_part;          // the second pass takes ||b||^2 from bbpart
   double rtol;
   int maxit;
   int32_t *step;
@@ -237,7 +316,7 @@ __global__ void k_rho(FineArgs a) {
   pdl_enter();
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
-  double v[1] = {0.0};
+  float2 sum = make_float2(0.f, 0.f);   // doubly periodic box: sum of rho
   VEC_BATCHES(base, nn) {
     unsigned long long a0[kVB], a1[kVB];
     float2 rx[kVB];
@@ -255,23 +334,26 @@ __global__ void k_rho(FineArgs a) {
                             pair_mul(a.qw[1], pair_from_ll((long long)a1[k])));
       rho = pair_add(rx[k], rho);
       if (a.surface && !g.px) {
-        const int i = n / g.nyn, j = n - (n / g.nyn) * g.nyn;
+        const int i = fdiv(n, g.dnyn), j = n - i * g.nyn;
         if (i == g.nx - 1) {
           // half of bottom face k's charge on nodes (nx-1, k) and (nx-1, k+1)
-          double s = 0.0;
-          if (j < g.ny) s += 0.5 * (a.sw[0] * double(a.bottom[j]) + a.sw[1] * double(a.bottom[g.ny + j]));
+          // (a.sw holds q_s w_s / 2)
           int jm = j - 1;
           if (g.py && jm < 0) jm += g.ny;
+          if (j < g.ny)
+            rho = pair_add(rho, pair_add(pair_mul(a.sw[0], pair_from_ll((long long)a.bottom[j])),
+                                         pair_mul(a.sw[1], pair_from_ll((long long)a.bottom[g.ny + j]))));
           if (jm >= 0 && jm < g.ny)
-            s += 0.5 * (a.sw[0] * double(a.bottom[jm]) + a.sw[1] * double(a.bottom[g.ny + jm]));
-          rho = pair_add(rho, pair_split(s));
+            rho = pair_add(rho, pair_add(pair_mul(a.sw[0], pair_from_ll((long long)a.bottom[jm])),
+                                         pair_mul(a.sw[1], pair_from_ll((long long)a.bottom[g.ny + jm]))));
         }
       }
       a.rho[n] = rho;
-      if (a.singular) v[0] += pair_join(rho);   // every node is free
+      if (a.singular) sum = pair_add(sum, rho);   // every node is free
     }
   }
   if (a.singular) {
+    double v[1] = {pair_join(sum)};
     if (grid_sum<1>(v, a.part, a.ticket) && threadIdx.x == 0) a.ps->bmean = v[0] / double(nn);
   } else if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.ps->bmean = 0.0;
@@ -307,7 +389,7 @@ __global__ void k_extrapolate(FineArgs a) {
 }
 
 __device__ __forceinline__ void nbr_index(const Geom &g, int n, int &xm, int &xp, int &ym, int &yp) {
-  const int i = n / g.nyn, j = n - (n / g.nyn) * g.nyn;
+  const int i = fdiv(n, g.dnyn), j = n - i * g.nyn;
   const int im = g.px ? wrapi(i - 1, g.nxn) : max(i - 1, 0);
   const int ip = g.px ? wrapi(i + 1, g.nxn) : min(i + 1, g.nxn - 1);
   const int jm = g.py ? wrapi(j - 1, g.nyn) : max(j - 1, 0);
@@ -318,18 +400,61 @@ __device__ __forceinline__ void nbr_index(const Geom &g, int n, int &xm, int &xp
   yp = i * g.nyn + jp;
 }
 
+// The difference a - b of two double-float values rounded to FP32: the high
+// parts by TwoSum, the low parts and its error in FP32.
+__device__ __forceinline__ float pair_diff(float2 a, float2 b) {
+  const float2 t = two_sum(a.x, -b.x);
+  return t.x + (t.y + (a.y - b.y));
+}
+
+// E = -grad phi at a node from its potential and its four neighbours' by the
+// open-edge rule: a central difference where both edges along an axis border
+// plasma, one-sided where one does, zero where neither does.
+__device__ __forceinline__ float2 node_field(uint8_t fk, const float2 (&ph)[5]) {
+  const bool xm = fk & kOpenXm, xp = fk & kOpenXp, ym = fk & kOpenYm, yp = fk & kOpenYp;
+  const float2 x0 = xm ? ph[1] : ph[0], x1 = xp ? ph[2] : ph[0];
+  const float2 y0 = ym ? ph[3] : ph[0], y1 = yp ? ph[4] : ph[0];
+  const float ex = (xm || xp) ? -pair_diff(x1, x0) * ((xm && xp) ? 0.5f : 1.f) : 0.f;
+  const float ey = (ym || yp) ? -pair_diff(y1, y0) * ((ym && yp) ? 0.5f : 1.f) : 0.f;
+  return make_float2(ex, ey);
+}
+
+// r = rho - A phi at a free node = rho + phi_xm + phi_xp + phi_ym + phi_yp -
+// 4 phi, rounded to FP32: the high parts are added by TwoSum, exactly, and
+// the low parts with TwoSum's error terms in FP32, which leaves an error of
+// a few units of 2^-46 |phi|.
+__device__ __forceinline__ float resid_node(float2 rho, const float2 (&ph)[5]) {
+  float2 s = two_sum(ph[1].x, ph[2].x);
+  float2 t = two_sum(ph[3].x, ph[4].x);
+  float lo = s.y + t.y;
+  s = two_sum(s.x, t.x);
+  lo += s.y;
+  s = two_sum(s.x, -4.f * ph[0].x);
+  lo += s.y;
+  s = two_sum(s.x, rho.x);
+  lo += s.y;
+  lo += ((ph[1].y + ph[2].y) + (ph[3].y + ph[4].y)) - 4.f * ph[0].y + rho.y;
+  return s.x + lo;
+}
+
 // Outer residual r = rho - A phi (the certificate; A applied to the whole
-// potential, so the Dirichlet neighbour values enter through phi) in
-// double-float, and the set-up of the inner solve of A e = r.  The norm of
-// b = rho + lift on the free nodes is formed on the first pass of a solve.
+// potential, so the Dirichlet neighbour values enter through phi) from the
+// double-float potential, and the set-up of the inner solve of A e = r.
+// ||b||^2 (b = rho + lift on the free nodes) is formed on the first pass of
+// a solve.  A checking pass (CHECK) also writes the field E of the potential
+// it checks and its energy, so the pass that accepts the potential leaves
+// the step's field, and decides whether the solve goes on.  A first pass
+// known not to be the last (the direct solve's, which always corrects once)
+// skips all that and leaves only its ||b||^2 block sums for the next pass.
+template <bool CHECK>
 __global__ void k_resid(FineArgs a) {
   pdl_enter();
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
   const bool first = a.ps->outer_iters == 0;
+  const bool bb_here = first;
   const float2 bm = a.singular ? pair_split(a.ps->bmean) : make_float2(0.f, 0.f);
-  float f[2] = {0.f, 0.f};
-  double d[2] = {0.0, 0.0}, v[2];
+  SqSum q3[3] = {};
   VEC_BATCHES(base, nn) {
     float2 rh[kVB], ph[kVB][5];
     float lf[kVB];
@@ -339,7 +464,7 @@ __global__ void k_resid(FineArgs a) {
       nbr_index(g, n, xm, xp, ym, yp);
       fl[k] = a.flags[n];
       rh[k] = a.rho[n];
-      lf[k] = first ? a.lift[n] : 0.f;
+      lf[k] = bb_here ? a.lift[n] : 0.f;
       ph[k][0] = a.phi[n];
       ph[k][1] = a.phi[xm];
       ph[k][2] = a.phi[xp];
@@ -349,15 +474,18 @@ __global__ void k_resid(FineArgs a) {
     VEC_NODES(k, n, base, nn) {
       float r32 = 0.f;
       if (fl[k] & kFree) {
-        const float2 rho = pair_sub(rh[k], bm);
-        // -A phi = phi_xm + phi_xp + phi_ym + phi_yp - 4 phi
-        float2 s = pair_add(pair_add(ph[k][1], ph[k][2]), pair_add(ph[k][3], ph[k][4]));
-        s = pair_sub(s, make_float2(4.f * ph[k][0].x, 4.f * ph[k][0].y));
-        r32 = pair_add(rho, s).x;
-        sq_add(f[0], d[0], r32);
-        if (first) sq_add(f[1], d[1], __fadd_rn(rho.x, __fadd_rn(rho.y, lf[k])));
+        const float2 rho = a.singular ? pair_sub(rh[k], bm) : rh[k];
+        r32 = resid_node(rho, ph[k]);
+        if (CHECK) sq_add(q3[0], r32);
+        if (bb_here) sq_add(q3[1], rho.x + (rho.y + lf[k]));
       }
       a.r32[n] = r32;
+      if (CHECK) {
+        const float2 E = node_field(fl[k], ph[k]);
+        a.E[n] = E;
+        sq_add(q3[2], E.x);
+        sq_add(q3[2], E.y);
+      }
       if (!a.direct) {             // the direct inner solve writes all of e and uses no p, q
         a.e[n] = 0.f;
         a.p[n] = 0.f;
@@ -365,32 +493,60 @@ __global__ void k_resid(FineArgs a) {
       }
     }
   }
-  if (grid_sum_sq<2>(f, d, v, a.part, a.ticket) && threadIdx.x == 0) {
-    PoissonState *ps = a.ps;
-    ps->rr64 = v[0];
-    if (first) ps->bb = v[1];
-    v[1] = ps->bb;
-    ps->rel = v[1] > 0 ? sqrt(v[0] / v[1]) : sqrt(v[0]);
-    const bool ok = ps->rel <= a.rtol || v[0] == 0.0;
+  if (!CHECK) {
+    float cb[3] = {q3[1].mid, q3[1].big, q3[1].tiny};
+    block_tree<3>(cb);
+    if (threadIdx.x == 0) {
+#pragma unroll
+      for (int k = 0; k < 3; ++k) a.bbpart[blockIdx.x * 3 + k] = cb[k];
+    }
+    return;
+  }
+  float c[9] = {q3[0].mid, q3[0].big, q3[0].tiny, q3[1].mid, q3[1].big, q3[1].tiny,
+                q3[2].mid, q3[2].big, q3[2].tiny};
+  if (!publish_sums<9>(c, a.partf, a.ticket)) return;
+  sum_published<9>(a.partf, gridDim.x, c);
+  PoissonState *ps = a.ps;
+  const bool bb_parts = a.bb_from_part && ps->outer_iters == 1;
+  float cb[3] = {0.f, 0.f, 0.f};
+  if (bb_parts) sum_published<3>(a.bbpart, gridDim.x, cb);
+  if (threadIdx.x == 0) {
+    const double rr = sq_join(c);
+    a.fe[0] = 0.5 * sq_join(c + 6);
+    ps->rr64 = rr;
+    if (first) ps->bb = sq_join(c + 3);
+    if (bb_parts) ps->bb = sq_join(cb);
+    const double bb = ps->bb;
+    ps->rel = sqrt_ratio(rr, bb > 0 ? bb : 1.0);
+    const bool ok = ps->rel <= a.rtol || rr == 0.0;
     const bool give_up = !ok && ps->outer_iters >= kMaxOuter;
     if (give_up) atomicOr(a.status, PIC_ST_NOCONV);
     const bool go = !ok && !give_up;
     ps->outer_done = ok ? 1 : 0;
     ps->go = go ? 1 : 0;
+    if (!go) {
+      ps->n_solves += 1;
+      ps->sum_outer += ps->outer_iters;
+      ps->sum_total += ps->total_iters;
+    }
     ps->inner_done = go ? 0 : 1;
     if (a.graph) {
       cudaGraphSetConditional(a.h_outer, go ? 1u : 0u);
-      cudaGraphSetConditional(a.h_if_outer, go ? 1u : 0u);
-      if (!a.direct) cudaGraphSetConditional(a.h_inner, go ? 1u : 0u);
+      if (!a.direct) {
+        cudaGraphSetConditional(a.h_if_outer, go ? 1u : 0u);
+        cudaGraphSetConditional(a.h_inner, go ? 1u : 0u);
+      }
     }
     ps->inner_iters = 0;
-    ps->rr0 = v[0];
-    ps->rr = v[0];
-    // inner target: bring ||r|| to half the outer target, no tighter than FP32 allows
-    const double t = 0.5 * a.rtol * sqrt(v[1]) / fmax(sqrt(v[0]), 1e-300);
-    ps->tol_in = fmin(fmax(t, 3e-6), 0.5);
+    ps->rr0 = rr;
+    ps->rr = rr;
+    // inner target: bring ||r|| to half the outer target (0.5 rtol / rel of
+    // the initial residual), no tighter than FP32 allows
+    const float t = 0.5f * float(a.rtol) / float(ps->rel);
+    ps->tol_in = fminf(fmaxf(t, 3e-6f), 0.5f);
     ps->beta = 0.0;
     ps->rz = 0.0;
+    *a.ticket = 0u;
   }
 }
 
@@ -528,14 +684,14 @@ __global__ void k_outer_init(PoissonState *ps) {
   ps->outer_iters = 0;
 }
 
-// E = -grad phi by the open-edge rule; field energy 1/2 sum |E|^2.  Each
-// difference of the potential is taken in double-float and rounded once.
+// E = -grad phi and the field energy 1/2 sum |E|^2 of the current potential
+// (the residual kernel forms them too; this kernel serves the paths that
+// change the potential without a solve)
 __global__ void k_field(FineArgs a) {
   pdl_enter();
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
-  float f[1] = {0.f};
-  double d[1] = {0.0}, v[1];
+  SqSum q1 = {};
   VEC_BATCHES(base, nn) {
     float2 ph[kVB][5];
     uint8_t fl[kVB];
@@ -551,20 +707,19 @@ __global__ void k_field(FineArgs a) {
       ph[k][4] = a.phi[yp];
     }
     VEC_NODES(k, n, base, nn) {
-      const uint8_t fk = fl[k];
-      // -dphi/dx: central difference where both edges are open, one-sided
-      // where one is, zero where neither is
-      const bool xm = fk & kOpenXm, xp = fk & kOpenXp, ym = fk & kOpenYm, yp = fk & kOpenYp;
-      const float2 x0 = xm ? ph[k][1] : ph[k][0], x1 = xp ? ph[k][2] : ph[k][0];
-      const float2 y0 = ym ? ph[k][3] : ph[k][0], y1 = yp ? ph[k][4] : ph[k][0];
-      const float ex = (xm || xp) ? -pair_sub(x1, x0).x * ((xm && xp) ? 0.5f : 1.f) : 0.f;
-      const float ey = (ym || yp) ? -pair_sub(y1, y0).x * ((ym && yp) ? 0.5f : 1.f) : 0.f;
-      a.E[n] = make_float2(ex, ey);
-      sq_add(f[0], d[0], ex);
-      sq_add(f[0], d[0], ey);
+      const float2 E = node_field(fl[k], ph[k]);
+      a.E[n] = E;
+      sq_add(q1, E.x);
+      sq_add(q1, E.y);
     }
   }
-  if (grid_sum_sq<1>(f, d, v, a.part, a.ticket) && threadIdx.x == 0) a.fe[0] = 0.5 * v[0];
+  float c[3] = {q1.mid, q1.big, q1.tiny};
+  if (!publish_sums<3>(c, a.partf, a.ticket)) return;
+  sum_published<3>(a.partf, gridDim.x, c);
+  if (threadIdx.x == 0) {
+    a.fe[0] = 0.5 * sq_join(c);
+    *a.ticket = 0u;
+  }
 }
 
 // --------------------------------------------------------------------------
@@ -1244,7 +1399,7 @@ FineArgs fine_args(pic_ctx *c) {
   for (int s = 0; s < 2; ++s) {
     const double w = 1.0 / double(c->cfg.ppc[s]);
     a.qw[s] = pair_split(c->cfg.charge[s] * w * std::ldexp(1.0, -kFracBits));
-    a.sw[s] = c->cfg.charge[s] * w;
+    a.sw[s] = pair_split(0.5 * c->cfg.charge[s] * w);
   }
   a.surface = c->cfg.surface_charge;
   a.r32 = c->d_r32;
@@ -1255,8 +1410,11 @@ FineArgs fine_args(pic_ctx *c) {
   a.e = c->d_e;
   a.ps = c->d_ps;
   a.part = c->red.part;
+  a.partf = reinterpret_cast<float *>(c->red.part);
+  a.bbpart = reinterpret_cast<float *>(c->red.part) + 16 * size_t(c->red.nblocks);
   a.ticket = c->red.ticket;
   a.singular = c->singular;
+  a.bb_from_part = 0;
   a.rtol = c->cfg.poisson_rtol;
   a.maxit = c->cfg.poisson_maxit;
   a.step = c->d_step;
@@ -1604,7 +1762,7 @@ cudaError_t poisson_setup(pic_ctx *c) {
   c->red.nblocks = blocks_for((int(nn) + kVB - 1) / kVB);
   // partials of the grid reductions: the vector kernels and the level-0 post-smoothing
   const int nparts = std::max(c->red.nblocks, c->lc > 0 ? post_tiles(c->lev[0], true) : 0);
-  c->red.part = (double *)dev_alloc(c, size_t(nparts) * 8 * sizeof(double));
+  c->red.part = (double *)dev_alloc(c, size_t(nparts) * 16 * sizeof(double));
   c->red.ticket = (unsigned int *)dev_alloc(c, 64);
   c->d_ps = (PoissonState *)dev_alloc(c, sizeof(PoissonState));
   if (!c->red.part || !c->red.ticket || !c->d_ps) return cudaErrorMemoryAllocation;
@@ -1648,7 +1806,7 @@ pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
   c->launches += 1;
   const int batch = 4;
   for (;;) {
-    launch(k_resid, nb, kThreads, 0, c->stream, a);
+    launch(k_resid<true>, nb, kThreads, 0, c->stream, a);
     c->launches += 1;
     cudaMemcpyAsync(c->h_ps, c->d_ps, sizeof(PoissonState), cudaMemcpyDeviceToHost, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
@@ -1682,6 +1840,10 @@ pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
   cudaEventElapsedTime(&ms, c->ev0, c->ev1);
   c->last_ms = ms;
   c->last_outer = c->h_ps->outer_iters;
+  // solves from the host loop count their own launches
+  c->seen_solves = c->h_ps->n_solves;
+  c->seen_outer = c->h_ps->sum_outer;
+  c->seen_total = c->h_ps->sum_total;
   if (note(cudaGetLastError(), "Poisson solve") != cudaSuccess) return PIC_ECUDA;
   return c->h_ps->outer_done ? PIC_OK : PIC_ENOCONV;
 }
@@ -1725,51 +1887,66 @@ cudaError_t add_cond(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
 }  // namespace
 
 // Appends the solve to graph `top` after the nodes in `deps`; on return
-// `deps` holds the solve's last node.  Structure:
-//   [phi reset] -> init -> WHILE(outer) { resid64 -> IF(go) { V-cycle ->
+// `deps` holds the solve's last node.  With the multigrid inner solve:
+//   [phi reset] -> init -> WHILE(outer) { resid -> IF(go) { V-cycle ->
 //     WHILE(inner) { cg -> IF(!done) { V-cycle } } -> correct } }
 // where a V-cycle also forms w = A z and the inner products of the next step.
+// With the direct inner solve, whose one pass nearly always suffices, the
+// first pass runs unconditionally (a potential that already meets the
+// tolerance takes one correction it does not need) and only further passes
+// are conditional:
+//   [phi reset] -> init -> resid -> solve -> correct -> resid ->
+//     WHILE(go) { solve -> correct -> resid }
 cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNode_t> &deps) {
   cudaStream_t s = c->stream;
   FineArgs a = fine_args(c);
   const MGArgs m = mg_args(c);
   const int nb = c->red.nblocks;
+  const bool direct = c->fp.enabled;
   cudaGraphConditionalHandle h[4];
-  const int nh = c->fp.enabled ? 2 : 4;
+  const int nh = direct ? 1 : 4;
   for (int k = 0; k < nh; ++k) {
-    cudaError_t e = cudaGraphConditionalHandleCreate(&h[k], top, k == 0 ? 1u : 0u,
+    cudaError_t e = cudaGraphConditionalHandleCreate(&h[k], top, (k == 0 && !direct) ? 1u : 0u,
                                                      cudaGraphCondAssignDefault);
     if (e != cudaSuccess) return note(e, "cudaGraphConditionalHandleCreate");
   }
   a.graph = 1;
   a.h_outer = h[0];
-  a.h_if_outer = h[1];
-  a.h_inner = c->fp.enabled ? 0 : h[2];
-  a.h_if_inner = c->fp.enabled ? 0 : h[3];
+  a.h_if_outer = direct ? 0 : h[1];
+  a.h_inner = direct ? 0 : h[2];
+  a.h_if_inner = direct ? 0 : h[3];
   cudaError_t e;
 #define CK(x) do { if ((e = (x)) != cudaSuccess) { note(e, #x); return e; } } while (0)
   CK(cap_begin(s, top, deps));
   if (c->cfg.warm_start == 0) launch(k_phi_reset, nb, kThreads, 0, s, a);
   if (c->cfg.warm_start == 2) launch(k_extrapolate, nb, kThreads, 0, s, a);
   launch(k_outer_init, 1, 1, 0, s, c->d_ps);
+  if (direct) {
+    // the first pass always corrects: it leaves ||b||^2 to the second
+    launch(k_resid<false>, nb, kThreads, 0, s, a);
+    fast_poisson_launch(c, c->d_r32, c->d_e, c->d_ps);
+    launch(k_correct, nb, kThreads, 0, s, a);
+    a.bb_from_part = 1;
+    launch(k_resid<true>, nb, kThreads, 0, s, a);
+  }
   CK(cap_end(s, deps));
   cudaGraphNode_t n_outer, n_if_outer, n_inner, n_if_inner;
   cudaGraph_t b_outer, b_if_outer, b_inner, b_if_inner;
   CK(add_cond(top, deps, h[0], cudaGraphCondTypeWhile, &n_outer, &b_outer));
   std::vector<cudaGraphNode_t> d;
-  CK(cap_begin(s, b_outer, {}));
-  launch(k_resid, nb, kThreads, 0, s, a);
-  CK(cap_end(s, d));
-  CK(add_cond(b_outer, d, h[1], cudaGraphCondTypeIf, &n_if_outer, &b_if_outer));
-  if (c->fp.enabled) {
-    // direct inner solve: IF(go) { solve, correct }
-    CK(cap_begin(s, b_if_outer, {}));
+  if (direct) {
+    CK(cap_begin(s, b_outer, {}));
     fast_poisson_launch(c, c->d_r32, c->d_e, c->d_ps);
     launch(k_correct, nb, kThreads, 0, s, a);
+    launch(k_resid<true>, nb, kThreads, 0, s, a);
     CK(cap_end(s, d));
     deps.assign(1, n_outer);
     return cudaGetLastError();
   }
+  CK(cap_begin(s, b_outer, {}));
+  launch(k_resid<true>, nb, kThreads, 0, s, a);
+  CK(cap_end(s, d));
+  CK(add_cond(b_outer, d, h[1], cudaGraphCondTypeIf, &n_if_outer, &b_if_outer));
   CK(cap_begin(s, b_if_outer, {}));
   launch_vcycle(c, m);
   launch_zw(c, a);
@@ -1792,17 +1969,16 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   return cudaGetLastError();
 }
 
-// Kernels one solve launched, from its device counters (graph mode).
-int64_t poisson_kernel_count(pic_ctx *c, const PoissonState &ps) {
-  const int64_t O = ps.outer_iters, I = ps.total_iters;
-  if (c->fp.enabled)   // init + resid per outer pass (+1 final) + per pass (direct solve, correct)
-    return 1 + (O + 1) + O * (c->fp.kernels + 1) + (c->cfg.warm_start != 1 ? 1 : 0);
+// Kernels that S solves with O outer passes and I inner iterations in all
+// launched (graph mode; every outer pass takes at least one inner iteration).
+int64_t poisson_kernel_count(pic_ctx *c, int64_t S, int64_t O, int64_t I) {
+  const int64_t per_solve = 2 + (c->cfg.warm_start != 1 ? 1 : 0);   // init, final resid, [guess]
+  if (c->fp.enabled)   // per pass: resid, direct solve, correct
+    return S * per_solve + O * (c->fp.kernels + 2);
   // a V-cycle with w = A z and the inner products: fused into its last kernel unless lc = 0
   const int64_t vc = 2 * c->lc + 1 + (c->lc == 0 ? 1 : 0);
-  // init + resid per outer pass (+1 final) + per inner solve (V-cycle, correct)
-  // + per iteration (cg) + per non-final iteration (V-cycle)
-  return 1 + (O + 1) + O * (vc + 1) + I + std::max<int64_t>(I - O, 0) * vc +
-         (c->cfg.warm_start != 1 ? 1 : 0);
+  // per pass: resid, V-cycle, correct; per iteration: cg; per non-final iteration: V-cycle
+  return S * per_solve + O * (vc + 2) + I + (I - O) * vc;
 }
 
 
@@ -1869,6 +2045,11 @@ pic_status ensure_vacuum_potential(pic_ctx *c) {
   cudaMemcpyAsync(c->d_phi, save_phi, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
   cudaMemcpyAsync(c->d_rho, save_rho, nn * 8, cudaMemcpyDeviceToDevice, c->stream);
   cudaMemcpyAsync(c->d_ps, &ps_save, sizeof(ps_save), cudaMemcpyHostToDevice, c->stream);
+  c->seen_solves = ps_save.n_solves;
+  c->seen_outer = ps_save.sum_outer;
+  c->seen_total = ps_save.sum_total;
+  // the solve's residual passes wrote the empty box's field: back to the restored potential's
+  launch_field(c);
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
   return st;
 }
@@ -1907,7 +2088,6 @@ pic_status poisson_with_guess(pic_ctx *c, int guess, const float *y, double scal
   }
   const pic_status st = poisson_solve(c, guess == 0);
   cudaEventRecord(c->tev[1], c->stream);
-  if (launch_field(c) != cudaSuccess) return PIC_ECUDA;
   if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
   float ms = 0.f;
   cudaEventElapsedTime(&ms, c->tev[0], c->tev[1]);

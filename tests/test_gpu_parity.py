@@ -161,6 +161,34 @@ def test_tuned_sort_interval_changes_no_result():
     assert np.array_equal(tuned.counts()[0], fixed.counts()[0])
 
 
+@pytest.mark.parametrize("name", ["trench64", "trench"])
+def test_phase_timing_changes_no_result(name):
+    # timed graph steps carry event nodes between the phases and record them
+    # into a pool of slots read back later; the physics is the same bitwise,
+    # and the counts of steps and launches agree with the untimed run's
+    w = ALL[name].replace(sort_every=8)
+    runs = []
+    for timing in (True, False):
+        gs = gpu_sim(w, timing=timing)
+        for s in (0, 1):
+            gs.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
+        gs.step(1)
+        gs.timing()
+        gs.step(70)                 # more steps than the pool's 64 slots
+        gs.set_timing(not timing)   # both graph kinds within one run
+        gs.step(5)
+        runs.append((gs, gs.timing()))
+    (a, ta), (b, tb) = runs
+    by_id = lambda st: st[:, np.argsort(st[4], kind="stable")]
+    for s in (0, 1):
+        assert np.array_equal(by_id(a.state(s)), by_id(b.state(s)))
+    assert np.array_equal(a.phi(), b.phi())
+    assert np.array_equal(a.efield()[0], b.efield()[0])
+    assert ta["steps"] == tb["steps"] == 75
+    assert ta["launches"] == tb["launches"] > 75 * 4
+    assert ta["ms_particles"] > 0 and ta["ms_poisson"] > 0 and tb["ms_particles"] > 0
+
+
 def test_direct_solver_applies_only_to_its_geometry():
     import paper_1610_03918_gb300 as pg
     for w in (synth.small_trench(nx=40, ny=40),            # ny not a power of two
