@@ -372,9 +372,13 @@ __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint3
   const Geom &g = a.g;
   const int i = cell_i(c);
   const int j = cell_j(c);
-  const int li = local_coord(i, wi0, g.nx, g.px);
-  const int lj = local_coord(j, wj0, g.ny, g.py);
-  const bool inw = (unsigned)li < (unsigned)WXc && (unsigned)lj < (unsigned)WYc;
+  int li = i - wi0, lj = j - wj0;
+  bool inw = (unsigned)li < (unsigned)WXc && (unsigned)lj < (unsigned)WYc;
+  if (!inw && (g.px | g.py)) {   // the window may reach across a periodic edge
+    li = local_coord(i, wi0, g.nx, g.px);
+    lj = local_coord(j, wj0, g.ny, g.py);
+    inw = (unsigned)li < (unsigned)WXc && (unsigned)lj < (unsigned)WYc;
+  }
   if (MODE == 1) {
     // deposit only, at the current position
     int w00, w01, w10, w11;
@@ -451,6 +455,15 @@ __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint3
   }
 }
 
+// The step kernel asks for the particle state of its next iteration (512
+// particles, one bulk L2 prefetch per array from thread 0) while the CTA
+// works on the current one, so the next loads find it in L2.  One iteration
+// ahead measured best (further ahead, or on into the next chunk, was slower).
+constexpr int kPrefetchAhead = 1;
+__device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
+  asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
+}
+
 template <int MODE>
 __global__ void __launch_bounds__(kParticleThreads, kParticleMinBlocks) k_particles(PArgs a) {
   __shared__ float2 sE[NWX * NWY];
@@ -483,7 +496,21 @@ __global__ void __launch_bounds__(kParticleThreads, kParticleMinBlocks) k_partic
     unsigned long long *acc = a.acc + (int64_t)s * nnodes;
     const ParticleBuf P = a.pbufs[2 * s + a.cur[s]];
     float ke = 0.f;
+    // L2 prefetch of the particle state kPrefetchAhead iterations ahead
+    const int64_t step = 4 * int64_t(blockDim.x);
+    auto prefetch = [&](int64_t from) {
+      if (MODE == 0 && threadIdx.x == 0 && from < ch.end) {
+        const unsigned bytes = unsigned(min((long long)step, (long long)ch.end - from)) * 4u;
+        prefetch_l2(P.cell + from, bytes);
+        prefetch_l2(P.fx + from, bytes);
+        prefetch_l2(P.fy + from, bytes);
+        prefetch_l2(P.vx + from, bytes);
+        prefetch_l2(P.vy + from, bytes);
+      }
+    };
+    for (int d = 0; d < kPrefetchAhead; ++d) prefetch(int64_t(ch.begin) + d * step);
     for (int64_t base = ch.begin + 4 * threadIdx.x; base < ch.end; base += 4 * blockDim.x) {
+      prefetch(base - 4 * threadIdx.x + kPrefetchAhead * step);
       int4 c4 = *reinterpret_cast<const int4 *>(P.cell + base);
       float4 fx4 = *reinterpret_cast<const float4 *>(P.fx + base);
       float4 fy4 = *reinterpret_cast<const float4 *>(P.fy + base);
