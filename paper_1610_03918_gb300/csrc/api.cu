@@ -290,7 +290,7 @@ cudaError_t capture_step(pic_ctx *c, cudaGraph_t g, std::vector<cudaGraphNode_t>
     rec(1);
     launch_particles(c, 0, 1.f, nullptr);
     rec(2);
-    launch_rho(c, 1);
+    launch_rho(c, 1, c->cfg.warm_start == 1);   // opens the solve captured next
     rec(3);
     e = note(capture_leaves(c->stream, deps), "capture: particle phase");
   }

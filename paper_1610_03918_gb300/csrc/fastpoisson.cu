@@ -21,8 +21,11 @@
 //   Slot: a sine transform across its wc columns (Dirichlet walls) gives wc
 //     tridiagonal systems along x (Dirichlet bottom row; the interface is a
 //     separate unknown), solved together by the same reduction.
-// Arithmetic is FP32; the FP64 iterative refinement around it (the residual
-// check of the solver) certifies the result.
+// Arithmetic is FP32; the iterative refinement around it (the residual check
+// of the solver) certifies the result.  Each kernel adds the correction it
+// forms straight into the double-float potential on the nodes it owns (the
+// interface row, the slab rows, the slot rows), so the solve needs no
+// separate correction pass.
 #include <cuda_runtime.h>
 
 #include <algorithm>
@@ -40,6 +43,7 @@ constexpr int kMaxRows = 4096;         // rectangle rows (one mode's reduction f
 constexpr int kPcrThreads = 512;
 constexpr int kSlotThreads = 256;
 constexpr size_t kSmemMax = 200 * 1024;
+constexpr int kRound = 2;              // global loads a thread issues before using them
 
 struct FPArgs {
   int ny, nk, logny, m, xs, slot, c0, wc, ms;
@@ -47,10 +51,13 @@ struct FPArgs {
   const float *dk, *z;               // diagonal per slab mode, interface responses
   float2 *vhat;
   const float *phi, *sb, *zs, *sinv; // slot basis, diagonal per sine mode, responses
+  const float2 *twc;                 // [wc][nk]: w_k exp(+2 pi i k (c0 + c) / ny) / ny
   float *vs;                         // [wc][ms] solved slot spectra
   float *ug;                         // [wc] interface values
+  float2 *fh;                        // [nk] spectrum of the interface values on row m + 1
+  float *sh;                         // [wc] sine spectrum of the interface values
   const float *r;
-  float *e;
+  float2 *pot;                       // the potential (double-float): the correction is added to it
   PoissonState *ps;
 };
 
@@ -163,8 +170,18 @@ __global__ void __launch_bounds__(kFftThreads) k_fp_forward(FPArgs f) {
   pdl_enter();
   const int i0 = 2 * blockIdx.x + 1, i1 = i0 + 1;
   const bool two = i1 <= f.m;
-  for (int j = threadIdx.x; j < f.ny; j += blockDim.x)
-    x[j] = make_float2(f.r[i0 * f.ny + j], two ? f.r[i1 * f.ny + j] : 0.f);
+  constexpr int R = 8;
+  for (int j0 = threadIdx.x; j0 < f.ny; j0 += R * blockDim.x) {   // a round's loads in flight together
+    float2 v[R];
+#pragma unroll
+    for (int u = 0; u < R; ++u) {
+      const int j = j0 + u * blockDim.x;
+      v[u] = j < f.ny ? make_float2(f.r[i0 * f.ny + j], two ? f.r[i1 * f.ny + j] : 0.f) : make_float2(0.f, 0.f);
+    }
+#pragma unroll
+    for (int u = 0; u < R; ++u)
+      if (j0 + u * int(blockDim.x) < f.ny) x[j0 + u * blockDim.x] = v[u];
+  }
   __syncthreads();
   const float2 *Z = fft_smem(x, y, tw, f.ny, f.logny, false);
   for (int k = threadIdx.x; k < f.nk; k += blockDim.x) {
@@ -196,7 +213,17 @@ __global__ void __launch_bounds__(kPcrThreads) k_fp_tridiag(FPArgs f) {
       p.c[i] = i + 1 < n ? -1.f : 0.f;
     }
     pdl_enter();
-    for (int i = threadIdx.x; i < n; i += blockDim.x) p.r[i] = f.vhat[i * f.nk + k];
+    for (int i0 = threadIdx.x; i0 < n; i0 += kRound * blockDim.x) {
+      float2 v[kRound];
+#pragma unroll
+      for (int u = 0; u < kRound; ++u) {
+        const int i = i0 + u * blockDim.x;
+        v[u] = i < n ? f.vhat[i * f.nk + k] : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < kRound; ++u)
+        if (i0 + u * int(blockDim.x) < n) p.r[i0 + u * blockDim.x] = v[u];
+    }
     __syncthreads();
     const Rows<float2> x = pcr(p, q, n);
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
@@ -219,7 +246,14 @@ __global__ void __launch_bounds__(kPcrThreads) k_fp_tridiag(FPArgs f) {
     for (int i = threadIdx.x; i < n; i += blockDim.x) {
       const float *rr = f.r + (f.xs + 1 + i) * f.ny + f.c0;
       float acc = 0.f;
-      for (int c = 0; c < f.wc; ++c) acc = fmaf(__ldg(rr + c), ph[c], acc);
+      for (int c0 = 0; c0 < f.wc; c0 += kRound) {
+        float v[kRound];
+#pragma unroll
+        for (int u = 0; u < kRound; ++u) v[u] = c0 + u < f.wc ? __ldg(rr + c0 + u) : 0.f;
+#pragma unroll
+        for (int u = 0; u < kRound; ++u)
+          if (c0 + u < f.wc) acc = fmaf(v[u], ph[c0 + u], acc);
+      }
       p.r[i] = acc;
     }
     __syncthreads();
@@ -232,39 +266,81 @@ __global__ void __launch_bounds__(kPcrThreads) k_fp_tridiag(FPArgs f) {
 // interface columns (v_R by the inverse DFT of the solved spectra of row m,
 // v_S from the solved slot spectra), then u_G = S^-1 g, written to ug and to
 // e on the interface.  The corrections that u_G makes to the slab and the
-// slot are applied by the inverse-transform kernel.
+// slot are applied by the inverse-transform kernel.  The sine basis and
+// S^-1 are staged before the wait for the solves; a warp per column forms
+// its sums across its lanes.
 __global__ void __launch_bounds__(kSlotThreads) k_fp_interface(FPArgs f) {
   extern __shared__ float ss[];
   const int wc = f.wc, ms = f.ms, ny = f.ny, nk = f.nk;
   float *sphi = ss;                  // [wc][wc] sine basis
-  float *gv = sphi + wc * wc;        // [wc] interface right-hand side g
-  for (int t = threadIdx.x; t < wc * wc; t += blockDim.x) sphi[t] = __ldg(f.phi + t);
+  float *sinv = sphi + wc * wc;      // [wc][wc] S^-1
+  float *gv = sinv + wc * wc;        // [wc] interface right-hand side g
+  for (int t = threadIdx.x; t < wc * wc; t += blockDim.x) {
+    sphi[t] = __ldg(f.phi + t);
+    sinv[t] = __ldg(f.sinv + t);
+  }
+  if (threadIdx.x == 0) {   // the DFT weights into L2 while the solves finish
+    const unsigned bytes = unsigned(size_t(wc) * nk * sizeof(float2)) & ~15u;
+    if (bytes) asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(f.twc), "r"(bytes) : "memory");
+  }
   pdl_enter();
   __syncthreads();
   const int lane = threadIdx.x & 31, warp = threadIdx.x >> 5, nw = blockDim.x >> 5;
+  const float2 *vm = f.vhat + size_t(f.m - 1) * nk;
+  constexpr int U = 8;   // loads of a round in flight together
   for (int c = warp; c < wc; c += nw) {
-    const int j = f.c0 + c;
+    const float2 *tc = f.twc + size_t(c) * nk;
     float acc = 0.f;
-    for (int k = lane; k < nk; k += 32) {
-      const float2 v = __ldg(f.vhat + (f.m - 1) * nk + k);
-      const float2 t = conj2(__ldg(f.tw + ((k * j) & (ny - 1))));   // exp(+2 pi i k j / ny)
-      const float wgt = (k == 0 || k == nk - 1) ? 1.f : 2.f;
-      acc = fmaf(wgt, v.x * t.x - v.y * t.y, acc);
+    for (int k0 = lane; k0 < nk; k0 += 32 * U) {
+      float2 v[U], t[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const int k = k0 + 32 * u;
+        v[u] = k < nk ? vm[k] : make_float2(0.f, 0.f);
+        t[u] = k < nk ? __ldg(tc + k) : make_float2(0.f, 0.f);
+      }
+#pragma unroll
+      for (int u = 0; u < U; ++u) acc = fmaf(v[u].x, t[u].x, fmaf(-v[u].y, t[u].y, acc));
     }
+    for (int pm = lane; pm < wc; pm += 32) acc = fmaf(f.vs[pm * ms], sphi[pm * wc + c], acc);
 #pragma unroll
     for (int o = 16; o > 0; o >>= 1) acc += __shfl_xor_sync(0xffffffffu, acc, o);
-    if (lane == 0) {
-      float vsum = 0.f;
-      for (int pm = 0; pm < wc; ++pm) vsum = fmaf(__ldg(f.vs + pm * ms), sphi[pm * wc + c], vsum);
-      gv[c] = __ldg(f.r + f.xs * ny + j) + acc / float(ny) + vsum;
-    }
+    if (lane == 0) gv[c] = f.r[f.xs * ny + f.c0 + c] + acc;
   }
   __syncthreads();
+  float *ugs = gv + wc;              // [wc] u_G
   for (int c = threadIdx.x; c < wc; c += blockDim.x) {
     float acc = 0.f;
-    for (int qq = 0; qq < wc; ++qq) acc = fmaf(__ldg(f.sinv + c * wc + qq), gv[qq], acc);
+    for (int qq = 0; qq < wc; ++qq) acc = fmaf(sinv[c * wc + qq], gv[qq], acc);
+    ugs[c] = acc;
     f.ug[c] = acc;
-    f.e[f.xs * ny + f.c0 + c] = acc;
+    const int n = f.xs * ny + f.c0 + c;
+    f.pot[n] = pair_add_f(f.pot[n], acc);
+  }
+  __syncthreads();
+  // the spectra of u_G the inverse-transform kernel applies: fh[k] = sum_c
+  // u_G(c) exp(-2 pi i k (c0 + c) / ny) and sh[p] = sum_c phi[p][c] u_G(c)
+  // (from the weights above: exp(-2 pi i k j / ny) = conj(twc[c][k]) ny / w_k)
+  for (int k = threadIdx.x; k < nk; k += blockDim.x) {
+    float2 h = make_float2(0.f, 0.f);
+    for (int c0 = 0; c0 < wc; c0 += U) {
+      float2 w[U];
+#pragma unroll
+      for (int u = 0; u < U; ++u) w[u] = c0 + u < wc ? __ldg(f.twc + size_t(c0 + u) * nk + k) : make_float2(0.f, 0.f);
+#pragma unroll
+      for (int u = 0; u < U; ++u) {
+        const float g = c0 + u < wc ? ugs[c0 + u] : 0.f;
+        h.x = fmaf(g, w[u].x, h.x);
+        h.y = fmaf(-g, w[u].y, h.y);
+      }
+    }
+    const float sc = float(ny) / ((k == 0 || k == nk - 1) ? 1.f : 2.f);
+    f.fh[k] = make_float2(h.x * sc, h.y * sc);
+  }
+  for (int pm = threadIdx.x; pm < wc; pm += blockDim.x) {
+    float acc = 0.f;
+    for (int c = 0; c < wc; ++c) acc = fmaf(sphi[pm * wc + c], ugs[c], acc);
+    f.sh[pm] = acc;
   }
   if (threadIdx.x == 0) {
     f.ps->inner_iters += 1;
@@ -283,75 +359,103 @@ __global__ void __launch_bounds__(kFftThreads) k_fp_inverse(FPArgs f) {
   extern __shared__ float2 sm[];
   const int rows = (f.m + 1) / 2, wc = f.wc;
   if (int(blockIdx.x) >= rows) {
-    float *sphi = reinterpret_cast<float *>(sm), *ug = sphi + wc * wc, *sh = ug + wc;
+    float *sphi = reinterpret_cast<float *>(sm), *sh = sphi + wc * wc;
     for (int t = threadIdx.x; t < wc * wc; t += blockDim.x) sphi[t] = __ldg(f.phi + t);
     pdl_enter();
-    for (int c = threadIdx.x; c < wc; c += blockDim.x) ug[c] = f.ug[c];
-    __syncthreads();
-    for (int pm = threadIdx.x; pm < wc; pm += blockDim.x) {
-      float acc = 0.f;
-      for (int c = 0; c < wc; ++c) acc = fmaf(sphi[pm * wc + c], ug[c], acc);
-      sh[pm] = acc;
-    }
+    for (int pm = threadIdx.x; pm < wc; pm += blockDim.x) sh[pm] = f.sh[pm];
     __syncthreads();
     const int t = (blockIdx.x - rows) * blockDim.x + threadIdx.x;
     if (t < f.ms * wc) {
       const int row = t / wc, c = t - row * wc;
       float acc = 0.f;
-      for (int pm = 0; pm < wc; ++pm)
-        acc = fmaf(fmaf(__ldg(f.zs + pm * f.ms + row), sh[pm], __ldg(f.vs + pm * f.ms + row)),
-                   sphi[pm * wc + c], acc);
-      f.e[(f.xs + 1 + row) * f.ny + f.c0 + c] = acc;
+      for (int p0 = 0; p0 < wc; p0 += kRound) {   // a round's loads in flight together
+        float zv[kRound], vv[kRound];
+#pragma unroll
+        for (int u = 0; u < kRound; ++u) {
+          const int pm = p0 + u;
+          zv[u] = pm < wc ? __ldg(f.zs + pm * f.ms + row) : 0.f;
+          vv[u] = pm < wc ? f.vs[pm * f.ms + row] : 0.f;
+        }
+#pragma unroll
+        for (int u = 0; u < kRound; ++u)
+          if (p0 + u < wc) acc = fmaf(fmaf(zv[u], sh[p0 + u], vv[u]), sphi[(p0 + u) * wc + c], acc);
+      }
+      const int n = (f.xs + 1 + row) * f.ny + f.c0 + c;
+      f.pot[n] = pair_add_f(f.pot[n], acc);
     }
     return;
   }
   float2 *x = sm, *y = sm + f.ny, *tw = sm + 2 * f.ny;
-  float *ug = reinterpret_cast<float *>(tw + (f.ny >> 1));
   for (int t = threadIdx.x; t < (f.ny >> 1); t += blockDim.x) tw[t] = f.tw[t];
-  pdl_enter();
-  if (f.slot)
-    for (int c = threadIdx.x; c < wc; c += blockDim.x) ug[c] = f.ug[c];
-  __syncthreads();
   const int i0 = 2 * blockIdx.x + 1, i1 = i0 + 1;
   const bool two = i1 <= f.m;
-  const int half = f.ny >> 1;
-  for (int k = threadIdx.x; k < f.nk; k += blockDim.x) {
-    float2 a = f.vhat[(i0 - 1) * f.nk + k];
-    float2 b = two ? f.vhat[(i1 - 1) * f.nk + k] : make_float2(0.f, 0.f);
-    if (f.slot) {
-      float2 fh = make_float2(0.f, 0.f);
-      for (int c = 0; c < wc; ++c) {
-        const int t = (k * (f.c0 + c)) & (f.ny - 1);
-        // exp(-2 pi i t / ny); the table holds t < ny / 2, the rest is its negative
-        const float2 w = t < half ? tw[t] : make_float2(-tw[t - half].x, -tw[t - half].y);
-        fh.x = fmaf(ug[c], w.x, fh.x);
-        fh.y = fmaf(ug[c], w.y, fh.y);
-      }
-      const float za = f.z[(i0 - 1) * f.nk + k];
-      a = make_float2(fmaf(za, fh.x, a.x), fmaf(za, fh.y, a.y));
-      if (two) {
-        const float zb = f.z[(i1 - 1) * f.nk + k];
-        b = make_float2(fmaf(zb, fh.x, b.x), fmaf(zb, fh.y, b.y));
-      }
+  if (f.slot && threadIdx.x == 0) {
+    // this row pair's interface responses (a static table) into L2 meanwhile:
+    // the 16-byte aligned part of z[i0 - 1 .. i1 - 1][*]
+    const uintptr_t lo = (reinterpret_cast<uintptr_t>(f.z + size_t(i0 - 1) * f.nk) + 15) & ~uintptr_t(15);
+    const uintptr_t hi = reinterpret_cast<uintptr_t>(f.z + size_t(two ? i1 : i0) * f.nk) & ~uintptr_t(15);
+    if (hi > lo)
+      asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(lo), "r"(unsigned(hi - lo)) : "memory");
+  }
+  pdl_enter();
+  // the potential of this thread's output nodes, read early (its loads
+  // overlap the spectra's); the row pair has at most kMaxNy / blockDim.x
+  // nodes per thread and row
+  constexpr int kOut = kMaxNy / kFftThreads;
+  float2 p0[kOut], p1[kOut];
+#pragma unroll
+  for (int u = 0; u < kOut; ++u) {
+    const int j = threadIdx.x + u * kFftThreads;
+    p0[u] = j < f.ny ? f.pot[i0 * f.ny + j] : make_float2(0.f, 0.f);
+    p1[u] = j < f.ny && two ? f.pot[i1 * f.ny + j] : make_float2(0.f, 0.f);
+  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    // this pass's correction is in the potential once this kernel is done
+    f.ps->outer_iters += 1;
+    if (!f.slot) {
+      f.ps->inner_iters += 1;
+      f.ps->total_iters += 1;
     }
-    // Z[k] = a + i b, Z[ny - k] = conj(a) + i conj(b)
-    x[k] = make_float2(a.x - b.y, a.y + b.x);
-    if (k > 0 && k < f.ny - k) x[f.ny - k] = make_float2(a.x + b.y, -a.y + b.x);
+  }
+  for (int k0 = threadIdx.x; k0 < f.nk; k0 += kRound * blockDim.x) {
+    float2 av[kRound], bv[kRound], hv[kRound];
+    float za[kRound], zb[kRound];
+#pragma unroll
+    for (int u = 0; u < kRound; ++u) {   // a round's loads in flight together
+      const int k = k0 + u * blockDim.x;
+      const bool in = k < f.nk;
+      av[u] = in ? f.vhat[(i0 - 1) * f.nk + k] : make_float2(0.f, 0.f);
+      bv[u] = in && two ? f.vhat[(i1 - 1) * f.nk + k] : make_float2(0.f, 0.f);
+      hv[u] = in && f.slot ? f.fh[k] : make_float2(0.f, 0.f);
+      za[u] = in && f.slot ? __ldg(f.z + (i0 - 1) * f.nk + k) : 0.f;
+      zb[u] = in && f.slot && two ? __ldg(f.z + (i1 - 1) * f.nk + k) : 0.f;
+    }
+#pragma unroll
+    for (int u = 0; u < kRound; ++u) {
+      const int k = k0 + u * blockDim.x;
+      if (k >= f.nk) continue;
+      // the interface term z_k(i) fhat[k] (zero without a slot)
+      const float2 a = make_float2(fmaf(za[u], hv[u].x, av[u].x), fmaf(za[u], hv[u].y, av[u].y));
+      const float2 b = make_float2(fmaf(zb[u], hv[u].x, bv[u].x), fmaf(zb[u], hv[u].y, bv[u].y));
+      // Z[k] = a + i b, Z[ny - k] = conj(a) + i conj(b)
+      x[k] = make_float2(a.x - b.y, a.y + b.x);
+      if (k > 0 && k < f.ny - k) x[f.ny - k] = make_float2(a.x + b.y, -a.y + b.x);
+    }
   }
   __syncthreads();
   const float2 *Z = fft_smem(x, y, tw, f.ny, f.logny, true);
   const float s = 1.f / float(f.ny);
-  for (int j = threadIdx.x; j < f.ny; j += blockDim.x) {
-    f.e[i0 * f.ny + j] = Z[j].x * s;
-    if (two) f.e[i1 * f.ny + j] = Z[j].y * s;
-  }
-  if (!f.slot && blockIdx.x == 0 && threadIdx.x == 0) {
-    f.ps->inner_iters += 1;
-    f.ps->total_iters += 1;
+#pragma unroll
+  for (int u = 0; u < kOut; ++u) {
+    const int j = threadIdx.x + u * kFftThreads;
+    if (j < f.ny) {
+      f.pot[i0 * f.ny + j] = pair_add_f(p0[u], Z[j].x * s);
+      if (two) f.pot[i1 * f.ny + j] = pair_add_f(p1[u], Z[j].y * s);
+    }
   }
 }
 
-FPArgs fp_args(pic_ctx *c, const float *r, float *e, PoissonState *ps) {
+FPArgs fp_args(pic_ctx *c, const float *r, float2 *pot, PoissonState *ps) {
   const FastPoisson &p = c->fp;
   FPArgs a;
   a.ny = p.ny;
@@ -373,8 +477,11 @@ FPArgs fp_args(pic_ctx *c, const float *r, float *e, PoissonState *ps) {
   a.sb = p.sb;
   a.zs = p.zs;
   a.sinv = p.sinv;
+  a.twc = p.twc;
+  a.fh = p.fh;
+  a.sh = p.sh;
   a.r = r;
-  a.e = e;
+  a.pot = pot;
   a.ps = ps;
   return a;
 }
@@ -388,7 +495,7 @@ size_t rows_bytes(int n, size_t tsize) { return 2 * (size_t(3 * n + (n & 1)) * 4
 size_t tridiag_smem_bytes(int m, int ms, int wc) {
   return std::max(rows_bytes(m, sizeof(float2)), rows_bytes(ms, 4) + size_t(wc) * 4);
 }
-size_t slot_smem_bytes(int wc) { return (size_t(wc) * wc + size_t(wc)) * 4; }
+size_t slot_smem_bytes(int wc) { return (2 * size_t(wc) * wc + 2 * size_t(wc)) * 4; }
 
 // Thomas factors of tridiag(-1, d, -1) of size n: w_1 = 1/d, w_i = 1/(d - w_{i-1})
 void thomas_factors(double d, int n, double *w) {
@@ -572,14 +679,27 @@ cudaError_t fast_poisson_setup(pic_ctx *c) {
     }
     if (!invert(S, wc, Sinv)) return cudaSuccess;   // cannot happen for an SPD system; keep the V-cycle
     std::vector<float> sinvf(Sinv.begin(), Sinv.end());
+    // inverse-DFT weights of the interface columns: w_k = 1 for k = 0 and
+    // k = ny / 2, 2 between (a real row's spectrum holds k <= ny / 2)
+    std::vector<float2> twc(size_t(wc) * nk);
+    for (int cc = 0; cc < wc; ++cc)
+      for (int k = 0; k < nk; ++k) {
+        const double wgt = (k == 0 || k == nk - 1) ? 1.0 : 2.0;
+        const double ang = 2 * pi * double((int64_t(k) * (c0 + cc)) % ny) / ny;
+        twc[size_t(cc) * nk + k] = make_float2(float(wgt * std::cos(ang) / ny), float(wgt * std::sin(ang) / ny));
+      }
     p.z = upload(c, z);
     p.phi = upload(c, phif);
     p.sb = upload(c, sbf);
     p.zs = upload(c, zsf);
     p.sinv = upload(c, sinvf);
+    p.twc = upload(c, twc);
     p.vs = static_cast<float *>(dev_alloc(c, size_t(wc) * ms * sizeof(float)));
     p.ug = static_cast<float *>(dev_alloc(c, size_t(wc) * sizeof(float)));
-    if (!p.z || !p.phi || !p.sb || !p.zs || !p.sinv || !p.vs || !p.ug) return cudaErrorMemoryAllocation;
+    p.fh = static_cast<float2 *>(dev_alloc(c, size_t(nk) * sizeof(float2)));
+    p.sh = static_cast<float *>(dev_alloc(c, size_t(wc) * sizeof(float)));
+    if (!p.z || !p.phi || !p.sb || !p.zs || !p.sinv || !p.twc || !p.vs || !p.ug || !p.fh || !p.sh)
+      return cudaErrorMemoryAllocation;
   }
   p.ny = ny;
   p.nk = nk;
@@ -602,8 +722,8 @@ cudaError_t fast_poisson_setup(pic_ctx *c) {
   return cudaGetLastError();
 }
 
-void fast_poisson_launch(pic_ctx *c, const float *r, float *e, PoissonState *ps) {
-  const FPArgs a = fp_args(c, r, e, ps);
+void fast_poisson_launch(pic_ctx *c, const float *r, float2 *pot, PoissonState *ps) {
+  const FPArgs a = fp_args(c, r, pot, ps);
   const int rows = (a.m + 1) / 2;
   launch(k_fp_forward, rows, kFftThreads, fft_smem_bytes(a.ny, a.wc), c->stream, a);
   launch(k_fp_tridiag, a.nk + (a.slot ? a.wc : 0), kPcrThreads,

@@ -198,6 +198,9 @@ struct FastPoisson {
   float *z = nullptr;              // [m][nk] column m of the inverse tridiagonal (interface response)
   float2 *vhat = nullptr;          // [m][nk] spectra of the rows
   float *phi = nullptr;            // [wc][wc] orthonormal sine basis of the slot, [mode][column]
+  float2 *twc = nullptr;          // [wc][nk] inverse-DFT weights of the interface columns
+  float2 *fh = nullptr;           // [nk] spectrum of the interface values
+  float *sh = nullptr;            // [wc] sine spectrum of the interface values
   float *sb = nullptr;             // [wc] diagonal of each slot sine mode's system
   float *zs = nullptr;             // [wc][ms] slot responses to a unit first-row value
   float *sinv = nullptr;           // [wc][wc] inverse of the interface Schur complement
@@ -364,8 +367,8 @@ cudaError_t poisson_setup(pic_ctx *c);
 // (leaves c->fp.enabled = 0 otherwise) and the launches that turn the FP32
 // residual r into the correction e.
 cudaError_t fast_poisson_setup(pic_ctx *c);
-void fast_poisson_launch(pic_ctx *c, const float *r, float *e, PoissonState *ps);
-cudaError_t launch_rho(pic_ctx *c, int advance_step);
+void fast_poisson_launch(pic_ctx *c, const float *r, float2 *pot, PoissonState *ps);
+cudaError_t launch_rho(pic_ctx *c, int advance_step, int init_solve = 0);
 pic_status poisson_solve(pic_ctx *c, bool zero_guess);
 cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNode_t> &deps);
 int64_t poisson_kernel_count(pic_ctx *c, int64_t S, int64_t O, int64_t I);

@@ -17,7 +17,8 @@
 //                                    where the geometry allows it, else PCG
 //                                    with a symmetric V-cycle preconditioner,
 //                                    inner products accumulated in FP64)
-//            phi += e               (double-float)
+//            phi += e               (double-float; the direct solve's
+//                                    kernels add their parts of e in place)
 //
 // V-cycle: factor-2 coarsening with injected Dirichlet masks; Galerkin coarse
 // operators A_c = R A P (9-point, built once on the host) with bilinear
@@ -228,18 +229,23 @@ __device__ void sum_published(const float *part, int nb, float (&c)[NC]) {
   __threadfence();
 #pragma unroll
   for (int q = 0; q < NC; ++q) c[q] = 0.f;
-  for (int b = threadIdx.x; b < nb; b += blockDim.x) {
-    float x[NC];
+  for (int b0 = threadIdx.x; b0 < nb; b0 += 2 * blockDim.x) {   // both loads of a round in flight
+    const int b1 = b0 + blockDim.x;
+    float x[2][NC];
 #pragma unroll
-    for (int q = 0; q < NC; ++q) x[q] = __ldcg(part + b * NC + q);
+    for (int q = 0; q < NC; ++q) {
+      x[0][q] = __ldcg(part + b0 * NC + q);
+      x[1][q] = b1 < nb ? __ldcg(part + b1 * NC + q) : 0.f;
+    }
 #pragma unroll
-    for (int q = 0; q < NC; ++q) c[q] += x[q];
+    for (int q = 0; q < NC; ++q) c[q] += x[0][q] + x[1][q];
   }
   block_tree<NC>(c);
 }
 
 // a class triple (mid, big, tiny) of sq_add as a double
 __device__ __forceinline__ double sq_join(const float *c) {
+  if (c[1] == 0.f && c[2] == 0.f) return double(c[0]);
   return double(c[0]) + double(c[1]) * 0x1p160 + double(c[2]) * 0x1p-160;
 }
 
@@ -288,6 +294,7 @@ struct FineArgs {
   int maxit;
   int32_t *step;
   int advance_step;
+  int init_solve;            // the density kernel also opens the next solve (resets its counters)
   float2 *E;
   double *fe;
   uint32_t *status;
@@ -312,6 +319,7 @@ constexpr int kVB = 4;
 
 // acc -> rho (double-float); clears acc.  A doubly periodic box also forms
 // the mean of rho, which the solve removes.
+template <bool SING>
 __global__ void k_rho(FineArgs a) {
   pdl_enter();
   const Geom g = a.g;
@@ -349,16 +357,22 @@ __global__ void k_rho(FineArgs a) {
         }
       }
       a.rho[n] = rho;
-      if (a.singular) sum = pair_add(sum, rho);   // every node is free
+      if (SING) sum = pair_add(sum, rho);   // every node is free
     }
   }
-  if (a.singular) {
+  if (SING) {
     double v[1] = {pair_join(sum)};
     if (grid_sum<1>(v, a.part, a.ticket) && threadIdx.x == 0) a.ps->bmean = v[0] / double(nn);
   } else if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.ps->bmean = 0.0;
   }
-  if (a.advance_step && blockIdx.x == 0 && threadIdx.x == 0) *a.step += 1;
+  if (blockIdx.x == 0 && threadIdx.x == 0) {
+    if (a.advance_step) *a.step += 1;
+    if (a.init_solve) {
+      a.ps->total_iters = 0;
+      a.ps->outer_iters = 0;
+    }
+  }
 }
 
 // phi <- Dirichlet values, zero on free nodes (cold start)
@@ -446,14 +460,15 @@ __device__ __forceinline__ float resid_node(float2 rho, const float2 (&ph)[5]) {
 // the step's field, and decides whether the solve goes on.  A first pass
 // known not to be the last (the direct solve's, which always corrects once)
 // skips all that and leaves only its ||b||^2 block sums for the next pass.
-template <bool CHECK>
+template <bool CHECK, bool SING>
 __global__ void k_resid(FineArgs a) {
   pdl_enter();
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
   const bool first = a.ps->outer_iters == 0;
   const bool bb_here = first;
-  const float2 bm = a.singular ? pair_split(a.ps->bmean) : make_float2(0.f, 0.f);
+  float2 bm = make_float2(0.f, 0.f);
+  if (SING) bm = pair_split(a.ps->bmean);
   SqSum q3[3] = {};
   VEC_BATCHES(base, nn) {
     float2 rh[kVB], ph[kVB][5];
@@ -474,7 +489,7 @@ __global__ void k_resid(FineArgs a) {
     VEC_NODES(k, n, base, nn) {
       float r32 = 0.f;
       if (fl[k] & kFree) {
-        const float2 rho = a.singular ? pair_sub(rh[k], bm) : rh[k];
+        const float2 rho = SING ? pair_sub(rh[k], bm) : rh[k];
         r32 = resid_node(rho, ph[k]);
         if (CHECK) sq_add(q3[0], r32);
         if (bb_here) sq_add(q3[1], rho.x + (rho.y + lf[k]));
@@ -517,7 +532,11 @@ __global__ void k_resid(FineArgs a) {
     if (first) ps->bb = sq_join(c + 3);
     if (bb_parts) ps->bb = sq_join(cb);
     const double bb = ps->bb;
-    ps->rel = sqrt_ratio(rr, bb > 0 ? bb : 1.0);
+    const float bbf = float(bb);
+    if (c[1] == 0.f && c[2] == 0.f && bbf > 1e-30f && bbf < 1e30f)
+      ps->rel = double(sqrtf(c[0] / bbf));   // both norms in FP32 range
+    else
+      ps->rel = sqrt_ratio(rr, bb > 0 ? bb : 1.0);
     const bool ok = ps->rel <= a.rtol || rr == 0.0;
     const bool give_up = !ok && ps->outer_iters >= kMaxOuter;
     if (give_up) atomicOr(a.status, PIC_ST_NOCONV);
@@ -1384,6 +1403,12 @@ __global__ void __launch_bounds__(kCoarseThreads) k_coarse(MGArgs a) {
 }
 
 // --------------------------------------------------------------------------
+// the residual kernel for the box: with or without the mean of rho removed
+template <bool CHECK>
+void (*resid_kernel(const pic_ctx *c))(FineArgs) {
+  return c->singular ? k_resid<CHECK, true> : k_resid<CHECK, false>;
+}
+
 FineArgs fine_args(pic_ctx *c) {
   FineArgs a;
   a.g = c->g;
@@ -1419,6 +1444,7 @@ FineArgs fine_args(pic_ctx *c) {
   a.maxit = c->cfg.poisson_maxit;
   a.step = c->d_step;
   a.advance_step = 0;
+  a.init_solve = 0;
   a.E = c->d_E;
   a.fe = c->d_fe;
   a.status = c->d_status;
@@ -1777,10 +1803,12 @@ cudaError_t poisson_setup(pic_ctx *c) {
   return cudaGetLastError();
 }
 
-cudaError_t launch_rho(pic_ctx *c, int advance_step) {
+cudaError_t launch_rho(pic_ctx *c, int advance_step, int init_solve) {
   FineArgs a = fine_args(c);
   a.advance_step = advance_step;
-  launch(k_rho, c->red.nblocks, kThreads, 0, c->stream, a);
+  a.init_solve = init_solve;
+  if (c->singular) launch(k_rho<true>, c->red.nblocks, kThreads, 0, c->stream, a);
+  else launch(k_rho<false>, c->red.nblocks, kThreads, 0, c->stream, a);
   return cudaGetLastError();
 }
 
@@ -1806,15 +1834,13 @@ pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
   c->launches += 1;
   const int batch = 4;
   for (;;) {
-    launch(k_resid<true>, nb, kThreads, 0, c->stream, a);
+    launch(resid_kernel<true>(c), nb, kThreads, 0, c->stream, a);
     c->launches += 1;
     cudaMemcpyAsync(c->h_ps, c->d_ps, sizeof(PoissonState), cudaMemcpyDeviceToHost, c->stream);
     if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
     if (!c->h_ps->go) break;
-    if (c->fp.enabled) {
-      fast_poisson_launch(c, c->d_r32, c->d_e, c->d_ps);
-      launch(k_correct, nb, kThreads, 0, c->stream, a);
-      c->launches += 1;
+    if (c->fp.enabled) {   // the direct solve adds its correction to phi itself
+      fast_poisson_launch(c, c->d_r32, c->d_phi, c->d_ps);
       continue;
     }
     launch_vcycle(c, m);
@@ -1894,9 +1920,8 @@ cudaError_t add_cond(cudaGraph_t g, const std::vector<cudaGraphNode_t> &deps,
 // With the direct inner solve, whose one pass nearly always suffices, the
 // first pass runs unconditionally (a potential that already meets the
 // tolerance takes one correction it does not need) and only further passes
-// are conditional:
-//   [phi reset] -> init -> resid -> solve -> correct -> resid ->
-//     WHILE(go) { solve -> correct -> resid }
+// are conditional (the direct solve adds its correction to phi itself):
+//   [phi reset] -> init -> resid -> solve -> resid -> WHILE(go) { solve -> resid }
 cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNode_t> &deps) {
   cudaStream_t s = c->stream;
   FineArgs a = fine_args(c);
@@ -1920,14 +1945,15 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   CK(cap_begin(s, top, deps));
   if (c->cfg.warm_start == 0) launch(k_phi_reset, nb, kThreads, 0, s, a);
   if (c->cfg.warm_start == 2) launch(k_extrapolate, nb, kThreads, 0, s, a);
-  launch(k_outer_init, 1, 1, 0, s, c->d_ps);
+  // (with the previous step's potential as the guess the density kernel just
+  // before opened the solve)
+  if (c->cfg.warm_start != 1) launch(k_outer_init, 1, 1, 0, s, c->d_ps);
   if (direct) {
     // the first pass always corrects: it leaves ||b||^2 to the second
-    launch(k_resid<false>, nb, kThreads, 0, s, a);
-    fast_poisson_launch(c, c->d_r32, c->d_e, c->d_ps);
-    launch(k_correct, nb, kThreads, 0, s, a);
+    launch(resid_kernel<false>(c), nb, kThreads, 0, s, a);
+    fast_poisson_launch(c, c->d_r32, c->d_phi, c->d_ps);
     a.bb_from_part = 1;
-    launch(k_resid<true>, nb, kThreads, 0, s, a);
+    launch(resid_kernel<true>(c), nb, kThreads, 0, s, a);
   }
   CK(cap_end(s, deps));
   cudaGraphNode_t n_outer, n_if_outer, n_inner, n_if_inner;
@@ -1936,15 +1962,14 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   std::vector<cudaGraphNode_t> d;
   if (direct) {
     CK(cap_begin(s, b_outer, {}));
-    fast_poisson_launch(c, c->d_r32, c->d_e, c->d_ps);
-    launch(k_correct, nb, kThreads, 0, s, a);
-    launch(k_resid<true>, nb, kThreads, 0, s, a);
+    fast_poisson_launch(c, c->d_r32, c->d_phi, c->d_ps);
+    launch(resid_kernel<true>(c), nb, kThreads, 0, s, a);
     CK(cap_end(s, d));
     deps.assign(1, n_outer);
     return cudaGetLastError();
   }
   CK(cap_begin(s, b_outer, {}));
-  launch(k_resid<true>, nb, kThreads, 0, s, a);
+  launch(resid_kernel<true>(c), nb, kThreads, 0, s, a);
   CK(cap_end(s, d));
   CK(add_cond(b_outer, d, h[1], cudaGraphCondTypeIf, &n_if_outer, &b_if_outer));
   CK(cap_begin(s, b_if_outer, {}));
@@ -1972,9 +1997,10 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
 // Kernels that S solves with O outer passes and I inner iterations in all
 // launched (graph mode; every outer pass takes at least one inner iteration).
 int64_t poisson_kernel_count(pic_ctx *c, int64_t S, int64_t O, int64_t I) {
-  const int64_t per_solve = 2 + (c->cfg.warm_start != 1 ? 1 : 0);   // init, final resid, [guess]
-  if (c->fp.enabled)   // per pass: resid, direct solve, correct
-    return S * per_solve + O * (c->fp.kernels + 2);
+  // final resid, and unless the density kernel opens the solve: guess and init
+  const int64_t per_solve = 1 + (c->cfg.warm_start != 1 ? 2 : 0);
+  if (c->fp.enabled)   // per pass: resid, direct solve (which corrects phi)
+    return S * per_solve + O * (c->fp.kernels + 1);
   // a V-cycle with w = A z and the inner products: fused into its last kernel unless lc = 0
   const int64_t vc = 2 * c->lc + 1 + (c->lc == 0 ? 1 : 0);
   // per pass: resid, V-cycle, correct; per iteration: cg; per non-final iteration: V-cycle
