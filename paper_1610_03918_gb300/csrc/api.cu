@@ -270,7 +270,8 @@ pic_status step_kernels(pic_ctx *c, bool sorting, cudaEvent_t *ev) {
 
 // Appends one step of context c to graph g after the nodes in `deps`:
 // [sort] -> particle kernel -> rho -> the Poisson solve as nested conditional
-// nodes (its residual passes write the field).  With `events`, external event
+// nodes (its residual passes write the field; with the direct solve and the
+// previous potential as the guess its first pass forms rho).  With `events`, external event
 // nodes recording c->tev separate the phases (PIC_DIAG_TIMING); the launch
 // points them at a slot of the event pool.  On return `deps` holds the step's last node(s).
 // Kernel arguments are fixed device pointers; the particle buffers are reached
@@ -290,7 +291,7 @@ cudaError_t capture_step(pic_ctx *c, cudaGraph_t g, std::vector<cudaGraphNode_t>
     rec(1);
     launch_particles(c, 0, 1.f, nullptr);
     rec(2);
-    launch_rho(c, 1, c->cfg.warm_start == 1);   // opens the solve captured next
+    if (!rho_in_solve(c)) launch_rho(c, 1, c->cfg.warm_start == 1);   // opens the solve captured next
     rec(3);
     e = note(capture_leaves(c->stream, deps), "capture: particle phase");
   }
@@ -851,7 +852,8 @@ pic_status pic_step(pic_ctx *c, int32_t nsteps) {
                    "step graph event") != cudaSuccess)
             return PIC_ECUDA;
       }
-      c->launches += (sorting ? 4 : 0) + 2;   // the solve's kernels are counted from its totals
+      // particle kernel, [sort], [density]; the solve's kernels are counted from its totals
+      c->launches += (sorting ? 4 : 0) + (rho_in_solve(c) ? 1 : 2);
       if (note(cudaGraphLaunch(c->gexec[ws][ev], c->stream), "step graph launch") != cudaSuccess)
         return PIC_ECUDA;
       if (sorting) {

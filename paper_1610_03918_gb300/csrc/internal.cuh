@@ -369,6 +369,9 @@ cudaError_t poisson_setup(pic_ctx *c);
 cudaError_t fast_poisson_setup(pic_ctx *c);
 void fast_poisson_launch(pic_ctx *c, const float *r, float2 *pot, PoissonState *ps);
 cudaError_t launch_rho(pic_ctx *c, int advance_step, int init_solve = 0);
+// In a captured step with the direct solve and the previous potential as the
+// guess, the solve's first residual pass forms rho itself (no density kernel).
+bool rho_in_solve(const pic_ctx *c);
 pic_status poisson_solve(pic_ctx *c, bool zero_guess);
 cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNode_t> &deps);
 int64_t poisson_kernel_count(pic_ctx *c, int64_t S, int64_t O, int64_t I);

@@ -317,6 +317,42 @@ constexpr int kVB = 4;
   _Pragma("unroll") for (int k = 0; k < kVB; ++k) \
     if (const int n = (base) + k * int(blockDim.x); n < (N))
 
+// rho at node n (double-float) from the species' deposit sums a0, a1, the
+// external charge rx and, on the bottom row, the surface charge
+__device__ __forceinline__ float2 node_rho(const FineArgs &a, const Geom &g, int n, unsigned long long a0,
+                                           unsigned long long a1, float2 rx) {
+  // two's-complement sums: a node's total can be slightly negative (CIC
+  // shares of -1 unit from the fixed-point rounding)
+  float2 rho = pair_add(pair_mul(a.qw[0], pair_from_ll((long long)a0)),
+                        pair_mul(a.qw[1], pair_from_ll((long long)a1)));
+  rho = pair_add(rx, rho);
+  if (a.surface && !g.px) {
+    const int i = fdiv(n, g.dnyn), j = n - i * g.nyn;
+    if (i == g.nx - 1) {
+      // half of bottom face k's charge on nodes (nx-1, k) and (nx-1, k+1)
+      // (a.sw holds q_s w_s / 2)
+      int jm = j - 1;
+      if (g.py && jm < 0) jm += g.ny;
+      if (j < g.ny)
+        rho = pair_add(rho, pair_add(pair_mul(a.sw[0], pair_from_ll((long long)a.bottom[j])),
+                                     pair_mul(a.sw[1], pair_from_ll((long long)a.bottom[g.ny + j]))));
+      if (jm >= 0 && jm < g.ny)
+        rho = pair_add(rho, pair_add(pair_mul(a.sw[0], pair_from_ll((long long)a.bottom[jm])),
+                                     pair_mul(a.sw[1], pair_from_ll((long long)a.bottom[g.ny + jm]))));
+    }
+  }
+  return rho;
+}
+
+// What the density kernel does once per launch (block 0, thread 0).
+__device__ __forceinline__ void rho_bookkeeping(const FineArgs &a) {
+  if (a.advance_step) *a.step += 1;
+  if (a.init_solve) {
+    a.ps->total_iters = 0;
+    a.ps->outer_iters = 0;
+  }
+}
+
 // acc -> rho (double-float); clears acc.  A doubly periodic box also forms
 // the mean of rho, which the solve removes.
 template <bool SING>
@@ -336,26 +372,7 @@ __global__ void k_rho(FineArgs a) {
     VEC_NODES(k, n, base, nn) {
       a.acc[n] = 0ull;
       a.acc[nn + n] = 0ull;
-      // two's-complement sums: a node's total can be slightly negative (CIC
-      // shares of -1 unit from the fixed-point rounding)
-      float2 rho = pair_add(pair_mul(a.qw[0], pair_from_ll((long long)a0[k])),
-                            pair_mul(a.qw[1], pair_from_ll((long long)a1[k])));
-      rho = pair_add(rx[k], rho);
-      if (a.surface && !g.px) {
-        const int i = fdiv(n, g.dnyn), j = n - i * g.nyn;
-        if (i == g.nx - 1) {
-          // half of bottom face k's charge on nodes (nx-1, k) and (nx-1, k+1)
-          // (a.sw holds q_s w_s / 2)
-          int jm = j - 1;
-          if (g.py && jm < 0) jm += g.ny;
-          if (j < g.ny)
-            rho = pair_add(rho, pair_add(pair_mul(a.sw[0], pair_from_ll((long long)a.bottom[j])),
-                                         pair_mul(a.sw[1], pair_from_ll((long long)a.bottom[g.ny + j]))));
-          if (jm >= 0 && jm < g.ny)
-            rho = pair_add(rho, pair_add(pair_mul(a.sw[0], pair_from_ll((long long)a.bottom[jm])),
-                                         pair_mul(a.sw[1], pair_from_ll((long long)a.bottom[g.ny + jm]))));
-        }
-      }
+      const float2 rho = node_rho(a, g, n, a0[k], a1[k], rx[k]);
       a.rho[n] = rho;
       if (SING) sum = pair_add(sum, rho);   // every node is free
     }
@@ -366,13 +383,7 @@ __global__ void k_rho(FineArgs a) {
   } else if (blockIdx.x == 0 && threadIdx.x == 0) {
     a.ps->bmean = 0.0;
   }
-  if (blockIdx.x == 0 && threadIdx.x == 0) {
-    if (a.advance_step) *a.step += 1;
-    if (a.init_solve) {
-      a.ps->total_iters = 0;
-      a.ps->outer_iters = 0;
-    }
-  }
+  if (blockIdx.x == 0 && threadIdx.x == 0) rho_bookkeeping(a);
 }
 
 // phi <- Dirichlet values, zero on free nodes (cold start)
@@ -460,12 +471,18 @@ __device__ __forceinline__ float resid_node(float2 rho, const float2 (&ph)[5]) {
 // the step's field, and decides whether the solve goes on.  A first pass
 // known not to be the last (the direct solve's, which always corrects once)
 // skips all that and leaves only its ||b||^2 block sums for the next pass.
-template <bool CHECK, bool SING>
+template <bool CHECK, bool SING, bool FROM_ACC = false>
 __global__ void k_resid(FineArgs a) {
+  static_assert(!FROM_ACC || (!CHECK && !SING), "rho is formed only by a first pass without a check");
   pdl_enter();
   const Geom g = a.g;
   const int nn = g.nxn * g.nyn;
-  const bool first = a.ps->outer_iters == 0;
+  // FROM_ACC: this kernel is the density kernel too, and so the solve's first pass
+  const bool first = FROM_ACC || a.ps->outer_iters == 0;
+  if (FROM_ACC && blockIdx.x == 0 && threadIdx.x == 0) {
+    a.ps->bmean = 0.0;
+    rho_bookkeeping(a);
+  }
   const bool bb_here = first;
   float2 bm = make_float2(0.f, 0.f);
   if (SING) bm = pair_split(a.ps->bmean);
@@ -474,11 +491,18 @@ __global__ void k_resid(FineArgs a) {
     float2 rh[kVB], ph[kVB][5];
     float lf[kVB];
     uint8_t fl[kVB];
+    unsigned long long a0[FROM_ACC ? kVB : 1], a1[FROM_ACC ? kVB : 1];
     VEC_NODES(k, n, base, nn) {
       int xm, xp, ym, yp;
       nbr_index(g, n, xm, xp, ym, yp);
       fl[k] = a.flags[n];
-      rh[k] = a.rho[n];
+      if (FROM_ACC) {
+        a0[k] = a.acc[n];
+        a1[k] = a.acc[nn + n];
+        rh[k] = a.rho_ext[n];
+      } else {
+        rh[k] = a.rho[n];
+      }
       lf[k] = bb_here ? a.lift[n] : 0.f;
       ph[k][0] = a.phi[n];
       ph[k][1] = a.phi[xm];
@@ -487,6 +511,12 @@ __global__ void k_resid(FineArgs a) {
       ph[k][4] = a.phi[yp];
     }
     VEC_NODES(k, n, base, nn) {
+      if (FROM_ACC) {
+        a.acc[n] = 0ull;
+        a.acc[nn + n] = 0ull;
+        rh[k] = node_rho(a, g, n, a0[k], a1[k], rh[k]);
+        a.rho[n] = rh[k];
+      }
       float r32 = 0.f;
       if (fl[k] & kFree) {
         const float2 rho = SING ? pair_sub(rh[k], bm) : rh[k];
@@ -1803,6 +1833,10 @@ cudaError_t poisson_setup(pic_ctx *c) {
   return cudaGetLastError();
 }
 
+bool rho_in_solve(const pic_ctx *c) {
+  return c->fp.enabled && c->cfg.warm_start == 1 && !c->singular;
+}
+
 cudaError_t launch_rho(pic_ctx *c, int advance_step, int init_solve) {
   FineArgs a = fine_args(c);
   a.advance_step = advance_step;
@@ -1950,7 +1984,14 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   if (c->cfg.warm_start != 1) launch(k_outer_init, 1, 1, 0, s, c->d_ps);
   if (direct) {
     // the first pass always corrects: it leaves ||b||^2 to the second
-    launch(resid_kernel<false>(c), nb, kThreads, 0, s, a);
+    if (rho_in_solve(c)) {   // and forms rho, opening the step's solve
+      FineArgs r = a;
+      r.advance_step = 1;
+      r.init_solve = 1;
+      launch(k_resid<false, false, true>, nb, kThreads, 0, s, r);
+    } else {
+      launch(resid_kernel<false>(c), nb, kThreads, 0, s, a);
+    }
     fast_poisson_launch(c, c->d_r32, c->d_phi, c->d_ps);
     a.bb_from_part = 1;
     launch(resid_kernel<true>(c), nb, kThreads, 0, s, a);
