@@ -151,6 +151,7 @@ struct PoissonState {
   double rz, rz_old, rr, rr0;       // inner PCG: gamma = <r, z>, its previous value, ||r||^2
   double delta;                      // <z, A z>
   double alpha, beta;
+  double alpha_next, beta_next;      // the coefficients of the next CG update
   double zmean;
   double tol_in;      // inner target relative to the inner initial residual
   int32_t inner_done, outer_done;

@@ -178,6 +178,22 @@ __device__ bool grid_sum(double (&v)[NV], double *part, unsigned int *ticket) {
   return grid_sum_blocks<NV>(v, part, ticket);
 }
 
+// The same from FP32 per-thread partials: summed over each warp in FP32 (a
+// tree of five roundings), then in FP64 from the warps' sums on, so FP64
+// arithmetic runs once per warp rather than in every thread.
+template <int NV>
+__device__ bool grid_sum_f(const float (&s)[NV], double (&v)[NV], double *part, unsigned int *ticket) {
+#pragma unroll
+  for (int k = 0; k < NV; ++k) {
+    float t = s[k];
+#pragma unroll
+    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
+    v[k] = 0.0;
+    if ((threadIdx.x & 31) == 0) v[k] = double(t);
+  }
+  return grid_sum_blocks<NV>(v, part, ticket);
+}
+
 // FP32 tree sums of the sq_add classes.  Each block reduces its NC class
 // sums by shuffles within the warps and then over the warps (block_tree,
 // result in thread 0); the last block to arrive adds the blocks' partials
@@ -609,6 +625,14 @@ __device__ __forceinline__ void store_gamma_delta(PoissonState *ps, const double
   ps->zmean = zm;
   ps->rz = v[0] - zm * v[2];
   ps->delta = v[3] - zm * v[4];
+  // the next CG step's coefficients (single-reduction form): once here
+  // rather than in every thread of the update kernel
+  const double gam = ps->rz;
+  const bool first = ps->inner_iters == 0;
+  const double beta = first ? 0.0 : gam / ps->rz_old;
+  const double alpha = first ? gam / ps->delta : gam / (ps->delta - beta * gam / ps->alpha);
+  ps->alpha_next = alpha;
+  ps->beta_next = beta;
 }
 
 // w = A z and the scalars of store_gamma_delta, after a V-cycle that ran
@@ -644,8 +668,8 @@ __global__ void k_zw(FineArgs a) {
       s[4] += w;
     }
   }
-  double v[5] = {s[0], s[1], s[2], s[3], s[4]};
-  if (grid_sum<5>(v, a.part, a.ticket) && threadIdx.x == 0) store_gamma_delta(a.ps, v, a.singular, nn);
+  double v[5];
+  if (grid_sum_f<5>(s, v, a.part, a.ticket) && threadIdx.x == 0) store_gamma_delta(a.ps, v, a.singular, nn);
 }
 
 // One step of the preconditioned conjugate gradient in its single-reduction
@@ -662,11 +686,7 @@ __global__ void k_cg(FineArgs a) {
   PoissonState *ps = a.ps;
   if (ps->inner_done) return;
   const int nn = a.g.nxn * a.g.nyn;
-  const bool first = ps->inner_iters == 0;
-  const double gam = ps->rz;
-  const double beta = first ? 0.0 : gam / ps->rz_old;
-  const double alpha = first ? gam / ps->delta : gam / (ps->delta - beta * gam / ps->alpha);
-  const float fb = float(beta), fa = float(alpha), zm = float(ps->zmean);
+  const float fb = float(ps->beta_next), fa = float(ps->alpha_next), zm = float(ps->zmean);
   float rr = 0.f;
   VEC_BATCHES(base, nn) {
     float z[kVB], w[kVB], p[kVB], q[kVB], e[kVB], r[kVB];
@@ -689,17 +709,18 @@ __global__ void k_cg(FineArgs a) {
       rr = fmaf(rn, rn, rr);
     }
   }
-  double v[1] = {rr};
-  if (grid_sum<1>(v, a.part, a.ticket) && threadIdx.x == 0) {
-    ps->rz_old = gam;
-    ps->alpha = alpha;
-    ps->beta = beta;
+  const float rs[1] = {rr};
+  double v[1];
+  if (grid_sum_f<1>(rs, v, a.part, a.ticket) && threadIdx.x == 0) {
+    ps->rz_old = ps->rz;
+    ps->alpha = ps->alpha_next;
+    ps->beta = ps->beta_next;
     ps->rr = v[0];
     ps->inner_iters += 1;
     ps->total_iters += 1;
     const double tol = ps->tol_in;
-    const bool done =
-        sqrt(v[0]) <= tol * sqrt(ps->rr0) || ps->inner_iters >= a.maxit || !(v[0] == v[0]);
+    // ||r|| <= tol ||r_0||, compared as squares (no square roots)
+    const bool done = v[0] <= tol * tol * ps->rr0 || ps->inner_iters >= a.maxit || !(v[0] == v[0]);
     if (done) ps->inner_done = 1;
     if (a.graph) {
       cudaGraphSetConditional(a.h_inner, done ? 0u : 1u);
@@ -1284,8 +1305,8 @@ __global__ void __launch_bounds__(kTileThreads) k_post(MGArgs a, int l) {
   }
   if (!FINE) return;
   // level 0: u is the preconditioned residual z; the PCG scalars of the next step
-  double v[5] = {s[0], s[1], s[2], s[3], s[4]};
-  if (grid_sum<5>(v, a.part, a.ticket) && threadIdx.x == 0)
+  double v[5];
+  if (grid_sum_f<5>(s, v, a.part, a.ticket) && threadIdx.x == 0)
     store_gamma_delta(a.ps, v, a.singular, F.nxn * F.nyn);
 }
 
