@@ -523,12 +523,13 @@ __global__ void __launch_bounds__(kParticleThreads, kParticleMinBlocks) k_partic
       move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 1, c4.y, fx4.y, fy4.y, vx4.y, vy4.y, ke);
       move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 2, c4.z, fx4.z, fy4.z, vx4.z, vy4.z, ke);
       move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 3, c4.w, fx4.w, fy4.w, vx4.w, vy4.w, ke);
-      if (MODE == 0) {
-        *reinterpret_cast<int4 *>(P.cell + base) = c4;
-        *reinterpret_cast<float4 *>(P.fx + base) = fx4;
-        *reinterpret_cast<float4 *>(P.fy + base) = fy4;
-      }
-      if (MODE != 1) {
+      if (MODE == 0) {   // streaming stores: the written state is not read again this step
+        __stcs(reinterpret_cast<int4 *>(P.cell + base), c4);
+        __stcs(reinterpret_cast<float4 *>(P.fx + base), fx4);
+        __stcs(reinterpret_cast<float4 *>(P.fy + base), fy4);
+        __stcs(reinterpret_cast<float4 *>(P.vx + base), vx4);
+        __stcs(reinterpret_cast<float4 *>(P.vy + base), vy4);
+      } else if (MODE != 1) {
         *reinterpret_cast<float4 *>(P.vx + base) = vx4;
         *reinterpret_cast<float4 *>(P.vy + base) = vy4;
       }
