@@ -798,9 +798,28 @@ pic_status pic_load(pic_ctx *c, int32_t species, int64_t n, const double *x, con
   if (n > 0 && (!x || !y || !vx || !vy)) return PIC_EINVAL;
   if (n > c->cfg.capacity[species]) return PIC_EOVERFLOW;
   const int s = species;
+  // pinned host arrays the device can address are read by the conversion
+  // kernel in place (one launch, no staging copies); others go through the
+  // device staging buffer
+  auto device_view = [](const void *p) -> const void * {
+    cudaPointerAttributes at;
+    if (!p || cudaPointerGetAttributes(&at, p) != cudaSuccess) {
+      cudaGetLastError();
+      return nullptr;
+    }
+    return at.type == cudaMemoryTypeHost ? at.devicePointer : nullptr;
+  };
+  const void *hx = device_view(x), *hy = device_view(y), *hvx = device_view(vx), *hvy = device_view(vy);
+  const void *hid = ids ? device_view(ids) : nullptr;
+  const bool direct = n > 0 && hx && hy && hvx && hvy && (!ids || hid);
+  if (direct &&
+      launch_load_convert(c, s, static_cast<const double *>(hx), static_cast<const double *>(hy),
+                          static_cast<const double *>(hvx), static_cast<const double *>(hvy),
+                          static_cast<const uint32_t *>(hid), 0, n) != cudaSuccess)
+    return PIC_ECUDA;
   double *sx = c->d_stage, *sy = sx + c->stage_n, *svx = sy + c->stage_n, *svy = svx + c->stage_n;
   uint32_t *sid = (uint32_t *)(svy + c->stage_n);
-  for (int64_t off = 0; off < n; off += c->stage_n) {
+  for (int64_t off = 0; !direct && off < n; off += c->stage_n) {
     const int64_t m = std::min<int64_t>(c->stage_n, n - off);
     cudaMemcpyAsync(sx, x + off, m * 8, cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(sy, y + off, m * 8, cudaMemcpyHostToDevice, c->stream);

@@ -578,12 +578,14 @@ __global__ void k_load_convert(ParticleBuf P, Geom g, const uint8_t *cellmask, c
   const int64_t k = int64_t(blockIdx.x) * blockDim.x + threadIdx.x;
   if (k >= n) return;
   double X = x[k], Y = y[k];
-  if (g.px) {
+  // (the reduction into a periodic box only for coordinates outside it: FP64
+  // remainders are long instruction sequences here)
+  if (g.px && !(X >= 0.0 && X < double(g.nx))) {
     X = fmod(X, double(g.nx));
     if (X < 0) X += g.nx;
     if (X >= g.nx) X -= g.nx;
   }
-  if (g.py) {
+  if (g.py && !(Y >= 0.0 && Y < double(g.ny))) {
     Y = fmod(Y, double(g.ny));
     if (Y < 0) Y += g.ny;
     if (Y >= g.ny) Y -= g.ny;
