@@ -6,7 +6,7 @@
 // A = -Delta_h (5-point, unit spacing) on the free nodes, periodic where the
 // box is.  rho and the potential are held as double-float pairs (hi + lo,
 // about 48 bits; FP64 arithmetic runs at a small fraction of the FP32 rate
-// on this GPU).  The solve is an iterative refinement around an FP32 inner
+// on GB300).  The solve is an iterative refinement around an FP32 inner
 // solve:
 //
 //   repeat:  r = rho - A phi        (double-float stencil over the whole
@@ -110,7 +110,7 @@ __device__ void block_sum(double (&v)[NV]) {
 // Sums of squares for the norms, in FP32 without overflow or underflow:
 // |x| in [2^-50, 2^50] is squared as it is, larger values after scaling by
 // 2^-80 and smaller ones by 2^80, each class in its own accumulator (selects,
-// no branch).  FP64 arithmetic is slow on this GPU, so the grid sum runs in
+// no branch).  FP64 arithmetic is slow on GB300, so the grid sum runs in
 // FP32 within each warp and in double-float pairs across warps and blocks;
 // only the last step joins the classes in FP64.  The relative error of a
 // norm is a few FP32 roundings.
@@ -267,7 +267,7 @@ __device__ __forceinline__ double sq_join(const float *c) {
 
 // sqrt(num / den) for finite num >= 0 and normal den > 0, to FP32 accuracy,
 // without the FP64 divide and square root (long instruction sequences on
-// this GPU's narrow FP64 unit): the exponents are split off by bit
+// GB300's narrow FP64 unit): the exponents are split off by bit
 // manipulation and the mantissa ratio is taken in FP32.  NaN in, NaN out.
 __device__ double sqrt_ratio(double num, double den) {
   if (num != num || den != den) return num + den;
