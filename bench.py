@@ -119,36 +119,38 @@ class ClockSampler:
 
 
 def _dist():
+    """(process group or None, rank, world size) from the torchrun environment;
+    NCCL when a GPU is visible, gloo otherwise (the host-side tests)."""
     ws = int(os.environ.get("WORLD_SIZE", "1"))
     if ws <= 1:
         return None, 0, 1
+    import torch
     import torch.distributed as dist
-    dist.init_process_group("nccl")
+    dist.init_process_group("nccl" if torch.cuda.is_available() else "gloo")
     return dist, dist.get_rank(), ws
 
 
-def _reduce_max(dist, v):
-    if dist is None:
-        return v
+def _reduce(dist, v, op):
     import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    dev = "cuda" if dist.get_backend() == "nccl" else "cpu"
+    t = torch.tensor([v], dtype=torch.float64, device=dev)
+    dist.all_reduce(t, op=op)
     return float(t.item())
+
+
+def _reduce_max(dist, v):
+    return v if dist is None else _reduce(dist, v, dist.ReduceOp.MAX)
 
 
 def _reduce_sum(dist, v):
-    if dist is None:
-        return v
-    import torch
-    t = torch.tensor([v], dtype=torch.float64, device="cuda")
-    dist.all_reduce(t, op=dist.ReduceOp.SUM)
-    return float(t.item())
+    return v if dist is None else _reduce(dist, v, dist.ReduceOp.SUM)
 
 
 def _barrier(dist):
     if dist is not None:
         import torch
-        torch.cuda.synchronize()
+        if torch.cuda.is_available():
+            torch.cuda.synchronize()
         dist.barrier()
 
 
