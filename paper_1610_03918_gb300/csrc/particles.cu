@@ -554,10 +554,10 @@ __global__ void __launch_bounds__(kParticleThreads, kParticleMinBlocks) k_partic
       }
     }
     if (MODE == 0) {
-      double v = ke;
+      float v = ke;   // FP32 within the warp, FP64 from the warps' sums on
 #pragma unroll
       for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-      if ((threadIdx.x & 31) == 0) sRed[threadIdx.x >> 5] = v;
+      if ((threadIdx.x & 31) == 0) sRed[threadIdx.x >> 5] = double(v);
       __syncthreads();
       if (threadIdx.x == 0) {
         double t = 0.0;
