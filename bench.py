@@ -42,7 +42,7 @@ NCU_TRAFFIC = {
     # k_particles<0>, 512x1024 trench at 20 ppc (16.96M particles, 0.4 GB of
     # state, larger than L2), launches 3 and 4: 354.5 MB read + 287.4 / 284.1
     # MB written
-    "source_sha256": "56bd44acc0a65587ca507999327cf4580a50725e6ac5aa20f3e7bf2143429a20",
+    "source_sha256": "d8165d50bd418ec719e26e14026c3717c435ba2332d99c06d94fdc30c1bc0b81",
     "bytes_per_particle": 37.77,
 }
 
