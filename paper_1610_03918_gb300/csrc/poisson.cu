@@ -178,21 +178,6 @@ __device__ bool grid_sum(double (&v)[NV], double *part, unsigned int *ticket) {
   return grid_sum_blocks<NV>(v, part, ticket);
 }
 
-// The same from FP32 per-thread partials: summed over each warp in FP32 (a
-// tree of five roundings), then in FP64 from the warps' sums on, so FP64
-// arithmetic runs once per warp rather than in every thread.
-template <int NV>
-__device__ bool grid_sum_f(const float (&s)[NV], double (&v)[NV], double *part, unsigned int *ticket) {
-#pragma unroll
-  for (int k = 0; k < NV; ++k) {
-    float t = s[k];
-#pragma unroll
-    for (int o = 16; o > 0; o >>= 1) t += __shfl_down_sync(0xffffffffu, t, o);
-    v[k] = 0.0;
-    if ((threadIdx.x & 31) == 0) v[k] = double(t);
-  }
-  return grid_sum_blocks<NV>(v, part, ticket);
-}
 
 // FP32 tree sums of the sq_add classes.  Each block reduces its NC class
 // sums by shuffles within the warps and then over the warps (block_tree,
@@ -257,6 +242,26 @@ __device__ void sum_published(const float *part, int nb, float (&c)[NC]) {
     for (int q = 0; q < NC; ++q) c[q] += x[0][q] + x[1][q];
   }
   block_tree<NC>(c);
+}
+
+// Deterministic grid sum of FP32 per-thread partials (inner products of
+// the PCG): FP32 tree sums within each block and over the blocks' published
+// sums (fixed order), converted to FP64 once by thread 0 of the last block,
+// where it returns true.  The partials buffer takes NV floats per block.
+template <int NV>
+__device__ bool grid_sum_f(const float (&s)[NV], double (&v)[NV], double *part, unsigned int *ticket) {
+  float c[NV];
+#pragma unroll
+  for (int k = 0; k < NV; ++k) c[k] = s[k];
+  float *pf = reinterpret_cast<float *>(part);
+  if (!publish_sums<NV>(c, pf, ticket)) return false;
+  sum_published<NV>(pf, gridDim.x, c);
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int k = 0; k < NV; ++k) v[k] = double(c[k]);
+    *ticket = 0u;
+  }
+  return true;
 }
 
 // a class triple (mid, big, tiny) of sq_add as a double
