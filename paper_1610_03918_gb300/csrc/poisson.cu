@@ -16,7 +16,8 @@
 //            solve A e = r          (FP32: the direct solve of fastpoisson.cu
 //                                    where the geometry allows it, else PCG
 //                                    with a symmetric V-cycle preconditioner,
-//                                    inner products accumulated in FP64)
+//                                    inner products by FP32 tree sums, CG
+//                                    coefficients in FP64)
 //            phi += e               (double-float; the direct solve's
 //                                    kernels add their parts of e in place)
 //
