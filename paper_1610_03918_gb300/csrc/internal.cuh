@@ -152,6 +152,7 @@ struct PoissonState {
   double delta;                      // <z, A z>
   double alpha, beta;
   double alpha_next, beta_next;      // the coefficients of the next CG update
+  float cg_f[3];                     // alpha_next, beta_next, zmean in FP32
   double zmean;
   double tol_in;      // inner target relative to the inner initial residual
   int32_t inner_done, outer_done;

@@ -639,6 +639,9 @@ __device__ __forceinline__ void store_gamma_delta(PoissonState *ps, const double
   const double alpha = first ? gam / ps->delta : gam / (ps->delta - beta * gam / ps->alpha);
   ps->alpha_next = alpha;
   ps->beta_next = beta;
+  ps->cg_f[0] = float(alpha);   // the update kernel's FP32 copies
+  ps->cg_f[1] = float(beta);
+  ps->cg_f[2] = float(zm);
 }
 
 // w = A z and the scalars of store_gamma_delta, after a V-cycle that ran
@@ -692,7 +695,7 @@ __global__ void k_cg(FineArgs a) {
   PoissonState *ps = a.ps;
   if (ps->inner_done) return;
   const int nn = a.g.nxn * a.g.nyn;
-  const float fb = float(ps->beta_next), fa = float(ps->alpha_next), zm = float(ps->zmean);
+  const float fa = ps->cg_f[0], fb = ps->cg_f[1], zm = ps->cg_f[2];
   float rr = 0.f;
   VEC_BATCHES(base, nn) {
     float z[kVB], w[kVB], p[kVB], q[kVB], e[kVB], r[kVB];
