@@ -80,7 +80,7 @@ class ClockSampler:
         try:
             self.proc = subprocess.Popen(
                 ["nvidia-smi", "-i", str(self.device), f"--query-gpu={self.FIELDS}",
-                 "--format=csv,noheader,nounits", "-lms", "200"],
+                 "--format=csv,noheader,nounits", "-lms", "100"],
                 stdout=subprocess.PIPE, stderr=subprocess.DEVNULL, text=True)
             self.thread = threading.Thread(target=self._read, daemon=True)
             self.thread.start()
@@ -374,7 +374,8 @@ def run_warmstart(args):
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
-    ap.add_argument("--steps", type=int, default=100)
+    ap.add_argument("--steps", type=int, default=None,
+                    help="timed steps (default 1000 for the trench step, 100 otherwise)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="trench", choices=["trench", "ensemble", "warmstart"],
@@ -398,6 +399,8 @@ def main():
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the step's kernels from the host loop (for kernel profilers)")
     args = ap.parse_args()
+    if args.steps is None:
+        args.steps = 1000 if (args.workload == "trench" and args.impl == "ours") else 100
     if args.impl == "reference":
         return run_reference(args)
     args.warmup = max(args.warmup, 3)
