@@ -51,30 +51,36 @@ def _neighbours(geom, i, j):
 
 def system(geom):
     """(A, free_i, free_j, lift): A over the free nodes in row-major order
-    and the Dirichlet lift vector.  Cached on the geometry."""
+    and the Dirichlet lift vector of the geometry's current Dirichlet
+    values.  A and the neighbour indices are cached on the geometry; the
+    lift is formed from geom.g on every call (it changes with an RF bias)."""
     cache = getattr(geom, "_poisson_system", None)
-    if cache is not None:
-        return cache
-    free = geom.free
-    fi, fj = np.nonzero(free)
-    nf = fi.size
-    index = -np.ones((geom.nxn, geom.nyn), dtype=np.int64)
-    index[fi, fj] = np.arange(nf)
-    rows = [np.arange(nf)]
-    cols = [np.arange(nf)]
-    vals = [np.full(nf, 4.0)]
-    lift = np.zeros(nf)
-    for ni, nj in _neighbours(geom, fi, fj):
-        m = index[ni, nj]
-        isfree = m >= 0
-        rows.append(np.arange(nf)[isfree])
-        cols.append(m[isfree])
-        vals.append(-np.ones(int(isfree.sum())))
-        lift[~isfree] += geom.g[ni[~isfree], nj[~isfree]]
-    A = sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
-                      shape=(nf, nf))
-    geom._poisson_system = (A, fi, fj, lift)
-    return geom._poisson_system
+    if cache is None:
+        free = geom.free
+        fi, fj = np.nonzero(free)
+        nf = fi.size
+        index = -np.ones((geom.nxn, geom.nyn), dtype=np.int64)
+        index[fi, fj] = np.arange(nf)
+        rows = [np.arange(nf)]
+        cols = [np.arange(nf)]
+        vals = [np.full(nf, 4.0)]
+        dir_nbrs = []
+        for ni, nj in _neighbours(geom, fi, fj):
+            m = index[ni, nj]
+            isfree = m >= 0
+            rows.append(np.arange(nf)[isfree])
+            cols.append(m[isfree])
+            vals.append(-np.ones(int(isfree.sum())))
+            dir_nbrs.append((np.nonzero(~isfree)[0], ni[~isfree], nj[~isfree]))
+        A = sp.csc_matrix((np.concatenate(vals), (np.concatenate(rows), np.concatenate(cols))),
+                          shape=(nf, nf))
+        cache = (A, fi, fj, dir_nbrs)
+        geom._poisson_system = cache
+    A, fi, fj, dir_nbrs = cache
+    lift = np.zeros(fi.size)
+    for k, ni, nj in dir_nbrs:
+        lift[k] += geom.g[ni, nj]
+    return A, fi, fj, lift
 
 
 def rhs(geom, rho):

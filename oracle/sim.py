@@ -13,6 +13,23 @@ then (3),(4)" is read as the standard leapfrog cycle of ref. [bir86]):
 Velocities live at half steps.  A species loaded with velocities at t = 0
 is started with the half back-kick v^{-1/2} = v^0 - (1/2) alpha_j E^0 dt.
 
+RF bias (Sec. III-B): the solve at time level n uses the electrode value at
+t = n dt (geometry.Geometry.set_time).
+
+Ion recycling (Sec. III-A: a lost ion is replaced by a thermal ion in the
+bulk plasma, as ionisation of the neutral gas; Sec. III-C: with the trench,
+ionisation only in the bulk region above the electrode).  Reading taken:
+every ion absorbed during step n (tallied and recorded as usual) re-enters,
+with its id, in the same step at a uniform position in the source rows
+[source_x0, source_x1) of cells (all y) with a Maxwellian velocity of the
+ion thermal speed, taken as its v^{n+1/2}; it joins the deposit of
+rho^{n+1}.  The draws are Philox4x32-10 (oracle.rng) keyed by the seed, with
+counter (id, n, 1, k):
+  k = 0: words r0..r3 -> cell row  source_x0 + floor(r0 L / 2^32)  (L rows),
+         cell column floor(r1 ny / 2^32), offsets top24(r2), top24(r3) / 2^24;
+  k = 1: Box-Muller on u1 = (top24(q0) + 1) / 2^24, u2 = top24(q1) / 2^24.
+Positions are then exact dyadic numbers, the same on any machine.
+
 Diagnostics of the step just taken (time level n):
   KE_s = 1/2 m_s w_s sum_p v^{n-1/2} . v^{n+1/2}  (m_s = q_s / alpha_s, w_s = 1/ppc_s)
   FE   = 1/2 sum_nodes |E^n|^2
@@ -22,8 +39,10 @@ from __future__ import annotations
 
 import numpy as np
 
-from . import deposit, field, poisson, push
+from . import deposit, field, poisson, push, rng
 from .geometry import from_workload
+
+RECYCLE_TAG = 1
 
 
 class Sim:
@@ -84,6 +103,7 @@ class Sim:
         return rho
 
     def solve_fields(self):
+        self.geom.set_time(self.nstep * self.w.dt)
         self.rho = self.charge_density()
         self.phi = poisson.solve_direct(self.geom, self.rho)
         self.Ex, self.Ey = field.efield(self.geom, self.phi)
@@ -117,9 +137,38 @@ class Sim:
         rec = dict(ids=ps["ids"][dead], species=np.full(int(dead.sum()), s), wall=wall[dead],
                    cell=wcell[dead], step=np.full(int(dead.sum()), self.nstep),
                    vx=vx1[dead], vy=vy1[dead])
-        self.p[s] = dict(x=x1[alive], y=y1[alive], vx=vx1[alive], vy=vy1[alive],
-                         ids=ps["ids"][alive])
+        new = dict(x=x1[alive], y=y1[alive], vx=vx1[alive], vy=vy1[alive], ids=ps["ids"][alive])
+        if s == 1 and getattr(self.w, "recycle", False) and dead.any():
+            r = self.recycled(ps["ids"][dead], self.nstep)
+            for k in new:
+                new[k] = np.concatenate([new[k], r[k]])
+        self.p[s] = new
         return rec
+
+    def source_rows(self):
+        x0 = int(getattr(self.w, "source_x0", 0))
+        x1 = int(getattr(self.w, "source_x1", 0)) or self.w.nx - self.w.trench_depth
+        return x0, x1
+
+    def recycled(self, ids, step):
+        """The thermal ions that replace the absorbed ions `ids` during step
+        `step` (see the module docstring)."""
+        ids = np.asarray(ids, np.uint64)
+        key = rng.seed_key(getattr(self.w, "recycle_seed", 0))
+        ctr = np.zeros((ids.size, 4), np.uint64)
+        ctr[:, 0] = ids
+        ctr[:, 1] = np.uint64(step)
+        ctr[:, 2] = RECYCLE_TAG
+        r = rng.philox4x32_10(ctr, key)
+        ctr[:, 3] = 1
+        q = rng.philox4x32_10(ctr, key)
+        x0, x1 = self.source_rows()
+        i = x0 + rng.below(r[:, 0], x1 - x0)
+        j = rng.below(r[:, 1], self.w.ny)
+        z0, z1 = rng.box_muller(rng.unit24_open(q[:, 0]), rng.unit24(q[:, 1]))
+        vth = self.w.vth[1]
+        return dict(x=i + rng.unit24(r[:, 2]), y=j + rng.unit24(r[:, 3]), vx=vth * z0, vy=vth * z1,
+                    ids=ids.astype(np.uint32))
 
     def step(self, n=1):
         for _ in range(n):

@@ -49,6 +49,17 @@ class Workload:
     surface_charge: bool = False  # bottom-face hits feed back into rho
     poisson_rtol: float = 1e-6
     sort_every: int = 8
+    # RF bias of the electrode (Sec. III-B): its Dirichlet value at time t is
+    # phi_electrode + phi_rf_amp * sin(omega_rf * t)
+    phi_rf_amp: float = 0.0
+    omega_rf: float = 0.0
+    # ion recycling (Sec. III-A, III-C): an absorbed ion is re-loaded as a
+    # thermal ion at a uniform position in the source rows [source_x0,
+    # source_x1) of cells (all y); source_x1 = 0 means nx - trench_depth
+    recycle: bool = False
+    source_x0: int = 0
+    source_x1: int = 0
+    recycle_seed: int = 0
 
     # ---- species constants (paper Sec. II: alpha_e = -1, alpha_i = (m_e/m_i)(q_i/e)) ----
     @property
