@@ -282,92 +282,106 @@ def run_ensemble(args):
 
 
 def run_warmstart(args):
-    """Poisson time to a 1e-6 relative residual on the trench geometry, from
-    the learned guess (network input, inference and solve) against the zero,
-    empty-box and previous-step starts, on held-out trench widths.  The
-    network is trained here on pairs dumped from runs at other widths."""
+    """Poisson time to a 1e-6 relative residual on the trench geometry with
+    the learned initial guess against the zero and previous-step starts, on
+    held-out trench widths, timed inside the captured step graph with CUDA
+    events (the learned guess -- network input, inference, guess -- is part of
+    the solve phase).  The network is initialised by the library and trained
+    by its kernels on (rho, phi) pairs dumped by the library from runs at
+    other widths; pairs stream through a shuffled ring buffer, so any number
+    of them fits in memory."""
     import torch
     torch.cuda.set_device(0)
     import __graft_entry__
     __graft_entry__.build()
     import paper_1610_03918_gb300 as pg
     from paper_1610_03918_gb300 import warmstart as ws
-    from oracle import unet as ounet   # only for the seeded He initialisation
     t0 = time.perf_counter()
 
     def trench(width, seed):
         return synth.trench_512x1024(trench_width=width, trench_y0=(512 - width) // 2, seed=seed)
 
-    pairs = []
-    for k, width in enumerate(int(v) for v in args.train_widths.split(",")):
-        w = trench(width, 200 + k)
+    net = pg.Unet(args.batch, ws.padded_rows(1025), 512)
+    net.init(seed=0)
+    widths = [int(v) for v in args.train_widths.split(",")]
+    rng = np.random.default_rng(0)
+    ring, n_pairs, n_steps = [], 0, 0
+    t_data = t_train = 0.0
+    per_run = max(1, args.pairs // max(args.runs, 1))
+    for r in range(args.runs):
+        td = time.perf_counter()
+        w = trench(widths[r % len(widths)], 200 + r)
         sim = pg.Sim(w, capacity=int(synth.plasma_cells(w).sum()) * w.ppc)
         for s in (0, 1):
             sim.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
-        sim.step(50)
-        pairs += ws.dump_pairs(sim, steps=2 * args.dumps, every=2)
+        sim.step(args.settle)
+        t_data += time.perf_counter() - td
+        for k in range(per_run):
+            td = time.perf_counter()
+            pair = ws.dump_pairs(sim, steps=args.dump_every, every=args.dump_every)[0]
+            n_pairs += 1
+            if len(ring) < args.ring:
+                ring.append(pair)
+            else:
+                ring[int(rng.integers(len(ring)))] = pair
+            t1 = time.perf_counter()
+            t_data += t1 - td
+            if len(ring) >= args.batch:
+                idx = rng.choice(len(ring), args.batch, replace=False)
+                x = torch.stack([ring[i][0] for i in idx])
+                t = torch.stack([ring[i][1] for i in idx])
+                frac = n_pairs / max(args.pairs, 1)
+                net.train_step(x, t, args.lr * (1.0 - 0.9 * min(frac, 1.0)))
+                n_steps += 1
+            torch.cuda.synchronize()
+            t_train += time.perf_counter() - t1
         sim.close()
-    t_data = time.perf_counter() - t0
-    net = pg.Unet(1, ws.padded_rows(1025), 512)
-    net.set_params(ounet.flat(ounet.init_params(0)).astype(np.float32))
-    t1 = time.perf_counter()
-    ws.train(net, pairs, epochs=args.epochs, lr=1e-3)
-    t_train = time.perf_counter() - t1
-    del pairs
-    lw = ws.LearnedWarmStart(net)
-    res = {"zero": [], "vacuum": [], "previous": [], "learned": []}
-    its = {k: [] for k in res}
-
-    def timed(fn):
-        e0 = torch.cuda.Event(enable_timing=True)
-        e1 = torch.cuda.Event(enable_timing=True)
-        torch.cuda.synchronize()
-        e0.record()
-        st = fn()
-        e1.record()
-        torch.cuda.synchronize()
-        return st, e0.elapsed_time(e1)
-
-    for k, width in enumerate(int(v) for v in args.eval_widths.split(",")):
-        w = trench(width, 900 + k)
-        # the warm starts serve the iterative inner solver
-        sim = pg.Sim(w, capacity=int(synth.plasma_cells(w).sum()) * w.ppc,
-                     poisson_method=pg.POISSON_MULTIGRID)
-        for s in (0, 1):
-            sim.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
-        sim.step(args.warmup * 10)
-        for rep in range(args.steps):
-            prev = sim.phi()          # the previous step's potential
-            sim.step(1)
-            for name, guess in (("zero", 0), ("vacuum", 2)):
-                st, ms = timed(lambda: sim.poisson(guess))
-                res[name].append(ms)
-                its[name].append(st[0])
-            sim.set_phi(prev)
-            st, ms = timed(lambda: sim.poisson(1))
-            res["previous"].append(ms)
-            its["previous"].append(st[0])
-            st, ms = lw.solve(sim)
-            res["learned"].append(ms)
-            its["learned"].append(st[0])
-        sim.close()
-    out = {k: float(np.median(v)) for k, v in res.items()}
+    del ring
+    eval_net = pg.Unet(1, ws.padded_rows(1025), 512)
+    eval_net.set_params(net.get_params())
+    res, its = {}, {}
+    for name, mode in (("zero", 0), ("previous", 1), ("learned", 3)):
+        ms, it = [], []
+        for k, width in enumerate(int(v) for v in args.eval_widths.split(",")):
+            w = trench(width, 900 + k)
+            sim = pg.Sim(w, capacity=int(synth.plasma_cells(w).sum()) * w.ppc,
+                         poisson_method=pg.POISSON_MULTIGRID, warm_start=1 if mode == 3 else mode,
+                         timing=True)
+            if mode == 3:
+                sim.set_learned_start(eval_net)
+            for s in (0, 1):
+                sim.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
+            sim.step(args.settle)
+            sim.timing()
+            for _ in range(args.steps):
+                sim.step(1)
+                it.append(sim.poisson_stats()[0])
+            tm = sim.timing()
+            ms.append(tm["ms_poisson"] / max(tm["steps"], 1))
+            sim.close()
+        res[name] = float(np.mean(ms))
+        its[name] = float(np.mean(it))
     line = {
         "metric": "Poisson ms to 1e-6 residual (learned warm start)",
-        "value": out["learned"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
-        "steps": args.steps, "warmup": args.warmup, "dtype": "bf16 net / f32+f64 solver",
+        "value": res["learned"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
+        "steps": args.steps, "warmup": args.settle, "dtype": "bf16 net / f32+f64 solver",
         "data": "synthetic", "vs_baseline": None,
         "config": {"workload": "trench_512x1024 geometry, held-out widths " + args.eval_widths,
                    "inner_solver": "multigrid PCG (the warm starts serve the iterative solver)",
-                   "train_widths": args.train_widths, "train_pairs": args.dumps * len(args.train_widths.split(",")),
-                   "epochs": args.epochs, "data_s": t_data, "train_s": t_train},
-        "median_ms": out,
-        "median_iterations": {k: float(np.median(v)) for k, v in its.items()},
-        "speedup_vs_zero": out["zero"] / out["learned"],
-        "speedup_vs_vacuum": out["vacuum"] / out["learned"],
+                   "timing": "CUDA events around the solve phase of each captured step "
+                             "(the learned guess included)",
+                   "train_widths": args.train_widths, "train_pairs": n_pairs, "runs": args.runs,
+                   "train_steps": n_steps, "batch": args.batch, "data_s": t_data,
+                   "train_s": t_train, "init": "library He initialisation (pic_unet_init)"},
+        "ms_per_solve": res,
+        "pcg_iterations_per_solve": its,
+        "speedup_vs_zero": res["zero"] / res["learned"],
+        "speedup_vs_previous": res["previous"] / res["learned"],
+        "wall_s": time.perf_counter() - t0,
     }
     print(json.dumps(line), flush=True)
     net.close()
+    eval_net.close()
     return 0
 
 
@@ -383,8 +397,13 @@ def main():
                          "warmstart: Poisson time to 1e-6 with the learned initial guess")
     ap.add_argument("--train-widths", default="2,6,10,14,20")
     ap.add_argument("--eval-widths", default="3,11,19")
-    ap.add_argument("--dumps", type=int, default=200, help="training pairs per training run")
-    ap.add_argument("--epochs", type=int, default=3)
+    ap.add_argument("--pairs", type=int, default=2000, help="training pairs (warmstart)")
+    ap.add_argument("--runs", type=int, default=10, help="training runs the pairs come from")
+    ap.add_argument("--dump-every", type=int, default=10, help="steps between dumped pairs")
+    ap.add_argument("--settle", type=int, default=100, help="steps before dumping / timing")
+    ap.add_argument("--ring", type=int, default=256, help="pairs held for shuffled minibatches")
+    ap.add_argument("--batch", type=int, default=4, help="training minibatch")
+    ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--members", type=int, default=48, help="ensemble members")
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--no-cpu-baseline", action="store_true")

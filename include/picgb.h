@@ -104,7 +104,9 @@ typedef struct {
   int32_t poisson_maxit;          /* cap on inner PCG iterations per solve */
   double poisson_rtol;            /* target ||b - A phi||_2 / ||b||_2 (A phi in double-float) */
   int32_t warm_start;             /* 0: zero initial guess each solve, 1: previous phi,
-                                     2: extrapolated 2 phi^n - phi^{n-1} */
+                                     2: extrapolated 2 phi^n - phi^{n-1}, 3: learned -- the
+                                     warm-start network's guess phi_L + s U(rho / s, mask)
+                                     (see unet_weights and pic_set_learned_start) */
   int32_t device;                 /* CUDA device ordinal */
   int32_t timing;                 /* 1: each step records its phase boundaries in CUDA
                                      events (a pool of 64 steps, read back when it fills or
@@ -122,9 +124,37 @@ typedef struct {
                                      1: conjugate gradient preconditioned by a multigrid V-cycle */
   int64_t hit_capacity;           /* hit records kept (PIC_DIAG_HITS) */
   void *stream;                   /* cudaStream_t to run on; NULL: a library-owned stream */
-  void *(*alloc)(size_t bytes, void *user); /* optional device allocator */
-  void (*free)(void *ptr, void *user);      /* its release function */
+  /* optional device allocator: called with the context's stream (the memory
+     is used in stream order on it); NULL: cudaMalloc / cudaFree */
+  void *(*alloc)(size_t bytes, void *stream, void *user);
+  void (*free)(void *ptr, void *stream, void *user);      /* its release function */
   void *alloc_user;
+  /* RF bias of the electrode (Sec. III-B: Phi = Phi_0 sin(omega_RF t) on the
+     biased plate): every node held at the electrode potential takes
+     phi_electrode + phi_rf_amp sin(omega_rf t) in the solve of time level
+     n, t = n dt.  phi_rf_amp = 0: a fixed bias. */
+  double phi_rf_amp;
+  double omega_rf;
+  /* ion recycling (Sec. III-A: a lost ion is replaced by a thermal ion in the
+     bulk, as ionisation of the neutral gas; Sec. III-C: ionisation only in
+     the bulk region).  With recycle = 1, every ion absorbed during step n
+     (tallied and recorded as usual) re-enters in the same step, with its id,
+     at a uniform position in the cell rows [source_x0, source_x1) (all y;
+     source_x1 = 0: nx - trench_depth, the rows above the electrode) and with
+     a Maxwellian velocity of standard deviation recycle_vth per component,
+     taken as its v^{n+1/2}.  The draws are Philox4x32-10 keyed by seed with
+     counter (id, n, 1, k): k = 0 gives the row source_x0 + floor(r0 L / 2^32),
+     the column floor(r1 ny / 2^32) and the offsets (r2 >> 8) 2^-24,
+     (r3 >> 8) 2^-24; k = 1 the Box-Muller pair of u1 = ((q0 >> 8) + 1) 2^-24,
+     u2 = (q1 >> 8) 2^-24.  Electrons are not recycled. */
+  int32_t recycle;
+  int32_t source_x0, source_x1;
+  double recycle_vth;
+  uint64_t seed;                  /* key of the counter-based draws */
+  /* warm_start = 3: file of the warm-start network's parameters (the flat
+     FP32 vector of pic_unet_save); the network then gives the initial guess
+     of every solve inside the step.  NULL otherwise. */
+  const char *unet_weights;
 } pic_config;
 
 /* One absorbed particle (PIC_DIAG_HITS): velocity is v^{n+1/2}. */
@@ -215,6 +245,30 @@ pic_status pic_set_timing(pic_ctx *ctx, int32_t on);
 pic_status pic_diag(pic_ctx *ctx, int32_t kind, void *out, int64_t cap_bytes,
                     int64_t *n_out);
 
+/* Checkpoint and restart (no counterpart in the paper; a service for long
+ * runs).  pic_save writes the complete state of the run into the host buffer
+ * buf of cap_bytes: the live particles in their stored form (cell index,
+ * FP32 in-cell offsets and half-step velocities, id), the potential (and the
+ * previous step's, for the warm start), the field, rho, rho_ext and the
+ * Dirichlet data as stored (double-float pairs), the wall tallies, the
+ * trench-bottom counts, the hit records kept and the total hit count, the
+ * step counter, the status word and the solver's last scalars.  *n_out
+ * receives the size; buf == NULL only reports it.  The particles are
+ * compacted through a temporary device buffer of 24 bytes per particle
+ * slot drawn from the context's allocator.  PIC_ESTATE after a pic_load that
+ * no step has brought up to date.  Synchronous.
+ *
+ * pic_restore loads such a checkpoint into a context created with the same
+ * configuration (grid, geometry, capacities at least the live counts, hit
+ * capacity at least the records kept; PIC_EINVAL / PIC_EOVERFLOW
+ * otherwise).  The next pic_step (or pic_batch_step of a batch member)
+ * sorts the particles and continues the run bit for bit as if it had not
+ * been interrupted: N steps, save, restore into a new context, N steps give
+ * the particles, fields, tallies and hit records of 2N uninterrupted steps.
+ * PIC_DIAG_ENERGY reports the kinetic energy again from the next step on. */
+pic_status pic_save(pic_ctx *ctx, void *buf, int64_t cap_bytes, int64_t *n_out);
+pic_status pic_restore(pic_ctx *ctx, const void *buf, int64_t n_bytes);
+
 /* Release the context and all its device memory. */
 pic_status pic_free(pic_ctx *ctx);
 
@@ -286,6 +340,32 @@ pic_status pic_unet_gradients(pic_unet *u, const float *x, const float *t, float
 pic_status pic_unet_train_step(pic_unet *u, const float *x, const float *t, float lr, double *loss);
 pic_status pic_unet_free(pic_unet *u);
 
+/* He initialisation of every weight (He et al., ICCV 2015: N(0, 2 / fan_in)
+ * for the layers followed by a ReLU, N(0, 1 / fan_in) for the linear head;
+ * fan_in = 9 x input channels for a 3x3 convolution, the input channels for
+ * a transposed one), zero biases, Adam state reset.  Weight e of layer k
+ * (layers in parameter order) takes the cosine half of the Box-Muller pair of
+ * Philox4x32-10 with key = seed and counter (e, k, 2, 0).  Synchronous. */
+pic_status pic_unet_init(pic_unet *u, uint64_t seed);
+/* The flat FP32 parameter vector to / from a file (raw, native byte order,
+ * pic_unet_num_params values).  Synchronous. */
+pic_status pic_unet_save(pic_unet *u, const char *path);
+pic_status pic_unet_load(pic_unet *u, const char *path);
+
+/* Use a copy of the parameters of net for the learned initial guess of every
+ * later solve of the context (its warm_start becomes 3): inside each step the
+ * guess phi_L + s U(rho / s, mask) is formed on the device (s = max |rho|, the
+ * input and the network's forward pass on the context's stream, captured in
+ * the step graph) and the solve runs from it to its tolerance.  net must have
+ * batch 1, height >= nxn (nxn rounded up to a multiple of 8) and width nyn.
+ * Computes the empty-box potential phi_L if not done yet.  Synchronous. */
+pic_status pic_set_learned_start(pic_ctx *c, const pic_unet *net);
+
+/* Training target of the warm-start network for the context's current
+ * potential: t [hpad][nyn] (device, FP32) = (phi - phi_L) / scale, rows
+ * nxn..hpad-1 zero.  Synchronous. */
+pic_status pic_learned_target(pic_ctx *c, int32_t hpad, double scale, float *t);
+
 /* Input of the warm-start network for the context's current charge density:
  * x [hpad][nyn][2] (device, FP32) = (rho / s, 1 on Dirichlet nodes), rows
  * nxn..hpad-1 filled as conductor; *scale = s = max |rho| (host).
@@ -313,15 +393,21 @@ pic_status pic_poisson(pic_ctx *c, int32_t guess, const float *y, double scale, 
  * at absolute positions x[k], y[k] on a grid of nx x ny cells (N + 1 nodes
  * in a bounded direction, N in a periodic one; periodic coordinates wrap).
  * x, y (n doubles each) and rho (nodes, row-major, y fastest) are DEVICE
- * pointers owned by the caller; particles outside the grid are skipped.
+ * pointers owned by the caller.  Particles outside the grid in a bounded
+ * direction, and particles with a NaN coordinate, are dropped without any
+ * report: the call still returns PIC_OK, and their charge is missing from rho.
  * Work is queued on `stream` (a cudaStream_t, NULL = legacy default stream)
- * of the current device and the call returns once it is queued.
+ * of the current device and the call returns once it is queued.  PIC_ECUDA
+ * means one of this call's own launches failed; errors left by earlier,
+ * unrelated CUDA calls are neither reported nor cleared.
  *
  * Scratch: one fixed array of 2^20 64-bit accumulators (8 MiB), a static
  * device variable of the library that every GPU loading the library holds
  * until the process exits.  Grids with more than 2^20 nodes return
- * PIC_ESIZE.  The first call on a device (that device current) looks up the
- * array's device address; make that first call before any stream capture.
+ * PIC_ESIZE.  Each call looks up the array's device address in the context
+ * current on the calling thread (so a caller may switch contexts, or reset
+ * the device, between calls); make the first call on a device before any
+ * stream capture, since that first lookup loads the library's module there.
  * Every call clears and reuses the same array, so calls whose work overlaps
  * on one GPU (different streams, or different host threads) race and must
  * be serialised by the caller. */

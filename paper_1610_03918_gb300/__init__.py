@@ -36,10 +36,12 @@ PIC_LOAD_V_AT_T0 = 1
 EXPORTED = ("pic_init", "pic_load", "pic_step", "pic_set_timing", "pic_diag", "pic_free", "pic_strerror",
             "pic_batch_init", "pic_batch_member", "pic_batch_step", "pic_batch_timing",
             "pic_batch_free", "pic_deposit_static", "pic_unet_create", "pic_unet_forward",
-            "pic_unet_gradients", "pic_unet_train_step", "pic_unet_free")
+            "pic_unet_gradients", "pic_unet_train_step", "pic_unet_free", "pic_save", "pic_restore",
+            "pic_unet_init", "pic_unet_save", "pic_unet_load", "pic_set_learned_start",
+            "pic_learned_target")
 
-ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p)
-FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p)
+ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
+FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
 
 
 # pic_config.poisson_method
@@ -66,6 +68,10 @@ class PicConfig(ctypes.Structure):
         ("hit_capacity", ctypes.c_int64),
         ("stream", ctypes.c_void_p),
         ("alloc", ALLOC_FN), ("free", FREE_FN), ("alloc_user", ctypes.c_void_p),
+        ("phi_rf_amp", ctypes.c_double), ("omega_rf", ctypes.c_double),
+        ("recycle", ctypes.c_int32), ("source_x0", ctypes.c_int32), ("source_x1", ctypes.c_int32),
+        ("recycle_vth", ctypes.c_double), ("seed", ctypes.c_uint64),
+        ("unet_weights", ctypes.c_char_p),
     ]
 
 
@@ -101,6 +107,10 @@ def load_library():
     lib.pic_set_timing.argtypes = [P, ctypes.c_int32]
     lib.pic_diag.argtypes = [P, ctypes.c_int32, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
     lib.pic_free.argtypes = [P]
+    lib.pic_save.argtypes = [P, P, ctypes.c_int64, ctypes.POINTER(ctypes.c_int64)]
+    lib.pic_restore.argtypes = [P, P, ctypes.c_int64]
+    lib.pic_save.restype = ctypes.c_int
+    lib.pic_restore.restype = ctypes.c_int
     lib.pic_strerror.argtypes = [ctypes.c_int]
     lib.pic_strerror.restype = ctypes.c_char_p
     lib.pic_last_error.argtypes = []
@@ -129,6 +139,14 @@ def load_library():
                                        ctypes.POINTER(ctypes.c_double)]
     lib.pic_unet_train_step.argtypes = [P, P, P, ctypes.c_float, ctypes.POINTER(ctypes.c_double)]
     lib.pic_unet_free.argtypes = [P]
+    lib.pic_unet_init.argtypes = [P, ctypes.c_uint64]
+    lib.pic_unet_save.argtypes = [P, ctypes.c_char_p]
+    lib.pic_unet_load.argtypes = [P, ctypes.c_char_p]
+    lib.pic_set_learned_start.argtypes = [P, P]
+    lib.pic_learned_target.argtypes = [P, ctypes.c_int32, ctypes.c_double, P]
+    for name in ("pic_unet_init", "pic_unet_save", "pic_unet_load", "pic_set_learned_start",
+                 "pic_learned_target"):
+        getattr(lib, name).restype = ctypes.c_int
     for name in ("pic_unet_create", "pic_unet_set_params", "pic_unet_get_params",
                  "pic_unet_forward", "pic_unet_gradients", "pic_unet_train_step", "pic_unet_free"):
         getattr(lib, name).restype = ctypes.c_int
@@ -204,13 +222,14 @@ class _TorchAllocator:
         self.device = device
         self.stream = stream
 
-        def _alloc(nbytes, user):
+        def _alloc(nbytes, stream, user):
             try:
-                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device, self.stream))
+                return int(torch.cuda.caching_allocator_alloc(int(nbytes), self.device,
+                                                              stream or self.stream))
             except Exception:
                 return None
 
-        def _free(ptr, user):
+        def _free(ptr, stream, user):
             torch.cuda.caching_allocator_delete(int(ptr))
 
         self.alloc = ALLOC_FN(_alloc)
@@ -220,7 +239,7 @@ class _TorchAllocator:
 def make_config(w, capacity=None, device: int = 0, stream=None, hit_capacity: int = 1 << 20,
                 poisson_maxit: int = 200, warm_start: int = 1, allocator=None,
                 timing: bool = False, graphs: bool = True,
-                poisson_method: int = POISSON_AUTO) -> PicConfig:
+                poisson_method: int = POISSON_AUTO, unet_weights=None) -> PicConfig:
     """PicConfig from a workload description (an object with the fields of
     synth.Workload)."""
     cfg = PicConfig()
@@ -246,6 +265,14 @@ def make_config(w, capacity=None, device: int = 0, stream=None, hit_capacity: in
     cfg.graphs = int(bool(graphs))
     cfg.poisson_method = int(poisson_method)
     cfg.hit_capacity = int(hit_capacity)
+    cfg.phi_rf_amp = float(getattr(w, "phi_rf_amp", 0.0))
+    cfg.omega_rf = float(getattr(w, "omega_rf", 0.0))
+    cfg.recycle = int(bool(getattr(w, "recycle", False)))
+    cfg.source_x0 = int(getattr(w, "source_x0", 0))
+    cfg.source_x1 = int(getattr(w, "source_x1", 0))
+    cfg.recycle_vth = float(w.vth[1]) if cfg.recycle else 0.0
+    cfg.seed = int(getattr(w, "recycle_seed", 0)) & 0xFFFFFFFFFFFFFFFF
+    cfg.unet_weights = os.fsencode(unet_weights) if unet_weights is not None else None
     cfg.stream = stream
     if allocator is not None:
         cfg.alloc = allocator.alloc
@@ -379,6 +406,20 @@ class Sim:
                 "launches", "slots")
         return dict(zip(keys, v.tolist()))
 
+    def save(self) -> bytes:
+        """A checkpoint of the whole run (pic_save)."""
+        lib = load_library()
+        n = ctypes.c_int64(0)
+        self._check(lib.pic_save(self.ctx, None, 0, ctypes.byref(n)), "pic_save")
+        buf = ctypes.create_string_buffer(int(n.value))
+        self._check(lib.pic_save(self.ctx, buf, int(n.value), ctypes.byref(n)), "pic_save")
+        return buf.raw[: int(n.value)]
+
+    def restore(self, blob: bytes):
+        """Continue the run saved in `blob` (pic_restore)."""
+        buf = ctypes.create_string_buffer(bytes(blob), len(blob))
+        return self._check(load_library().pic_restore(self.ctx, buf, len(blob)), "pic_restore")
+
     def set_phi(self, phi):
         return self._check(pic_load(self.ctx, -2, np.asarray(phi, np.float64).ravel()), "pic_load(phi)")
 
@@ -394,6 +435,20 @@ class Sim:
         self._check(load_library().pic_learned_input(self.ctx, int(hpad), x.data_ptr(), ctypes.byref(s)),
                     "pic_learned_input")
         return x, s.value
+
+    def learned_target(self, hpad, scale):
+        """The warm-start network's training target (phi - phi_L) / scale for
+        the current potential, as a torch CUDA tensor [hpad, nyn]."""
+        import torch
+        t = torch.empty((hpad, self.nyn), dtype=torch.float32, device="cuda")
+        self._check(load_library().pic_learned_target(self.ctx, int(hpad), float(scale), t.data_ptr()),
+                    "pic_learned_target")
+        return t
+
+    def set_learned_start(self, net):
+        """Every later solve starts from the guess of (a copy of) the trained
+        network `net` (warm_start 3, inside the step graph)."""
+        return self._check(load_library().pic_set_learned_start(self.ctx, net.h), "pic_set_learned_start")
 
     def poisson(self, guess, y=None, scale=0.0):
         """Re-solve for the current rho from guess 0 zero, 1 previous, 2 vacuum,
@@ -501,6 +556,22 @@ class Unet:
         self.h = h
         self.shape = (batch, height, width)
         self.nparam = int(lib.pic_unet_num_params(h))
+
+    def init(self, seed: int = 0):
+        """He initialisation by the library (seeded Philox draws), zero biases."""
+        st = load_library().pic_unet_init(self.h, int(seed) & 0xFFFFFFFFFFFFFFFF)
+        if st != PIC_OK:
+            raise PicError(st, "pic_unet_init")
+
+    def save(self, path):
+        st = load_library().pic_unet_save(self.h, os.fsencode(path))
+        if st != PIC_OK:
+            raise PicError(st, "pic_unet_save")
+
+    def load(self, path):
+        st = load_library().pic_unet_load(self.h, os.fsencode(path))
+        if st != PIC_OK:
+            raise PicError(st, "pic_unet_load")
 
     def set_params(self, flat):
         flat = np.ascontiguousarray(flat, dtype=np.float32)

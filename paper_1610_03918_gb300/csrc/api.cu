@@ -20,15 +20,29 @@ cudaError_t note(cudaError_t e, const char *where) {
   return e;
 }
 
-void *dev_alloc(pic_ctx *c, size_t bytes) {
+void *tmp_alloc(pic_ctx *c, size_t bytes) {
   if (bytes == 0) bytes = 16;
   bytes = (bytes + 255) & ~size_t(255);
   void *p = nullptr;
   if (c->cfg.alloc) {
-    p = c->cfg.alloc(bytes, c->cfg.alloc_user);
+    p = c->cfg.alloc(bytes, c->stream, c->cfg.alloc_user);
   } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
     p = nullptr;
   }
+  return p;
+}
+
+void tmp_free(pic_ctx *c, void *p) {
+  if (!p) return;
+  if (c->cfg.alloc) {
+    if (c->cfg.free) c->cfg.free(p, c->stream, c->cfg.alloc_user);
+  } else {
+    cudaFree(p);
+  }
+}
+
+void *dev_alloc(pic_ctx *c, size_t bytes) {
+  void *p = tmp_alloc(c, bytes);
   if (p) c->allocs.push_back(p);
   return p;
 }
@@ -38,15 +52,6 @@ namespace {
 constexpr int64_t kStageParticles = int64_t(1) << 22;
 constexpr int kTuneSteps = 48;   // particle steps timed after a sort when tuning the interval
 constexpr int kTuneMin = 4;      // shortest interval the tuning may choose
-
-void release(pic_ctx *c, void *p) {
-  if (!p) return;
-  if (c->cfg.alloc) {
-    if (c->cfg.free) c->cfg.free(p, c->cfg.alloc_user);
-  } else {
-    cudaFree(p);
-  }
-}
 
 // Node arrays held on the device as double-float (hi, lo) pairs
 std::vector<float2> to_pairs(const double *x, size_t n) {
@@ -99,6 +104,8 @@ void build_geometry(pic_ctx *c, std::vector<uint8_t> &cellmask, std::vector<doub
   const size_t nn = size_t(g.nxn) * g.nyn;
   std::vector<uint8_t> dir(nn, 0);
   std::vector<double> val(nn, 0.0);
+  std::vector<uint8_t> &elec = c->h_electrode;   // held at the electrode potential
+  elec.assign(nn, 0);
   for (int i = 0; i < g.nxn; ++i) {
     for (int j = 0; j < g.nyn; ++j) {
       const size_t n = size_t(i) * g.nyn + j;
@@ -113,6 +120,7 @@ void build_geometry(pic_ctx *c, std::vector<uint8_t> &cellmask, std::vector<doub
       if (!g.px && i == g.nxn - 1) {
         dir[n] = 1;
         val[n] = cfg.phi_electrode;
+        elec[n] = 1;
       }
       // touching a conductor cell (in-domain cells only)
       bool touch = false;
@@ -127,6 +135,7 @@ void build_geometry(pic_ctx *c, std::vector<uint8_t> &cellmask, std::vector<doub
       if (touch) {
         dir[n] = 1;
         val[n] = cfg.phi_electrode;
+        elec[n] = 1;
       }
     }
   }
@@ -195,7 +204,15 @@ pic_status validate(const pic_config *cfg) {
   if (cfg->periodic_y && (cfg->ny % 2)) return PIC_EINVAL;
   if (!(cfg->dt > 0) || !(cfg->poisson_rtol > 0)) return PIC_EINVAL;
   if (cfg->poisson_maxit < 1 || cfg->sort_every < 0) return PIC_EINVAL;
-  if (cfg->warm_start < 0 || cfg->warm_start > 2) return PIC_EINVAL;
+  if (cfg->warm_start < 0 || cfg->warm_start > 3) return PIC_EINVAL;
+  if (cfg->warm_start == 3 && !cfg->unet_weights) return PIC_EINVAL;
+  if (!std::isfinite(cfg->phi_rf_amp) || !std::isfinite(cfg->omega_rf)) return PIC_EINVAL;
+  if (cfg->recycle) {
+    const int plasma_rows = cfg->nx - cfg->trench_depth;
+    const int x1 = cfg->source_x1 ? cfg->source_x1 : plasma_rows;
+    if (cfg->source_x0 < 0 || x1 <= cfg->source_x0 || x1 > plasma_rows) return PIC_EINVAL;
+    if (!(cfg->recycle_vth >= 0) || !std::isfinite(cfg->recycle_vth)) return PIC_EINVAL;
+  }
   if (cfg->poisson_method < 0 || cfg->poisson_method > 1) return PIC_EINVAL;
   for (int s = 0; s < 2; ++s) {
     if (cfg->ppc[s] < 1 || cfg->capacity[s] < 0) return PIC_EINVAL;
@@ -216,7 +233,9 @@ pic_status prepare(pic_ctx *c) {
   pic_status st;
   if ((st = check(launch_sort(c))) != PIC_OK) return st;
   c->steps_since_sort = 0;
+  c->needs_sort = 0;
   if ((st = check(launch_particles(c, 1, 0.f, nullptr))) != PIC_OK) return st;
+  if ((st = check(launch_rf_bias(c, 0))) != PIC_OK) return st;
   if ((st = check(launch_rho(c, 0))) != PIC_OK) return st;
   st = poisson_solve(c, true);
   if (st != PIC_OK) return st;
@@ -259,6 +278,7 @@ pic_status step_kernels(pic_ctx *c, bool sorting, cudaEvent_t *ev) {
   cudaEventRecord(ev[1], c->stream);
   if ((st = check(launch_particles(c, 0, 1.f, nullptr))) != PIC_OK) return st;
   cudaEventRecord(ev[2], c->stream);
+  if ((st = check(launch_rf_bias(c, 1))) != PIC_OK) return st;
   if ((st = check(launch_rho(c, 1))) != PIC_OK) return st;
   cudaEventRecord(ev[3], c->stream);
   st = poisson_solve(c, c->cfg.warm_start == 0);
@@ -291,6 +311,7 @@ cudaError_t capture_step(pic_ctx *c, cudaGraph_t g, std::vector<cudaGraphNode_t>
     rec(1);
     launch_particles(c, 0, 1.f, nullptr);
     rec(2);
+    launch_rf_bias(c, 1);
     if (!rho_in_solve(c)) launch_rho(c, 1, c->cfg.warm_start == 1);   // opens the solve captured next
     rec(3);
     e = note(capture_leaves(c->stream, deps), "capture: particle phase");
@@ -535,7 +556,11 @@ pic_status pic_batch_step(pic_batch *b, int32_t nsteps) {
     for (pic_ctx *c : b->m) c->steps_since_sort = 0;
   }
   for (int32_t k = 0; k < nsteps; ++k) {
-    const int sorting = b->steps_since_sort >= b->sort_every ? 1 : 0;
+    int sorting = b->steps_since_sort >= b->sort_every ? 1 : 0;
+    for (pic_ctx *c : b->m) {   // a member restored from a checkpoint
+      if (c->needs_sort) sorting = 1;
+      c->needs_sort = 0;
+    }
     if (check(batch_graph(b, sorting)) != PIC_OK) return PIC_ECUDA;
     if (note(cudaGraphLaunch(b->gexec[sorting], b->stream), "ensemble graph launch") != cudaSuccess)
       return PIC_ECUDA;
@@ -708,6 +733,53 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
   c->d_hits = (pic_hit *)A(std::max<int64_t>(cfg->hit_capacity, 1) * sizeof(pic_hit));
   c->d_nhits = (unsigned long long *)A(8);
   c->d_status = (uint32_t *)A(4);
+  c->src_x0 = cfg->source_x0;
+  c->src_x1 = cfg->source_x1 ? cfg->source_x1 : cfg->nx - cfg->trench_depth;
+  // RF bias: the electrode's Dirichlet nodes, and the free nodes next to them
+  // with their number of electrode neighbours (the lift changes by that
+  // count times the RF part)
+  std::vector<int32_t> rf_dir, rf_lift;
+  std::vector<float2> rf_g0;
+  std::vector<float> rf_cnt, rf_lift0;
+  if (cfg->phi_rf_amp != 0.0) {
+    for (int i = 0; i < g.nxn; ++i)
+      for (int j = 0; j < g.nyn; ++j) {
+        const size_t n = size_t(i) * g.nyn + j;
+        if (!(c->h_nodeflags[n] & kFree)) {
+          if (c->h_electrode[n]) {
+            rf_dir.push_back(int32_t(n));
+            rf_g0.push_back(pair_split(c->h_g[n]));
+          }
+          continue;
+        }
+        const int nb[4][2] = {{i - 1, j}, {i + 1, j}, {i, j - 1}, {i, j + 1}};
+        int cnt = 0;
+        for (auto &q : nb) {
+          int a = q[0], b = q[1];
+          if (g.px) a = (a + g.nxn) % g.nxn;
+          if (g.py) b = (b + g.nyn) % g.nyn;
+          if (a < 0 || a >= g.nxn || b < 0 || b >= g.nyn) continue;
+          const size_t m = size_t(a) * g.nyn + b;
+          if (!(c->h_nodeflags[m] & kFree) && c->h_electrode[m]) ++cnt;
+        }
+        if (cnt) {
+          rf_lift.push_back(int32_t(n));
+          rf_cnt.push_back(float(cnt));
+          rf_lift0.push_back(float(lift[n]));
+        }
+      }
+  }
+  c->n_rf_dir = int(rf_dir.size());
+  c->n_rf_lift = int(rf_lift.size());
+  if (c->n_rf_dir) {
+    c->d_rf_dir = (int32_t *)A(rf_dir.size() * 4);
+    c->d_rf_g0 = (float2 *)A(rf_g0.size() * 8);
+  }
+  if (c->n_rf_lift) {
+    c->d_rf_lift = (int32_t *)A(rf_lift.size() * 4);
+    c->d_rf_cnt = (float *)A(rf_cnt.size() * 4);
+    c->d_rf_lift0 = (float *)A(rf_lift0.size() * 4);
+  }
   c->stage_n = std::min<int64_t>(kStageParticles,
                                  std::max<int64_t>(std::max(cfg->capacity[0], cfg->capacity[1]), 1));
   c->d_stage = (double *)A(size_t(c->stage_n) * 5 * 8);
@@ -729,6 +801,15 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
     cudaMemcpyAsync(c->d_lift, liftf.data(), nn * 4, cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(c->d_g, gp.data(), nn * 8, cudaMemcpyHostToDevice, c->stream);
     cudaMemcpyAsync(c->d_phi, gp.data(), nn * 8, cudaMemcpyHostToDevice, c->stream);
+    if (c->n_rf_dir) {
+      cudaMemcpyAsync(c->d_rf_dir, rf_dir.data(), rf_dir.size() * 4, cudaMemcpyHostToDevice, c->stream);
+      cudaMemcpyAsync(c->d_rf_g0, rf_g0.data(), rf_g0.size() * 8, cudaMemcpyHostToDevice, c->stream);
+    }
+    if (c->n_rf_lift) {
+      cudaMemcpyAsync(c->d_rf_lift, rf_lift.data(), rf_lift.size() * 4, cudaMemcpyHostToDevice, c->stream);
+      cudaMemcpyAsync(c->d_rf_cnt, rf_cnt.data(), rf_cnt.size() * 4, cudaMemcpyHostToDevice, c->stream);
+      cudaMemcpyAsync(c->d_rf_lift0, rf_lift0.data(), rf_lift0.size() * 4, cudaMemcpyHostToDevice, c->stream);
+    }
     cudaStreamSynchronize(c->stream);   // the host vectors go out of scope
   }
   cudaMemsetAsync(c->d_acc, 0, 2 * nn * 8, c->stream);
@@ -766,8 +847,55 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
   c->fields_dirty = 1;
   c->needs_sort = 1;
   c->step = 0;
+  if (cfg->warm_start == 3) {
+    // the learned guess from a parameter file: a network of this grid's shape
+    c->cfg.warm_start = 1;
+    c->cfg.unet_weights = nullptr;   // the caller's string is not kept
+    pic_unet *net = nullptr;
+    st = pic_unet_create(1, (g.nxn + 7) / 8 * 8, g.nyn, c->stream, &net);
+    if (st == PIC_OK) st = pic_unet_load(net, cfg->unet_weights);
+    if (st == PIC_OK) st = pic_set_learned_start(c, net);
+    pic_unet_free(net);
+    if (st != PIC_OK) {
+      pic_free(c);
+      return st;
+    }
+  }
   *out = c;
   return PIC_OK;
+}
+
+pic_status pic_set_learned_start(pic_ctx *c, const pic_unet *net) {
+  if (!c || !net) return PIC_EINVAL;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
+  const int hpad = (c->g.nxn + 7) / 8 * 8;
+  if (unet_batch(net) != 1 || unet_height(net) < hpad || unet_width(net) != c->g.nyn) return PIC_EINVAL;
+  pic_status st = PIC_OK;
+  if (!c->net) {
+    st = pic_unet_create(1, unet_height(net), c->g.nyn, c->stream, &c->net);
+    if (st != PIC_OK) return st;
+    c->d_net_x = (float *)dev_alloc(c, size_t(unet_height(net)) * c->g.nyn * 2 * 4);
+    if (!c->d_net_x) return PIC_ENOMEM;
+  }
+  if (unet_height(c->net) != unet_height(net)) return PIC_EINVAL;
+  if ((st = unet_copy_params(c->net, net)) != PIC_OK) return st;
+  if ((st = ensure_vacuum_potential(c)) != PIC_OK) return st;
+  // the step graphs hold the old initial guess: capture them again
+  for (int k = 0; k < 2; ++k)
+    for (int v = 0; v < 2; ++v) {
+      if (c->gexec[k][v]) cudaGraphExecDestroy(c->gexec[k][v]);
+      if (c->graph[k][v]) cudaGraphDestroy(c->graph[k][v]);
+      c->gexec[k][v] = nullptr;
+      c->graph[k][v] = nullptr;
+    }
+  c->cfg.warm_start = 3;
+  return PIC_OK;
+}
+
+pic_status pic_learned_target(pic_ctx *c, int32_t hpad, double scale, float *t) {
+  if (!c || !t) return PIC_EINVAL;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
+  return learned_target(c, hpad, scale, t);
 }
 
 pic_status pic_load(pic_ctx *c, int32_t species, int64_t n, const double *x, const double *y,
@@ -853,6 +981,9 @@ pic_status pic_step(pic_ctx *c, int32_t nsteps) {
     else if (c->tune_state == 0) sorting = true;
     else if (c->tune_state == 1) sorting = false;
     else sorting = c->steps_since_sort >= c->sort_interval;
+    // particles restored from a checkpoint are sorted before they move
+    if (c->needs_sort) sorting = true;
+    c->needs_sort = 0;
     // steps of the host loop are always timed; graph steps when timing is on
     // or the sort interval is being tuned
     const bool timed = c->cfg.timing || tuning || !c->cfg.graphs;
@@ -872,7 +1003,8 @@ pic_status pic_step(pic_ctx *c, int32_t nsteps) {
             return PIC_ECUDA;
       }
       // particle kernel, [sort], [density]; the solve's kernels are counted from its totals
-      c->launches += (sorting ? 4 : 0) + (rho_in_solve(c) ? 1 : 2);
+      c->launches += (sorting ? 4 : 0) + (rho_in_solve(c) ? 1 : 2) +
+                     (c->cfg.phi_rf_amp != 0.0 && (c->n_rf_dir || c->n_rf_lift) ? 1 : 0);
       if (note(cudaGraphLaunch(c->gexec[ws][ev], c->stream), "step graph launch") != cudaSuccess)
         return PIC_ECUDA;
       if (sorting) {
@@ -1028,11 +1160,12 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
       if (st != PIC_OK) return st;
       const int64_t live = int64_t(m[s][2]);
       if (!need(5 * live * 8)) return PIC_EINVAL;
-      double *buf = nullptr;
-      unsigned long long *ctr = nullptr;
-      if (cudaMalloc(&buf, size_t(std::max<int64_t>(live, 1)) * 5 * 8) != cudaSuccess) return PIC_ENOMEM;
-      if (cudaMalloc(&ctr, 8) != cudaSuccess) {
-        cudaFree(buf);
+      // temporaries through the context's allocator
+      double *buf = (double *)tmp_alloc(c, size_t(std::max<int64_t>(live, 1)) * 5 * 8);
+      unsigned long long *ctr = (unsigned long long *)tmp_alloc(c, 8);
+      if (!buf || !ctr) {
+        tmp_free(c, buf);
+        tmp_free(c, ctr);
         return PIC_ENOMEM;
       }
       cudaMemsetAsync(ctr, 0, 8, c->stream);
@@ -1040,8 +1173,8 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
       if (e == cudaSuccess)
         e = cudaMemcpyAsync(out, buf, size_t(live) * 5 * 8, cudaMemcpyDeviceToHost, c->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
-      cudaFree(buf);
-      cudaFree(ctr);
+      tmp_free(c, buf);
+      tmp_free(c, ctr);
       if (e != cudaSuccess) return PIC_ECUDA;
       count = live;
       break;
@@ -1121,11 +1254,207 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
   return status_from_bits(bits);
 }
 
+namespace {
+
+// Checkpoint layout (host memory): the header, then per species the live
+// particles in stored form (cell, fx, fy, vx, vy, id arrays), the node
+// arrays (phi, phi of the previous step, E, rho, rho_ext, Dirichlet data as
+// double-float pairs; the lift), the wall and bottom tallies, the hit
+// records kept, and the solver's device scalars.
+struct CkptHeader {
+  char magic[8];
+  int32_t version;
+  int32_t nx, ny, px, py, nxn, nyn;
+  int32_t d_step;
+  int64_t n_live[2];
+  int64_t hits_kept, hits_total;
+  int64_t step;
+  uint32_t status;
+  int32_t pending_kick[2];
+  int32_t reserved;
+  double fe[2];
+};
+constexpr char kCkptMagic[8] = {'P', 'I', 'C', 'G', 'B', 'C', 'K', '1'};
+
+int64_t ckpt_bytes(const pic_ctx *c, const int64_t n_live[2], int64_t hits) {
+  const int64_t nn = int64_t(c->g.nxn) * c->g.nyn;
+  return int64_t(sizeof(CkptHeader)) + 24 * (n_live[0] + n_live[1]) + nn * (6 * 8 + 4) +
+         8 * (2 * PIC_NWALLS + 2 * int64_t(c->g.ny)) + hits * int64_t(sizeof(pic_hit)) +
+         int64_t(sizeof(PoissonState));
+}
+
+// the node arrays of a checkpoint, in order, with their element sizes
+struct NodeArray {
+  void *d;
+  size_t elem;
+};
+std::vector<NodeArray> node_arrays(pic_ctx *c) {
+  return {{c->d_phi, 8}, {c->d_phi_prev, 8}, {c->d_E, 8}, {c->d_rho, 8},
+          {c->d_rho_ext, 8}, {c->d_g, 8}, {c->d_lift, 4}};
+}
+
+}  // namespace
+
+pic_status pic_save(pic_ctx *c, void *buf, int64_t cap_bytes, int64_t *n_out) {
+  if (!c) return PIC_EINVAL;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
+  if (c->fields_dirty) return PIC_ESTATE;   // loaded but not yet brought up to date
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
+  int64_t nslots[2];
+  unsigned long long nh = 0;
+  if (cudaMemcpy(nslots, c->d_nslots, 16, cudaMemcpyDeviceToHost) != cudaSuccess ||
+      cudaMemcpy(&nh, c->d_nhits, 8, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PIC_ECUDA;
+  // live counts: compaction of each species into a temporary device buffer
+  ParticleBuf tmp[2] = {};
+  void *mem[2] = {nullptr, nullptr};
+  unsigned long long *ctr = (unsigned long long *)tmp_alloc(c, 16);
+  pic_status st = ctr ? PIC_OK : PIC_ENOMEM;
+  int64_t n_live[2] = {0, 0};
+  for (int s = 0; s < 2 && st == PIC_OK; ++s) {
+    const int64_t m = std::max<int64_t>(nslots[s], 1);
+    mem[s] = tmp_alloc(c, size_t(m) * 24);
+    if (!mem[s]) {
+      st = PIC_ENOMEM;
+      break;
+    }
+    char *b = (char *)mem[s];
+    tmp[s] = ParticleBuf{(int32_t *)b, (float *)(b + 4 * m), (float *)(b + 8 * m),
+                         (float *)(b + 12 * m), (float *)(b + 16 * m), (uint32_t *)(b + 20 * m)};
+    cudaMemsetAsync(ctr + s, 0, 8, c->stream);
+    if (launch_export_raw(c, s, tmp[s], m, ctr + s) != cudaSuccess) st = PIC_ECUDA;
+  }
+  unsigned long long cnt[2] = {0, 0};
+  if (st == PIC_OK && (cudaMemcpyAsync(cnt, ctr, 16, cudaMemcpyDeviceToHost, c->stream) != cudaSuccess ||
+                       cudaStreamSynchronize(c->stream) != cudaSuccess))
+    st = PIC_ECUDA;
+  n_live[0] = int64_t(cnt[0]);
+  n_live[1] = int64_t(cnt[1]);
+  const int64_t hits = std::min<int64_t>(int64_t(nh), c->cfg.hit_capacity);
+  const int64_t bytes = ckpt_bytes(c, n_live, hits);
+  if (n_out) *n_out = bytes;
+  if (st == PIC_OK && buf && cap_bytes < bytes) st = PIC_EINVAL;
+  if (st == PIC_OK && buf) {
+    char *o = (char *)buf;
+    CkptHeader h;
+    std::memset(&h, 0, sizeof(h));
+    std::memcpy(h.magic, kCkptMagic, 8);
+    h.version = 1;
+    h.nx = c->g.nx;
+    h.ny = c->g.ny;
+    h.px = c->g.px;
+    h.py = c->g.py;
+    h.nxn = c->g.nxn;
+    h.nyn = c->g.nyn;
+    h.n_live[0] = n_live[0];
+    h.n_live[1] = n_live[1];
+    h.hits_kept = hits;
+    h.hits_total = int64_t(nh);
+    h.step = c->step;
+    h.pending_kick[0] = c->pending_kick[0];
+    h.pending_kick[1] = c->pending_kick[1];
+    cudaError_t e = cudaMemcpy(&h.d_step, c->d_step, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(&h.status, c->d_status, 4, cudaMemcpyDeviceToHost);
+    if (e == cudaSuccess) e = cudaMemcpy(h.fe, c->d_fe, 16, cudaMemcpyDeviceToHost);
+    std::memcpy(o, &h, sizeof(h));
+    o += sizeof(h);
+    for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
+      const int64_t m = std::max<int64_t>(nslots[s], 1), n = n_live[s];
+      // the six arrays of the compacted buffer, n elements each
+      for (int k = 0; k < 6 && e == cudaSuccess; ++k) {
+        e = cudaMemcpy(o, (char *)mem[s] + 4 * k * m, size_t(n) * 4, cudaMemcpyDeviceToHost);
+        o += 4 * n;
+      }
+    }
+    const size_t nn = size_t(c->g.nxn) * c->g.nyn;
+    for (const NodeArray &a : node_arrays(c)) {
+      if (e == cudaSuccess) e = cudaMemcpy(o, a.d, nn * a.elem, cudaMemcpyDeviceToHost);
+      o += nn * a.elem;
+    }
+    if (e == cudaSuccess) e = cudaMemcpy(o, c->d_walls, 8 * 2 * PIC_NWALLS, cudaMemcpyDeviceToHost);
+    o += 8 * 2 * PIC_NWALLS;
+    if (e == cudaSuccess) e = cudaMemcpy(o, c->d_bottom, 8 * 2 * size_t(c->g.ny), cudaMemcpyDeviceToHost);
+    o += 8 * 2 * size_t(c->g.ny);
+    if (e == cudaSuccess && hits > 0) e = cudaMemcpy(o, c->d_hits, size_t(hits) * sizeof(pic_hit), cudaMemcpyDeviceToHost);
+    o += size_t(hits) * sizeof(pic_hit);
+    if (e == cudaSuccess) e = cudaMemcpy(o, c->d_ps, sizeof(PoissonState), cudaMemcpyDeviceToHost);
+    if (e != cudaSuccess) st = PIC_ECUDA;
+  }
+  for (int s = 0; s < 2; ++s) tmp_free(c, mem[s]);
+  tmp_free(c, ctr);
+  return st;
+}
+
+pic_status pic_restore(pic_ctx *c, const void *buf, int64_t n_bytes) {
+  if (!c || !buf || n_bytes < int64_t(sizeof(CkptHeader))) return PIC_EINVAL;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
+  CkptHeader h;
+  std::memcpy(&h, buf, sizeof(h));
+  if (std::memcmp(h.magic, kCkptMagic, 8) != 0 || h.version != 1) return PIC_EINVAL;
+  if (h.nx != c->g.nx || h.ny != c->g.ny || h.px != c->g.px || h.py != c->g.py || h.nxn != c->g.nxn ||
+      h.nyn != c->g.nyn)
+    return PIC_EINVAL;
+  for (int s = 0; s < 2; ++s)
+    if (h.n_live[s] < 0 || h.n_live[s] > c->cfg.capacity[s]) return PIC_EOVERFLOW;
+  if (h.hits_kept < 0 || h.hits_kept > c->cfg.hit_capacity || h.hits_total < h.hits_kept) return PIC_EINVAL;
+  if (n_bytes != ckpt_bytes(c, h.n_live, h.hits_kept)) return PIC_EINVAL;
+  if (cudaStreamSynchronize(c->stream) != cudaSuccess) return PIC_ECUDA;
+  const char *o = (const char *)buf + sizeof(h);
+  cudaError_t e = cudaSuccess;
+  for (int s = 0; s < 2 && e == cudaSuccess; ++s) {
+    const ParticleBuf &P = c->pb[s][c->cur[s]];
+    void *dst[6] = {P.cell, P.fx, P.fy, P.vx, P.vy, P.id};
+    const int64_t n = h.n_live[s];
+    for (int k = 0; k < 6; ++k) {
+      if (e == cudaSuccess && n > 0) e = cudaMemcpy(dst[k], o, size_t(n) * 4, cudaMemcpyHostToDevice);
+      o += 4 * n;
+    }
+  }
+  const size_t nn = size_t(c->g.nxn) * c->g.nyn;
+  for (const NodeArray &a : node_arrays(c)) {
+    if (e == cudaSuccess) e = cudaMemcpy(a.d, o, nn * a.elem, cudaMemcpyHostToDevice);
+    o += nn * a.elem;
+  }
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_walls, o, 8 * 2 * PIC_NWALLS, cudaMemcpyHostToDevice);
+  o += 8 * 2 * PIC_NWALLS;
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_bottom, o, 8 * 2 * size_t(c->g.ny), cudaMemcpyHostToDevice);
+  o += 8 * 2 * size_t(c->g.ny);
+  if (e == cudaSuccess && h.hits_kept > 0)
+    e = cudaMemcpy(c->d_hits, o, size_t(h.hits_kept) * sizeof(pic_hit), cudaMemcpyHostToDevice);
+  o += size_t(h.hits_kept) * sizeof(pic_hit);
+  // the solver's scalars, keeping this context's running launch totals
+  PoissonState ps;
+  std::memcpy(&ps, o, sizeof(ps));
+  PoissonState mine;
+  if (e == cudaSuccess) e = cudaMemcpy(&mine, c->d_ps, sizeof(mine), cudaMemcpyDeviceToHost);
+  ps.n_solves = mine.n_solves;
+  ps.sum_outer = mine.sum_outer;
+  ps.sum_total = mine.sum_total;
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_ps, &ps, sizeof(ps), cudaMemcpyHostToDevice);
+  const unsigned long long nh = (unsigned long long)h.hits_total;
+  const int64_t slots[2] = {h.n_live[0], h.n_live[1]};
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_nhits, &nh, 8, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_nslots, slots, 16, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_step, &h.d_step, 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_status, &h.status, 4, cudaMemcpyHostToDevice);
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_fe, h.fe, 16, cudaMemcpyHostToDevice);
+  // no particle kernel has run on the restored particles: no work items yet
+  const int32_t zero = 0;
+  if (e == cudaSuccess) e = cudaMemcpy(c->d_nchunks, &zero, 4, cudaMemcpyHostToDevice);
+  if (e != cudaSuccess) return PIC_ECUDA;
+  c->step = h.step;
+  c->pending_kick[0] = h.pending_kick[0];
+  c->pending_kick[1] = h.pending_kick[1];
+  c->fields_dirty = 0;
+  c->needs_sort = 1;
+  return PIC_OK;
+}
+
 pic_status pic_free(pic_ctx *c) {
   if (!c) return PIC_OK;
   cudaSetDevice(c->dev);
   if (c->stream) cudaStreamSynchronize(c->stream);
-  for (void *p : c->allocs) release(c, p);
+  for (void *p : c->allocs) tmp_free(c, p);
   c->allocs.clear();
   if (c->h_status) cudaFreeHost(c->h_status);
   if (c->h_ps) cudaFreeHost(c->h_ps);
@@ -1141,6 +1470,7 @@ pic_status pic_free(pic_ctx *c) {
   }
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
+  if (c->net) pic_unet_free(c->net);
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return PIC_OK;

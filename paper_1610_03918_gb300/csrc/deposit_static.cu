@@ -15,34 +15,26 @@
 // integers, so the result does not depend on particle order.
 #include <cuda_runtime.h>
 
-#include <mutex>
-
 #include "picgb.h"
 
 namespace {
 
 constexpr long long kStaticMaxNodes = 1ll << 20;   // 8 MiB of 64-bit accumulators
-constexpr int kMaxDevices = 64;
 constexpr int kThreads = 256;
 
 // The scratch.  In host code this name is only a stand-in for the device
 // symbol: its device address comes from cudaGetSymbolAddress below.
 static __device__ __align__(256) unsigned long long g_deposit_scratch[kStaticMaxNodes];
 
-std::mutex g_mu;
-unsigned long long *g_scratch_ptr[kMaxDevices] = {};
-
-// Device address of the scratch on the current device, looked up once per
-// device (with that device current) and cached.
-pic_status scratch_address(int dev, unsigned long long **out) {
-  if (dev < 0 || dev >= kMaxDevices) return PIC_EINVAL;
-  std::lock_guard<std::mutex> lock(g_mu);
-  if (!g_scratch_ptr[dev]) {
-    void *p = nullptr;
-    if (cudaGetSymbolAddress(&p, g_deposit_scratch) != cudaSuccess || !p) return PIC_ECUDA;
-    g_scratch_ptr[dev] = static_cast<unsigned long long *>(p);
-  }
-  *out = g_scratch_ptr[dev];
+// Device address of the scratch in the current context.  It is looked up
+// on every call (a cheap host-side query): a cached address would go stale
+// when the caller switches to another context of the same device (a
+// runtime that drives its own, non-primary context) or after the device
+// was reset and the module loaded again.
+pic_status scratch_address(unsigned long long **out) {
+  void *p = nullptr;
+  if (cudaGetSymbolAddress(&p, g_deposit_scratch) != cudaSuccess || !p) return PIC_ECUDA;
+  *out = static_cast<unsigned long long *>(p);
   return PIC_OK;
 }
 
@@ -101,6 +93,12 @@ int grid_for(long long n) {
   return int(b);
 }
 
+// Launches one kernel and returns the error of this launch alone (the
+// runtime's thread-wide last-error state is neither read nor cleared).
+cudaError_t launch1(const void *k, long long work, void **args, cudaStream_t s) {
+  return cudaLaunchKernel(k, dim3(unsigned(grid_for(work))), dim3(kThreads), args, 0, s);
+}
+
 }  // namespace
 
 extern "C" pic_status pic_deposit_static(int32_t nx, int32_t ny, int32_t periodic_x,
@@ -110,19 +108,21 @@ extern "C" pic_status pic_deposit_static(int32_t nx, int32_t ny, int32_t periodi
   if (nx < 1 || ny < 1 || n < 0 || !rho || (n > 0 && (!x || !y))) return PIC_EINVAL;
   const long long nxn = periodic_x ? nx : (long long)nx + 1;
   const long long nyn = periodic_y ? ny : (long long)ny + 1;
-  const long long nn = nxn * nyn;
+  long long nn = nxn * nyn;
   if (nn > kStaticMaxNodes) return PIC_ESIZE;
-  int dev = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess) return PIC_ECUDA;
   unsigned long long *acc = nullptr;
-  const pic_status st = scratch_address(dev, &acc);
+  const pic_status st = scratch_address(&acc);
   if (st != PIC_OK) return st;
   cudaStream_t s = static_cast<cudaStream_t>(stream);
+  int ix = nx, iy = ny, px = periodic_x ? 1 : 0, py = periodic_y ? 1 : 0, inyn = int(nyn);
+  long long np = n;
+  double scale = weight / 1048576.0;
   // the scratch keeps the previous call's sums: clear the part this call uses
-  k_clear<<<grid_for(nn), kThreads, 0, s>>>(acc, nn);
-  if (n > 0)
-    k_deposit<<<grid_for(n), kThreads, 0, s>>>(x, y, n, nx, ny, periodic_x ? 1 : 0,
-                                               periodic_y ? 1 : 0, int(nyn), acc);
-  k_finish<<<grid_for(nn), kThreads, 0, s>>>(acc, nn, weight / 1048576.0, rho);
-  return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
+  void *a_clear[] = {&acc, &nn};
+  void *a_dep[] = {&x, &y, &np, &ix, &iy, &px, &py, &inyn, &acc};
+  void *a_fin[] = {&acc, &nn, &scale, &rho};
+  if (launch1((const void *)k_clear, nn, a_clear, s) != cudaSuccess) return PIC_ECUDA;
+  if (n > 0 && launch1((const void *)k_deposit, n, a_dep, s) != cudaSuccess) return PIC_ECUDA;
+  if (launch1((const void *)k_finish, nn, a_fin, s) != cudaSuccess) return PIC_ECUDA;
+  return PIC_OK;
 }

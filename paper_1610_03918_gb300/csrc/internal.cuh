@@ -252,12 +252,22 @@ struct pic_ctx {
   bool own_stream;
 
   // geometry
+  int src_x0, src_x1;       // ion recycling source rows [src_x0, src_x1)
   uint8_t *d_cellmask;      // [nx*ny] 1 = plasma
   uint8_t *d_nodeflags;     // [nxn*nyn]
   float *d_lift;            // [nxn*nyn] sum of Dirichlet neighbour values (free nodes; norms only)
   float2 *d_g;              // [nxn*nyn] Dirichlet values (0 at free nodes), double-float
   std::vector<uint8_t> h_nodeflags;
   std::vector<double> h_g;
+  std::vector<uint8_t> h_electrode;   // [nxn*nyn] node held at the electrode potential
+  // RF bias (phi_rf_amp != 0): the electrode's Dirichlet nodes with their
+  // static values, and the free nodes next to them with their count of such
+  // neighbours and their static lift
+  int n_rf_dir, n_rf_lift;
+  int32_t *d_rf_dir;
+  float2 *d_rf_g0;
+  int32_t *d_rf_lift;
+  float *d_rf_cnt, *d_rf_lift0;
 
   // fields
   unsigned long long *d_acc;   // [2][nnodes] fixed-point species weights
@@ -267,6 +277,8 @@ struct pic_ctx {
   float2 *d_phi;               // the potential (Dirichlet values included)
   float2 *d_phi_prev;          // potential of the previous step (extrapolated warm start)
   float2 *d_phiL;              // potential of the empty box (learned warm start), lazily
+  pic_unet *net;               // warm-start network of this context (warm_start 3), owned
+  float *d_net_x;              // its input [hpad][nyn][2]
   float2 *d_E;
   double *d_fe;                // [2]: field energy of E just computed, of E used by last step
 
@@ -348,6 +360,9 @@ namespace picgb {
 
 // api.cu
 void *dev_alloc(pic_ctx *c, size_t bytes);
+// a temporary device buffer through the context's allocator (released by tmp_free)
+void *tmp_alloc(pic_ctx *c, size_t bytes);
+void tmp_free(pic_ctx *c, void *p);
 // records "where: CUDA error string" as the calling thread's last error; returns e
 cudaError_t note(cudaError_t e, const char *where);
 
@@ -360,6 +375,9 @@ cudaError_t launch_load_convert(pic_ctx *c, int s, const double *d_x, const doub
                                 int64_t offset, int64_t n);
 cudaError_t launch_export_state(pic_ctx *c, int s, double *d_out, int64_t n_live,
                                 unsigned long long *d_counter);
+// live particles of species s in stored form, compacted into out (checkpoints)
+cudaError_t launch_export_raw(pic_ctx *c, int s, ParticleBuf out, int64_t cap,
+                              unsigned long long *d_counter);
 // per-block partials [sum vx, sum vy, live] of species s into d_part[3 * nblocks]
 cudaError_t launch_moments(pic_ctx *c, int s, double *d_part, int nblocks);
 
@@ -381,5 +399,21 @@ pic_status ensure_vacuum_potential(pic_ctx *c);
 pic_status learned_input(pic_ctx *c, int hpad, float *x, double *scale);
 pic_status poisson_with_guess(pic_ctx *c, int guess, const float *y, double scale, double *stats);
 cudaError_t launch_field(pic_ctx *c);
+// learned warm start inside the step: absmax of rho, network input, network,
+// guess phi = phi_L + s y on the free nodes (device-side scale)
+cudaError_t launch_learned_guess(pic_ctx *c);
+pic_status learned_target(pic_ctx *c, int hpad, double scale, float *t);
+
+// unet.cu
+void unet_forward_only(pic_unet *u, const float *x);
+const float *unet_output(const pic_unet *u);
+int unet_height(const pic_unet *u);
+int unet_width(const pic_unet *u);
+int unet_batch(const pic_unet *u);
+int unet_forward_kernels();
+pic_status unet_copy_params(pic_unet *dst, const pic_unet *src);
+// RF bias: the electrode's Dirichlet values (in phi and in the Dirichlet
+// data) and the lift at t = (step + advance) dt; no-op without RF
+cudaError_t launch_rf_bias(pic_ctx *c, int advance);
 
 }  // namespace picgb

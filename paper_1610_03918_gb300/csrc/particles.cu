@@ -10,6 +10,7 @@
 #include <cuda_runtime.h>
 
 #include "internal.cuh"
+#include "philox.cuh"
 
 namespace picgb {
 namespace {
@@ -238,6 +239,11 @@ struct PArgs {
   const int32_t *step;
   double *ke_part;
   double *fe;                // [0] energy of the current E, [1] of the E used by the last step
+  // ion recycling: absorbed ions re-enter in cell rows [src_x0, src_x0 + src_rows)
+  int recycle;
+  int src_x0, src_rows;
+  uint2 key;                 // Philox key (the seed)
+  float vth_i;               // thermal speed of the re-entering ions
 };
 
 constexpr int WXc = kTileX + 2 * kHalo;   // window cells
@@ -303,7 +309,7 @@ __device__ __forceinline__ void deposit_shared(uint32_t *sAcc, int li, int lj, i
 // parameter (x face first on a tie).  The first face whose far cell is a
 // conductor or outside a bounded direction absorbs the particle: its wall
 // and bottom-cell tallies and a hit record are written and 1 is returned.
-// A move longer than the walk limit is dropped (status bit, no tally) and 1
+// A move longer than the walk limit is dropped (status bit, no tally) and 2
 // is returned.  Otherwise the cell offset (oi, oj) of the end point is set
 // and 0 returned.  Only particles in cells next to a wall or conductor, or
 // moving more than one cell, come here.
@@ -360,7 +366,29 @@ __device__ __forceinline__ int walk_move(const PArgs &a, int s, int i, int j, fl
   }
   if (oi == cx && oj == cy) return 0;
   atomicOr(a.status, PIC_ST_CFL);   // moved farther than the walk limit: dropped untallied
-  return 1;
+  return 2;
+}
+
+// Ion recycling (Sec. III-A, III-C): the thermal ion that replaces an ion
+// absorbed during step `step` keeps its id and enters at a uniform position
+// of the source rows with a Maxwellian velocity, taken as its v^{n+1/2}.
+// Draws: Philox4x32-10 with key = seed and counter (id, step, tag, k);
+// k = 0 gives the cell (row, column by multiply-high) and the two in-cell
+// offsets (top 24 bits, exact in FP32), k = 1 the Box-Muller pair.
+__device__ __forceinline__ void recycled_ion(const PArgs &a, uint32_t id, int step, int &c, float &fx,
+                                             float &fy, float &vx, float &vy) {
+  const uint4 r = philox4x32_10(make_uint4(id, uint32_t(step), kTagRecycle, 0u), a.key);
+  const uint4 q = philox4x32_10(make_uint4(id, uint32_t(step), kTagRecycle, 1u), a.key);
+  const int i = a.src_x0 + int(below(r.x, uint32_t(a.src_rows)));
+  const int j = int(below(r.y, uint32_t(a.g.ny)));
+  c = pack_cell(i, j);
+  fx = unit24(r.z);
+  fy = unit24(r.w);
+  const float rad = sqrtf(-2.0f * logf(unit24_open(q.x)));
+  float sn, cs;
+  sincospif(2.0f * unit24(q.y), &sn, &cs);
+  vx = a.vth_i * (rad * cs);
+  vy = a.vth_i * (rad * sn);
 }
 
 template <int MODE>
@@ -429,7 +457,15 @@ __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint3
       // all eight neighbours are plasma: no face within one cell can absorb
       oi = cx;
       oj = cy;
-    } else if (walk_move(a, s, i, j, fx, fy, dx, dy, cx, cy, vx1, vy1, id, slot, oi, oj)) {
+    } else if (const int gone = walk_move(a, s, i, j, fx, fy, dx, dy, cx, cy, vx1, vy1, id, slot, oi, oj)) {
+      if (gone == 1 && s == 1 && a.recycle) {
+        // tallied above; a thermal ion takes its place and joins the deposit
+        recycled_ion(a, id[slot], *a.step, c, fx, fy, vx, vy);
+        int w00, w01, w10, w11;
+        cic_weights(fx, fy, w00, w01, w10, w11);
+        deposit_global(a, acc, cell_i(c), cell_j(c), w00, w01, w10, w11);
+        return;
+      }
       c = -1;   // absorbed and tallied, or moved beyond the walk limit
       return;
     }
@@ -638,6 +674,35 @@ __global__ void k_export(ParticleBuf P, Geom g, const int64_t *nslots_p, double 
   }
 }
 
+// Live particles of one species in their stored form (cell, offsets,
+// velocities, id), compacted into out (a checkpoint); order arbitrary.
+__global__ void k_export_raw(ParticleBuf P, const int64_t *nslots_p, ParticleBuf out, int64_t cap,
+                             unsigned long long *counter) {
+  const int64_t nslots = *nslots_p;
+  const int lane = threadIdx.x & 31;
+  const int64_t warp = (int64_t(blockIdx.x) * blockDim.x + threadIdx.x) >> 5;
+  const int64_t nwarps = (int64_t(gridDim.x) * blockDim.x) >> 5;
+  for (int64_t base = warp * 32; base < nslots; base += nwarps * 32) {
+    const int64_t p = base + lane;
+    const int c = p < nslots ? P.cell[p] : -1;
+    const unsigned live = __ballot_sync(0xffffffffu, c >= 0);
+    unsigned long long b = 0;
+    if (lane == 0 && live) b = atomicAdd(counter, (unsigned long long)__popc(live));
+    b = __shfl_sync(0xffffffffu, b, 0);
+    if (c >= 0) {
+      const int64_t d = int64_t(b) + __popc(live & ((1u << lane) - 1u));
+      if (d < cap) {
+        out.cell[d] = c;
+        out.fx[d] = P.fx[p];
+        out.fy[d] = P.fy[p];
+        out.vx[d] = P.vx[p];
+        out.vy[d] = P.vy[p];
+        out.id[d] = P.id[p];
+      }
+    }
+  }
+}
+
 // per-block partial sums of [vx, vy, live] of one species
 __global__ void k_moments(ParticleBuf P, const int64_t *nslots_p, double *part) {
   const int64_t nslots = *nslots_p;
@@ -734,6 +799,11 @@ cudaError_t launch_particles(pic_ctx *c, int mode, float kick_factor, const int 
   a.step = c->d_step;
   a.ke_part = c->d_ke_part;
   a.fe = c->d_fe;
+  a.recycle = c->cfg.recycle ? 1 : 0;
+  a.src_x0 = c->src_x0;
+  a.src_rows = c->src_x1 - c->src_x0;
+  a.key = make_uint2(uint32_t(c->cfg.seed), uint32_t(c->cfg.seed >> 32));
+  a.vth_i = float(c->cfg.recycle_vth);
   const int grid = particle_grid(c);
   switch (mode) {
     case 0: k_particles<0><<<grid, kParticleThreads, 0, c->stream>>>(a); break;
@@ -758,6 +828,13 @@ cudaError_t launch_export_state(pic_ctx *c, int s, double *d_out, int64_t cap,
                                 unsigned long long *d_counter) {
   k_export<<<c->num_sms * 4, 256, 0, c->stream>>>(c->pb[s][c->cur[s]], c->g, c->d_nslots + s,
                                                    d_out, cap, d_counter);
+  return cudaGetLastError();
+}
+
+cudaError_t launch_export_raw(pic_ctx *c, int s, ParticleBuf out, int64_t cap,
+                              unsigned long long *d_counter) {
+  k_export_raw<<<c->num_sms * 4, 256, 0, c->stream>>>(c->pb[s][c->cur[s]], c->d_nslots + s, out, cap,
+                                                       d_counter);
   return cudaGetLastError();
 }
 

@@ -1882,6 +1882,66 @@ cudaError_t launch_field(pic_ctx *c) {
   return cudaGetLastError();
 }
 
+namespace {
+
+struct RFArgs {
+  const int32_t *dir;        // the electrode's Dirichlet nodes
+  const float2 *g0;          // their static values
+  int ndir;
+  const int32_t *lnodes;     // free nodes next to them
+  const float *cnt;          // their number of electrode neighbours
+  const float *lift0;        // their static lift
+  int nlift;
+  float2 *phi, *gval;
+  float *lift;
+  const int32_t *step;
+  int advance;
+  double dt, amp, omega;
+};
+
+// RF bias (Sec. III-B): the electrode value at t = (step + advance) dt is the
+// static value plus amp sin(omega t), written into the potential's and the
+// Dirichlet data's electrode nodes; the lift of their free neighbours (used
+// only for ||b||) follows.
+__global__ void k_rf_bias(RFArgs a) {
+  pdl_enter();
+  const double t = double(*a.step + a.advance) * a.dt;
+  const double v = a.amp * sin(a.omega * t);
+  const float2 vp = pair_split(v);
+  GRID_STRIDE(k, a.ndir) {
+    const float2 gv = pair_add(a.g0[k], vp);
+    a.phi[a.dir[k]] = gv;
+    a.gval[a.dir[k]] = gv;
+  }
+  GRID_STRIDE(k, a.nlift) a.lift[a.lnodes[k]] = a.lift0[k] + float(v) * a.cnt[k];
+}
+
+}  // namespace
+
+cudaError_t launch_rf_bias(pic_ctx *c, int advance) {
+  if (c->cfg.phi_rf_amp == 0.0 || (c->n_rf_dir == 0 && c->n_rf_lift == 0)) return cudaSuccess;
+  RFArgs a;
+  a.dir = c->d_rf_dir;
+  a.g0 = c->d_rf_g0;
+  a.ndir = c->n_rf_dir;
+  a.lnodes = c->d_rf_lift;
+  a.cnt = c->d_rf_cnt;
+  a.lift0 = c->d_rf_lift0;
+  a.nlift = c->n_rf_lift;
+  a.phi = c->d_phi;
+  a.gval = c->d_g;
+  a.lift = c->d_lift;
+  a.step = c->d_step;
+  a.advance = advance;
+  a.dt = c->cfg.dt;
+  a.amp = c->cfg.phi_rf_amp;
+  a.omega = c->cfg.omega_rf;
+  const int n = std::max(a.ndir, a.nlift);
+  launch(k_rf_bias, std::max(1, std::min(64, (n + kThreads - 1) / kThreads)), kThreads, 0, c->stream, a);
+  c->launches += 1;
+  return cudaGetLastError();
+}
+
 pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
   FineArgs a = fine_args(c);
   const MGArgs m = mg_args(c);
@@ -1893,6 +1953,8 @@ pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
   } else if (c->cfg.warm_start == 2) {
     launch(k_extrapolate, nb, kThreads, 0, c->stream, a);
     c->launches += 1;
+  } else if (c->cfg.warm_start == 3) {
+    if (launch_learned_guess(c) != cudaSuccess) return PIC_ECUDA;
   }
   launch(k_outer_init, 1, 1, 0, c->stream, c->d_ps);
   c->launches += 1;
@@ -2009,6 +2071,7 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   CK(cap_begin(s, top, deps));
   if (c->cfg.warm_start == 0) launch(k_phi_reset, nb, kThreads, 0, s, a);
   if (c->cfg.warm_start == 2) launch(k_extrapolate, nb, kThreads, 0, s, a);
+  if (c->cfg.warm_start == 3) CK(launch_learned_guess(c));
   // (with the previous step's potential as the guess the density kernel just
   // before opened the solve)
   if (c->cfg.warm_start != 1) launch(k_outer_init, 1, 1, 0, s, c->d_ps);
@@ -2069,7 +2132,8 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
 // launched (graph mode; every outer pass takes at least one inner iteration).
 int64_t poisson_kernel_count(pic_ctx *c, int64_t S, int64_t O, int64_t I) {
   // final resid, and unless the density kernel opens the solve: guess and init
-  const int64_t per_solve = 1 + (c->cfg.warm_start != 1 ? 2 : 0);
+  int64_t per_solve = 1 + (c->cfg.warm_start != 1 ? 2 : 0);
+  if (c->cfg.warm_start == 3) per_solve += 2 + unet_forward_kernels();   // absmax, input, network
   if (c->fp.enabled)   // per pass: resid, direct solve (which corrects phi)
     return S * per_solve + O * (c->fp.kernels + 1);
   // a V-cycle with w = A z and the inner products: fused into its last kernel unless lc = 0
@@ -2113,6 +2177,24 @@ __global__ void k_guess_learned(float2 *phi, const float2 *phiL, const uint8_t *
   GRID_STRIDE(n, nn) {
     if (flags[n] & kFree) phi[n] = pair_split(pair_join(phiL[n]) + scale * double(y[n]));
   }
+}
+
+// the same with the scale s = max |rho| read on the device (the in-step guess)
+__global__ void k_guess_learned_dev(float2 *phi, const float2 *phiL, const uint8_t *flags, const float *y,
+                                    const unsigned int *smax, int nn) {
+  pdl_enter();
+  const double s = double(fmaxf(__uint_as_float(*smax), 1e-30f));
+  GRID_STRIDE(n, nn) {
+    if (flags[n] & kFree) phi[n] = pair_split(pair_join(phiL[n]) + s * double(y[n]));
+  }
+}
+
+// training target of the warm-start network: (phi - phi_L) / s on the nodes,
+// 0 on the padding rows
+__global__ void k_learned_target(const float2 *phi, const float2 *phiL, int nn, int npad, double inv_s,
+                                 float *t) {
+  pdl_enter();
+  GRID_STRIDE(n, npad) t[n] = n < nn ? float((pair_join(phi[n]) - pair_join(phiL[n])) * inv_s) : 0.f;
 }
 
 }  // namespace
@@ -2167,6 +2249,33 @@ pic_status learned_input(pic_ctx *c, int hpad, float *x, double *scale) {
   std::memcpy(&f, &bits, 4);
   *scale = std::max(double(f), 1e-30);
   return PIC_OK;
+}
+
+pic_status learned_target(pic_ctx *c, int hpad, double scale, float *t) {
+  const int nn = c->g.nxn * c->g.nyn;
+  if (hpad < c->g.nxn || !(scale > 0)) return PIC_EINVAL;
+  const pic_status st = ensure_vacuum_potential(c);
+  if (st != PIC_OK) return st;
+  launch(k_learned_target, c->red.nblocks, kThreads, 0, c->stream, c->d_phi, c->d_phiL, nn,
+         hpad * c->g.nyn, 1.0 / scale, t);
+  return cudaStreamSynchronize(c->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+// The learned initial guess inside the step, all on the device: s = max |rho|,
+// the network's input, its forward pass, phi = phi_L + s y on the free nodes.
+cudaError_t launch_learned_guess(pic_ctx *c) {
+  const int nn = c->g.nxn * c->g.nyn;
+  const int hpad = unet_height(c->net);
+  unsigned int *smax = reinterpret_cast<unsigned int *>(c->red.ticket) + 8;   // spare word
+  cudaMemsetAsync(smax, 0, 4, c->stream);
+  launch(k_absmax, c->red.nblocks, kThreads, 0, c->stream, c->d_rho, nn, smax);
+  launch(k_learned_input, c->red.nblocks, kThreads, 0, c->stream, c->d_rho, c->d_nodeflags, c->g.nxn,
+         c->g.nyn, hpad, smax, c->d_net_x);
+  unet_forward_only(c->net, c->d_net_x);
+  launch(k_guess_learned_dev, c->red.nblocks, kThreads, 0, c->stream, c->d_phi, c->d_phiL, c->d_nodeflags,
+         unet_output(c->net), smax, nn);
+  c->launches += 3 + unet_forward_kernels();
+  return cudaGetLastError();
 }
 
 pic_status poisson_with_guess(pic_ctx *c, int guess, const float *y, double scale, double *stats) {

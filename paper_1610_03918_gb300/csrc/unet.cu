@@ -21,11 +21,13 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
 #include <cstring>
 #include <new>
 #include <vector>
 
 #include "internal.cuh"
+#include "philox.cuh"
 
 namespace picgb {
 namespace unet {
@@ -507,6 +509,20 @@ __global__ void k_w_fold(const float *gc, float *gm, int cout, int ci_m, int ci_
   }
 }
 
+// He initialisation (He, Zhang, Ren and Sun, ICCV 2015): w ~ N(0, gain /
+// fan_in) with gain 2 for layers whose output goes through a ReLU and 1 for
+// the linear head.  Element e of layer `layer` draws Philox4x32-10 with
+// counter (e, layer, init tag, 0) and takes the cosine half of one
+// Box-Muller pair.
+__global__ void k_he_init(float *w, long long n, float std, uint2 key, uint32_t layer) {
+  for (long long e = blockIdx.x * (long long)blockDim.x + threadIdx.x; e < n;
+       e += (long long)gridDim.x * blockDim.x) {
+    const uint4 r = philox4x32_10(make_uint4(uint32_t(e), layer, kTagInit, 0u), key);
+    const float rad = sqrtf(-2.0f * logf(unit24_open(r.x)));
+    w[e] = std * (rad * cospif(2.0f * unit24(r.y)));
+  }
+}
+
 inline int gridn(long long n, int t = 256) {
   long long b = (n + t - 1) / t;
   return int(b < 1 ? 1 : (b > 65535 * 8 ? 65535 * 8 : b));
@@ -911,6 +927,51 @@ pic_status pic_unet_train_step(pic_unet *u, const float *x, const float *t, floa
   return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }
 
+pic_status pic_unet_init(pic_unet *u, uint64_t seed) {
+  if (!u) return PIC_EINVAL;
+  const uint2 key = make_uint2(uint32_t(seed), uint32_t(seed >> 32));
+  cudaMemsetAsync(u->P, 0, size_t(u->nparam) * 4, u->stream);   // biases 0
+  uint32_t layer = 0;
+  for (auto &c : u->conv) {
+    const long long n = (long long)c.cout * 9 * c.cin_m;
+    k_he_init<<<gridn(n), 256, 0, u->stream>>>(u->P + c.w_off, n, std::sqrt(2.0f / (9.0f * c.cin_m)),
+                                                key, layer++);
+  }
+  for (int l = 2; l >= 0; --l) {
+    const pic_unet::Up &up = u->up[l];
+    const long long n = 4LL * up.cin * up.cout;
+    k_he_init<<<gridn(n), 256, 0, u->stream>>>(u->P + up.w_off, n, std::sqrt(2.0f / up.cin), key, layer++);
+  }
+  k_he_init<<<1, 256, 0, u->stream>>>(u->P + u->head_w, kC[0], std::sqrt(1.0f / kC[0]), key, layer++);
+  cudaMemsetAsync(u->M, 0, size_t(u->nparam) * 4, u->stream);
+  cudaMemsetAsync(u->V, 0, size_t(u->nparam) * 4, u->stream);
+  u->step = 0;
+  weights_to_bf16(u);
+  return cudaStreamSynchronize(u->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+pic_status pic_unet_save(pic_unet *u, const char *path) {
+  if (!u || !path) return PIC_EINVAL;
+  std::vector<float> h(size_t(u->nparam));
+  const pic_status st = pic_unet_get_params(u, h.data());
+  if (st != PIC_OK) return st;
+  std::FILE *f = std::fopen(path, "wb");
+  if (!f) return PIC_EINVAL;
+  const size_t w = std::fwrite(h.data(), 4, h.size(), f);
+  return (std::fclose(f) == 0 && w == h.size()) ? PIC_OK : PIC_EINVAL;
+}
+
+pic_status pic_unet_load(pic_unet *u, const char *path) {
+  if (!u || !path) return PIC_EINVAL;
+  std::FILE *f = std::fopen(path, "rb");
+  if (!f) return PIC_EINVAL;
+  std::vector<float> h(size_t(u->nparam) + 1);
+  const size_t r = std::fread(h.data(), 4, h.size(), f);
+  std::fclose(f);
+  if (r != size_t(u->nparam)) return PIC_EINVAL;   // too short, or longer than this network
+  return pic_unet_set_params(u, h.data());
+}
+
 pic_status pic_unet_free(pic_unet *u) {
   if (!u) return PIC_OK;
   if (u->stream) cudaStreamSynchronize(u->stream);
@@ -920,3 +981,26 @@ pic_status pic_unet_free(pic_unet *u) {
 }
 
 }  // extern "C"
+
+namespace picgb {
+
+// y = U(x) queued on the net's stream; the output stays in the net's buffer.
+void unet_forward_only(pic_unet *u, const float *x) { unet::forward(u, x); }
+const float *unet_output(const pic_unet *u) { return u->y; }
+int unet_height(const pic_unet *u) { return u->H; }
+int unet_width(const pic_unet *u) { return u->W; }
+int unet_batch(const pic_unet *u) { return u->B; }
+// kernels one forward launches: the input conversion, 14 convolutions, 3
+// pools, 3 transposed convolutions and the head
+int unet_forward_kernels() { return 1 + 14 + 3 + 3 + 1; }
+// copies the FP32 parameters of src into dst (same architecture) on dst's stream
+pic_status unet_copy_params(pic_unet *dst, const pic_unet *src) {
+  if (dst->nparam != src->nparam) return PIC_EINVAL;
+  if (cudaMemcpyAsync(dst->P, src->P, size_t(src->nparam) * 4, cudaMemcpyDeviceToDevice, dst->stream) !=
+      cudaSuccess)
+    return PIC_ECUDA;
+  unet::weights_to_bf16(dst);
+  return cudaStreamSynchronize(dst->stream) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+}  // namespace picgb

@@ -19,18 +19,14 @@ def padded_rows(nxn: int) -> int:
 
 def dump_pairs(sim, steps: int, every: int):
     """Advance `sim` by `steps` steps; every `every` steps record a training
-    pair (x [hpad, nyn, 2], target [hpad, nyn]) as torch CUDA tensors."""
-    import torch
+    pair (x [hpad, nyn, 2], target [hpad, nyn]) as torch CUDA tensors, both
+    formed by the library's kernels."""
     hpad = padded_rows(sim.nxn)
-    phiL = torch.tensor(sim.phi_vacuum(), dtype=torch.float64, device="cuda")
     pairs = []
     for k in range(steps // every):
         sim.step(every)
         x, s = sim.learned_input(hpad)
-        phi = torch.tensor(sim.phi(), dtype=torch.float64, device="cuda")
-        t = torch.zeros((hpad, sim.nyn), dtype=torch.float32, device="cuda")
-        t[: sim.nxn] = ((phi - phiL) / s).to(torch.float32)
-        pairs.append((x[0].clone(), t))
+        pairs.append((x[0], sim.learned_target(hpad, s)))
     return pairs
 
 

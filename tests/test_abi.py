@@ -75,3 +75,16 @@ def test_batch_init_rejects_mixed_sort_schedules_without_gpu(lib):
         pg.Batch([synth.small_trench(sort_every=8), synth.small_trench(sort_every=4)],
                  torch_memory=False)
     assert e.value.code == pg.PIC_EINVAL
+
+
+def test_init_rejects_bad_recycling_source_without_gpu(lib):
+    import paper_1610_03918_gb300 as pg
+    import synth
+    ctx = ctypes.c_void_p()
+    for x0, x1 in ((10, 5), (-1, 5), (0, 60)):     # empty, negative, into the electrode
+        w = synth.small_trench(nx=64, ny=32, depth=16).replace(recycle=True, source_x0=x0,
+                                                                 source_x1=x1)
+        cfg = pg.make_config(w)
+        assert pg.load_library().pic_init(ctypes.byref(cfg), ctypes.byref(ctx)) == pg.PIC_EINVAL
+    cfg = pg.make_config(synth.small_trench().replace(phi_rf_amp=float("nan"), omega_rf=0.1))
+    assert pg.load_library().pic_init(ctypes.byref(cfg), ctypes.byref(ctx)) == pg.PIC_EINVAL

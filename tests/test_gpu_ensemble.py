@@ -8,6 +8,8 @@ import pytest
 
 import synth
 
+from gpu_helpers import parity_post, parity_pre
+
 pytestmark = pytest.mark.gpu
 
 
@@ -59,6 +61,35 @@ def test_batch_matches_solo_runs_bitwise(lib):
     t = batch.timing()
     batch.close()
     assert t["steps"] == 0 or t["ms"] >= 0
+
+
+def test_batch_members_match_oracle_per_step(lib):
+    # members of different grid sizes and trench widths, each checked
+    # against the FP64 oracle step by step by the parity protocol (the
+    # oracle restarts from the member's state before every step)
+    pg = lib
+    ws = [synth.small_trench(nx=72, ny=40, depth=20, width=6, ppc=8, seed=51),
+          synth.small_trench(nx=48, ny=64, depth=12, width=3, ppc=8, seed=52),
+          synth.bounded_square_256(nx=37, ny=30, ppc=6, seed=53)]
+    ws = [w.replace(sort_every=2, poisson_rtol=1e-10) for w in ws]
+    loads = [[synth.maxwellian_load(w, s) for s in (0, 1)] for w in ws]
+    batch = pg.Batch(ws, capacities=[max(len(p[0]), len(p[1])) for p in loads])
+    for m, p in zip(batch.members, loads):
+        for s in (0, 1):
+            m.load_particles(s, p[s], v_at_t0=True)
+    batch.step(0)
+    ties = 0
+    for k in range(3):                 # crosses a sort (every 2 steps)
+        pres = [parity_pre(w, m, k) for w, m in zip(ws, batch.members)]
+        batch.step(1)
+        for w, m, pre in zip(ws, batch.members, pres):
+            t, os_ = parity_post(w, m, pre, k)
+            ties += t
+            e = m.energy()
+            assert e[0] == pytest.approx(os_.ke[0], rel=1e-5)
+            assert e[2] == pytest.approx(os_.fe, rel=1e-5)
+    assert ties <= 2
+    batch.close()
 
 
 def test_solo_runs_are_bitwise_reproducible(lib):

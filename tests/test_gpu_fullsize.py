@@ -12,7 +12,8 @@ from oracle import poisson as opoisson
 from oracle import push as opush
 from oracle.geometry import from_workload
 
-from gpu_helpers import POS_TOL, RHO_TOL, VEL_TOL, FIELD_TOL, face_distance
+from gpu_helpers import (POS_TOL, RHO_TOL, VEL_TOL, FIELD_TOL, check_gpu_classification,
+                         face_distance)
 
 pytestmark = pytest.mark.gpu
 
@@ -80,19 +81,34 @@ def test_fullsize_push_sampled(full):
     Ex, Ey = sim.efield()
     before = [sim.state(s) for s in (0, 1)]
     walls0, live0 = sim.counts()
+    step = int(sim.energy()[3]) + 1      # index of the step about to run
     sim.step(1)
     walls1, live1 = sim.counts()
     # particle number: every particle is either live or tallied on a wall
     for s in (0, 1):
         assert live1[s] + (walls1[s] - walls0[s]).sum() == live0[s]
     rng = np.random.default_rng(11)
+    hits = sim.hits()
+    after_all = [sim.state(s) for s in (0, 1)]
+    sample_b, sample_a = [], []
+    for s in (0, 1):
+        # protocol part (ii) on a sample of 200k particles per species,
+        # grazing moves included: the oracle's classifier on the GPU's own
+        # positions decides every particle as the GPU did
+        b = before[s]
+        pick = rng.choice(b.shape[1], 200000, replace=False)
+        sample_b.append(b[:, pick])
+        sample_a.append(after_all[s][:, np.isin(after_all[s][4], b[4, pick])])
+    ids = np.concatenate([sample_b[0][4], sample_b[1][4] + 2 ** 33])
+    hsel = hits[np.isin(hits["id"].astype(np.int64) + hits["species"].astype(np.int64) * 2 ** 33, ids)]
+    assert check_gpu_classification(w, sample_b, sample_a, hsel, step, None, None) <= 2
     for s in (0, 1):
         b = before[s]
         pick = rng.choice(b.shape[1], 20000, replace=False)
         x, y, vx, vy, ids = b[0, pick], b[1, pick], b[2, pick], b[3, pick], b[4, pick]
         x1, y1, vx1, vy1, alive, wall, wcell = opush.leapfrog(
             geom, w.alpha[s], w.dt, x, y, vx, vy, Ex, Ey)
-        after = sim.state(s)
+        after = after_all[s]
         order = np.argsort(after[4])
         pos = np.searchsorted(after[4][order], ids)
         pos = np.minimum(pos, after.shape[1] - 1)

@@ -9,8 +9,8 @@ from oracle import field as ofield
 from oracle import poisson as opoisson
 from oracle.geometry import from_workload
 
-from gpu_helpers import (FIELD_TOL, RHO_TOL, compare_states, compare_states_grazing, gpu_sim,
-                         load_both, off_face_state, oracle_sim, oracle_state, vacuum_field)
+from gpu_helpers import (FIELD_TOL, RHO_TOL, compare_states, gpu_sim, load_both, off_face_state,
+                         oracle_sim, oracle_state, step_parity_once, vacuum_field)
 
 pytestmark = pytest.mark.gpu
 
@@ -236,37 +236,25 @@ def test_direct_solver_applies_only_to_its_geometry():
 @pytest.mark.parametrize("name,graphs", [(n, True) for n in SMALL] + [("trench", False)] +
                          [("trench64", True), ("trench64", False)])
 def test_step_by_step_parity(name, graphs):
-    """Each step starts both sides from the GPU's state; the oracle recomputes
-    its own fields from it.  graphs=False drives the same kernels from the
-    host loop instead of the captured step graph."""
+    """Each step starts the oracle from the GPU's state (its own fields
+    recomputed from it).  After the step: states agree (moves ending within
+    1e-5 of a face may be decided differently by FP32 and FP64), the oracle's
+    classifier on the GPU's own positions reproduces the GPU's absorptions,
+    walls, wall cells and tallies bit for bit, and the GPU's rho is the
+    oracle deposit of the GPU's state within 1e-5 of max |rho|.  graphs=False
+    drives the same kernels from the host loop instead of the captured step
+    graph."""
     w, gs, os_ = _loaded(ALL[name], graphs=graphs)
-    geom = from_workload(w)
     gs.step(0)
-    os_.prepare()
+    ties = 0
     for k in range(4):
-        st = [gs.state(0), gs.state(1)]
-        os_ = oracle_sim(w)
-        for s in (0, 1):
-            os_.load(s, st[s][0], st[s][1], st[s][2], st[s][3], st[s][4].astype(np.uint32))
-        # the charge collected on the trench bottom so far is part of the state
-        os_.bottom[:] = gs.surface()
-        os_.counts[:] = gs.counts()[0]
-        os_.prepare()
-        # fields of the same state agree
-        Exg, Eyg = gs.efield()
-        emax = max(np.abs(os_.Ex).max(), np.abs(os_.Ey).max())
-        assert np.abs(Exg - os_.Ex).max() <= FIELD_TOL * emax
-        assert np.abs(Eyg - os_.Ey).max() <= FIELD_TOL * emax
-        gs.step(1)
-        os_.step(1)
-        for s in (0, 1):
-            compare_states_grazing(gs.state(s), oracle_state(os_, s), w, s)
-        rg, ro = gs.rho(), os_.rho
-        assert np.abs(rg - ro).max() <= RHO_TOL * np.abs(ro).max() + 1e-3 / w.ppc
+        t, os_ = step_parity_once(w, gs, lambda: gs.step(1), k)
+        ties += t
         e = gs.energy()
         assert e[0] == pytest.approx(os_.ke[0], rel=1e-5)
         assert e[1] == pytest.approx(os_.ke[1], rel=1e-5)
         assert e[2] == pytest.approx(os_.fe, rel=1e-5)
+    assert ties <= 2, ties
 
 
 def test_absorption_tallies_bit_exact():
