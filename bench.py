@@ -154,50 +154,135 @@ def _barrier(dist):
         dist.barrier()
 
 
-def oracle_baseline(w, seconds_budget=20.0, n_sample=1_000_000, steps=2):
-    """The FP64 oracle as it stands on a bounded sample of the workload: the
-    full 512x1024 trench grid (factorisation outside the timing) with
-    n_sample particles per species, timed over `steps` steps."""
+# The oracle's timed sample of the trench workload, shared by the CPU-baseline
+# leg and the reference arm: the full 512 x 1024 grid (its sparse LU
+# factorised once, untimed) with ORACLE_SAMPLE particles per species drawn
+# uniformly over the plasma cells, advanced by whole oracle steps.
+ORACLE_SAMPLE = 100_000
+
+
+def _oracle_sample(w, seed_shift=0):
     from oracle.sim import Sim as OracleSim
     from oracle import poisson
     os_ = OracleSim(w)
     for s in (0, 1):
-        p = synth.random_state(w, s, n_sample, seed=w.seed + 17)
-        os_.load_particles(s, p)
-    poisson.solve_direct(os_.geom, np.zeros((os_.geom.nxn, os_.geom.nyn)))   # factorise
+        os_.load_particles(s, synth.random_state(w, s, ORACLE_SAMPLE, seed=w.seed + 17 + seed_shift))
+    poisson.solve_direct(os_.geom, np.zeros((os_.geom.nxn, os_.geom.nyn)))   # factorise once
     os_.prepare()
-    t0 = time.perf_counter()
+    return os_
+
+
+def _oracle_timed(w, steps, seed_shift=0):
+    """(particle-steps, seconds) of `steps` oracle steps on the sample."""
+    os_ = _oracle_sample(w, seed_shift)
     done = 0
-    while done < steps:
-        live = int(os_.live().sum())
+    t0 = time.perf_counter()
+    for _ in range(steps):
+        done += int(os_.live().sum())
         os_.step(1)
-        done += 1
-        if time.perf_counter() - t0 > seconds_budget:
-            break
-    dt = time.perf_counter() - t0
-    ps = live * done / dt
-    return {"value": ps, "unit": UNIT, "cores": 1, "kind": "oracle",
-            "sample": f"{w.name}: full grid, {n_sample} particles/species "
-                      f"(of {int(synth.plasma_cells(w).sum()) * w.ppc}), {done} steps, "
-                      f"{dt:.1f} s; numpy/scipy single-threaded"}
+    return done, time.perf_counter() - t0
+
+
+def _oracle_replica(a):
+    w, steps, k = a
+    return _oracle_timed(w, steps, seed_shift=k)
+
+
+def _host_info():
+    info = {"nproc": os.cpu_count()}
+    try:
+        out = subprocess.run(["lscpu"], capture_output=True, text=True, timeout=10).stdout
+        keep = ("Architecture", "Model name", "CPU(s)", "Thread(s) per core", "Core(s) per socket",
+                "Socket(s)", "CPU max MHz")
+        info["lscpu"] = {k.strip(): v.strip() for k, v in
+                         (l.split(":", 1) for l in out.splitlines() if ":" in l) if k.strip() in keep}
+    except (OSError, subprocess.SubprocessError):
+        info["lscpu"] = None
+    return info
+
+
+def oracle_baseline(w, steps=40):
+    """The FP64 oracle as it stands on the shared sample: one process (numpy
+    and scipy run it on one core), and one independent replica per core at
+    once (different particle draws), all started by spawn."""
+    import multiprocessing as mp
+    n1, t1 = _oracle_timed(w, steps)
+    cores = min(os.cpu_count() or 1, 16)
+    ctx = mp.get_context("spawn")
+    with ctx.Pool(cores) as pool:
+        t0 = time.perf_counter()
+        res = pool.map(_oracle_replica, [(w, steps, 1 + k) for k in range(cores)])
+        wall = time.perf_counter() - t0
+    # the replicas' factorisations overlap their timed steps only partly:
+    # the all-core figure uses each replica's own timed seconds, the slowest
+    nall = sum(r[0] for r in res)
+    tall = max(r[1] for r in res)
+    sample = (f"{w.name}: full 512x1024 grid (sparse LU factorised once, untimed), "
+              f"{ORACLE_SAMPLE} particles/species of {int(synth.plasma_cells(w).sum()) * w.ppc}, "
+              f"{steps} oracle steps")
+    return {"value": n1 / t1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "all_cores": {"value": nall / tall, "unit": UNIT, "cores": cores,
+                          "sample": f"{cores} independent replicas of the sample at once "
+                                    f"(spawned processes, {wall:.1f} s wall with their set-up)"},
+            "host": _host_info()}
+
+
+def errors_vs_oracle(pg):
+    """The CUDA path against the FP64 oracle on a small seeded trench state
+    (72 x 40 cells, 12 ppc/species, solves to 1e-10): the largest error of
+    every quantity after the first solve and after one step."""
+    from oracle.sim import Sim as OracleSim
+    w = synth.small_trench(nx=72, ny=40, depth=20, width=6, ppc=12, seed=11).replace(poisson_rtol=1e-10)
+    gs = pg.Sim(w)
+    os_ = OracleSim(w)
+    for s in (0, 1):
+        p = synth.maxwellian_load(w, s)
+        gs.load_particles(s, p)
+        os_.load_particles(s, p)
+    gs.step(0)
+    os_.prepare()
+    out = {"workload": w.name}
+    rmax = np.abs(os_.rho).max()
+    out["rho_rel_max"] = float(np.abs(gs.rho() - os_.rho).max() / rmax)
+    ex, ey = gs.efield()
+    emax = max(np.abs(os_.Ex).max(), np.abs(os_.Ey).max())
+    out["E_rel_max"] = float(max(np.abs(ex - os_.Ex).max(), np.abs(ey - os_.Ey).max()) / emax)
+    out["phi_rel_max"] = float(np.abs(gs.phi() - os_.phi).max() / np.abs(os_.phi).max())
+    gs.step(1)
+    os_.step(1)
+    dx = dv = 0.0
+    for s in (0, 1):
+        g = gs.state(s)
+        g = g[:, np.argsort(g[4], kind="stable")]
+        ps = os_.p[s]
+        o = np.argsort(ps["ids"], kind="stable")
+        common, ig, io = np.intersect1d(g[4].astype(np.int64), ps["ids"][o].astype(np.int64),
+                                        return_indices=True)
+        dx = max(dx, np.abs(g[0, ig] - ps["x"][o][io]).max(), np.abs(g[1, ig] - ps["y"][o][io]).max())
+        vs = np.maximum(np.maximum(np.abs(ps["vx"][o][io]), np.abs(ps["vy"][o][io])), w.vth[s])
+        dv = max(dv, (np.abs(g[2, ig] - ps["vx"][o][io]) / vs).max(), (np.abs(g[3, ig] - ps["vy"][o][io]) / vs).max())
+    out["x_abs_max_cells"] = float(dx)
+    out["v_rel_max"] = float(dv)
+    e = gs.energy()
+    out["KE_rel"] = [float(abs(e[s] - os_.ke[s]) / os_.ke[s]) for s in (0, 1)]
+    out["FE_rel"] = float(abs(e[2] - os_.fe) / os_.fe)
+    walls, live = gs.counts()
+    out["wall_tallies_equal"] = bool(np.array_equal(walls, os_.counts))
+    out["live_counts_equal"] = bool(np.array_equal(live, os_.live()))
+    out["bottom_counts_equal"] = bool(np.array_equal(gs.surface(), os_.bottom))
+    gs.close()
+    return out
 
 
 def run_reference(args):
     """The oracle as it stands on the host cores, on the trench workload's
-    full grid with a bounded particle sample, one oracle step per step."""
+    full grid with the shared particle sample, one oracle step per step."""
     dist, rank, ws = _dist()
     if rank != 0:
         return 0
-    from oracle.sim import Sim as OracleSim
-    from oracle import poisson
     w = synth.trench_512x1024()
-    n_sample = 100_000
     t_start = time.perf_counter()
-    os_ = OracleSim(w)
-    for s in (0, 1):
-        os_.load_particles(s, synth.random_state(w, s, n_sample, seed=w.seed + 17))
-    poisson.solve_direct(os_.geom, np.zeros((os_.geom.nxn, os_.geom.nyn)))   # factorise once
-    os_.prepare()
+    os_ = _oracle_sample(w)
     os_.step(max(args.warmup, 0))
     live = []
     t0 = time.perf_counter()
@@ -206,8 +291,8 @@ def run_reference(args):
         os_.step(1)
     dt = time.perf_counter() - t0
     v = float(np.sum(live)) / dt
-    sample = (f"full 512x1024 trench grid (sparse LU factorised once, untimed), "
-              f"{n_sample} particles/species of {int(synth.plasma_cells(w).sum()) * w.ppc}, "
+    sample = (f"{w.name}: full 512x1024 grid (sparse LU factorised once, untimed), "
+              f"{ORACLE_SAMPLE} particles/species of {int(synth.plasma_cells(w).sum()) * w.ppc}, "
               f"{args.steps} oracle steps in {dt:.1f} s")
     line = {"impl": "reference", "metric": METRIC, "value": v, "unit": UNIT, "n_gpus": ws,
             "steps": args.steps, "warmup": args.warmup, "ms_per_step": 1e3 * dt / max(args.steps, 1),
@@ -385,6 +470,71 @@ def run_warmstart(args):
     return 0
 
 
+# The paper's tallies (Sec. III-C, III-D): ions reaching the trench bottom and
+# the two sidewalls in the window, and their ratio sidewalls / bottom (the
+# paper's printed ratios 2.31, 1.85 and 3.49; the printed counts give 2.30,
+# 1.87 and 3.49).
+PAPER_TALLIES = {"w15": (2137, 4920, 6000), "w4": (831, 1558, 6000), "w15_buildup": (1094, 3820, 7000)}
+
+
+def run_paper(args):
+    """The paper's own trench runs (80 x 30, widths 15 and 4, and width 15
+    with the fixed test-ion density n_i = 5 on the row above the bottom; RF
+    electrode, m_i / m_e = 3672, T_i = T_e, ions recycled in the bulk,
+    t <= 1000), several seeds each, as one ensemble; the bottom and
+    sidewall ion tallies in the paper's windows (600 <= t <= 1000, and
+    700 <= t <= 1000 for the build-up run) beside the paper's counts."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1610_03918_gb300 as pg
+    t0 = time.perf_counter()
+    cases = list(PAPER_TALLIES)
+    ws_, tags = [], []
+    for case in cases:
+        for seed in range(1, args.paper_seeds + 1):
+            ws_.append(synth.paper_trench(4 if case == "w4" else 15, seed=seed, sort_every=8))
+            tags.append(case)
+    caps = [int(synth.plasma_cells(w).sum()) * w.ppc + 64 for w in ws_]
+    batch = pg.Batch(ws_, capacities=caps, hit_capacity=16)
+    for m, w, tag in zip(batch.members, ws_, tags):
+        for s in (0, 1):
+            m.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
+        if tag == "w15_buildup":
+            m.set_rho_ext(synth.paper_buildup_density(w))
+    marks = {}
+    done = 0
+    for at in sorted({v[2] for v in PAPER_TALLIES.values()} | {10000}):
+        batch.step(at - done)
+        done = at
+        marks[at] = [m.counts()[0][1].copy() for m in batch.members]
+    wall_s = time.perf_counter() - t0
+    out = {}
+    for case in cases:
+        start = PAPER_TALLIES[case][2]
+        ks = [k for k, t in enumerate(tags) if t == case]
+        d = sum(marks[10000][k] - marks[start][k] for k in ks)
+        bottom = int(d[pg.WALL_XMAX])
+        side = int(d[pg.WALL_COND_PY] + d[pg.WALL_COND_MY])
+        pb, ps, _ = PAPER_TALLIES[case]
+        out[case] = {"bottom_per_run": bottom / len(ks), "sidewalls_per_run": side / len(ks),
+                     "ratio_sidewalls_to_bottom": side / max(bottom, 1),
+                     "paper": {"bottom": pb, "sidewalls": ps, "ratio": ps / pb},
+                     "window_t": [start * 0.1, 1000.0], "seeds": len(ks)}
+    line = {"metric": "ions reaching the trench bottom and sidewalls (paper Sec. III-C, III-D)",
+            "value": out["w15"]["ratio_sidewalls_to_bottom"], "unit": "sidewalls / bottom",
+            "higher_is_better": False, "n_gpus": 1, "steps": 10000, "warmup": 0, "dtype": "f32",
+            "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": "paper_trench_80x30 (w15, w4, w15 + n_i = 5 build-up)",
+                       "members": len(ws_), "ppc": 100, "mass_ratio": 3672, "tau": 1.0,
+                       "rf": "5 sin(0.01 t)", "recycling": "ions, bulk rows 0 <= x < 60"},
+            "tallies": out, "wall_s": wall_s}
+    print(json.dumps(line), flush=True)
+    batch.close()
+    return 0
+
+
 def main():
     ap = argparse.ArgumentParser()
     ap.add_argument("--gpus", type=int, default=1)
@@ -392,7 +542,8 @@ def main():
                     help="timed steps (default 1000 for the trench step, 100 otherwise)")
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
-    ap.add_argument("--workload", default="trench", choices=["trench", "ensemble", "warmstart"],
+    ap.add_argument("--workload", default="trench",
+                    choices=["trench", "ensemble", "warmstart", "paper"],
                     help="trench: the 512x1024 trench run; ensemble: the 48-run width sweep; "
                          "warmstart: Poisson time to 1e-6 with the learned initial guess")
     ap.add_argument("--train-widths", default="2,6,10,14,20")
@@ -405,7 +556,9 @@ def main():
     ap.add_argument("--batch", type=int, default=4, help="training minibatch")
     ap.add_argument("--lr", type=float, default=1e-3)
     ap.add_argument("--members", type=int, default=48, help="ensemble members")
+    ap.add_argument("--paper-seeds", type=int, default=4, help="seeds per case (paper workload)")
     ap.add_argument("--e2e-steps", type=int, default=3)
+    ap.add_argument("--cold-steps", type=int, default=50, help="captured steps timed with a cold start")
     ap.add_argument("--no-cpu-baseline", action="store_true")
     ap.add_argument("--ppc", type=int, default=None, help="override particles per cell")
     ap.add_argument("--poisson-method", default="auto", choices=["auto", "multigrid"],
@@ -427,6 +580,8 @@ def main():
         return run_ensemble(args)
     if args.workload == "warmstart":
         return run_warmstart(args)
+    if args.workload == "paper":
+        return run_paper(args)
 
     dist, rank, ws = _dist()
     import torch
@@ -500,7 +655,31 @@ def main():
     tm_ms = e0p.elapsed_time(e1p) / args.steps
     tm = sim.timing()
     livep1 = int(sim.counts()[1].sum())
+
+    # Poisson time to 1e-6 from the zero guess (cold start), in the captured
+    # step on the same run: the solve phase's CUDA events, direct inner solve
+    sim.set_warm_start(0)
+    sim.step(3)
+    sim.timing()
+    sim.step(args.cold_steps)
+    tcold = sim.timing()
+    cold_direct = tcold["ms_poisson"] / max(tcold["steps"], 1)
+    sim.set_warm_start(args.warm_start)
     sim.set_timing(False)
+    # ... and with the multigrid-preconditioned CG inner solve: a context of
+    # the same geometry holding this run's charge density as a fixed external
+    # density (no particles), each captured step solving from zero
+    rho_now = sim.rho()
+    mg = pg.Sim(w, capacity=16, device=local, timing=True, warm_start=0,
+                poisson_method=pg.POISSON_MULTIGRID)
+    mg.set_rho_ext(rho_now)
+    mg.step(3)
+    mg.timing()
+    mg.step(args.cold_steps)
+    tmg = mg.timing()
+    cold_mg = tmg["ms_poisson"] / max(tmg["steps"], 1)
+    mg_iters = mg.poisson_stats()[0]
+    mg.close()
 
     live_mean = 0.5 * (live0 + live1)
     ps_local = live_mean * args.steps
@@ -548,10 +727,28 @@ def main():
                "d2h_bytes_per_step": 32,
                "note": "per step: pic_load of the full state from pinned host memory "
                        "(which re-deposits and re-solves), pic_step(1), pic_diag(ENERGY)"}
+        # the same with the whole particle state read back to the host every step
+        d2h = 0
+        torch.cuda.synchronize()
+        t0 = time.perf_counter()
+        for _ in range(args.e2e_steps):
+            for s in (0, 1):
+                bufs, ids = pinned[s]
+                sim.load(s, bufs[0], bufs[1], bufs[2], bufs[3], ids)
+            sim.step(1)
+            d2h = 0
+            for s in (0, 1):
+                d2h += sim.state(s).nbytes
+        t_full = time.perf_counter() - t0
+        e2e_full = {"value": _reduce_sum(dist, n_state * args.e2e_steps) / _reduce_max(dist, t_full),
+                    "unit": UNIT, "h2d_bytes_per_step": int(h2d), "d2h_bytes_per_step": int(d2h),
+                    "note": "per step: pic_load of the full state from pinned host memory, "
+                            "pic_step(1), pic_diag(STATE) of both species (x, y, vx, vy, id as FP64)"}
 
-    cpu = None
+    cpu = errs = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_baseline(synth.trench_512x1024())
+        errs = errors_vs_oracle(pg)
 
     if rank == 0:
         line = {
@@ -582,12 +779,21 @@ def main():
                 "rho": tm["ms_rho"] / max(tm["steps"], 1),
             },
             "poisson_ms_to_1e-6": tm["ms_poisson"] / max(tm["steps"], 1),
+            "poisson_ms_to_1e-6_by_start": {
+                "previous_step": tm["ms_poisson"] / max(tm["steps"], 1),
+                "zero_direct": cold_direct,
+                "zero_multigrid_pcg": cold_mg,
+                "multigrid_pcg_iterations_from_zero": mg_iters,
+                "note": "CUDA events around the solve phase of captured steps (E included); "
+                        "zero: cold start each step"},
             "poisson_last": {"iterations": pstats[0], "outer": pstats[1], "rel_residual": pstats[2]},
             "gpu_launches": launches,
             "ms_per_step_with_phase_events": tm_ms,
             "clocks": clk,
             "e2e": e2e,
+            "e2e_full_state": e2e_full if args.e2e_steps > 0 else None,
             "cpu_baseline": cpu,
+            "errors_vs_oracle": errs,
         }
         print(json.dumps(line), flush=True)
     sim.close()

@@ -155,6 +155,17 @@ typedef struct {
      FP32 vector of pic_unet_save); the network then gives the initial guess
      of every solve inside the step.  NULL otherwise. */
   const char *unet_weights;
+  /* 1: this context is one rank of a run split by particles (each rank holds
+     a share of the particles and the whole grid); it is advanced by
+     pic_step_particles, an all-reduce of its exchange buffer, and
+     pic_step_fields, not by pic_step.  Requires sort_every >= 1. */
+  int32_t decomposed;
+  /* tile variant of the particle store (shape of the sort's tiles and of the
+     particle kernel's shared-memory windows, CTA size): 0: 16 x 16 cells,
+     128 threads; 1: 32 (x) x 16 (y), 128; 2: 16 x 32, 128; 3: 32 x 32, 256;
+     halo 4 cells.  pic_autotune chooses one by timing.  Results do not
+     depend on it. */
+  int32_t tile_variant;
 } pic_config;
 
 /* One absorbed particle (PIC_DIAG_HITS): velocity is v^{n+1/2}. */
@@ -193,8 +204,10 @@ enum {
                                solved once to 1e-10 */
   PIC_DIAG_SOLVER = 14,     /* int32: inner Poisson solver in use, 0 direct, 1 multigrid PCG
                                (pic_config.poisson_method) */
-  PIC_DIAG_SORT = 15        /* int32[2]: steps between tile sorts in use (0 while it is being
+  PIC_DIAG_SORT = 15,       /* int32[2]: steps between tile sorts in use (0 while it is being
                                tuned), and 1 if it was chosen by the tuning of sort_every = 0 */
+  PIC_DIAG_TILE = 16        /* int32[5]: tile variant in use, its tile cells along x and y,
+                               halo cells, particle-kernel threads per CTA */
 };
 
 /* Create a context from cfg.  Builds the conductor mask, Dirichlet nodes and
@@ -229,6 +242,21 @@ pic_status pic_load(pic_ctx *ctx, int32_t species, int64_t n, const double *x,
  * the next pic_diag.  Without graphs the call waits on each solve and
  * returns PIC_ENOCONV directly. */
 pic_status pic_step(pic_ctx *ctx, int32_t nsteps);
+
+/* Autotuner of the particle store's tile variant (pic_config.tile_variant).
+ * With cache_path naming a file that holds an entry for this GPU (device
+ * name), grid, geometry and particles per cell, that entry's variant is
+ * taken.  Otherwise every variant is timed on the live run: the particles
+ * are sorted into its tiles, then `steps` steps run with no further sort and
+ * the particle kernel's mean device time (CUDA events) is recorded; the
+ * fastest variant is kept and, with cache_path, stored in the file (a JSON
+ * array, one object per line: key, tile_variant, particle_ms of every
+ * variant).  The timed steps advance the run; results do not depend on the
+ * variant.  A tuned sort interval (sort_every = 0) is chosen again for the
+ * new tiles.  *chosen (may be NULL) receives the variant.  Synchronous;
+ * PIC_EINVAL for a decomposed context or a cache file that cannot be
+ * written. */
+pic_status pic_autotune(pic_ctx *c, int32_t steps, const char *cache_path, int32_t *chosen);
 
 /* Turn the per-phase timing of cfg->timing on (1) or off (0) for the steps
  * that follow; totals already recorded are kept until PIC_DIAG_TIMING reads
@@ -268,6 +296,39 @@ pic_status pic_diag(pic_ctx *ctx, int32_t kind, void *out, int64_t cap_bytes,
  * PIC_DIAG_ENERGY reports the kinetic energy again from the next step on. */
 pic_status pic_save(pic_ctx *ctx, void *buf, int64_t cap_bytes, int64_t *n_out);
 pic_status pic_restore(pic_ctx *ctx, const void *buf, int64_t n_bytes);
+
+/* ---- One run split by particles across ranks (GPUs) ---------------------
+ * The paper's model has one grid and many particles; a run too large for one
+ * GPU is split by particles.  Every rank (a context with decomposed = 1, the
+ * same configuration on every rank, its own share of the particles through
+ * pic_load) keeps the whole grid.  One step is
+ *   pic_step_particles   [tile sort] gather, push, absorption with this
+ *                        rank's tallies and hit records, and the fixed-point
+ *                        deposit of this rank's particles (Eqs. 1-5);
+ *   all-reduce           the caller sums the rank's exchange buffer in place
+ *                        over all ranks (int64 addition; e.g. NCCL ncclInt64
+ *                        ncclSum on the context's stream): the deposit sums
+ *                        [2][nodes] and the bottom counts [2][ny];
+ *   pic_step_fields      rho from the summed deposit and surface charge, the
+ *                        Poisson solve and the field (identical on every
+ *                        rank: same inputs, deterministic kernels).
+ * Integer sums are exact and order-free, so an R-rank run gives, bit for bit,
+ * the rho, phi, E and particles (as a union) of the same particles in one
+ * context.  After pic_load the first pic_step_particles / pic_step_fields
+ * pair brings the fields up to date (as pic_step(ctx, 0) does).  Per-rank
+ * diagnostics (COUNTS, SURFACE, HITS, STATE, the kinetic energies of ENERGY)
+ * cover the rank's own particles; fields (RHO, PHI, E, FE) are global.
+ * pic_step_particles and pic_step_fields queue work on the context's stream
+ * and return; calling them out of order returns PIC_ESTATE. */
+pic_status pic_step_particles(pic_ctx *ctx);
+pic_status pic_step_fields(pic_ctx *ctx);
+/* The rank's exchange buffer: *buf (device, int64, *count elements). */
+pic_status pic_exchange_buffer(pic_ctx *ctx, int64_t **buf, int64_t *count);
+/* The all-reduce of n ranks' exchange buffers when all are contexts of this
+ * process on one device (a single-GPU stand-in for the collective): waits for
+ * each context's stream, writes the element-wise sum into every buffer,
+ * synchronously.  n <= 64. */
+pic_status pic_exchange_sum(pic_ctx *const *ctxs, int32_t n);
 
 /* Release the context and all its device memory. */
 pic_status pic_free(pic_ctx *ctx);
@@ -360,6 +421,12 @@ pic_status pic_unet_load(pic_unet *u, const char *path);
  * batch 1, height >= nxn (nxn rounded up to a multiple of 8) and width nyn.
  * Computes the empty-box potential phi_L if not done yet.  Synchronous. */
 pic_status pic_set_learned_start(pic_ctx *c, const pic_unet *net);
+
+/* Change the initial guess of the solves that follow (pic_config.warm_start:
+ * 0 zero, 1 previous, 2 extrapolated, 3 learned -- only once
+ * pic_set_learned_start has given the context a network); the step graphs
+ * are captured again.  Synchronous. */
+pic_status pic_set_warm_start(pic_ctx *c, int32_t mode);
 
 /* Training target of the warm-start network for the context's current
  * potential: t [hpad][nyn] (device, FP32) = (phi - phi_L) / scale, rows

@@ -29,7 +29,7 @@ PIC_LOAD_V_AT_T0 = 1
 (PIC_DIAG_ENERGY, PIC_DIAG_MOMENTUM, PIC_DIAG_COUNTS, PIC_DIAG_SURFACE, PIC_DIAG_HITS,
  PIC_DIAG_RHO, PIC_DIAG_PHI, PIC_DIAG_E, PIC_DIAG_STATE_E, PIC_DIAG_STATE_I,
  PIC_DIAG_POISSON, PIC_DIAG_STATUS, PIC_DIAG_TIMING, PIC_DIAG_PHI_VACUUM,
- PIC_DIAG_SOLVER, PIC_DIAG_SORT) = range(16)
+ PIC_DIAG_SOLVER, PIC_DIAG_SORT, PIC_DIAG_TILE) = range(17)
 (WALL_XMIN, WALL_XMAX, WALL_YMIN, WALL_YMAX, WALL_COND_PX, WALL_COND_MX,
  WALL_COND_PY, WALL_COND_MY) = range(8)
 
@@ -38,7 +38,8 @@ EXPORTED = ("pic_init", "pic_load", "pic_step", "pic_set_timing", "pic_diag", "p
             "pic_batch_free", "pic_deposit_static", "pic_unet_create", "pic_unet_forward",
             "pic_unet_gradients", "pic_unet_train_step", "pic_unet_free", "pic_save", "pic_restore",
             "pic_unet_init", "pic_unet_save", "pic_unet_load", "pic_set_learned_start",
-            "pic_learned_target")
+            "pic_learned_target", "pic_set_warm_start", "pic_step_particles", "pic_step_fields",
+            "pic_exchange_buffer", "pic_exchange_sum", "pic_autotune")
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -72,6 +73,7 @@ class PicConfig(ctypes.Structure):
         ("recycle", ctypes.c_int32), ("source_x0", ctypes.c_int32), ("source_x1", ctypes.c_int32),
         ("recycle_vth", ctypes.c_double), ("seed", ctypes.c_uint64),
         ("unet_weights", ctypes.c_char_p),
+        ("decomposed", ctypes.c_int32), ("tile_variant", ctypes.c_int32),
     ]
 
 
@@ -144,8 +146,19 @@ def load_library():
     lib.pic_unet_load.argtypes = [P, ctypes.c_char_p]
     lib.pic_set_learned_start.argtypes = [P, P]
     lib.pic_learned_target.argtypes = [P, ctypes.c_int32, ctypes.c_double, P]
+    lib.pic_set_warm_start.argtypes = [P, ctypes.c_int32]
+    lib.pic_set_warm_start.restype = ctypes.c_int
+    lib.pic_step_particles.argtypes = [P]
+    lib.pic_step_fields.argtypes = [P]
+    lib.pic_exchange_buffer.argtypes = [P, ctypes.POINTER(ctypes.c_void_p), ctypes.POINTER(ctypes.c_int64)]
+    lib.pic_exchange_sum.argtypes = [ctypes.POINTER(ctypes.c_void_p), ctypes.c_int32]
+    for name in ("pic_step_particles", "pic_step_fields", "pic_exchange_buffer", "pic_exchange_sum"):
+        getattr(lib, name).restype = ctypes.c_int
+    lib.pic_autotune.argtypes = [P, ctypes.c_int32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]
+    lib.pic_autotune.restype = ctypes.c_int
     for name in ("pic_unet_init", "pic_unet_save", "pic_unet_load", "pic_set_learned_start",
-                 "pic_learned_target"):
+                 "pic_learned_target", "pic_set_warm_start", "pic_step_particles", "pic_step_fields",
+            "pic_exchange_buffer", "pic_exchange_sum", "pic_autotune"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("pic_unet_create", "pic_unet_set_params", "pic_unet_get_params",
                  "pic_unet_forward", "pic_unet_gradients", "pic_unet_train_step", "pic_unet_free"):
@@ -239,7 +252,8 @@ class _TorchAllocator:
 def make_config(w, capacity=None, device: int = 0, stream=None, hit_capacity: int = 1 << 20,
                 poisson_maxit: int = 200, warm_start: int = 1, allocator=None,
                 timing: bool = False, graphs: bool = True,
-                poisson_method: int = POISSON_AUTO, unet_weights=None) -> PicConfig:
+                poisson_method: int = POISSON_AUTO, unet_weights=None,
+                decomposed: bool = False, tile_variant: int = 0) -> PicConfig:
     """PicConfig from a workload description (an object with the fields of
     synth.Workload)."""
     cfg = PicConfig()
@@ -273,6 +287,8 @@ def make_config(w, capacity=None, device: int = 0, stream=None, hit_capacity: in
     cfg.recycle_vth = float(w.vth[1]) if cfg.recycle else 0.0
     cfg.seed = int(getattr(w, "recycle_seed", 0)) & 0xFFFFFFFFFFFFFFFF
     cfg.unet_weights = os.fsencode(unet_weights) if unet_weights is not None else None
+    cfg.decomposed = int(bool(decomposed))
+    cfg.tile_variant = int(tile_variant)
     cfg.stream = stream
     if allocator is not None:
         cfg.alloc = allocator.alloc
@@ -442,8 +458,37 @@ class Sim:
         import torch
         t = torch.empty((hpad, self.nyn), dtype=torch.float32, device="cuda")
         self._check(load_library().pic_learned_target(self.ctx, int(hpad), float(scale), t.data_ptr()),
-                    "pic_learned_target")
+                    "pic_learned_target", "pic_set_warm_start", "pic_step_particles", "pic_step_fields",
+            "pic_exchange_buffer", "pic_exchange_sum", "pic_autotune")
         return t
+
+    # one rank of a run split by particles -------------------------------
+    def step_particles(self):
+        """Particle phase of a decomposed step (pic_step_particles)."""
+        return self._check(load_library().pic_step_particles(self.ctx), "pic_step_particles")
+
+    def step_fields(self):
+        """Field phase of a decomposed step (pic_step_fields)."""
+        return self._check(load_library().pic_step_fields(self.ctx), "pic_step_fields")
+
+    def exchange_buffer(self):
+        """The rank's exchange buffer as a torch int64 CUDA tensor viewing the
+        library's device memory (to be all-reduced in place, sum)."""
+        import torch
+        ptr = ctypes.c_void_p()
+        n = ctypes.c_int64()
+        self._check(load_library().pic_exchange_buffer(self.ctx, ctypes.byref(ptr), ctypes.byref(n)),
+                    "pic_exchange_buffer")
+
+        class _View:
+            __cuda_array_interface__ = {"shape": (int(n.value),), "typestr": "<i8",
+                                        "data": (int(ptr.value), False), "version": 3}
+        return torch.as_tensor(_View(), device="cuda")
+
+    def set_warm_start(self, mode: int):
+        """Initial guess of the solves that follow: 0 zero, 1 previous,
+        2 extrapolated, 3 learned (after set_learned_start)."""
+        return self._check(load_library().pic_set_warm_start(self.ctx, int(mode)), "pic_set_warm_start")
 
     def set_learned_start(self, net):
         """Every later solve starts from the guess of (a copy of) the trained
@@ -465,6 +510,18 @@ class Sim:
         v = self.diag(PIC_DIAG_SORT, np.zeros(2, np.int32))[0]
         return int(v[0]), bool(v[1])
 
+    def autotune(self, steps: int = 8, cache=None):
+        """Choose the tile variant by timing (pic_autotune); returns its index."""
+        v = ctypes.c_int32(-1)
+        self._check(load_library().pic_autotune(self.ctx, int(steps),
+                                                os.fsencode(cache) if cache else None, ctypes.byref(v)),
+                    "pic_autotune")
+        return int(v.value)
+
+    def tile(self):
+        """(variant, tile cells x, tile cells y, halo, threads) in use."""
+        return tuple(int(v) for v in self.diag(PIC_DIAG_TILE, np.zeros(5, np.int32))[0])
+
     def solver(self):
         """Inner Poisson solver in use: POISSON_AUTO (0) = the direct one,
         POISSON_MULTIGRID (1) = multigrid-preconditioned CG."""
@@ -475,6 +532,16 @@ class Sim:
         st, _ = pic_diag(self.ctx, PIC_DIAG_STATUS, out)
         self._check(st, "pic_diag(status)")
         return int(out[0])
+
+
+def exchange_sum(sims):
+    """The all-reduce of the exchange buffers of several ranks held by this
+    process on one GPU (pic_exchange_sum)."""
+    arr = (ctypes.c_void_p * len(sims))(*[s.ctx.value if isinstance(s.ctx, ctypes.c_void_p) else s.ctx
+                                          for s in sims])
+    st = load_library().pic_exchange_sum(arr, len(sims))
+    if st != PIC_OK:
+        raise PicError(st, "pic_exchange_sum")
 
 
 class Batch:

@@ -4,6 +4,8 @@
 
 #include <algorithm>
 #include <cmath>
+#include <cstdio>
+#include <cstdlib>
 #include <cstring>
 #include <new>
 #include <string>
@@ -206,6 +208,8 @@ pic_status validate(const pic_config *cfg) {
   if (cfg->poisson_maxit < 1 || cfg->sort_every < 0) return PIC_EINVAL;
   if (cfg->warm_start < 0 || cfg->warm_start > 3) return PIC_EINVAL;
   if (cfg->warm_start == 3 && !cfg->unet_weights) return PIC_EINVAL;
+  if (cfg->decomposed && cfg->sort_every < 1) return PIC_EINVAL;
+  if (cfg->tile_variant < 0 || cfg->tile_variant >= kNumTileVariants) return PIC_EINVAL;
   if (!std::isfinite(cfg->phi_rf_amp) || !std::isfinite(cfg->omega_rf)) return PIC_EINVAL;
   if (cfg->recycle) {
     const int plasma_rows = cfg->nx - cfg->trench_depth;
@@ -296,8 +300,11 @@ pic_status step_kernels(pic_ctx *c, bool sorting, cudaEvent_t *ev) {
 // points them at a slot of the event pool.  On return `deps` holds the step's last node(s).
 // Kernel arguments are fixed device pointers; the particle buffers are reached
 // through the device-side buffer table, so the sort's swap needs no re-capture.
+// part 0: the whole step; 1: its particle phase (a decomposed run's, which
+// ends by copying the rank's bottom counts into the exchange buffer); 2: its
+// field phase.
 cudaError_t capture_step(pic_ctx *c, cudaGraph_t g, std::vector<cudaGraphNode_t> &deps,
-                         int with_sort, bool events) {
+                         int with_sort, bool events, int part = 0) {
   const int cur_save[2] = {c->cur[0], c->cur[1]};
   const int64_t launches_save = c->launches;
   auto rec = [&](int k) {
@@ -307,16 +314,24 @@ cudaError_t capture_step(pic_ctx *c, cudaGraph_t g, std::vector<cudaGraphNode_t>
                                                 nullptr, deps.size(), cudaStreamCaptureModeThreadLocal);
   if (e == cudaSuccess) {
     rec(0);
-    if (with_sort) launch_sort(c);
-    rec(1);
-    launch_particles(c, 0, 1.f, nullptr);
-    rec(2);
-    launch_rf_bias(c, 1);
-    if (!rho_in_solve(c)) launch_rho(c, 1, c->cfg.warm_start == 1);   // opens the solve captured next
+    if (part != 2) {
+      if (with_sort) launch_sort(c);
+      rec(1);
+      launch_particles(c, 0, 1.f, nullptr);
+      rec(2);
+    }
+    if (part == 1) {
+      const size_t nn = size_t(c->g.nxn) * c->g.nyn;
+      cudaMemcpyAsync(c->d_acc + 2 * nn, c->d_bottom, 2 * size_t(c->g.ny) * 8, cudaMemcpyDeviceToDevice,
+                      c->stream);
+    } else {
+      launch_rf_bias(c, 1);
+      if (!rho_in_solve(c)) launch_rho(c, 1, c->cfg.warm_start == 1);   // opens the solve captured next
+    }
     rec(3);
     e = note(capture_leaves(c->stream, deps), "capture: particle phase");
   }
-  if (e == cudaSuccess) e = note(poisson_capture(c, g, deps), "capture: Poisson conditionals");
+  if (e == cudaSuccess && part != 1) e = note(poisson_capture(c, g, deps), "capture: Poisson conditionals");
   if (e == cudaSuccess && events) {
     e = cudaStreamBeginCaptureToGraph(c->stream, g, deps.data(), nullptr, deps.size(),
                                       cudaStreamCaptureModeThreadLocal);
@@ -497,7 +512,7 @@ pic_status pic_batch_init(const pic_config *cfgs, int32_t n, void *stream, pic_b
   *out = nullptr;
   for (int32_t k = 0; k < n; ++k) {
     if (cfgs[k].sort_every < 1 || cfgs[k].sort_every != cfgs[0].sort_every ||
-        cfgs[k].device != cfgs[0].device)
+        cfgs[k].device != cfgs[0].device || cfgs[k].decomposed)
       return PIC_EINVAL;
     const pic_status st = validate(&cfgs[k]);
     if (st != PIC_OK) return st;
@@ -678,9 +693,11 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
   g.nxn = g.px ? g.nx : g.nx + 1;
   g.nyn = g.py ? g.ny : g.ny + 1;
   g.dnyn = make_fastdiv(uint32_t(g.nyn));
-  g.ntx = (g.nx + kTileX - 1) / kTileX;
-  g.nty = (g.ny + kTileY - 1) / kTileY;
-  const int ntiles = g.ntx * g.nty;
+  // tile arrays sized for the smallest tile shape; the variant in use sets ntx, nty
+  const int ntiles = ((g.nx + (1 << kMinTileLog2) - 1) >> kMinTileLog2) *
+                     ((g.ny + (1 << kMinTileLog2) - 1) >> kMinTileLog2);
+  c->max_tiles = ntiles;
+  set_tile_variant(c, cfg->tile_variant);
   const size_t nn = size_t(g.nxn) * g.nyn;
 
   std::vector<uint8_t> cellmask;
@@ -697,7 +714,7 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
   c->d_nodeflags = (uint8_t *)A(nn);
   c->d_lift = (float *)A(nn * 4);
   c->d_g = (float2 *)A(nn * 8);
-  c->d_acc = (unsigned long long *)A(2 * nn * 8);
+  c->d_acc = (unsigned long long *)A((2 * nn + 2 * size_t(g.ny)) * 8);
   c->d_rho_ext = (float2 *)A(nn * 8);
   c->d_rho = (float2 *)A(nn * 8);
   c->d_phi = (float2 *)A(nn * 8);
@@ -812,7 +829,7 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
     }
     cudaStreamSynchronize(c->stream);   // the host vectors go out of scope
   }
-  cudaMemsetAsync(c->d_acc, 0, 2 * nn * 8, c->stream);
+  cudaMemsetAsync(c->d_acc, 0, (2 * nn + 2 * size_t(g.ny)) * 8, c->stream);
   cudaMemsetAsync(c->d_rho_ext, 0, nn * 8, c->stream);
   cudaMemsetAsync(c->d_rho, 0, nn * 8, c->stream);
   cudaMemsetAsync(c->d_E, 0, nn * sizeof(float2), c->stream);
@@ -881,6 +898,15 @@ pic_status pic_set_learned_start(pic_ctx *c, const pic_unet *net) {
   if ((st = unet_copy_params(c->net, net)) != PIC_OK) return st;
   if ((st = ensure_vacuum_potential(c)) != PIC_OK) return st;
   // the step graphs hold the old initial guess: capture them again
+  if (c->cfg.warm_start == 3) c->cfg.warm_start = 1;
+  return pic_set_warm_start(c, 3);
+}
+
+pic_status pic_set_warm_start(pic_ctx *c, int32_t mode) {
+  if (!c || mode < 0 || mode > 3 || (mode == 3 && !c->net)) return PIC_EINVAL;
+  if (cudaSetDevice(c->dev) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
+    return PIC_ECUDA;
+  if (mode == c->cfg.warm_start) return PIC_OK;
   for (int k = 0; k < 2; ++k)
     for (int v = 0; v < 2; ++v) {
       if (c->gexec[k][v]) cudaGraphExecDestroy(c->gexec[k][v]);
@@ -888,7 +914,13 @@ pic_status pic_set_learned_start(pic_ctx *c, const pic_unet *net) {
       c->gexec[k][v] = nullptr;
       c->graph[k][v] = nullptr;
     }
-  c->cfg.warm_start = 3;
+  for (int k = 0; k < 3; ++k) {
+    if (c->gexec_dp[k]) cudaGraphExecDestroy(c->gexec_dp[k]);
+    if (c->graph_dp[k]) cudaGraphDestroy(c->graph_dp[k]);
+    c->gexec_dp[k] = nullptr;
+    c->graph_dp[k] = nullptr;
+  }
+  c->cfg.warm_start = mode;
   return PIC_OK;
 }
 
@@ -969,6 +1001,7 @@ pic_status pic_load(pic_ctx *c, int32_t species, int64_t n, const double *x, con
 
 pic_status pic_step(pic_ctx *c, int32_t nsteps) {
   if (!c || nsteps < 0) return PIC_EINVAL;
+  if (c->cfg.decomposed) return PIC_ESTATE;   // steps of a decomposed run come in two phases
   if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
   pic_status st = prepare(c);
   if (st != PIC_OK) return st;
@@ -981,7 +1014,8 @@ pic_status pic_step(pic_ctx *c, int32_t nsteps) {
     else if (c->tune_state == 0) sorting = true;
     else if (c->tune_state == 1) sorting = false;
     else sorting = c->steps_since_sort >= c->sort_interval;
-    // particles restored from a checkpoint are sorted before they move
+    if (c->suppress_sort) sorting = false;
+    // particles restored from a checkpoint, or a new tile variant, are sorted before they move
     if (c->needs_sort) sorting = true;
     c->needs_sort = 0;
     // steps of the host loop are always timed; graph steps when timing is on
@@ -1030,6 +1064,279 @@ pic_status pic_step(pic_ctx *c, int32_t nsteps) {
     }
   }
   return PIC_OK;
+}
+
+namespace picgb {
+namespace {
+
+// graph of one phase of a decomposed step (k: 0 particles, 1 particles with
+// the sort, 2 fields), captured once
+cudaError_t phase_graph(pic_ctx *c, int k) {
+  if (c->gexec_dp[k]) return cudaSuccess;
+  cudaGraph_t g;
+  cudaError_t e = cudaGraphCreate(&g, 0);
+  if (e != cudaSuccess) return e;
+  std::vector<cudaGraphNode_t> deps;
+  e = note(capture_step(c, g, deps, k == 1 ? 1 : 0, false, k == 2 ? 2 : 1), "phase graph capture");
+  if (e == cudaSuccess) e = note(cudaGraphInstantiate(&c->gexec_dp[k], g, 0), "phase graph instantiate");
+  if (e == cudaSuccess) c->graph_dp[k] = g;
+  else cudaGraphDestroy(g);
+  cudaGetLastError();
+  return e;
+}
+
+__global__ void k_exchange_sum(DevPtrs p, int n, long long count) {
+  for (long long k = blockIdx.x * (long long)blockDim.x + threadIdx.x; k < count;
+       k += (long long)gridDim.x * blockDim.x) {
+    unsigned long long s = 0;
+    for (int r = 0; r < n; ++r) s += p.p[r][k];
+    for (int r = 0; r < n; ++r) p.p[r][k] = s;
+  }
+}
+
+}  // namespace
+}  // namespace picgb
+
+pic_status pic_step_particles(pic_ctx *c) {
+  if (!c || !c->cfg.decomposed) return PIC_EINVAL;
+  if (c->phase != 0) return PIC_ESTATE;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
+  const size_t nn = size_t(c->g.nxn) * c->g.nyn;
+  pic_status st;
+  if (c->fields_dirty) {
+    // bring the fields up to date: deposit of the loaded particles
+    if ((st = check(launch_sort(c))) != PIC_OK) return st;
+    c->steps_since_sort = 0;
+    c->needs_sort = 0;
+    if ((st = check(launch_particles(c, 1, 0.f, nullptr))) != PIC_OK) return st;
+    if (cudaMemcpyAsync(c->d_acc + 2 * nn, c->d_bottom, 2 * size_t(c->g.ny) * 8, cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess)
+      return PIC_ECUDA;
+    c->phase = 1;
+    return PIC_OK;
+  }
+  const bool sorting = c->steps_since_sort >= c->cfg.sort_every || c->needs_sort;
+  c->needs_sort = 0;
+  if (c->cfg.graphs) {
+    if ((st = check(phase_graph(c, sorting ? 1 : 0))) != PIC_OK) return st;
+    if (note(cudaGraphLaunch(c->gexec_dp[sorting ? 1 : 0], c->stream), "phase graph launch") != cudaSuccess)
+      return PIC_ECUDA;
+    if (sorting) {
+      c->cur[0] ^= 1;
+      c->cur[1] ^= 1;
+    }
+    c->launches += (sorting ? 4 : 0) + 1;
+  } else {
+    if (sorting && (st = check(launch_sort(c))) != PIC_OK) return st;
+    if ((st = check(launch_particles(c, 0, 1.f, nullptr))) != PIC_OK) return st;
+    if (cudaMemcpyAsync(c->d_acc + 2 * nn, c->d_bottom, 2 * size_t(c->g.ny) * 8, cudaMemcpyDeviceToDevice,
+                        c->stream) != cudaSuccess)
+      return PIC_ECUDA;
+    c->launches += (sorting ? 4 : 0) + 1;
+  }
+  if (sorting) {
+    c->steps_since_sort = 0;
+    c->t_sorts += 1;
+  }
+  c->steps_since_sort += 1;
+  c->phase = 2;
+  return PIC_OK;
+}
+
+pic_status pic_step_fields(pic_ctx *c) {
+  if (!c || !c->cfg.decomposed) return PIC_EINVAL;
+  if (c->phase == 0) return PIC_ESTATE;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
+  pic_status st;
+  if (c->phase == 1) {
+    // the rest of the bring-up: rho, a cold solve, pending half kicks
+    c->phase = 0;
+    if ((st = check(launch_rf_bias(c, 0))) != PIC_OK) return st;
+    if ((st = check(launch_rho(c, 0))) != PIC_OK) return st;
+    if ((st = poisson_solve(c, true)) != PIC_OK) return st;
+    if (cudaMemcpyAsync(c->d_phi_prev, c->d_phi, size_t(c->g.nxn) * c->g.nyn * sizeof(float2),
+                        cudaMemcpyDeviceToDevice, c->stream) != cudaSuccess)
+      return PIC_ECUDA;
+    if (c->pending_kick[0] || c->pending_kick[1]) {
+      if ((st = check(launch_particles(c, 2, -0.5f, c->pending_kick))) != PIC_OK) return st;
+      c->pending_kick[0] = c->pending_kick[1] = 0;
+    }
+    c->fields_dirty = 0;
+    return PIC_OK;
+  }
+  c->phase = 0;
+  if (c->cfg.graphs) {
+    if ((st = check(phase_graph(c, 2))) != PIC_OK) return st;
+    if (note(cudaGraphLaunch(c->gexec_dp[2], c->stream), "phase graph launch") != cudaSuccess) return PIC_ECUDA;
+    c->launches += (rho_in_solve(c) ? 0 : 1) +
+                   (c->cfg.phi_rf_amp != 0.0 && (c->n_rf_dir || c->n_rf_lift) ? 1 : 0);
+  } else {
+    if ((st = check(launch_rf_bias(c, 1))) != PIC_OK) return st;
+    if ((st = check(launch_rho(c, 1))) != PIC_OK) return st;
+    if ((st = poisson_solve(c, c->cfg.warm_start == 0)) != PIC_OK) return st;
+    c->launches += 1;
+  }
+  c->step += 1;
+  c->t_steps += 1;
+  return PIC_OK;
+}
+
+pic_status pic_exchange_buffer(pic_ctx *c, int64_t **buf, int64_t *count) {
+  if (!c || !buf || !count) return PIC_EINVAL;
+  *buf = reinterpret_cast<int64_t *>(c->d_acc);
+  *count = 2 * int64_t(c->g.nxn) * c->g.nyn + 2 * int64_t(c->g.ny);
+  return PIC_OK;
+}
+
+pic_status pic_exchange_sum(pic_ctx *const *ctxs, int32_t n) {
+  if (!ctxs || n < 1 || n > 64) return PIC_EINVAL;
+  DevPtrs p = {};
+  int64_t count = -1;
+  for (int32_t r = 0; r < n; ++r) {
+    pic_ctx *c = ctxs[r];
+    if (!c || !c->cfg.decomposed || c->dev != ctxs[0]->dev || c->phase == 0) return PIC_EINVAL;
+    int64_t *b, m;
+    pic_exchange_buffer(c, &b, &m);
+    if (count >= 0 && m != count) return PIC_EINVAL;
+    count = m;
+    p.p[r] = reinterpret_cast<unsigned long long *>(b);
+    if (cudaSetDevice(c->dev) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
+      return PIC_ECUDA;
+  }
+  cudaStream_t s = ctxs[0]->stream;
+  k_exchange_sum<<<ctxs[0]->num_sms * 4, 256, 0, s>>>(p, n, (long long)count);
+  if (note(cudaGetLastError(), "exchange sum") != cudaSuccess) return PIC_ECUDA;
+  return cudaStreamSynchronize(s) == cudaSuccess ? PIC_OK : PIC_ECUDA;
+}
+
+namespace picgb {
+namespace {
+
+void drop_step_graphs(pic_ctx *c) {
+  for (int k = 0; k < 2; ++k)
+    for (int v = 0; v < 2; ++v) {
+      if (c->gexec[k][v]) cudaGraphExecDestroy(c->gexec[k][v]);
+      if (c->graph[k][v]) cudaGraphDestroy(c->graph[k][v]);
+      c->gexec[k][v] = nullptr;
+      c->graph[k][v] = nullptr;
+    }
+  for (int k = 0; k < 3; ++k) {
+    if (c->gexec_dp[k]) cudaGraphExecDestroy(c->gexec_dp[k]);
+    if (c->graph_dp[k]) cudaGraphDestroy(c->graph_dp[k]);
+    c->gexec_dp[k] = nullptr;
+    c->graph_dp[k] = nullptr;
+  }
+}
+
+// Key of a tuning-cache entry: the GPU, the grid and geometry, the loading.
+std::string tune_key(pic_ctx *c) {
+  cudaDeviceProp prop;
+  std::string gpu = "unknown";
+  if (cudaGetDeviceProperties(&prop, c->dev) == cudaSuccess) gpu = prop.name;
+  for (char &ch : gpu)
+    if (ch == '"' || ch == '|' || ch == '\\') ch = '_';
+  const pic_config &f = c->cfg;
+  return gpu + "|" + std::to_string(f.nx) + "|" + std::to_string(f.ny) + "|" + std::to_string(f.periodic_x) +
+         "|" + std::to_string(f.periodic_y) + "|" + std::to_string(f.trench_depth) + "|" +
+         std::to_string(f.trench_width) + "|" + std::to_string(f.ppc[0]) + "|" + std::to_string(f.ppc[1]);
+}
+
+// The cache is a JSON array with one object per line; the entry of a key is
+// the line holding "key": "<key>", its choice the value of "tile_variant".
+int cache_lookup(const char *path, const std::string &key) {
+  std::FILE *f = std::fopen(path, "r");
+  if (!f) return -1;
+  const std::string want = "\"key\": \"" + key + "\"";
+  char line[4096];
+  int found = -1;
+  while (std::fgets(line, sizeof(line), f)) {
+    const std::string l(line);
+    if (l.find(want) == std::string::npos) continue;
+    const size_t p = l.find("\"tile_variant\": ");
+    if (p != std::string::npos) found = std::atoi(l.c_str() + p + 16);
+  }
+  std::fclose(f);
+  return (found >= 0 && found < kNumTileVariants) ? found : -1;
+}
+
+bool cache_store(const char *path, const std::string &key, int v, const double *ms) {
+  std::vector<std::string> keep;
+  if (std::FILE *f = std::fopen(path, "r")) {
+    char line[4096];
+    const std::string want = "\"key\": \"" + key + "\"";
+    while (std::fgets(line, sizeof(line), f)) {
+      std::string l(line);
+      while (!l.empty() && (l.back() == '\n' || l.back() == ',')) l.pop_back();
+      if (l.size() > 1 && l[0] == '{' && l.find(want) == std::string::npos) keep.push_back(l);
+    }
+    std::fclose(f);
+  }
+  char buf[1024];
+  std::snprintf(buf, sizeof(buf),
+                "{\"key\": \"%s\", \"tile_variant\": %d, \"particle_ms\": [%.5f, %.5f, %.5f, %.5f]}",
+                key.c_str(), v, ms[0], ms[1], ms[2], ms[3]);
+  keep.push_back(buf);
+  const std::string tmp = std::string(path) + ".tmp";
+  std::FILE *f = std::fopen(tmp.c_str(), "w");
+  if (!f) return false;
+  std::fputs("[\n", f);
+  for (size_t k = 0; k < keep.size(); ++k) {
+    std::fputs(keep[k].c_str(), f);
+    std::fputs(k + 1 < keep.size() ? ",\n" : "\n", f);
+  }
+  std::fputs("]\n", f);
+  const bool ok = std::fclose(f) == 0;
+  return ok && std::rename(tmp.c_str(), path) == 0;
+}
+
+}  // namespace
+}  // namespace picgb
+
+pic_status pic_autotune(pic_ctx *c, int32_t steps, const char *cache_path, int32_t *chosen) {
+  if (!c || steps < 1 || c->cfg.decomposed) return PIC_EINVAL;
+  if (cudaSetDevice(c->dev) != cudaSuccess) return PIC_ECUDA;
+  const std::string key = tune_key(c);
+  int best = cache_path ? cache_lookup(cache_path, key) : -1;
+  double ms[kNumTileVariants] = {0, 0, 0, 0};
+  pic_status st = PIC_OK;
+  if (best < 0) {
+    // time the particle kernel of each variant over `steps` steps right after
+    // its own sort (no scheduled sort in between); the steps advance the run,
+    // whose results do not depend on the variant
+    st = pic_step(c, 0);
+    const int timing_save = c->cfg.timing;
+    double best_ms = 0.0;
+    for (int v = 0; v < kNumTileVariants && st == PIC_OK; ++v) {
+      drop_step_graphs(c);
+      set_tile_variant(c, v);
+      if ((st = pic_step(c, 1)) != PIC_OK) break;   // sorts into the new tiles
+      c->cfg.timing = 1;
+      c->suppress_sort = 1;
+      if ((st = flush_timing(c)) != PIC_OK) break;
+      const double p0 = c->t_part;
+      const int64_t n0 = c->t_steps;
+      st = pic_step(c, steps);
+      if (st == PIC_OK) st = flush_timing(c);
+      c->suppress_sort = 0;
+      c->cfg.timing = timing_save;
+      ms[v] = (c->t_part - p0) / double(std::max<int64_t>(c->t_steps - n0, 1));
+      if (best < 0 || ms[v] < best_ms) {
+        best = v;
+        best_ms = ms[v];
+      }
+    }
+    c->suppress_sort = 0;
+    c->cfg.timing = timing_save;
+    if (st != PIC_OK) return st;
+    if (cache_path && !cache_store(cache_path, key, best, ms)) st = PIC_EINVAL;
+  }
+  drop_step_graphs(c);
+  set_tile_variant(c, best);
+  c->cfg.tile_variant = best;
+  // a tuned sort interval is chosen again for the new tiles
+  if (c->cfg.sort_every == 0) c->tune_state = 0;
+  if (chosen) *chosen = best;
+  return st;
 }
 
 pic_status pic_set_timing(pic_ctx *c, int32_t on) {
@@ -1202,6 +1509,18 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
         o[1] = c->tune_state == 2 ? 1 : 0;
       }
       count = 2;
+      break;
+    }
+    case PIC_DIAG_TILE: {
+      if (!need(5 * 4)) return PIC_EINVAL;
+      int32_t *o = (int32_t *)out;
+      const TileVariant &t = kTileVariants[c->tile_variant];
+      o[0] = c->tile_variant;
+      o[1] = 1 << t.log2x;
+      o[2] = 1 << t.log2y;
+      o[3] = t.halo;
+      o[4] = t.threads;
+      count = 5;
       break;
     }
     case PIC_DIAG_SOLVER: {
@@ -1471,6 +1790,10 @@ pic_status pic_free(pic_ctx *c) {
   if (c->ev0) cudaEventDestroy(c->ev0);
   if (c->ev1) cudaEventDestroy(c->ev1);
   if (c->net) pic_unet_free(c->net);
+  for (int k = 0; k < 3; ++k) {
+    if (c->gexec_dp[k]) cudaGraphExecDestroy(c->gexec_dp[k]);
+    if (c->graph_dp[k]) cudaGraphDestroy(c->graph_dp[k]);
+  }
   if (c->own_stream && c->stream) cudaStreamDestroy(c->stream);
   delete c;
   return PIC_OK;

@@ -18,16 +18,23 @@ constexpr uint32_t kQ = 1u << kFracBits;
 
 // Particle tiles: a sorted tile's particles are processed by one CTA with
 // the field and the deposit of a window (tile + halo) held in shared memory.
-constexpr int kTileX = 16;
-constexpr int kTileY = 16;
-constexpr int kHalo = 4;
+// The tile shape (powers of two, in cells), the halo and the CTA size form a
+// variant of the particle store, chosen per run by the autotuner
+// (pic_autotune); results do not depend on it.
+struct TileVariant {
+  int log2x, log2y;   // tile of 2^log2x x 2^log2y cells
+  int halo;           // window = tile + halo cells on every side
+  int threads;        // CTA size of the particle kernel
+};
+constexpr int kNumTileVariants = 4;
+constexpr TileVariant kTileVariants[kNumTileVariants] = {
+    {4, 4, 4, 128},    // 16 x 16
+    {5, 4, 4, 128},    // 32 (x) x 16 (y)
+    {4, 5, 4, 128},    // 16 (x) x 32 (y)
+    {5, 5, 4, 256},    // 32 x 32
+};
+constexpr int kMinTileLog2 = 4;  // the smallest tile (16 x 16) sizes the tile arrays
 constexpr int kChunk = 4092;     // particles per work item (multiple of 4, <= 4095)
-#ifndef PIC_PARTICLE_THREADS
-#define PIC_PARTICLE_THREADS 128
-#endif
-constexpr int kParticleThreads = PIC_PARTICLE_THREADS;
-// resident CTAs per SM the register budget allows (64 registers per thread)
-constexpr int kParticleMinBlocks = 1024 / PIC_PARTICLE_THREADS;
 constexpr int kWalkLimit = 16;   // face crossings followed per move
 
 // Double-float values.  The potential, the charge density and the Dirichlet
@@ -117,7 +124,8 @@ struct Geom {
   int nx, ny;          // cells
   int px, py;          // periodic flags
   int nxn, nyn;        // nodes
-  int ntx, nty;        // tiles
+  int ntx, nty;        // tiles of the tile variant in use
+  int tsx, tsy;        // its tile shape: 2^tsx x 2^tsy cells
   FastDiv dnyn;        // division by nyn (node index -> row)
 };
 
@@ -140,6 +148,11 @@ struct ParticleBuf {
 
 struct Chunk {
   int32_t species, tile, begin, end;
+};
+
+// device pointers of up to 64 ranks' exchange buffers (by value, as a kernel argument)
+struct DevPtrs {
+  unsigned long long *p[64];
 };
 
 // Device-side scalars of one Poisson solve.
@@ -270,7 +283,9 @@ struct pic_ctx {
   float *d_rf_cnt, *d_rf_lift0;
 
   // fields
-  unsigned long long *d_acc;   // [2][nnodes] fixed-point species weights
+  unsigned long long *d_acc;   // [2][nnodes] fixed-point species weights, then (exchange
+                               // buffer of a decomposed run) the bottom counts [2][ny]
+  int phase;                   // decomposed run: 0 idle, 1 prepare / 2 step particle phase done
   // double-float (hi, lo) node arrays
   float2 *d_rho_ext;
   float2 *d_rho;               // net charge density
@@ -321,6 +336,9 @@ struct pic_ctx {
   picgb::Chunk *d_chunks;
   int32_t *d_nchunks;
   int64_t max_chunks;
+  int tile_variant;            // index into kTileVariants
+  int suppress_sort;           // autotuning: no scheduled sorts while a variant is timed
+  int max_tiles;               // tiles of the smallest tile shape (array sizes)
   int64_t *d_nslots;           // [4]: slots in use per species; [2..3] staged by the sort
   double *d_ke_part;           // [max_chunks]
   int32_t *d_step;
@@ -342,6 +360,9 @@ struct pic_ctx {
   // captured step graphs [with the tile sort][with phase event nodes]
   cudaGraph_t graph[2][2];
   cudaGraphExec_t gexec[2][2];
+  // decomposed run: particle phase without / with the sort, field phase
+  cudaGraph_t graph_dp[3];
+  cudaGraphExec_t gexec_dp[3];
   cudaGraphNode_t evnode[2][picgb::kPhaseEvents];   // event nodes of the [.][1] graphs
   // per-phase timing (PIC_DIAG_TIMING): each timed step records its phase
   // boundaries into its own slot of the pool, read back when the pool is full
@@ -368,6 +389,8 @@ cudaError_t note(cudaError_t e, const char *where);
 
 // particles.cu
 cudaError_t launch_sort(pic_ctx *c);
+// switches the particle store to tile variant v (the next step must sort)
+void set_tile_variant(pic_ctx *c, int v);
 // mode 0: full step; 1: deposit only; 2: kick only (factor * dt, flagged species)
 cudaError_t launch_particles(pic_ctx *c, int mode, float kick_factor, const int *species_mask);
 cudaError_t launch_load_convert(pic_ctx *c, int s, const double *d_x, const double *d_y,

@@ -25,7 +25,7 @@ __device__ __forceinline__ int cell_j(int c) { return c & 0xffff; }
 __device__ __forceinline__ int pack_cell(int i, int j) { return (i << 16) | j; }
 
 __device__ __forceinline__ int tile_of(const Geom &g, int c) {
-  return (cell_i(c) / kTileX) * g.nty + cell_j(c) / kTileY;
+  return (cell_i(c) >> g.tsx) * g.nty + (cell_j(c) >> g.tsy);
 }
 
 // ---------------------------------------------------------------------------
@@ -246,10 +246,18 @@ struct PArgs {
   float vth_i;               // thermal speed of the re-entering ions
 };
 
-constexpr int WXc = kTileX + 2 * kHalo;   // window cells
-constexpr int WYc = kTileY + 2 * kHalo;
-constexpr int NWX = WXc + 1;              // window nodes
-constexpr int NWY = WYc + 1;
+// The shared-memory window of a tile variant: tile + halo cells, +1 nodes.
+template <int V>
+struct Win {
+  static constexpr int TX = 1 << kTileVariants[V].log2x;
+  static constexpr int TY = 1 << kTileVariants[V].log2y;
+  static constexpr int H = kTileVariants[V].halo;
+  static constexpr int THREADS = kTileVariants[V].threads;
+  static constexpr int WXc = TX + 2 * H;   // window cells
+  static constexpr int WYc = TY + 2 * H;
+  static constexpr int NWX = WXc + 1;      // window nodes
+  static constexpr int NWY = WYc + 1;
+};
 
 
 __device__ __forceinline__ void deposit_global(const PArgs &a, unsigned long long *acc, int i,
@@ -296,6 +304,7 @@ __device__ __forceinline__ int local_coord(int i, int w0, int n, int periodic) {
   return l;
 }
 
+template <int NWY>
 __device__ __forceinline__ void deposit_shared(uint32_t *sAcc, int li, int lj, int w00, int w01,
                                                int w10, int w11) {
   const int k = li * NWY + lj;
@@ -391,12 +400,13 @@ __device__ __forceinline__ void recycled_ion(const PArgs &a, uint32_t id, int st
   vy = a.vth_i * (rad * sn);
 }
 
-template <int MODE>
+template <int MODE, int V>
 __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint32_t *sAcc,
                                          unsigned long long *acc, int s, int wi0, int wj0,
                                          const uint32_t *id, int64_t slot, int &c, float &fx,
                                          float &fy, float &vx, float &vy, float &ke) {
   if (c < 0) return;
+  constexpr int WXc = Win<V>::WXc, WYc = Win<V>::WYc, NWY = Win<V>::NWY;
   const Geom &g = a.g;
   const int i = cell_i(c);
   const int j = cell_j(c);
@@ -411,7 +421,7 @@ __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint3
     // deposit only, at the current position
     int w00, w01, w10, w11;
     cic_weights(fx, fy, w00, w01, w10, w11);
-    if (inw) deposit_shared(sAcc, li, lj, w00, w01, w10, w11);
+    if (inw) deposit_shared<NWY>(sAcc, li, lj, w00, w01, w10, w11);
     else deposit_global(a, acc, i, j, w00, w01, w10, w11);
     return;
   }
@@ -485,7 +495,7 @@ __device__ __forceinline__ void move_one(const PArgs &a, const float2 *sE, uint3
   cic_weights(fx, fy, w00, w01, w10, w11);
   const int lni = li + oi, lnj = lj + oj;
   if ((unsigned)lni < (unsigned)WXc && (unsigned)lnj < (unsigned)WYc) {
-    deposit_shared(sAcc, lni, lnj, w00, w01, w10, w11);
+    deposit_shared<NWY>(sAcc, lni, lnj, w00, w01, w10, w11);
   } else {
     deposit_global(a, acc, cell_i(c), cell_j(c), w00, w01, w10, w11);
   }
@@ -500,11 +510,12 @@ __device__ __forceinline__ void prefetch_l2(const void *p, unsigned bytes) {
   asm volatile("cp.async.bulk.prefetch.L2.global [%0], %1;" ::"l"(p), "r"(bytes) : "memory");
 }
 
-template <int MODE>
-__global__ void __launch_bounds__(kParticleThreads, kParticleMinBlocks) k_particles(PArgs a) {
+template <int MODE, int V>
+__global__ void __launch_bounds__(Win<V>::THREADS, 1024 / Win<V>::THREADS) k_particles(PArgs a) {
+  constexpr int NWX = Win<V>::NWX, NWY = Win<V>::NWY, THREADS = Win<V>::THREADS;
   __shared__ float2 sE[NWX * NWY];
   __shared__ uint32_t sAcc[NWX * NWY];
-  __shared__ double sRed[kParticleThreads / 32];
+  __shared__ double sRed[THREADS / 32];
   const Geom g = a.g;
   const int nch = *a.nchunks;
   const int nnodes = g.nxn * g.nyn;
@@ -514,8 +525,8 @@ __global__ void __launch_bounds__(kParticleThreads, kParticleMinBlocks) k_partic
     const int s = ch.species;
     const int ti = ch.tile / g.nty;
     const int tj = ch.tile - ti * g.nty;
-    const int wi0 = ti * kTileX - kHalo;
-    const int wj0 = tj * kTileY - kHalo;
+    const int wi0 = ti * Win<V>::TX - Win<V>::H;
+    const int wj0 = tj * Win<V>::TY - Win<V>::H;
     for (int k = threadIdx.x; k < NWX * NWY; k += blockDim.x) {
       if (MODE != 1) {
         const int wi = k / NWY, wj = k - (k / NWY) * NWY;
@@ -555,10 +566,10 @@ __global__ void __launch_bounds__(kParticleThreads, kParticleMinBlocks) k_partic
         vx4 = *reinterpret_cast<const float4 *>(P.vx + base);
         vy4 = *reinterpret_cast<const float4 *>(P.vy + base);
       }
-      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 0, c4.x, fx4.x, fy4.x, vx4.x, vy4.x, ke);
-      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 1, c4.y, fx4.y, fy4.y, vx4.y, vy4.y, ke);
-      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 2, c4.z, fx4.z, fy4.z, vx4.z, vy4.z, ke);
-      move_one<MODE>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 3, c4.w, fx4.w, fy4.w, vx4.w, vy4.w, ke);
+      move_one<MODE, V>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 0, c4.x, fx4.x, fy4.x, vx4.x, vy4.x, ke);
+      move_one<MODE, V>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 1, c4.y, fx4.y, fy4.y, vx4.y, vy4.y, ke);
+      move_one<MODE, V>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 2, c4.z, fx4.z, fy4.z, vx4.z, vy4.z, ke);
+      move_one<MODE, V>(a, sE, sAcc, acc, s, wi0, wj0, P.id, base + 3, c4.w, fx4.w, fy4.w, vx4.w, vy4.w, ke);
       if (MODE == 0) {   // streaming stores: the written state is not read again this step
         __stcs(reinterpret_cast<int4 *>(P.cell + base), c4);
         __stcs(reinterpret_cast<float4 *>(P.fx + base), fx4);
@@ -597,7 +608,7 @@ __global__ void __launch_bounds__(kParticleThreads, kParticleMinBlocks) k_partic
       __syncthreads();
       if (threadIdx.x == 0) {
         double t = 0.0;
-        for (int w = 0; w < kParticleThreads / 32; ++w) t += sRed[w];
+        for (int w = 0; w < THREADS / 32; ++w) t += sRed[w];
         a.ke_part[ci] = t;
       }
     }
@@ -741,11 +752,23 @@ __global__ void k_moments(ParticleBuf P, const int64_t *nslots_p, double *part) 
   }
 }
 
-int particle_grid(pic_ctx *c) {
+template <int MODE, int V>
+cudaError_t launch_particles_v(pic_ctx *c, const PArgs &a) {
   int per_sm = 0;
-  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_particles<0>, kParticleThreads, 0);
+  cudaOccupancyMaxActiveBlocksPerMultiprocessor(&per_sm, k_particles<0, V>, Win<V>::THREADS, 0);
   if (per_sm < 1) per_sm = 1;
-  return c->num_sms * per_sm;
+  k_particles<MODE, V><<<c->num_sms * per_sm, Win<V>::THREADS, 0, c->stream>>>(a);
+  return cudaGetLastError();
+}
+
+template <int MODE>
+cudaError_t launch_particles_mode(pic_ctx *c, const PArgs &a) {
+  switch (c->tile_variant) {
+    case 1: return launch_particles_v<MODE, 1>(c, a);
+    case 2: return launch_particles_v<MODE, 2>(c, a);
+    case 3: return launch_particles_v<MODE, 3>(c, a);
+    default: return launch_particles_v<MODE, 0>(c, a);
+  }
 }
 
 }  // namespace
@@ -804,13 +827,21 @@ cudaError_t launch_particles(pic_ctx *c, int mode, float kick_factor, const int 
   a.src_rows = c->src_x1 - c->src_x0;
   a.key = make_uint2(uint32_t(c->cfg.seed), uint32_t(c->cfg.seed >> 32));
   a.vth_i = float(c->cfg.recycle_vth);
-  const int grid = particle_grid(c);
   switch (mode) {
-    case 0: k_particles<0><<<grid, kParticleThreads, 0, c->stream>>>(a); break;
-    case 1: k_particles<1><<<grid, kParticleThreads, 0, c->stream>>>(a); break;
-    default: k_particles<2><<<grid, kParticleThreads, 0, c->stream>>>(a); break;
+    case 0: return launch_particles_mode<0>(c, a);
+    case 1: return launch_particles_mode<1>(c, a);
+    default: return launch_particles_mode<2>(c, a);
   }
-  return cudaGetLastError();
+}
+
+void set_tile_variant(pic_ctx *c, int v) {
+  const TileVariant &t = kTileVariants[v];
+  c->tile_variant = v;
+  c->g.tsx = t.log2x;
+  c->g.tsy = t.log2y;
+  c->g.ntx = (c->g.nx + (1 << t.log2x) - 1) >> t.log2x;
+  c->g.nty = (c->g.ny + (1 << t.log2y) - 1) >> t.log2y;
+  c->needs_sort = 1;
 }
 
 cudaError_t launch_load_convert(pic_ctx *c, int s, const double *d_x, const double *d_y,

@@ -1480,7 +1480,8 @@ FineArgs fine_args(pic_ctx *c) {
   a.phi_prev = c->d_phi_prev;
   a.acc = c->d_acc;
   a.rho_ext = c->d_rho_ext;
-  a.bottom = c->d_bottom;
+  // a decomposed run's rho takes the bottom counts summed over the ranks
+  a.bottom = c->cfg.decomposed ? c->d_acc + 2 * size_t(c->g.nxn) * c->g.nyn : c->d_bottom;
   for (int s = 0; s < 2; ++s) {
     const double w = 1.0 / double(c->cfg.ppc[s]);
     a.qw[s] = pair_split(c->cfg.charge[s] * w * std::ldexp(1.0, -kFracBits));

@@ -149,6 +149,33 @@ def ensemble_member(k: int, **kw) -> Workload:
                     surface_charge=True).replace(**kw)
 
 
+def paper_trench(width: int = 15, seed: int = 1, **kw) -> Workload:
+    """The paper's own trench runs (Sec. III-C): a 60 x 30 periodic bulk above
+    a 20-deep electrode (80 x-cells, 30 y-cells), trench of width 15 at
+    5 <= y <= 20 (Fig. 5) or of width 4 at 10 <= y <= 14 (Fig. 6); grounded
+    plate at x = 0, RF electrode Phi = 5 sin(0.01 t) (Sec. III-B);
+    m_i / m_e = 3672, T_i = T_e (Sec. III); 100 ppc/species; ions recycled
+    into the bulk rows 0 <= x < 60 (Sec. III-A, III-C); dt = 0.1 up to
+    t = 1000."""
+    y0 = {15: 5, 4: 10}.get(width, (30 - width) // 2)
+    return Workload(name=f"paper_trench_80x30_w{width}", nx=80, ny=30, periodic_x=False,
+                    periodic_y=True, phi_top=0.0, phi_electrode=0.0, phi_rf_amp=5.0,
+                    omega_rf=0.01, trench_depth=20, trench_y0=y0, trench_width=width,
+                    mass_ratio=3672.0, tau=1.0, ppc=100, seed=seed, nsteps=10000,
+                    recycle=True, source_x0=0, source_x1=60, recycle_seed=seed,
+                    surface_charge=False).replace(**kw)
+
+
+def paper_buildup_density(w: Workload, value: float = 5.0) -> np.ndarray:
+    """The fixed test-ion density of the paper's charge build-up run (Sec.
+    III-D): n_i = 5 on the node row x = nx - 1 (x = 79) across the trench
+    bottom, y = y0 .. y0 + width (5 <= y <= 20 for the width-15 trench)."""
+    nyn = w.ny if w.periodic_y else w.ny + 1
+    rho = np.zeros((w.nx + 1, nyn))
+    rho[w.nx - 1, w.trench_y0:w.trench_y0 + w.trench_width + 1] = value
+    return rho
+
+
 # ---------------------------------------------------------------------------
 # Particle generators
 # ---------------------------------------------------------------------------

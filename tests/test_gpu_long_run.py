@@ -1,0 +1,104 @@
+"""Long-run statistical parity: runs that diverge from the oracle particle
+by particle (chaos amplifies FP32 rounding) must keep its statistics.  The
+oracle side was written by tests/golden/make_long_run_stats.py (same
+workloads and seeds).  Needs a GB300.
+
+1. Impact angles theta = atan(|v_y| / v_x) of ions reaching the trench
+   bottom (Sec. III-C, Fig. 5b), pooled over 16 seeds: two-sample
+   Kolmogorov-Smirnov distance between the GPU's and the oracle's binned
+   distributions <= 0.02, with >= 2e4 hits on each side; the 5% critical
+   value is reported beside it.
+2. Field energy of the 64 x 64 doubly periodic box over 500 steps, 4 seeds:
+   mean and standard deviation over 100-step windows within the oracle's
+   seed-to-seed spread (or 5%)."""
+import os
+
+import numpy as np
+import pytest
+
+import synth
+
+pytestmark = pytest.mark.gpu
+
+GOLDEN = os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden")
+import importlib.util as _ilu
+
+_spec = _ilu.spec_from_file_location("make_long_run_stats", os.path.join(GOLDEN, "make_long_run_stats.py"))
+recipe = _ilu.module_from_spec(_spec)
+_spec.loader.exec_module(recipe)   # the workload recipes and constants (no oracle run on import)
+
+
+@pytest.fixture(scope="module", autouse=True)
+def _built():
+    import __graft_entry__
+    __graft_entry__.build()
+
+
+def _load_counts(path):
+    return np.array([int(l) for l in open(path) if not l.startswith("#")])
+
+
+def ks_binned(h1, h2):
+    """Kolmogorov-Smirnov distance of two binned samples (max gap of their
+    empirical CDFs at the bin edges)."""
+    c1 = np.cumsum(h1) / h1.sum()
+    c2 = np.cumsum(h2) / h2.sum()
+    return float(np.abs(c1 - c2).max())
+
+
+def test_ion_bottom_angle_distribution_matches_oracle():
+    import paper_1610_03918_gb300 as pg
+    ref = _load_counts(os.path.join(GOLDEN, "ion_bottom_angles.txt"))
+    assert ref.size == recipe.ANGLE_BINS
+    ws = [recipe.angle_workload(s).replace(sort_every=8) for s in recipe.ANGLE_SEEDS]
+    loads = [[synth.maxwellian_load(w, s) for s in (0, 1)] for w in ws]
+    batch = pg.Batch(ws, capacities=[max(len(p[0]), len(p[1])) for p in loads],
+                     hit_capacity=1 << 20, poisson_method=pg.POISSON_MULTIGRID)
+    for m, p in zip(batch.members, loads):
+        for s in (0, 1):
+            m.load_particles(s, p[s], v_at_t0=True)
+    batch.step(recipe.ANGLE_STEPS)
+    hist = np.zeros(recipe.ANGLE_BINS, np.int64)
+    for m in batch.members:
+        assert m.status() & pg.PIC_ST_FULL == 0
+        h = m.hits()
+        sel = (h["species"] == 1) & (h["wall"] == pg.WALL_XMAX) & (h["step"] >= recipe.ANGLE_SETTLE)
+        theta = np.arctan2(np.abs(h["vy"][sel].astype(np.float64)), h["vx"][sel].astype(np.float64))
+        hist += np.histogram(theta, bins=recipe.ANGLE_BINS, range=(0.0, np.pi / 2))[0]
+    batch.close()
+    n, m = int(hist.sum()), int(ref.sum())
+    assert n >= 20000 and m >= 20000, (n, m)
+    ks = ks_binned(hist, ref)
+    crit = 1.358 * np.sqrt((n + m) / (n * m))    # two-sample KS, 5% level
+    print(f"ion bottom angles: KS = {ks:.4f} (5% critical value {crit:.4f}), n = {n}, m = {m}")
+    assert ks <= 0.02, (ks, crit, n, m)
+
+
+def test_field_energy_history_matches_oracle():
+    import paper_1610_03918_gb300 as pg
+    path = os.path.join(GOLDEN, "field_energy_periodic64.txt")
+    ref = np.array([[float(v) for v in l.split()] for l in open(path) if not l.startswith("#")])
+    assert ref.shape == (recipe.FE_STEPS, len(recipe.FE_SEEDS))
+    gpu = np.zeros_like(ref)
+    for k, seed in enumerate(recipe.FE_SEEDS):
+        w = recipe.fe_workload(seed)
+        sim = pg.Sim(w)
+        for s in (0, 1):
+            sim.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
+        sim.step(0)
+        for n in range(recipe.FE_STEPS):
+            sim.step(1)
+            gpu[n, k] = sim.energy()[2]
+        sim.close()
+    # the first step's field energy is that of the identical loaded state
+    np.testing.assert_allclose(gpu[0], ref[0], rtol=1e-4)
+    for w0 in range(0, recipe.FE_STEPS, 100):
+        win = slice(w0, w0 + 100)
+        for stat in (np.mean, np.std):
+            g = stat(gpu[win], axis=0)       # per seed
+            o = stat(ref[win], axis=0)
+            spread = o.std(ddof=1)
+            gap = abs(g.mean() - o.mean())
+            print(f"window {w0}-{w0 + 99} {stat.__name__}: gpu {g.mean():.5g} oracle {o.mean():.5g} "
+                  f"seed spread {spread:.3g}")
+            assert gap <= max(2 * spread, 0.05 * abs(o.mean())), (w0, stat.__name__, g, o)
