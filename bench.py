@@ -671,7 +671,7 @@ def main():
     # density (no particles), each captured step solving from zero
     rho_now = sim.rho()
     mg = pg.Sim(w, capacity=16, device=local, timing=True, warm_start=0,
-                poisson_method=pg.POISSON_MULTIGRID)
+                poisson_method=pg.POISSON_MULTIGRID, graphs=not args.no_graphs)
     mg.set_rho_ext(rho_now)
     mg.step(3)
     mg.timing()
