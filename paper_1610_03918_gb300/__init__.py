@@ -458,8 +458,7 @@ class Sim:
         import torch
         t = torch.empty((hpad, self.nyn), dtype=torch.float32, device="cuda")
         self._check(load_library().pic_learned_target(self.ctx, int(hpad), float(scale), t.data_ptr()),
-                    "pic_learned_target", "pic_set_warm_start", "pic_step_particles", "pic_step_fields",
-            "pic_exchange_buffer", "pic_exchange_sum", "pic_autotune")
+                    "pic_learned_target")
         return t
 
     # one rank of a run split by particles -------------------------------
