@@ -470,6 +470,77 @@ def run_warmstart(args):
     return 0
 
 
+def unet_flops(H, W, B=1):
+    """FLOPs of one forward pass of the warm-start U-Net at H x W: the 3x3
+    convolutions (2 x 9 x cin x cout per output pixel), the transposed 2x2
+    convolutions (2 x cin x cout per output pixel) and the head."""
+    C = (32, 64, 128, 256)
+    f = 0.0
+    cin = 16                        # the input's 2 channels padded to 16
+    for l in range(4):
+        px = B * (H >> l) * (W >> l)
+        f += 2 * 9 * px * (cin * C[l] + C[l] * C[l])
+        cin = C[l]
+    for l in (2, 1, 0):
+        px = B * (H >> l) * (W >> l)
+        f += 2 * px * C[l + 1] * C[l] + 2 * 9 * px * (2 * C[l] * C[l] + C[l] * C[l])
+    return f + 2 * B * H * W * C[0]
+
+
+def run_unet(args):
+    """Forward and training-step time of the warm-start U-Net at the trench
+    grid (1032 x 512, batch 1 for inference), on the tcgen05 convolutions and
+    on the mma.sync ones, CUDA events over repeated calls on the net's stream."""
+    import torch
+    torch.cuda.set_device(0)
+    import __graft_entry__
+    __graft_entry__.build()
+    import paper_1610_03918_gb300 as pg
+    H, W = 1032, 512
+    peak = json.load(open(os.path.join(ROOT, "MEASURED_PEAKS.json")))["bf16_tflops"] \
+        if os.path.exists(os.path.join(ROOT, "MEASURED_PEAKS.json")) else 1900.0
+    out = {}
+    for name, impl in (("tcgen05", 0), ("mma_sync", 1)):
+        res = {}
+        for B, what in ((1, "forward"), (args.batch, "train_step")):
+            net = pg.Unet(B, H, W)
+            net.set_conv_impl(impl)
+            net.init(seed=0)
+            x = torch.randn((B, H, W, 2), device="cuda")
+            t = torch.randn((B, H, W), device="cuda")
+            fn = (lambda: net.forward(x)) if what == "forward" else (lambda: net.train_step(x, t, 1e-4))
+            for _ in range(3):
+                fn()
+            torch.cuda.synchronize()
+            e0 = torch.cuda.Event(enable_timing=True)
+            e1 = torch.cuda.Event(enable_timing=True)
+            e0.record(net.stream)
+            for _ in range(args.steps):
+                fn()
+            e1.record(net.stream)
+            torch.cuda.synchronize()
+            assert net.status() == pg.PIC_OK
+            ms = e0.elapsed_time(e1) / args.steps
+            fl = unet_flops(H, W, B) * (1 if what == "forward" else 3)
+            res[what] = {"ms": ms, "batch": B, "tflops": fl / (ms * 1e-3) / 1e12,
+                         "frac_of_bf16_peak": fl / (ms * 1e-3) / 1e12 / peak}
+            net.close()
+        out[name] = res
+    line = {"metric": "warm-start U-Net forward ms (1032 x 512 trench grid)",
+            "value": out["tcgen05"]["forward"]["ms"], "unit": "ms", "higher_is_better": False,
+            "n_gpus": 1, "steps": args.steps, "warmup": 3, "dtype": "bf16 (fp32 accumulate)",
+            "data": "synthetic", "vs_baseline": None,
+            "config": {"workload": "unet_4level_32ch_1032x512", "forward_flop": unet_flops(H, W),
+                       "train_step_flop": "3 x forward per sample (forward, data and weight gradients)"},
+            "roofline": {"bound": "tensor", "achieved": out["tcgen05"]["forward"]["tflops"],
+                         "peak": peak, "unit": "TFLOP/s",
+                         "frac": out["tcgen05"]["forward"]["tflops"] / peak, "traffic": None,
+                         "peak_kind": "measured bf16 burst"},
+            "by_kernel": out}
+    print(json.dumps(line), flush=True)
+    return 0
+
+
 # The paper's tallies (Sec. III-C, III-D): ions reaching the trench bottom and
 # the two sidewalls in the window, and their ratio sidewalls / bottom (the
 # paper's printed ratios 2.31, 1.85 and 3.49; the printed counts give 2.30,
@@ -543,7 +614,7 @@ def main():
     ap.add_argument("--warmup", type=int, default=20)
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--workload", default="trench",
-                    choices=["trench", "ensemble", "warmstart", "paper"],
+                    choices=["trench", "ensemble", "warmstart", "paper", "unet"],
                     help="trench: the 512x1024 trench run; ensemble: the 48-run width sweep; "
                          "warmstart: Poisson time to 1e-6 with the learned initial guess")
     ap.add_argument("--train-widths", default="2,6,10,14,20")
@@ -582,6 +653,8 @@ def main():
         return run_warmstart(args)
     if args.workload == "paper":
         return run_paper(args)
+    if args.workload == "unet":
+        return run_unet(args)
 
     dist, rank, ws = _dist()
     import torch

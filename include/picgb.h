@@ -401,6 +401,31 @@ pic_status pic_unet_gradients(pic_unet *u, const float *x, const float *t, float
 pic_status pic_unet_train_step(pic_unet *u, const float *x, const float *t, float lr, double *loss);
 pic_status pic_unet_free(pic_unet *u);
 
+/* The U-Net's 3x3 convolutions run on the fifth-generation tensor cores
+ * (tcgen05.mma, FP32 accumulators in tensor memory, operands staged by TMA)
+ * wherever the shapes allow -- cin a multiple of 16, cout 32, 64, 128 or 256,
+ * channel strides and offsets multiples of 8 -- and on the mma.sync path
+ * otherwise; impl 1 selects mma.sync for all of them (impl 0: the default).
+ * Synchronous. */
+pic_status pic_unet_set_conv_impl(pic_unet *u, int32_t impl);
+/* PIC_ETIMEOUT (and clears it) if a bounded wait of a tensor-core kernel of
+ * this network gave up since the last call; waits for the net's stream. */
+pic_status pic_unet_status(pic_unet *u);
+
+/* One 3x3 convolution with zero padding (the U-Net's layer):
+ * out[b][h][w][out_off + n] = act(bias[n] + sum_{dy, dx, c}
+ *   in[b][h + dy - 1][w + dx - 1][in_off + c] * w[n][3 dy + dx][c]),
+ * dy, dx in {0, 1, 2}, act = ReLU when relu, else identity.  in, out: DEVICE
+ * BF16 NHWC with channel strides in_cs, out_cs; w: DEVICE BF16 [cout][9][cin];
+ * bias: DEVICE FP32 [cout] or NULL.  impl 0: tcgen05 tensor cores (shapes as
+ * above, else PIC_EINVAL); impl 1: mma.sync (cout 32 with cin 16 or a
+ * multiple of 32, or cout a multiple of 64 with cin a multiple of 32).
+ * FP32 accumulation, BF16 rounding of the result.  Synchronous on `stream`;
+ * PIC_ETIMEOUT if a bounded wait of the tensor-core kernel gave up. */
+pic_status pic_conv3x3_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const void *in, int32_t in_cs,
+                            int32_t in_off, int32_t cin, const void *w, const float *bias, int32_t relu,
+                            void *out, int32_t out_cs, int32_t out_off, int32_t cout, void *stream);
+
 /* He initialisation of every weight (He et al., ICCV 2015: N(0, 2 / fan_in)
  * for the layers followed by a ReLU, N(0, 1 / fan_in) for the linear head;
  * fan_in = 9 x input channels for a 3x3 convolution, the input channels for

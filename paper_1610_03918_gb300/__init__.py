@@ -39,7 +39,8 @@ EXPORTED = ("pic_init", "pic_load", "pic_step", "pic_set_timing", "pic_diag", "p
             "pic_unet_gradients", "pic_unet_train_step", "pic_unet_free", "pic_save", "pic_restore",
             "pic_unet_init", "pic_unet_save", "pic_unet_load", "pic_set_learned_start",
             "pic_learned_target", "pic_set_warm_start", "pic_step_particles", "pic_step_fields",
-            "pic_exchange_buffer", "pic_exchange_sum", "pic_autotune")
+            "pic_exchange_buffer", "pic_exchange_sum", "pic_autotune", "pic_unet_set_conv_impl",
+            "pic_unet_status", "pic_conv3x3_bf16")
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -156,9 +157,14 @@ def load_library():
         getattr(lib, name).restype = ctypes.c_int
     lib.pic_autotune.argtypes = [P, ctypes.c_int32, ctypes.c_char_p, ctypes.POINTER(ctypes.c_int32)]
     lib.pic_autotune.restype = ctypes.c_int
+    lib.pic_unet_set_conv_impl.argtypes = [P, ctypes.c_int32]
+    lib.pic_unet_status.argtypes = [P]
+    lib.pic_unet_set_conv_impl.restype = ctypes.c_int
+    lib.pic_unet_status.restype = ctypes.c_int
     for name in ("pic_unet_init", "pic_unet_save", "pic_unet_load", "pic_set_learned_start",
                  "pic_learned_target", "pic_set_warm_start", "pic_step_particles", "pic_step_fields",
-            "pic_exchange_buffer", "pic_exchange_sum", "pic_autotune"):
+            "pic_exchange_buffer", "pic_exchange_sum", "pic_autotune", "pic_unet_set_conv_impl",
+            "pic_unet_status", "pic_conv3x3_bf16"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("pic_unet_create", "pic_unet_set_params", "pic_unet_get_params",
                  "pic_unet_forward", "pic_unet_gradients", "pic_unet_train_step", "pic_unet_free"):
@@ -622,6 +628,17 @@ class Unet:
         self.h = h
         self.shape = (batch, height, width)
         self.nparam = int(lib.pic_unet_num_params(h))
+
+    def set_conv_impl(self, impl: int):
+        """3x3 convolutions on the tcgen05 tensor cores where the shapes allow
+        (0, the default) or all on the mma.sync kernel (1)."""
+        st = load_library().pic_unet_set_conv_impl(self.h, int(impl))
+        if st != PIC_OK:
+            raise PicError(st, "pic_unet_set_conv_impl")
+
+    def status(self):
+        """PIC_ETIMEOUT if a bounded wait of a tensor-core kernel gave up."""
+        return load_library().pic_unet_status(self.h)
 
     def init(self, seed: int = 0):
         """He initialisation by the library (seeded Philox draws), zero biases."""

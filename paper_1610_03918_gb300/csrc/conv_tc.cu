@@ -1,0 +1,400 @@
+// 3x3 convolutions of the warm-start U-Net on the fifth-generation tensor
+// cores: an implicit GEMM whose products run as tcgen05.mma with the FP32
+// accumulator in tensor memory (TMEM), operands staged in shared memory by
+// the tensor memory accelerator (TMA).
+//
+// out[b][h][w][n] = act(bias[n] + sum_{dy,dx,c} in[b][h+dy-1][w+dx-1][c] W[n][3 dy + dx][c])
+// with BF16 tensors in NHWC (channel slices given by a channel stride and
+// offset), FP32 accumulation, act = ReLU or identity, zero padding.
+//
+// One CTA computes a tile of M = 128 output pixels (a BH x BW block of one
+// image, BW = min(W, 128) rounded down to a power of two) for all N = cout
+// output channels.  The K loop runs over the 9 taps times cin / KB channel
+// blocks.  For each block a 4-D TMA box {KB channels, BW, BH, 1} of the input,
+// shifted by the tap, lands in shared memory in the swizzled K-major layout
+// the MMA reads (zero fill supplies the padding), and a 2-D box {KB, N} of
+// the weights [cout][9][cin] beside it.  Warp 0 lane 0 issues the TMA loads
+// into a ring of stages (mbarrier expect-tx), warp 1 lane 0 issues KB / 16
+// MMAs of 128 x N x 16 per stage and releases the stage by tcgen05.commit;
+// then all four warps read their 32 TMEM lanes (one pixel per thread),
+// add the bias, apply the activation and store BF16.  Every wait is bounded:
+// a wait that gives up sets the error word and the CTA winds down (releasing
+// its TMEM) instead of hanging.
+#include <cuda.h>
+#include <cuda_bf16.h>
+#include <cuda_runtime.h>
+#include <cudaTypedefs.h>
+
+#include <mutex>
+
+#include "internal.cuh"
+
+namespace picgb {
+namespace tc {
+
+typedef __nv_bfloat16 bf16;
+
+constexpr int kM = 128;            // output pixels per CTA = TMEM lanes
+constexpr int kThreads = 128;      // four warps
+constexpr uint32_t kSpin = 1u << 22;   // polls of one wait before it gives up
+
+// ---------------------------------------------------------------- PTX wrappers
+__device__ __forceinline__ uint32_t saddr(const void *p) {
+  return static_cast<uint32_t>(__cvta_generic_to_shared(p));
+}
+__device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
+  asm volatile("mbarrier.init.shared::cta.b64 [%0], %1;" ::"r"(bar), "r"(count) : "memory");
+}
+__device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
+  asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
+}
+__device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
+  uint32_t ok;
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "selp.u32 %0, 1, 0, p;\n\t}"
+      : "=r"(ok)
+      : "r"(bar), "r"(parity)
+      : "memory");
+  return ok != 0;
+}
+// bounded wait for the phase of the given parity to complete
+__device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
+  for (uint32_t i = 0; i < kSpin; ++i)
+    if (mbar_try(bar, parity)) return true;
+  return false;
+}
+__device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            int c3, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.4d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5}], [%6];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
+                                            uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.2d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3}], [%4];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(bar)
+      : "memory");
+}
+__device__ __forceinline__ void tmem_alloc(uint32_t slot, uint32_t ncols) {
+  asm volatile("tcgen05.alloc.cta_group::1.sync.aligned.shared::cta.b32 [%0], %1;" ::"r"(slot), "r"(ncols)
+               : "memory");
+  asm volatile("tcgen05.relinquish_alloc_permit.cta_group::1.sync.aligned;" ::: "memory");
+}
+__device__ __forceinline__ void tmem_dealloc(uint32_t taddr, uint32_t ncols) {
+  asm volatile("tcgen05.dealloc.cta_group::1.sync.aligned.b32 %0, %1;" ::"r"(taddr), "r"(ncols) : "memory");
+}
+__device__ __forceinline__ void tc_fence_before() {
+  asm volatile("tcgen05.fence::before_thread_sync;" ::: "memory");
+}
+__device__ __forceinline__ void tc_fence_after() {
+  asm volatile("tcgen05.fence::after_thread_sync;" ::: "memory");
+}
+// D[tmem] (+)= A[smem] . B[smem]^T, M = 128, N from the instruction descriptor, K = 16
+__device__ __forceinline__ void mma_bf16(uint32_t tmem_d, uint64_t da, uint64_t db, uint32_t idesc,
+                                         uint32_t accumulate) {
+  asm volatile(
+      "{\n\t.reg .pred p;\n\t"
+      "setp.ne.b32 p, %4, 0;\n\t"
+      "tcgen05.mma.cta_group::1.kind::f16 [%0], %1, %2, %3, p;\n\t}" ::"r"(tmem_d),
+      "l"(da), "l"(db), "r"(idesc), "r"(accumulate)
+      : "memory");
+}
+// arrives on the mbarrier once every MMA this thread issued before has completed
+__device__ __forceinline__ void mma_commit(uint32_t bar) {
+  asm volatile("tcgen05.commit.cta_group::1.mbarrier::arrive::one.shared::cluster.b64 [%0];" ::"r"(bar)
+               : "memory");
+}
+// 32 lanes x 16 consecutive 32-bit columns: register k of lane l = TMEM[lane base + l][col + k]
+__device__ __forceinline__ void tmem_ld16(uint32_t taddr, uint32_t (&r)[16]) {
+  asm volatile(
+      "tcgen05.ld.sync.aligned.32x32b.x16.b32 "
+      "{%0, %1, %2, %3, %4, %5, %6, %7, %8, %9, %10, %11, %12, %13, %14, %15}, [%16];"
+      : "=r"(r[0]), "=r"(r[1]), "=r"(r[2]), "=r"(r[3]), "=r"(r[4]), "=r"(r[5]), "=r"(r[6]),
+        "=r"(r[7]), "=r"(r[8]), "=r"(r[9]), "=r"(r[10]), "=r"(r[11]), "=r"(r[12]), "=r"(r[13]),
+        "=r"(r[14]), "=r"(r[15])
+      : "r"(taddr));
+  asm volatile("tcgen05.wait::ld.sync.aligned;" ::: "memory");
+}
+
+// Shared-memory matrix descriptor of a K-major operand tile in the swizzled
+// layout TMA wrote: start address, the (unused) leading byte offset, the
+// stride between groups of 8 rows (8 x row bytes), the descriptor version of
+// this architecture, and the swizzle mode (2: 128 B, 4: 64 B, 6: 32 B rows).
+template <int KB>
+struct Swz {
+  static constexpr uint32_t row_bytes = KB * 2;
+  static constexpr uint64_t layout = KB == 64 ? 2 : (KB == 32 ? 4 : 6);
+};
+template <int KB>
+__device__ __forceinline__ uint64_t smem_desc(uint32_t addr) {
+  return uint64_t((addr & 0x3FFFF) >> 4) | (uint64_t(1) << 16) |
+         (uint64_t((8 * Swz<KB>::row_bytes) >> 4) << 32) | (uint64_t(1) << 46) | (Swz<KB>::layout << 61);
+}
+// Instruction descriptor of kind::f16: FP32 accumulator, BF16 A and B, both
+// K-major, N / 8 and M / 16.
+template <int N>
+__host__ __device__ constexpr uint32_t instr_desc() {
+  return (1u << 4) | (1u << 7) | (1u << 10) | (uint32_t(N >> 3) << 17) | (uint32_t(kM >> 4) << 24);
+}
+
+struct TCArgs {
+  bf16 *out;
+  int out_cs, out_off;
+  const float *bias;   // [cout] or null
+  int relu;
+  int B, H, W, cin, in_off;
+  int BW, BH, tiles_w, tiles_h;
+  int *err;            // error word: 1 producer, 2 MMA, 3 epilogue wait gave up
+};
+
+template <int N, int KB, int STAGES>
+struct Layout {
+  static constexpr uint32_t A_BYTES = kM * KB * 2;
+  static constexpr uint32_t B_BYTES = N * KB * 2;
+  static constexpr uint32_t BAR_OFF = STAGES * (A_BYTES + B_BYTES);
+  static constexpr uint32_t BYTES = BAR_OFF + (2 * STAGES + 1) * 8 + 16 + 1024;   // + alignment slack
+  static constexpr uint32_t NCOLS = N < 32 ? 32 : N;
+};
+
+template <int N, int KB, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TCArgs a) {
+  using L = Layout<N, KB, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t sA = saddr(smem), sB = sA + STAGES * L::A_BYTES;
+  const uint32_t bar0 = sA + L::BAR_OFF;           // full[s] = bar0 + 8 s, empty[s] = bar0 + 8 (STAGES + s)
+  const uint32_t done = bar0 + 16 * STAGES;
+  uint32_t *slot = reinterpret_cast<uint32_t *>(smem + L::BAR_OFF + (2 * STAGES + 1) * 8);
+  __shared__ int s_fail;
+
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  int t = blockIdx.x;
+  const int tw = t % a.tiles_w;
+  t /= a.tiles_w;
+  const int th = t % a.tiles_h;
+  const int b = t / a.tiles_h;
+  const int w0 = tw * a.BW, h0 = th * a.BH;
+
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(bar0 + 8 * s, 1);
+      mbar_init(bar0 + 8 * (STAGES + s), 1);
+    }
+    mbar_init(done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(saddr(slot), L::NCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+  const int kchunks = a.cin / KB;
+  const int nk = 9 * kchunks;
+
+  if (tid == 0) {
+    // TMA producer: stage s of round r is reused once the MMAs of round r - 1 released it
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (kb >= STAGES && !mbar_wait(bar0 + 8 * (STAGES + s), ph ^ 1)) {
+        atomicExch(&s_fail, 1);
+        atomicCAS(a.err, 0, 1);
+        break;
+      }
+      if (s_fail) break;
+      const int tap = kb / kchunks, c0 = (kb - tap * kchunks) * KB;
+      const int dy = tap / 3 - 1, dx = tap - 3 * (tap / 3) - 1;
+      mbar_expect_tx(bar0 + 8 * s, L::A_BYTES + L::B_BYTES);
+      tma_load_4d(sA + s * L::A_BYTES, &tmA, a.in_off + c0, w0 + dx, h0 + dy, b, bar0 + 8 * s);
+      tma_load_2d(sB + s * L::B_BYTES, &tmB, tap * a.cin + c0, 0, bar0 + 8 * s);
+    }
+  } else if (tid == 32) {
+    // MMA issuer
+    constexpr uint32_t idesc = instr_desc<N>();
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(bar0 + 8 * s, ph)) {
+        atomicExch(&s_fail, 1);
+        atomicCAS(a.err, 0, 2);
+        break;
+      }
+      tc_fence_after();
+      const uint64_t da = smem_desc<KB>(sA + s * L::A_BYTES);
+      const uint64_t db = smem_desc<KB>(sB + s * L::B_BYTES);
+#pragma unroll
+      for (int k = 0; k < KB / 16; ++k)   // 16 elements = 32 bytes along the swizzled row
+        mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+      mma_commit(bar0 + 8 * (STAGES + s));
+    }
+    mma_commit(done);
+  }
+
+  // epilogue: thread (warp w, lane l) owns pixel 32 w + l, the accumulator's TMEM lane
+  __syncwarp();
+  const bool ok = mbar_wait(done, 0);
+  tc_fence_after();
+  if (!ok) atomicCAS(a.err, 0, 3);
+  const int p = 32 * warp + lane;
+  const int h = h0 + p / a.BW, w = w0 + p % a.BW;
+  const bool inside = h < a.H && w < a.W;
+  bf16 *dst = a.out + ((size_t(b) * a.H + h) * a.W + w) * a.out_cs + a.out_off;
+  const uint32_t tl = tmem + (uint32_t(32 * warp) << 16);
+#pragma unroll 1
+  for (int n0 = 0; n0 < N; n0 += 16) {
+    uint32_t r[16];
+    tmem_ld16(tl + n0, r);
+    if (ok && !s_fail && inside) {
+      __align__(16) bf16 o[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        float v = __uint_as_float(r[k]) + (a.bias ? __ldg(a.bias + n0 + k) : 0.f);
+        if (a.relu) v = fmaxf(v, 0.f);
+        o[k] = __float2bfloat16_rn(v);
+      }
+      reinterpret_cast<uint4 *>(dst + n0)[0] = reinterpret_cast<const uint4 *>(o)[0];
+      reinterpret_cast<uint4 *>(dst + n0)[1] = reinterpret_cast<const uint4 *>(o)[1];
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
+}
+
+// ---------------------------------------------------------------- host side
+PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
+  static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
+  static std::once_flag once;
+  std::call_once(once, [] {
+    void *p = nullptr;
+    cudaDriverEntryPointQueryResult q;
+    if (cudaGetDriverEntryPointByVersion("cuTensorMapEncodeTiled", &p, 12000, cudaEnableDefault, &q) ==
+            cudaSuccess &&
+        q == cudaDriverEntryPointSuccess)
+      fn = reinterpret_cast<PFN_cuTensorMapEncodeTiled_v12000>(p);
+  });
+  return fn;
+}
+
+CUtensorMapSwizzle swizzle_of(int kb) {
+  return kb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (kb == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
+}
+
+template <int N, int KB>
+constexpr int stages_of() {
+  return (N * KB * 2 + kM * KB * 2) * 4 <= 160 * 1024 ? 4 : 3;
+}
+
+// the dynamic shared memory size of one instantiation (set once per process,
+// before any stream capture)
+template <int N, int KB>
+cudaError_t prepare_nk() {
+  constexpr int STAGES = stages_of<N, KB>();
+  static cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<N, KB, STAGES>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(Layout<N, KB, STAGES>::BYTES));
+  return e;
+}
+
+template <int N, int KB>
+cudaError_t launch_nk(const ConvTC &c, cudaStream_t s) {
+  constexpr int STAGES = stages_of<N, KB>();
+  using L = Layout<N, KB, STAGES>;
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  CUtensorMap ta, tb;
+  // input: {channels (the buffer's channel stride), W, H, B}; box {KB, BW, BH, 1}
+  const cuuint64_t adim[4] = {cuuint64_t(c.in_cs), cuuint64_t(c.W), cuuint64_t(c.H), cuuint64_t(c.B)};
+  const cuuint64_t astr[3] = {cuuint64_t(c.in_cs) * 2, cuuint64_t(c.in_cs) * 2 * c.W,
+                              cuuint64_t(c.in_cs) * 2 * c.W * c.H};
+  const int BW = c.W >= kM ? kM : (1 << (31 - __builtin_clz(unsigned(c.W))));
+  const int BH = kM / BW;
+  const cuuint32_t abox[4] = {cuuint32_t(KB), cuuint32_t(BW), cuuint32_t(BH), 1};
+  const cuuint32_t one[4] = {1, 1, 1, 1};
+  if (fn(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(c.in), adim, astr, abox, one,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(KB), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  // weights [cout][9][cin]: {9 cin, cout}; box {KB, N}
+  const cuuint64_t bdim[2] = {cuuint64_t(9) * c.cin, cuuint64_t(c.cout)};
+  const cuuint64_t bstr[1] = {cuuint64_t(9) * c.cin * 2};
+  const cuuint32_t bbox[2] = {cuuint32_t(KB), cuuint32_t(N)};
+  if (fn(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(c.w), bdim, bstr, bbox, one,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(KB), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  TCArgs a;
+  a.out = c.out;
+  a.out_cs = c.out_cs;
+  a.out_off = c.out_off;
+  a.bias = c.bias;
+  a.relu = c.relu;
+  a.B = c.B;
+  a.H = c.H;
+  a.W = c.W;
+  a.cin = c.cin;
+  a.in_off = c.in_off;
+  a.BW = BW;
+  a.BH = BH;
+  a.tiles_w = (c.W + BW - 1) / BW;
+  a.tiles_h = (c.H + BH - 1) / BH;
+  a.err = c.err;
+  auto k = k_conv3x3_tc<N, KB, STAGES>;
+  const cudaError_t e = prepare_nk<N, KB>();
+  if (e != cudaSuccess) return e;
+  const long long tiles = (long long)a.tiles_w * a.tiles_h * c.B;
+  k<<<dim3(unsigned(tiles)), kThreads, L::BYTES, s>>>(ta, tb, a);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_n(const ConvTC &c, cudaStream_t s) {
+  if (c.cin % 64 == 0) return launch_nk<N, 64>(c, s);
+  if (c.cin % 32 == 0) return launch_nk<N, 32>(c, s);
+  return launch_nk<N, 16>(c, s);
+}
+
+template <int N>
+cudaError_t prepare_n() {
+  cudaError_t e = prepare_nk<N, 64>();
+  if (e == cudaSuccess) e = prepare_nk<N, 32>();
+  if (e == cudaSuccess) e = prepare_nk<N, 16>();
+  return e;
+}
+
+}  // namespace tc
+
+cudaError_t conv3x3_tc_prepare() {
+  cudaError_t e = tc::prepare_n<32>();
+  if (e == cudaSuccess) e = tc::prepare_n<64>();
+  if (e == cudaSuccess) e = tc::prepare_n<128>();
+  if (e == cudaSuccess) e = tc::prepare_n<256>();
+  return e;
+}
+
+bool conv3x3_tc_supported(int cin, int cout, int in_cs, int in_off, int out_cs, int out_off, int W) {
+  return cin >= 16 && cin % 16 == 0 && (cout == 32 || cout == 64 || cout == 128 || cout == 256) &&
+         in_cs % 8 == 0 && in_off % 8 == 0 && out_cs % 8 == 0 && out_off % 8 == 0 && W >= 8 &&
+         tc::encode_fn() != nullptr;
+}
+
+cudaError_t conv3x3_tc(const ConvTC &c, cudaStream_t s) {
+  if (!conv3x3_tc_supported(c.cin, c.cout, c.in_cs, c.in_off, c.out_cs, c.out_off, c.W))
+    return cudaErrorNotSupported;
+  switch (c.cout) {
+    case 32: return tc::launch_n<32>(c, s);
+    case 64: return tc::launch_n<64>(c, s);
+    case 128: return tc::launch_n<128>(c, s);
+    default: return tc::launch_n<256>(c, s);
+  }
+}
+
+}  // namespace picgb

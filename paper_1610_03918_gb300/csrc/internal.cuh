@@ -1,6 +1,7 @@
 // Internal declarations shared by the library's translation units.
 #pragma once
 
+#include <cuda_bf16.h>
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -426,6 +427,24 @@ cudaError_t launch_field(pic_ctx *c);
 // guess phi = phi_L + s y on the free nodes (device-side scale)
 cudaError_t launch_learned_guess(pic_ctx *c);
 pic_status learned_target(pic_ctx *c, int hpad, double scale, float *t);
+
+// conv_tc.cu: one 3x3 convolution on the tcgen05 tensor cores (BF16 NHWC,
+// FP32 accumulation, bias and optional ReLU)
+struct ConvTC {
+  const __nv_bfloat16 *in;
+  int in_cs, in_off, cin;
+  const __nv_bfloat16 *w;     // [cout][9][cin]
+  const float *bias;          // [cout] or null
+  __nv_bfloat16 *out;
+  int out_cs, out_off, cout;
+  int B, H, W;
+  int relu;
+  int *err;                   // device error word (a bounded wait gave up)
+};
+bool conv3x3_tc_supported(int cin, int cout, int in_cs, int in_off, int out_cs, int out_off, int W);
+cudaError_t conv3x3_tc(const ConvTC &c, cudaStream_t s);
+// sets the kernels' shared-memory attributes (before any stream capture)
+cudaError_t conv3x3_tc_prepare();
 
 // unet.cu
 void unet_forward_only(pic_unet *u, const float *x);

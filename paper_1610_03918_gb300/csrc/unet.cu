@@ -558,6 +558,8 @@ struct pic_unet {
   // activations (BF16 NHWC) and gradients
   picgb::unet::bf16 *x16, *a[4], *cat[3], *da[3], *dout[3], *p[4], *b3;
   picgb::unet::bf16 *gx[4], *gcat[3], *gda[3], *gdout[3], *gp[4], *gb3, *dpre[4];
+  int conv_impl = 0;                     // 3x3 convolutions: 0 tcgen05 where it applies, 1 mma.sync
+  int *d_err = nullptr;                  // error word of the tcgen05 kernels (a wait gave up)
 };
 
 namespace picgb {
@@ -576,9 +578,35 @@ enum { E0A, E0B, E1A, E1B, E2A, E2B, E3A, E3B, D2A, D2B, D1A, D1B, D0A, D0B };
 
 int pix(const pic_unet *u, int l) { return u->B * (u->H >> l) * (u->W >> l); }
 
+// the tcgen05 convolution when the net uses it and the shapes allow it
+bool conv_tc(pic_unet *u, const bf16 *in, int in_cs, int in_off, int cin, const bf16 *w,
+             const float *bias, bf16 *out, int out_cs, int out_off, int cout, int l, bool relu) {
+  if (u->conv_impl != 0) return false;
+  ConvTC c;
+  c.in = in;
+  c.in_cs = in_cs;
+  c.in_off = in_off;
+  c.cin = cin;
+  c.w = w;
+  c.bias = bias;
+  c.out = out;
+  c.out_cs = out_cs;
+  c.out_off = out_off;
+  c.cout = cout;
+  c.B = u->B;
+  c.H = u->H >> l;
+  c.W = u->W >> l;
+  c.relu = relu ? 1 : 0;
+  c.err = u->d_err;
+  if (!conv3x3_tc_supported(cin, cout, in_cs, in_off, out_cs, out_off, c.W)) return false;
+  return conv3x3_tc(c, u->stream) == cudaSuccess;
+}
+
 void conv_fwd(pic_unet *u, int ci, const bf16 *in, int in_cs, int in_off, bf16 *out, int out_cs,
               int out_off, int l, bool relu) {
   const pic_unet::Conv &c = u->conv[ci];
+  if (conv_tc(u, in, in_cs, in_off, c.cin_c, c.w, u->P + c.b_off, out, out_cs, out_off, c.cout, l, relu))
+    return;
   ConvArgs a;
   a.in = in;
   a.in_cs = in_cs;
@@ -609,6 +637,7 @@ void conv_fwd(pic_unet *u, int ci, const bf16 *in, int in_cs, int in_off, bf16 *
 void conv_back_data(pic_unet *u, int ci, const bf16 *dpre, bf16 *gin, int gin_cs, int gin_off, int l) {
   const pic_unet::Conv &c = u->conv[ci];
   k_wflip<<<gridn((long long)c.cout * 9 * c.cin_c), 256, 0, u->stream>>>(c.w, c.wt, c.cout, c.cin_c);
+  if (conv_tc(u, dpre, c.cout, 0, c.cout, c.wt, nullptr, gin, gin_cs, gin_off, c.cin_c, l, false)) return;
   ConvArgs a;
   a.in = dpre;
   a.in_cs = c.cout;
@@ -820,6 +849,7 @@ pic_status pic_unet_create(int32_t batch, int32_t height, int32_t width, void *s
   u->M = (float *)A(off * 4);
   u->V = (float *)A(off * 4);
   u->d_loss = (double *)A(8);
+  u->d_err = (int *)A(4);
   for (auto &c : u->conv) {
     c.w = (bf16 *)A(size_t(c.cout) * 9 * c.cin_c * 2);
     c.wt = (bf16 *)A(size_t(c.cout) * 9 * c.cin_c * 2);
@@ -858,6 +888,9 @@ pic_status pic_unet_create(int32_t batch, int32_t height, int32_t width, void *s
   cudaMemsetAsync(u->P, 0, size_t(off) * 4, u->stream);
   cudaMemsetAsync(u->M, 0, size_t(off) * 4, u->stream);
   cudaMemsetAsync(u->V, 0, size_t(off) * 4, u->stream);
+  cudaMemsetAsync(u->d_err, 0, 4, u->stream);
+  if (picgb::conv3x3_tc_prepare() != cudaSuccess) u->conv_impl = 1;   // no tcgen05 kernels: mma.sync
+  cudaGetLastError();
   if (cudaStreamSynchronize(u->stream) != cudaSuccess) {
     pic_unet_free(u);
     return PIC_ECUDA;
@@ -907,6 +940,9 @@ pic_status pic_unet_gradients(pic_unet *u, const float *x, const float *t, float
   if (loss && cudaMemcpyAsync(loss, u->d_loss, 8, cudaMemcpyDeviceToHost, u->stream) != cudaSuccess)
     return PIC_ECUDA;
   if (cudaStreamSynchronize(u->stream) != cudaSuccess) return PIC_ECUDA;
+  int err = 0;
+  if (cudaMemcpy(&err, u->d_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
+  if (err) return PIC_ETIMEOUT;
   return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
 }
 
@@ -970,6 +1006,99 @@ pic_status pic_unet_load(pic_unet *u, const char *path) {
   std::fclose(f);
   if (r != size_t(u->nparam)) return PIC_EINVAL;   // too short, or longer than this network
   return pic_unet_set_params(u, h.data());
+}
+
+}  // extern "C"
+
+namespace {
+// error word of pic_conv3x3_bf16's tcgen05 kernel (a bounded wait gave up)
+__device__ int g_conv_err;
+}  // namespace
+
+extern "C" {
+
+pic_status pic_conv3x3_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const void *in, int32_t in_cs,
+                            int32_t in_off, int32_t cin, const void *w, const float *bias, int32_t relu,
+                            void *out, int32_t out_cs, int32_t out_off, int32_t cout, void *stream) {
+  if (!in || !w || !out || B < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 || in_off + cin > in_cs ||
+      out_off + cout > out_cs || impl < 0 || impl > 1)
+    return PIC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bf16 *bin = static_cast<const bf16 *>(in), *bw = static_cast<const bf16 *>(w);
+  bf16 *bout = static_cast<bf16 *>(out);
+  if (impl == 0) {
+    int *err = nullptr;
+    if (cudaGetSymbolAddress((void **)&err, g_conv_err) != cudaSuccess) return PIC_ECUDA;
+    if (!picgb::conv3x3_tc_supported(cin, cout, in_cs, in_off, out_cs, out_off, W)) return PIC_EINVAL;
+    if (cudaMemsetAsync(err, 0, 4, s) != cudaSuccess) return PIC_ECUDA;
+    picgb::ConvTC c;
+    c.in = bin;
+    c.in_cs = in_cs;
+    c.in_off = in_off;
+    c.cin = cin;
+    c.w = bw;
+    c.bias = bias;
+    c.out = bout;
+    c.out_cs = out_cs;
+    c.out_off = out_off;
+    c.cout = cout;
+    c.B = B;
+    c.H = H;
+    c.W = W;
+    c.relu = relu ? 1 : 0;
+    c.err = err;
+    if (picgb::conv3x3_tc(c, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+    int e = 0;
+    if (cudaMemcpy(&e, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
+    return e ? PIC_ETIMEOUT : PIC_OK;
+  }
+  // the mma.sync implicit GEMM: cout 32 (cin 16 or a multiple of 32) or a multiple of 64
+  ConvArgs a;
+  a.in = bin;
+  a.in_cs = in_cs;
+  a.in_off = in_off;
+  a.cin = cin;
+  a.w = bw;
+  a.bias = bias;
+  a.out = bout;
+  a.out_cs = out_cs;
+  a.out_off = out_off;
+  a.cout = cout;
+  a.B = B;
+  a.H = H;
+  a.W = W;
+  a.relu = relu ? 1 : 0;
+  const int nwt = (W + kTM - 1) / kTM;
+  if (cout == 32 && cin == 16)
+    k_conv3x3<32, 16><<<dim3(B * H * nwt, 1), kConvThreads, 0, s>>>(a);
+  else if (cout == 32 && cin % 32 == 0)
+    k_conv3x3<32, 32><<<dim3(B * H * nwt, 1), kConvThreads, 0, s>>>(a);
+  else if (cout % 64 == 0 && cin % 32 == 0)
+    k_conv3x3<64, 32><<<dim3(B * H * nwt, cout / 64), kConvThreads, 0, s>>>(a);
+  else
+    return PIC_EINVAL;
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+  return PIC_OK;
+}
+
+pic_status pic_unet_set_conv_impl(pic_unet *u, int32_t impl) {
+  if (!u || impl < 0 || impl > 1) return PIC_EINVAL;
+  if (cudaStreamSynchronize(u->stream) != cudaSuccess) return PIC_ECUDA;
+  u->conv_impl = impl;
+  return PIC_OK;
+}
+
+pic_status pic_unet_status(pic_unet *u) {
+  if (!u) return PIC_EINVAL;
+  int err = 0;
+  if (cudaStreamSynchronize(u->stream) != cudaSuccess ||
+      cudaMemcpy(&err, u->d_err, 4, cudaMemcpyDeviceToHost) != cudaSuccess)
+    return PIC_ECUDA;
+  if (err) {
+    cudaMemset(u->d_err, 0, 4);
+    return PIC_ETIMEOUT;
+  }
+  return PIC_OK;
 }
 
 pic_status pic_unet_free(pic_unet *u) {

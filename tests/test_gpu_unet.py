@@ -18,8 +18,8 @@ def bf16_round(a):
     return u.astype(np.uint32).view(np.float32).astype(np.float64)
 
 
-@pytest.fixture(scope="module")
-def setup():
+@pytest.fixture(scope="module", params=[0, 1], ids=["tcgen05", "mma_sync"])
+def setup(request):
     import torch
     import __graft_entry__
     __graft_entry__.build()
@@ -36,6 +36,7 @@ def setup():
     x = bf16_round(rng.standard_normal((B, H, W, 2)))
     t = rng.standard_normal((B, H, W))
     net = pg.Unet(B, H, W)
+    net.set_conv_impl(request.param)
     net.set_params(ounet.flat(p).astype(np.float32))
     xd = torch.tensor(x, dtype=torch.float32, device="cuda")
     td = torch.tensor(t, dtype=torch.float32, device="cuda")
