@@ -150,6 +150,8 @@ struct TCArgs {
   int relu;
   int B, H, W, cin, in_off;
   int BW, BH, tiles_w, tiles_h;
+  int n_base;          // transposed convolution: first GEMM column of this launch
+  int up_cout;         // transposed convolution: output channels (GEMM column n = (2a + c) up_cout + co)
   int *err;            // error word: 1 producer, 2 MMA, 3 epilogue wait gave up
 };
 
@@ -162,7 +164,10 @@ struct Layout {
   static constexpr uint32_t NCOLS = N < 32 ? 32 : N;
 };
 
-template <int N, int KB, int STAGES>
+// UP: the 2x2 stride-2 transposed convolution instead of the 3x3 one -- one
+// tap (the input pixel itself), GEMM columns n = (2a + c) up_cout + co, and
+// the result of input pixel (y, x) written to output pixel (2y + a, 2x + c).
+template <int N, int KB, int STAGES, bool UP>
 __global__ void __launch_bounds__(kThreads, 1)
     k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TCArgs a) {
   using L = Layout<N, KB, STAGES>;
@@ -197,7 +202,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *slot;
   const int kchunks = a.cin / KB;
-  const int nk = 9 * kchunks;
+  const int nk = (UP ? 1 : 9) * kchunks;
 
   if (tid == 0) {
     // TMA producer: stage s of round r is reused once the MMAs of round r - 1 released it
@@ -210,11 +215,14 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       if (s_fail) break;
-      const int tap = kb / kchunks, c0 = (kb - tap * kchunks) * KB;
+      const int tap = UP ? 4 : kb / kchunks, c0 = (kb - (UP ? 0 : tap) * kchunks) * KB;
       const int dy = tap / 3 - 1, dx = tap - 3 * (tap / 3) - 1;
       mbar_expect_tx(bar0 + 8 * s, L::A_BYTES + L::B_BYTES);
       tma_load_4d(sA + s * L::A_BYTES, &tmA, a.in_off + c0, w0 + dx, h0 + dy, b, bar0 + 8 * s);
-      tma_load_2d(sB + s * L::B_BYTES, &tmB, tap * a.cin + c0, 0, bar0 + 8 * s);
+      if (UP)
+        tma_load_2d(sB + s * L::B_BYTES, &tmB, c0, a.n_base, bar0 + 8 * s);
+      else
+        tma_load_2d(sB + s * L::B_BYTES, &tmB, tap * a.cin + c0, 0, bar0 + 8 * s);
     }
   } else if (tid == 32) {
     // MMA issuer
@@ -246,22 +254,33 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int p = 32 * warp + lane;
   const int h = h0 + p / a.BW, w = w0 + p % a.BW;
   const bool inside = h < a.H && w < a.W;
-  bf16 *dst = a.out + ((size_t(b) * a.H + h) * a.W + w) * a.out_cs + a.out_off;
   const uint32_t tl = tmem + (uint32_t(32 * warp) << 16);
 #pragma unroll 1
   for (int n0 = 0; n0 < N; n0 += 16) {
     uint32_t r[16];
     tmem_ld16(tl + n0, r);
     if (ok && !s_fail && inside) {
+      // destination and bias of these 16 columns (16 divides up_cout: one (a, c) per chunk)
+      bf16 *dst;
+      int co;
+      if (UP) {
+        const int n = a.n_base + n0, ac = n / a.up_cout;
+        co = n - ac * a.up_cout;
+        const int oh = 2 * h + (ac >> 1), ow = 2 * w + (ac & 1);
+        dst = a.out + ((size_t(b) * 2 * a.H + oh) * 2 * a.W + ow) * a.out_cs + a.out_off + co;
+      } else {
+        co = n0;
+        dst = a.out + ((size_t(b) * a.H + h) * a.W + w) * a.out_cs + a.out_off + co;
+      }
       __align__(16) bf16 o[16];
 #pragma unroll
       for (int k = 0; k < 16; ++k) {
-        float v = __uint_as_float(r[k]) + (a.bias ? __ldg(a.bias + n0 + k) : 0.f);
+        float v = __uint_as_float(r[k]) + (a.bias ? __ldg(a.bias + co + k) : 0.f);
         if (a.relu) v = fmaxf(v, 0.f);
         o[k] = __float2bfloat16_rn(v);
       }
-      reinterpret_cast<uint4 *>(dst + n0)[0] = reinterpret_cast<const uint4 *>(o)[0];
-      reinterpret_cast<uint4 *>(dst + n0)[1] = reinterpret_cast<const uint4 *>(o)[1];
+      reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(o)[0];
+      reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
     }
   }
   tc_fence_before();
@@ -295,19 +314,18 @@ constexpr int stages_of() {
 
 // the dynamic shared memory size of one instantiation (set once per process,
 // before any stream capture)
-template <int N, int KB>
+template <int N, int KB, bool UP>
 cudaError_t prepare_nk() {
   constexpr int STAGES = stages_of<N, KB>();
-  static cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<N, KB, STAGES>,
+  static cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<N, KB, STAGES, UP>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               int(Layout<N, KB, STAGES>::BYTES));
   return e;
 }
 
-template <int N, int KB>
+template <int N, int KB, bool UP>
 cudaError_t launch_nk(const ConvTC &c, cudaStream_t s) {
   constexpr int STAGES = stages_of<N, KB>();
-  using L = Layout<N, KB, STAGES>;
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   CUtensorMap ta, tb;
@@ -323,9 +341,11 @@ cudaError_t launch_nk(const ConvTC &c, cudaStream_t s) {
          CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(KB), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
-  // weights [cout][9][cin]: {9 cin, cout}; box {KB, N}
-  const cuuint64_t bdim[2] = {cuuint64_t(9) * c.cin, cuuint64_t(c.cout)};
-  const cuuint64_t bstr[1] = {cuuint64_t(9) * c.cin * 2};
+  // weights [cout][9][cin]: {9 cin, cout}, or of the transposed convolution
+  // [4 up_cout][cin]: {cin, 4 up_cout}; box {KB, N}
+  const int taps = UP ? 1 : 9;
+  const cuuint64_t bdim[2] = {cuuint64_t(taps) * c.cin, cuuint64_t(UP ? 4 * c.up_cout : c.cout)};
+  const cuuint64_t bstr[1] = {cuuint64_t(taps) * c.cin * 2};
   const cuuint32_t bbox[2] = {cuuint32_t(KB), cuuint32_t(N)};
   if (fn(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(c.w), bdim, bstr, bbox, one,
          CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(KB), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
@@ -346,27 +366,30 @@ cudaError_t launch_nk(const ConvTC &c, cudaStream_t s) {
   a.BH = BH;
   a.tiles_w = (c.W + BW - 1) / BW;
   a.tiles_h = (c.H + BH - 1) / BH;
+  a.n_base = c.n_base;
+  a.up_cout = c.up_cout;
   a.err = c.err;
-  auto k = k_conv3x3_tc<N, KB, STAGES>;
-  const cudaError_t e = prepare_nk<N, KB>();
+  auto k = k_conv3x3_tc<N, KB, STAGES, UP>;
+  const cudaError_t e = prepare_nk<N, KB, UP>();
   if (e != cudaSuccess) return e;
   const long long tiles = (long long)a.tiles_w * a.tiles_h * c.B;
-  k<<<dim3(unsigned(tiles)), kThreads, L::BYTES, s>>>(ta, tb, a);
+  k<<<dim3(unsigned(tiles)), kThreads, Layout<N, KB, STAGES>::BYTES, s>>>(ta, tb, a);
   return cudaGetLastError();
 }
 
-template <int N>
+template <int N, bool UP>
 cudaError_t launch_n(const ConvTC &c, cudaStream_t s) {
-  if (c.cin % 64 == 0) return launch_nk<N, 64>(c, s);
-  if (c.cin % 32 == 0) return launch_nk<N, 32>(c, s);
-  return launch_nk<N, 16>(c, s);
+  if (c.cin % 64 == 0) return launch_nk<N, 64, UP>(c, s);
+  if (c.cin % 32 == 0) return launch_nk<N, 32, UP>(c, s);
+  return launch_nk<N, 16, UP>(c, s);
 }
 
 template <int N>
 cudaError_t prepare_n() {
-  cudaError_t e = prepare_nk<N, 64>();
-  if (e == cudaSuccess) e = prepare_nk<N, 32>();
-  if (e == cudaSuccess) e = prepare_nk<N, 16>();
+  cudaError_t e = cudaSuccess;
+  for (cudaError_t f : {prepare_nk<N, 64, false>(), prepare_nk<N, 32, false>(), prepare_nk<N, 16, false>(),
+                        prepare_nk<N, 64, true>(), prepare_nk<N, 32, true>(), prepare_nk<N, 16, true>()})
+    if (e == cudaSuccess) e = f;
   return e;
 }
 
@@ -389,11 +412,22 @@ bool conv3x3_tc_supported(int cin, int cout, int in_cs, int in_off, int out_cs, 
 cudaError_t conv3x3_tc(const ConvTC &c, cudaStream_t s) {
   if (!conv3x3_tc_supported(c.cin, c.cout, c.in_cs, c.in_off, c.out_cs, c.out_off, c.W))
     return cudaErrorNotSupported;
+  if (c.up_cout) {
+    // the transposed convolution's GEMM columns in launches of at most 256
+    if (c.up_cout % 16 || c.n_base % c.up_cout || c.n_base + c.cout > 4 * c.up_cout)
+      return cudaErrorNotSupported;
+    switch (c.cout) {
+      case 32: return tc::launch_n<32, true>(c, s);
+      case 64: return tc::launch_n<64, true>(c, s);
+      case 128: return tc::launch_n<128, true>(c, s);
+      default: return tc::launch_n<256, true>(c, s);
+    }
+  }
   switch (c.cout) {
-    case 32: return tc::launch_n<32>(c, s);
-    case 64: return tc::launch_n<64>(c, s);
-    case 128: return tc::launch_n<128>(c, s);
-    default: return tc::launch_n<256>(c, s);
+    case 32: return tc::launch_n<32, false>(c, s);
+    case 64: return tc::launch_n<64, false>(c, s);
+    case 128: return tc::launch_n<128, false>(c, s);
+    default: return tc::launch_n<256, false>(c, s);
   }
 }
 

@@ -440,6 +440,11 @@ struct ConvTC {
   int B, H, W;
   int relu;
   int *err;                   // device error word (a bounded wait gave up)
+  // transposed 2x2 stride-2 convolution instead (up_cout > 0): w is
+  // [4 up_cout][cin] (row (2a + c) up_cout + co), H x W the input's size,
+  // out 2H x 2W; this launch computes the cout GEMM columns from n_base
+  int up_cout = 0;
+  int n_base = 0;
 };
 bool conv3x3_tc_supported(int cin, int cout, int in_cs, int in_off, int out_cs, int out_off, int W);
 cudaError_t conv3x3_tc(const ConvTC &c, cudaStream_t s);

@@ -276,15 +276,6 @@ __global__ void __launch_bounds__(128) k_wgrad3x3(WgradArgs a) {
 #define GSTRIDE(i, n) \
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
-// input: x [B][H][W][2] FP32 -> [B][H][W][16] BF16, channels 2..15 zero
-__global__ void k_input(const float *x, bf16 *out, long long npix) {
-  GSTRIDE(p, npix) {
-    bf16 *o = out + p * kCin0;
-    o[0] = __float2bfloat16(x[2 * p]);
-    o[1] = __float2bfloat16(x[2 * p + 1]);
-    for (int c = 2; c < kCin0; ++c) o[c] = __float2bfloat16(0.f);
-  }
-}
 
 // dpre[p][c] = g[p][c] * (y[p][c] > 0) (contiguous output)
 __global__ void k_relu_mask(const bf16 *g, int g_cs, int g_off, const bf16 *y, int y_cs, int y_off,
@@ -323,20 +314,6 @@ __global__ void k_wflip(const bf16 *w, bf16 *wt, int cout, int cin) {
   }
 }
 
-// 2x2 average pool: out (H/2 x W/2) from in (H x W), C channels
-__global__ void k_pool(const bf16 *in, int in_cs, int in_off, bf16 *out, int C, int B, int H, int W) {
-  const int Ho = H / 2, Wo = W / 2;
-  GSTRIDE(i, (long long)B * Ho * Wo * C) {
-    const int c = int(i % C);
-    const long long p = i / C;
-    const int wo = int(p % Wo), ho = int((p / Wo) % Ho), b = int(p / ((long long)Wo * Ho));
-    float s = 0.f;
-    for (int a = 0; a < 2; ++a)
-      for (int d = 0; d < 2; ++d)
-        s += __bfloat162float(in[((size_t(b) * H + 2 * ho + a) * W + 2 * wo + d) * in_cs + in_off + c]);
-    out[i] = __float2bfloat16(0.25f * s);
-  }
-}
 
 // gradient of the pool, added into g (H x W, channel stride/offset)
 __global__ void k_pool_back_add(const bf16 *gp, bf16 *g, int g_cs, int g_off, int C, int B, int H, int W) {
@@ -433,14 +410,6 @@ __global__ void __launch_bounds__(256) k_up_back_w(const bf16 *in, int cin, cons
   if (ty == 0 && ci0 == 0 && co0 + tx < cout) atomicAdd(&db[co0 + tx], bacc);
 }
 
-// head: y[p] = sum_c h[p][c] w[c] + b
-__global__ void k_head_fwd(const bf16 *hin, const float *w, const float *b, float *y, long long npix) {
-  GSTRIDE(p, npix) {
-    float s = b[0];
-    for (int c = 0; c < kC0; ++c) s = fmaf(__bfloat162float(hin[p * kC0 + c]), w[c], s);
-    y[p] = s;
-  }
-}
 
 // MSE: dy = 2 (y - t) / n, loss partial sums in FP64
 __global__ void k_mse(const float *y, const float *t, float *dy, long long n, double *loss) {
@@ -523,6 +492,63 @@ __global__ void k_he_init(float *w, long long n, float std, uint2 key, uint32_t 
   }
 }
 
+// the transposed convolution's FP32 weights [2][2][ci][co] as the K-major
+// BF16 matrix of its GEMM: row n = (2a + c) cout + co, column ci
+__global__ void k_upw_to_bf16(const float *w, bf16 *wt, int cin, int cout) {
+  GSTRIDE(i, 4LL * cout * cin) {
+    const long long n = i / cin;
+    const int ci = int(i - n * cin);
+    const int ac = int(n / cout), co = int(n - (long long)ac * cout);
+    wt[i] = __float2bfloat16(w[(size_t(ac) * cin + ci) * cout + co]);
+  }
+}
+
+// network input: 2 channels padded to 16 with zeros, one 32-byte row per pixel
+__global__ void k_input_vec(const float2 *x, uint4 *out, long long npix) {
+  GSTRIDE(p, npix) {
+    const float2 v = x[p];
+    __align__(16) bf16 o[8] = {__float2bfloat16(v.x), __float2bfloat16(v.y)};
+    for (int c = 2; c < 8; ++c) o[c] = __float2bfloat16(0.f);
+    out[2 * p] = *reinterpret_cast<const uint4 *>(o);
+    out[2 * p + 1] = make_uint4(0u, 0u, 0u, 0u);
+  }
+}
+
+// 2x2 average pool, 8 channels (16 bytes) per thread
+__global__ void k_pool_vec(const bf16 *in, int in_cs, int in_off, bf16 *out, int C, int B, int H, int W) {
+  const int Ho = H / 2, Wo = W / 2, C8 = C / 8;
+  GSTRIDE(i, (long long)B * Ho * Wo * C8) {
+    const int c = int(i % C8) * 8;
+    const long long p = i / C8;
+    const int wo = int(p % Wo), ho = int((p / Wo) % Ho), b = int(p / ((long long)Wo * Ho));
+    float s[8] = {0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f, 0.f};
+    for (int a = 0; a < 2; ++a)
+      for (int d = 0; d < 2; ++d) {
+        const uint4 v = *reinterpret_cast<const uint4 *>(
+            in + ((size_t(b) * H + 2 * ho + a) * W + 2 * wo + d) * in_cs + in_off + c);
+        const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+        for (int k = 0; k < 8; ++k) s[k] += __bfloat162float(e[k]);
+      }
+    __align__(16) bf16 o[8];
+    for (int k = 0; k < 8; ++k) o[k] = __float2bfloat16(0.25f * s[k]);
+    *reinterpret_cast<uint4 *>(out + p * C + c) = *reinterpret_cast<const uint4 *>(o);
+  }
+}
+
+// head with 16-byte loads of the 32 input channels
+__global__ void k_head_vec(const bf16 *hin, const float *w, const float *b, float *y, long long npix) {
+  GSTRIDE(p, npix) {
+    const uint4 *src = reinterpret_cast<const uint4 *>(hin + p * kC0);
+    float s = b[0];
+    for (int q = 0; q < kC0 / 8; ++q) {
+      const uint4 v = src[q];
+      const bf16 *e = reinterpret_cast<const bf16 *>(&v);
+      for (int k = 0; k < 8; ++k) s = fmaf(__bfloat162float(e[k]), w[8 * q + k], s);
+    }
+    y[p] = s;
+  }
+}
+
 inline int gridn(long long n, int t = 256) {
   long long b = (n + t - 1) / t;
   return int(b < 1 ? 1 : (b > 65535 * 8 ? 65535 * 8 : b));
@@ -553,6 +579,7 @@ struct pic_unet {
   struct Up {
     int cin, cout;
     long long w_off, b_off;
+    picgb::unet::bf16 *wt;               // BF16 [4 cout][cin], row (2a + c) cout + co (tensor cores)
   } up[3];                               // up2, up1, up0 (index = level)
   long long head_w, head_b;
   // activations (BF16 NHWC) and gradients
@@ -708,21 +735,56 @@ void weights_to_bf16(pic_unet *u) {
   for (auto &c : u->conv)
     k_w_to_bf16<<<gridn((long long)c.cout * 9 * c.cin_c), 256, 0, u->stream>>>(u->P + c.w_off, c.w, c.cout,
                                                                              c.cin_m, c.cin_c);
+  for (auto &up : u->up)
+    k_upw_to_bf16<<<gridn(4LL * up.cout * up.cin), 256, 0, u->stream>>>(u->P + up.w_off, up.wt, up.cin,
+                                                                          up.cout);
+}
+
+// the transposed convolution of level l on the tensor cores (GEMM columns in
+// launches of at most 256); false where the kernel does not apply
+bool up_tc(pic_unet *u, int l, const bf16 *in, int in_cs) {
+  if (u->conv_impl != 0) return false;
+  const pic_unet::Up &up = u->up[l];
+  ConvTC c;
+  c.in = in;
+  c.in_cs = in_cs;
+  c.in_off = 0;
+  c.cin = up.cin;
+  c.w = up.wt;
+  c.bias = u->P + up.b_off;
+  c.out = u->cat[l];
+  c.out_cs = 2 * kC[l];
+  c.out_off = 0;
+  c.B = u->B;
+  c.H = u->H >> (l + 1);
+  c.W = u->W >> (l + 1);
+  c.relu = 0;
+  c.err = u->d_err;
+  c.up_cout = up.cout;
+  const int total = 4 * up.cout, step = total > 256 ? 256 : total;
+  if (!conv3x3_tc_supported(up.cin, step, in_cs, 0, c.out_cs, 0, c.W)) return false;
+  for (int n0 = 0; n0 < total; n0 += step) {
+    c.cout = step;
+    c.n_base = n0;
+    if (conv3x3_tc(c, u->stream) != cudaSuccess) return false;
+  }
+  return true;
 }
 
 void forward(pic_unet *u, const float *x) {
   const int C0 = kC[0], C1 = kC[1], C2 = kC[2], C3 = kC[3];
-  k_input<<<gridn(pix(u, 0)), 256, 0, u->stream>>>(x, u->x16, pix(u, 0));
+  k_input_vec<<<gridn(pix(u, 0)), 256, 0, u->stream>>>(reinterpret_cast<const float2 *>(x),
+                                                       reinterpret_cast<uint4 *>(u->x16), pix(u, 0));
   // encoder; each level's output is written into the skip half of its concat buffer
   conv_fwd(u, E0A, u->x16, kCin0, 0, u->a[0], C0, 0, 0, true);
   conv_fwd(u, E0B, u->a[0], C0, 0, u->cat[0], 2 * C0, C0, 0, true);
-  k_pool<<<gridn((long long)pix(u, 1) * C0), 256, 0, u->stream>>>(u->cat[0], 2 * C0, C0, u->p[1], C0, u->B, u->H, u->W);
+  k_pool_vec<<<gridn((long long)pix(u, 1) * C0 / 8), 256, 0, u->stream>>>(u->cat[0], 2 * C0, C0, u->p[1], C0, u->B, u->H, u->W);
   conv_fwd(u, E1A, u->p[1], C0, 0, u->a[1], C1, 0, 1, true);
   conv_fwd(u, E1B, u->a[1], C1, 0, u->cat[1], 2 * C1, C1, 1, true);
-  k_pool<<<gridn((long long)pix(u, 2) * C1), 256, 0, u->stream>>>(u->cat[1], 2 * C1, C1, u->p[2], C1, u->B, u->H >> 1, u->W >> 1);
+  k_pool_vec<<<gridn((long long)pix(u, 2) * C1 / 8), 256, 0, u->stream>>>(u->cat[1], 2 * C1, C1, u->p[2], C1, u->B, u->H >> 1, u->W >> 1);
   conv_fwd(u, E2A, u->p[2], C1, 0, u->a[2], C2, 0, 2, true);
   conv_fwd(u, E2B, u->a[2], C2, 0, u->cat[2], 2 * C2, C2, 2, true);
-  k_pool<<<gridn((long long)pix(u, 3) * C2), 256, 0, u->stream>>>(u->cat[2], 2 * C2, C2, u->p[3], C2, u->B, u->H >> 2, u->W >> 2);
+  k_pool_vec<<<gridn((long long)pix(u, 3) * C2 / 8), 256, 0, u->stream>>>(u->cat[2], 2 * C2, C2, u->p[3], C2, u->B, u->H >> 2, u->W >> 2);
   conv_fwd(u, E3A, u->p[3], C2, 0, u->a[3], C3, 0, 3, true);
   conv_fwd(u, E3B, u->a[3], C3, 0, u->b3, C3, 0, 3, true);
   // decoder
@@ -731,15 +793,16 @@ void forward(pic_unet *u, const float *x) {
   for (int l = 2; l >= 0; --l) {
     const pic_unet::Up &up = u->up[l];
     const int hl = u->H >> (l + 1), wl = u->W >> (l + 1);
-    k_up_fwd<<<gridn((long long)pix(u, l) * up.cout), 256, 0, u->stream>>>(
-        h, hc, u->P + up.w_off, u->P + up.b_off, u->cat[l], 2 * kC[l], 0, up.cout, u->B, hl, wl);
+    if (!up_tc(u, l, h, hc))
+      k_up_fwd<<<gridn((long long)pix(u, l) * up.cout), 256, 0, u->stream>>>(
+          h, hc, u->P + up.w_off, u->P + up.b_off, u->cat[l], 2 * kC[l], 0, up.cout, u->B, hl, wl);
     const int ca = (l == 2) ? D2A : (l == 1) ? D1A : D0A;
     conv_fwd(u, ca, u->cat[l], 2 * kC[l], 0, u->da[l], kC[l], 0, l, true);
     conv_fwd(u, ca + 1, u->da[l], kC[l], 0, u->dout[l], kC[l], 0, l, true);
     h = u->dout[l];
     hc = kC[l];
   }
-  k_head_fwd<<<gridn(pix(u, 0)), 256, 0, u->stream>>>(u->dout[0], u->P + u->head_w, u->P + u->head_b, u->y, pix(u, 0));
+  k_head_vec<<<gridn(pix(u, 0)), 256, 0, u->stream>>>(u->dout[0], u->P + u->head_w, u->P + u->head_b, u->y, pix(u, 0));
 }
 
 void backward(pic_unet *u) {
@@ -854,6 +917,7 @@ pic_status pic_unet_create(int32_t batch, int32_t height, int32_t width, void *s
     c.w = (bf16 *)A(size_t(c.cout) * 9 * c.cin_c * 2);
     c.wt = (bf16 *)A(size_t(c.cout) * 9 * c.cin_c * 2);
   }
+  for (auto &up : u->up) up.wt = (bf16 *)A(4 * size_t(up.cout) * up.cin * 2);
   u->g0tmp = (float *)A(size_t(kC[0]) * 9 * kCin0 * 4);
   const size_t np0 = size_t(batch) * height * width;
   u->y = (float *)A(np0 * 4);

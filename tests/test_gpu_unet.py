@@ -98,3 +98,30 @@ def test_unet_training_reduces_loss(setup):
         net.train_step(xd, td, 1e-3)
     l1, _ = net.gradients(xd, td)
     assert l1 < 0.7 * l0, (l0, l1)
+
+
+def test_unet_forward_every_layer_on_tensor_cores():
+    # 64 x 64: every level is at least 8 wide, so all fourteen 3x3 and all
+    # three transposed convolutions take the tcgen05 kernel; against the
+    # BF16-emulating oracle and against the mma.sync network
+    import torch
+    import paper_1610_03918_gb300 as pg
+    rng = np.random.default_rng(8)
+    p = ounet.init_params(7)
+    for n in p:
+        p[n] = bf16_round(p[n]) if not n.endswith(".b") else rng.standard_normal(p[n].shape) * 0.05
+    B, H, W = 1, 64, 64
+    x = bf16_round(rng.standard_normal((B, H, W, 2)))
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    ys = []
+    for impl in (0, 1):
+        net = pg.Unet(B, H, W)
+        net.set_conv_impl(impl)
+        net.set_params(ounet.flat(p).astype(np.float32))
+        ys.append(net.forward(xd).cpu().numpy())
+        assert net.status() == pg.PIC_OK
+        net.close()
+    yo, _ = ounet.forward(p, x, q=bf16_round)
+    for y in ys:
+        assert np.linalg.norm(y - yo) / np.linalg.norm(yo) < 1e-2
+    assert np.linalg.norm(ys[0] - ys[1]) / np.linalg.norm(ys[1]) < 1e-2
