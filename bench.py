@@ -411,7 +411,8 @@ def run_warmstart(args):
                 ring[int(rng.integers(len(ring)))] = pair
             t1 = time.perf_counter()
             t_data += t1 - td
-            if len(ring) >= args.batch:
+            # one Adam step per `batch` new pairs, on a minibatch drawn from the ring
+            if len(ring) >= args.batch and n_pairs % args.batch == 0:
                 idx = rng.choice(len(ring), args.batch, replace=False)
                 x = torch.stack([ring[i][0] for i in idx])
                 t = torch.stack([ring[i][1] for i in idx])
@@ -617,7 +618,7 @@ def main():
                     choices=["trench", "ensemble", "warmstart", "paper", "unet"],
                     help="trench: the 512x1024 trench run; ensemble: the 48-run width sweep; "
                          "warmstart: Poisson time to 1e-6 with the learned initial guess")
-    ap.add_argument("--train-widths", default="2,6,10,14,20")
+    ap.add_argument("--train-widths", default="2,4,5,6,7,8,9,10,12,13,14,15,16,17,18,20")
     ap.add_argument("--eval-widths", default="3,11,19")
     ap.add_argument("--pairs", type=int, default=2000, help="training pairs (warmstart)")
     ap.add_argument("--runs", type=int, default=10, help="training runs the pairs come from")
