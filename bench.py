@@ -306,6 +306,33 @@ def run_reference(args):
     return 0
 
 
+def ensemble_cut(pg, device, members, steps):
+    """A cut of the trench-width ensemble: members k = 0 .. members-1 of the
+    48-member recipe, one captured graph per ensemble step; particle-steps
+    per second over `steps` steps after 10 warm-up steps (CUDA events)."""
+    import torch
+    wl = [synth.ensemble_member(k).replace(sort_every=24) for k in range(members)]
+    batch = pg.Batch(wl, capacities=[int(synth.plasma_cells(w).sum()) * w.ppc for w in wl],
+                     device=device, timing=True)
+    for m, w in zip(batch.members, wl):
+        for s in (0, 1):
+            m.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
+    batch.step(10)
+    batch.timing()
+    live0 = sum(int(m.counts()[1].sum()) for m in batch.members)
+    batch.step(steps)
+    t = batch.timing()
+    live1 = sum(int(m.counts()[1].sum()) for m in batch.members)
+    batch.close()
+    torch.cuda.synchronize()
+    v = 0.5 * (live0 + live1) * steps / (t["ms"] * 1e-3)
+    return {"members": members, "live_particles": 0.5 * (live0 + live1), "steps": steps,
+            "ms_per_step": t["ms"] / max(t["steps"], 1), "particle_steps_per_s": v,
+            "hbm_frac_at_40B": BYTES_PER_PARTICLE_STEP * v / 1e9 / _peaks()[0],
+            "note": "members 0.. of the 48-member width sweep (widths 1 + round(39k/47), grids "
+                    "128x256 .. 512x512, 64 ppc); bench.py --workload ensemble runs all 48"}
+
+
 def run_ensemble(args):
     """The trench-width sweep: members k = 0..M-1 of the recipe (widths
     1..40, grids 128x256 .. 512x512, 64 ppc), one graph launch per step."""
@@ -422,10 +449,31 @@ def run_warmstart(args):
             torch.cuda.synchronize()
             t_train += time.perf_counter() - t1
         sim.close()
-    del ring
+    # the network's error on pairs from the ring (training) and on held-out widths
+    def rel_mse(pairs_):
+        out = []
+        for x, t in pairs_:
+            loss, _ = probe.gradients(x[None], t[None])
+            out.append(loss / float((t * t).mean()))
+        return float(np.mean(out))
+    probe = pg.Unet(1, ws.padded_rows(1025), 512)
+    probe.set_params(net.get_params())
+    train_err = rel_mse(ring[:8]) if ring else None
+    held = []
+    for k, width in enumerate(int(v) for v in args.eval_widths.split(",")):
+        w = trench(width, 950 + k)
+        sim = pg.Sim(w, capacity=int(synth.plasma_cells(w).sum()) * w.ppc)
+        for s in (0, 1):
+            sim.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
+        sim.step(args.settle)
+        held += ws.dump_pairs(sim, steps=20, every=10)
+        sim.close()
+    held_err = rel_mse(held)
+    probe.close()
+    del held, ring
     eval_net = pg.Unet(1, ws.padded_rows(1025), 512)
     eval_net.set_params(net.get_params())
-    res, its = {}, {}
+    res, its, rel0 = {}, {}, {}
     for name, mode in (("zero", 0), ("previous", 1), ("learned", 3)):
         ms, it = [], []
         for k, width in enumerate(int(v) for v in args.eval_widths.split(",")):
@@ -439,14 +487,18 @@ def run_warmstart(args):
                 sim.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
             sim.step(args.settle)
             sim.timing()
+            r0 = []
             for _ in range(args.steps):
                 sim.step(1)
-                it.append(sim.poisson_stats()[0])
+                st = sim.poisson_stats()
+                it.append(st[0])
+                r0.append(st[4])
             tm = sim.timing()
             ms.append(tm["ms_poisson"] / max(tm["steps"], 1))
             sim.close()
         res[name] = float(np.mean(ms))
         its[name] = float(np.mean(it))
+        rel0[name] = float(np.exp(np.mean(np.log(np.maximum(r0, 1e-30)))))
     line = {
         "metric": "Poisson ms to 1e-6 residual (learned warm start)",
         "value": res["learned"], "unit": "ms", "higher_is_better": False, "n_gpus": 1,
@@ -461,6 +513,8 @@ def run_warmstart(args):
                    "train_s": t_train, "init": "library He initialisation (pic_unet_init)"},
         "ms_per_solve": res,
         "pcg_iterations_per_solve": its,
+        "initial_rel_residual_geomean": rel0,
+        "network_relative_mse": {"training_pairs": train_err, "held_out_pairs": held_err},
         "speedup_vs_zero": res["zero"] / res["learned"],
         "speedup_vs_previous": res["previous"] / res["learned"],
         "wall_s": time.perf_counter() - t0,
@@ -632,6 +686,10 @@ def main():
     ap.add_argument("--e2e-steps", type=int, default=3)
     ap.add_argument("--cold-steps", type=int, default=50, help="captured steps timed with a cold start")
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--no-extras", action="store_true",
+                    help="skip the U-Net forward and the ensemble cut in the trench line")
+    ap.add_argument("--ensemble-members", type=int, default=16)
+    ap.add_argument("--ensemble-steps", type=int, default=100)
     ap.add_argument("--ppc", type=int, default=None, help="override particles per cell")
     ap.add_argument("--poisson-method", default="auto", choices=["auto", "multigrid"],
                     help="inner Poisson solver: auto (direct where the box allows) or multigrid PCG")
@@ -819,6 +877,37 @@ def main():
                     "note": "per step: pic_load of the full state from pinned host memory, "
                             "pic_step(1), pic_diag(STATE) of both species (x, y, vx, vy, id as FP64)"}
 
+    # the warm-start network's forward pass at this grid (tcgen05 convolutions)
+    # and a cut of the trench-width ensemble, measured in the same run
+    unet = ens = None
+    if rank == 0 and not args.no_extras:
+        net = pg.Unet(1, 1032, 512)
+        net.init(seed=0)
+        xin = torch.randn((1, 1032, 512, 2), device="cuda")
+        for _ in range(3):
+            net.forward(xin)
+        torch.cuda.synchronize()
+        e0u = torch.cuda.Event(enable_timing=True)
+        e1u = torch.cuda.Event(enable_timing=True)
+        e0u.record(net.stream)
+        for _ in range(20):
+            net.forward(xin)
+        e1u.record(net.stream)
+        torch.cuda.synchronize()
+        ums = e0u.elapsed_time(e1u) / 20
+        bf16_peak = 1900.0
+        pp = os.path.join(ROOT, "MEASURED_PEAKS.json")
+        if os.path.exists(pp):
+            bf16_peak = float(json.load(open(pp))["bf16_tflops"])
+        ufl = unet_flops(1032, 512)
+        unet = {"forward_ms": ums, "tflops": ufl / (ums * 1e-3) / 1e12,
+                "frac_of_bf16_peak": ufl / (ums * 1e-3) / 1e12 / bf16_peak,
+                "note": "4-level BF16 U-Net at 1032 x 512, tcgen05 convolutions, CUDA events; "
+                        "bench.py --workload unet / warmstart for the full figures"}
+        net.close()
+        del xin
+        ens = ensemble_cut(pg, local, args.ensemble_members, args.ensemble_steps)
+
     cpu = errs = None
     if rank == 0 and not args.no_cpu_baseline:
         cpu = oracle_baseline(synth.trench_512x1024())
@@ -868,6 +957,8 @@ def main():
             "e2e_full_state": e2e_full if args.e2e_steps > 0 else None,
             "cpu_baseline": cpu,
             "errors_vs_oracle": errs,
+            "unet_forward": unet,
+            "ensemble": ens,
         }
         print(json.dumps(line), flush=True)
     sim.close()

@@ -193,7 +193,8 @@ enum {
   PIC_DIAG_E = 7,        /* [2*nxn*nyn]: Ex then Ey at the nodes */
   PIC_DIAG_STATE_E = 8,  /* [5*n]: x, y, vx, vy, id blocks of live electrons */
   PIC_DIAG_STATE_I = 9,  /* same for ions */
-  PIC_DIAG_POISSON = 10, /* [inner iterations, outer iterations, rel residual, ms] of the last solve */
+  PIC_DIAG_POISSON = 10, /* [inner iterations, outer iterations, rel residual, ms] of the last solve,
+                            and (with room for a fifth double) the rel residual of its initial guess */
   PIC_DIAG_STATUS = 11,  /* uint32: status word; reading clears it */
   PIC_DIAG_TIMING = 12,  /* [steps, ms particle kernel, ms sort, ms Poisson (the solve's
                             residual passes also form E), ms rho,

@@ -417,7 +417,9 @@ class Sim:
         return out
 
     def poisson_stats(self):
-        return self.diag(PIC_DIAG_POISSON, np.empty(4))[0]
+        """[inner iterations, outer passes, relative residual, ms, relative
+        residual of the initial guess] of the last solve."""
+        return self.diag(PIC_DIAG_POISSON, np.empty(5))[0]
 
     def timing(self):
         """Per-phase device time since the last call (and resets it):

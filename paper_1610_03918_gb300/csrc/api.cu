@@ -1496,6 +1496,10 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
       o[2] = ps.rel;
       o[3] = c->last_ms;
       count = 4;
+      if (need(5 * 8)) {
+        o[4] = ps.rel_first;
+        count = 5;
+      }
       break;
     }
     case PIC_DIAG_SORT: {

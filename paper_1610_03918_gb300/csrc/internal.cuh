@@ -161,6 +161,7 @@ struct PoissonState {
   double bb;          // ||b||^2
   double rr64;        // ||b - A phi||^2 (outer: the certificate)
   double rel;         // sqrt(rr64 / bb)
+  double rel_first;   // rel of the initial guess (the solve's first checking pass)
   double bmean;       // mean of b (doubly periodic box only)
   double rz, rz_old, rr, rr0;       // inner PCG: gamma = <r, z>, its previous value, ||r||^2
   double delta;                      // <z, A z>

@@ -589,6 +589,7 @@ __global__ void k_resid(FineArgs a) {
       ps->rel = double(sqrtf(c[0] / bbf));   // both norms in FP32 range
     else
       ps->rel = sqrt_ratio(rr, bb > 0 ? bb : 1.0);
+    if (first || bb_parts) ps->rel_first = ps->rel;
     const bool ok = ps->rel <= a.rtol || rr == 0.0;
     const bool give_up = !ok && ps->outer_iters >= kMaxOuter;
     if (give_up) atomicOr(a.status, PIC_ST_NOCONV);

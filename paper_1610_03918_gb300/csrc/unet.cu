@@ -761,14 +761,10 @@ bool up_tc(pic_unet *u, int l, const bf16 *in, int in_cs) {
   c.relu = 0;
   c.err = u->d_err;
   c.up_cout = up.cout;
-  const int total = 4 * up.cout, step = total > 256 ? 256 : total;
-  if (!conv3x3_tc_supported(up.cin, step, in_cs, 0, c.out_cs, 0, c.W)) return false;
-  for (int n0 = 0; n0 < total; n0 += step) {
-    c.cout = step;
-    c.n_base = n0;
-    if (conv3x3_tc(c, u->stream) != cudaSuccess) return false;
-  }
-  return true;
+  c.cout = 4 * up.cout;   // all GEMM columns in one launch
+  c.n_base = 0;
+  if (!conv3x3_tc_supported(up.cin, c.cout, in_cs, 0, c.out_cs, 0, c.W)) return false;
+  return conv3x3_tc(c, u->stream) == cudaSuccess;
 }
 
 void forward(pic_unet *u, const float *x) {

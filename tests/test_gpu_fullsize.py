@@ -43,7 +43,7 @@ def test_fullsize_deposit(full):
     # sampled nodes: the oracle deposits the particles of the four cells around each
     rng = np.random.default_rng(7)
     free = np.argwhere(geom.free)
-    nodes = free[rng.choice(len(free), 64, replace=False)]
+    nodes = free[rng.choice(len(free), 1024, replace=False)]
     near = np.zeros((w.nx, w.ny), bool)          # cells touching a sampled node
     for (i, j) in nodes:
         for di in (-1, 0):
