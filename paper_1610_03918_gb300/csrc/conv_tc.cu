@@ -36,7 +36,7 @@ typedef __nv_bfloat16 bf16;
 
 constexpr int kM = 128;            // output pixels per tile = TMEM lanes
 constexpr int kThreads = 192;      // TMA warp, MMA warp, four epilogue warps
-constexpr uint32_t kSpin = 1u << 22;   // polls of one wait before it gives up
+constexpr uint64_t kWaitNs = 2000000000ull;   // a wait gives up after 2 s (globaltimer)
 
 // ---------------------------------------------------------------- PTX wrappers
 __device__ __forceinline__ uint32_t saddr(const void *p) {
@@ -48,21 +48,30 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
+// one poll that suspends for at most about 20 us (the time hint, in ns)
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(parity)
+      : "r"(bar), "r"(parity), "r"(20000u)
       : "memory");
   return ok != 0;
 }
-// bounded wait for the phase of the given parity to complete
+__device__ __forceinline__ uint64_t gtime() {
+  uint64_t t;
+  asm volatile("mov.u64 %0, %%globaltimer;" : "=l"(t));
+  return t;
+}
+// wait for the phase of the given parity to complete, giving up after kWaitNs
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
-  for (uint32_t i = 0; i < kSpin; ++i)
+  if (mbar_try(bar, parity)) return true;
+  const uint64_t t0 = gtime();
+  do {
     if (mbar_try(bar, parity)) return true;
+  } while (gtime() - t0 < kWaitNs);
   return false;
 }
 __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
@@ -153,7 +162,7 @@ struct TCArgs {
   int n_base;          // transposed convolution: first GEMM column of this launch
   int nblocks;         // column blocks of NT per tile
   int up_cout;         // transposed convolution: output channels (GEMM column n = (2a + c) up_cout + co)
-  int *err;            // error word: 1 producer, 2 MMA, 3 epilogue wait gave up
+  int *err;            // error word: site (1 producer, 2 MMA stage, 3 epilogue, 4 MMA accumulator) | iteration << 4
 };
 
 template <int NT, int KB, int STAGES>
@@ -216,7 +225,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   auto fail = [&](int code) {
     atomicExch(&s_fail, 1);
     atomicCAS(a.err, 0, code);
-  };
+  };   // code = site | iteration << 4
 
   if (warp == 0) {
     if (lane == 0) {
@@ -231,7 +240,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
           if (it >= STAGES && !mbar_wait(bar0 + 8 * (STAGES + s), ph ^ 1)) {
-            fail(1);
+            fail(1 | int(it << 4));
             break;
           }
           const int tap = UP ? 4 : kb / kchunks, c0 = (kb - (UP ? 0 : tap) * kchunks) * KB;
@@ -252,7 +261,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       for (int t = blockIdx.x; t < tiles && !s_fail; t += gridDim.x, ++i) {
         const uint32_t buf = i & 1;
         if (i >= 2 && !mbar_wait(acce + 8 * buf, ((i >> 1) & 1) ^ 1)) {
-          fail(2);
+          fail(4 | int(i << 4));
           break;
         }
         tc_fence_after();
@@ -261,7 +270,7 @@ __global__ void __launch_bounds__(kThreads, 1)
         for (int kb = 0; kb < nk; ++kb, ++it) {
           const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
           if (!mbar_wait(bar0 + 8 * s, ph)) {
-            fail(2);
+            fail(2 | int(it << 4));
             ok = false;
             break;
           }
@@ -288,7 +297,7 @@ __global__ void __launch_bounds__(kThreads, 1)
       const uint32_t buf = i & 1;
       const bool got = __all_sync(0xffffffffu, mbar_wait(accf + 8 * buf, (i >> 1) & 1));
       if (!got) {
-        if (lane == 0) fail(3);
+        if (lane == 0) fail(3 | int(i << 4));
         break;
       }
       tc_fence_after();
@@ -333,6 +342,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       if (lane == 0) mbar_arrive(acce + 8 * buf);   // the accumulator may be written again
     }
   }
+  // warps 0 and 1 reconverge (their lane 0 ran the producer / MMA loop)
+  // before the CTA-wide barrier and the warp-wide TMEM release
+  __syncwarp();
   tc_fence_before();
   __syncthreads();
   if (warp == 1) tmem_dealloc(tmem, L::NCOLS);

@@ -24,6 +24,7 @@
 #include <cstdio>
 #include <cstring>
 #include <new>
+#include <string>
 #include <vector>
 
 #include "internal.cuh"
@@ -1110,7 +1111,14 @@ pic_status pic_conv3x3_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const
     if (picgb::conv3x3_tc(c, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
     int e = 0;
     if (cudaMemcpy(&e, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
-    return e ? PIC_ETIMEOUT : PIC_OK;
+    if (e) {
+      // site of the wait that gave up (1 producer, 2 MMA stage, 3 epilogue, 4 MMA
+      // accumulator) and its iteration, for pic_last_error
+      picgb::note(cudaErrorTimeout, ("tcgen05 convolution wait, site " + std::to_string(e & 15) +
+                                     " iteration " + std::to_string(e >> 4)).c_str());
+      return PIC_ETIMEOUT;
+    }
+    return PIC_OK;
   }
   // the mma.sync implicit GEMM: cout 32 (cin 16 or a multiple of 32) or a multiple of 64
   ConvArgs a;
