@@ -34,8 +34,8 @@ namespace tc {
 
 typedef __nv_bfloat16 bf16;
 
-constexpr int kM = 128;            // output pixels per tile = TMEM lanes
-constexpr int kThreads = 192;      // TMA warp, MMA warp, four epilogue warps
+constexpr int kM = 128;            // output pixels per CTA = TMEM lanes
+constexpr int kThreads = 128;      // four warps
 constexpr uint64_t kWaitNs = 2000000000ull;   // a wait gives up after 2 s (globaltimer)
 
 // ---------------------------------------------------------------- PTX wrappers
@@ -48,15 +48,14 @@ __device__ __forceinline__ void mbar_init(uint32_t bar, uint32_t count) {
 __device__ __forceinline__ void mbar_expect_tx(uint32_t bar, uint32_t bytes) {
   asm volatile("mbarrier.arrive.expect_tx.shared::cta.b64 _, [%0], %1;" ::"r"(bar), "r"(bytes) : "memory");
 }
-// one poll that suspends for at most about 20 us (the time hint, in ns)
 __device__ __forceinline__ bool mbar_try(uint32_t bar, uint32_t parity) {
   uint32_t ok;
   asm volatile(
       "{\n\t.reg .pred p;\n\t"
-      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2, %3;\n\t"
+      "mbarrier.try_wait.parity.shared::cta.b64 p, [%1], %2;\n\t"
       "selp.u32 %0, 1, 0, p;\n\t}"
       : "=r"(ok)
-      : "r"(bar), "r"(parity), "r"(20000u)
+      : "r"(bar), "r"(parity)
       : "memory");
   return ok != 0;
 }
@@ -66,6 +65,8 @@ __device__ __forceinline__ uint64_t gtime() {
   return t;
 }
 // wait for the phase of the given parity to complete, giving up after kWaitNs
+// of wall time (one poll may itself suspend for a while, so the number of
+// polls alone would not bound the time)
 __device__ __forceinline__ bool mbar_wait(uint32_t bar, uint32_t parity) {
   if (mbar_try(bar, parity)) return true;
   const uint64_t t0 = gtime();
@@ -160,194 +161,141 @@ struct TCArgs {
   int B, H, W, cin, in_off;
   int BW, BH, tiles_w, tiles_h;
   int n_base;          // transposed convolution: first GEMM column of this launch
-  int nblocks;         // column blocks of NT per tile
   int up_cout;         // transposed convolution: output channels (GEMM column n = (2a + c) up_cout + co)
-  int *err;            // error word: site (1 producer, 2 MMA stage, 3 epilogue, 4 MMA accumulator) | iteration << 4
+  int *err;            // error word: 1 producer, 2 MMA, 3 epilogue wait gave up
 };
 
-template <int NT, int KB, int STAGES>
+template <int N, int KB, int STAGES>
 struct Layout {
   static constexpr uint32_t A_BYTES = kM * KB * 2;
-  static constexpr uint32_t B_BYTES = NT * KB * 2;
+  static constexpr uint32_t B_BYTES = N * KB * 2;
   static constexpr uint32_t BAR_OFF = STAGES * (A_BYTES + B_BYTES);
-  // full[STAGES], empty[STAGES], acc_full[2], acc_empty[2], then the TMEM address slot
-  static constexpr uint32_t BYTES = BAR_OFF + (2 * STAGES + 4) * 8 + 16 + 1024;   // + alignment slack
-  static constexpr uint32_t NCOLS = 2 * (NT < 32 ? 32 : NT);   // two accumulators
+  static constexpr uint32_t BYTES = BAR_OFF + (2 * STAGES + 1) * 8 + 16 + 1024;   // + alignment slack
+  static constexpr uint32_t NCOLS = N < 32 ? 32 : N;
 };
 
-__device__ __forceinline__ void mbar_arrive(uint32_t bar) {
-  asm volatile("mbarrier.arrive.shared::cta.b64 _, [%0];" ::"r"(bar) : "memory");
-}
-
-// Persistent, warp-specialised: warp 0 lane 0 issues the TMA loads of every
-// (tile, K block) of this CTA into a ring of STAGES stages; warp 1 holds the
-// TMEM allocation and its lane 0 issues the MMAs of each tile into one of two
-// accumulators; warps 2-5 drain an accumulator (TMEM lanes 32 (w % 4) ..) into
-// global memory while the next tile accumulates in the other.  A tile is 128
-// pixels x NT output columns (column block nb of the layer's N).
-template <int NT, int KB, int STAGES, bool UP>
+// UP: the 2x2 stride-2 transposed convolution instead of the 3x3 one -- one
+// tap (the input pixel itself), GEMM columns n = (2a + c) up_cout + co, and
+// the result of input pixel (y, x) written to output pixel (2y + a, 2x + c).
+template <int N, int KB, int STAGES, bool UP>
 __global__ void __launch_bounds__(kThreads, 1)
     k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TCArgs a) {
-  using L = Layout<NT, KB, STAGES>;
+  using L = Layout<N, KB, STAGES>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sA = saddr(smem), sB = sA + STAGES * L::A_BYTES;
   const uint32_t bar0 = sA + L::BAR_OFF;           // full[s] = bar0 + 8 s, empty[s] = bar0 + 8 (STAGES + s)
-  const uint32_t accf = bar0 + 16 * STAGES;        // acc_full[k] = accf + 8 k
-  const uint32_t acce = accf + 16;                 // acc_empty[k] = acce + 8 k
-  uint32_t *slot = reinterpret_cast<uint32_t *>(smem + L::BAR_OFF + (2 * STAGES + 4) * 8);
+  const uint32_t done = bar0 + 16 * STAGES;
+  uint32_t *slot = reinterpret_cast<uint32_t *>(smem + L::BAR_OFF + (2 * STAGES + 1) * 8);
   __shared__ int s_fail;
 
   const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
-  const int nblocks = a.nblocks;
-  const int tiles = a.tiles_w * a.tiles_h * a.B * nblocks;
-  const int kchunks = a.cin / KB;
-  const int nk = (UP ? 1 : 9) * kchunks;
+  int t = blockIdx.x;
+  const int tw = t % a.tiles_w;
+  t /= a.tiles_w;
+  const int th = t % a.tiles_h;
+  const int b = t / a.tiles_h;
+  const int w0 = tw * a.BW, h0 = th * a.BH;
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(bar0 + 8 * s, 1);
       mbar_init(bar0 + 8 * (STAGES + s), 1);
     }
-    for (int k = 0; k < 2; ++k) {
-      mbar_init(accf + 8 * k, 1);
-      mbar_init(acce + 8 * k, 4);   // one arrival per epilogue warp
-    }
+    mbar_init(done, 1);
     s_fail = 0;
     asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
   }
-  if (warp == 1) tmem_alloc(saddr(slot), L::NCOLS);
+  if (warp == 0) tmem_alloc(saddr(slot), L::NCOLS);
   tc_fence_before();
   __syncthreads();
   tc_fence_after();
   const uint32_t tmem = *slot;
+  const int kchunks = a.cin / KB;
+  const int nk = (UP ? 1 : 9) * kchunks;
 
-  auto fail = [&](int code) {
-    atomicExch(&s_fail, 1);
-    atomicCAS(a.err, 0, code);
-  };   // code = site | iteration << 4
-
-  if (warp == 0) {
-    if (lane == 0) {
-      uint32_t it = 0;
-      for (int t = blockIdx.x; t < tiles && !s_fail; t += gridDim.x) {
-        const int nb = t % nblocks;
-        int r = t / nblocks;
-        const int tw = r % a.tiles_w;
-        r /= a.tiles_w;
-        const int th = r % a.tiles_h, b = r / a.tiles_h;
-        const int w0 = tw * a.BW, h0 = th * a.BH;
-        for (int kb = 0; kb < nk; ++kb, ++it) {
-          const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
-          if (it >= STAGES && !mbar_wait(bar0 + 8 * (STAGES + s), ph ^ 1)) {
-            fail(1 | int(it << 4));
-            break;
-          }
-          const int tap = UP ? 4 : kb / kchunks, c0 = (kb - (UP ? 0 : tap) * kchunks) * KB;
-          const int dy = tap / 3 - 1, dx = tap - 3 * (tap / 3) - 1;
-          mbar_expect_tx(bar0 + 8 * s, L::A_BYTES + L::B_BYTES);
-          tma_load_4d(sA + s * L::A_BYTES, &tmA, a.in_off + c0, w0 + dx, h0 + dy, b, bar0 + 8 * s);
-          if (UP)
-            tma_load_2d(sB + s * L::B_BYTES, &tmB, c0, a.n_base + nb * NT, bar0 + 8 * s);
-          else
-            tma_load_2d(sB + s * L::B_BYTES, &tmB, tap * a.cin + c0, nb * NT, bar0 + 8 * s);
-        }
+  if (tid == 0) {
+    // TMA producer: stage s of round r is reused once the MMAs of round r - 1 released it
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (kb >= STAGES && !mbar_wait(bar0 + 8 * (STAGES + s), ph ^ 1)) {
+        atomicExch(&s_fail, 1);
+        atomicCAS(a.err, 0, 1);
+        break;
       }
+      if (s_fail) break;
+      const int tap = UP ? 4 : kb / kchunks, c0 = (kb - (UP ? 0 : tap) * kchunks) * KB;
+      const int dy = tap / 3 - 1, dx = tap - 3 * (tap / 3) - 1;
+      mbar_expect_tx(bar0 + 8 * s, L::A_BYTES + L::B_BYTES);
+      tma_load_4d(sA + s * L::A_BYTES, &tmA, a.in_off + c0, w0 + dx, h0 + dy, b, bar0 + 8 * s);
+      if (UP)
+        tma_load_2d(sB + s * L::B_BYTES, &tmB, c0, a.n_base, bar0 + 8 * s);
+      else
+        tma_load_2d(sB + s * L::B_BYTES, &tmB, tap * a.cin + c0, 0, bar0 + 8 * s);
     }
-  } else if (warp == 1) {
-    if (lane == 0) {
-      constexpr uint32_t idesc = instr_desc<NT>();
-      uint32_t it = 0, i = 0;
-      for (int t = blockIdx.x; t < tiles && !s_fail; t += gridDim.x, ++i) {
-        const uint32_t buf = i & 1;
-        if (i >= 2 && !mbar_wait(acce + 8 * buf, ((i >> 1) & 1) ^ 1)) {
-          fail(4 | int(i << 4));
-          break;
-        }
-        tc_fence_after();
-        const uint32_t d = tmem + buf * NT;
-        bool ok = true;
-        for (int kb = 0; kb < nk; ++kb, ++it) {
-          const uint32_t s = it % STAGES, ph = (it / STAGES) & 1;
-          if (!mbar_wait(bar0 + 8 * s, ph)) {
-            fail(2 | int(it << 4));
-            ok = false;
-            break;
-          }
-          tc_fence_after();
-          const uint64_t da = smem_desc<KB>(sA + s * L::A_BYTES);
-          const uint64_t db = smem_desc<KB>(sB + s * L::B_BYTES);
-#pragma unroll
-          for (int k = 0; k < KB / 16; ++k)   // 16 elements = 32 bytes along the swizzled row
-            mma_bf16(d, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
-          mma_commit(bar0 + 8 * (STAGES + s));
-        }
-        mma_commit(accf + 8 * buf);   // arrives when this tile's MMAs are done
-        if (!ok) break;
-      }
-    }
-  } else {
-    // epilogue: warp w drains TMEM lanes 32 (w % 4) .. + 31, one pixel per thread
-    const int q = warp & 3;
-    const int p = 32 * q + lane;
-    uint32_t i = 0;
-    for (int t = blockIdx.x; t < tiles; t += gridDim.x, ++i) {
-      // decisions taken by the whole warp: tcgen05.ld below is a warp-wide instruction
-      if (__any_sync(0xffffffffu, s_fail != 0)) break;
-      const uint32_t buf = i & 1;
-      const bool got = __all_sync(0xffffffffu, mbar_wait(accf + 8 * buf, (i >> 1) & 1));
-      if (!got) {
-        if (lane == 0) fail(3 | int(i << 4));
+  } else if (tid == 32) {
+    // MMA issuer
+    constexpr uint32_t idesc = instr_desc<N>();
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(bar0 + 8 * s, ph)) {
+        atomicExch(&s_fail, 1);
+        atomicCAS(a.err, 0, 2);
         break;
       }
       tc_fence_after();
-      const int nb = t % nblocks;
-      int r = t / nblocks;
-      const int tw = r % a.tiles_w;
-      r /= a.tiles_w;
-      const int th = r % a.tiles_h, b = r / a.tiles_h;
-      const int h = th * a.BH + p / a.BW, w = tw * a.BW + p % a.BW;
-      const bool inside = h < a.H && w < a.W && !__any_sync(0xffffffffu, s_fail != 0);
-      const uint32_t tl = tmem + (uint32_t(32 * q) << 16) + buf * NT;
-#pragma unroll 1
-      for (int n0 = 0; n0 < NT; n0 += 16) {
-        uint32_t rg[16];
-        tmem_ld16(tl + n0, rg);
-        if (inside) {
-          // destination and bias of these 16 columns (16 divides up_cout: one (a, c) per chunk)
-          bf16 *dst;
-          int co;
-          if (UP) {
-            const int n = a.n_base + nb * NT + n0, ac = n / a.up_cout;
-            co = n - ac * a.up_cout;
-            const int oh = 2 * h + (ac >> 1), ow = 2 * w + (ac & 1);
-            dst = a.out + ((size_t(b) * 2 * a.H + oh) * 2 * a.W + ow) * a.out_cs + a.out_off + co;
-          } else {
-            co = nb * NT + n0;
-            dst = a.out + ((size_t(b) * a.H + h) * a.W + w) * a.out_cs + a.out_off + co;
-          }
-          __align__(16) bf16 o[16];
+      const uint64_t da = smem_desc<KB>(sA + s * L::A_BYTES);
+      const uint64_t db = smem_desc<KB>(sB + s * L::B_BYTES);
 #pragma unroll
-          for (int k = 0; k < 16; ++k) {
-            float v = __uint_as_float(rg[k]) + (a.bias ? __ldg(a.bias + co + k) : 0.f);
-            if (a.relu) v = fmaxf(v, 0.f);
-            o[k] = __float2bfloat16_rn(v);
-          }
-          reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(o)[0];
-          reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
-        }
+      for (int k = 0; k < KB / 16; ++k)   // 16 elements = 32 bytes along the swizzled row
+        mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+      mma_commit(bar0 + 8 * (STAGES + s));
+    }
+    mma_commit(done);
+  }
+
+  // epilogue: thread (warp w, lane l) owns pixel 32 w + l, the accumulator's TMEM lane
+  __syncwarp();
+  const bool ok = mbar_wait(done, 0);
+  tc_fence_after();
+  if (!ok) atomicCAS(a.err, 0, 3);
+  const int p = 32 * warp + lane;
+  const int h = h0 + p / a.BW, w = w0 + p % a.BW;
+  const bool inside = h < a.H && w < a.W;
+  const uint32_t tl = tmem + (uint32_t(32 * warp) << 16);
+#pragma unroll 1
+  for (int n0 = 0; n0 < N; n0 += 16) {
+    uint32_t r[16];
+    tmem_ld16(tl + n0, r);
+    if (ok && !s_fail && inside) {
+      // destination and bias of these 16 columns (16 divides up_cout: one (a, c) per chunk)
+      bf16 *dst;
+      int co;
+      if (UP) {
+        const int n = a.n_base + n0, ac = n / a.up_cout;
+        co = n - ac * a.up_cout;
+        const int oh = 2 * h + (ac >> 1), ow = 2 * w + (ac & 1);
+        dst = a.out + ((size_t(b) * 2 * a.H + oh) * 2 * a.W + ow) * a.out_cs + a.out_off + co;
+      } else {
+        co = n0;
+        dst = a.out + ((size_t(b) * a.H + h) * a.W + w) * a.out_cs + a.out_off + co;
       }
-      tc_fence_before();
-      __syncwarp();
-      if (lane == 0) mbar_arrive(acce + 8 * buf);   // the accumulator may be written again
+      __align__(16) bf16 o[16];
+#pragma unroll
+      for (int k = 0; k < 16; ++k) {
+        float v = __uint_as_float(r[k]) + (a.bias ? __ldg(a.bias + co + k) : 0.f);
+        if (a.relu) v = fmaxf(v, 0.f);
+        o[k] = __float2bfloat16_rn(v);
+      }
+      reinterpret_cast<uint4 *>(dst)[0] = reinterpret_cast<const uint4 *>(o)[0];
+      reinterpret_cast<uint4 *>(dst)[1] = reinterpret_cast<const uint4 *>(o)[1];
     }
   }
-  // warps 0 and 1 reconverge (their lane 0 ran the producer / MMA loop)
-  // before the CTA-wide barrier and the warp-wide TMEM release
-  __syncwarp();
   tc_fence_before();
   __syncthreads();
-  if (warp == 1) tmem_dealloc(tmem, L::NCOLS);
+  if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
 }
 
 // ---------------------------------------------------------------- host side
@@ -369,29 +317,25 @@ CUtensorMapSwizzle swizzle_of(int kb) {
   return kb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (kb == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
-template <int NT, int KB>
+template <int N, int KB>
 constexpr int stages_of() {
-  return (NT * KB * 2 + kM * KB * 2) * 4 <= 160 * 1024 ? 4 : 3;
+  return (N * KB * 2 + kM * KB * 2) * 4 <= 160 * 1024 ? 4 : 3;
 }
 
 // the dynamic shared memory size of one instantiation (set once per process,
 // before any stream capture)
-template <int NT, int KB, bool UP>
+template <int N, int KB, bool UP>
 cudaError_t prepare_nk() {
-  constexpr int STAGES = stages_of<NT, KB>();
-  static cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<NT, KB, STAGES, UP>,
+  constexpr int STAGES = stages_of<N, KB>();
+  static cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<N, KB, STAGES, UP>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              int(Layout<NT, KB, STAGES>::BYTES));
+                                              int(Layout<N, KB, STAGES>::BYTES));
   return e;
 }
 
-// One launch: tiles of 128 pixels x NT columns of the layer's N (c.cout) in
-// a persistent grid of at most (SMs x resident CTAs) CTAs, the resident
-// count limited by shared memory and by the SM's 512 TMEM columns.
-template <int NT, int KB, bool UP>
+template <int N, int KB, bool UP>
 cudaError_t launch_nk(const ConvTC &c, cudaStream_t s) {
-  constexpr int STAGES = stages_of<NT, KB>();
-  using L = Layout<NT, KB, STAGES>;
+  constexpr int STAGES = stages_of<N, KB>();
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   CUtensorMap ta, tb;
@@ -408,11 +352,11 @@ cudaError_t launch_nk(const ConvTC &c, cudaStream_t s) {
          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
     return cudaErrorInvalidValue;
   // weights [cout][9][cin]: {9 cin, cout}, or of the transposed convolution
-  // [4 up_cout][cin]: {cin, 4 up_cout}; box {KB, NT}
+  // [4 up_cout][cin]: {cin, 4 up_cout}; box {KB, N}
   const int taps = UP ? 1 : 9;
   const cuuint64_t bdim[2] = {cuuint64_t(taps) * c.cin, cuuint64_t(UP ? 4 * c.up_cout : c.cout)};
   const cuuint64_t bstr[1] = {cuuint64_t(taps) * c.cin * 2};
-  const cuuint32_t bbox[2] = {cuuint32_t(KB), cuuint32_t(NT)};
+  const cuuint32_t bbox[2] = {cuuint32_t(KB), cuuint32_t(N)};
   if (fn(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(c.w), bdim, bstr, bbox, one,
          CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(KB), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
          CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
@@ -433,47 +377,30 @@ cudaError_t launch_nk(const ConvTC &c, cudaStream_t s) {
   a.tiles_w = (c.W + BW - 1) / BW;
   a.tiles_h = (c.H + BH - 1) / BH;
   a.n_base = c.n_base;
-  a.nblocks = c.cout / NT;
   a.up_cout = c.up_cout;
   a.err = c.err;
-  auto k = k_conv3x3_tc<NT, KB, STAGES, UP>;
-  cudaError_t e = prepare_nk<NT, KB, UP>();
+  auto k = k_conv3x3_tc<N, KB, STAGES, UP>;
+  const cudaError_t e = prepare_nk<N, KB, UP>();
   if (e != cudaSuccess) return e;
-  int dev = 0, sms = 0, occ = 0;
-  if ((e = cudaGetDevice(&dev)) != cudaSuccess) return e;
-  if ((e = cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev)) != cudaSuccess) return e;
-  if ((e = cudaOccupancyMaxActiveBlocksPerMultiprocessor(&occ, k, kThreads, L::BYTES)) != cudaSuccess)
-    return e;
-  occ = occ < 1 ? 1 : occ;
-  if (occ > int(512 / L::NCOLS)) occ = int(512 / L::NCOLS);
-  const long long tiles = (long long)a.tiles_w * a.tiles_h * c.B * a.nblocks;
-  const long long grid = tiles < (long long)sms * occ ? tiles : (long long)sms * occ;
-  k<<<dim3(unsigned(grid)), kThreads, L::BYTES, s>>>(ta, tb, a);
+  const long long tiles = (long long)a.tiles_w * a.tiles_h * c.B;
+  k<<<dim3(unsigned(tiles)), kThreads, Layout<N, KB, STAGES>::BYTES, s>>>(ta, tb, a);
   return cudaGetLastError();
 }
 
-template <int NT, bool UP>
+template <int N, bool UP>
 cudaError_t launch_n(const ConvTC &c, cudaStream_t s) {
-  if (c.cin % 64 == 0) return launch_nk<NT, 64, UP>(c, s);
-  if (c.cin % 32 == 0) return launch_nk<NT, 32, UP>(c, s);
-  return launch_nk<NT, 16, UP>(c, s);
+  if (c.cin % 64 == 0) return launch_nk<N, 64, UP>(c, s);
+  if (c.cin % 32 == 0) return launch_nk<N, 32, UP>(c, s);
+  return launch_nk<N, 16, UP>(c, s);
 }
 
-template <int NT>
+template <int N>
 cudaError_t prepare_n() {
   cudaError_t e = cudaSuccess;
-  for (cudaError_t f : {prepare_nk<NT, 64, false>(), prepare_nk<NT, 32, false>(), prepare_nk<NT, 16, false>(),
-                        prepare_nk<NT, 64, true>(), prepare_nk<NT, 32, true>(), prepare_nk<NT, 16, true>()})
+  for (cudaError_t f : {prepare_nk<N, 64, false>(), prepare_nk<N, 32, false>(), prepare_nk<N, 16, false>(),
+                        prepare_nk<N, 64, true>(), prepare_nk<N, 32, true>(), prepare_nk<N, 16, true>()})
     if (e == cudaSuccess) e = f;
   return e;
-}
-
-// Column block of a layer with N columns over `ptiles` pixel tiles: the
-// widest of 256, 128, 64, 32 dividing N that still gives >= 2 tiles per SM.
-int pick_nt(int N, long long ptiles, int sms) {
-  int nt = N < 256 ? N : 256;
-  while (nt > 32 && (N % nt != 0 || ptiles * (N / nt) < 2LL * sms)) nt >>= 1;
-  return nt;
 }
 
 }  // namespace tc
@@ -487,27 +414,30 @@ cudaError_t conv3x3_tc_prepare() {
 }
 
 bool conv3x3_tc_supported(int cin, int cout, int in_cs, int in_off, int out_cs, int out_off, int W) {
-  return cin >= 16 && cin % 16 == 0 && cout >= 32 && cout <= 1024 && cout % 32 == 0 && in_cs % 8 == 0 &&
-         in_off % 8 == 0 && out_cs % 8 == 0 && out_off % 8 == 0 && W >= 8 && tc::encode_fn() != nullptr;
+  return cin >= 16 && cin % 16 == 0 && (cout == 32 || cout == 64 || cout == 128 || cout == 256) &&
+         in_cs % 8 == 0 && in_off % 8 == 0 && out_cs % 8 == 0 && out_off % 8 == 0 && W >= 8 &&
+         tc::encode_fn() != nullptr;
 }
 
 cudaError_t conv3x3_tc(const ConvTC &c, cudaStream_t s) {
   if (!conv3x3_tc_supported(c.cin, c.cout, c.in_cs, c.in_off, c.out_cs, c.out_off, c.W))
     return cudaErrorNotSupported;
-  if (c.up_cout && (c.up_cout % 16 || c.n_base % c.up_cout || c.n_base + c.cout > 4 * c.up_cout))
-    return cudaErrorNotSupported;
-  int dev = 0, sms = 0;
-  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
-    return cudaErrorInvalidValue;
-  const int BW = c.W >= tc::kM ? tc::kM : (1 << (31 - __builtin_clz(unsigned(c.W))));
-  const long long ptiles = (long long)((c.W + BW - 1) / BW) * ((c.H + tc::kM / BW - 1) / (tc::kM / BW)) * c.B;
-  const int nt = tc::pick_nt(c.cout, ptiles, sms);
-  const bool up = c.up_cout != 0;
-  switch (nt) {
-    case 256: return up ? tc::launch_n<256, true>(c, s) : tc::launch_n<256, false>(c, s);
-    case 128: return up ? tc::launch_n<128, true>(c, s) : tc::launch_n<128, false>(c, s);
-    case 64: return up ? tc::launch_n<64, true>(c, s) : tc::launch_n<64, false>(c, s);
-    default: return up ? tc::launch_n<32, true>(c, s) : tc::launch_n<32, false>(c, s);
+  if (c.up_cout) {
+    // the transposed convolution's GEMM columns in launches of at most 256
+    if (c.up_cout % 16 || c.n_base % c.up_cout || c.n_base + c.cout > 4 * c.up_cout)
+      return cudaErrorNotSupported;
+    switch (c.cout) {
+      case 32: return tc::launch_n<32, true>(c, s);
+      case 64: return tc::launch_n<64, true>(c, s);
+      case 128: return tc::launch_n<128, true>(c, s);
+      default: return tc::launch_n<256, true>(c, s);
+    }
+  }
+  switch (c.cout) {
+    case 32: return tc::launch_n<32, false>(c, s);
+    case 64: return tc::launch_n<64, false>(c, s);
+    case 128: return tc::launch_n<128, false>(c, s);
+    default: return tc::launch_n<256, false>(c, s);
   }
 }
 

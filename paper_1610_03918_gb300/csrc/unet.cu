@@ -762,10 +762,14 @@ bool up_tc(pic_unet *u, int l, const bf16 *in, int in_cs) {
   c.relu = 0;
   c.err = u->d_err;
   c.up_cout = up.cout;
-  c.cout = 4 * up.cout;   // all GEMM columns in one launch
-  c.n_base = 0;
-  if (!conv3x3_tc_supported(up.cin, c.cout, in_cs, 0, c.out_cs, 0, c.W)) return false;
-  return conv3x3_tc(c, u->stream) == cudaSuccess;
+  const int total = 4 * up.cout, step = total > 256 ? 256 : total;
+  if (!conv3x3_tc_supported(up.cin, step, in_cs, 0, c.out_cs, 0, c.W)) return false;
+  for (int n0 = 0; n0 < total; n0 += step) {
+    c.cout = step;
+    c.n_base = n0;
+    if (conv3x3_tc(c, u->stream) != cudaSuccess) return false;
+  }
+  return true;
 }
 
 void forward(pic_unet *u, const float *x) {
@@ -1112,10 +1116,8 @@ pic_status pic_conv3x3_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const
     int e = 0;
     if (cudaMemcpy(&e, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
     if (e) {
-      // site of the wait that gave up (1 producer, 2 MMA stage, 3 epilogue, 4 MMA
-      // accumulator) and its iteration, for pic_last_error
-      picgb::note(cudaErrorTimeout, ("tcgen05 convolution wait, site " + std::to_string(e & 15) +
-                                     " iteration " + std::to_string(e >> 4)).c_str());
+      // the wait that gave up (1 producer, 2 MMA, 3 epilogue), for pic_last_error
+      picgb::note(cudaErrorTimeout, ("tcgen05 convolution wait " + std::to_string(e)).c_str());
       return PIC_ETIMEOUT;
     }
     return PIC_OK;
