@@ -63,7 +63,7 @@ def test_fullsize_poisson_certificate_and_field(full):
     w, sim, parts = full
     geom = from_workload(w)
     rho, phi = sim.rho(), sim.phi()
-    it, outer, rel, ms = sim.poisson_stats()
+    it, outer, rel, ms, rel0 = sim.poisson_stats()
     assert rel <= w.poisson_rtol
     # the oracle's own FP64 residual of the GPU potential
     assert opoisson.residual_rel(geom, phi, rho) <= 1.05 * w.poisson_rtol

@@ -96,7 +96,7 @@ def test_poisson_and_field_match_oracle(name):
     rho = synth.random_rho(w, seed=21, scale=0.3)
     gs.set_rho_ext(rho)
     gs.step(0)
-    it, outer, rel, ms = gs.poisson_stats()
+    it, outer, rel, ms, rel0 = gs.poisson_stats()
     assert rel <= 1e-10
     phi_g = gs.phi()
     phi_o = opoisson.solve_direct(geom, rho)
@@ -201,8 +201,12 @@ def test_warm_start_modes_reach_the_same_fields(name):
         for s in (0, 1):
             gs.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
         gs.step(3)
-        it, outer, rel, ms = gs.poisson_stats()
+        it, outer, rel, ms, rel0 = gs.poisson_stats()
         assert rel <= 1e-10 and outer >= 1, (ws, rel, outer)
+        # from the zero guess the initial residual is b itself
+        if ws == 0:
+            assert abs(rel0 - 1.0) <= 1e-5, rel0
+        assert rel0 >= rel
         assert gs.status() == 0
         phis.append(gs.phi())
     for p in phis[1:]:
