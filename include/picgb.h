@@ -194,7 +194,10 @@ enum {
   PIC_DIAG_STATE_E = 8,  /* [5*n]: x, y, vx, vy, id blocks of live electrons */
   PIC_DIAG_STATE_I = 9,  /* same for ions */
   PIC_DIAG_POISSON = 10, /* [inner iterations, outer iterations, rel residual, ms] of the last solve,
-                            and (with room for a fifth double) the rel residual of its initial guess */
+                            and (with room for a fifth double) the rel residual at its first check:
+                            that of the initial guess with the multigrid inner solver, that after
+                            the first correction with the direct one (whose first pass always
+                            corrects) */
   PIC_DIAG_STATUS = 11,  /* uint32: status word; reading clears it */
   PIC_DIAG_TIMING = 12,  /* [steps, ms particle kernel, ms sort, ms Poisson (the solve's
                             residual passes also form E), ms rho,

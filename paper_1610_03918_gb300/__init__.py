@@ -418,7 +418,8 @@ class Sim:
 
     def poisson_stats(self):
         """[inner iterations, outer passes, relative residual, ms, relative
-        residual of the initial guess] of the last solve."""
+        residual at the first check (the initial guess's with multigrid PCG)]
+        of the last solve."""
         return self.diag(PIC_DIAG_POISSON, np.empty(5))[0]
 
     def timing(self):
