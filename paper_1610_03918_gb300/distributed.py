@@ -38,13 +38,20 @@ def allreduce_sum_int64(t, group=None):
     return t
 
 
+def _device(group=None):
+    """Where the group's collectives take their tensors: the GPU for NCCL."""
+    import torch.distributed as dist
+    return "cuda" if dist.get_backend(group) == "nccl" else "cpu"
+
+
 def reduce_counts(walls, live, group=None):
     """Wall tallies [2, 8] and live counts [2] summed over the ranks."""
     import torch
     v = torch.tensor(np.concatenate([np.asarray(walls, np.int64).ravel(),
-                                     np.asarray(live, np.int64).ravel()]), dtype=torch.int64)
+                                     np.asarray(live, np.int64).ravel()]), dtype=torch.int64,
+                     device=_device(group))
     allreduce_sum_int64(v, group)
-    v = v.numpy()
+    v = v.cpu().numpy()
     return v[:16].reshape(2, 8), v[16:]
 
 
@@ -52,9 +59,9 @@ def reduce_sum_f64(x, group=None):
     """Element-wise FP64 sum over the ranks (kinetic energies, momenta)."""
     import torch
     import torch.distributed as dist
-    v = torch.tensor(np.asarray(x, np.float64).ravel(), dtype=torch.float64)
+    v = torch.tensor(np.asarray(x, np.float64).ravel(), dtype=torch.float64, device=_device(group))
     dist.all_reduce(v, op=dist.ReduceOp.SUM, group=group)
-    return v.numpy().reshape(np.shape(x))
+    return v.cpu().numpy().reshape(np.shape(x))
 
 
 class DistributedSim:

@@ -83,3 +83,40 @@ def test_phases_out_of_order_are_refused():
     with pytest.raises(pg.PicError) as e:
         sim.step_particles()
     assert e.value.code == pg.PIC_ESTATE
+
+
+def test_distributed_driver_over_nccl_single_rank():
+    # distributed.DistributedSim through a real NCCL process group (one rank on
+    # this GPU): the all-reduce of the exchange buffer on the context's stream
+    # is then the identity, and the run equals an undecomposed one bit for bit
+    import socket
+    import torch
+    import torch.distributed as dist
+    import paper_1610_03918_gb300 as pg
+    from paper_1610_03918_gb300 import distributed as pd
+    with socket.socket() as s:
+        s.bind(("127.0.0.1", 0))
+        port = s.getsockname()[1]
+    dist.init_process_group("nccl", init_method=f"tcp://127.0.0.1:{port}", rank=0, world_size=1)
+    try:
+        w = synth.small_trench(nx=72, ny=64, depth=20, width=6, ppc=8, seed=82).replace(
+            recycle=True, recycle_seed=4, sort_every=4)
+        loads = [synth.maxwellian_load(w, s) for s in (0, 1)]
+        cap = max(len(p) for p in loads) + 64
+        one = gpu_sim(w, capacity=cap)
+        rank = gpu_sim(w, capacity=cap, decomposed=True)
+        for s in (0, 1):
+            one.load_particles(s, loads[s], v_at_t0=True)
+            rank.load_particles(s, pd.shard(loads[s], 0, 1), v_at_t0=True)
+        one.step(7)
+        drv = pd.DistributedSim(rank)
+        drv.step(8)                      # the first step brings the fields up to date
+        torch.cuda.synchronize()
+        assert np.array_equal(rank.rho(), one.rho()) and np.array_equal(rank.phi(), one.phi())
+        for s in (0, 1):
+            assert np.array_equal(by_id(rank.state(s)), by_id(one.state(s)))
+        walls, live = drv.counts()
+        assert np.array_equal(walls, one.counts()[0]) and np.array_equal(live, one.counts()[1])
+        np.testing.assert_allclose(drv.energy()[:2], one.energy()[:2], rtol=1e-6)
+    finally:
+        dist.destroy_process_group()
