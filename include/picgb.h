@@ -125,7 +125,9 @@ typedef struct {
   int64_t hit_capacity;           /* hit records kept (PIC_DIAG_HITS) */
   void *stream;                   /* cudaStream_t to run on; NULL: a library-owned stream */
   /* optional device allocator: called with the context's stream (the memory
-     is used in stream order on it); NULL: cudaMalloc / cudaFree */
+     is used in stream order on it); NULL: cudaMalloc / cudaFree.  Blocks
+     must be aligned to 16 bytes at least; a misaligned block is released
+     again and the call fails with PIC_ENOMEM. */
   void *(*alloc)(size_t bytes, void *stream, void *user);
   void (*free)(void *ptr, void *stream, void *user);      /* its release function */
   void *alloc_user;
@@ -191,7 +193,8 @@ enum {
   PIC_DIAG_RHO = 5,      /* [nxn*nyn]: net charge density of the last deposit */
   PIC_DIAG_PHI = 6,      /* [nxn*nyn]: potential (held as a double-float pair, ~48 bits) */
   PIC_DIAG_E = 7,        /* [2*nxn*nyn]: Ex then Ey at the nodes */
-  PIC_DIAG_STATE_E = 8,  /* [5*n]: x, y, vx, vy, id blocks of live electrons */
+  PIC_DIAG_STATE_E = 8,  /* [5*n]: x, y, vx, vy, id blocks of live electrons (into pinned
+                            host memory the export kernel writes directly) */
   PIC_DIAG_STATE_I = 9,  /* same for ions */
   PIC_DIAG_POISSON = 10, /* [inner iterations, outer iterations, rel residual, ms] of the last solve,
                             and (with room for a fifth double) the rel residual at its first check:

@@ -410,11 +410,20 @@ class Sim:
         _, n = self.diag(PIC_DIAG_HITS, out)
         return out[:n]
 
-    def state(self, species):
-        live = self.counts()[1][species]
-        out = np.empty((5, int(live)), np.float64)
-        self.diag(PIC_DIAG_STATE_E if species == 0 else PIC_DIAG_STATE_I, out)
-        return out
+    def state(self, species, out=None):
+        """(5, live) array of x, y, vx, vy, id of the live particles.  `out`: a
+        C-contiguous float64 buffer of at least 5 * live elements to fill (pinned
+        host memory is written by the device directly); its front is returned."""
+        live = int(self.counts()[1][species])
+        if out is None:
+            view = np.empty((5, live), np.float64)
+        else:
+            flat = out.reshape(-1)
+            if out.dtype != np.float64 or not out.flags["C_CONTIGUOUS"] or flat.size < 5 * live:
+                raise ValueError("state: out must be a contiguous float64 buffer of >= 5 * live elements")
+            view = flat[:5 * live].reshape(5, live)
+        self.diag(PIC_DIAG_STATE_E if species == 0 else PIC_DIAG_STATE_I, view)
+        return view
 
     def poisson_stats(self):
         """[inner iterations, outer passes, relative residual, ms, relative

@@ -28,6 +28,12 @@ void *tmp_alloc(pic_ctx *c, size_t bytes) {
   void *p = nullptr;
   if (c->cfg.alloc) {
     p = c->cfg.alloc(bytes, c->stream, c->cfg.alloc_user);
+    // the kernels move 16-byte vectors: a block the caller's allocator did
+    // not align is given back and counts as a failed allocation
+    if (p && (reinterpret_cast<uintptr_t>(p) & 15)) {
+      if (c->cfg.free) c->cfg.free(p, c->stream, c->cfg.alloc_user);
+      p = nullptr;
+    }
   } else if (cudaMalloc(&p, bytes) != cudaSuccess) {
     p = nullptr;
   }
@@ -1467,17 +1473,27 @@ pic_status pic_diag(pic_ctx *c, int32_t kind, void *out, int64_t cap_bytes, int6
       if (st != PIC_OK) return st;
       const int64_t live = int64_t(m[s][2]);
       if (!need(5 * live * 8)) return PIC_EINVAL;
-      // temporaries through the context's allocator
-      double *buf = (double *)tmp_alloc(c, size_t(std::max<int64_t>(live, 1)) * 5 * 8);
+      // pinned host memory the device can address is written by the export
+      // kernel in place; otherwise through a device buffer and one copy
+      // (temporaries through the context's allocator)
+      double *direct = nullptr;
+      {
+        cudaPointerAttributes at;
+        if (cudaPointerGetAttributes(&at, out) == cudaSuccess && at.type == cudaMemoryTypeHost)
+          direct = static_cast<double *>(at.devicePointer);
+        else
+          cudaGetLastError();
+      }
+      double *buf = direct ? nullptr : (double *)tmp_alloc(c, size_t(std::max<int64_t>(live, 1)) * 5 * 8);
       unsigned long long *ctr = (unsigned long long *)tmp_alloc(c, 8);
-      if (!buf || !ctr) {
+      if ((!direct && !buf) || !ctr) {
         tmp_free(c, buf);
         tmp_free(c, ctr);
         return PIC_ENOMEM;
       }
       cudaMemsetAsync(ctr, 0, 8, c->stream);
-      cudaError_t e = launch_export_state(c, s, buf, live, ctr);
-      if (e == cudaSuccess)
+      cudaError_t e = launch_export_state(c, s, direct ? direct : buf, live, ctr);
+      if (e == cudaSuccess && !direct)
         e = cudaMemcpyAsync(out, buf, size_t(live) * 5 * 8, cudaMemcpyDeviceToHost, c->stream);
       if (e == cudaSuccess) e = cudaStreamSynchronize(c->stream);
       tmp_free(c, buf);

@@ -150,6 +150,7 @@ struct ParticleBuf {
 struct Chunk {
   int32_t species, tile, begin, end;
 };
+static_assert(sizeof(Chunk) == 16, "a chunk is written as one 16-byte vector");
 
 // device pointers of up to 64 ranks' exchange buffers (by value, as a kernel argument)
 struct DevPtrs {

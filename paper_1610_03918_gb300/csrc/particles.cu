@@ -119,14 +119,20 @@ __device__ uint32_t block_exscan(uint32_t v, uint32_t *total) {
 }
 
 // One CTA of 1024 threads: tile starts (padded to 4 slots), the chunk work
-// list of both species, padding slots marked dead, counters reset.
+// list of both species, padding slots marked dead, counters reset.  The chunk
+// list is written with consecutive threads on consecutive chunks: each thread
+// finds the tile of its chunk by a binary search over the tiles' first chunk
+// indices, kept in shared memory.
 __global__ void __launch_bounds__(1024) k_sort_scan(SortArgs a) {
+  __shared__ uint32_t s_first[1025];   // first chunk of each tile of the round, then the round's total
+  __shared__ uint32_t s_off[1024], s_padded[1024];
   uint32_t chunk_base = 0;
   for (int s = 0; s < 2; ++s) {
     uint32_t slot_base = 0;
     uint32_t *cnt = a.count + int64_t(s) * a.ntiles;
     uint32_t *cur = a.cursor + int64_t(s) * a.ntiles;
     uint32_t *st = a.start + int64_t(s) * a.ntiles;
+    int32_t *dcell = a.pbufs[2 * s + (a.cur[s] ^ 1)].cell;
     for (int t0 = 0; t0 < a.ntiles; t0 += 1024) {
       const int t = t0 + threadIdx.x;
       uint32_t n = 0, padded = 0, nch = 0;
@@ -137,22 +143,31 @@ __global__ void __launch_bounds__(1024) k_sort_scan(SortArgs a) {
       }
       uint32_t tot_slots, tot_ch;
       const uint32_t off = block_exscan(padded, &tot_slots) + slot_base;
-      const uint32_t coff = block_exscan(nch, &tot_ch) + chunk_base;
+      const uint32_t first = block_exscan(nch, &tot_ch);
+      s_first[threadIdx.x] = first;
+      s_off[threadIdx.x] = off;
+      s_padded[threadIdx.x] = padded;
+      if (threadIdx.x == 0) s_first[1024] = tot_ch;
       if (t < a.ntiles) {
         st[t] = off;
         cur[t] = 0;
         cnt[t] = 0;
-        int32_t *dcell = a.pbufs[2 * s + (a.cur[s] ^ 1)].cell;
         for (uint32_t k = n; k < padded; ++k) dcell[off + k] = -1;
-        for (uint32_t k = 0; k < nch; ++k) {
-          Chunk ch;
-          ch.species = s;
-          ch.tile = t;
-          ch.begin = int32_t(off + k * kChunk);
-          ch.end = int32_t(off + min(padded, (k + 1) * kChunk));
-          a.chunks[coff + k] = ch;
-        }
       }
+      __syncthreads();
+      for (uint32_t c = threadIdx.x; c < tot_ch; c += 1024) {
+        // the last tile k of the round with first[k] <= c (it has at least one chunk)
+        int lo = 0, hi = 1024;
+        while (hi - lo > 1) {
+          const int mid = (lo + hi) >> 1;
+          if (s_first[mid] <= c) lo = mid; else hi = mid;
+        }
+        const uint32_t q = c - s_first[lo];
+        const uint32_t b0 = s_off[lo] + q * kChunk;
+        const uint32_t b1 = s_off[lo] + min(s_padded[lo], (q + 1) * kChunk);
+        reinterpret_cast<int4 *>(a.chunks)[chunk_base + c] = make_int4(s, t0 + lo, int(b0), int(b1));
+      }
+      __syncthreads();
       slot_base += tot_slots;
       chunk_base += tot_ch;
     }
