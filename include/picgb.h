@@ -387,7 +387,8 @@ pic_status pic_batch_free(pic_batch *b);
  * concatenation, 1x1 head; BF16 activations and weights, FP32 accumulation
  * and master weights.  All arrays are DEVICE memory, NHWC, FP32:
  * x [batch][height][width][2], y and targets [batch][height][width].
- * height and width are multiples of 8 (at least 16).  Parameters travel as
+ * height and width are multiples of 8 (at least 16), and 2 batch height width
+ * < 2^31 (PIC_EINVAL otherwise).  Parameters travel as
  * one flat FP32 vector (layer by layer: enc0a..enc3b conv weights [out][3][3][in]
  * and biases, then per decoder level the transposed conv [2][2][in][out] and
  * bias and the two convs, then the head weight [32] and bias). */

@@ -317,9 +317,14 @@ CUtensorMapSwizzle swizzle_of(int kb) {
   return kb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (kb == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
+// Ring depth per shape, from timings of the network's layers at 1032 x 512
+// (the results do not depend on it): a shallower ring leaves room for more
+// CTAs per SM, which hides the TMA latency better than a deeper ring does
+// (N 32, KB 64: 51 us with 2 stages, 74 us with 4; N 128, KB 64: 23 us with
+// 3, 35 us with 4; N 256: 3 and 4 equal, 2 slower).
 template <int N, int KB>
 constexpr int stages_of() {
-  return (N * KB * 2 + kM * KB * 2) * 4 <= 160 * 1024 ? 4 : 3;
+  return (N == 32 && KB == 16) ? 4 : ((N <= 64 && KB == 64) ? 2 : 3);
 }
 
 // the dynamic shared memory size of one instantiation (set once per process,

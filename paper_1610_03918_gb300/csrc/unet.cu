@@ -515,6 +515,65 @@ __global__ void k_input_vec(const float2 *x, uint4 *out, long long npix) {
   }
 }
 
+// First 3x3 convolution of the network (2 input channels -> kC0) on the CUDA
+// cores, straight from the FP32 input pairs.  The tensor-core kernel takes K
+// in blocks of 16 channels, so there it reads and multiplies 14 zero
+// channels for every 2 real ones.  Here two threads form one pixel's kC0
+// outputs (half each) from its 9 x 2 BF16-rounded inputs and the same BF16
+// weights (w: [kC0][9][wcin], channels 0 and 1 used), in FP32 from the bias
+// on, in tap order, then ReLU (if relu) and a BF16 store to out[p][kC0].
+constexpr int kIn = 2;
+constexpr int kHalf = kC0 / 2;
+__global__ void __launch_bounds__(256) k_conv_in(const float2 *x, const bf16 *w, int wcin, const float *bias,
+                                                 bf16 *out, int B, int H, int W, int relu) {
+  __shared__ float4 sw[9 * kIn][kC0 / 4];   // [2 tap + c][n / 4]
+  __shared__ float sb[kC0];
+  for (int i = threadIdx.x; i < 9 * kIn * kC0; i += blockDim.x) {
+    const int n = i % kC0, tc = i / kC0, tap = tc / kIn, c = tc - tap * kIn;
+    reinterpret_cast<float *>(sw)[i] = __bfloat162float(w[(size_t(n) * 9 + tap) * wcin + c]);
+  }
+  for (int i = threadIdx.x; i < kC0; i += blockDim.x) sb[i] = bias ? bias[i] : 0.f;
+  __syncthreads();
+  // 32-bit index arithmetic (2 B H W < 2^31, checked when the network is
+  // created): 64-bit division is a long instruction sequence
+  const unsigned total = 2u * unsigned(B) * unsigned(H) * unsigned(W);
+  for (unsigned i = blockIdx.x * blockDim.x + threadIdx.x; i < total; i += gridDim.x * blockDim.x) {
+    const unsigned p = i >> 1;
+    const int half = int(i & 1u), q0 = half * (kHalf / 4);
+    const unsigned r = p / unsigned(W);
+    const int wq = int(p - r * unsigned(W));
+    const int h = int(r % unsigned(H));
+    float acc[kHalf];
+#pragma unroll
+    for (int n = 0; n < kHalf; ++n) acc[n] = sb[half * kHalf + n];
+#pragma unroll 1
+    for (int t = 0; t < 9; ++t) {
+      const int dy = t / 3 - 1, dx = t - 3 * (t / 3) - 1;
+      const int hh = h + dy, ww = wq + dx;
+      float2 v = make_float2(0.f, 0.f);
+      if (hh >= 0 && hh < H && ww >= 0 && ww < W) v = x[int(p) + dy * W + dx];
+      const float v0 = __bfloat162float(__float2bfloat16(v.x));
+      const float v1 = __bfloat162float(__float2bfloat16(v.y));
+#pragma unroll
+      for (int q = 0; q < kHalf / 4; ++q) {
+        const float4 a = sw[2 * t][q0 + q], b = sw[2 * t + 1][q0 + q];
+        acc[4 * q + 0] = fmaf(v1, b.x, fmaf(v0, a.x, acc[4 * q + 0]));
+        acc[4 * q + 1] = fmaf(v1, b.y, fmaf(v0, a.y, acc[4 * q + 1]));
+        acc[4 * q + 2] = fmaf(v1, b.z, fmaf(v0, a.z, acc[4 * q + 2]));
+        acc[4 * q + 3] = fmaf(v1, b.w, fmaf(v0, a.w, acc[4 * q + 3]));
+      }
+    }
+    uint4 *dst = reinterpret_cast<uint4 *>(out + size_t(p) * kC0 + half * kHalf);
+#pragma unroll
+    for (int q = 0; q < kHalf / 8; ++q) {
+      __align__(16) bf16 o[8];
+#pragma unroll
+      for (int k = 0; k < 8; ++k) o[k] = __float2bfloat16(relu ? fmaxf(acc[8 * q + k], 0.f) : acc[8 * q + k]);
+      dst[q] = *reinterpret_cast<const uint4 *>(o);
+    }
+  }
+}
+
 // 2x2 average pool, 8 channels (16 bytes) per thread
 __global__ void k_pool_vec(const bf16 *in, int in_cs, int in_off, bf16 *out, int C, int B, int H, int W) {
   const int Ho = H / 2, Wo = W / 2, C8 = C / 8;
@@ -563,6 +622,7 @@ inline int gridn(long long n, int t = 256) {
 // ============================================================================
 struct pic_unet {
   int B, H, W;
+  int num_sms = 1;
   cudaStream_t stream = nullptr;
   std::vector<void *> allocs;
   // parameters: FP32 master (flat, in the order of the layer list), grads, Adam moments
@@ -772,12 +832,21 @@ bool up_tc(pic_unet *u, int l, const bf16 *in, int in_cs) {
   return true;
 }
 
-void forward(pic_unet *u, const float *x) {
+// keep_input: also the BF16 copy of the input padded to kCin0 channels, which
+// the weight gradient of the first convolution reads
+void forward(pic_unet *u, const float *x, bool keep_input) {
   const int C0 = kC[0], C1 = kC[1], C2 = kC[2], C3 = kC[3];
-  k_input_vec<<<gridn(pix(u, 0)), 256, 0, u->stream>>>(reinterpret_cast<const float2 *>(x),
-                                                       reinterpret_cast<uint4 *>(u->x16), pix(u, 0));
+  if (keep_input)
+    k_input_vec<<<gridn(pix(u, 0)), 256, 0, u->stream>>>(reinterpret_cast<const float2 *>(x),
+                                                         reinterpret_cast<uint4 *>(u->x16), pix(u, 0));
   // encoder; each level's output is written into the skip half of its concat buffer
-  conv_fwd(u, E0A, u->x16, kCin0, 0, u->a[0], C0, 0, 0, true);
+  {
+    const pic_unet::Conv &c = u->conv[E0A];
+    // resident CTAs (5 of 256 threads per SM) that stage the weights once each
+    const int grid = std::min(gridn(2 * pix(u, 0)), 5 * u->num_sms);
+    k_conv_in<<<grid, 256, 0, u->stream>>>(reinterpret_cast<const float2 *>(x), c.w, c.cin_c,
+                                                       u->P + c.b_off, u->a[0], u->B, u->H, u->W, 1);
+  }
   conv_fwd(u, E0B, u->a[0], C0, 0, u->cat[0], 2 * C0, C0, 0, true);
   k_pool_vec<<<gridn((long long)pix(u, 1) * C0 / 8), 256, 0, u->stream>>>(u->cat[0], 2 * C0, C0, u->p[1], C0, u->B, u->H, u->W);
   conv_fwd(u, E1A, u->p[1], C0, 0, u->a[1], C1, 0, 1, true);
@@ -861,12 +930,21 @@ extern "C" {
 
 pic_status pic_unet_create(int32_t batch, int32_t height, int32_t width, void *stream, pic_unet **out) {
   if (!out || batch < 1 || height < 16 || width < 16 || (height % 8) || (width % 8)) return PIC_EINVAL;
+  if (2LL * batch * height * width >= (1LL << 31)) return PIC_EINVAL;   // 32-bit pixel indices
   pic_unet *u = new (std::nothrow) pic_unet();
   if (!u) return PIC_ENOMEM;
   u->B = batch;
   u->H = height;
   u->W = width;
   u->stream = static_cast<cudaStream_t>(stream);
+  {
+    int dev = 0;
+    if (cudaGetDevice(&dev) != cudaSuccess ||
+        cudaDeviceGetAttribute(&u->num_sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess) {
+      delete u;
+      return PIC_ECUDA;
+    }
+  }
   // parameter layout (the order of the layer list)
   long long off = 0;
   auto add_conv = [&](int idx, int cin_m, int cin_c, int cout) {
@@ -986,7 +1064,7 @@ pic_status pic_unet_get_params(pic_unet *u, float *host) {
 
 pic_status pic_unet_forward(pic_unet *u, const float *x, float *y) {
   if (!u || !x || !y) return PIC_EINVAL;
-  forward(u, x);
+  forward(u, x, false);
   if (cudaMemcpyAsync(y, u->y, size_t(u->B) * u->H * u->W * 4, cudaMemcpyDeviceToDevice, u->stream) != cudaSuccess)
     return PIC_ECUDA;
   return cudaGetLastError() == cudaSuccess ? PIC_OK : PIC_ECUDA;
@@ -994,7 +1072,7 @@ pic_status pic_unet_forward(pic_unet *u, const float *x, float *y) {
 
 pic_status pic_unet_gradients(pic_unet *u, const float *x, const float *t, float *host_grad, double *loss) {
   if (!u || !x || !t) return PIC_EINVAL;
-  forward(u, x);
+  forward(u, x, true);
   cudaMemsetAsync(u->d_loss, 0, 8, u->stream);
   const long long n = (long long)u->B * u->H * u->W;
   k_mse<<<std::min(1024, gridn(n)), 256, 0, u->stream>>>(u->y, t, u->dy, n, u->d_loss);
@@ -1013,7 +1091,7 @@ pic_status pic_unet_gradients(pic_unet *u, const float *x, const float *t, float
 
 pic_status pic_unet_train_step(pic_unet *u, const float *x, const float *t, float lr, double *loss) {
   if (!u || !x || !t) return PIC_EINVAL;
-  forward(u, x);
+  forward(u, x, true);
   cudaMemsetAsync(u->d_loss, 0, 8, u->stream);
   const long long n = (long long)u->B * u->H * u->W;
   k_mse<<<std::min(1024, gridn(n)), 256, 0, u->stream>>>(u->y, t, u->dy, n, u->d_loss);
@@ -1184,7 +1262,7 @@ pic_status pic_unet_free(pic_unet *u) {
 namespace picgb {
 
 // y = U(x) queued on the net's stream; the output stays in the net's buffer.
-void unet_forward_only(pic_unet *u, const float *x) { unet::forward(u, x); }
+void unet_forward_only(pic_unet *u, const float *x) { unet::forward(u, x, false); }
 const float *unet_output(const pic_unet *u) { return u->y; }
 int unet_height(const pic_unet *u) { return u->H; }
 int unet_width(const pic_unet *u) { return u->W; }
