@@ -383,3 +383,52 @@ def test_periodic_box_conservation():
     pscale = np.sqrt(n) / 20
     assert np.abs(m1 - m0).max() <= 1e-3 * pscale
     assert abs(tot1 - tot0) <= 0.01 * tot0
+
+
+def test_walk_limit_drops_and_flags_the_particle():
+    # A move across more cell faces than the walk limit (16) is dropped
+    # untallied and flagged (PIC_ST_CFL); a long move within the limit (12
+    # faces, out of the tile's shared-memory window) lands where the oracle's
+    # segment walk puts it.
+    import paper_1610_03918_gb300 as pg
+    w = synth.periodic_square_64(ppc=1, poisson_rtol=1e-10)
+    gs = gpu_sim(w, capacity=64)
+    os_ = oracle_sim(w)
+    x = np.array([10.5, 20.25, 30.5, 40.5])
+    y = np.array([10.5, 20.75, 40.5, 50.5])
+    vx = np.array([12.0, 10.0, 0.1, -0.2]) / w.dt
+    vy = np.array([0.0, 10.0, 0.0, 0.3]) / w.dt
+    p = synth.Particles(x, y, vx, vy, np.arange(4, dtype=np.uint32))
+    load_both(gs, os_, 0, p)
+    gs.step(1)
+    os_.step(1)
+    assert gs.status() & pg.PIC_ST_CFL
+    assert gs.status() == 0          # reading cleared it
+    walls, live = gs.counts()
+    assert live.tolist() == [3, 0]
+    assert walls.sum() == 0
+    o = oracle_state(os_, 0)
+    keep = o[4] != 1
+    compare_states(gs.state(0), o[:, keep], w, 0)
+
+
+@pytest.mark.parametrize("graphs", [False, True])
+def test_unreachable_tolerance_is_reported(graphs):
+    # rtol below what the double-float residual can show: the solve of the
+    # loaded state stops after its pass cap and pic_step reports it
+    # (PIC_ENOCONV, the fields stay marked for another solve); the field it
+    # leaves is still the oracle's to the field tolerance.
+    import paper_1610_03918_gb300 as pg
+    w = SMALL["trench"].replace(poisson_rtol=1e-30)
+    gs = gpu_sim(w, graphs=graphs)
+    os_ = oracle_sim(w.replace(poisson_rtol=1e-12))
+    for s in (0, 1):
+        load_both(gs, os_, s, synth.maxwellian_load(w, s), v_at_t0=True)
+    assert pg.pic_step(gs.ctx, 0) == pg.PIC_ENOCONV
+    assert pg.pic_step(gs.ctx, 1) == pg.PIC_ENOCONV   # no step before a solve succeeds
+    gs.status()
+    assert gs.counts()[1].sum() == sum(len(synth.maxwellian_load(w, s)) for s in (0, 1))
+    os_.prepare()
+    E = np.stack(gs.efield())
+    Eo = np.stack([os_.Ex, os_.Ey])
+    assert np.abs(E - Eo).max() <= FIELD_TOL * np.abs(Eo).max()
