@@ -8,9 +8,11 @@
 // offset), FP32 accumulation, act = ReLU or identity, zero padding.
 //
 // One CTA computes a tile of M = 128 output pixels (a BH x BW block of one
-// image, BW = min(W, 128) rounded down to a power of two) for all N = cout
-// output channels.  The K loop runs over the 9 taps times cin / KB channel
-// blocks.  For each block a 4-D TMA box {KB channels, BW, BH, 1} of the input,
+// image, BW = min(W, 128) rounded down to a power of two) for a block of N
+// output channels: all of them, or, for layers with fewer pixel tiles than
+// SMs, one of the column blocks that the grid's second index selects.  The
+// K loop runs over the 9 taps times cin / KB channel blocks.  For each block
+// a 4-D TMA box {KB channels, BW, BH, 1} of the input,
 // shifted by the tap, lands in shared memory in the swizzled K-major layout
 // the MMA reads (zero fill supplies the padding), and a 2-D box {KB, N} of
 // the weights [cout][9][cin] beside it.  Warp 0 lane 0 issues the TMA loads
@@ -160,7 +162,7 @@ struct TCArgs {
   int relu;
   int B, H, W, cin, in_off;
   int BW, BH, tiles_w, tiles_h;
-  int n_base;          // transposed convolution: first GEMM column of this launch
+  int n_base;          // first GEMM column of this launch; CTA row y of the grid adds y N
   int up_cout;         // transposed convolution: output channels (GEMM column n = (2a + c) up_cout + co)
   int *err;            // error word: 1 producer, 2 MMA, 3 epilogue wait gave up
 };
@@ -196,6 +198,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   const int th = t % a.tiles_h;
   const int b = t / a.tiles_h;
   const int w0 = tw * a.BW, h0 = th * a.BH;
+  const int nb0 = a.n_base + int(blockIdx.y) * N;   // this CTA's first GEMM column
 
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
@@ -230,9 +233,9 @@ __global__ void __launch_bounds__(kThreads, 1)
       mbar_expect_tx(bar0 + 8 * s, L::A_BYTES + L::B_BYTES);
       tma_load_4d(sA + s * L::A_BYTES, &tmA, a.in_off + c0, w0 + dx, h0 + dy, b, bar0 + 8 * s);
       if (UP)
-        tma_load_2d(sB + s * L::B_BYTES, &tmB, c0, a.n_base, bar0 + 8 * s);
+        tma_load_2d(sB + s * L::B_BYTES, &tmB, c0, nb0, bar0 + 8 * s);
       else
-        tma_load_2d(sB + s * L::B_BYTES, &tmB, tap * a.cin + c0, 0, bar0 + 8 * s);
+        tma_load_2d(sB + s * L::B_BYTES, &tmB, tap * a.cin + c0, nb0, bar0 + 8 * s);
     }
   } else if (tid == 32) {
     // MMA issuer
@@ -274,12 +277,12 @@ __global__ void __launch_bounds__(kThreads, 1)
       bf16 *dst;
       int co;
       if (UP) {
-        const int n = a.n_base + n0, ac = n / a.up_cout;
+        const int n = nb0 + n0, ac = n / a.up_cout;
         co = n - ac * a.up_cout;
         const int oh = 2 * h + (ac >> 1), ow = 2 * w + (ac & 1);
         dst = a.out + ((size_t(b) * 2 * a.H + oh) * 2 * a.W + ow) * a.out_cs + a.out_off + co;
       } else {
-        co = n0;
+        co = nb0 + n0;
         dst = a.out + ((size_t(b) * a.H + h) * a.W + w) * a.out_cs + a.out_off + co;
       }
       __align__(16) bf16 o[16];
@@ -317,21 +320,40 @@ CUtensorMapSwizzle swizzle_of(int kb) {
   return kb == 64 ? CU_TENSOR_MAP_SWIZZLE_128B : (kb == 32 ? CU_TENSOR_MAP_SWIZZLE_64B : CU_TENSOR_MAP_SWIZZLE_32B);
 }
 
-// Ring depth per shape, from timings of the network's layers at 1032 x 512
-// (the results do not depend on it): a shallower ring leaves room for more
-// CTAs per SM, which hides the TMA latency better than a deeper ring does
-// (N 32, KB 64: 51 us with 2 stages, 74 us with 4; N 128, KB 64: 23 us with
-// 3, 35 us with 4; N 256: 3 and 4 equal, 2 slower).
+// Launch shape, from timings of the network's layers at 1032 x 512 (the
+// results do not depend on it, bit for bit):
+//  * column blocks: a layer with fewer pixel tiles than SMs splits its N
+//    columns into blocks of N / 2, N / 4 (no narrower than 64), one per CTA
+//    row of the grid (N 256 over 65 tiles: 22.7 us -> 18.6 us as 4 x 64);
+//  * ring depth: the deepest ring (4, 3 or 2 stages) whose CTAs all fit on
+//    the SMs at once; when no depth gives one wave, the depth that leaves
+//    the most CTAs per SM, because more resident CTAs hide the TMA round
+//    trips better than a deeper ring (N 32, KB 64: 51 us with 2 stages, 74 us
+//    with 4; N 128, KB 64 over 258 tiles: 12.4 us with 3, 16.6 us with 4).
+// The depth is chosen at run time for KB = 64; KB = 16 and 32 (the wide
+// top level only) take one tabled depth.
+constexpr uint32_t kSmemPerSm = 233472;   // shared memory of an SM for CTAs
+constexpr uint32_t kSmemPerCta = 1024;    // reserved by the system per CTA
+
 template <int N, int KB>
 constexpr int stages_of() {
-  return (N == 32 && KB == 16) ? 4 : ((N <= 64 && KB == 64) ? 2 : 3);
+  return KB == 16 ? 4 : (KB == 32 ? 3 : 2);
+}
+
+// resident CTAs per SM of an instantiation: shared memory, TMEM columns, threads
+template <int N, int KB, int STAGES>
+constexpr int occupancy_of() {
+  constexpr int by_smem = int(kSmemPerSm / (Layout<N, KB, STAGES>::BYTES + kSmemPerCta));
+  constexpr int by_tmem = int(512 / Layout<N, KB, STAGES>::NCOLS);
+  constexpr int by_threads = 2048 / kThreads;
+  return by_smem < by_tmem ? (by_smem < by_threads ? by_smem : by_threads)
+                           : (by_tmem < by_threads ? by_tmem : by_threads);
 }
 
 // the dynamic shared memory size of one instantiation (set once per process,
 // before any stream capture)
-template <int N, int KB, bool UP>
-cudaError_t prepare_nk() {
-  constexpr int STAGES = stages_of<N, KB>();
+template <int N, int KB, int STAGES, bool UP>
+cudaError_t prepare_nks() {
   static cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<N, KB, STAGES, UP>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
                                               int(Layout<N, KB, STAGES>::BYTES));
@@ -339,8 +361,20 @@ cudaError_t prepare_nk() {
 }
 
 template <int N, int KB, bool UP>
-cudaError_t launch_nk(const ConvTC &c, cudaStream_t s) {
-  constexpr int STAGES = stages_of<N, KB>();
+cudaError_t prepare_nk() {
+  if constexpr (KB != 64) {
+    return prepare_nks<N, KB, stages_of<N, KB>(), UP>();
+  } else {
+    cudaError_t e = cudaSuccess;
+    for (cudaError_t f : {prepare_nks<N, KB, 2, UP>(), prepare_nks<N, KB, 3, UP>(), prepare_nks<N, KB, 4, UP>()})
+      if (e == cudaSuccess) e = f;
+    return e;
+  }
+}
+
+// One launch: grid (pixel tiles, column blocks of N of the c.cout columns)
+template <int N, int KB, int STAGES, bool UP>
+cudaError_t launch_nks(const ConvTC &c, cudaStream_t s, int nblk) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
   CUtensorMap ta, tb;
@@ -385,18 +419,29 @@ cudaError_t launch_nk(const ConvTC &c, cudaStream_t s) {
   a.up_cout = c.up_cout;
   a.err = c.err;
   auto k = k_conv3x3_tc<N, KB, STAGES, UP>;
-  const cudaError_t e = prepare_nk<N, KB, UP>();
+  const cudaError_t e = prepare_nks<N, KB, STAGES, UP>();
   if (e != cudaSuccess) return e;
   const long long tiles = (long long)a.tiles_w * a.tiles_h * c.B;
-  k<<<dim3(unsigned(tiles)), kThreads, Layout<N, KB, STAGES>::BYTES, s>>>(ta, tb, a);
+  k<<<dim3(unsigned(tiles), unsigned(nblk)), kThreads, Layout<N, KB, STAGES>::BYTES, s>>>(ta, tb, a);
   return cudaGetLastError();
 }
 
+template <int N, int KB, bool UP>
+cudaError_t launch_nk(const ConvTC &c, cudaStream_t s, int nblk, long long ctas, int sms) {
+  if constexpr (KB != 64) {
+    return launch_nks<N, KB, stages_of<N, KB>(), UP>(c, s, nblk);
+  } else {
+    if (ctas <= (long long)sms * occupancy_of<N, KB, 4>()) return launch_nks<N, KB, 4, UP>(c, s, nblk);
+    if (ctas <= (long long)sms * occupancy_of<N, KB, 3>()) return launch_nks<N, KB, 3, UP>(c, s, nblk);
+    return launch_nks<N, KB, 2, UP>(c, s, nblk);
+  }
+}
+
 template <int N, bool UP>
-cudaError_t launch_n(const ConvTC &c, cudaStream_t s) {
-  if (c.cin % 64 == 0) return launch_nk<N, 64, UP>(c, s);
-  if (c.cin % 32 == 0) return launch_nk<N, 32, UP>(c, s);
-  return launch_nk<N, 16, UP>(c, s);
+cudaError_t launch_n(const ConvTC &c, cudaStream_t s, int nblk, long long ctas, int sms) {
+  if (c.cin % 64 == 0) return launch_nk<N, 64, UP>(c, s, nblk, ctas, sms);
+  if (c.cin % 32 == 0) return launch_nk<N, 32, UP>(c, s, nblk, ctas, sms);
+  return launch_nk<N, 16, UP>(c, s, nblk, ctas, sms);
 }
 
 template <int N>
@@ -406,6 +451,13 @@ cudaError_t prepare_n() {
                         prepare_nk<N, 64, true>(), prepare_nk<N, 32, true>(), prepare_nk<N, 16, true>()})
     if (e == cudaSuccess) e = f;
   return e;
+}
+
+int sm_count() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess || cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return sms;
 }
 
 }  // namespace tc
@@ -427,22 +479,26 @@ bool conv3x3_tc_supported(int cin, int cout, int in_cs, int in_off, int out_cs, 
 cudaError_t conv3x3_tc(const ConvTC &c, cudaStream_t s) {
   if (!conv3x3_tc_supported(c.cin, c.cout, c.in_cs, c.in_off, c.out_cs, c.out_off, c.W))
     return cudaErrorNotSupported;
-  if (c.up_cout) {
-    // the transposed convolution's GEMM columns in launches of at most 256
-    if (c.up_cout % 16 || c.n_base % c.up_cout || c.n_base + c.cout > 4 * c.up_cout)
-      return cudaErrorNotSupported;
-    switch (c.cout) {
-      case 32: return tc::launch_n<32, true>(c, s);
-      case 64: return tc::launch_n<64, true>(c, s);
-      case 128: return tc::launch_n<128, true>(c, s);
-      default: return tc::launch_n<256, true>(c, s);
-    }
+  // the transposed convolution's GEMM columns come in launches of at most 256
+  if (c.up_cout && (c.up_cout % 16 || c.n_base % c.up_cout || c.n_base + c.cout > 4 * c.up_cout))
+    return cudaErrorNotSupported;
+  const int sms = tc::sm_count();
+  if (sms < 1) return cudaErrorInvalidValue;
+  const int BW = c.W >= tc::kM ? tc::kM : (1 << (31 - __builtin_clz(unsigned(c.W))));
+  const long long tiles = (long long)((c.W + BW - 1) / BW) * ((c.H + tc::kM / BW - 1) / (tc::kM / BW)) * c.B;
+  // column blocks while the pixel tiles alone leave SMs idle
+  int n = c.cout, nblk = 1;
+  while (n > 64 && tiles * nblk < sms) {
+    n >>= 1;
+    nblk <<= 1;
   }
-  switch (c.cout) {
-    case 32: return tc::launch_n<32, false>(c, s);
-    case 64: return tc::launch_n<64, false>(c, s);
-    case 128: return tc::launch_n<128, false>(c, s);
-    default: return tc::launch_n<256, false>(c, s);
+  const long long ctas = tiles * nblk;
+  const bool up = c.up_cout != 0;
+  switch (n) {
+    case 32: return up ? tc::launch_n<32, true>(c, s, nblk, ctas, sms) : tc::launch_n<32, false>(c, s, nblk, ctas, sms);
+    case 64: return up ? tc::launch_n<64, true>(c, s, nblk, ctas, sms) : tc::launch_n<64, false>(c, s, nblk, ctas, sms);
+    case 128: return up ? tc::launch_n<128, true>(c, s, nblk, ctas, sms) : tc::launch_n<128, false>(c, s, nblk, ctas, sms);
+    default: return up ? tc::launch_n<256, true>(c, s, nblk, ctas, sms) : tc::launch_n<256, false>(c, s, nblk, ctas, sms);
   }
 }
 
