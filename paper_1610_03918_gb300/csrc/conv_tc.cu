@@ -167,10 +167,18 @@ struct TCArgs {
   int *err;            // error word: 1 producer, 2 MMA, 3 epilogue wait gave up
 };
 
-template <int N, int KB, int STAGES>
+constexpr int kHaloPix = kM + 2;   // one image row of the tile and its two neighbours
+
+// Shared memory of one CTA: STAGES A stages, then STAGES B stages, then the
+// barriers.  Per stage, A is the 128 x KB input tile of one tap, or (HALO) the
+// 130 x KB input row of one vertical tap, and B is the N x KB weight tile of
+// one tap, or (HALO) the three horizontal taps' tiles side by side.
+template <int N, int KB, int STAGES, bool HALO = false>
 struct Layout {
-  static constexpr uint32_t A_BYTES = kM * KB * 2;
-  static constexpr uint32_t B_BYTES = N * KB * 2;
+  static constexpr uint32_t B_TILE = N * KB * 2;
+  static constexpr uint32_t A_BYTES = HALO ? ((kHaloPix * KB * 2 + 1023) / 1024) * 1024 : kM * KB * 2;
+  static constexpr uint32_t A_TX = HALO ? kHaloPix * KB * 2 : kM * KB * 2;   // bytes TMA writes
+  static constexpr uint32_t B_BYTES = (HALO ? 3 : 1) * B_TILE;
   static constexpr uint32_t BAR_OFF = STAGES * (A_BYTES + B_BYTES);
   static constexpr uint32_t BYTES = BAR_OFF + (2 * STAGES + 1) * 8 + 16 + 1024;   // + alignment slack
   static constexpr uint32_t NCOLS = N < 32 ? 32 : N;
@@ -179,10 +187,17 @@ struct Layout {
 // UP: the 2x2 stride-2 transposed convolution instead of the 3x3 one -- one
 // tap (the input pixel itself), GEMM columns n = (2a + c) up_cout + co, and
 // the result of input pixel (y, x) written to output pixel (2y + a, 2x + c).
-template <int N, int KB, int STAGES, bool UP>
+// HALO (tiles of one image row, BW = 128): the K loop runs over the three
+// vertical taps times the channel blocks; each step loads the 130-pixel input
+// row once and the three horizontal taps read it from rows 0, 1, 2 -- the
+// MMA's start address moves by whole swizzled rows, and the swizzle follows
+// the shared-memory address, so the shifted operand is the tap's tile.  That
+// moves a third of the input bytes of nine shifted tiles.
+template <int N, int KB, int STAGES, bool UP, bool HALO = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TCArgs a) {
-  using L = Layout<N, KB, STAGES>;
+  static_assert(!(UP && HALO), "the transposed convolution has one tap");
+  using L = Layout<N, KB, STAGES, HALO>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t sA = saddr(smem), sB = sA + STAGES * L::A_BYTES;
@@ -215,7 +230,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *slot;
   const int kchunks = a.cin / KB;
-  const int nk = (UP ? 1 : 9) * kchunks;
+  const int nk = (UP ? 1 : (HALO ? 3 : 9)) * kchunks;
 
   if (tid == 0) {
     // TMA producer: stage s of round r is reused once the MMAs of round r - 1 released it
@@ -228,9 +243,17 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       if (s_fail) break;
+      if (HALO) {
+        const int dy = kb / kchunks, c0 = (kb - dy * kchunks) * KB;
+        mbar_expect_tx(bar0 + 8 * s, L::A_TX + L::B_BYTES);
+        tma_load_4d(sA + s * L::A_BYTES, &tmA, a.in_off + c0, w0 - 1, h0 + dy - 1, b, bar0 + 8 * s);
+        for (int dx = 0; dx < 3; ++dx)
+          tma_load_2d(sB + s * L::B_BYTES + dx * L::B_TILE, &tmB, (3 * dy + dx) * a.cin + c0, nb0, bar0 + 8 * s);
+        continue;
+      }
       const int tap = UP ? 4 : kb / kchunks, c0 = (kb - (UP ? 0 : tap) * kchunks) * KB;
       const int dy = tap / 3 - 1, dx = tap - 3 * (tap / 3) - 1;
-      mbar_expect_tx(bar0 + 8 * s, L::A_BYTES + L::B_BYTES);
+      mbar_expect_tx(bar0 + 8 * s, L::A_TX + L::B_BYTES);
       tma_load_4d(sA + s * L::A_BYTES, &tmA, a.in_off + c0, w0 + dx, h0 + dy, b, bar0 + 8 * s);
       if (UP)
         tma_load_2d(sB + s * L::B_BYTES, &tmB, c0, nb0, bar0 + 8 * s);
@@ -249,11 +272,22 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       tc_fence_after();
-      const uint64_t da = smem_desc<KB>(sA + s * L::A_BYTES);
-      const uint64_t db = smem_desc<KB>(sB + s * L::B_BYTES);
+      if (HALO) {
 #pragma unroll
-      for (int k = 0; k < KB / 16; ++k)   // 16 elements = 32 bytes along the swizzled row
-        mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+        for (int dx = 0; dx < 3; ++dx) {
+          const uint64_t da = smem_desc<KB>(sA + s * L::A_BYTES + dx * Swz<KB>::row_bytes);   // row dx on
+          const uint64_t db = smem_desc<KB>(sB + s * L::B_BYTES + dx * L::B_TILE);
+#pragma unroll
+          for (int k = 0; k < KB / 16; ++k)
+            mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb | dx | k) != 0 ? 1u : 0u);
+        }
+      } else {
+        const uint64_t da = smem_desc<KB>(sA + s * L::A_BYTES);
+        const uint64_t db = smem_desc<KB>(sB + s * L::B_BYTES);
+#pragma unroll
+        for (int k = 0; k < KB / 16; ++k)   // 16 elements = 32 bytes along the swizzled row
+          mma_bf16(tmem, da + 2 * k, db + 2 * k, idesc, (kb | k) != 0 ? 1u : 0u);
+      }
       mma_commit(bar0 + 8 * (STAGES + s));
     }
     mma_commit(done);
@@ -352,20 +386,22 @@ constexpr int occupancy_of() {
 
 // the dynamic shared memory size of one instantiation (set once per process,
 // before any stream capture)
-template <int N, int KB, int STAGES, bool UP>
+template <int N, int KB, int STAGES, bool UP, bool HALO = false>
 cudaError_t prepare_nks() {
-  static cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<N, KB, STAGES, UP>,
+  static cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<N, KB, STAGES, UP, HALO>,
                                               cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              int(Layout<N, KB, STAGES>::BYTES));
+                                              int(Layout<N, KB, STAGES, HALO>::BYTES));
   return e;
 }
 
 template <int N, int KB, bool UP>
 cudaError_t prepare_nk() {
+  cudaError_t e = cudaSuccess;
+  if constexpr (!UP && N <= 64) e = prepare_nks<N, KB, 2, false, true>();
   if constexpr (KB != 64) {
-    return prepare_nks<N, KB, stages_of<N, KB>(), UP>();
+    const cudaError_t f = prepare_nks<N, KB, stages_of<N, KB>(), UP>();
+    return e == cudaSuccess ? f : e;
   } else {
-    cudaError_t e = cudaSuccess;
     for (cudaError_t f : {prepare_nks<N, KB, 2, UP>(), prepare_nks<N, KB, 3, UP>(), prepare_nks<N, KB, 4, UP>()})
       if (e == cudaSuccess) e = f;
     return e;
@@ -373,7 +409,7 @@ cudaError_t prepare_nk() {
 }
 
 // One launch: grid (pixel tiles, column blocks of N of the c.cout columns)
-template <int N, int KB, int STAGES, bool UP>
+template <int N, int KB, int STAGES, bool UP, bool HALO = false>
 cudaError_t launch_nks(const ConvTC &c, cudaStream_t s, int nblk) {
   auto fn = encode_fn();
   if (!fn) return cudaErrorNotSupported;
@@ -384,7 +420,9 @@ cudaError_t launch_nks(const ConvTC &c, cudaStream_t s, int nblk) {
                               cuuint64_t(c.in_cs) * 2 * c.W * c.H};
   const int BW = c.W >= kM ? kM : (1 << (31 - __builtin_clz(unsigned(c.W))));
   const int BH = kM / BW;
-  const cuuint32_t abox[4] = {cuuint32_t(KB), cuuint32_t(BW), cuuint32_t(BH), 1};
+  if (HALO && BW != kM) return cudaErrorInvalidValue;
+  // the halo box is one image row of the tile and one pixel on either side
+  const cuuint32_t abox[4] = {cuuint32_t(KB), cuuint32_t(HALO ? kHaloPix : BW), cuuint32_t(HALO ? 1 : BH), 1};
   const cuuint32_t one[4] = {1, 1, 1, 1};
   if (fn(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(c.in), adim, astr, abox, one,
          CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(KB), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
@@ -418,16 +456,21 @@ cudaError_t launch_nks(const ConvTC &c, cudaStream_t s, int nblk) {
   a.n_base = c.n_base;
   a.up_cout = c.up_cout;
   a.err = c.err;
-  auto k = k_conv3x3_tc<N, KB, STAGES, UP>;
-  const cudaError_t e = prepare_nks<N, KB, STAGES, UP>();
+  auto k = k_conv3x3_tc<N, KB, STAGES, UP, HALO>;
+  const cudaError_t e = prepare_nks<N, KB, STAGES, UP, HALO>();
   if (e != cudaSuccess) return e;
   const long long tiles = (long long)a.tiles_w * a.tiles_h * c.B;
-  k<<<dim3(unsigned(tiles), unsigned(nblk)), kThreads, Layout<N, KB, STAGES>::BYTES, s>>>(ta, tb, a);
+  k<<<dim3(unsigned(tiles), unsigned(nblk)), kThreads, Layout<N, KB, STAGES, HALO>::BYTES, s>>>(ta, tb, a);
   return cudaGetLastError();
 }
 
 template <int N, int KB, bool UP>
 cudaError_t launch_nk(const ConvTC &c, cudaStream_t s, int nblk, long long ctas, int sms) {
+  // the halo loads for the 3x3 convolutions of up to 64 columns on images at
+  // least one tile wide (32 -> 32 at 1032 x 512: 42.5 -> 34.9 us; 128 -> 64 at
+  // 516 x 256: 34.3 -> 31.1 us); with 128 columns it was slower
+  if constexpr (!UP && N <= 64)
+    if (c.W >= kM) return launch_nks<N, KB, 2, false, true>(c, s, nblk);
   if constexpr (KB != 64) {
     return launch_nks<N, KB, stages_of<N, KB>(), UP>(c, s, nblk);
   } else {

@@ -68,6 +68,13 @@ CASES = [
     (1, 17, 40, 256, 128, 256, 0, 256, 128, False),
     # N = 256 (bottleneck)
     (1, 9, 32, 128, 256, 128, 0, 256, 0, True),
+    # halo loads (images at least 128 wide, up to 64 columns): W = 200 (the
+    # second tile ragged), batch 2, an input channel slice, KB = 32
+    (2, 7, 200, 32, 64, 64, 32, 64, 0, True),
+    # halo loads into an output slice, KB = 64, no activation
+    (1, 5, 128, 64, 32, 64, 0, 96, 32, False),
+    # 128 columns on a wide image: the per-tap loads
+    (1, 4, 256, 64, 128, 64, 0, 128, 0, True),
 ]
 
 
