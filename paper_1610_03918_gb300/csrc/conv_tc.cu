@@ -335,6 +335,132 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
 }
 
+// ---------------------------------------------------------------- first layer
+// The network's first 3x3 convolution (2 input channels -> 32) on the tensor
+// cores.  The 9 taps x 2 channels of a pixel, BF16-rounded, form one K row of
+// 32 (k = 2 tap + c, zeros from 18 on) of an A tile that the threads write to
+// shared memory, in the non-swizzled K-major layout: core matrices of 8 rows
+// x 16 bytes, 8 K values per plane of 128 rows, planes LBO = 2048 B apart,
+// 8-row groups SBO = 128 B apart.  B, the 32 x 32 weight matrix, has the same
+// layout (planes of 32 rows).  A CTA takes tiles of 128 consecutive pixels
+// (row-major over images, rows and columns) in turn: the threads build A,
+// one thread issues two MMAs of K = 16 into the TMEM accumulator and commits,
+// and the four warps read their 32 lanes back (bias, activation, BF16).
+constexpr int kInCh = 2, kInK = 32, kInN = 32;
+
+__device__ __forceinline__ uint64_t plain_desc(uint32_t addr, uint32_t lbo, uint32_t sbo) {
+  return uint64_t((addr & 0x3FFFF) >> 4) | (uint64_t(lbo >> 4) << 16) | (uint64_t(sbo >> 4) << 32) |
+         (uint64_t(1) << 46);   // layout type 0: no swizzle
+}
+__device__ __forceinline__ void fence_async_smem() {
+  asm volatile("fence.proxy.async.shared::cta;" ::: "memory");
+}
+__device__ __forceinline__ uint32_t pack_bf16(float lo, float hi) {
+  const uint32_t a = __bfloat16_as_ushort(__float2bfloat16_rn(lo));
+  const uint32_t b = __bfloat16_as_ushort(__float2bfloat16_rn(hi));
+  return a | (b << 16);
+}
+
+__global__ void __launch_bounds__(kThreads, 1)
+    k_conv_in_tc(const float2 *x, const bf16 *w, int wcin, const float *bias, bf16 *out, int B, int H, int W,
+                 int relu, int *err) {
+  __shared__ __align__(1024) uint8_t sA[(kInK / 8) * kM * 16];     // 4 planes of 128 rows
+  __shared__ __align__(1024) uint8_t sB[(kInK / 8) * kInN * 16];   // 4 planes of 32 rows
+  __shared__ __align__(8) uint64_t bar;
+  __shared__ uint32_t slot;
+  __shared__ float sbias[kInN];
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  // B[n][k] = w[n][tap][c], k = 2 tap + c < 18, else 0
+  for (int i = tid; i < kInN * kInK; i += kThreads) {
+    const int n = i / kInK, k = i - (i / kInK) * kInK;
+    const bf16 v = k < 9 * kInCh ? w[(size_t(n) * 9 + k / kInCh) * wcin + (k % kInCh)] : __float2bfloat16(0.f);
+    *reinterpret_cast<bf16 *>(sB + (k / 8) * (kInN * 16) + n * 16 + (k % 8) * 2) = v;
+  }
+  for (int i = tid; i < kInN; i += kThreads) sbias[i] = bias ? bias[i] : 0.f;
+  if (tid == 0) {
+    mbar_init(saddr(&bar), 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(saddr(&slot), kInN);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = slot;
+  constexpr uint32_t idesc = instr_desc<kInN>();
+  const unsigned npix = unsigned(B) * unsigned(H) * unsigned(W);
+  const unsigned ntiles = (npix + kM - 1) / kM;
+  uint32_t it = 0;
+  for (unsigned tile = blockIdx.x; tile < ntiles; tile += gridDim.x, ++it) {
+    // this thread's pixel (the A row tid) and its 9 x 2 inputs, zeros outside
+    // the image or past the end
+    const unsigned p = tile * kM + unsigned(tid);
+    const bool valid = p < npix;
+    const unsigned r = valid ? p / unsigned(W) : 0u;
+    const int wq = valid ? int(p - r * unsigned(W)) : 0;
+    const int h = int(r % unsigned(H));
+    float v[2 * 9];
+#pragma unroll
+    for (int t = 0; t < 9; ++t) {
+      const int hh = h + t / 3 - 1, ww = wq + t % 3 - 1;
+      float2 e = make_float2(0.f, 0.f);
+      if (valid && hh >= 0 && hh < H && ww >= 0 && ww < W) e = x[int(p) + (t / 3 - 1) * W + (t % 3 - 1)];
+      v[2 * t] = e.x;
+      v[2 * t + 1] = e.y;
+    }
+    const uint4 q0 = make_uint4(pack_bf16(v[0], v[1]), pack_bf16(v[2], v[3]), pack_bf16(v[4], v[5]), pack_bf16(v[6], v[7]));
+    const uint4 q1 = make_uint4(pack_bf16(v[8], v[9]), pack_bf16(v[10], v[11]), pack_bf16(v[12], v[13]),
+                                pack_bf16(v[14], v[15]));
+    const uint4 q2 = make_uint4(pack_bf16(v[16], v[17]), 0u, 0u, 0u);
+    const uint4 q3 = make_uint4(0u, 0u, 0u, 0u);
+    reinterpret_cast<uint4 *>(sA + 0 * kM * 16)[tid] = q0;
+    reinterpret_cast<uint4 *>(sA + 1 * kM * 16)[tid] = q1;
+    reinterpret_cast<uint4 *>(sA + 2 * kM * 16)[tid] = q2;
+    reinterpret_cast<uint4 *>(sA + 3 * kM * 16)[tid] = q3;
+    fence_async_smem();   // the threads' writes become visible to the tensor core's reads
+    __syncthreads();
+    if (tid == 0) {
+      tc_fence_after();
+#pragma unroll
+      for (int k = 0; k < kInK / 16; ++k)   // planes 2k, 2k + 1
+        mma_bf16(tmem, plain_desc(saddr(sA) + 2 * k * (kM * 16), kM * 16, 128),
+                 plain_desc(saddr(sB) + 2 * k * (kInN * 16), kInN * 16, 128), idesc, k ? 1u : 0u);
+      mma_commit(saddr(&bar));
+    }
+    __syncwarp();
+    const bool ok = __all_sync(0xffffffffu, mbar_wait(saddr(&bar), it & 1));
+    tc_fence_after();
+    if (ok) {
+      const uint32_t tl = tmem + (uint32_t(32 * warp) << 16);
+#pragma unroll
+      for (int n0 = 0; n0 < kInN; n0 += 16) {
+        uint32_t rr[16];
+        tmem_ld16(tl + n0, rr);
+        if (valid) {
+          __align__(16) bf16 o[16];
+#pragma unroll
+          for (int k = 0; k < 16; ++k) {
+            float y = __uint_as_float(rr[k]) + sbias[n0 + k];
+            if (relu) y = fmaxf(y, 0.f);
+            o[k] = __float2bfloat16_rn(y);
+          }
+          uint4 *dst = reinterpret_cast<uint4 *>(out + size_t(p) * kInN + n0);
+          dst[0] = reinterpret_cast<const uint4 *>(o)[0];
+          dst[1] = reinterpret_cast<const uint4 *>(o)[1];
+        }
+      }
+    } else if (lane == 0) {
+      atomicExch(&s_fail, 1);
+      atomicCAS(err, 0, 3);
+    }
+    tc_fence_before();
+    __syncthreads();   // TMEM read and A free for the next tile
+    if (s_fail) break;
+  }
+  if (warp == 0) tmem_dealloc(tmem, kInN);
+}
+
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -543,6 +669,18 @@ cudaError_t conv3x3_tc(const ConvTC &c, cudaStream_t s) {
     case 128: return up ? tc::launch_n<128, true>(c, s, nblk, ctas, sms) : tc::launch_n<128, false>(c, s, nblk, ctas, sms);
     default: return up ? tc::launch_n<256, true>(c, s, nblk, ctas, sms) : tc::launch_n<256, false>(c, s, nblk, ctas, sms);
   }
+}
+
+cudaError_t conv_in_tc(const float2 *x, const __nv_bfloat16 *w, int wcin, const float *bias,
+                       __nv_bfloat16 *out, int B, int H, int W, int relu, int *err, cudaStream_t s) {
+  const int sms = tc::sm_count();
+  if (sms < 1 || wcin < tc::kInCh) return cudaErrorInvalidValue;
+  const long long npix = (long long)B * H * W;
+  if (npix < 1 || npix >= (1LL << 31)) return cudaErrorInvalidValue;
+  const long long ntiles = (npix + tc::kM - 1) / tc::kM;
+  const long long grid = ntiles < 8LL * sms ? ntiles : 8LL * sms;   // 8 CTAs per SM, tiles in turn
+  tc::k_conv_in_tc<<<unsigned(grid), tc::kThreads, 0, s>>>(x, w, wcin, bias, out, B, H, W, relu, err);
+  return cudaGetLastError();
 }
 
 }  // namespace picgb

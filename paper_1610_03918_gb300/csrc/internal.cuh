@@ -452,6 +452,10 @@ bool conv3x3_tc_supported(int cin, int cout, int in_cs, int in_off, int out_cs, 
 cudaError_t conv3x3_tc(const ConvTC &c, cudaStream_t s);
 // sets the kernels' shared-memory attributes (before any stream capture)
 cudaError_t conv3x3_tc_prepare();
+// the network's first 3x3 convolution (2 FP32 input channels per pixel ->
+// 32 BF16 outputs [p][32]) on the tensor cores; w: BF16 [32][9][wcin]
+cudaError_t conv_in_tc(const float2 *x, const __nv_bfloat16 *w, int wcin, const float *bias,
+                       __nv_bfloat16 *out, int B, int H, int W, int relu, int *err, cudaStream_t s);
 
 // unet.cu
 void unet_forward_only(pic_unet *u, const float *x);

@@ -841,11 +841,17 @@ void forward(pic_unet *u, const float *x, bool keep_input) {
                                                          reinterpret_cast<uint4 *>(u->x16), pix(u, 0));
   // encoder; each level's output is written into the skip half of its concat buffer
   {
+    // the first convolution on the tensor cores (K = 9 taps x 2 channels
+    // packed into 32), or with the mma.sync kernels on the CUDA cores
     const pic_unet::Conv &c = u->conv[E0A];
-    // resident CTAs (5 of 256 threads per SM) that stage the weights once each
-    const int grid = std::min(gridn(2 * pix(u, 0)), 5 * u->num_sms);
-    k_conv_in<<<grid, 256, 0, u->stream>>>(reinterpret_cast<const float2 *>(x), c.w, c.cin_c,
-                                                       u->P + c.b_off, u->a[0], u->B, u->H, u->W, 1);
+    const float2 *x2 = reinterpret_cast<const float2 *>(x);
+    if (u->conv_impl != 0 || picgb::conv_in_tc(x2, c.w, c.cin_c, u->P + c.b_off, u->a[0], u->B, u->H, u->W, 1,
+                                               u->d_err, u->stream) != cudaSuccess) {
+      cudaGetLastError();
+      // resident CTAs (5 of 256 threads per SM) that stage the weights once each
+      const int grid = std::min(gridn(2 * pix(u, 0)), 5 * u->num_sms);
+      k_conv_in<<<grid, 256, 0, u->stream>>>(x2, c.w, c.cin_c, u->P + c.b_off, u->a[0], u->B, u->H, u->W, 1);
+    }
   }
   conv_fwd(u, E0B, u->a[0], C0, 0, u->cat[0], 2 * C0, C0, 0, true);
   k_pool_vec<<<gridn((long long)pix(u, 1) * C0 / 8), 256, 0, u->stream>>>(u->cat[0], 2 * C0, C0, u->p[1], C0, u->B, u->H, u->W);

@@ -101,9 +101,9 @@ def test_unet_training_reduces_loss(setup):
 
 
 def test_unet_forward_every_layer_on_tensor_cores():
-    # 64 x 64: every level is at least 8 wide, so the thirteen 3x3
-    # convolutions after the first (whose two input channels take a CUDA-core
-    # kernel) and all three transposed convolutions take the tcgen05 kernel;
+    # 64 x 64: every level is at least 8 wide, so all fourteen 3x3
+    # convolutions (the first with its 9 taps x 2 channels packed into one K
+    # row of 32) and all three transposed convolutions run on tcgen05;
     # against the BF16-emulating oracle and against the mma.sync network
     import torch
     import paper_1610_03918_gb300 as pg
