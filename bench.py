@@ -531,7 +531,7 @@ def unet_flops(H, W, B=1):
     convolutions (2 x cin x cout per output pixel) and the head."""
     C = (32, 64, 128, 256)
     f = 0.0
-    cin = 16                        # the input's 2 channels padded to 16
+    cin = 2                         # the input's two channels (rho / s and the mask)
     for l in range(4):
         px = B * (H >> l) * (W >> l)
         f += 2 * 9 * px * (cin * C[l] + C[l] * C[l])
