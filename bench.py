@@ -698,6 +698,10 @@ def main():
                          "during the warm-up")
     ap.add_argument("--warm-start", type=int, default=1,
                     help="Poisson initial guess: 0 zero, 1 previous, 2 extrapolated")
+    ap.add_argument("--no-autotune", action="store_true",
+                    help="keep the 16x16 tile variant instead of the library's autotuner's choice")
+    ap.add_argument("--autotune-steps", type=int, default=16,
+                    help="particle steps timed per tile variant by the autotuner")
     ap.add_argument("--no-graphs", action="store_true",
                     help="launch the step's kernels from the host loop (for kernel profilers)")
     args = ap.parse_args()
@@ -738,6 +742,24 @@ def main():
         sim.load_particles(s, parts[s], v_at_t0=True)
     sim.step(args.warmup)
     warm = args.warmup
+    # the tile variant chosen by the library's autotuner on this run (each
+    # variant's particle kernel timed right after a sort into its tiles)
+    tile_tune = None
+    if not args.no_autotune:
+        import shutil
+        import tempfile
+        tdir = tempfile.mkdtemp(prefix="picgb_tiles_")
+        try:
+            cache = os.path.join(tdir, "tiles.json")
+            chosen = sim.autotune(steps=args.autotune_steps, cache=cache)
+            with open(cache) as f:
+                entry = json.load(f)[0]
+            tile_tune = {"particle_ms_per_variant": entry["particle_ms"], "chosen": chosen,
+                         "steps_per_variant": args.autotune_steps}
+        finally:
+            shutil.rmtree(tdir, ignore_errors=True)
+        warm += 4 * (args.autotune_steps + 1)
+    tile = sim.tile()
     while sim.sort_interval()[0] == 0:    # a tuned sort interval is chosen before timing starts
         sim.step(8)
         warm += 8
@@ -823,8 +845,9 @@ def main():
     peak, peak_kind = _peaks()
     part_ms = tm["ms_particles"] / max(tm["steps"], 1)
     achieved = BYTES_PER_PARTICLE_STEP * 0.5 * (livep0 + livep1) / (part_ms * 1e-3) / 1e9
-    traffic = None
-    if NCU_TRAFFIC["source_sha256"] == _kernel_sha() and NCU_TRAFFIC["bytes_per_particle"]:
+    traffic = None   # captured for the 16x16 variant's kernel
+    if (NCU_TRAFFIC["source_sha256"] == _kernel_sha() and NCU_TRAFFIC["bytes_per_particle"]
+            and tile[0] == 0):
         traffic = NCU_TRAFFIC["bytes_per_particle"] * live_mean
 
     # end to end through the C ABI with pinned host buffers: every step loads
@@ -927,6 +950,10 @@ def main():
                        "particles_loaded": n0, "live_particles": live_mean,
                        "sort_every": (f"tuned by the library: {sort_interval}" if sort_tuned
                                       else sort_interval),
+                       "tile": {"variant": tile[0], "cells": [tile[1], tile[2]], "halo": tile[3],
+                                "threads": tile[4],
+                                "chosen_by": ("pic_autotune" if tile_tune else "fixed (--no-autotune)"),
+                                "autotune": tile_tune},
                        "warmup_steps_run": warm, "poisson_rtol": w.poisson_rtol,
                        "warm_start": ["zero", "previous", "extrapolated"][args.warm_start],
                        "poisson_inner_solver": "direct" if sim.solver() == pg.POISSON_AUTO else "multigrid PCG",
@@ -937,7 +964,7 @@ def main():
                        "parallelism": f"replicas{ws}" if ws > 1 else "single"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": traffic,
-                         "kernel": "k_particles<0> (gather+push+absorb+deposit)",
+                         "kernel": f"k_particles<0, {tile[0]}> (gather+push+absorb+deposit)",
                          "peak_kind": peak_kind, "bytes_per_particle_step": BYTES_PER_PARTICLE_STEP},
             "phases_ms_per_step": {
                 "particles": part_ms,
