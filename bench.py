@@ -382,6 +382,8 @@ def run_ensemble(args):
             "scaling": "weak", "vs_baseline": None, "dtype": "f32", "data": "synthetic",
             "config": {"workload": f"trench_width_ensemble_{args.members}", "members": args.members,
                        "ppc": wl[0].ppc, "particles_loaded": n0, "sort_every": wl[0].sort_every,
+                       "tile": ("16x16 for every member (timed one by one, most members "
+                                "prefer 32x32 or 16x32, which share the GPU worse)"),
                        "l2": "inputs larger than L2"},
             "roofline": {"bound": "hbm", "achieved": achieved, "peak": peak, "unit": "GB/s",
                          "frac": achieved / peak, "traffic": None, "peak_kind": peak_kind,
