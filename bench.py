@@ -397,7 +397,8 @@ def run_ensemble(args):
 
 def run_warmstart(args):
     """Poisson time to a 1e-6 relative residual on the trench geometry with
-    the learned initial guess against the zero and previous-step starts, on
+    the learned initial guess against the zero, lift (empty-box potential)
+    and previous-step starts, on
     held-out trench widths, timed inside the captured step graph with CUDA
     events (the learned guess -- network input, inference, guess -- is part of
     the solve phase).  The network is initialised by the library and trained
@@ -476,7 +477,7 @@ def run_warmstart(args):
     eval_net = pg.Unet(1, ws.padded_rows(1025), 512)
     eval_net.set_params(net.get_params())
     res, its, rel0 = {}, {}, {}
-    for name, mode in (("zero", 0), ("previous", 1), ("learned", 3)):
+    for name, mode in (("zero", 0), ("lift", 4), ("previous", 1), ("learned", 3)):
         ms, it = [], []
         for k, width in enumerate(int(v) for v in args.eval_widths.split(",")):
             w = trench(width, 900 + k)
@@ -518,6 +519,7 @@ def run_warmstart(args):
         "initial_rel_residual_geomean": rel0,
         "network_relative_mse": {"training_pairs": train_err, "held_out_pairs": held_err},
         "speedup_vs_zero": res["zero"] / res["learned"],
+        "speedup_vs_lift": res["lift"] / res["learned"],
         "speedup_vs_previous": res["previous"] / res["learned"],
         "wall_s": time.perf_counter() - t0,
     }
@@ -699,7 +701,7 @@ def main():
                     help="steps between tile sorts; 0 (default): the library times and picks it "
                          "during the warm-up")
     ap.add_argument("--warm-start", type=int, default=1,
-                    help="Poisson initial guess: 0 zero, 1 previous, 2 extrapolated")
+                    help="Poisson initial guess: 0 zero, 1 previous, 2 extrapolated, 4 lift")
     ap.add_argument("--no-autotune", action="store_true",
                     help="keep the 16x16 tile variant instead of the library's autotuner's choice")
     ap.add_argument("--autotune-steps", type=int, default=16,
@@ -957,7 +959,8 @@ def main():
                                 "chosen_by": ("pic_autotune" if tile_tune else "fixed (--no-autotune)"),
                                 "autotune": tile_tune},
                        "warmup_steps_run": warm, "poisson_rtol": w.poisson_rtol,
-                       "warm_start": ["zero", "previous", "extrapolated"][args.warm_start],
+                       "warm_start": {0: "zero", 1: "previous", 2: "extrapolated",
+                                      4: "lift"}[args.warm_start],
                        "poisson_inner_solver": "direct" if sim.solver() == pg.POISSON_AUTO else "multigrid PCG",
                        "l2": "inputs larger than L2 (particle state %.1f GB)" % (n0 * 24 / 1e9),
                        "timing": "value: the timed steps run without phase events; phases and the "

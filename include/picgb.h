@@ -106,7 +106,9 @@ typedef struct {
   int32_t warm_start;             /* 0: zero initial guess each solve, 1: previous phi,
                                      2: extrapolated 2 phi^n - phi^{n-1}, 3: learned -- the
                                      warm-start network's guess phi_L + s U(rho / s, mask)
-                                     (see unet_weights and pic_set_learned_start) */
+                                     (see unet_weights and pic_set_learned_start), 4: the
+                                     lift start -- phi_L, the potential of the empty box
+                                     (solved once), on the free nodes */
   int32_t device;                 /* CUDA device ordinal */
   int32_t timing;                 /* 1: each step records its phase boundaries in CUDA
                                      events (a pool of 64 steps, read back when it fills or
@@ -457,8 +459,9 @@ pic_status pic_set_learned_start(pic_ctx *c, const pic_unet *net);
 
 /* Change the initial guess of the solves that follow (pic_config.warm_start:
  * 0 zero, 1 previous, 2 extrapolated, 3 learned -- only once
- * pic_set_learned_start has given the context a network); the step graphs
- * are captured again.  Synchronous. */
+ * pic_set_learned_start has given the context a network -- 4 lift, whose
+ * empty-box potential is solved on the first switch); the step graphs are
+ * captured again.  Synchronous. */
 pic_status pic_set_warm_start(pic_ctx *c, int32_t mode);
 
 /* Training target of the warm-start network for the context's current

@@ -504,7 +504,8 @@ class Sim:
 
     def set_warm_start(self, mode: int):
         """Initial guess of the solves that follow: 0 zero, 1 previous,
-        2 extrapolated, 3 learned (after set_learned_start)."""
+        2 extrapolated, 3 learned (after set_learned_start), 4 lift (the
+        potential of the empty box)."""
         return self._check(load_library().pic_set_warm_start(self.ctx, int(mode)), "pic_set_warm_start")
 
     def set_learned_start(self, net):

@@ -212,7 +212,7 @@ pic_status validate(const pic_config *cfg) {
   if (cfg->periodic_y && (cfg->ny % 2)) return PIC_EINVAL;
   if (!(cfg->dt > 0) || !(cfg->poisson_rtol > 0)) return PIC_EINVAL;
   if (cfg->poisson_maxit < 1 || cfg->sort_every < 0) return PIC_EINVAL;
-  if (cfg->warm_start < 0 || cfg->warm_start > 3) return PIC_EINVAL;
+  if (cfg->warm_start < 0 || cfg->warm_start > 4) return PIC_EINVAL;
   if (cfg->warm_start == 3 && !cfg->unet_weights) return PIC_EINVAL;
   if (cfg->decomposed && cfg->sort_every < 1) return PIC_EINVAL;
   if (cfg->tile_variant < 0 || cfg->tile_variant >= kNumTileVariants) return PIC_EINVAL;
@@ -870,6 +870,14 @@ pic_status pic_init(const pic_config *cfg, pic_ctx **out) {
   c->fields_dirty = 1;
   c->needs_sort = 1;
   c->step = 0;
+  if (cfg->warm_start == 4) {   // the lift start: its potential is solved now
+    c->cfg.warm_start = 1;
+    st = pic_set_warm_start(c, 4);
+    if (st != PIC_OK) {
+      pic_free(c);
+      return st;
+    }
+  }
   if (cfg->warm_start == 3) {
     // the learned guess from a parameter file: a network of this grid's shape
     c->cfg.warm_start = 1;
@@ -909,10 +917,14 @@ pic_status pic_set_learned_start(pic_ctx *c, const pic_unet *net) {
 }
 
 pic_status pic_set_warm_start(pic_ctx *c, int32_t mode) {
-  if (!c || mode < 0 || mode > 3 || (mode == 3 && !c->net)) return PIC_EINVAL;
+  if (!c || mode < 0 || mode > 4 || (mode == 3 && !c->net)) return PIC_EINVAL;
   if (cudaSetDevice(c->dev) != cudaSuccess || cudaStreamSynchronize(c->stream) != cudaSuccess)
     return PIC_ECUDA;
   if (mode == c->cfg.warm_start) return PIC_OK;
+  if (mode == 4) {   // the empty-box potential, solved once, before any capture
+    const pic_status st = ensure_vacuum_potential(c);
+    if (st != PIC_OK) return st;
+  }
   for (int k = 0; k < 2; ++k)
     for (int v = 0; v < 2; ++v) {
       if (c->gexec[k][v]) cudaGraphExecDestroy(c->gexec[k][v]);

@@ -414,6 +414,15 @@ __global__ void k_phi_reset(FineArgs a) {
   GRID_STRIDE(n, a.g.nxn * a.g.nyn) a.phi[n] = a.gval[n];
 }
 
+// the lift start: phi <- phi_L, the potential of the empty box, on the free
+// nodes (the Dirichlet nodes keep their values, which the RF bias moves)
+__global__ void k_guess_lift(float2 *phi, const float2 *phiL, const uint8_t *flags, int nn) {
+  pdl_enter();
+  GRID_STRIDE(n, nn) {
+    if (flags[n] & kFree) phi[n] = phiL[n];
+  }
+}
+
 // initial guess extrapolated in time: phi <- 2 phi^n - phi^{n-1} on free nodes
 __global__ void k_extrapolate(FineArgs a) {
   pdl_enter();
@@ -1957,6 +1966,10 @@ pic_status poisson_solve(pic_ctx *c, bool zero_guess) {
     c->launches += 1;
   } else if (c->cfg.warm_start == 3) {
     if (launch_learned_guess(c) != cudaSuccess) return PIC_ECUDA;
+  } else if (c->cfg.warm_start == 4) {
+    launch(k_guess_lift, nb, kThreads, 0, c->stream, c->d_phi, c->d_phiL, c->d_nodeflags,
+           c->g.nxn * c->g.nyn);
+    c->launches += 1;
   }
   launch(k_outer_init, 1, 1, 0, c->stream, c->d_ps);
   c->launches += 1;
@@ -2074,6 +2087,8 @@ cudaError_t poisson_capture(pic_ctx *c, cudaGraph_t top, std::vector<cudaGraphNo
   if (c->cfg.warm_start == 0) launch(k_phi_reset, nb, kThreads, 0, s, a);
   if (c->cfg.warm_start == 2) launch(k_extrapolate, nb, kThreads, 0, s, a);
   if (c->cfg.warm_start == 3) CK(launch_learned_guess(c));
+  if (c->cfg.warm_start == 4)
+    launch(k_guess_lift, nb, kThreads, 0, s, c->d_phi, c->d_phiL, c->d_nodeflags, c->g.nxn * c->g.nyn);
   // (with the previous step's potential as the guess the density kernel just
   // before opened the solve)
   if (c->cfg.warm_start != 1) launch(k_outer_init, 1, 1, 0, s, c->d_ps);

@@ -192,12 +192,13 @@ def test_phase_timing_changes_no_result(name):
 @pytest.mark.parametrize("name", ["trench64", "trench"])
 def test_warm_start_modes_reach_the_same_fields(name):
     import paper_1610_03918_gb300 as pg
-    # zero, previous and extrapolated initial guesses (in the captured step
-    # graph the first two differ in their kernels: with the direct solve and
-    # the previous potential the first residual pass also forms rho)
+    # zero, previous, extrapolated and lift (the empty-box potential)
+    # initial guesses (in the captured step graph the first two differ in
+    # their kernels: with the direct solve and the previous potential the
+    # first residual pass also forms rho)
     w = ALL[name].replace(poisson_rtol=1e-10, sort_every=8)
     phis = []
-    for ws in (0, 1, 2):
+    for ws in (0, 1, 2, 4):
         gs = gpu_sim(w, warm_start=ws)
         for s in (0, 1):
             gs.load_particles(s, synth.maxwellian_load(w, s), v_at_t0=True)
