@@ -172,15 +172,23 @@ def _oracle_sample(w, seed_shift=0):
     return os_
 
 
-def _oracle_timed(w, steps, seed_shift=0):
-    """(particle-steps, seconds) of `steps` oracle steps on the sample."""
+def _oracle_timed(w, steps, seed_shift=0, solves=0):
+    """(particle-steps, seconds) of `steps` oracle steps on the sample; with
+    solves > 0 also the seconds of one field solve (the oracle's own
+    solve_fields, repeated `solves` times on the final state)."""
     os_ = _oracle_sample(w, seed_shift)
     done = 0
     t0 = time.perf_counter()
     for _ in range(steps):
         done += int(os_.live().sum())
         os_.step(1)
-    return done, time.perf_counter() - t0
+    t = time.perf_counter() - t0
+    if solves <= 0:
+        return done, t
+    t1 = time.perf_counter()
+    for _ in range(solves):
+        os_.solve_fields()
+    return done, t, (time.perf_counter() - t1) / solves
 
 
 def _oracle_replica(a):
@@ -206,7 +214,7 @@ def oracle_baseline(w, steps=40):
     and scipy run it on one core), and one independent replica per core at
     once (different particle draws), all started by spawn."""
     import multiprocessing as mp
-    n1, t1 = _oracle_timed(w, steps)
+    n1, t1, t_solve = _oracle_timed(w, steps, solves=5)
     cores = min(os.cpu_count() or 1, 16)
     ctx = mp.get_context("spawn")
     with ctx.Pool(cores) as pool:
@@ -220,7 +228,14 @@ def oracle_baseline(w, steps=40):
     sample = (f"{w.name}: full 512x1024 grid (sparse LU factorised once, untimed), "
               f"{ORACLE_SAMPLE} particles/species of {int(synth.plasma_cells(w).sum()) * w.ppc}, "
               f"{steps} oracle steps")
+    # the step split into its field solve and its particle phase (one core)
+    t_part = max(t1 / steps - t_solve, 1e-12)
+    phases = {"poisson_ms_per_solve": 1e3 * t_solve,
+              "particle_phase_particle_steps_per_s": n1 / steps / t_part,
+              "note": "the oracle's solve_fields (rho from the particles, sparse LU solve, E) "
+                      "timed 5 times on the final state; the particle phase is the rest of a step"}
     return {"value": n1 / t1, "unit": UNIT, "cores": 1, "kind": "oracle", "sample": sample,
+            "phases_one_core": phases,
             "all_cores": {"value": nall / tall, "unit": UNIT, "cores": cores,
                           "sample": f"{cores} independent replicas of the sample at once "
                                     f"(spawned processes, {wall:.1f} s wall with their set-up)"},
