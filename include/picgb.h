@@ -436,6 +436,38 @@ pic_status pic_conv3x3_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const
                             int32_t in_off, int32_t cin, const void *w, const float *bias, int32_t relu,
                             void *out, int32_t out_cs, int32_t out_off, int32_t cout, void *stream);
 
+/* The weight gradient of one 3x3 convolution with zero padding (the U-Net's
+ * layer): dw[n][3 dy + dx][c] += sum_{b, h, w} dpre[b][h][w][n] *
+ *   in[b][h + dy - 1][w + dx - 1][in_off + c], dy, dx in {0, 1, 2}.
+ * dpre: DEVICE BF16 [B][H][W][cout] (the gradient before the activation);
+ * in: DEVICE BF16 NHWC with channel stride in_cs; dw: DEVICE FP32
+ * [cout][9][cin], ADDED to (zero it first), 16-byte aligned for impl 0.
+ * impl 0: tcgen05 tensor cores (cout 32 or a multiple of 64, cin 16, 32 or a
+ * multiple of 64, in_cs and in_off multiples of 8, else PIC_EINVAL); impl 1:
+ * mma.sync (channel counts, in_cs and in_off multiples of 8).  FP32 products
+ * of the BF16 values, summed in FP32 with atomic adds (the order of the sum
+ * varies from run to run).  Synchronous on `stream`; PIC_ETIMEOUT if a
+ * bounded wait of the tensor-core kernel gave up. */
+pic_status pic_conv3x3_wgrad_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const void *dpre,
+                                  const void *in, int32_t in_cs, int32_t in_off, int32_t cin, int32_t cout,
+                                  float *dw, void *stream);
+
+/* The data gradient of the U-Net's 2x2 stride-2 transposed convolution (the
+ * input-side gradient of its upsampling layer):
+ * gin[b][y][x][n] = sum_{a, c in {0, 1}} sum_{k < cout}
+ *   gout[b][2y + a][2x + c][gout_off + k] * w[2a + c][n][k].
+ * gout: DEVICE BF16 NHWC [B][2H][2W] with channel stride gout_cs; w: DEVICE
+ * FP32 [2][2][cin][cout] (the layer's parameter order); gin: DEVICE BF16
+ * [B][H][W][cin].  impl 0: tcgen05 tensor cores on a BF16 copy of w (a
+ * temporary device buffer of 8 cin cout bytes; cin 32, 64, 128 or 256, cout a
+ * multiple of 16, gout_cs and gout_off multiples of 8, W >= 8, else
+ * PIC_EINVAL); impl 1: CUDA cores with the FP32 weights.  FP32 accumulation,
+ * BF16 rounding of the result.  Synchronous on `stream`; PIC_ETIMEOUT if a
+ * bounded wait of the tensor-core kernel gave up. */
+pic_status pic_upconv_back_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const void *gout,
+                                int32_t gout_cs, int32_t gout_off, int32_t cout, const float *w, void *gin,
+                                int32_t cin, void *stream);
+
 /* He initialisation of every weight (He et al., ICCV 2015: N(0, 2 / fan_in)
  * for the layers followed by a ReLU, N(0, 1 / fan_in) for the linear head;
  * fan_in = 9 x input channels for a 3x3 convolution, the input channels for

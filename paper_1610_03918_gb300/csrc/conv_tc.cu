@@ -85,6 +85,14 @@ __device__ __forceinline__ void tma_load_4d(uint32_t dst, const CUtensorMap *map
       "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(bar)
       : "memory");
 }
+__device__ __forceinline__ void tma_load_5d(uint32_t dst, const CUtensorMap *map, int c0, int c1, int c2,
+                                            int c3, int c4, uint32_t bar) {
+  asm volatile(
+      "cp.async.bulk.tensor.5d.shared::cluster.global.tile.mbarrier::complete_tx::bytes "
+      "[%0], [%1, {%2, %3, %4, %5, %6}], [%7];" ::"r"(dst),
+      "l"(reinterpret_cast<uint64_t>(map)), "r"(c0), "r"(c1), "r"(c2), "r"(c3), "r"(c4), "r"(bar)
+      : "memory");
+}
 __device__ __forceinline__ void tma_load_2d(uint32_t dst, const CUtensorMap *map, int c0, int c1,
                                             uint32_t bar) {
   asm volatile(
@@ -164,6 +172,7 @@ struct TCArgs {
   int BW, BH, tiles_w, tiles_h;
   int n_base;          // first GEMM column of this launch; CTA row y of the grid adds y N
   int up_cout;         // transposed convolution: output channels (GEMM column n = (2a + c) up_cout + co)
+  int ncols;           // data gradient of the transposed convolution: GEMM columns (weight rows per tap)
   int *err;            // error word: 1 producer, 2 MMA, 3 epilogue wait gave up
 };
 
@@ -193,10 +202,17 @@ struct Layout {
 // MMA's start address moves by whole swizzled rows, and the swizzle follows
 // the shared-memory address, so the shifted operand is the tap's tile.  That
 // moves a third of the input bytes of nine shifted tiles.
-template <int N, int KB, int STAGES, bool UP, bool HALO = false>
+// UPB: the data gradient of the transposed convolution.  Input pixel (y, x)
+// of that convolution gathers, over its four children (2y + a, 2x + c), the
+// output gradient's channels: four taps t = 2a + c, each a 5-D box {KB, 1,
+// BW, 1, BH} of the gradient viewed as {channels, c, x, a, image rows} -- the
+// rows of the tap's 128 pixels, in the same K-major layout as the other
+// modes.  B: the weights [4 ncols][cout], rows t ncols + n.
+template <int N, int KB, int STAGES, bool UP, bool HALO = false, bool UPB = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_conv3x3_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, TCArgs a) {
   static_assert(!(UP && HALO), "the transposed convolution has one tap");
+  static_assert(!(UPB && (UP || HALO)), "one mode at a time");
   using L = Layout<N, KB, STAGES, HALO>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
@@ -230,7 +246,7 @@ __global__ void __launch_bounds__(kThreads, 1)
   tc_fence_after();
   const uint32_t tmem = *slot;
   const int kchunks = a.cin / KB;
-  const int nk = (UP ? 1 : (HALO ? 3 : 9)) * kchunks;
+  const int nk = (UP ? 1 : (HALO ? 3 : (UPB ? 4 : 9))) * kchunks;
 
   if (tid == 0) {
     // TMA producer: stage s of round r is reused once the MMAs of round r - 1 released it
@@ -243,6 +259,13 @@ __global__ void __launch_bounds__(kThreads, 1)
         break;
       }
       if (s_fail) break;
+      if (UPB) {
+        const int tap = kb / kchunks, c0 = (kb - tap * kchunks) * KB;
+        mbar_expect_tx(bar0 + 8 * s, L::A_TX + L::B_BYTES);
+        tma_load_5d(sA + s * L::A_BYTES, &tmA, a.in_off + c0, tap & 1, w0, tap >> 1, b * a.H + h0, bar0 + 8 * s);
+        tma_load_2d(sB + s * L::B_BYTES, &tmB, c0, tap * a.ncols + nb0, bar0 + 8 * s);
+        continue;
+      }
       if (HALO) {
         const int dy = kb / kchunks, c0 = (kb - dy * kchunks) * KB;
         mbar_expect_tx(bar0 + 8 * s, L::A_TX + L::B_BYTES);
@@ -461,6 +484,185 @@ __global__ void __launch_bounds__(kThreads, 1)
   if (warp == 0) tmem_dealloc(tmem, kInN);
 }
 
+// ---------------------------------------------------------------- weight gradient
+// dW[co][3 dy + dx][ci] += sum_p dpre[p][co] in[p + (dy - 1, dx - 1)][ci] (zero
+// padding), dpre the gradient before the ReLU [B][H][W][cout], in the layer's
+// input.  A K block is KP = 64 consecutive pixels (w0 .. w0 + 63) of one input
+// row hq of one image.  Both operands are MN-major: pixels (K) are the rows
+// of a swizzled tile, channels (M, N) run along the row.
+//  * B, the input: the row hq from pixel w0 - 8 to w0 + KP + 7 (TMA box
+//    {CI, KP + 16}; the x coordinate stays a multiple of 8), CI channels.
+//    The three horizontal taps are three N chunks of CI channels whose
+//    starts lie one pixel row apart (LBO = one row), so N = 3 CI covers
+//    dx = 0, 1, 2 at once, each chunk being the input shifted by dx - 1.
+//  * A, the gradient: three slots, slot s the dpre row hq + 1 - s (pixels w0
+//    .. w0 + KP - 1, zero fill off the image), one slot per vertical tap
+//    (dpre row hq + 1 - dy meets input row hq at tap dy), and a fourth slot
+//    of zeros.  M = 128 rows of D are slots of CO channels at LBO = one slot:
+//    CO = 32, all four slots in one MMA; CO = 64, slots {0, 1} and {2, 3}.
+// D row (s, co), column (dx, ci) thus accumulates dW[co][3 s + dx][ci] over
+// the CTA's K blocks; the epilogue adds it to dW with vector atomics (FP32,
+// so the sum order, not the terms, depends on the grid).
+constexpr int kWKP = 64;   // pixels per K block
+
+template <int CO, int CI, int STAGES>
+struct WLayout {
+  static constexpr int KPB = kWKP + 16;   // the input row with 8-pixel margins
+  static constexpr uint32_t SLOT = kWKP * CO * 2;
+  static constexpr uint32_t A_BYTES = 4 * SLOT;
+  static constexpr uint32_t B_TX = KPB * CI * 2;
+  static constexpr uint32_t B_BYTES = ((B_TX + 1023) / 1024) * 1024;
+  static constexpr uint32_t STAGE = A_BYTES + B_BYTES;
+  static constexpr uint32_t BAR_OFF = STAGES * STAGE;
+  // allocated, never written: keeps every address the descriptors of the last
+  // stage can form inside this CTA's shared memory (the widest reading of
+  // the B tile spans 3 CI rows of 8-row groups from row 55)
+  static constexpr uint32_t TAIL = 6 * CI * CI + 112 * CI;
+  static constexpr uint32_t BYTES = BAR_OFF + (2 * STAGES + 1) * 8 + 16 + TAIL + 1024;
+  static constexpr int NM = CO == 32 ? 1 : 2;   // MMAs along M per 16 pixels
+  static constexpr int N = 3 * CI;
+  static constexpr uint32_t NCOLS = NM * N <= 32 ? 32 : NM * N <= 64 ? 64 : NM * N <= 128 ? 128 : NM * N <= 256 ? 256 : 512;
+};
+
+// descriptor of an MN-major tile in the swizzled layout TMA wrote with rows
+// of CH channels: K rows CH x 2 bytes apart, groups of 8 rows SBO = 8 rows
+// apart, chunks of CH channels along M or N at LBO
+template <int CH>
+__device__ __forceinline__ uint64_t mn_desc(uint32_t addr, uint32_t lbo) {
+  return uint64_t((addr & 0x3FFFF) >> 4) | (uint64_t(lbo >> 4) << 16) |
+         (uint64_t((8 * Swz<CH>::row_bytes) >> 4) << 32) | (uint64_t(1) << 46) | (Swz<CH>::layout << 61);
+}
+// kind::f16 with BF16 A and B, both MN-major (transpose bits 15 and 16)
+template <int N>
+__host__ __device__ constexpr uint32_t instr_desc_mn() {
+  return instr_desc<N>() | (1u << 15) | (1u << 16);
+}
+
+struct WArgs {
+  float *dw;           // [cout][9][cin]
+  int cin, cout, in_off, H, nwc;
+  long long nkb;       // K blocks: B H rows x nwc pixel chunks
+  long long per_cta;   // K blocks per CTA along the grid's first index
+  int *err;
+};
+
+template <int CO, int CI, int STAGES>
+__global__ void __launch_bounds__(kThreads, 1)
+    k_wgrad_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, WArgs a) {
+  using L = WLayout<CO, CI, STAGES>;
+  extern __shared__ uint8_t smem_raw[];
+  uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
+  const uint32_t s0 = saddr(smem);
+  const uint32_t bar0 = s0 + L::BAR_OFF;   // full[s] = bar0 + 8 s, empty[s] = bar0 + 8 (STAGES + s)
+  const uint32_t done = bar0 + 16 * STAGES;
+  uint32_t *slot = reinterpret_cast<uint32_t *>(smem + L::BAR_OFF + (2 * STAGES + 1) * 8);
+  __shared__ int s_fail;
+  const int tid = threadIdx.x, warp = tid >> 5, lane = tid & 31;
+  const int ncib = a.cin / CI;
+  const int co0 = int(blockIdx.y) / ncib * CO, ci0 = int(blockIdx.y) % ncib * CI;
+  const long long k0 = blockIdx.x * a.per_cta;
+  const long long k1 = k0 + a.per_cta < a.nkb ? k0 + a.per_cta : a.nkb;
+  const int nk = int(k1 - k0);   // at least 1 (the host sizes the grid so)
+
+  // the fourth A slot of every stage holds zeros (the MMA's rows 96..127 for
+  // CO = 32, 64..127 of the second MMA for CO = 64; discarded)
+  for (int st = 0; st < STAGES; ++st)
+    for (uint32_t o = 16 * tid; o < L::SLOT; o += 16 * kThreads)
+      *reinterpret_cast<uint4 *>(smem + st * L::STAGE + 3 * L::SLOT + o) = make_uint4(0, 0, 0, 0);
+  fence_async_smem();
+  if (tid == 0) {
+    for (int s = 0; s < STAGES; ++s) {
+      mbar_init(bar0 + 8 * s, 1);
+      mbar_init(bar0 + 8 * (STAGES + s), 1);
+    }
+    mbar_init(done, 1);
+    s_fail = 0;
+    asm volatile("fence.mbarrier_init.release.cluster;" ::: "memory");
+  }
+  if (warp == 0) tmem_alloc(saddr(slot), L::NCOLS);
+  tc_fence_before();
+  __syncthreads();
+  tc_fence_after();
+  const uint32_t tmem = *slot;
+
+  if (tid == 0) {
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (kb >= STAGES && !mbar_wait(bar0 + 8 * (STAGES + s), ph ^ 1)) {
+        atomicExch(&s_fail, 1);
+        atomicCAS(a.err, 0, 1);
+        break;
+      }
+      if (s_fail) break;
+      const long long g = k0 + kb;
+      const long long r = g / a.nwc;              // b H + hq
+      const int w0 = int(g - r * a.nwc) * kWKP;
+      const int b = int(r / a.H), hq = int(r - (long long)b * a.H);
+      const uint32_t st = s0 + s * L::STAGE;
+      mbar_expect_tx(bar0 + 8 * s, 3 * L::SLOT + L::B_TX);
+      for (int sl = 0; sl < 3; ++sl)
+        tma_load_4d(st + sl * L::SLOT, &tmA, co0, w0, hq + 1 - sl, b, bar0 + 8 * s);
+      tma_load_4d(st + L::A_BYTES, &tmB, a.in_off + ci0, w0 - 8, hq, b, bar0 + 8 * s);
+    }
+  } else if (tid == 32) {
+    constexpr uint32_t idesc = instr_desc_mn<L::N>();
+    for (int kb = 0; kb < nk; ++kb) {
+      const int s = kb % STAGES;
+      const uint32_t ph = (kb / STAGES) & 1;
+      if (!mbar_wait(bar0 + 8 * s, ph)) {
+        atomicExch(&s_fail, 1);
+        atomicCAS(a.err, 0, 2);
+        break;
+      }
+      tc_fence_after();
+      const uint32_t st = s0 + s * L::STAGE;
+#pragma unroll
+      for (int k = 0; k < kWKP / 16; ++k) {
+        // input rows 7 + 16 k ..: pixel w0 - 1 + 16 k on, the tap dx = 0 chunk
+        const uint64_t db = mn_desc<CI>(st + L::A_BYTES + (7 + 16 * k) * (CI * 2), CI * 2);
+#pragma unroll
+        for (int m = 0; m < L::NM; ++m) {
+          const uint64_t da = mn_desc<CO>(st + 2 * m * L::SLOT + 16 * k * (CO * 2), L::SLOT);
+          mma_bf16(tmem + m * L::N, da, db, idesc, (kb | k) != 0 ? 1u : 0u);
+        }
+      }
+      mma_commit(bar0 + 8 * (STAGES + s));
+    }
+    mma_commit(done);
+  }
+
+  // epilogue: warp w reads D rows 32 w .. 32 w + 31 of each accumulator
+  __syncwarp();
+  const bool ok = mbar_wait(done, 0);
+  tc_fence_after();
+  if (!ok) atomicCAS(a.err, 0, 3);
+#pragma unroll
+  for (int m = 0; m < L::NM; ++m) {
+    const int row = 32 * warp + lane;                       // D row of MMA m
+    const int sl = CO == 32 ? warp : 2 * m + (row >> 6);    // A slot = vertical tap
+    const int co = co0 + (CO == 32 ? lane : (row & 63));
+    if (sl == 3) continue;                                  // warp-uniform: the zero slot
+    const uint32_t tl = tmem + (uint32_t(32 * warp) << 16) + m * L::N;
+#pragma unroll 1
+    for (int n0 = 0; n0 < L::N; n0 += 16) {
+      uint32_t v[16];
+      tmem_ld16(tl + n0, v);
+      if (ok && !s_fail) {
+        const int dx = n0 / CI, ci = ci0 + (n0 - dx * CI);
+        float4 *dst = reinterpret_cast<float4 *>(a.dw + (size_t(co) * 9 + 3 * sl + dx) * a.cin + ci);
+#pragma unroll
+        for (int q = 0; q < 4; ++q)
+          atomicAdd(dst + q, make_float4(__uint_as_float(v[4 * q]), __uint_as_float(v[4 * q + 1]),
+                                         __uint_as_float(v[4 * q + 2]), __uint_as_float(v[4 * q + 3])));
+      }
+    }
+  }
+  tc_fence_before();
+  __syncthreads();
+  if (warp == 0) tmem_dealloc(tmem, L::NCOLS);
+}
+
 // ---------------------------------------------------------------- host side
 PFN_cuTensorMapEncodeTiled_v12000 encode_fn() {
   static PFN_cuTensorMapEncodeTiled_v12000 fn = nullptr;
@@ -613,13 +815,146 @@ cudaError_t launch_n(const ConvTC &c, cudaStream_t s, int nblk, long long ctas, 
   return launch_nk<N, 16, UP>(c, s, nblk, ctas, sms);
 }
 
+constexpr int kUpbStages = 3;
+template <int N, int KB>
+cudaError_t prepare_upb() {
+  static cudaError_t e = cudaFuncSetAttribute(k_conv3x3_tc<N, KB, kUpbStages, false, false, true>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(Layout<N, KB, kUpbStages>::BYTES));
+  return e;
+}
+
 template <int N>
 cudaError_t prepare_n() {
   cudaError_t e = cudaSuccess;
   for (cudaError_t f : {prepare_nk<N, 64, false>(), prepare_nk<N, 32, false>(), prepare_nk<N, 16, false>(),
-                        prepare_nk<N, 64, true>(), prepare_nk<N, 32, true>(), prepare_nk<N, 16, true>()})
+                        prepare_nk<N, 64, true>(), prepare_nk<N, 32, true>(), prepare_nk<N, 16, true>(),
+                        prepare_upb<N, 64>(), prepare_upb<N, 32>(), prepare_upb<N, 16>()})
     if (e == cudaSuccess) e = f;
   return e;
+}
+
+// Data gradient of the transposed convolution (UPB): grid (pixel tiles of
+// the transposed convolution's input, column blocks of its input channels)
+template <int N, int KB>
+cudaError_t launch_upb(const ConvTC &c, cudaStream_t s, int nblk) {
+  constexpr int STAGES = kUpbStages;
+  using L = Layout<N, KB, STAGES>;
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cudaError_t attr = prepare_upb<N, KB>();
+  if (attr != cudaSuccess) return attr;
+  CUtensorMap ta, tb;
+  // the output gradient [B][2H][2W][in_cs] as {channels, c, x, a, B H}: child (a, c)
+  // of input pixel (y, x) is (2y + a, 2x + c)
+  const cuuint64_t e = 2;   // bytes per element
+  const cuuint64_t adim[5] = {cuuint64_t(c.in_cs), 2, cuuint64_t(c.W), 2, cuuint64_t(c.B) * c.H};
+  const cuuint64_t astr[4] = {cuuint64_t(c.in_cs) * e, cuuint64_t(c.in_cs) * e * 2,
+                              cuuint64_t(c.in_cs) * e * 2 * c.W, cuuint64_t(c.in_cs) * e * 4 * c.W};
+  const int BW = c.W >= kM ? kM : (1 << (31 - __builtin_clz(unsigned(c.W))));
+  const int BH = kM / BW;
+  const cuuint32_t abox[5] = {cuuint32_t(KB), 1, cuuint32_t(BW), 1, cuuint32_t(BH)};
+  const cuuint32_t one[5] = {1, 1, 1, 1, 1};
+  if (fn(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(c.in), adim, astr, abox, one,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(KB), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  // weights [4 ncols][K]: {K, 4 ncols}; box {KB, N}
+  const cuuint64_t bdim[2] = {cuuint64_t(c.cin), cuuint64_t(4) * c.cout};
+  const cuuint64_t bstr[1] = {cuuint64_t(c.cin) * e};
+  const cuuint32_t bbox[2] = {cuuint32_t(KB), cuuint32_t(N)};
+  if (fn(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 2, const_cast<bf16 *>(c.w), bdim, bstr, bbox, one,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(KB), CU_TENSOR_MAP_L2_PROMOTION_L2_256B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  TCArgs a;
+  a.out = c.out;
+  a.out_cs = c.out_cs;
+  a.out_off = c.out_off;
+  a.bias = nullptr;
+  a.relu = 0;
+  a.B = c.B;
+  a.H = c.H;
+  a.W = c.W;
+  a.cin = c.cin;
+  a.in_off = c.in_off;
+  a.BW = BW;
+  a.BH = BH;
+  a.tiles_w = (c.W + BW - 1) / BW;
+  a.tiles_h = (c.H + BH - 1) / BH;
+  a.n_base = 0;
+  a.up_cout = 0;
+  a.ncols = c.cout;
+  a.err = c.err;
+  const long long tiles = (long long)a.tiles_w * a.tiles_h * c.B;
+  k_conv3x3_tc<N, KB, STAGES, false, false, true>
+      <<<dim3(unsigned(tiles), unsigned(nblk)), kThreads, L::BYTES, s>>>(ta, tb, a);
+  return cudaGetLastError();
+}
+
+template <int N>
+cudaError_t launch_upb_n(const ConvTC &c, cudaStream_t s, int nblk) {
+  if (c.cin % 64 == 0) return launch_upb<N, 64>(c, s, nblk);
+  if (c.cin % 32 == 0) return launch_upb<N, 32>(c, s, nblk);
+  return launch_upb<N, 16>(c, s, nblk);
+}
+
+constexpr int kWStages = 3;
+template <int CO, int CI>
+cudaError_t prepare_wgrad() {
+  static cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<CO, CI, kWStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(WLayout<CO, CI, kWStages>::BYTES));
+  return e;
+}
+
+template <int CO, int CI>
+cudaError_t launch_wgrad(const WgradTC &g, cudaStream_t s, int sms) {
+  using L = WLayout<CO, CI, kWStages>;
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cudaError_t attr = prepare_wgrad<CO, CI>();
+  if (attr != cudaSuccess) return attr;
+  const cuuint64_t e = 2;
+  const cuuint32_t one[4] = {1, 1, 1, 1};
+  CUtensorMap ta, tb;
+  // the gradient [B][H][W][cout] as {cout, W, H, B}, boxes {CO, 64 pixels}
+  const cuuint64_t adim[4] = {cuuint64_t(g.cout), cuuint64_t(g.W), cuuint64_t(g.H), cuuint64_t(g.B)};
+  const cuuint64_t astr[3] = {cuuint64_t(g.cout) * e, cuuint64_t(g.cout) * e * g.W, cuuint64_t(g.cout) * e * g.W * g.H};
+  const cuuint32_t abox[4] = {cuuint32_t(CO), cuuint32_t(kWKP), 1, 1};
+  if (fn(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(g.dpre), adim, astr, abox, one,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(CO), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  // the input [B][H][W][in_cs] as {in_cs, W, H, B}, boxes {CI, 80 pixels}
+  const cuuint64_t bdim[4] = {cuuint64_t(g.in_cs), cuuint64_t(g.W), cuuint64_t(g.H), cuuint64_t(g.B)};
+  const cuuint64_t bstr[3] = {cuuint64_t(g.in_cs) * e, cuuint64_t(g.in_cs) * e * g.W,
+                              cuuint64_t(g.in_cs) * e * g.W * g.H};
+  const cuuint32_t bbox[4] = {cuuint32_t(CI), cuuint32_t(L::KPB), 1, 1};
+  if (fn(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(g.in), bdim, bstr, bbox, one,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(CI), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  WArgs a;
+  a.dw = g.dw;
+  a.cin = g.cin;
+  a.cout = g.cout;
+  a.in_off = g.in_off;
+  a.H = g.H;
+  a.nwc = (g.W + kWKP - 1) / kWKP;
+  a.nkb = (long long)g.B * g.H * a.nwc;
+  a.err = g.err;
+  // one wave: the CTAs that fit on the SMs at once (shared memory, TMEM
+  // columns), shared out over the (co, ci) blocks, each a run of K blocks
+  const int yb = (g.cout / CO) * (g.cin / CI);
+  const int res_smem = int((227u * 1024u) / L::BYTES), res_tmem = int(512u / L::NCOLS);
+  const int res = res_smem < res_tmem ? (res_smem > 0 ? res_smem : 1) : res_tmem;
+  long long splits = ((long long)sms * res + yb - 1) / yb;
+  if (splits > a.nkb) splits = a.nkb;
+  if (splits < 1) splits = 1;
+  a.per_cta = (a.nkb + splits - 1) / splits;
+  splits = (a.nkb + a.per_cta - 1) / a.per_cta;
+  k_wgrad_tc<CO, CI, kWStages><<<dim3(unsigned(splits), unsigned(yb)), kThreads, L::BYTES, s>>>(ta, tb, a);
+  return cudaGetLastError();
 }
 
 int sm_count() {
@@ -636,6 +971,9 @@ cudaError_t conv3x3_tc_prepare() {
   if (e == cudaSuccess) e = tc::prepare_n<64>();
   if (e == cudaSuccess) e = tc::prepare_n<128>();
   if (e == cudaSuccess) e = tc::prepare_n<256>();
+  for (cudaError_t f : {tc::prepare_wgrad<32, 16>(), tc::prepare_wgrad<32, 32>(), tc::prepare_wgrad<32, 64>(),
+                        tc::prepare_wgrad<64, 16>(), tc::prepare_wgrad<64, 32>(), tc::prepare_wgrad<64, 64>()})
+    if (e == cudaSuccess) e = f;
   return e;
 }
 
@@ -681,6 +1019,49 @@ cudaError_t conv_in_tc(const float2 *x, const __nv_bfloat16 *w, int wcin, const 
   const long long grid = ntiles < 8LL * sms ? ntiles : 8LL * sms;   // 8 CTAs per SM, tiles in turn
   tc::k_conv_in_tc<<<unsigned(grid), tc::kThreads, 0, s>>>(x, w, wcin, bias, out, B, H, W, relu, err);
   return cudaGetLastError();
+}
+
+cudaError_t conv_upback_tc(const ConvTC &c, cudaStream_t s) {
+  if (!conv3x3_tc_supported(c.cin, c.cout, c.in_cs, c.in_off, c.out_cs, c.out_off, c.W) ||
+      (long long)c.B * c.H >= (1LL << 31))
+    return cudaErrorNotSupported;
+  const int sms = tc::sm_count();
+  if (sms < 1) return cudaErrorInvalidValue;
+  const int BW = c.W >= tc::kM ? tc::kM : (1 << (31 - __builtin_clz(unsigned(c.W))));
+  const long long tiles = (long long)((c.W + BW - 1) / BW) * ((c.H + tc::kM / BW - 1) / (tc::kM / BW)) * c.B;
+  int n = c.cout, nblk = 1;
+  while (n > 64 && tiles * nblk < sms) {
+    n >>= 1;
+    nblk <<= 1;
+  }
+  switch (n) {
+    case 32: return tc::launch_upb_n<32>(c, s, nblk);
+    case 64: return tc::launch_upb_n<64>(c, s, nblk);
+    case 128: return tc::launch_upb_n<128>(c, s, nblk);
+    default: return tc::launch_upb_n<256>(c, s, nblk);
+  }
+}
+
+bool conv_wgrad_tc_supported(int cin, int cout, int in_cs, int in_off, const float *dw) {
+  return (cout == 32 || (cout >= 64 && cout % 64 == 0)) && (cin == 16 || cin == 32 || (cin >= 64 && cin % 64 == 0)) &&
+         in_cs % 8 == 0 && in_off % 8 == 0 && in_off + cin <= in_cs && (reinterpret_cast<uintptr_t>(dw) & 15) == 0 &&
+         tc::encode_fn() != nullptr;
+}
+
+cudaError_t conv_wgrad_tc(const WgradTC &g, cudaStream_t s) {
+  if (!conv_wgrad_tc_supported(g.cin, g.cout, g.in_cs, g.in_off, g.dw) || g.B < 1 || g.H < 1 || g.W < 1)
+    return cudaErrorNotSupported;
+  const int sms = tc::sm_count();
+  if (sms < 1) return cudaErrorInvalidValue;
+  const int ci = g.cin >= 64 ? 64 : g.cin;
+  if (g.cout == 32) {
+    if (ci == 16) return tc::launch_wgrad<32, 16>(g, s, sms);
+    if (ci == 32) return tc::launch_wgrad<32, 32>(g, s, sms);
+    return tc::launch_wgrad<32, 64>(g, s, sms);
+  }
+  if (ci == 16) return tc::launch_wgrad<64, 16>(g, s, sms);
+  if (ci == 32) return tc::launch_wgrad<64, 32>(g, s, sms);
+  return tc::launch_wgrad<64, 64>(g, s, sms);
 }
 
 }  // namespace picgb

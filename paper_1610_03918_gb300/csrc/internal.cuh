@@ -452,6 +452,26 @@ bool conv3x3_tc_supported(int cin, int cout, int in_cs, int in_off, int out_cs, 
 cudaError_t conv3x3_tc(const ConvTC &c, cudaStream_t s);
 // sets the kernels' shared-memory attributes (before any stream capture)
 cudaError_t conv3x3_tc_prepare();
+// data gradient of the 2x2 stride-2 transposed convolution on the tensor
+// cores: in = its output gradient [B][2H][2W][in_cs] (channels in_off ..
+// in_off + cin), w = BF16 [4 cout][cin] (row (2a + c) cout + ci: the master
+// weights' own order), out = the gradient at its input [B][H][W] (cout
+// channels from out_off in rows of out_cs)
+cudaError_t conv_upback_tc(const ConvTC &c, cudaStream_t s);
+// weight gradient of a 3x3 convolution on the tensor cores:
+// dw[co][3 dy + dx][ci] += sum over pixels p of dpre[p][co] in[p + (dy - 1, dx - 1)][in_off + ci]
+// (zero padding); dpre [B][H][W][cout] contiguous, in [B][H][W][in_cs]; FP32
+// atomic adds.  cout 32 or a multiple of 64, cin 16, 32 or a multiple of 64,
+// dw 16-byte aligned.
+struct WgradTC {
+  const __nv_bfloat16 *dpre, *in;
+  int in_cs, in_off, cin, cout;
+  float *dw;
+  int B, H, W;
+  int *err;                   // device error word (a bounded wait gave up)
+};
+bool conv_wgrad_tc_supported(int cin, int cout, int in_cs, int in_off, const float *dw);
+cudaError_t conv_wgrad_tc(const WgradTC &g, cudaStream_t s);
 // the network's first 3x3 convolution (2 FP32 input channels per pixel ->
 // 32 BF16 outputs [p][32]) on the tensor cores; w: BF16 [32][9][wcin]
 cudaError_t conv_in_tc(const float2 *x, const __nv_bfloat16 *w, int wcin, const float *bias,

@@ -278,30 +278,55 @@ __global__ void __launch_bounds__(128) k_wgrad3x3(WgradArgs a) {
   for (long long i = blockIdx.x * (long long)blockDim.x + threadIdx.x; i < (n); i += (long long)gridDim.x * blockDim.x)
 
 
-// dpre[p][c] = g[p][c] * (y[p][c] > 0) (contiguous output)
-__global__ void k_relu_mask(const bf16 *g, int g_cs, int g_off, const bf16 *y, int y_cs, int y_off,
-                            bf16 *dpre, int C, long long npix) {
-  GSTRIDE(i, npix * C) {
-    const long long p = i / C;
-    const int c = int(i - p * C);
-    const float yv = __bfloat162float(y[p * y_cs + y_off + c]);
-    dpre[i] = yv > 0.f ? g[p * g_cs + g_off + c] : __float2bfloat16(0.f);
+// backward through the ReLU, with the bias gradient: dpre[p][c] = g[p][c] where
+// y[p][c] > 0, else 0, and db[c] += sum_p dpre[p][c].  With POOL, g first gains
+// the average pool's gradient 0.25 gp[parent of p][c] (gp [B][H/2][W/2][C]),
+// rounded to BF16 as a stored sum would be.  Each thread moves 8 channels (16
+// bytes) of a pixel and keeps one channel group for the whole grid-stride loop,
+// so its 8 bias sums are reduced once per block.  C, channel strides and
+// offsets multiples of 8.
+template <bool POOL>
+__global__ void __launch_bounds__(256) k_relu_back(const bf16 *g, int g_cs, int g_off, const bf16 *y, int y_cs,
+                                                   int y_off, const bf16 *gp, int H, int W, bf16 *dpre, int C,
+                                                   long long npix, float *db) {
+  const int G = C >> 3, grp = threadIdx.x % G, ppb = blockDim.x / G;
+  float s[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s[k] = 0.f;
+  for (long long p = blockIdx.x * (long long)ppb + threadIdx.x / G; p < npix; p += (long long)gridDim.x * ppb) {
+    uint4 gv = *reinterpret_cast<const uint4 *>(g + p * g_cs + g_off + 8 * grp);
+    const uint4 yv = *reinterpret_cast<const uint4 *>(y + p * y_cs + y_off + 8 * grp);
+    bf16 *gg = reinterpret_cast<bf16 *>(&gv);
+    const bf16 *yy = reinterpret_cast<const bf16 *>(&yv);
+    if (POOL) {
+      const int w = int(p % W);
+      const long long r = p / W;   // b H + h
+      const int h = int(r % H);
+      const long long b = r / H;
+      const uint4 pv =
+          *reinterpret_cast<const uint4 *>(gp + ((b * (H / 2) + h / 2) * (W / 2) + w / 2) * C + 8 * grp);
+      const bf16 *pp = reinterpret_cast<const bf16 *>(&pv);
+#pragma unroll
+      for (int k = 0; k < 8; ++k) gg[k] = __float2bfloat16(__bfloat162float(gg[k]) + 0.25f * __bfloat162float(pp[k]));
+    }
+    uint4 ov;
+    bf16 *oo = reinterpret_cast<bf16 *>(&ov);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      oo[k] = __bfloat162float(yy[k]) > 0.f ? gg[k] : __float2bfloat16(0.f);
+      s[k] += __bfloat162float(oo[k]);
+    }
+    *reinterpret_cast<uint4 *>(dpre + p * C + 8 * grp) = ov;
   }
-}
-
-// db[c] += sum_p dpre[p][c]
-__global__ void k_bias_grad(const bf16 *dpre, int C, long long npix, float *db) {
-  const int c = blockIdx.y;
-  float s = 0.f;
-  GSTRIDE(p, npix) s += __bfloat162float(dpre[p * C + c]);
-  for (int o = 16; o > 0; o >>= 1) s += __shfl_down_sync(0xffffffffu, s, o);
-  __shared__ float sh[32];
-  if ((threadIdx.x & 31) == 0) sh[threadIdx.x >> 5] = s;
+  __shared__ float red[8][256];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = s[k];
   __syncthreads();
-  if (threadIdx.x == 0) {
+  if (int(threadIdx.x) < C) {
+    const int q = threadIdx.x >> 3, k = threadIdx.x & 7;
     float t = 0.f;
-    for (int k = 0; k < int(blockDim.x >> 5); ++k) t += sh[k];
-    atomicAdd(&db[c], t);
+    for (int j = q; j < int(blockDim.x); j += G) t += red[k][j];
+    atomicAdd(&db[threadIdx.x], t);
   }
 }
 
@@ -315,19 +340,6 @@ __global__ void k_wflip(const bf16 *w, bf16 *wt, int cout, int cin) {
   }
 }
 
-
-// gradient of the pool, added into g (H x W, channel stride/offset)
-__global__ void k_pool_back_add(const bf16 *gp, bf16 *g, int g_cs, int g_off, int C, int B, int H, int W) {
-  const int Ho = H / 2, Wo = W / 2;
-  GSTRIDE(i, (long long)B * H * W * C) {
-    const int c = int(i % C);
-    const long long p = i / C;
-    const int w = int(p % W), h = int((p / W) % H), b = int(p / ((long long)W * H));
-    const float v = 0.25f * __bfloat162float(gp[((size_t(b) * Ho + h / 2) * Wo + w / 2) * C + c]);
-    bf16 *d = g + p * g_cs + g_off + c;
-    *d = __float2bfloat16(__bfloat162float(*d) + v);
-  }
-}
 
 // transposed 2x2 stride-2 convolution: out (2h x 2w) from in (h x w); W [2][2][ci][co] FP32
 __global__ void k_up_fwd(const bf16 *in, int cin, const float *w, const float *bias, bf16 *out,
@@ -505,6 +517,10 @@ __global__ void k_upw_to_bf16(const float *w, bf16 *wt, int cin, int cout) {
 }
 
 // network input: 2 channels padded to 16 with zeros, one 32-byte row per pixel
+__global__ void k_to_bf16(const float *a, bf16 *b, long long n) {
+  GSTRIDE(i, n) b[i] = __float2bfloat16(a[i]);
+}
+
 __global__ void k_input_vec(const float2 *x, uint4 *out, long long npix) {
   GSTRIDE(p, npix) {
     const float2 v = x[p];
@@ -641,6 +657,7 @@ struct pic_unet {
     int cin, cout;
     long long w_off, b_off;
     picgb::unet::bf16 *wt;               // BF16 [4 cout][cin], row (2a + c) cout + co (tensor cores)
+    picgb::unet::bf16 *wb;               // BF16 [4 cin][cout], the master order (data gradient)
   } up[3];                               // up2, up1, up0 (index = level)
   long long head_w, head_b;
   // activations (BF16 NHWC) and gradients
@@ -749,45 +766,73 @@ void conv_back_data(pic_unet *u, int ci, const bf16 *dpre, bf16 *gin, int gin_cs
   }
 }
 
-void conv_back_weights(pic_unet *u, int ci, const bf16 *dpre, const bf16 *in, int in_cs, int in_off, int l) {
-  const pic_unet::Conv &c = u->conv[ci];
-  const int H = u->H >> l, W = u->W >> l;
-  float *dw = (c.cin_c == c.cin_m) ? u->G + c.w_off : u->g0tmp;
-  if (c.cin_c != c.cin_m) cudaMemsetAsync(u->g0tmp, 0, size_t(c.cout) * 9 * c.cin_c * 4, u->stream);
+// the weight gradient on the mma.sync kernel (FP32 atomics over row groups)
+void wgrad_mma(int B, int H, int W, int cin, int cout, const bf16 *dpre, const bf16 *in, int in_cs, int in_off,
+               float *dw, cudaStream_t s) {
   WgradArgs a;
   a.dpre = dpre;
   a.in = in;
   a.in_cs = in_cs;
   a.in_off = in_off;
-  a.cin = c.cin_c;
-  a.cout = c.cout;
+  a.cin = cin;
+  a.cout = cout;
   a.dw = dw;
-  a.B = u->B;
+  a.B = B;
   a.H = H;
   a.W = W;
-  const int rows = u->B * H;
+  const int rows = B * H;
   // enough CTAs to fill the GPU: rows split so that every (co, ci, tap) tile has work
-  const int tiles = ((c.cout + 31) / 32) * ((c.cin_c + 31) / 32) * 9;
+  const int tiles = ((cout + 31) / 32) * ((cin + 31) / 32) * 9;
   int groups = std::max(1, std::min(rows, 4096 / tiles));
   a.rows_per_cta = (rows + groups - 1) / groups;
   groups = (rows + a.rows_per_cta - 1) / a.rows_per_cta;
-  k_wgrad3x3<<<dim3(groups, ((c.cout + 31) / 32) * ((c.cin_c + 31) / 32), 9), 128, 0, u->stream>>>(a);
+  k_wgrad3x3<<<dim3(groups, ((cout + 31) / 32) * ((cin + 31) / 32), 9), 128, 0, s>>>(a);
+}
+
+void conv_back_weights(pic_unet *u, int ci, const bf16 *dpre, const bf16 *in, int in_cs, int in_off, int l) {
+  const pic_unet::Conv &c = u->conv[ci];
+  const int H = u->H >> l, W = u->W >> l;
+  float *dw = (c.cin_c == c.cin_m) ? u->G + c.w_off : u->g0tmp;
+  if (c.cin_c != c.cin_m) cudaMemsetAsync(u->g0tmp, 0, size_t(c.cout) * 9 * c.cin_c * 4, u->stream);
+  bool done = false;
+  if (u->conv_impl == 0) {
+    WgradTC g;
+    g.dpre = dpre;
+    g.in = in;
+    g.in_cs = in_cs;
+    g.in_off = in_off;
+    g.cin = c.cin_c;
+    g.cout = c.cout;
+    g.dw = dw;
+    g.B = u->B;
+    g.H = H;
+    g.W = W;
+    g.err = u->d_err;
+    done = conv_wgrad_tc(g, u->stream) == cudaSuccess;
+  }
+  if (!done) wgrad_mma(u->B, H, W, c.cin_c, c.cout, dpre, in, in_cs, in_off, dw, u->stream);
   if (c.cin_c != c.cin_m)
     k_w_fold<<<gridn((long long)c.cout * 9 * c.cin_m), 256, 0, u->stream>>>(u->g0tmp, u->G + c.w_off,
                                                                           c.cout, c.cin_m, c.cin_c);
-  k_bias_grad<<<dim3(std::min(256, gridn(pix(u, l))), c.cout), 256, 0, u->stream>>>(
-      dpre, c.cout, pix(u, l), u->G + c.b_off);
 }
 
 // backward through relu(conv(in)) given the gradient g at its output;
 // writes the gradient at its input into gin (unless gin is null)
+// gp: the gradient of the average pool that follows y's block (added to g), or null
 void conv_block_back(pic_unet *u, int ci, const bf16 *g, int g_cs, int g_off, const bf16 *y, int y_cs,
                      int y_off, const bf16 *in, int in_cs, int in_off, bf16 *gin, int gin_cs,
-                     int gin_off, int l) {
+                     int gin_off, int l, const bf16 *gp = nullptr) {
   const pic_unet::Conv &c = u->conv[ci];
   const long long np = pix(u, l);
   bf16 *dpre = u->dpre[l];
-  k_relu_mask<<<gridn(np * c.cout), 256, 0, u->stream>>>(g, g_cs, g_off, y, y_cs, y_off, dpre, c.cout, np);
+  const long long ppb = 256 / (c.cout / 8);
+  const int grid = int(std::min<long long>((np + ppb - 1) / ppb, 8LL * u->num_sms));
+  if (gp)
+    k_relu_back<true><<<grid, 256, 0, u->stream>>>(g, g_cs, g_off, y, y_cs, y_off, gp, u->H >> l, u->W >> l,
+                                                   dpre, c.cout, np, u->G + c.b_off);
+  else
+    k_relu_back<false><<<grid, 256, 0, u->stream>>>(g, g_cs, g_off, y, y_cs, y_off, nullptr, 1, 1, dpre,
+                                                    c.cout, np, u->G + c.b_off);
   conv_back_weights(u, ci, dpre, in, in_cs, in_off, l);
   if (gin) conv_back_data(u, ci, dpre, gin, gin_cs, gin_off, l);
 }
@@ -796,9 +841,37 @@ void weights_to_bf16(pic_unet *u) {
   for (auto &c : u->conv)
     k_w_to_bf16<<<gridn((long long)c.cout * 9 * c.cin_c), 256, 0, u->stream>>>(u->P + c.w_off, c.w, c.cout,
                                                                              c.cin_m, c.cin_c);
-  for (auto &up : u->up)
+  for (auto &up : u->up) {
     k_upw_to_bf16<<<gridn(4LL * up.cout * up.cin), 256, 0, u->stream>>>(u->P + up.w_off, up.wt, up.cin,
                                                                           up.cout);
+    k_to_bf16<<<gridn(4LL * up.cout * up.cin), 256, 0, u->stream>>>(u->P + up.w_off, up.wb,
+                                                                      4LL * up.cout * up.cin);
+  }
+}
+
+// data gradient of the transposed convolution of level l on the tensor cores:
+// a GEMM of the output gradient's 4 children per input pixel (K = 4 x cout)
+// with the master-order weights; false where the kernel does not apply
+bool up_back_tc(pic_unet *u, int l, bf16 *gin) {
+  if (u->conv_impl != 0) return false;
+  const pic_unet::Up &up = u->up[l];
+  ConvTC c;
+  c.in = u->gcat[l];
+  c.in_cs = 2 * kC[l];
+  c.in_off = 0;
+  c.cin = up.cout;
+  c.w = up.wb;
+  c.bias = nullptr;
+  c.out = gin;
+  c.out_cs = up.cin;
+  c.out_off = 0;
+  c.cout = up.cin;
+  c.B = u->B;
+  c.H = u->H >> (l + 1);
+  c.W = u->W >> (l + 1);
+  c.relu = 0;
+  c.err = u->d_err;
+  return conv_upback_tc(c, u->stream) == cudaSuccess;
 }
 
 // the transposed convolution of level l on the tensor cores (GEMM columns in
@@ -898,8 +971,9 @@ void backward(pic_unet *u) {
     const int hl = u->H >> (l + 1), wl = u->W >> (l + 1);
     const bf16 *hin = (l == 2) ? u->b3 : u->dout[l + 1];
     bf16 *gin = (l == 2) ? u->gb3 : u->gdout[l + 1];
-    k_up_back_data<<<gridn((long long)pix(u, l + 1) * up.cin), 256, 0, u->stream>>>(
-        u->gcat[l], 2 * C, 0, up.cout, u->P + up.w_off, gin, up.cin, u->B, hl, wl);
+    if (!up_back_tc(u, l, gin))
+      k_up_back_data<<<gridn((long long)pix(u, l + 1) * up.cin), 256, 0, u->stream>>>(
+          u->gcat[l], 2 * C, 0, up.cout, u->P + up.w_off, gin, up.cin, u->B, hl, wl);
     const int rows = u->B * hl;
     const int tiles = ((up.cin + 31) / 32) * ((up.cout + 31) / 32) * 4;
     int groups = std::max(1, std::min(rows, 2048 / tiles));
@@ -912,13 +986,13 @@ void backward(pic_unet *u) {
   // bottleneck
   conv_block_back(u, E3B, u->gb3, C3, 0, u->b3, C3, 0, u->a[3], C3, 0, u->gx[3], C3, 0, 3);
   conv_block_back(u, E3A, u->gx[3], C3, 0, u->a[3], C3, 0, u->p[3], kC[2], 0, u->gp[3], kC[2], 0, 3);
-  // encoder, back down: the pooled gradient joins the skip gradient in gcat[l][C:2C]
+  // encoder, back down: the pool's gradient joins the skip gradient gcat[l][C:2C]
+  // inside the ReLU's backward
   for (int l = 2; l >= 0; --l) {
     const int C = kC[l];
-    k_pool_back_add<<<gridn((long long)pix(u, l) * C), 256, 0, u->stream>>>(
-        u->gp[l + 1], u->gcat[l], 2 * C, C, C, u->B, u->H >> l, u->W >> l);
     const int ea = 2 * l;   // E0A, E1A, E2A
-    conv_block_back(u, ea + 1, u->gcat[l], 2 * C, C, u->cat[l], 2 * C, C, u->a[l], C, 0, u->gx[l], C, 0, l);
+    conv_block_back(u, ea + 1, u->gcat[l], 2 * C, C, u->cat[l], 2 * C, C, u->a[l], C, 0, u->gx[l], C, 0, l,
+                    u->gp[l + 1]);
     if (l > 0)
       conv_block_back(u, ea, u->gx[l], C, 0, u->a[l], C, 0, u->p[l], kC[l - 1], 0, u->gp[l], kC[l - 1], 0, l);
     else
@@ -1002,7 +1076,10 @@ pic_status pic_unet_create(int32_t batch, int32_t height, int32_t width, void *s
     c.w = (bf16 *)A(size_t(c.cout) * 9 * c.cin_c * 2);
     c.wt = (bf16 *)A(size_t(c.cout) * 9 * c.cin_c * 2);
   }
-  for (auto &up : u->up) up.wt = (bf16 *)A(4 * size_t(up.cout) * up.cin * 2);
+  for (auto &up : u->up) {
+    up.wt = (bf16 *)A(4 * size_t(up.cout) * up.cin * 2);
+    up.wb = (bf16 *)A(4 * size_t(up.cout) * up.cin * 2);
+  }
   u->g0tmp = (float *)A(size_t(kC[0]) * 9 * kCin0 * 4);
   const size_t np0 = size_t(batch) * height * width;
   u->y = (float *)A(np0 * 4);
@@ -1233,6 +1310,98 @@ pic_status pic_conv3x3_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const
     return PIC_EINVAL;
   if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
   return PIC_OK;
+}
+
+pic_status pic_conv3x3_wgrad_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const void *dpre,
+                                  const void *in, int32_t in_cs, int32_t in_off, int32_t cin, int32_t cout,
+                                  float *dw, void *stream) {
+  if (!dpre || !in || !dw || B < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 || in_off < 0 ||
+      in_off + cin > in_cs || impl < 0 || impl > 1 || (long long)B * H * W >= (1LL << 31))
+    return PIC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bf16 *bd = static_cast<const bf16 *>(dpre), *bi = static_cast<const bf16 *>(in);
+  if (impl == 1) {
+    if (in_cs % 8 || in_off % 8 || cin % 8 || cout % 8) return PIC_EINVAL;   // 16-byte cp.async rows
+    wgrad_mma(B, H, W, cin, cout, bd, bi, in_cs, in_off, dw, s);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+    return PIC_OK;
+  }
+  if (!picgb::conv_wgrad_tc_supported(cin, cout, in_cs, in_off, dw)) return PIC_EINVAL;
+  int *err = nullptr;
+  if (cudaGetSymbolAddress((void **)&err, g_conv_err) != cudaSuccess) return PIC_ECUDA;
+  if (cudaMemsetAsync(err, 0, 4, s) != cudaSuccess) return PIC_ECUDA;
+  picgb::WgradTC g;
+  g.dpre = bd;
+  g.in = bi;
+  g.in_cs = in_cs;
+  g.in_off = in_off;
+  g.cin = cin;
+  g.cout = cout;
+  g.dw = dw;
+  g.B = B;
+  g.H = H;
+  g.W = W;
+  g.err = err;
+  if (picgb::conv_wgrad_tc(g, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+  int e = 0;
+  if (cudaMemcpy(&e, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
+  if (e) {
+    picgb::note(cudaErrorTimeout, ("tcgen05 weight gradient wait " + std::to_string(e)).c_str());
+    return PIC_ETIMEOUT;
+  }
+  return PIC_OK;
+}
+
+pic_status pic_upconv_back_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const void *gout,
+                                int32_t gout_cs, int32_t gout_off, int32_t cout, const float *w, void *gin,
+                                int32_t cin, void *stream) {
+  if (!gout || !w || !gin || B < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 || gout_off < 0 ||
+      gout_off + cout > gout_cs || impl < 0 || impl > 1 || (long long)B * H * W * 4 >= (1LL << 31))
+    return PIC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bf16 *bg = static_cast<const bf16 *>(gout);
+  bf16 *bin = static_cast<bf16 *>(gin);
+  if (impl == 1) {
+    k_up_back_data<<<gridn((long long)B * H * W * cin), 256, 0, s>>>(bg, gout_cs, gout_off, cout, w, bin, cin,
+                                                                    B, H, W);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+    return PIC_OK;
+  }
+  if (!picgb::conv3x3_tc_supported(cout, cin, gout_cs, gout_off, cin, 0, W)) return PIC_EINVAL;
+  int *err = nullptr;
+  if (cudaGetSymbolAddress((void **)&err, g_conv_err) != cudaSuccess) return PIC_ECUDA;
+  const long long nw = 4LL * cin * cout;
+  bf16 *wb = nullptr;
+  if (cudaMalloc(&wb, size_t(nw) * 2) != cudaSuccess) return PIC_ENOMEM;
+  picgb::ConvTC c;
+  c.in = bg;
+  c.in_cs = gout_cs;
+  c.in_off = gout_off;
+  c.cin = cout;
+  c.w = wb;
+  c.bias = nullptr;
+  c.out = bin;
+  c.out_cs = cin;
+  c.out_off = 0;
+  c.cout = cin;
+  c.B = B;
+  c.H = H;
+  c.W = W;
+  c.relu = 0;
+  c.err = err;
+  k_to_bf16<<<gridn(nw), 256, 0, s>>>(w, wb, nw);
+  pic_status st = PIC_OK;
+  if (cudaGetLastError() != cudaSuccess || cudaMemsetAsync(err, 0, 4, s) != cudaSuccess ||
+      picgb::conv_upback_tc(c, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess)
+    st = PIC_ECUDA;
+  int e = 0;
+  if (st == PIC_OK && cudaMemcpy(&e, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) st = PIC_ECUDA;
+  cudaFree(wb);
+  if (st == PIC_OK && e) {
+    picgb::note(cudaErrorTimeout, ("tcgen05 convolution wait " + std::to_string(e)).c_str());
+    st = PIC_ETIMEOUT;
+  }
+  return st;
 }
 
 pic_status pic_unet_set_conv_impl(pic_unet *u, int32_t impl) {

@@ -144,3 +144,149 @@ def test_unsupported_shapes_are_refused(lib):
     Wt = np.zeros((48, 3, 3, 16))
     _, st = run_conv(lib, 0, np.zeros((1, 8, 16, 16)), 0, 16, Wt, None, True, 48, 0)   # cout 48
     assert st == lib.PIC_EINVAL
+
+
+def run_upback(pg, impl, gout_full, gout_off, cout, Wup, cin):
+    """Data gradient of the 2x2 stride-2 transposed convolution through
+    pic_upconv_back_bf16: gout_full [B,2H,2W,gout_cs] (BF16 values), Wup
+    [2,2,cin,cout] (FP32); returns (gin [B,H,W,cin] as float64, status)."""
+    import ctypes
+    import torch
+    B, H2, W2, gout_cs = gout_full.shape
+    H, W = H2 // 2, W2 // 2
+    gd = _dev(gout_full, torch, torch.bfloat16)
+    wd = _dev(Wup, torch, torch.float32)
+    od = torch.full((B, H, W, cin), 7.0, dtype=torch.bfloat16, device="cuda")
+    lib = pg.load_library()
+    f = lib.pic_upconv_back_bf16
+    P, I = ctypes.c_void_p, ctypes.c_int32
+    f.argtypes = [I, I, I, I, P, I, I, I, P, P, I, P]
+    st = f(impl, B, H, W, gd.data_ptr(), gout_cs, gout_off, cout, wd.data_ptr(), od.data_ptr(), cin,
+           torch.cuda.current_stream().cuda_stream)
+    return od.float().cpu().numpy().astype(np.float64), st
+
+
+UP_CASES = [
+    # B, H, W (the layer's input), cin, cout, gout_cs, gout_off
+    # the finest level's shape (gradient of the 64-channel concatenation's
+    # first half), W = 20: 16-wide tiles, ragged; K = 32
+    (1, 36, 20, 64, 32, 64, 0),
+    # W = 130: 128-wide tiles, the second ragged; batch 2; K = 64
+    (2, 9, 130, 128, 64, 128, 0),
+    # the coarsest level's shape: 3 pixel tiles, the 256 columns in 4 blocks
+    (1, 5, 64, 256, 128, 256, 0),
+    # a channel slice at an offset, K = 16
+    (1, 16, 32, 32, 16, 48, 16),
+    # K = 48 (blocks of 16) from an offset slice, W = 8
+    (1, 12, 8, 64, 48, 64, 8),
+]
+
+
+@pytest.mark.parametrize("case", UP_CASES)
+@pytest.mark.parametrize("impl", [0, 1])
+def test_upconv_data_gradient_matches_oracle(lib, case, impl):
+    B, H, W, cin, cout, gout_cs, gout_off = case
+    rng = np.random.default_rng(cin * 100 + cout + W)
+    g_full = bf16_round(rng.standard_normal((B, 2 * H, 2 * W, gout_cs)))
+    Wup = bf16_round(rng.standard_normal((2, 2, cin, cout)) / np.sqrt(cin))
+    got, st = run_upback(lib, impl, g_full, gout_off, cout, Wup, cin)
+    assert st == lib.PIC_OK, lib.pic_strerror(st)
+    x0 = np.zeros((B, H, W, cin))
+    ref, _, _ = ounet.upconv2x2_backward(x0, Wup, g_full[..., gout_off:gout_off + cout])
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    cos = float((got * ref).sum() / (np.linalg.norm(got) * np.linalg.norm(ref)))
+    assert rel <= 4e-3 and cos >= 0.99999, (rel, cos)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-3 * np.abs(ref).max())
+
+
+def test_upconv_data_gradient_refuses_unsupported_shapes(lib):
+    g = np.zeros((1, 16, 16, 64))
+    _, st = run_upback(lib, 0, g, 0, 64, np.zeros((2, 2, 48, 64)), 48)     # 48 output channels
+    assert st == lib.PIC_EINVAL
+    _, st = run_upback(lib, 0, g, 4, 32, np.zeros((2, 2, 64, 32)), 64)     # offset not a multiple of 8
+    assert st == lib.PIC_EINVAL
+    _, st = run_upback(lib, 0, np.zeros((1, 8, 8, 64)), 0, 64, np.zeros((2, 2, 64, 64)), 64)   # W = 4
+    assert st == lib.PIC_EINVAL
+
+
+def run_wgrad(pg, impl, dpre, x_full, in_off, cin, prefill=0.0):
+    """Weight gradient of a 3x3 convolution through pic_conv3x3_wgrad_bf16:
+    dpre [B,H,W,cout], x_full [B,H,W,in_cs] (BF16 values); returns (dW
+    [cout,3,3,cin] as float64 after adding into `prefill`, status)."""
+    import ctypes
+    import torch
+    B, H, W, in_cs = x_full.shape
+    cout = dpre.shape[3]
+    dd = _dev(dpre, torch, torch.bfloat16)
+    xd = _dev(x_full, torch, torch.bfloat16)
+    wd = torch.full((cout, 9, cin), prefill, dtype=torch.float32, device="cuda")
+    lib = pg.load_library()
+    f = lib.pic_conv3x3_wgrad_bf16
+    P, I = ctypes.c_void_p, ctypes.c_int32
+    f.argtypes = [I, I, I, I, P, P, I, I, I, I, P, P]
+    st = f(impl, B, H, W, dd.data_ptr(), xd.data_ptr(), in_cs, in_off, cin, cout, wd.data_ptr(),
+           torch.cuda.current_stream().cuda_stream)
+    return wd.cpu().numpy().astype(np.float64).reshape(cout, 3, 3, cin), st
+
+
+WG_CASES = [
+    # B, H, W, cin, cout, in_cs, in_off
+    # the first layer's padded input (16 channels), 4 chunks of 64 pixels
+    (1, 40, 256, 16, 32, 16, 0),
+    # batch 2 (taps across the images' edge rows), W = 72 (second chunk 8
+    # pixels), the skip half of a concatenation as input
+    (2, 33, 72, 32, 32, 64, 32),
+    # W = 24 < 64, 64 x 64 from an offset slice
+    (1, 18, 24, 64, 64, 128, 64),
+    # 4 x 2 channel blocks of 64
+    (1, 17, 40, 256, 128, 256, 0),
+    # 256 outputs (4 blocks), 2 input blocks
+    (1, 9, 32, 128, 256, 128, 0),
+    # 64 outputs from 32 inputs, W = 130 (3 chunks, the last 2 pixels)
+    (1, 6, 130, 32, 64, 32, 0),
+    # 32 outputs from 64 inputs
+    (1, 5, 64, 64, 32, 64, 0),
+]
+
+
+@pytest.mark.parametrize("case", WG_CASES)
+@pytest.mark.parametrize("impl", [0, 1])
+def test_conv3x3_weight_gradient_matches_oracle(lib, case, impl):
+    # BF16 x BF16 products are exact in FP32; only the FP32 sum over the
+    # pixels (in the tensor core's and the atomics' order) separates the two
+    # sides, far below the 1e-3 bound, while a wrong tap, shift or operand
+    # moves whole rows of dW by O(1)
+    B, H, W, cin, cout, in_cs, in_off = case
+    rng = np.random.default_rng(cin * 7 + cout * 3 + W)
+    x_full = bf16_round(rng.standard_normal((B, H, W, in_cs)))
+    dpre = bf16_round(rng.standard_normal((B, H, W, cout)))
+    got, st = run_wgrad(lib, impl, dpre, x_full, in_off, cin)
+    assert st == lib.PIC_OK, lib.pic_strerror(st)
+    _, ref, _ = ounet.conv3x3_backward(x_full[..., in_off:in_off + cin], np.zeros((cout, 3, 3, cin)), dpre)
+    scale = np.abs(ref).max()
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    assert rel <= 1e-4, rel
+    assert np.all(np.abs(got - ref) <= 1e-3 * scale), np.abs(got - ref).max() / scale
+
+
+def test_conv3x3_weight_gradient_adds_into_dw(lib):
+    B, H, W, cin, cout = 1, 8, 16, 32, 32
+    rng = np.random.default_rng(4)
+    x = bf16_round(rng.standard_normal((B, H, W, cin)))
+    d = bf16_round(rng.standard_normal((B, H, W, cout)))
+    a, st = run_wgrad(lib, 0, d, x, 0, cin, prefill=0.0)
+    assert st == lib.PIC_OK
+    b, st = run_wgrad(lib, 0, d, x, 0, cin, prefill=1.5)
+    assert st == lib.PIC_OK
+    assert np.allclose(b - 1.5, a, rtol=0, atol=1e-5 * np.abs(a).max())
+
+
+def test_conv3x3_weight_gradient_refuses_unsupported_shapes(lib):
+    x = np.zeros((1, 8, 16, 48))
+    d = np.zeros((1, 8, 16, 32))
+    _, st = run_wgrad(lib, 0, d, x, 0, 48)                               # cin 48
+    assert st == lib.PIC_EINVAL
+    _, st = run_wgrad(lib, 0, np.zeros((1, 8, 16, 96)), x[..., :32], 0, 32)   # cout 96
+    assert st == lib.PIC_EINVAL
+    _, st = run_wgrad(lib, 0, d, x, 4, 32)                               # offset not a multiple of 8
+    assert st == lib.PIC_EINVAL

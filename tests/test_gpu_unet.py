@@ -126,3 +126,39 @@ def test_unet_forward_every_layer_on_tensor_cores():
     for y in ys:
         assert np.linalg.norm(y - yo) / np.linalg.norm(yo) < 1e-2
     assert np.linalg.norm(ys[0] - ys[1]) / np.linalg.norm(ys[1]) < 1e-2
+
+
+def test_unet_gradients_every_level_on_tensor_cores():
+    # 72 x 80: every level is at least 8 wide and none a whole number of
+    # tiles, so every 3x3 convolution, its data gradient and the transposed
+    # convolutions' data gradients (36 x 40, 18 x 20, 9 x 10 inputs) run on
+    # tcgen05 with ragged tiles; against the BF16-emulating oracle, with the
+    # bounds of the smaller network above, and against the mma.sync network
+    import torch
+    import paper_1610_03918_gb300 as pg
+    rng = np.random.default_rng(11)
+    p = ounet.init_params(9)
+    for n in p:
+        p[n] = bf16_round(p[n]) if not n.endswith(".b") else rng.standard_normal(p[n].shape) * 0.05
+    B, H, W = 1, 72, 80
+    x = bf16_round(rng.standard_normal((B, H, W, 2)))
+    t = rng.standard_normal((B, H, W))
+    xd = torch.tensor(x, dtype=torch.float32, device="cuda")
+    td = torch.tensor(t, dtype=torch.float32, device="cuda")
+    out = []
+    for impl in (0, 1):
+        net = pg.Unet(B, H, W)
+        net.set_conv_impl(impl)
+        net.set_params(ounet.flat(p).astype(np.float32))
+        out.append(net.gradients(xd, td))
+        assert net.status() == pg.PIC_OK
+        net.close()
+    lo, go = ounet.loss_and_grads(p, x, t, q=bf16_round)
+    for loss, g in out:
+        assert loss == pytest.approx(lo, rel=1e-3)
+        for name, (rel, cos) in _compare(g, go).items():
+            assert rel < 0.15 and cos > 0.995, (name, rel, cos)
+    G0, G1 = ounet.unflat(out[0][1].astype(np.float64)), ounet.unflat(out[1][1].astype(np.float64))
+    for name in ("up0.W", "up1.W", "up2.W", "enc1a.W", "enc2a.W", "enc3a.W"):
+        a, b = G0[name].ravel(), G1[name].ravel()
+        assert np.linalg.norm(a - b) / np.linalg.norm(b) < 0.15, name
