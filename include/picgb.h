@@ -452,6 +452,21 @@ pic_status pic_conv3x3_wgrad_bf16(int32_t impl, int32_t B, int32_t H, int32_t W,
                                   const void *in, int32_t in_cs, int32_t in_off, int32_t cin, int32_t cout,
                                   float *dw, void *stream);
 
+/* The weight and bias gradients of the U-Net's 2x2 stride-2 transposed
+ * convolution: dw[a][c][ci][co] += sum_{b, y, x} in[b][y][x][ci] *
+ *   gout[b][2y + a][2x + c][gout_off + co], db[co] += sum over all gout
+ * pixels of gout[..][gout_off + co].  in: DEVICE BF16 [B][H][W][cin]
+ * (contiguous); gout: DEVICE BF16 NHWC [B][2H][2W] with channel stride
+ * gout_cs; dw: DEVICE FP32 [2][2][cin][cout], db: DEVICE FP32 [cout], both
+ * ADDED to.  impl 0: tcgen05 tensor cores and a vector column sum (cin a
+ * multiple of 64, cout 32, 64, 128 or 256, gout_cs and gout_off multiples
+ * of 8, else PIC_EINVAL); impl 1: CUDA cores.  FP32 sums with atomic adds
+ * (their order varies from run to run).  Synchronous on `stream`;
+ * PIC_ETIMEOUT if a bounded wait of the tensor-core kernel gave up. */
+pic_status pic_upconv_wgrad_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const void *in, int32_t cin,
+                                 const void *gout, int32_t gout_cs, int32_t gout_off, int32_t cout, float *dw,
+                                 float *db, void *stream);
+
 /* The data gradient of the U-Net's 2x2 stride-2 transposed convolution (the
  * input-side gradient of its upsampling layer):
  * gin[b][y][x][n] = sum_{a, c in {0, 1}} sum_{k < cout}

@@ -503,9 +503,15 @@ __global__ void __launch_bounds__(kThreads, 1)
 // D row (s, co), column (dx, ci) thus accumulates dW[co][3 s + dx][ci] over
 // the CTA's K blocks; the epilogue adds it to dW with vector atomics (FP32,
 // so the sum order, not the terms, depends on the grid).
+// UPW: the weight gradient of the 2x2 stride-2 transposed convolution,
+// dW[a][c][ci][co] = sum over input pixels p of in[p][ci] g[child (a, c) of p][co],
+// g its output gradient.  The four slots of A are the four children's tiles
+// of g (5-D boxes {CO, 1, 64, 1, 1} of g viewed as {channels, c, x, a, rows}),
+// B is the input row without a shift (N = CI), and D row (t, co), column ci
+// holds dW[t][ci][co].
 constexpr int kWKP = 64;   // pixels per K block
 
-template <int CO, int CI, int STAGES>
+template <int CO, int CI, int STAGES, bool UPW = false>
 struct WLayout {
   static constexpr int KPB = kWKP + 16;   // the input row with 8-pixel margins
   static constexpr uint32_t SLOT = kWKP * CO * 2;
@@ -520,7 +526,7 @@ struct WLayout {
   static constexpr uint32_t TAIL = 6 * CI * CI + 112 * CI;
   static constexpr uint32_t BYTES = BAR_OFF + (2 * STAGES + 1) * 8 + 16 + TAIL + 1024;
   static constexpr int NM = CO == 32 ? 1 : 2;   // MMAs along M per 16 pixels
-  static constexpr int N = 3 * CI;
+  static constexpr int N = UPW ? CI : 3 * CI;
   static constexpr uint32_t NCOLS = NM * N <= 32 ? 32 : NM * N <= 64 ? 64 : NM * N <= 128 ? 128 : NM * N <= 256 ? 256 : 512;
 };
 
@@ -539,17 +545,17 @@ __host__ __device__ constexpr uint32_t instr_desc_mn() {
 }
 
 struct WArgs {
-  float *dw;           // [cout][9][cin]
-  int cin, cout, in_off, H, nwc;
+  float *dw;           // [cout][9][cin]; UPW: [4][cin][cout]
+  int cin, cout, in_off, a_off, H, nwc;
   long long nkb;       // K blocks: B H rows x nwc pixel chunks
   long long per_cta;   // K blocks per CTA along the grid's first index
   int *err;
 };
 
-template <int CO, int CI, int STAGES>
+template <int CO, int CI, int STAGES, bool UPW = false>
 __global__ void __launch_bounds__(kThreads, 1)
     k_wgrad_tc(const __grid_constant__ CUtensorMap tmA, const __grid_constant__ CUtensorMap tmB, WArgs a) {
-  using L = WLayout<CO, CI, STAGES>;
+  using L = WLayout<CO, CI, STAGES, UPW>;
   extern __shared__ uint8_t smem_raw[];
   uint8_t *smem = reinterpret_cast<uint8_t *>((reinterpret_cast<uintptr_t>(smem_raw) + 1023) & ~uintptr_t(1023));
   const uint32_t s0 = saddr(smem);
@@ -566,10 +572,12 @@ __global__ void __launch_bounds__(kThreads, 1)
 
   // the fourth A slot of every stage holds zeros (the MMA's rows 96..127 for
   // CO = 32, 64..127 of the second MMA for CO = 64; discarded)
-  for (int st = 0; st < STAGES; ++st)
-    for (uint32_t o = 16 * tid; o < L::SLOT; o += 16 * kThreads)
-      *reinterpret_cast<uint4 *>(smem + st * L::STAGE + 3 * L::SLOT + o) = make_uint4(0, 0, 0, 0);
-  fence_async_smem();
+  if (!UPW) {
+    for (int st = 0; st < STAGES; ++st)
+      for (uint32_t o = 16 * tid; o < L::SLOT; o += 16 * kThreads)
+        *reinterpret_cast<uint4 *>(smem + st * L::STAGE + 3 * L::SLOT + o) = make_uint4(0, 0, 0, 0);
+    fence_async_smem();
+  }
   if (tid == 0) {
     for (int s = 0; s < STAGES; ++s) {
       mbar_init(bar0 + 8 * s, 1);
@@ -600,9 +608,14 @@ __global__ void __launch_bounds__(kThreads, 1)
       const int w0 = int(g - r * a.nwc) * kWKP;
       const int b = int(r / a.H), hq = int(r - (long long)b * a.H);
       const uint32_t st = s0 + s * L::STAGE;
-      mbar_expect_tx(bar0 + 8 * s, 3 * L::SLOT + L::B_TX);
-      for (int sl = 0; sl < 3; ++sl)
-        tma_load_4d(st + sl * L::SLOT, &tmA, co0, w0, hq + 1 - sl, b, bar0 + 8 * s);
+      mbar_expect_tx(bar0 + 8 * s, (UPW ? 4 : 3) * L::SLOT + L::B_TX);
+      if (UPW) {
+        for (int t = 0; t < 4; ++t)
+          tma_load_5d(st + t * L::SLOT, &tmA, a.a_off + co0, t & 1, w0, t >> 1, int(r), bar0 + 8 * s);
+      } else {
+        for (int sl = 0; sl < 3; ++sl)
+          tma_load_4d(st + sl * L::SLOT, &tmA, co0, w0, hq + 1 - sl, b, bar0 + 8 * s);
+      }
       tma_load_4d(st + L::A_BYTES, &tmB, a.in_off + ci0, w0 - 8, hq, b, bar0 + 8 * s);
     }
   } else if (tid == 32) {
@@ -620,7 +633,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
       for (int k = 0; k < kWKP / 16; ++k) {
         // input rows 7 + 16 k ..: pixel w0 - 1 + 16 k on, the tap dx = 0 chunk
-        const uint64_t db = mn_desc<CI>(st + L::A_BYTES + (7 + 16 * k) * (CI * 2), CI * 2);
+        // (UPW: rows 8 + 16 k .., pixel w0 + 16 k on)
+        const uint64_t db = mn_desc<CI>(st + L::A_BYTES + ((UPW ? 8 : 7) + 16 * k) * (CI * 2), CI * 2);
 #pragma unroll
         for (int m = 0; m < L::NM; ++m) {
           const uint64_t da = mn_desc<CO>(st + 2 * m * L::SLOT + 16 * k * (CO * 2), L::SLOT);
@@ -640,15 +654,22 @@ __global__ void __launch_bounds__(kThreads, 1)
 #pragma unroll
   for (int m = 0; m < L::NM; ++m) {
     const int row = 32 * warp + lane;                       // D row of MMA m
-    const int sl = CO == 32 ? warp : 2 * m + (row >> 6);    // A slot = vertical tap
+    const int sl = CO == 32 ? warp : 2 * m + (row >> 6);    // A slot: vertical tap (UPW: child)
     const int co = co0 + (CO == 32 ? lane : (row & 63));
-    if (sl == 3) continue;                                  // warp-uniform: the zero slot
+    if (!UPW && sl == 3) continue;                          // warp-uniform: the zero slot
     const uint32_t tl = tmem + (uint32_t(32 * warp) << 16) + m * L::N;
 #pragma unroll 1
     for (int n0 = 0; n0 < L::N; n0 += 16) {
       uint32_t v[16];
       tmem_ld16(tl + n0, v);
-      if (ok && !s_fail) {
+      if (UPW) {
+        // consecutive lanes: consecutive co of one (t, ci) row of dW
+        if (ok && !s_fail) {
+          float *dst = a.dw + (size_t(sl) * a.cin + ci0 + n0) * a.cout + co;
+#pragma unroll
+          for (int q = 0; q < 16; ++q) atomicAdd(dst + size_t(q) * a.cout, __uint_as_float(v[q]));
+        }
+      } else if (ok && !s_fail) {
         const int dx = n0 / CI, ci = ci0 + (n0 - dx * CI);
         float4 *dst = reinterpret_cast<float4 *>(a.dw + (size_t(co) * 9 + 3 * sl + dx) * a.cin + ci);
 #pragma unroll
@@ -900,11 +921,24 @@ cudaError_t launch_upb_n(const ConvTC &c, cudaStream_t s, int nblk) {
 }
 
 constexpr int kWStages = 3;
-template <int CO, int CI>
+template <int CO, int CI, bool UPW = false>
 cudaError_t prepare_wgrad() {
-  static cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<CO, CI, kWStages>, cudaFuncAttributeMaxDynamicSharedMemorySize,
-                                              int(WLayout<CO, CI, kWStages>::BYTES));
+  static cudaError_t e = cudaFuncSetAttribute(k_wgrad_tc<CO, CI, kWStages, UPW>,
+                                              cudaFuncAttributeMaxDynamicSharedMemorySize,
+                                              int(WLayout<CO, CI, kWStages, UPW>::BYTES));
   return e;
+}
+
+// CTAs of one wave over yb (co, ci) blocks, each a run of K blocks (at least one)
+template <class L>
+long long wgrad_split(WArgs &a, int sms, int yb) {
+  const int res_smem = int((227u * 1024u) / L::BYTES), res_tmem = int(512u / L::NCOLS);
+  const int res = res_smem < res_tmem ? (res_smem > 0 ? res_smem : 1) : res_tmem;
+  long long splits = ((long long)sms * res + yb - 1) / yb;
+  if (splits > a.nkb) splits = a.nkb;
+  if (splits < 1) splits = 1;
+  a.per_cta = (a.nkb + splits - 1) / splits;
+  return (a.nkb + a.per_cta - 1) / a.per_cta;
 }
 
 template <int CO, int CI>
@@ -939,6 +973,7 @@ cudaError_t launch_wgrad(const WgradTC &g, cudaStream_t s, int sms) {
   a.cin = g.cin;
   a.cout = g.cout;
   a.in_off = g.in_off;
+  a.a_off = 0;
   a.H = g.H;
   a.nwc = (g.W + kWKP - 1) / kWKP;
   a.nkb = (long long)g.B * g.H * a.nwc;
@@ -946,14 +981,53 @@ cudaError_t launch_wgrad(const WgradTC &g, cudaStream_t s, int sms) {
   // one wave: the CTAs that fit on the SMs at once (shared memory, TMEM
   // columns), shared out over the (co, ci) blocks, each a run of K blocks
   const int yb = (g.cout / CO) * (g.cin / CI);
-  const int res_smem = int((227u * 1024u) / L::BYTES), res_tmem = int(512u / L::NCOLS);
-  const int res = res_smem < res_tmem ? (res_smem > 0 ? res_smem : 1) : res_tmem;
-  long long splits = ((long long)sms * res + yb - 1) / yb;
-  if (splits > a.nkb) splits = a.nkb;
-  if (splits < 1) splits = 1;
-  a.per_cta = (a.nkb + splits - 1) / splits;
-  splits = (a.nkb + a.per_cta - 1) / a.per_cta;
+  const long long splits = wgrad_split<L>(a, sms, yb);
   k_wgrad_tc<CO, CI, kWStages><<<dim3(unsigned(splits), unsigned(yb)), kThreads, L::BYTES, s>>>(ta, tb, a);
+  return cudaGetLastError();
+}
+
+template <int CO>
+cudaError_t launch_upw(const UpWgradTC &g, cudaStream_t s, int sms) {
+  constexpr int CI = 64;
+  using L = WLayout<CO, CI, kWStages, true>;
+  auto fn = encode_fn();
+  if (!fn) return cudaErrorNotSupported;
+  const cudaError_t attr = prepare_wgrad<CO, CI, true>();
+  if (attr != cudaSuccess) return attr;
+  const cuuint64_t e = 2;
+  const cuuint32_t one[5] = {1, 1, 1, 1, 1};
+  CUtensorMap ta, tb;
+  // the output gradient [B][2H][2W][g_cs] as {g_cs, c, x, a, B H}: child (a, c)
+  // of input pixel (y, x) is (2y + a, 2x + c); boxes {CO, 1, 64, 1, 1}
+  const cuuint64_t adim[5] = {cuuint64_t(g.g_cs), 2, cuuint64_t(g.W), 2, cuuint64_t(g.B) * g.H};
+  const cuuint64_t astr[4] = {cuuint64_t(g.g_cs) * e, cuuint64_t(g.g_cs) * e * 2, cuuint64_t(g.g_cs) * e * 2 * g.W,
+                              cuuint64_t(g.g_cs) * e * 4 * g.W};
+  const cuuint32_t abox[5] = {cuuint32_t(CO), 1, cuuint32_t(kWKP), 1, 1};
+  if (fn(&ta, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 5, const_cast<bf16 *>(g.g), adim, astr, abox, one,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(CO), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  // the input [B][H][W][cin] as {cin, W, H, B}, boxes {64, 80 pixels} from 8 before
+  const cuuint64_t bdim[4] = {cuuint64_t(g.cin), cuuint64_t(g.W), cuuint64_t(g.H), cuuint64_t(g.B)};
+  const cuuint64_t bstr[3] = {cuuint64_t(g.cin) * e, cuuint64_t(g.cin) * e * g.W, cuuint64_t(g.cin) * e * g.W * g.H};
+  const cuuint32_t bbox[4] = {cuuint32_t(CI), cuuint32_t(L::KPB), 1, 1};
+  if (fn(&tb, CU_TENSOR_MAP_DATA_TYPE_BFLOAT16, 4, const_cast<bf16 *>(g.in), bdim, bstr, bbox, one,
+         CU_TENSOR_MAP_INTERLEAVE_NONE, swizzle_of(CI), CU_TENSOR_MAP_L2_PROMOTION_L2_128B,
+         CU_TENSOR_MAP_FLOAT_OOB_FILL_NONE) != CUDA_SUCCESS)
+    return cudaErrorInvalidValue;
+  WArgs a;
+  a.dw = g.dw;
+  a.cin = g.cin;
+  a.cout = g.cout;
+  a.in_off = 0;
+  a.a_off = g.g_off;
+  a.H = g.H;
+  a.nwc = (g.W + kWKP - 1) / kWKP;
+  a.nkb = (long long)g.B * g.H * a.nwc;
+  a.err = g.err;
+  const int yb = (g.cout / CO) * (g.cin / CI);
+  const long long splits = wgrad_split<L>(a, sms, yb);
+  k_wgrad_tc<CO, CI, kWStages, true><<<dim3(unsigned(splits), unsigned(yb)), kThreads, L::BYTES, s>>>(ta, tb, a);
   return cudaGetLastError();
 }
 
@@ -972,7 +1046,8 @@ cudaError_t conv3x3_tc_prepare() {
   if (e == cudaSuccess) e = tc::prepare_n<128>();
   if (e == cudaSuccess) e = tc::prepare_n<256>();
   for (cudaError_t f : {tc::prepare_wgrad<32, 16>(), tc::prepare_wgrad<32, 32>(), tc::prepare_wgrad<32, 64>(),
-                        tc::prepare_wgrad<64, 16>(), tc::prepare_wgrad<64, 32>(), tc::prepare_wgrad<64, 64>()})
+                        tc::prepare_wgrad<64, 16>(), tc::prepare_wgrad<64, 32>(), tc::prepare_wgrad<64, 64>(),
+                        tc::prepare_wgrad<32, 64, true>(), tc::prepare_wgrad<64, 64, true>()})
     if (e == cudaSuccess) e = f;
   return e;
 }
@@ -1062,6 +1137,20 @@ cudaError_t conv_wgrad_tc(const WgradTC &g, cudaStream_t s) {
   if (ci == 16) return tc::launch_wgrad<64, 16>(g, s, sms);
   if (ci == 32) return tc::launch_wgrad<64, 32>(g, s, sms);
   return tc::launch_wgrad<64, 64>(g, s, sms);
+}
+
+bool conv_upwgrad_tc_supported(int cin, int cout, int g_cs, int g_off) {
+  return (cout == 32 || (cout >= 64 && cout % 64 == 0)) && cin >= 64 && cin % 64 == 0 && g_cs % 8 == 0 &&
+         g_off % 8 == 0 && g_off + cout <= g_cs && tc::encode_fn() != nullptr;
+}
+
+cudaError_t conv_upwgrad_tc(const UpWgradTC &g, cudaStream_t s) {
+  if (!conv_upwgrad_tc_supported(g.cin, g.cout, g.g_cs, g.g_off) || g.B < 1 || g.H < 1 || g.W < 1 ||
+      (long long)g.B * g.H >= (1LL << 31))
+    return cudaErrorNotSupported;
+  const int sms = tc::sm_count();
+  if (sms < 1) return cudaErrorInvalidValue;
+  return g.cout == 32 ? tc::launch_upw<32>(g, s, sms) : tc::launch_upw<64>(g, s, sms);
 }
 
 }  // namespace picgb

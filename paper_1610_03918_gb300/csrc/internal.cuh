@@ -472,6 +472,20 @@ struct WgradTC {
 };
 bool conv_wgrad_tc_supported(int cin, int cout, int in_cs, int in_off, const float *dw);
 cudaError_t conv_wgrad_tc(const WgradTC &g, cudaStream_t s);
+// weight gradient of the 2x2 stride-2 transposed convolution on the tensor
+// cores: dw[a][c][ci][co] += sum over input pixels (y, x) of
+// in[y][x][ci] g[2y + a][2x + c][g_off + co]; in [B][H][W][cin] contiguous,
+// g [B][2H][2W][g_cs]; FP32 atomic adds.  cin a multiple of 64, cout 32 or a
+// multiple of 64.
+struct UpWgradTC {
+  const __nv_bfloat16 *in, *g;
+  int cin, g_cs, g_off, cout;
+  float *dw;
+  int B, H, W;
+  int *err;
+};
+bool conv_upwgrad_tc_supported(int cin, int cout, int g_cs, int g_off);
+cudaError_t conv_upwgrad_tc(const UpWgradTC &g, cudaStream_t s);
 // the network's first 3x3 convolution (2 FP32 input channels per pixel ->
 // 32 BF16 outputs [p][32]) on the tensor cores; w: BF16 [32][9][wcin]
 cudaError_t conv_in_tc(const float2 *x, const __nv_bfloat16 *w, int wcin, const float *bias,

@@ -437,26 +437,76 @@ __global__ void k_mse(const float *y, const float *t, float *dy, long long n, do
 }
 
 // head backward: gh[p][c] = dy[p] w[c]; dw[c] += sum_p dy h; db += sum dy
-__global__ void k_head_back(const float *dy, const bf16 *hin, const float *w, bf16 *gh, float *dw,
-                            float *db, long long npix) {
-  float acc[kC0];
-  for (int c = 0; c < kC0; ++c) acc[c] = 0.f;
-  float bs = 0.f;
-  GSTRIDE(p, npix) {
+// backward through the 1x1 head y[p] = b + sum_c w[c] h[p][c]: gh[p][c] = dy[p] w[c],
+// dw[c] += sum_p dy[p] h[p][c], db += sum_p dy[p].  Each thread moves 8 channels
+// (16 bytes) of a pixel and keeps one channel group for the whole loop.
+__global__ void __launch_bounds__(256) k_head_back(const float *dy, const bf16 *hin, const float *w, bf16 *gh,
+                                                   float *dw, float *db, long long npix) {
+  constexpr int G = kC0 / 8, PPB = 256 / G;
+  const int grp = threadIdx.x % G;
+  float wk[8], s[8], bs = 0.f;
+#pragma unroll
+  for (int k = 0; k < 8; ++k) {
+    wk[k] = w[8 * grp + k];
+    s[k] = 0.f;
+  }
+  for (long long p = blockIdx.x * (long long)PPB + threadIdx.x / G; p < npix; p += (long long)gridDim.x * PPB) {
     const float d = dy[p];
     bs += d;
-    for (int c = 0; c < kC0; ++c) {
-      gh[p * kC0 + c] = __float2bfloat16(d * w[c]);
-      acc[c] = fmaf(d, __bfloat162float(hin[p * kC0 + c]), acc[c]);
+    const uint4 hv = *reinterpret_cast<const uint4 *>(hin + p * kC0 + 8 * grp);
+    const bf16 *hh = reinterpret_cast<const bf16 *>(&hv);
+    uint4 ov;
+    bf16 *oo = reinterpret_cast<bf16 *>(&ov);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) {
+      oo[k] = __float2bfloat16(d * wk[k]);
+      s[k] = fmaf(d, __bfloat162float(hh[k]), s[k]);
+    }
+    *reinterpret_cast<uint4 *>(gh + p * kC0 + 8 * grp) = ov;
+  }
+  __shared__ float red[9][256];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = s[k];
+  red[8][threadIdx.x] = grp == 0 ? bs : 0.f;
+  __syncthreads();
+  if (threadIdx.x <= kC0) {
+    float t = 0.f;
+    if (threadIdx.x < kC0) {
+      const int q = threadIdx.x >> 3, k = threadIdx.x & 7;
+      for (int j = q; j < 256; j += G) t += red[k][j];
+      atomicAdd(&dw[threadIdx.x], t);
+    } else {
+      for (int j = 0; j < 256; j += G) t += red[8][j];
+      atomicAdd(db, t);
     }
   }
-  for (int c = 0; c < kC0; ++c) {
-    float v = acc[c];
-    for (int o = 16; o > 0; o >>= 1) v += __shfl_down_sync(0xffffffffu, v, o);
-    if ((threadIdx.x & 31) == 0) atomicAdd(&dw[c], v);
+}
+
+// db[c] += sum_p g[p][g_off + c] (the transposed convolution's bias gradient),
+// 8 channels (16 bytes) a thread, one channel group per thread; C, g_cs and
+// g_off multiples of 8, C at most 256
+__global__ void __launch_bounds__(256) k_colsum(const bf16 *g, int g_cs, int g_off, int C, long long npix,
+                                                float *db) {
+  const int G = C >> 3, grp = threadIdx.x % G, ppb = blockDim.x / G;
+  float s[8];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) s[k] = 0.f;
+  for (long long p = blockIdx.x * (long long)ppb + threadIdx.x / G; p < npix; p += (long long)gridDim.x * ppb) {
+    const uint4 v = *reinterpret_cast<const uint4 *>(g + p * g_cs + g_off + 8 * grp);
+    const bf16 *vv = reinterpret_cast<const bf16 *>(&v);
+#pragma unroll
+    for (int k = 0; k < 8; ++k) s[k] += __bfloat162float(vv[k]);
   }
-  for (int o = 16; o > 0; o >>= 1) bs += __shfl_down_sync(0xffffffffu, bs, o);
-  if ((threadIdx.x & 31) == 0) atomicAdd(db, bs);
+  __shared__ float red[8][256];
+#pragma unroll
+  for (int k = 0; k < 8; ++k) red[k][threadIdx.x] = s[k];
+  __syncthreads();
+  if (int(threadIdx.x) < C) {
+    const int q = threadIdx.x >> 3, k = threadIdx.x & 7;
+    float t = 0.f;
+    for (int j = q; j < int(blockDim.x); j += G) t += red[k][j];
+    atomicAdd(&db[threadIdx.x], t);
+  }
 }
 
 // Adam on the FP32 master parameters
@@ -874,6 +924,32 @@ bool up_back_tc(pic_unet *u, int l, bf16 *gin) {
   return conv_upback_tc(c, u->stream) == cudaSuccess;
 }
 
+// weight and bias gradients of the transposed convolution of level l (input
+// hin) on the tensor cores and a vector column sum; false where the kernel does
+// not apply
+bool up_wgrad_tc(pic_unet *u, int l, const bf16 *hin) {
+  if (u->conv_impl != 0) return false;
+  const pic_unet::Up &up = u->up[l];
+  UpWgradTC g;
+  g.in = hin;
+  g.g = u->gcat[l];
+  g.cin = up.cin;
+  g.g_cs = 2 * kC[l];
+  g.g_off = 0;
+  g.cout = up.cout;
+  g.dw = u->G + up.w_off;
+  g.B = u->B;
+  g.H = u->H >> (l + 1);
+  g.W = u->W >> (l + 1);
+  g.err = u->d_err;
+  if (conv_upwgrad_tc(g, u->stream) != cudaSuccess) return false;
+  const long long np = pix(u, l);
+  const long long ppb = 256 / (up.cout / 8);
+  k_colsum<<<int(std::min<long long>((np + ppb - 1) / ppb, 8LL * u->num_sms)), 256, 0, u->stream>>>(
+      u->gcat[l], 2 * kC[l], 0, up.cout, np, u->G + up.b_off);
+  return true;
+}
+
 // the transposed convolution of level l on the tensor cores (GEMM columns in
 // launches of at most 256); false where the kernel does not apply
 bool up_tc(pic_unet *u, int l, const bf16 *in, int in_cs) {
@@ -957,7 +1033,7 @@ void forward(pic_unet *u, const float *x, bool keep_input) {
 void backward(pic_unet *u) {
   const int C3 = kC[3];
   cudaMemsetAsync(u->G, 0, size_t(u->nparam) * 4, u->stream);
-  k_head_back<<<std::min(1024, gridn(pix(u, 0))), 256, 0, u->stream>>>(
+  k_head_back<<<int(std::min<long long>((pix(u, 0) + 63) / 64, 8LL * u->num_sms)), 256, 0, u->stream>>>(
       u->dy, u->dout[0], u->P + u->head_w, u->gdout[0], u->G + u->head_w, u->G + u->head_b, pix(u, 0));
   // decoder, from the output up
   bf16 *g = u->gdout[0];
@@ -974,13 +1050,15 @@ void backward(pic_unet *u) {
     if (!up_back_tc(u, l, gin))
       k_up_back_data<<<gridn((long long)pix(u, l + 1) * up.cin), 256, 0, u->stream>>>(
           u->gcat[l], 2 * C, 0, up.cout, u->P + up.w_off, gin, up.cin, u->B, hl, wl);
-    const int rows = u->B * hl;
-    const int tiles = ((up.cin + 31) / 32) * ((up.cout + 31) / 32) * 4;
-    int groups = std::max(1, std::min(rows, 2048 / tiles));
-    const int rpc = (rows + groups - 1) / groups;
-    groups = (rows + rpc - 1) / rpc;
-    k_up_back_w<<<dim3(groups, ((up.cin + 31) / 32) * ((up.cout + 31) / 32), 4), 256, 0, u->stream>>>(
-        hin, up.cin, u->gcat[l], 2 * C, 0, up.cout, u->G + up.w_off, u->G + up.b_off, u->B, hl, wl, rpc);
+    if (!up_wgrad_tc(u, l, hin)) {
+      const int rows = u->B * hl;
+      const int tiles = ((up.cin + 31) / 32) * ((up.cout + 31) / 32) * 4;
+      int groups = std::max(1, std::min(rows, 2048 / tiles));
+      const int rpc = (rows + groups - 1) / groups;
+      groups = (rows + rpc - 1) / rpc;
+      k_up_back_w<<<dim3(groups, ((up.cin + 31) / 32) * ((up.cout + 31) / 32), 4), 256, 0, u->stream>>>(
+          hin, up.cin, u->gcat[l], 2 * C, 0, up.cout, u->G + up.w_off, u->G + up.b_off, u->B, hl, wl, rpc);
+    }
     g = gin;
   }
   // bottleneck
@@ -1343,6 +1421,61 @@ pic_status pic_conv3x3_wgrad_bf16(int32_t impl, int32_t B, int32_t H, int32_t W,
   g.W = W;
   g.err = err;
   if (picgb::conv_wgrad_tc(g, s) != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+  int e = 0;
+  if (cudaMemcpy(&e, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
+  if (e) {
+    picgb::note(cudaErrorTimeout, ("tcgen05 weight gradient wait " + std::to_string(e)).c_str());
+    return PIC_ETIMEOUT;
+  }
+  return PIC_OK;
+}
+
+pic_status pic_upconv_wgrad_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const void *in, int32_t cin,
+                                 const void *gout, int32_t gout_cs, int32_t gout_off, int32_t cout, float *dw,
+                                 float *db, void *stream) {
+  if (!in || !gout || !dw || !db || B < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 || gout_off < 0 ||
+      gout_off + cout > gout_cs || impl < 0 || impl > 1 || (long long)B * H * W * 4 >= (1LL << 31))
+    return PIC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bf16 *bi = static_cast<const bf16 *>(in), *bg = static_cast<const bf16 *>(gout);
+  if (impl == 1) {
+    const int rows = B * H;
+    const int tiles = ((cin + 31) / 32) * ((cout + 31) / 32) * 4;
+    int groups = std::max(1, std::min(rows, 2048 / tiles));
+    const int rpc = (rows + groups - 1) / groups;
+    groups = (rows + rpc - 1) / rpc;
+    k_up_back_w<<<dim3(groups, ((cin + 31) / 32) * ((cout + 31) / 32), 4), 256, 0, s>>>(
+        bi, cin, bg, gout_cs, gout_off, cout, dw, db, B, H, W, rpc);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+    return PIC_OK;
+  }
+  if (!picgb::conv_upwgrad_tc_supported(cin, cout, gout_cs, gout_off) || cout > 256 ||
+      (reinterpret_cast<uintptr_t>(gout) & 15))
+    return PIC_EINVAL;
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return PIC_ECUDA;
+  int *err = nullptr;
+  if (cudaGetSymbolAddress((void **)&err, g_conv_err) != cudaSuccess) return PIC_ECUDA;
+  if (cudaMemsetAsync(err, 0, 4, s) != cudaSuccess) return PIC_ECUDA;
+  picgb::UpWgradTC g;
+  g.in = bi;
+  g.g = bg;
+  g.cin = cin;
+  g.g_cs = gout_cs;
+  g.g_off = gout_off;
+  g.cout = cout;
+  g.dw = dw;
+  g.B = B;
+  g.H = H;
+  g.W = W;
+  g.err = err;
+  if (picgb::conv_upwgrad_tc(g, s) != cudaSuccess) return PIC_ECUDA;
+  const long long np = 4LL * B * H * W, ppb = 256 / (cout / 8);
+  k_colsum<<<int(std::min<long long>((np + ppb - 1) / ppb, 8LL * sms)), 256, 0, s>>>(bg, gout_cs, gout_off, cout,
+                                                                                   np, db);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
   int e = 0;
   if (cudaMemcpy(&e, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) return PIC_ECUDA;
   if (e) {

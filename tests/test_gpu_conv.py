@@ -290,3 +290,63 @@ def test_conv3x3_weight_gradient_refuses_unsupported_shapes(lib):
     assert st == lib.PIC_EINVAL
     _, st = run_wgrad(lib, 0, d, x, 4, 32)                               # offset not a multiple of 8
     assert st == lib.PIC_EINVAL
+
+
+def run_upwgrad(pg, impl, x, g_full, g_off, cout):
+    """Weight and bias gradients of the 2x2 stride-2 transposed convolution
+    through pic_upconv_wgrad_bf16: x [B,H,W,cin], g_full [B,2H,2W,g_cs] (BF16
+    values); returns (dW [2,2,cin,cout], db [cout]) as float64, status."""
+    import ctypes
+    import torch
+    B, H, W, cin = x.shape
+    g_cs = g_full.shape[3]
+    xd = _dev(x, torch, torch.bfloat16)
+    gd = _dev(g_full, torch, torch.bfloat16)
+    dw = torch.zeros((2, 2, cin, cout), dtype=torch.float32, device="cuda")
+    db = torch.zeros((cout,), dtype=torch.float32, device="cuda")
+    lib = pg.load_library()
+    f = lib.pic_upconv_wgrad_bf16
+    P, I = ctypes.c_void_p, ctypes.c_int32
+    f.argtypes = [I, I, I, I, P, I, P, I, I, I, P, P, P]
+    st = f(impl, B, H, W, xd.data_ptr(), cin, gd.data_ptr(), g_cs, g_off, cout, dw.data_ptr(), db.data_ptr(),
+           torch.cuda.current_stream().cuda_stream)
+    return dw.cpu().numpy().astype(np.float64), db.cpu().numpy().astype(np.float64), st
+
+
+UPW_CASES = [
+    # B, H, W (the layer's input), cin, cout, gout_cs, gout_off
+    # the finest level's shape, batch 2, W = 40 < 64
+    (2, 18, 40, 64, 32, 64, 0),
+    # W = 130: three chunks of 64 input pixels, the last 2
+    (1, 9, 130, 128, 64, 128, 0),
+    # 2 output x 4 input channel blocks
+    (1, 5, 64, 256, 128, 256, 0),
+    # a channel slice of the gradient at an offset
+    (1, 6, 16, 64, 32, 96, 32),
+    # 256 outputs
+    (1, 4, 8, 64, 256, 256, 0),
+]
+
+
+@pytest.mark.parametrize("case", UPW_CASES)
+@pytest.mark.parametrize("impl", [0, 1])
+def test_upconv_weight_gradient_matches_oracle(lib, case, impl):
+    B, H, W, cin, cout, g_cs, g_off = case
+    rng = np.random.default_rng(cin + cout * 5 + W)
+    x = bf16_round(rng.standard_normal((B, H, W, cin)))
+    g_full = bf16_round(rng.standard_normal((B, 2 * H, 2 * W, g_cs)))
+    dw, db, st = run_upwgrad(lib, impl, x, g_full, g_off, cout)
+    assert st == lib.PIC_OK, lib.pic_strerror(st)
+    _, dw_ref, db_ref = ounet.upconv2x2_backward(x, np.zeros((2, 2, cin, cout)), g_full[..., g_off:g_off + cout])
+    rel = np.linalg.norm(dw - dw_ref) / np.linalg.norm(dw_ref)
+    assert rel <= 1e-4, rel
+    assert np.all(np.abs(dw - dw_ref) <= 1e-3 * np.abs(dw_ref).max())
+    assert np.all(np.abs(db - db_ref) <= 1e-3 * np.abs(db_ref).max() + 1e-4 * np.sqrt(4 * B * H * W))
+
+
+def test_upconv_weight_gradient_refuses_unsupported_shapes(lib):
+    x = np.zeros((1, 4, 8, 48))
+    _, _, st = run_upwgrad(lib, 0, x, np.zeros((1, 8, 16, 32)), 0, 32)     # cin 48
+    assert st == lib.PIC_EINVAL
+    _, _, st = run_upwgrad(lib, 0, np.zeros((1, 4, 8, 64)), np.zeros((1, 8, 16, 96)), 0, 96)   # cout 96
+    assert st == lib.PIC_EINVAL
