@@ -452,6 +452,22 @@ pic_status pic_conv3x3_wgrad_bf16(int32_t impl, int32_t B, int32_t H, int32_t W,
                                   const void *in, int32_t in_cs, int32_t in_off, int32_t cin, int32_t cout,
                                   float *dw, void *stream);
 
+/* The U-Net's 2x2 stride-2 transposed convolution (its upsampling layer):
+ * out[b][2y + a][2x + c][out_off + co] = bias[co] + sum_{ci}
+ *   in[b][y][x][ci] * w[a][c][ci][co],  a, c in {0, 1}.
+ * in: DEVICE BF16 [B][H][W][cin] (contiguous); w: DEVICE FP32
+ * [2][2][cin][cout] (the layer's parameter order); bias: DEVICE FP32 [cout];
+ * out: DEVICE BF16 NHWC [B][2H][2W] with channel stride out_cs.  impl 0:
+ * tcgen05 tensor cores on a BF16 copy of w (a temporary device buffer; cin a
+ * multiple of 16, cout 16, 32 or a multiple of 64, out_cs and out_off
+ * multiples of 8, W >= 8, else PIC_EINVAL); impl 1: CUDA cores with the
+ * FP32 weights.  FP32
+ * accumulation, BF16 rounding of the result.  Synchronous on `stream`;
+ * PIC_ETIMEOUT if a bounded wait of the tensor-core kernel gave up. */
+pic_status pic_upconv_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const void *in, int32_t cin,
+                           const float *w, const float *bias, void *out, int32_t out_cs, int32_t out_off,
+                           int32_t cout, void *stream);
+
 /* The weight and bias gradients of the U-Net's 2x2 stride-2 transposed
  * convolution: dw[a][c][ci][co] += sum_{b, y, x} in[b][y][x][ci] *
  *   gout[b][2y + a][2x + c][gout_off + co], db[co] += sum over all gout

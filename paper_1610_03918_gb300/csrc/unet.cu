@@ -1430,6 +1430,63 @@ pic_status pic_conv3x3_wgrad_bf16(int32_t impl, int32_t B, int32_t H, int32_t W,
   return PIC_OK;
 }
 
+pic_status pic_upconv_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const void *in, int32_t cin,
+                           const float *w, const float *bias, void *out, int32_t out_cs, int32_t out_off,
+                           int32_t cout, void *stream) {
+  if (!in || !w || !bias || !out || B < 1 || H < 1 || W < 1 || cin < 1 || cout < 1 || out_off < 0 ||
+      out_off + cout > out_cs || impl < 0 || impl > 1 || (long long)B * H * W * 4 >= (1LL << 31))
+    return PIC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const bf16 *bi = static_cast<const bf16 *>(in);
+  bf16 *bo = static_cast<bf16 *>(out);
+  if (impl == 1) {
+    k_up_fwd<<<gridn(4LL * B * H * W * cout), 256, 0, s>>>(bi, cin, w, bias, bo, out_cs, out_off, cout, B, H, W);
+    if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+    return PIC_OK;
+  }
+  const int total = 4 * cout, step = total > 256 ? 256 : total;
+  if (total % step || cout % 16 || !picgb::conv3x3_tc_supported(cin, step, cin, 0, out_cs, out_off, W))
+    return PIC_EINVAL;
+  int *err = nullptr;
+  if (cudaGetSymbolAddress((void **)&err, g_conv_err) != cudaSuccess) return PIC_ECUDA;
+  bf16 *wt = nullptr;
+  if (cudaMalloc(&wt, size_t(total) * cin * 2) != cudaSuccess) return PIC_ENOMEM;
+  k_upw_to_bf16<<<gridn(4LL * cout * cin), 256, 0, s>>>(w, wt, cin, cout);
+  picgb::ConvTC c;
+  c.in = bi;
+  c.in_cs = cin;
+  c.in_off = 0;
+  c.cin = cin;
+  c.w = wt;
+  c.bias = bias;
+  c.out = bo;
+  c.out_cs = out_cs;
+  c.out_off = out_off;
+  c.B = B;
+  c.H = H;
+  c.W = W;
+  c.relu = 0;
+  c.err = err;
+  c.up_cout = cout;
+  pic_status st = (cudaGetLastError() == cudaSuccess && cudaMemsetAsync(err, 0, 4, s) == cudaSuccess) ? PIC_OK
+                                                                                                   : PIC_ECUDA;
+  for (int n0 = 0; st == PIC_OK && n0 < total; n0 += step) {
+    c.cout = step;
+    c.n_base = n0;
+    if (picgb::conv3x3_tc(c, s) != cudaSuccess) st = PIC_ECUDA;
+  }
+  if (st == PIC_OK && cudaStreamSynchronize(s) != cudaSuccess) st = PIC_ECUDA;
+  int e = 0;
+  if (st == PIC_OK && cudaMemcpy(&e, err, 4, cudaMemcpyDeviceToHost) != cudaSuccess) st = PIC_ECUDA;
+  cudaStreamSynchronize(s);
+  cudaFree(wt);
+  if (st == PIC_OK && e) {
+    picgb::note(cudaErrorTimeout, ("tcgen05 convolution wait " + std::to_string(e)).c_str());
+    st = PIC_ETIMEOUT;
+  }
+  return st;
+}
+
 pic_status pic_upconv_wgrad_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const void *in, int32_t cin,
                                  const void *gout, int32_t gout_cs, int32_t gout_off, int32_t cout, float *dw,
                                  float *db, void *stream) {

@@ -350,3 +350,53 @@ def test_upconv_weight_gradient_refuses_unsupported_shapes(lib):
     assert st == lib.PIC_EINVAL
     _, _, st = run_upwgrad(lib, 0, np.zeros((1, 4, 8, 64)), np.zeros((1, 8, 16, 96)), 0, 96)   # cout 96
     assert st == lib.PIC_EINVAL
+
+
+def run_upconv(pg, impl, x, Wup, bias, out_cs, out_off):
+    """The 2x2 stride-2 transposed convolution through pic_upconv_bf16: x
+    [B,H,W,cin] (BF16 values), Wup [2,2,cin,cout], bias [cout]; returns (the
+    output buffer [B,2H,2W,out_cs] as float64, status)."""
+    import ctypes
+    import torch
+    B, H, W, cin = x.shape
+    cout = Wup.shape[3]
+    xd = _dev(x, torch, torch.bfloat16)
+    wd = _dev(Wup, torch, torch.float32)
+    bd = _dev(bias, torch, torch.float32)
+    od = torch.full((B, 2 * H, 2 * W, out_cs), 7.0, dtype=torch.bfloat16, device="cuda")
+    lib = pg.load_library()
+    f = lib.pic_upconv_bf16
+    P, I = ctypes.c_void_p, ctypes.c_int32
+    f.argtypes = [I, I, I, I, P, I, P, P, P, I, I, I, P]
+    st = f(impl, B, H, W, xd.data_ptr(), cin, wd.data_ptr(), bd.data_ptr(), od.data_ptr(), out_cs, out_off, cout,
+           torch.cuda.current_stream().cuda_stream)
+    return od.float().cpu().numpy().astype(np.float64), st
+
+
+UPF_CASES = [
+    # B, H, W (the layer's input), cin, cout, out_cs, out_off
+    (2, 9, 20, 64, 32, 64, 0),       # the finest level into the first half of a concatenation
+    (1, 5, 130, 128, 64, 128, 0),    # 128-wide tiles, the second ragged
+    (1, 4, 64, 256, 128, 256, 0),    # 512 GEMM columns in two launches
+    (1, 6, 16, 32, 16, 48, 16),      # an offset slice, cout 16
+]
+
+
+@pytest.mark.parametrize("case", UPF_CASES)
+@pytest.mark.parametrize("impl", [0, 1])
+def test_upconv_layer_matches_oracle(lib, case, impl):
+    B, H, W, cin, cout, out_cs, out_off = case
+    rng = np.random.default_rng(cin * 3 + cout + W)
+    x = bf16_round(rng.standard_normal((B, H, W, cin)))
+    Wup = bf16_round(rng.standard_normal((2, 2, cin, cout)) / np.sqrt(cin))
+    bias = rng.standard_normal(cout) * 0.1
+    out, st = run_upconv(lib, impl, x, Wup, bias, out_cs, out_off)
+    assert st == lib.PIC_OK, lib.pic_strerror(st)
+    ref = ounet.upconv2x2(x, Wup, bias)
+    got = out[..., out_off:out_off + cout]
+    rel = np.linalg.norm(got - ref) / np.linalg.norm(ref)
+    cos = float((got * ref).sum() / (np.linalg.norm(got) * np.linalg.norm(ref)))
+    assert rel <= 4e-3 and cos >= 0.99999, (rel, cos)
+    assert np.all(np.abs(got - ref) <= 2.0 ** -8 * np.abs(ref) + 1e-3 * np.abs(ref).max())
+    rest = np.delete(out, np.s_[out_off:out_off + cout], axis=3)
+    assert np.all(rest == 7.0)
