@@ -452,6 +452,39 @@ pic_status pic_conv3x3_wgrad_bf16(int32_t impl, int32_t B, int32_t H, int32_t W,
                                   const void *in, int32_t in_cs, int32_t in_off, int32_t cin, int32_t cout,
                                   float *dw, void *stream);
 
+/* The U-Net's 2x2 average pool: out[b][y][x][c] = BF16(0.25 * sum_{a, d in
+ * {0, 1}} in[b][2y + a][2x + d][in_off + c]) (FP32 sum).  in: DEVICE BF16
+ * NHWC [B][H][W] with channel stride in_cs; out: DEVICE BF16
+ * [B][H/2][W/2][C] (contiguous).  H and W even; C, in_cs and in_off
+ * multiples of 8; both pointers 16-byte aligned; else PIC_EINVAL.
+ * Synchronous on `stream`. */
+pic_status pic_avgpool2_bf16(int32_t B, int32_t H, int32_t W, const void *in, int32_t in_cs, int32_t in_off,
+                             int32_t C, void *out, void *stream);
+/* The U-Net's 1x1 head on its 32 last channels: y[p] = b[0] + sum_{c < 32}
+ * hin[p][c] w[c] (FP32).  hin: DEVICE BF16 [npix][32], 16-byte aligned; w:
+ * DEVICE FP32 [32]; b: DEVICE FP32 [1]; y: DEVICE FP32 [npix].  Synchronous
+ * on `stream`. */
+pic_status pic_head_bf16(int64_t npix, const void *hin, const float *w, const float *b, float *y, void *stream);
+/* Its backward: gh[p][c] = BF16(dy[p] w[c]), dw[c] += sum_p dy[p] hin[p][c],
+ * db[0] += sum_p dy[p] (FP32, atomic adds in a varying order).  dy: DEVICE
+ * FP32 [npix]; gh: DEVICE BF16 [npix][32], 16-byte aligned; dw, db: DEVICE
+ * FP32, ADDED to.  Synchronous on `stream`. */
+pic_status pic_head_back_bf16(int64_t npix, const float *dy, const void *hin, const float *w, void *gh, float *dw,
+                              float *db, void *stream);
+/* Backward through a ReLU, with the bias gradient of the convolution before
+ * it: dpre[p][c] = y[p][off_y + c] > 0 ? t[p][c] : 0 and db[c] += sum_p
+ * dpre[p][c], where t = g[p][g_off + c], or, with gp (the gradient of the
+ * 2x2 average pool that follows y, DEVICE BF16 [B][H/2][W/2][C]),
+ * t = BF16(g[p][g_off + c] + 0.25 gp[parent of p][c]).  g, y: DEVICE BF16
+ * NHWC [B][H][W] with channel strides g_cs, y_cs; dpre: DEVICE BF16
+ * [B][H][W][C]; db: DEVICE FP32 [C], ADDED to (atomic adds in a varying
+ * order).  C 8, 16, 32, 64, 128 or 256; strides and offsets multiples of 8;
+ * pointers 16-byte aligned; H and W even with gp; else PIC_EINVAL.
+ * Synchronous on `stream`. */
+pic_status pic_relu_back_bf16(int32_t B, int32_t H, int32_t W, const void *g, int32_t g_cs, int32_t g_off,
+                              const void *y, int32_t y_cs, int32_t y_off, const void *gp, void *dpre, int32_t C,
+                              float *db, void *stream);
+
 /* The U-Net's 2x2 stride-2 transposed convolution (its upsampling layer):
  * out[b][2y + a][2x + c][out_off + co] = bias[co] + sum_{ci}
  *   in[b][y][x][ci] * w[a][c][ci][co],  a, c in {0, 1}.

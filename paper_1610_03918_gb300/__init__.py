@@ -41,7 +41,8 @@ EXPORTED = ("pic_init", "pic_load", "pic_step", "pic_set_timing", "pic_diag", "p
             "pic_learned_target", "pic_set_warm_start", "pic_step_particles", "pic_step_fields",
             "pic_exchange_buffer", "pic_exchange_sum", "pic_autotune", "pic_unet_set_conv_impl",
             "pic_unet_status", "pic_conv3x3_bf16", "pic_upconv_back_bf16",
-            "pic_conv3x3_wgrad_bf16", "pic_upconv_wgrad_bf16", "pic_upconv_bf16")
+            "pic_conv3x3_wgrad_bf16", "pic_upconv_wgrad_bf16", "pic_upconv_bf16", "pic_avgpool2_bf16",
+            "pic_head_bf16", "pic_head_back_bf16", "pic_relu_back_bf16")
 
 ALLOC_FN = ctypes.CFUNCTYPE(ctypes.c_void_p, ctypes.c_size_t, ctypes.c_void_p, ctypes.c_void_p)
 FREE_FN = ctypes.CFUNCTYPE(None, ctypes.c_void_p, ctypes.c_void_p, ctypes.c_void_p)
@@ -166,7 +167,8 @@ def load_library():
                  "pic_learned_target", "pic_set_warm_start", "pic_step_particles", "pic_step_fields",
             "pic_exchange_buffer", "pic_exchange_sum", "pic_autotune", "pic_unet_set_conv_impl",
             "pic_unet_status", "pic_conv3x3_bf16", "pic_upconv_back_bf16",
-            "pic_conv3x3_wgrad_bf16", "pic_upconv_wgrad_bf16", "pic_upconv_bf16"):
+            "pic_conv3x3_wgrad_bf16", "pic_upconv_wgrad_bf16", "pic_upconv_bf16", "pic_avgpool2_bf16",
+            "pic_head_bf16", "pic_head_back_bf16", "pic_relu_back_bf16"):
         getattr(lib, name).restype = ctypes.c_int
     for name in ("pic_unet_create", "pic_unet_set_params", "pic_unet_get_params",
                  "pic_unet_forward", "pic_unet_gradients", "pic_unet_train_step", "pic_unet_free"):

@@ -1430,6 +1430,74 @@ pic_status pic_conv3x3_wgrad_bf16(int32_t impl, int32_t B, int32_t H, int32_t W,
   return PIC_OK;
 }
 
+namespace {
+int device_sms() {
+  int dev = 0, sms = 0;
+  if (cudaGetDevice(&dev) != cudaSuccess ||
+      cudaDeviceGetAttribute(&sms, cudaDevAttrMultiProcessorCount, dev) != cudaSuccess)
+    return 0;
+  return sms;
+}
+bool aligned16(const void *p) { return (reinterpret_cast<uintptr_t>(p) & 15) == 0; }
+}  // namespace
+
+pic_status pic_avgpool2_bf16(int32_t B, int32_t H, int32_t W, const void *in, int32_t in_cs, int32_t in_off,
+                             int32_t C, void *out, void *stream) {
+  if (!in || !out || B < 1 || H < 2 || W < 2 || (H % 2) || (W % 2) || C < 8 || C % 8 || in_cs % 8 ||
+      in_off % 8 || in_off < 0 || in_off + C > in_cs || !aligned16(in) || !aligned16(out) ||
+      (long long)B * H * W >= (1LL << 31))
+    return PIC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_pool_vec<<<gridn((long long)B * (H / 2) * (W / 2) * (C / 8)), 256, 0, s>>>(
+      static_cast<const bf16 *>(in), in_cs, in_off, static_cast<bf16 *>(out), C, B, H, W);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+  return PIC_OK;
+}
+
+pic_status pic_head_bf16(int64_t npix, const void *hin, const float *w, const float *b, float *y, void *stream) {
+  if (!hin || !w || !b || !y || npix < 1 || !aligned16(hin)) return PIC_EINVAL;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_head_vec<<<gridn(npix), 256, 0, s>>>(static_cast<const bf16 *>(hin), w, b, y, npix);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+  return PIC_OK;
+}
+
+pic_status pic_head_back_bf16(int64_t npix, const float *dy, const void *hin, const float *w, void *gh, float *dw,
+                              float *db, void *stream) {
+  if (!dy || !hin || !w || !gh || !dw || !db || npix < 1 || !aligned16(hin) || !aligned16(gh)) return PIC_EINVAL;
+  const int sms = device_sms();
+  if (sms < 1) return PIC_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  k_head_back<<<int(std::min<long long>((npix + 63) / 64, 8LL * sms)), 256, 0, s>>>(
+      dy, static_cast<const bf16 *>(hin), w, static_cast<bf16 *>(gh), dw, db, npix);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+  return PIC_OK;
+}
+
+pic_status pic_relu_back_bf16(int32_t B, int32_t H, int32_t W, const void *g, int32_t g_cs, int32_t g_off,
+                              const void *y, int32_t y_cs, int32_t y_off, const void *gp, void *dpre, int32_t C,
+                              float *db, void *stream) {
+  if (!g || !y || !dpre || !db || B < 1 || H < 1 || W < 1 || !(C == 8 || C == 16 || C == 32 || C == 64 ||
+      C == 128 || C == 256) || g_cs % 8 || g_off % 8 || y_cs % 8 || y_off % 8 || g_off < 0 || y_off < 0 ||
+      g_off + C > g_cs || y_off + C > y_cs || !aligned16(g) || !aligned16(y) || !aligned16(dpre) ||
+      (gp && (!aligned16(gp) || (H % 2) || (W % 2))) || (long long)B * H * W >= (1LL << 31))
+    return PIC_EINVAL;
+  const int sms = device_sms();
+  if (sms < 1) return PIC_ECUDA;
+  cudaStream_t s = static_cast<cudaStream_t>(stream);
+  const long long np = (long long)B * H * W, ppb = 256 / (C / 8);
+  const int grid = int(std::min<long long>((np + ppb - 1) / ppb, 8LL * sms));
+  const bf16 *bg = static_cast<const bf16 *>(g), *by = static_cast<const bf16 *>(y);
+  if (gp)
+    k_relu_back<true><<<grid, 256, 0, s>>>(bg, g_cs, g_off, by, y_cs, y_off, static_cast<const bf16 *>(gp), H, W,
+                                           static_cast<bf16 *>(dpre), C, np, db);
+  else
+    k_relu_back<false><<<grid, 256, 0, s>>>(bg, g_cs, g_off, by, y_cs, y_off, nullptr, 1, 1,
+                                            static_cast<bf16 *>(dpre), C, np, db);
+  if (cudaGetLastError() != cudaSuccess || cudaStreamSynchronize(s) != cudaSuccess) return PIC_ECUDA;
+  return PIC_OK;
+}
+
 pic_status pic_upconv_bf16(int32_t impl, int32_t B, int32_t H, int32_t W, const void *in, int32_t cin,
                            const float *w, const float *bias, void *out, int32_t out_cs, int32_t out_off,
                            int32_t cout, void *stream) {
