@@ -88,3 +88,31 @@ def test_init_rejects_bad_recycling_source_without_gpu(lib):
         assert pg.load_library().pic_init(ctypes.byref(cfg), ctypes.byref(ctx)) == pg.PIC_EINVAL
     cfg = pg.make_config(synth.small_trench().replace(phi_rf_amp=float("nan"), omega_rf=0.1))
     assert pg.load_library().pic_init(ctypes.byref(cfg), ctypes.byref(ctx)) == pg.PIC_EINVAL
+
+
+def test_layer_entries_reject_bad_arguments_without_gpu(lib):
+    # argument checks come before any CUDA call: null pointers, empty or
+    # inconsistent shapes and unknown implementations are refused on the host
+    import paper_1610_03918_gb300 as pg
+    L = pg.load_library()
+    P, I, Q = ctypes.c_void_p, ctypes.c_int32, ctypes.c_int64
+    fake = ctypes.c_void_p(16)                 # never dereferenced: the call is refused first
+    L.pic_conv3x3_wgrad_bf16.argtypes = [I, I, I, I, P, P, I, I, I, I, P, P]
+    assert L.pic_conv3x3_wgrad_bf16(0, 1, 8, 8, None, fake, 32, 0, 32, 32, fake, None) == pg.PIC_EINVAL
+    assert L.pic_conv3x3_wgrad_bf16(2, 1, 8, 8, fake, fake, 32, 0, 32, 32, fake, None) == pg.PIC_EINVAL
+    assert L.pic_conv3x3_wgrad_bf16(0, 1, 8, 8, fake, fake, 32, 8, 32, 32, fake, None) == pg.PIC_EINVAL
+    L.pic_upconv_back_bf16.argtypes = [I, I, I, I, P, I, I, I, P, P, I, P]
+    assert L.pic_upconv_back_bf16(0, 0, 8, 8, fake, 64, 0, 32, fake, fake, 64, None) == pg.PIC_EINVAL
+    assert L.pic_upconv_back_bf16(0, 1, 8, 8, fake, 32, 16, 32, fake, fake, 64, None) == pg.PIC_EINVAL
+    L.pic_upconv_wgrad_bf16.argtypes = [I, I, I, I, P, I, P, I, I, I, P, P, P]
+    assert L.pic_upconv_wgrad_bf16(0, 1, 8, 8, fake, 64, fake, 64, 0, 32, fake, None, None) == pg.PIC_EINVAL
+    L.pic_upconv_bf16.argtypes = [I, I, I, I, P, I, P, P, P, I, I, I, P]
+    assert L.pic_upconv_bf16(1, 1, 8, 8, fake, 64, fake, fake, fake, 32, 8, 32, None) == pg.PIC_EINVAL
+    L.pic_avgpool2_bf16.argtypes = [I, I, I, P, I, I, I, P, P]
+    assert L.pic_avgpool2_bf16(1, 7, 8, fake, 32, 0, 32, fake, None) == pg.PIC_EINVAL
+    L.pic_head_bf16.argtypes = [Q, P, P, P, P, P]
+    assert L.pic_head_bf16(0, fake, fake, fake, fake, None) == pg.PIC_EINVAL
+    L.pic_head_back_bf16.argtypes = [Q, P, P, P, P, P, P, P]
+    assert L.pic_head_back_bf16(10, fake, ctypes.c_void_p(18), fake, fake, fake, fake, None) == pg.PIC_EINVAL
+    L.pic_relu_back_bf16.argtypes = [I, I, I, P, I, I, P, I, I, P, P, I, P, P]
+    assert L.pic_relu_back_bf16(1, 8, 8, fake, 24, 0, fake, 24, 0, None, fake, 24, fake, None) == pg.PIC_EINVAL
