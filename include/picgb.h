@@ -411,12 +411,13 @@ pic_status pic_unet_gradients(pic_unet *u, const float *x, const float *t, float
 pic_status pic_unet_train_step(pic_unet *u, const float *x, const float *t, float lr, double *loss);
 pic_status pic_unet_free(pic_unet *u);
 
-/* The U-Net's 3x3 convolutions run on the fifth-generation tensor cores
- * (tcgen05.mma, FP32 accumulators in tensor memory, operands staged by TMA)
- * wherever the shapes allow -- cin a multiple of 16, cout 32, 64, 128 or 256,
- * channel strides and offsets multiples of 8 -- and on the mma.sync path
- * otherwise; impl 1 selects mma.sync for all of them (impl 0: the default).
- * Synchronous. */
+/* The U-Net's contractions -- the 3x3 and transposed 2x2 convolutions, their
+ * data gradients and their weight gradients -- run on the fifth-generation
+ * tensor cores (tcgen05.mma, FP32 accumulators in tensor memory, operands
+ * staged by TMA) wherever the shapes allow (the network's own shapes always
+ * do when each level is at least 8 wide), and on the mma.sync / CUDA-core
+ * kernels otherwise; impl 1 selects those for all of them (impl 0: the
+ * default).  Synchronous. */
 pic_status pic_unet_set_conv_impl(pic_unet *u, int32_t impl);
 /* PIC_ETIMEOUT (and clears it) if a bounded wait of a tensor-core kernel of
  * this network gave up since the last call; waits for the net's stream. */

@@ -647,8 +647,9 @@ class Unet:
         self.nparam = int(lib.pic_unet_num_params(h))
 
     def set_conv_impl(self, impl: int):
-        """3x3 convolutions on the tcgen05 tensor cores where the shapes allow
-        (0, the default) or all on the mma.sync kernel (1)."""
+        """Convolutions and their data and weight gradients on the tcgen05
+        tensor cores where the shapes allow (0, the default), or all on the
+        mma.sync and CUDA-core kernels (1)."""
         st = load_library().pic_unet_set_conv_impl(self.h, int(impl))
         if st != PIC_OK:
             raise PicError(st, "pic_unet_set_conv_impl")
