@@ -22,6 +22,10 @@
 // add the bias, apply the activation and store BF16.  Every wait is bounded:
 // a wait that gives up sets the error word and the CTA winds down (releasing
 // its TMEM) instead of hanging.
+//
+// The same kernel, in further modes, computes the 2x2 stride-2 transposed
+// convolution and its data gradient; k_wgrad_tc below computes the weight
+// gradients of both kinds of convolution with both operands MN-major.
 #include <cuda.h>
 #include <cuda_bf16.h>
 #include <cuda_runtime.h>
@@ -508,7 +512,8 @@ __global__ void __launch_bounds__(kThreads, 1)
 // g its output gradient.  The four slots of A are the four children's tiles
 // of g (5-D boxes {CO, 1, 64, 1, 1} of g viewed as {channels, c, x, a, rows}),
 // B is the input row without a shift (N = CI), and D row (t, co), column ci
-// holds dW[t][ci][co].
+// holds dW[t][ci][co]; the epilogue adds it with scalar atomics, consecutive
+// lanes on consecutive co.
 constexpr int kWKP = 64;   // pixels per K block
 
 template <int CO, int CI, int STAGES, bool UPW = false>
